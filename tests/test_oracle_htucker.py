@@ -1,0 +1,140 @@
+"""Pins of the Sub-R-RtL-HT oracle (Alg. 2): the paper's order-8 dimension tree
+(tests/golden), the transfer-tensor and root definitions written with explicit
+Kronecker products, the full-sampling case that reduces to deterministic RtL-HT,
+exact recovery of tensors of known hierarchical rank, nestedness, and the
+float32 input generator of the 1/||x|| workload."""
+
+import itertools
+import os
+
+import numpy as np
+
+import synth
+from oracle import brute, htucker, tucker
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_tree_matches_paper_figure_d8():
+    with open(os.path.join(GOLDEN, "dimtree_d8.txt")) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    tree = htucker.balanced_tree(8)
+    assert len(tree) == len(rows) == 15
+    for (nid, modes, bname), nd in zip(rows, tree):
+        want = [int(m) - 1 for m in modes.split(",")]
+        assert int(nid) == nd.id
+        assert list(range(nd.a, nd.b + 1)) == want
+        assert (bname != "-") == (not nd.is_leaf)
+    # 14 node bases, 7 transfer tensors (Sec. 4.2.2)
+    assert sum(1 for nd in tree if nd.id != 0) == 14
+    assert sum(1 for nd in tree if not nd.is_leaf) == 7
+    for nd in tree:
+        if not nd.is_leaf:
+            l, r = tree[nd.left], tree[nd.right]
+            assert (l.a, r.b) == (nd.a, nd.b) and l.b + 1 == r.a
+
+
+def test_tree_definition_properties_other_orders():
+    for d in range(2, 12):
+        tree = htucker.balanced_tree(d)
+        leaves = sorted(nd.a for nd in tree if nd.is_leaf)
+        assert leaves == list(range(d)) and len(tree) == 2 * d - 1
+        depth = max(nd.level for nd in tree)
+        assert depth == int(np.ceil(np.log2(d)))  # z = ceil(log2 d), Sec. 4
+
+
+def test_transfer_and_root_tensors_match_kronecker_definition():
+    rs = np.random.default_rng(1)
+    Ul, Ur = rs.standard_normal((3, 2)), rs.standard_normal((4, 3))
+    US = rs.standard_normal((12, 2))
+    B = htucker.transfer_tensor(US, Ul, Ur)
+    for i, j, k in itertools.product(range(2), range(2), range(3)):
+        assert np.isclose(B[i, j, k], US[:, i] @ np.kron(Ul[:, j], Ur[:, k]), rtol=1e-13, atol=1e-13)
+    X = rs.standard_normal((3, 2, 2, 2))  # R_l = modes {0,1} (6 rows), R_r = {2,3} (4)
+    Vl, Vr = rs.standard_normal((6, 2)), rs.standard_normal((4, 3))
+    BR = htucker.root_transfer(X, Vl, Vr)
+    for j, k in itertools.product(range(2), range(3)):
+        assert np.isclose(BR[0, j, k], X.ravel() @ np.kron(Vl[:, j], Vr[:, k]), rtol=1e-13, atol=1e-13)
+
+
+def test_full_sampling_reduces_to_deterministic_rtl_ht():
+    # w_S = n_{notin S} and r_S + p = n_S at every node: each U_S is the dominant
+    # left singular basis of X^(S), i.e. deterministic RtL-HT (Sec. 4)
+    rs = np.random.default_rng(2)
+    X = rs.standard_normal((3, 4, 3, 4))
+    tree = htucker.balanced_tree(4)
+    p = 1
+    ranks = [1] + [htucker.node_rows(X.shape, nd) - p for nd in tree[1:]]
+    w = [0] + [htucker.node_cols(X.shape, nd) for nd in tree[1:]]
+    out = htucker.sub_r_rtl_ht(X, ranks, p, w=w, seed=5)
+    ref = brute.rtl_ht(X, ranks)
+    for nd in tree[1:]:
+        assert np.abs(out["US"][nd.id] - ref["US"][nd.id]).max() < 1e-10
+    for nd in tree:
+        if not nd.is_leaf:
+            assert np.abs(out["B"][nd.id] - ref["B"][nd.id]).max() < 1e-10
+
+
+def _random_ht_tensor(shape, r, seed):
+    """Tensor built from a random H-Tucker format of hierarchical rank <= r."""
+    rs = np.random.default_rng(seed)
+    tree = htucker.balanced_tree(len(shape))
+    U = [synth.haar(n, r, rs) for n in shape]
+    B = [None] * len(tree)
+    for nd in tree:
+        if nd.is_leaf:
+            continue
+        rout = 1 if nd.id == 0 else r
+        B[nd.id] = rs.standard_normal((rout, r, r))
+    return htucker.reconstruct(U, B, tree, shape)
+
+
+def test_exact_recovery_of_known_hierarchical_rank():
+    shape = (5, 6, 4, 5, 6)
+    X = _random_ht_tensor(shape, 2, 3)
+    out = htucker.sub_r_rtl_ht(X, 2, p=2, seed=7)
+    Xh = htucker.reconstruct(out["U"], out["B"], out["tree"], shape)
+    assert tucker.relerr(X, Xh) < 1e-10
+    # nestedness Range(U_S) in Range(U_l (x) U_r) (Sec. 4)
+    for nd in out["tree"]:
+        if nd.is_leaf or nd.id == 0:
+            continue
+        K = np.kron(out["US"][nd.left], out["US"][nd.right])
+        res = out["US"][nd.id] - K @ (K.T @ out["US"][nd.id])
+        assert np.abs(res).max() < 1e-10
+    for nd in out["tree"][1:]:
+        U = out["US"][nd.id]
+        assert np.abs(U.T @ U - np.eye(U.shape[1])).max() < 1e-13
+
+
+def test_full_rank_format_reconstructs_exactly():
+    rs = np.random.default_rng(4)
+    X = rs.standard_normal((2, 3, 2, 2))
+    tree = htucker.balanced_tree(4)
+    ranks = [1] + [htucker.node_rows(X.shape, nd) for nd in tree[1:]]
+    ref = brute.rtl_ht(X, ranks)
+    Xh = htucker.reconstruct(ref["U"], ref["B"], tree, X.shape)
+    assert np.abs(Xh - X).max() < 1e-12
+
+
+def test_inv_norm_generator_matches_definition():
+    # X(i) = (sum_j x_{i_j}^2)^{-1/2} on the uniform grid over [1, 2]^d (Sec. 4.2.1)
+    n, d = 5, 4
+    X = synth.inv_norm_tensor(n, d)
+    x = np.linspace(1.0, 2.0, n)
+    for i in itertools.product(range(n), repeat=d):
+        want = 1.0 / np.sqrt(sum(x[v] ** 2 for v in i))
+        assert abs(float(X[i]) - want) <= 6e-8 * want
+    # entries at arbitrary indices agree bit-for-bit with the full tensor
+    rs = np.random.default_rng(0)
+    idx = tuple(rs.integers(0, n, size=50) for _ in range(d))
+    assert np.array_equal(synth.inv_norm_entries(idx, n), X[idx])
+
+
+def test_inv_norm_workload_ht_runs_and_is_accurate():
+    # small restriction of the 1/||x|| workload; the paper reports no bound for
+    # Sub-R-RtL-HT (Sec. 4), so only sanity: error well below 1e-2 at rank 5
+    X = synth.inv_norm_tensor(8, 6).astype(np.float64)
+    out = htucker.sub_r_rtl_ht(X, 5, p=3, seed=3)
+    Xh = htucker.reconstruct(out["U"], out["B"], out["tree"], X.shape)
+    assert tucker.relerr(X, Xh) < 1e-2
