@@ -1,0 +1,182 @@
+/*
+ * rtucker.h - C ABI of the GB300 (sm_103a) library for the subsampled
+ * randomized Tucker and H-Tucker decompositions of arXiv 2603.21379
+ * ("A practical mode-parallel implementation of the (H-)Tucker decomposition
+ * via randomization").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Tensors are dense and in C order (last mode fastest).  Modes are numbered
+ *   0..d-1 (the paper numbers them 1..d).  The mode-k unfolding X^(k) of
+ *   Sec. 2.2 uses the natural (C-order) linear index of the other modes for its
+ *   columns; the set unfolding X^(S) of a contiguous mode range S has the
+ *   C-order index over S as rows.
+ * - Pointers named X, Z, U, G, B, idx are DEVICE pointers owned by the caller;
+ *   size arrays (n, r, s, w, rank) are HOST arrays.  Outputs are float32,
+ *   row-major.  X must be aligned to its element size.
+ * - Calls are asynchronous on the handle's stream.  The returned status covers
+ *   argument checks and launches.  Errors found on the device (a bounded loop
+ *   that ran out, a numerical breakdown) are recorded in a device status word
+ *   and returned by rt_sync() or by the next call on the handle.
+ * - Workspace: the handle owns one device workspace (cudaMalloc), grown on
+ *   demand and freed by rt_destroy().  A failed allocation returns RT_ENOMEM
+ *   and leaves the outputs untouched.  There is no CPU fallback: every step of
+ *   the computation runs in the library's CUDA kernels.
+ * - Random streams: fiber indices and Gaussian test matrices are drawn from a
+ *   64-bit seed with Philox4x32-10 (Salmon et al., SC'11): the sample of
+ *   column indices is a keyed Feistel permutation of [0, N) restricted by
+ *   cycle-walking (uniform without repetition, Sec. 3.1), and entry (j, c) of
+ *   Omega is the Box-Muller normal keyed by the sampled column index pi(j) and
+ *   c.  Stream id "node" = mode k for Tucker, the dimension-tree node id for
+ *   H-Tucker.
+ */
+#ifndef RTUCKER_H
+#define RTUCKER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RT_OK = 0,
+  RT_EINVAL = 1,    /* an argument is out of range (message in rt_last_error) */
+  RT_ENOMEM = 2,    /* device workspace allocation failed                      */
+  RT_ECUDA = 3,     /* a CUDA runtime call or launch failed                    */
+  RT_ETIMEOUT = 4,  /* a bounded device loop ran out (status word)             */
+  RT_EDEVICE = 5,   /* a device-side check failed (status word)                */
+  RT_ENUMERIC = 6,  /* numerical breakdown (non-finite value) on the device     */
+  RT_ENOTSUP = 7    /* valid but unsupported combination                       */
+} rt_status;
+
+typedef enum { RT_F32 = 0, RT_F64 = 1, RT_BF16 = 2 } rt_dtype; /* storage type of X */
+
+typedef enum {
+  RT_PREC_FP32 = 0, /* float32 arithmetic throughout (default)                 */
+  RT_PREC_BF16 = 1  /* bfloat16 sketch / multi-TTM operands, float32 accumulate */
+} rt_prec;
+
+typedef struct rt_handle_s* rt_handle;
+
+typedef struct {
+  int32_t prec;        /* rt_prec                                              */
+  int32_t use_graph;   /* 1: capture the launch sequence in a CUDA graph once per
+                          shape and replay it (pointers must stay the same)      */
+  int32_t reserved[6]; /* must be zero                                          */
+} rt_options;
+
+/* ----------------------------------------------------------- handle
+ * rt_create: new handle bound to `stream` (a cudaStream_t; NULL = legacy
+ * default stream) on the current device.  rt_destroy frees the workspace.
+ * rt_sync waits for the stream and returns the device status word (then
+ * clears it).  rt_last_error: message of the last failure on this handle. */
+rt_status rt_create(rt_handle* h, void* stream);
+rt_status rt_destroy(rt_handle h);
+rt_status rt_set_stream(rt_handle h, void* stream);
+rt_status rt_sync(rt_handle h);
+const char* rt_last_error(rt_handle h);
+const char* rt_status_string(rt_status s);
+int rt_version(void);
+/* Number of kernel launches the last rtucker_ / rhtucker_ call enqueued. */
+int rt_last_launch_count(rt_handle h);
+/* Bytes of device workspace currently held by the handle. */
+size_t rt_workspace_bytes(rt_handle h);
+
+/* ----------------------------------------------------------- Sub-R-HOSVD
+ * Shared arguments (Alg. 1 inputs):
+ *   X      device, d-way C-order tensor of sizes n[0..d-1], storage `dtype`;
+ *   d      order, 2 <= d <= 16;  n[k] >= 1, prod n < 2^62;
+ *   r      ranks r[k] >= 1 (host);   p  oversampling >= 0;
+ *   s      samples per mode (host) or NULL for s_k = min(10 n_k, n_{!=k})
+ *          (the paper's rule of thumb s_k >= 10 n_k, Sec. 3.2);
+ *   seed   64-bit seed of the random streams;  opt  NULL = defaults.
+ * Rules (Alg. 1 and the Sub-R-HOSVD error bound, Sec. 3.2): r_k + p <= n_k,
+ * r_k + p <= n_{!=k}, r_k + p <= s_k <= n_{!=k}; else RT_EINVAL.
+ */
+
+/* S1 - fiber sample (Sec. 3.1): idx = concat_k pi_k[0..s_k-1], int64, the
+ * sampled column indices of X^(k) (distinct, in [0, n_{!=k})).  No X needed. */
+rt_status rtucker_indices(rt_handle h, int d, const int64_t* n, const int64_t* s, uint64_t seed,
+                          int64_t* idx);
+
+/* S1-S4 - sketch Z_k = Y_k Omega_k = X^(k) E_k Omega_k (Sec. 3.1, Alg. 1):
+ * Z = concat_k of n_k x (r_k + p) row-major blocks. */
+rt_status rtucker_sketch(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                         const int32_t* r, int32_t p, const int64_t* s, uint64_t seed,
+                         const rt_options* opt, float* Z);
+
+/* S1-S6 - factors U_k = Q_k W_k (Alg. 1): Q_k the orthonormal factor of the
+ * thin QR of Z_k with diag(R) > 0, W_k the dominant r_k left singular vectors
+ * of Q_k^T Y_k.  U = concat_k of n_k x r_k row-major blocks; each column's
+ * largest-magnitude entry is positive (ties: lowest row).  sigma (optional,
+ * may be NULL): concat_k of the r_k + p singular values of Q_k^T Y_k. */
+rt_status rtucker_factors(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                          const int32_t* r, int32_t p, const int64_t* s, uint64_t seed,
+                          const rt_options* opt, float* U, float* sigma);
+
+/* S7 - core G = X x_1 U_1^T ... x_d U_d^T (Alg. 1, core step): U as returned
+ * by rtucker_factors (any n_k x r_k blocks), G the r_0 x ... x r_{d-1} C-order
+ * core. */
+rt_status rtucker_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                       const int32_t* r, const float* U, const rt_options* opt, float* G);
+
+/* S1-S7 - the whole Sub-R-HOSVD (Alg. 1): factors then core in one call. */
+rt_status rtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                            const int32_t* r, int32_t p, const int64_t* s, uint64_t seed,
+                            const rt_options* opt, float* U, float* G);
+
+/* Same as rtucker_decompose with X, U and G in HOST memory (pinned memory
+ * recommended): X is copied to device workspace, the decomposition runs, and
+ * U and G are copied back; the call returns after the copies completed. */
+rt_status rtucker_decompose_host(rt_handle h, const void* X_host, rt_dtype dtype, int d,
+                                 const int64_t* n, const int32_t* r, int32_t p, const int64_t* s,
+                                 uint64_t seed, const rt_options* opt, float* U_host, float* G_host);
+
+/* Batched Sub-R-HOSVD: T independent tensors (tensor t: X[t], order d[t],
+ * sizes n[t][.], ranks r[t][.], samples s[t] or s == NULL / s[t] == NULL for
+ * the default, seed seeds[t]) decomposed with one grouped launch per stage for
+ * all (tensor, mode) problems.  X, U, G: HOST arrays of DEVICE pointers. */
+rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt_dtype dtype,
+                                    const int32_t* d, const int64_t* const* n,
+                                    const int32_t* const* r, int32_t p,
+                                    const int64_t* const* s, const uint64_t* seeds,
+                                    const rt_options* opt, float* const* U, float* const* G);
+
+/* Relative reconstruction error ||X - (U_1..U_d) G||_F / ||X||_F computed on
+ * the device in float64 (evaluator; not part of the decomposition).  The
+ * result is written to *out (HOST) after the call synchronises the stream. */
+rt_status rtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                         const int32_t* r, const float* U, const float* G, double* out);
+
+/* ----------------------------------------------------------- Sub-R-RtL-HT
+ * rhtucker_decompose (Alg. 2) on the balanced dimension tree (the node {a..b}
+ * splits into its first ceil(len/2) modes and the rest; nodes numbered level
+ * by level, left to right: for d = 8 the paper's heap numbering, root 0,
+ * leaves 7..14).  The tree has 2d-1 nodes.
+ *   rank[node]  rank per node (host, 2d-1 entries; rank[0] is ignored: the
+ *               root rank is 1);  p oversampling;
+ *   w[node]     samples per node (host) or NULL for
+ *               w_S = min(20 max_k n_k, n_{notin S}) (the paper's 20 n fibers
+ *               per node, Sec. 4.2);
+ *   U_leaf      device, concat over leaves (mode order) of n_k x rank_k;
+ *   B           device, concat over internal nodes in id order of the
+ *               transfer tensors r_S x r_{S_l} x r_{S_r} (C order), the root's
+ *               first (1 x r_{R_l} x r_{R_r});
+ *   U_nodes     device or NULL: concat over non-root nodes in id order of the
+ *               node bases U_S (n_S x r_S).
+ * Rules: r_S + p <= min(n_S, n_{notin S}), r_S + p <= w_S <= n_{notin S}. */
+rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                             const int32_t* rank, int32_t p, const int64_t* w, uint64_t seed,
+                             const rt_options* opt, float* U_leaf, float* B, float* U_nodes);
+
+/* Relative error of the H-Tucker format (U_leaf, B) against X, float64 on the
+ * device; *out (HOST) written after the call synchronises. */
+rt_status rhtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                          const int32_t* rank, const float* U_leaf, const float* B, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RTUCKER_H */

@@ -1,0 +1,400 @@
+"""GB300-native subsampled randomized Tucker / H-Tucker (arXiv 2603.21379).
+
+Thin ctypes binding over the C ABI of ``librtucker.so`` (``include/rtucker.h``).
+Functions carry the C names and only marshal arguments: PyTorch supplies device
+memory and the current CUDA stream, and every step of the decomposition runs
+in the library's CUDA kernels.  There is no CPU fallback: if the library is
+missing, calls raise.
+
+Conventions: tensors are C-order CUDA tensors (float32, float64 or bfloat16);
+factors come back as float32 ``n_k x r_k`` matrices, cores as float32 C-order
+``r_1 x ... x r_d`` tensors.
+"""
+
+import ctypes
+import os
+
+import torch
+
+__all__ = [
+    "load_library", "library_path", "RtError",
+    "rtucker_indices", "rtucker_sketch", "rtucker_factors", "rtucker_core", "rtucker_decompose",
+    "rtucker_decompose_host", "rtucker_decompose_batched", "rtucker_relerr",
+    "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "last_launch_count", "workspace_bytes",
+]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIBNAME = "librtucker.so"
+
+RT_F32, RT_F64, RT_BF16 = 0, 1, 2
+_DT = {torch.float32: RT_F32, torch.float64: RT_F64, torch.bfloat16: RT_BF16}
+
+
+class RtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("rtucker status %d: %s" % (status, msg))
+        self.status = status
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+
+
+_lib = None
+
+
+def library_path():
+    return os.path.join(_PKG, _LIBNAME)
+
+
+def load_library():
+    """Load librtucker.so (built by ``paper_2603_21379_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError("librtucker.so is not built (run: python -m paper_2603_21379_gb300.build); "
+                           "there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    PU64 = ctypes.POINTER(ctypes.c_uint64)
+    PD = ctypes.POINTER(ctypes.c_double)
+    PO = ctypes.POINTER(_Options)
+    sig = {
+        "rt_create": (ctypes.c_int, [ctypes.POINTER(vp), vp]),
+        "rt_destroy": (ctypes.c_int, [vp]),
+        "rt_set_stream": (ctypes.c_int, [vp, vp]),
+        "rt_sync": (ctypes.c_int, [vp]),
+        "rt_last_error": (ctypes.c_char_p, [vp]),
+        "rt_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "rt_version": (ctypes.c_int, []),
+        "rt_last_launch_count": (ctypes.c_int, [vp]),
+        "rt_workspace_bytes": (ctypes.c_size_t, [vp]),
+        "rtucker_indices": (ctypes.c_int, [vp, ctypes.c_int, P64, P64, u64, vp]),
+        "rtucker_sketch": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64, PO, vp]),
+        "rtucker_factors": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64, PO, vp, vp]),
+        "rtucker_core": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, vp, PO, vp]),
+        "rtucker_decompose": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64, PO, vp, vp]),
+        "rtucker_decompose_host": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64, PO,
+                                                  vp, vp]),
+        "rtucker_decompose_batched": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, P32,
+                                                     ctypes.POINTER(P64), ctypes.POINTER(P32), i32,
+                                                     ctypes.POINTER(P64), PU64, PO, ctypes.POINTER(vp),
+                                                     ctypes.POINTER(vp)]),
+        "rtucker_relerr": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, vp, vp, PD]),
+        "rhtucker_decompose": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64, PO,
+                                              vp, vp, vp]),
+        "rhtucker_relerr": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, vp, vp, PD]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------------ handles
+_handles = {}
+
+
+def _handle(device=None):
+    """Handle bound to the current CUDA stream of ``device`` (cached)."""
+    lib = load_library()
+    if device is None:
+        device = torch.cuda.current_device()
+    stream = torch.cuda.current_stream(device)
+    key = (device, stream.cuda_stream)
+    h = _handles.get(key)
+    if h is None:
+        with torch.cuda.device(device):
+            hp = ctypes.c_void_p()
+            st = lib.rt_create(ctypes.byref(hp), ctypes.c_void_p(stream.cuda_stream))
+            if st != 0:
+                raise RtError(st, "rt_create failed")
+        h = hp
+        _handles[key] = h
+    return h
+
+
+def _check(h, st):
+    if st != 0:
+        raise RtError(st, load_library().rt_last_error(h).decode())
+
+
+def _i64(vals):
+    vals = [int(v) for v in vals]
+    return (ctypes.c_int64 * len(vals))(*vals)
+
+
+def _i32(vals):
+    vals = [int(v) for v in vals]
+    return (ctypes.c_int32 * len(vals))(*vals)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _as_list(v, d):
+    if isinstance(v, (list, tuple)):
+        return [int(x) for x in v]
+    return [int(v)] * d
+
+
+def _tensor_args(X):
+    if not X.is_cuda:
+        raise ValueError("X must be a CUDA tensor")
+    if X.dtype not in _DT:
+        raise ValueError("X must be float32, float64 or bfloat16")
+    if not X.is_contiguous():
+        raise ValueError("X must be C-contiguous")
+    return _DT[X.dtype], X.dim(), list(X.shape)
+
+
+def _split(flat, rows, cols):
+    out, off = [], 0
+    for n, r in zip(rows, cols):
+        out.append(flat[off:off + n * r].view(n, r))
+        off += n * r
+    return out
+
+
+def last_launch_count(device=None):
+    """Kernel launches enqueued by the last call on the current stream's handle."""
+    return int(load_library().rt_last_launch_count(_handle(device)))
+
+
+def workspace_bytes(device=None):
+    return int(load_library().rt_workspace_bytes(_handle(device)))
+
+
+# ------------------------------------------------------------------ Sub-R-HOSVD
+def rtucker_indices(n, s=None, seed=0, device=None):
+    """S1: concatenated sampled column indices pi_k (int64, on the device)."""
+    lib = load_library()
+    d = len(n)
+    sv = [min(10 * n[k], _prod(n) // n[k]) for k in range(d)] if s is None else _as_list(s, d)
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    idx = torch.empty(sum(sv), dtype=torch.int64, device=dev)
+    h = _handle(dev.index)
+    _check(h, lib.rtucker_indices(h, d, _i64(n), _i64(sv), ctypes.c_uint64(seed), _ptr(idx)))
+    return list(torch.split(idx, sv))
+
+
+def _prod(v):
+    out = 1
+    for x in v:
+        out *= int(x)
+    return out
+
+
+def rtucker_sketch(X, r, p, s=None, seed=0):
+    """S1-S4: sketches Z_k = Y_k Omega_k (n_k x (r_k + p)), float32."""
+    lib = load_library()
+    dt, d, n = _tensor_args(X)
+    r = _as_list(r, d)
+    Z = torch.empty(sum(nk * (rk + p) for nk, rk in zip(n, r)), dtype=torch.float32, device=X.device)
+    h = _handle(X.device.index)
+    sp = _i64(_as_list(s, d)) if s is not None else None
+    _check(h, lib.rtucker_sketch(h, _ptr(X), dt, d, _i64(n), _i32(r), int(p), sp, ctypes.c_uint64(seed), None,
+                                 _ptr(Z)))
+    return _split(Z, n, [rk + p for rk in r])
+
+
+def rtucker_factors(X, r, p, s=None, seed=0, with_sigma=False):
+    """S1-S6: factors U_k (n_k x r_k) with the column-sign rule; optionally the
+    singular values of Q_k^T Y_k."""
+    lib = load_library()
+    dt, d, n = _tensor_args(X)
+    r = _as_list(r, d)
+    U = torch.empty(sum(nk * rk for nk, rk in zip(n, r)), dtype=torch.float32, device=X.device)
+    sig = torch.empty(sum(rk + p for rk in r), dtype=torch.float32, device=X.device) if with_sigma else None
+    h = _handle(X.device.index)
+    sp = _i64(_as_list(s, d)) if s is not None else None
+    _check(h, lib.rtucker_factors(h, _ptr(X), dt, d, _i64(n), _i32(r), int(p), sp, ctypes.c_uint64(seed), None,
+                                  _ptr(U), _ptr(sig)))
+    Us = _split(U, n, r)
+    if with_sigma:
+        return Us, list(torch.split(sig, [rk + p for rk in r]))
+    return Us
+
+
+def _cat_u(U):
+    return torch.cat([u.reshape(-1).to(torch.float32) for u in U]).contiguous()
+
+
+def rtucker_core(X, U):
+    """S7: core G = X x_1 U_1^T ... x_d U_d^T (float32)."""
+    lib = load_library()
+    dt, d, n = _tensor_args(X)
+    r = [int(u.shape[1]) for u in U]
+    Uc = _cat_u(U)
+    G = torch.empty(r, dtype=torch.float32, device=X.device)
+    h = _handle(X.device.index)
+    _check(h, lib.rtucker_core(h, _ptr(X), dt, d, _i64(n), _i32(r), _ptr(Uc), None, _ptr(G)))
+    return G
+
+
+def rtucker_decompose(X, r, p, s=None, seed=0, out=None):
+    """S1-S7: Sub-R-HOSVD; returns (G, [U_k]).  ``out`` = (Uflat, G) reuses buffers."""
+    lib = load_library()
+    dt, d, n = _tensor_args(X)
+    r = _as_list(r, d)
+    if out is None:
+        U = torch.empty(sum(nk * rk for nk, rk in zip(n, r)), dtype=torch.float32, device=X.device)
+        G = torch.empty(r, dtype=torch.float32, device=X.device)
+    else:
+        U, G = out
+    h = _handle(X.device.index)
+    sp = _i64(_as_list(s, d)) if s is not None else None
+    _check(h, lib.rtucker_decompose(h, _ptr(X), dt, d, _i64(n), _i32(r), int(p), sp, ctypes.c_uint64(seed), None,
+                                    _ptr(U), _ptr(G)))
+    return G, _split(U, n, r)
+
+
+def rtucker_decompose_host(X, r, p, s=None, seed=0, out=None):
+    """Sub-R-HOSVD of a HOST tensor (pinned memory recommended); copies in,
+    decomposes, copies U and G back to host tensors; synchronous."""
+    lib = load_library()
+    if X.is_cuda or X.dtype not in _DT or not X.is_contiguous():
+        raise ValueError("X must be a contiguous host tensor of float32/float64/bfloat16")
+    d, n = X.dim(), list(X.shape)
+    r = _as_list(r, d)
+    if out is None:
+        U = torch.empty(sum(nk * rk for nk, rk in zip(n, r)), dtype=torch.float32, pin_memory=True)
+        G = torch.empty(r, dtype=torch.float32, pin_memory=True)
+    else:
+        U, G = out
+    h = _handle()
+    sp = _i64(_as_list(s, d)) if s is not None else None
+    _check(h, lib.rtucker_decompose_host(h, _ptr(X), _DT[X.dtype], d, _i64(n), _i32(r), int(p), sp,
+                                         ctypes.c_uint64(seed), None, _ptr(U), _ptr(G)))
+    return G, _split(U, n, r)
+
+
+def rtucker_decompose_batched(Xs, ranks, p, seeds, s=None):
+    """Batched Sub-R-HOSVD: one grouped launch per stage for all (tensor, mode)
+    problems.  Returns a list of (G, [U_k])."""
+    lib = load_library()
+    T = len(Xs)
+    dts = {X.dtype for X in Xs}
+    if len(dts) != 1:
+        raise ValueError("all tensors of a batch share one dtype")
+    dt = _DT[Xs[0].dtype]
+    dev = Xs[0].device
+    ds, ns, rs, Us, Gs = [], [], [], [], []
+    for X, r in zip(Xs, ranks):
+        _, d, n = _tensor_args(X)
+        r = _as_list(r, d)
+        ds.append(d)
+        ns.append(_i64(n))
+        rs.append(_i32(r))
+        Us.append(torch.empty(sum(nk * rk for nk, rk in zip(n, r)), dtype=torch.float32, device=dev))
+        Gs.append(torch.empty(r, dtype=torch.float32, device=dev))
+    P64 = ctypes.POINTER(ctypes.c_int64)
+    P32 = ctypes.POINTER(ctypes.c_int32)
+    n_arr = (P64 * T)(*[ctypes.cast(a, P64) for a in ns])
+    r_arr = (P32 * T)(*[ctypes.cast(a, P32) for a in rs])
+    s_arr = None
+    if s is not None:
+        s_keep = [_i64(_as_list(sv, dd)) for sv, dd in zip(s, ds)]
+        s_arr = (P64 * T)(*[ctypes.cast(a, P64) for a in s_keep])
+    X_arr = (ctypes.c_void_p * T)(*[X.data_ptr() for X in Xs])
+    U_arr = (ctypes.c_void_p * T)(*[u.data_ptr() for u in Us])
+    G_arr = (ctypes.c_void_p * T)(*[g.data_ptr() for g in Gs])
+    h = _handle(dev.index)
+    _check(h, lib.rtucker_decompose_batched(h, T, X_arr, dt, _i32(ds), n_arr, r_arr, int(p), s_arr,
+                                            (ctypes.c_uint64 * T)(*[int(v) for v in seeds]), None, U_arr, G_arr))
+    out = []
+    for X, r, U, G in zip(Xs, ranks, Us, Gs):
+        n = list(X.shape)
+        out.append((G, _split(U, n, _as_list(r, X.dim()))))
+    return out
+
+
+def rtucker_relerr(X, G, U):
+    """||X - (U_1..U_d) G||_F / ||X||_F, float64 on the device (evaluator)."""
+    lib = load_library()
+    dt, d, n = _tensor_args(X)
+    r = [int(u.shape[1]) for u in U]
+    Uc = _cat_u(U)
+    Gc = G.to(torch.float32).contiguous()
+    out = ctypes.c_double()
+    h = _handle(X.device.index)
+    _check(h, lib.rtucker_relerr(h, _ptr(X), dt, d, _i64(n), _i32(r), _ptr(Uc), _ptr(Gc), ctypes.byref(out)))
+    return out.value
+
+
+# ------------------------------------------------------------------ Sub-R-RtL-HT
+def ht_tree(d):
+    """Balanced dimension tree: list of (a, b, left, right, level), node 0 the root."""
+    nodes = [[0, d - 1, -1, -1, 0]]
+    q = 0
+    while q < len(nodes):
+        a, b, _, _, lev = nodes[q]
+        if a != b:
+            mid = a + (b - a + 2) // 2
+            nodes[q][2] = len(nodes)
+            nodes.append([a, mid - 1, -1, -1, lev + 1])
+            nodes[q][3] = len(nodes)
+            nodes.append([mid, b, -1, -1, lev + 1])
+        q += 1
+    return [tuple(x) for x in nodes]
+
+
+def _ht_ranks(d, rank):
+    nn = 2 * d - 1
+    rk = _as_list(rank, nn) if isinstance(rank, (list, tuple)) else [int(rank)] * nn
+    rk[0] = 1
+    return rk
+
+
+def rhtucker_decompose(X, rank, p, w=None, seed=0, return_nodes=False):
+    """Sub-R-RtL-HT on the balanced tree.  Returns (U_leaf list, B dict node->
+    transfer tensor) and, with ``return_nodes``, the node bases U_S."""
+    lib = load_library()
+    dt, d, n = _tensor_args(X)
+    tree = ht_tree(d)
+    rk = _ht_ranks(d, rank)
+    nrows = [_prod(n[a:b + 1]) for (a, b, _, _, _) in tree]
+    leaves = sorted((i for i, t in enumerate(tree) if t[0] == t[1]), key=lambda i: tree[i][0])
+    internal = [i for i, t in enumerate(tree) if t[0] != t[1]]
+    Ul = torch.empty(sum(n[tree[i][0]] * rk[i] for i in leaves), dtype=torch.float32, device=X.device)
+    Bsz = [rk[i] * rk[tree[i][2]] * rk[tree[i][3]] for i in internal]
+    B = torch.empty(sum(Bsz), dtype=torch.float32, device=X.device)
+    Un = None
+    if return_nodes:
+        Un = torch.empty(sum(nrows[i] * rk[i] for i in range(1, len(tree))), dtype=torch.float32,
+                         device=X.device)
+    h = _handle(X.device.index)
+    wp = _i64(_as_list(w, len(tree))) if w is not None else None
+    _check(h, lib.rhtucker_decompose(h, _ptr(X), dt, d, _i64(n), _i32(rk), int(p), wp, ctypes.c_uint64(seed), None,
+                                     _ptr(Ul), _ptr(B), _ptr(Un)))
+    U_leaf = _split(Ul, [n[tree[i][0]] for i in leaves], [rk[i] for i in leaves])
+    Bd, off = {}, 0
+    for i, sz in zip(internal, Bsz):
+        Bd[i] = B[off:off + sz].view(rk[i], rk[tree[i][2]], rk[tree[i][3]])
+        off += sz
+    if return_nodes:
+        Ud = dict(zip(range(1, len(tree)), _split(Un, nrows[1:], rk[1:])))
+        return U_leaf, Bd, Ud
+    return U_leaf, Bd
+
+
+def rhtucker_relerr(X, U_leaf, B, rank):
+    """Relative error of an H-Tucker result against X, float64 on the device."""
+    lib = load_library()
+    dt, d, n = _tensor_args(X)
+    tree = ht_tree(d)
+    rk = _ht_ranks(d, rank)
+    internal = [i for i, t in enumerate(tree) if t[0] != t[1]]
+    Uc = _cat_u(U_leaf)
+    Bc = torch.cat([B[i].reshape(-1) for i in internal]).to(torch.float32).contiguous()
+    out = ctypes.c_double()
+    h = _handle(X.device.index)
+    _check(h, lib.rhtucker_relerr(h, _ptr(X), dt, d, _i64(n), _i32(rk), _ptr(Uc), _ptr(Bc), ctypes.byref(out)))
+    return out.value

@@ -1,0 +1,937 @@
+// api.cu - C ABI of the rtucker library (declared in include/rtucker.h).
+//
+// Host orchestration only: argument checks, planning the grouped problem
+// tables, the device workspace, and the launch sequence.  Every step of the
+// decomposition runs in this library's CUDA kernels; there is no CPU path.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cmath>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/rtucker.h"
+#include "rt_common.cuh"
+#include "rt_host.h"
+
+using namespace rt;
+
+struct rt_handle_s {
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  char* ws = nullptr;          // device workspace
+  size_t ws_bytes = 0;
+  int* d_status = nullptr;     // device status word
+  int* h_status = nullptr;     // pinned copy of the status word
+  cudaEvent_t ev_status = nullptr;
+  bool status_pending = false;
+  char* h_stage = nullptr;     // pinned staging of the problem tables
+  size_t h_stage_bytes = 0;
+  cudaEvent_t ev_stage = nullptr;
+  bool stage_pending = false;
+  std::string err;
+  int launches = 0;
+  char* hc_buf = nullptr;      // device buffers of rtucker_decompose_host
+  size_t hc_bytes = 0;
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
+
+rt_status fail(rt_handle h, rt_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+rt_status cuda_fail(rt_handle h, cudaError_t e, const char* where) {
+  return fail(h, RT_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define RT_CUDA(h, call)                                  \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return cuda_fail(h, _e, #call); \
+  } while (0)
+
+int dtype_size(rt_dtype t) { return t == RT_F64 ? 8 : (t == RT_BF16 ? 2 : 4); }
+
+bool mul_ok(int64_t a, int64_t b, int64_t* out) {
+  if (a <= 0 || b <= 0) return false;
+  if (a > (int64_t)(((uint64_t)1 << 62) / (uint64_t)b)) return false;
+  *out = a * b;
+  return true;
+}
+
+int feistel_half(int64_t N) {
+  // smallest even b >= 2 with 2^b >= N; returns b / 2
+  int b = 0;
+  uint64_t v = (uint64_t)(N - 1);
+  while (v) { ++b; v >>= 1; }
+  if (b < 2) b = 2;
+  b += (b & 1);
+  return b / 2;
+}
+
+inline int odd(int m) { return m | 1; }
+
+// Bump allocator over the device workspace.
+struct Bump {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  }
+};
+
+// --- range-finder problem planning ------------------------------------------
+struct ProbSpec {
+  const void* X;
+  rt_dtype dtype;
+  int d;
+  int64_t n[MAXD];
+  int a, b;           // contiguous mode range S
+  int r, p;
+  int64_t s;
+  uint64_t seed;
+  uint32_t node;
+  float* U;           // output (device) or null -> workspace
+  float* sigma_out;
+  int64_t* idx_out;   // sampled indices straight to the caller (or null)
+};
+
+struct ProbPlan {
+  RFProb q;
+  size_t o_idx, o_off, o_Om, o_Yt, o_Zp, o_Q, o_Rb, o_Q2, o_Bp, o_Rc, o_W, o_sig, o_keys, o_U;
+  int64_t units[STG_COUNT];
+};
+
+rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp) {
+  RFProb& q = pp.q;
+  memset(&q, 0, sizeof(q));
+  const int d = ps.d;
+  int64_t stride[MAXD];
+  stride[d - 1] = 1;
+  for (int j = d - 2; j >= 0; --j) stride[j] = stride[j + 1] * ps.n[j + 1];
+  int64_t nS = 1, N = 1;
+  for (int j = ps.a; j <= ps.b; ++j) nS *= ps.n[j];
+  q.ncm = 0;
+  for (int j = 0; j < d; ++j) {
+    if (j >= ps.a && j <= ps.b) continue;
+    q.csize[q.ncm] = ps.n[j];
+    q.cstride[q.ncm] = stride[j];
+    ++q.ncm;
+    N *= ps.n[j];
+  }
+  const int c = ps.r + ps.p;
+  if (ps.r < 1 || ps.p < 0) return fail(h, RT_EINVAL, "need r >= 1 and p >= 0");
+  if (c > nS || c > N) return fail(h, RT_EINVAL, "need r + p <= min(n_S, n_notin_S) (node " + std::to_string(ps.node) + ")");
+  if (ps.s < c || ps.s > N) return fail(h, RT_EINVAL, "need r + p <= s <= n_notin_S (node " + std::to_string(ps.node) + ")");
+  if (c > CMAX) return fail(h, RT_ENOTSUP, "r + p > 64 is not supported");
+  if (nS >= ((int64_t)1 << 31)) return fail(h, RT_ENOTSUP, "unfolding with 2^31 or more rows");
+  q.X = ps.X;
+  q.dtype = (int)ps.dtype;
+  q.nS = nS;
+  q.N = N;
+  q.rowstride = stride[ps.b];
+  q.r = ps.r;
+  q.c = c;
+  q.s = ps.s;
+  q.seed = ps.seed;
+  q.node = ps.node;
+  q.fh = feistel_half(N);
+  q.nzc = (int)((ps.s + SK_TJ - 1) / SK_TJ);
+  // TSQR of Z
+  int rb = (QR_MAXF / c - 1) & ~31;
+  if (rb < 32) rb = 32;
+  if (odd((int)std::min<int64_t>(nS, 1 << 30)) * (int64_t)c <= QR_MAXF) {
+    q.nrb = 1;
+    q.rbrows = (int)nS;
+  } else {
+    q.rbrows = rb;
+    q.nrb = (int)((nS + rb - 1) / rb);
+    if ((int64_t)odd(q.nrb * c) * c > QR2_MAXF)
+      return fail(h, RT_ENOTSUP, "unfolding too tall for the two-level TSQR");
+  }
+  q.scrows = BT_SC;
+  q.nsc = (int)((ps.s + BT_SC - 1) / BT_SC);
+  q.nbi = (int)((nS + BT_IB - 1) / BT_IB);
+  if ((int64_t)odd(q.nsc * c) * c > WS_MAXF) return fail(h, RT_ENOTSUP, "too many samples for the W-step");
+  const int64_t s = ps.s;
+  pp.o_idx = ps.idx_out ? (size_t)-1 : bump.take(s * 8);
+  pp.o_off = bump.take(s * 8);
+  pp.o_Om = bump.take(s * c * 4);
+  pp.o_Yt = bump.take((size_t)s * nS * 4);
+  pp.o_Zp = bump.take((size_t)q.nzc * nS * c * 4);
+  pp.o_Q = bump.take((size_t)nS * c * 4);
+  pp.o_Rb = bump.take(q.nrb > 1 ? (size_t)q.nrb * c * c * 4 : 4);
+  pp.o_Q2 = bump.take(q.nrb > 1 ? (size_t)q.nrb * c * c * 4 : 4);
+  pp.o_Bp = bump.take((size_t)q.nbi * s * c * 4);
+  pp.o_Rc = bump.take((size_t)q.nsc * c * c * 4);
+  pp.o_W = bump.take((size_t)c * c * 4);
+  pp.o_sig = bump.take((size_t)c * 4);
+  pp.o_keys = bump.take((size_t)ps.r * 8);
+  pp.o_U = ps.U ? (size_t)-1 : bump.take((size_t)nS * ps.r * 4);
+  q.U = ps.U;
+  q.sigma_out = ps.sigma_out;
+  q.idx = ps.idx_out;
+  const int64_t nrt = (nS + SK_TI - 1) / SK_TI;
+  pp.units[STG_SAMPLE] = s;
+  pp.units[STG_GS] = nrt * q.nzc;
+  pp.units[STG_QR1] = q.nrb;
+  pp.units[STG_QR2] = q.nrb > 1 ? 1 : 0;
+  pp.units[STG_QR3] = q.nrb > 1 ? q.nrb : 0;
+  pp.units[STG_BTP] = (int64_t)q.nsc * q.nbi;
+  pp.units[STG_BTQ] = q.nsc;
+  pp.units[STG_WSVD] = 1;
+  pp.units[STG_QW] = (nS + QW_TI - 1) / QW_TI;
+  pp.units[STG_FLIP] = pp.units[STG_QW];
+  pp.units[STG_ZSUM] = nS * c;
+  return RT_OK;
+}
+
+void bind_problem(ProbPlan& pp, char* ws) {
+  RFProb& q = pp.q;
+  if (pp.o_idx != (size_t)-1) q.idx = reinterpret_cast<int64_t*>(ws + pp.o_idx);
+  q.off = reinterpret_cast<int64_t*>(ws + pp.o_off);
+  q.Om = reinterpret_cast<float*>(ws + pp.o_Om);
+  q.Yt = reinterpret_cast<float*>(ws + pp.o_Yt);
+  q.Zp = reinterpret_cast<float*>(ws + pp.o_Zp);
+  q.Q = reinterpret_cast<float*>(ws + pp.o_Q);
+  q.Rb = reinterpret_cast<float*>(ws + pp.o_Rb);
+  q.Q2 = reinterpret_cast<float*>(ws + pp.o_Q2);
+  q.Bp = reinterpret_cast<float*>(ws + pp.o_Bp);
+  q.Rc = reinterpret_cast<float*>(ws + pp.o_Rc);
+  q.W = reinterpret_cast<float*>(ws + pp.o_W);
+  q.sigma = reinterpret_cast<float*>(ws + pp.o_sig);
+  q.keys = reinterpret_cast<unsigned long long*>(ws + pp.o_keys);
+  if (!q.U) q.U = reinterpret_cast<float*>(ws + pp.o_U);
+}
+
+// Grows the workspace to at least `bytes` (synchronising the stream first).
+rt_status ensure_ws(rt_handle h, size_t bytes) {
+  if (bytes <= h->ws_bytes) return RT_OK;
+  RT_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (h->ws) cudaFree(h->ws);
+  h->ws = nullptr;
+  h->ws_bytes = 0;
+  const size_t want = align_up(bytes + bytes / 8);
+  cudaError_t e = cudaMalloc(&h->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->ws = nullptr;
+    return fail(h, RT_ENOMEM, "device workspace allocation of " + std::to_string(want) + " bytes failed");
+  }
+  h->ws_bytes = want;
+  return RT_OK;
+}
+
+rt_status ensure_stage(rt_handle h, size_t bytes) {
+  if (h->stage_pending) {
+    RT_CUDA(h, cudaEventSynchronize(h->ev_stage));
+    h->stage_pending = false;
+  }
+  if (bytes <= h->h_stage_bytes) return RT_OK;
+  if (h->h_stage) cudaFreeHost(h->h_stage);
+  h->h_stage = nullptr;
+  h->h_stage_bytes = 0;
+  const size_t want = align_up(bytes * 2);
+  RT_CUDA(h, cudaMallocHost(&h->h_stage, want));
+  h->h_stage_bytes = want;
+  return RT_OK;
+}
+
+rt_status check_prior_status(rt_handle h) {
+  if (h->status_pending && cudaEventQuery(h->ev_status) == cudaSuccess) {
+    h->status_pending = false;
+    const int s = *h->h_status;
+    if (s != ST_OK) {
+      *h->h_status = 0;
+      cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream);
+      if (s == ST_TIMEOUT) return fail(h, RT_ETIMEOUT, "a bounded device loop ran out in an earlier call");
+      if (s == ST_NUMERIC) return fail(h, RT_ENUMERIC, "numerical breakdown on the device in an earlier call");
+      return fail(h, RT_EDEVICE, "device-side check failed in an earlier call");
+    }
+  }
+  return RT_OK;
+}
+
+void post_status_copy(rt_handle h) {
+  if (cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream) == cudaSuccess &&
+      cudaEventRecord(h->ev_status, h->stream) == cudaSuccess)
+    h->status_pending = true;
+}
+
+// A grouped range-finder plan with its tables uploaded into the workspace.
+struct Group {
+  std::vector<ProbPlan> pp;
+  size_t o_tab = 0, o_pre = 0;
+  RFGroup g{};
+};
+
+void group_layout(Group& G, Bump& bump) {
+  const int np = (int)G.pp.size();
+  G.o_tab = bump.take(sizeof(RFProb) * np);
+  G.o_pre = bump.take(sizeof(int64_t) * STG_COUNT * (np + 1));
+}
+
+// Writes the tables into staging and enqueues the upload; fills G.g.
+rt_status group_upload(rt_handle h, Group& G, char* stage, size_t stage_off) {
+  const int np = (int)G.pp.size();
+  RFProb* tab = reinterpret_cast<RFProb*>(stage + stage_off);
+  int64_t* pre = reinterpret_cast<int64_t*>(stage + stage_off + align_up(sizeof(RFProb) * np));
+  for (int i = 0; i < np; ++i) {
+    bind_problem(G.pp[i], h->ws);
+    tab[i] = G.pp[i].q;
+  }
+  for (int st = 0; st < STG_COUNT; ++st) {
+    int64_t acc = 0;
+    for (int i = 0; i < np; ++i) {
+      pre[st * (np + 1) + i] = acc;
+      acc += G.pp[i].units[st];
+    }
+    pre[st * (np + 1) + np] = acc;
+    G.g.total[st] = acc;
+  }
+  RT_CUDA(h, cudaMemcpyAsync(h->ws + G.o_tab, tab, sizeof(RFProb) * np, cudaMemcpyHostToDevice, h->stream));
+  RT_CUDA(h, cudaMemcpyAsync(h->ws + G.o_pre, pre, sizeof(int64_t) * STG_COUNT * (np + 1),
+                             cudaMemcpyHostToDevice, h->stream));
+  G.g.probs = reinterpret_cast<const RFProb*>(h->ws + G.o_tab);
+  G.g.pre = reinterpret_cast<const int64_t*>(h->ws + G.o_pre);
+  G.g.nprob = np;
+  return RT_OK;
+}
+
+size_t group_stage_bytes(const Group& G) {
+  const int np = (int)G.pp.size();
+  return align_up(sizeof(RFProb) * np) + align_up(sizeof(int64_t) * STG_COUNT * (np + 1));
+}
+
+rt_status check_tensor(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, int64_t* total) {
+  if (!h) return RT_EINVAL;
+  if (!X) return fail(h, RT_EINVAL, "X is null");
+  if (dtype != RT_F32 && dtype != RT_F64 && dtype != RT_BF16) return fail(h, RT_EINVAL, "unknown dtype");
+  if (d < 2 || d > MAXD) return fail(h, RT_EINVAL, "need 2 <= d <= 16");
+  if (!n) return fail(h, RT_EINVAL, "n is null");
+  int64_t t = 1;
+  for (int k = 0; k < d; ++k) {
+    if (n[k] < 1) return fail(h, RT_EINVAL, "need n_k >= 1");
+    if (!mul_ok(t, n[k], &t)) return fail(h, RT_EINVAL, "tensor too large (prod n >= 2^62)");
+  }
+  if (((uintptr_t)X) % (uintptr_t)dtype_size(dtype)) return fail(h, RT_EINVAL, "X is misaligned");
+  if (total) *total = t;
+  return RT_OK;
+}
+
+rt_status check_opts(rt_handle h, const rt_options* opt) {
+  if (!opt) return RT_OK;
+  if (opt->prec != RT_PREC_FP32) return fail(h, RT_ENOTSUP, "only RT_PREC_FP32 is available");
+  for (int i = 0; i < 6; ++i)
+    if (opt->reserved[i]) return fail(h, RT_EINVAL, "reserved option fields must be zero");
+  return RT_OK;
+}
+
+int64_t default_s(const int64_t* n, int d, int k) {
+  int64_t N = 1;
+  for (int j = 0; j < d; ++j)
+    if (j != k) N *= n[j];
+  return std::min<int64_t>(10 * n[k], N);
+}
+
+// Tucker problems of one tensor appended to G.
+rt_status add_tucker_problems(rt_handle h, Group& G, Bump& bump, const void* X, rt_dtype dtype, int d,
+                              const int64_t* n, const int32_t* r, int32_t p, const int64_t* s,
+                              uint64_t seed, float* U, float* sigma) {
+  size_t uoff = 0, soff = 0;
+  for (int k = 0; k < d; ++k) {
+    ProbSpec ps{};
+    ps.X = X;
+    ps.dtype = dtype;
+    ps.d = d;
+    for (int j = 0; j < d; ++j) ps.n[j] = n[j];
+    ps.a = ps.b = k;
+    ps.r = r[k];
+    ps.p = p;
+    ps.s = s ? s[k] : default_s(n, d, k);
+    ps.seed = seed;
+    ps.node = (uint32_t)k;
+    ps.U = U ? U + uoff : nullptr;
+    ps.sigma_out = sigma ? sigma + soff : nullptr;
+    ProbPlan pp;
+    rt_status st = plan_problem(h, ps, bump, pp);
+    if (st != RT_OK) return st;
+    G.pp.push_back(pp);
+    uoff += (size_t)n[k] * r[k];
+    soff += (size_t)(r[k] + p);
+  }
+  return RT_OK;
+}
+
+// Core chain sizes: contraction of mode k on (L_k, n_k, R_k) for k = d-1..0.
+size_t core_buffer_floats(int d, const int64_t* n, const int32_t* r) {
+  size_t best = 0;
+  for (int k = d - 1; k >= 1; --k) {  // output of the mode-k step (k >= 1)
+    size_t L = 1, R = 1;
+    for (int j = 0; j < k; ++j) L *= (size_t)n[j];
+    for (int j = k; j < d; ++j) R *= (size_t)r[j];
+    best = std::max(best, L * R);
+  }
+  return best;
+}
+
+int enqueue_core(const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
+                 const float* U, float* G, float* bufA, float* bufB, cudaStream_t st) {
+  int nl = 0;
+  const void* A = X;
+  int adt = (int)dtype;
+  size_t uoff[MAXD];
+  size_t acc = 0;
+  for (int k = 0; k < d; ++k) { uoff[k] = acc; acc += (size_t)n[k] * r[k]; }
+  int ping = 0;
+  for (int k = d - 1; k >= 0; --k) {
+    int64_t L = 1, R = 1;
+    for (int j = 0; j < k; ++j) L *= n[j];
+    for (int j = k + 1; j < d; ++j) R *= r[j];
+    float* out = (k == 0) ? G : (ping ? bufB : bufA);
+    nl += launch_ttm_t(A, adt, L, n[k], R, U + uoff[k], r[k], out, st);
+    A = out;
+    adt = DT_F32;
+    ping ^= 1;
+  }
+  return nl;
+}
+
+
+// --- dimension tree (Sec. 4): node {a..b} splits into its first ceil(len/2)
+// modes and the rest; nodes numbered level by level, left to right.
+struct TNode {
+  int a, b, left, right, level;
+};
+
+std::vector<TNode> balanced_tree(int d) {
+  std::vector<TNode> t;
+  t.push_back(TNode{0, d - 1, -1, -1, 0});
+  for (size_t q = 0; q < t.size(); ++q) {
+    if (t[q].a == t[q].b) continue;
+    const int len = t[q].b - t[q].a + 1;
+    const int mid = t[q].a + (len + 1) / 2;
+    const TNode l{t[q].a, mid - 1, -1, -1, t[q].level + 1};
+    const TNode r{mid, t[q].b, -1, -1, t[q].level + 1};
+    t[q].left = (int)t.size();
+    t.push_back(l);
+    t[q].right = (int)t.size();
+    t.push_back(r);
+  }
+  return t;
+}
+
+int64_t range_prod(const int64_t* n, int a, int b) {
+  int64_t v = 1;
+  for (int j = a; j <= b; ++j) v *= n[j];
+  return v;
+}
+
+bool g_attrs_done[64] = {false};
+
+rt_status init_device_attrs(rt_handle h) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && g_attrs_done[dev]) return RT_OK;
+  RT_CUDA(h, rf_init_attributes());
+  RT_CUDA(h, core_init_attributes());
+  if (dev >= 0 && dev < 64) g_attrs_done[dev] = true;
+  return RT_OK;
+}
+
+rt_status finish(rt_handle h, int launches) {
+  h->launches = launches;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "kernel launch");
+  post_status_copy(h);
+  return RT_OK;
+}
+
+// Full Tucker pipeline for one tensor: tables, range finder, optional core.
+rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
+                     int32_t p, const int64_t* s, uint64_t seed, const rt_options* opt, float* U,
+                     float* sigma, float* G, float* Zout) {
+  rt_status st;
+  if ((st = check_tensor(h, X, dtype, d, n, nullptr)) != RT_OK) return st;
+  if ((st = check_opts(h, opt)) != RT_OK) return st;
+  if (!r) return fail(h, RT_EINVAL, "r is null");
+  if ((st = check_prior_status(h)) != RT_OK) return st;
+  if ((st = init_device_attrs(h)) != RT_OK) return st;
+  Group Gp;
+  Bump bump;
+  st = add_tucker_problems(h, Gp, bump, X, dtype, d, n, r, p, s, seed, U, sigma);
+  if (st != RT_OK) return st;
+  group_layout(Gp, bump);
+  size_t o_zp = 0;
+  if (Zout) o_zp = bump.take(sizeof(float*) * d);
+  size_t o_bufA = 0, o_bufB = 0;
+  if (G) {
+    const size_t cb = core_buffer_floats(d, n, r);
+    o_bufA = bump.take(cb * 4);
+    o_bufB = bump.take(cb * 4);
+  }
+  if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
+  const size_t sb = group_stage_bytes(Gp) + align_up(sizeof(float*) * d);
+  if ((st = ensure_stage(h, sb)) != RT_OK) return st;
+  if ((st = group_upload(h, Gp, h->h_stage, 0)) != RT_OK) return st;
+  int nl = 0;
+  if (Zout) {
+    float** zp = reinterpret_cast<float**>(h->h_stage + group_stage_bytes(Gp));
+    size_t off = 0;
+    for (int k = 0; k < d; ++k) { zp[k] = Zout + off; off += (size_t)n[k] * (r[k] + p); }
+    RT_CUDA(h, cudaMemcpyAsync(h->ws + o_zp, zp, sizeof(float*) * d, cudaMemcpyHostToDevice, h->stream));
+  }
+  RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
+  h->stage_pending = true;
+  nl += launch_range_finder(Gp.g, h->stream, h->d_status);
+  if (Zout) nl += launch_sketch_sum(Gp.g, reinterpret_cast<float* const*>(h->ws + o_zp), h->stream);
+  if (G) {
+    const float* Ucat = U ? U : nullptr;
+    if (!Ucat) return fail(h, RT_EINVAL, "U is required with G");
+    nl += enqueue_core(X, dtype, d, n, r, Ucat, G, reinterpret_cast<float*>(h->ws + o_bufA),
+                       reinterpret_cast<float*>(h->ws + o_bufB), h->stream);
+  }
+  return finish(h, nl);
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+int rt_version(void) { return 1; }
+
+const char* rt_status_string(rt_status s) {
+  switch (s) {
+    case RT_OK: return "ok";
+    case RT_EINVAL: return "invalid argument";
+    case RT_ENOMEM: return "out of device memory";
+    case RT_ECUDA: return "CUDA error";
+    case RT_ETIMEOUT: return "device loop bound exceeded";
+    case RT_EDEVICE: return "device-side check failed";
+    case RT_ENUMERIC: return "numerical breakdown";
+    case RT_ENOTSUP: return "not supported";
+  }
+  return "unknown status";
+}
+
+rt_status rt_create(rt_handle* out, void* stream) {
+  if (!out) return RT_EINVAL;
+  *out = nullptr;
+  rt_handle h = new rt_handle_s();
+  h->stream = static_cast<cudaStream_t>(stream);
+  cudaGetDevice(&h->device);
+  if (cudaMalloc(&h->d_status, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return RT_ENOMEM;
+  }
+  if (cudaMallocHost(&h->h_status, sizeof(int)) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_status, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_stage, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMemset(h->d_status, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    rt_destroy(h);
+    return RT_ECUDA;
+  }
+  *h->h_status = 0;
+  *out = h;
+  return RT_OK;
+}
+
+rt_status rt_destroy(rt_handle h) {
+  if (!h) return RT_EINVAL;
+  cudaStreamSynchronize(h->stream);
+  if (h->ws) cudaFree(h->ws);
+  if (h->hc_buf) cudaFree(h->hc_buf);
+  if (h->d_status) cudaFree(h->d_status);
+  if (h->h_status) cudaFreeHost(h->h_status);
+  if (h->h_stage) cudaFreeHost(h->h_stage);
+  if (h->ev_status) cudaEventDestroy(h->ev_status);
+  if (h->ev_stage) cudaEventDestroy(h->ev_stage);
+  delete h;
+  return RT_OK;
+}
+
+rt_status rt_set_stream(rt_handle h, void* stream) {
+  if (!h) return RT_EINVAL;
+  cudaStreamSynchronize(h->stream);
+  h->stream = static_cast<cudaStream_t>(stream);
+  return RT_OK;
+}
+
+rt_status rt_sync(rt_handle h) {
+  if (!h) return RT_EINVAL;
+  RT_CUDA(h, cudaStreamSynchronize(h->stream));
+  int s = 0;
+  RT_CUDA(h, cudaMemcpy(&s, h->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  h->status_pending = false;
+  if (s != ST_OK) {
+    RT_CUDA(h, cudaMemset(h->d_status, 0, sizeof(int)));
+    if (s == ST_TIMEOUT) return fail(h, RT_ETIMEOUT, "a bounded device loop ran out");
+    if (s == ST_NUMERIC) return fail(h, RT_ENUMERIC, "numerical breakdown on the device");
+    return fail(h, RT_EDEVICE, "device-side check failed");
+  }
+  return RT_OK;
+}
+
+const char* rt_last_error(rt_handle h) { return h ? h->err.c_str() : "null handle"; }
+int rt_last_launch_count(rt_handle h) { return h ? h->launches : 0; }
+size_t rt_workspace_bytes(rt_handle h) { return h ? h->ws_bytes : 0; }
+
+rt_status rtucker_indices(rt_handle h, int d, const int64_t* n, const int64_t* s, uint64_t seed, int64_t* idx) {
+  if (!h) return RT_EINVAL;
+  if (!idx) return fail(h, RT_EINVAL, "idx is null");
+  // the sample needs no tensor; idx only stands in for X in the size checks
+  rt_status st = check_tensor(h, reinterpret_cast<const void*>(idx), RT_F32, d, n, nullptr);
+  if (st != RT_OK) return st;
+  if ((st = check_prior_status(h)) != RT_OK) return st;
+  if ((st = init_device_attrs(h)) != RT_OK) return st;
+  Group Gp;
+  Bump bump;
+  size_t off = 0;
+  for (int k = 0; k < d; ++k) {
+    ProbSpec ps{};
+    ps.X = idx;
+    ps.dtype = RT_F32;
+    ps.d = d;
+    for (int j = 0; j < d; ++j) ps.n[j] = n[j];
+    ps.a = ps.b = k;
+    ps.r = 1;
+    ps.p = 0;
+    ps.s = s ? s[k] : default_s(n, d, k);
+    ps.seed = seed;
+    ps.node = (uint32_t)k;
+    ps.idx_out = idx + off;
+    ProbPlan pp;
+    if ((st = plan_problem(h, ps, bump, pp)) != RT_OK) return st;
+    Gp.pp.push_back(pp);
+    off += (size_t)ps.s;
+  }
+  group_layout(Gp, bump);
+  if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
+  if ((st = ensure_stage(h, group_stage_bytes(Gp))) != RT_OK) return st;
+  if ((st = group_upload(h, Gp, h->h_stage, 0)) != RT_OK) return st;
+  RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
+  h->stage_pending = true;
+  const int nl = launch_sample_only(Gp.g, h->stream, h->d_status);
+  return finish(h, nl);
+}
+
+rt_status rtucker_sketch(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
+                         int32_t p, const int64_t* s, uint64_t seed, const rt_options* opt, float* Z) {
+  if (!h) return RT_EINVAL;
+  if (!Z) return fail(h, RT_EINVAL, "Z is null");
+  return tucker_run(h, X, dtype, d, n, r, p, s, seed, opt, nullptr, nullptr, nullptr, Z);
+}
+
+rt_status rtucker_factors(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
+                          int32_t p, const int64_t* s, uint64_t seed, const rt_options* opt, float* U,
+                          float* sigma) {
+  if (!h) return RT_EINVAL;
+  if (!U) return fail(h, RT_EINVAL, "U is null");
+  return tucker_run(h, X, dtype, d, n, r, p, s, seed, opt, U, sigma, nullptr, nullptr);
+}
+
+rt_status rtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                            const int32_t* r, int32_t p, const int64_t* s, uint64_t seed, const rt_options* opt,
+                            float* U, float* G) {
+  if (!h) return RT_EINVAL;
+  if (!U || !G) return fail(h, RT_EINVAL, "U and G are required");
+  return tucker_run(h, X, dtype, d, n, r, p, s, seed, opt, U, nullptr, G, nullptr);
+}
+
+rt_status rtucker_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
+                       const float* U, const rt_options* opt, float* G) {
+  rt_status st;
+  if ((st = check_tensor(h, X, dtype, d, n, nullptr)) != RT_OK) return st;
+  if ((st = check_opts(h, opt)) != RT_OK) return st;
+  if (!r || !U || !G) return fail(h, RT_EINVAL, "r, U and G are required");
+  for (int k = 0; k < d; ++k)
+    if (r[k] < 1) return fail(h, RT_EINVAL, "need r_k >= 1");
+  if ((st = check_prior_status(h)) != RT_OK) return st;
+  Bump bump;
+  const size_t cb = core_buffer_floats(d, n, r);
+  const size_t oA = bump.take(cb * 4), oB = bump.take(cb * 4);
+  if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
+  const int nl = enqueue_core(X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + oA),
+                              reinterpret_cast<float*>(h->ws + oB), h->stream);
+  return finish(h, nl);
+}
+
+rt_status rtucker_decompose_host(rt_handle h, const void* X_host, rt_dtype dtype, int d, const int64_t* n,
+                                 const int32_t* r, int32_t p, const int64_t* s, uint64_t seed,
+                                 const rt_options* opt, float* U_host, float* G_host) {
+  if (!h) return RT_EINVAL;
+  int64_t total = 0;
+  rt_status st = check_tensor(h, X_host, dtype, d, n, &total);
+  if (st != RT_OK) return st;
+  if (!r || !U_host || !G_host) return fail(h, RT_EINVAL, "r, U and G are required");
+  size_t usz = 0, gsz = 1;
+  for (int k = 0; k < d; ++k) { usz += (size_t)n[k] * r[k]; gsz *= (size_t)r[k]; }
+  // Device copies live in a separate allocation owned by the handle so that
+  // the decomposition's own workspace planning is unchanged.
+  const size_t xb = align_up((size_t)total * dtype_size(dtype));
+  const size_t need = xb + align_up(usz * 4) + align_up(gsz * 4);
+  if (need > h->hc_bytes) {
+    RT_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->hc_buf) cudaFree(h->hc_buf);
+    h->hc_buf = nullptr;
+    h->hc_bytes = 0;
+    if (cudaMalloc(&h->hc_buf, need) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, RT_ENOMEM, "device buffers for the host-memory call");
+    }
+    h->hc_bytes = need;
+  }
+  char* base = h->hc_buf;
+  void* dX = base;
+  float* dU = reinterpret_cast<float*>(base + xb);
+  float* dG = reinterpret_cast<float*>(base + xb + align_up(usz * 4));
+  RT_CUDA(h, cudaMemcpyAsync(dX, X_host, (size_t)total * dtype_size(dtype), cudaMemcpyHostToDevice, h->stream));
+  st = rtucker_decompose(h, dX, dtype, d, n, r, p, s, seed, opt, dU, dG);
+  if (st != RT_OK) return st;
+  const int nl = h->launches;
+  RT_CUDA(h, cudaMemcpyAsync(U_host, dU, usz * 4, cudaMemcpyDeviceToHost, h->stream));
+  RT_CUDA(h, cudaMemcpyAsync(G_host, dG, gsz * 4, cudaMemcpyDeviceToHost, h->stream));
+  st = rt_sync(h);
+  h->launches = nl;
+  return st;
+}
+
+rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt_dtype dtype, const int32_t* d,
+                                    const int64_t* const* n, const int32_t* const* r, int32_t p,
+                                    const int64_t* const* s, const uint64_t* seeds, const rt_options* opt,
+                                    float* const* U, float* const* G) {
+  if (!h) return RT_EINVAL;
+  if (T < 1 || !X || !d || !n || !r || !seeds || !U || !G) return fail(h, RT_EINVAL, "null batched argument");
+  rt_status st;
+  if ((st = check_opts(h, opt)) != RT_OK) return st;
+  for (int t = 0; t < T; ++t)
+    if ((st = check_tensor(h, X[t], dtype, d[t], n[t], nullptr)) != RT_OK) return st;
+  if ((st = check_prior_status(h)) != RT_OK) return st;
+  if ((st = init_device_attrs(h)) != RT_OK) return st;
+  Group Gp;
+  Bump bump;
+  for (int t = 0; t < T; ++t) {
+    st = add_tucker_problems(h, Gp, bump, X[t], dtype, d[t], n[t], r[t], p, s ? s[t] : nullptr, seeds[t], U[t],
+                             nullptr);
+    if (st != RT_OK) return st;
+  }
+  group_layout(Gp, bump);
+  // per-tensor core buffers
+  std::vector<size_t> oA(T), oB(T);
+  for (int t = 0; t < T; ++t) {
+    const size_t cb = core_buffer_floats(d[t], n[t], r[t]);
+    oA[t] = bump.take(cb * 4);
+    oB[t] = bump.take(cb * 4);
+  }
+  if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
+  if ((st = ensure_stage(h, group_stage_bytes(Gp))) != RT_OK) return st;
+  if ((st = group_upload(h, Gp, h->h_stage, 0)) != RT_OK) return st;
+  RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
+  h->stage_pending = true;
+  int nl = launch_range_finder(Gp.g, h->stream, h->d_status);
+  for (int t = 0; t < T; ++t)
+    nl += enqueue_core(X[t], dtype, d[t], n[t], r[t], U[t], G[t], reinterpret_cast<float*>(h->ws + oA[t]),
+                       reinterpret_cast<float*>(h->ws + oB[t]), h->stream);
+  return finish(h, nl);
+}
+
+rt_status rtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
+                         const float* U, const float* G, double* out) {
+  rt_status st;
+  if ((st = check_tensor(h, X, dtype, d, n, nullptr)) != RT_OK) return st;
+  if (!r || !U || !G || !out) return fail(h, RT_EINVAL, "r, U, G and out are required");
+  const size_t sd = tucker_relerr_scratch(d, n, r);
+  Bump bump;
+  const size_t o = bump.take(sd * 8);
+  const size_t o_res = bump.take(16);
+  if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
+  const float* Uk[MAXD];
+  size_t off = 0;
+  for (int k = 0; k < d; ++k) { Uk[k] = U + off; off += (size_t)n[k] * r[k]; }
+  if ((size_t)r[d - 2] * n[d - 1] * 8 > 200 * 1024) return fail(h, RT_ENOTSUP, "evaluator slab too large");
+  double* res = reinterpret_cast<double*>(h->ws + o_res);
+  const int nl = launch_tucker_relerr(X, (int)dtype, d, n, r, Uk, G, reinterpret_cast<double*>(h->ws + o), sd, res,
+                                      h->stream);
+  h->launches = nl;
+  RT_CUDA(h, cudaGetLastError());
+  double hr[2];
+  RT_CUDA(h, cudaMemcpyAsync(hr, res, 16, cudaMemcpyDeviceToHost, h->stream));
+  RT_CUDA(h, cudaStreamSynchronize(h->stream));
+  *out = (hr[1] > 0) ? sqrt(hr[0] / hr[1]) : 0.0;
+  return RT_OK;
+}
+
+rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                             const int32_t* rank, int32_t p, const int64_t* w, uint64_t seed,
+                             const rt_options* opt, float* U_leaf, float* B, float* U_nodes) {
+  rt_status st;
+  int64_t total = 0;
+  if ((st = check_tensor(h, X, dtype, d, n, &total)) != RT_OK) return st;
+  if ((st = check_opts(h, opt)) != RT_OK) return st;
+  if (!rank || !U_leaf || !B) return fail(h, RT_EINVAL, "rank, U_leaf and B are required");
+  if ((st = check_prior_status(h)) != RT_OK) return st;
+  if ((st = init_device_attrs(h)) != RT_OK) return st;
+  const std::vector<TNode> tree = balanced_tree(d);
+  const int nn = (int)tree.size();
+  std::vector<int> rk(nn);
+  for (int i = 0; i < nn; ++i) rk[i] = (i == 0) ? 1 : rank[i];
+  int64_t nmax = 0;
+  for (int k = 0; k < d; ++k) nmax = std::max(nmax, n[k]);
+  // output offsets
+  std::vector<size_t> o_unode(nn, 0), o_leaf(nn, 0), o_B(nn, 0);
+  size_t acc = 0;
+  for (int i = 1; i < nn; ++i) { o_unode[i] = acc; acc += (size_t)range_prod(n, tree[i].a, tree[i].b) * rk[i]; }
+  acc = 0;
+  for (int k = 0; k < d; ++k)
+    for (int i = 1; i < nn; ++i)
+      if (tree[i].a == k && tree[i].b == k) { o_leaf[i] = acc; acc += (size_t)n[k] * rk[i]; }
+  acc = 0;
+  for (int i = 0; i < nn; ++i)
+    if (tree[i].a != tree[i].b) { o_B[i] = acc; acc += (size_t)rk[i] * rk[tree[i].left] * rk[tree[i].right]; }
+  Group Gp;
+  Bump bump;
+  std::vector<int> prob_of(nn, -1);
+  for (int i = 1; i < nn; ++i) {
+    const TNode& nd = tree[i];
+    const bool leaf = nd.a == nd.b;
+    ProbSpec ps{};
+    ps.X = X;
+    ps.dtype = dtype;
+    ps.d = d;
+    for (int j = 0; j < d; ++j) ps.n[j] = n[j];
+    ps.a = nd.a;
+    ps.b = nd.b;
+    ps.r = rk[i];
+    ps.p = p;
+    const int64_t N = total / range_prod(n, nd.a, nd.b);
+    ps.s = w ? w[i] : std::min<int64_t>(20 * nmax, N);
+    ps.seed = seed;
+    ps.node = (uint32_t)i;
+    ps.U = U_nodes ? U_nodes + o_unode[i] : (leaf ? U_leaf + o_leaf[i] : nullptr);
+    ProbPlan pp;
+    if ((st = plan_problem(h, ps, bump, pp)) != RT_OK) return st;
+    prob_of[i] = (int)Gp.pp.size();
+    Gp.pp.push_back(pp);
+  }
+  group_layout(Gp, bump);
+  // transfer jobs (internal non-root nodes) and the root
+  std::vector<int> internal;
+  for (int i = 1; i < nn; ++i)
+    if (tree[i].a != tree[i].b) internal.push_back(i);
+  const size_t o_jobs = bump.take(sizeof(TransferJob) * std::max<size_t>(1, internal.size()));
+  const TNode& root = tree[0];
+  const int64_t nl = range_prod(n, root.a, tree[root.left].b), nr = total / nl;
+  const int rl = rk[root.left], rr = rk[root.right];
+  if (rr > 12) return fail(h, RT_ENOTSUP, "rank of the root's right child above 12");
+  const size_t o_rootp = bump.take(root_scratch_floats(nl, nr, rl, rr) * 4);
+  for (int i : internal) {
+    const int64_t nlc = range_prod(n, tree[tree[i].left].a, tree[tree[i].left].b);
+    if ((size_t)nlc * rk[tree[i].right] * 4 > 200 * 1024)
+      return fail(h, RT_ENOTSUP, "child basis too large for the transfer-tensor kernel");
+  }
+  if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
+  const size_t sb = group_stage_bytes(Gp) + align_up(sizeof(TransferJob) * std::max<size_t>(1, internal.size()));
+  if ((st = ensure_stage(h, sb)) != RT_OK) return st;
+  if ((st = group_upload(h, Gp, h->h_stage, 0)) != RT_OK) return st;
+  auto Uof = [&](int i) { return Gp.pp[prob_of[i]].q.U; };
+  TransferJob* jobs = reinterpret_cast<TransferJob*>(h->h_stage + group_stage_bytes(Gp));
+  for (size_t q = 0; q < internal.size(); ++q) {
+    const int i = internal[q];
+    const TNode& nd = tree[i];
+    TransferJob jb;
+    jb.US = Uof(i);
+    jb.Ul = Uof(nd.left);
+    jb.Ur = Uof(nd.right);
+    jb.B = B + o_B[i];
+    jb.nl = range_prod(n, tree[nd.left].a, tree[nd.left].b);
+    jb.nr = range_prod(n, tree[nd.right].a, tree[nd.right].b);
+    jb.rS = rk[i];
+    jb.rl = rk[nd.left];
+    jb.rr = rk[nd.right];
+    jobs[q] = jb;
+  }
+  if (!internal.empty())
+    RT_CUDA(h, cudaMemcpyAsync(h->ws + o_jobs, jobs, sizeof(TransferJob) * internal.size(),
+                               cudaMemcpyHostToDevice, h->stream));
+  RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
+  h->stage_pending = true;
+  int nlaunch = launch_range_finder(Gp.g, h->stream, h->d_status);
+  if (U_nodes) {
+    for (int i = 1; i < nn; ++i)
+      if (tree[i].a == tree[i].b)
+        RT_CUDA(h, cudaMemcpyAsync(U_leaf + o_leaf[i], U_nodes + o_unode[i], (size_t)n[tree[i].a] * rk[i] * 4,
+                                   cudaMemcpyDeviceToDevice, h->stream));
+  }
+  nlaunch += launch_transfer(reinterpret_cast<const TransferJob*>(h->ws + o_jobs), jobs, (int)internal.size(),
+                             h->stream);
+  nlaunch += launch_root(X, (int)dtype, nl, nr, Uof(root.left), rl, Uof(root.right), rr, B + o_B[0],
+                         reinterpret_cast<float*>(h->ws + o_rootp), h->stream);
+  return finish(h, nlaunch);
+}
+
+rt_status rhtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                          const int32_t* rank, const float* U_leaf, const float* B, double* out) {
+  rt_status st;
+  int64_t total = 0;
+  if ((st = check_tensor(h, X, dtype, d, n, &total)) != RT_OK) return st;
+  if (!rank || !U_leaf || !B || !out) return fail(h, RT_EINVAL, "rank, U_leaf, B and out are required");
+  const std::vector<TNode> tree = balanced_tree(d);
+  const int nn = (int)tree.size();
+  std::vector<int> rk(nn);
+  for (int i = 0; i < nn; ++i) rk[i] = (i == 0) ? 1 : rank[i];
+  const TNode& root = tree[0];
+  if (rk[root.right] > 16) return fail(h, RT_ENOTSUP, "rank of the root's right child above 16");
+  std::vector<size_t> o_u(nn, 0), o_leaf(nn, 0), o_B(nn, 0);
+  Bump bump;
+  for (int i = 1; i < nn; ++i) o_u[i] = bump.take((size_t)range_prod(n, tree[i].a, tree[i].b) * rk[i] * 8);
+  size_t acc = 0;
+  for (int k = 0; k < d; ++k)
+    for (int i = 1; i < nn; ++i)
+      if (tree[i].a == k && tree[i].b == k) { o_leaf[i] = acc; acc += (size_t)n[k] * rk[i]; }
+  acc = 0;
+  for (int i = 0; i < nn; ++i)
+    if (tree[i].a != tree[i].b) { o_B[i] = acc; acc += (size_t)rk[i] * rk[tree[i].left] * rk[tree[i].right]; }
+  const int64_t nl = range_prod(n, root.a, tree[root.left].b), nr = total / nl;
+  const size_t o_scr = bump.take(ht_relerr_scratch(nl, nr) * 8);
+  const size_t o_res = bump.take(16);
+  if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
+  auto U64 = [&](int i) { return reinterpret_cast<double*>(h->ws + o_u[i]); };
+  int nlaunch = 0;
+  for (int i = 1; i < nn; ++i)
+    if (tree[i].a == tree[i].b)
+      nlaunch += launch_f32_to_f64(U_leaf + o_leaf[i], U64(i), n[tree[i].a] * rk[i], h->stream);
+  int maxlev = 0;
+  for (int i = 0; i < nn; ++i) maxlev = std::max(maxlev, tree[i].level);
+  for (int lev = maxlev; lev >= 1; --lev)
+    for (int i = 1; i < nn; ++i) {
+      const TNode& nd = tree[i];
+      if (nd.level != lev || nd.a == nd.b) continue;
+      nlaunch += launch_ht_expand(U64(nd.left), range_prod(n, tree[nd.left].a, tree[nd.left].b), rk[nd.left],
+                                  U64(nd.right), range_prod(n, tree[nd.right].a, tree[nd.right].b), rk[nd.right],
+                                  B + o_B[i], rk[i], U64(i), h->stream);
+    }
+  double* res = reinterpret_cast<double*>(h->ws + o_res);
+  nlaunch += launch_ht_relerr(X, (int)dtype, nl, nr, U64(root.left), rk[root.left], B + o_B[0], U64(root.right),
+                              rk[root.right], reinterpret_cast<double*>(h->ws + o_scr), res, h->stream);
+  h->launches = nlaunch;
+  RT_CUDA(h, cudaGetLastError());
+  double hr[2];
+  RT_CUDA(h, cudaMemcpyAsync(hr, res, 16, cudaMemcpyDeviceToHost, h->stream));
+  RT_CUDA(h, cudaStreamSynchronize(h->stream));
+  *out = (hr[1] > 0) ? sqrt(hr[0] / hr[1]) : 0.0;
+  return RT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,660 @@
+// rf_kernels.cu - range finder of the subsampled randomized HOSVD / RtL-HT.
+//
+// For every problem (mode k of a tensor, Alg. 1; or node S of the dimension
+// tree, Alg. 2) the stages are:
+//   S1  sample  : pi(j), column offsets in X, Gaussian rows Omega(j, :)  (Sec. 3.1)
+//   S2+S4 gather/sketch : Y = X^(S) E (kept as Y^T), Z = Y Omega (partials per
+//         sample chunk)                                                  (Sec. 3.1)
+//   S5  qr      : Z = Q R, Householder in shared memory, diag(R) > 0; tall Z
+//         by a two-level TSQR                                     (Alg. 1, Q_k)
+//   S6  W-step  : B = Q^T Y; TSQR of B^T -> R; one-sided Jacobi on R^T gives
+//         the left singular vectors W of B (B B^T = R^T R); U = Q W(:, :r) with
+//         each column's largest-magnitude entry made positive     (Alg. 1, W_k, U_k)
+// All arithmetic is float32.  GB300's float64 rate is ~1/64 of float32, so the
+// small factorisations use backward-stable float32 algorithms (Householder,
+// one-sided Jacobi) instead of float64 Gram/eigen solves: the singular vectors
+// then carry errors of order u ||B|| / gap rather than u ||B||^2 / gap^2.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rt_common.cuh"
+#include "rt_host.h"
+#include "rt_rng.cuh"
+
+namespace rt {
+
+// ------------------------------------------------------------------ S1
+__global__ void __launch_bounds__(256) k_sample(const RFProb* __restrict__ P,
+                                                const int64_t* __restrict__ pre, int np,
+                                                int* status) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= pre[np]) return;
+  const int p = find_prob(pre, np, t);
+  const RFProb& q = P[p];
+  const int64_t j = t - pre[p];
+  const PhiloxKey key = philox_key(q.seed);
+  const uint64_t m = sample_index((uint64_t)j, (uint64_t)q.N, q.fh, key, q.node, status);
+  q.idx[j] = (int64_t)m;
+  uint64_t rem = m;
+  int64_t off = 0;
+  for (int t2 = q.ncm - 1; t2 >= 0; --t2) {
+    const uint64_t sz = (uint64_t)q.csize[t2];
+    off += (int64_t)(rem % sz) * q.cstride[t2];
+    rem /= sz;
+  }
+  q.off[j] = off;
+  float* om = q.Om + j * q.c;
+  for (int c = 0; c < q.c; ++c) om[c] = gauss_entry(m, (uint32_t)c, key, q.node);
+}
+
+// ------------------------------------------------------------------ S2 + S4
+// One CTA: rows [i0, i0+TI) x samples [j0, j0+TJ) of Y = X^(S) E.
+// Dynamic smem: Ys[TJ][TI] | Os[TJ][CMAX] | offs[TJ] (int64)
+__global__ void __launch_bounds__(256) k_gather_sketch(const RFProb* __restrict__ P,
+                                                       const int64_t* __restrict__ pre, int np) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ys = reinterpret_cast<float*>(smem_raw);
+  float* Os = Ys + SK_TJ * SK_TI;
+  int64_t* offs = reinterpret_cast<int64_t*>(Os + SK_TJ * CMAX);
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int64_t local = (int64_t)blockIdx.x - pre[p];
+  const int64_t nrt = (q.nS + SK_TI - 1) / SK_TI;
+  const int64_t chunk = local / nrt, rtile = local % nrt;
+  const int64_t i0 = rtile * SK_TI, j0 = chunk * SK_TJ;
+  const int c = q.c, cp = (c + 3) & ~3;
+  const int tid = threadIdx.x;
+  if (tid < SK_TJ) offs[tid] = (j0 + tid < q.s) ? q.off[j0 + tid] : (int64_t)-1;
+  __syncthreads();
+  const int64_t nS = q.nS, rs = q.rowstride;
+#pragma unroll 4
+  for (int e = tid; e < SK_TI * SK_TJ; e += 256) {
+    const int jj = e / SK_TI, ii = e % SK_TI;
+    const int64_t i = i0 + ii;
+    float v = 0.f;
+    const int64_t o = offs[jj];
+    if (i < nS && o >= 0) {
+      v = load_x(q.X, q.dtype, o + i * rs);
+      q.Yt[(j0 + jj) * nS + i] = v;
+    }
+    Ys[jj * SK_TI + ii] = v;
+  }
+  for (int e = tid; e < SK_TJ * cp; e += 256) {
+    const int jj = e / cp, cc = e % cp;
+    Os[jj * CMAX + cc] = (j0 + jj < q.s && cc < c) ? q.Om[(j0 + jj) * c + cc] : 0.f;
+  }
+  __syncthreads();
+  const int ncg = cp >> 2;
+  float* zp = q.Zp + chunk * nS * c;
+  for (int t = tid; t < (SK_TI / 4) * ncg; t += 256) {
+    const int rg = t % (SK_TI / 4), cg = t / (SK_TI / 4);
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+#pragma unroll 8
+    for (int jj = 0; jj < SK_TJ; ++jj) {
+      const float4 y = *reinterpret_cast<const float4*>(Ys + jj * SK_TI + rg * 4);
+      const float4 o = *reinterpret_cast<const float4*>(Os + jj * CMAX + cg * 4);
+      const float ya[4] = {y.x, y.y, y.z, y.w};
+      const float ob[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(ya[a], ob[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int64_t i = i0 + rg * 4 + a;
+      if (i >= nS) continue;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int col = cg * 4 + b;
+        if (col < c) zp[i * c + col] = acc[a][b];
+      }
+    }
+  }
+}
+
+// Z = sum over sample chunks of the partial sketches (test/inspection path).
+__global__ void k_sketch_sum(const RFProb* __restrict__ P, const int64_t* __restrict__ pre, int np,
+                             float* const* __restrict__ Zout) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= pre[np]) return;
+  const int p = find_prob(pre, np, t);
+  const RFProb& q = P[p];
+  const int64_t e = t - pre[p];
+  const int64_t sz = q.nS * q.c;
+  float acc = 0.f;
+  for (int ch = 0; ch < q.nzc; ++ch) acc += q.Zp[ch * sz + e];
+  Zout[p][e] = acc;
+}
+
+// ------------------------------------------------------------------ Householder QR in smem
+// A is column-major (A[col * ld + row]), m x c.  On exit the columns hold the
+// Householder vectors v_k (v_k[k] stored at A[k*ld+k]), the strict upper part
+// holds R, rdiag[k] = R_kk and tau[k] the reflector scales, H_k = I - tau v v^T.
+__device__ void hh_factor(float* A, int ld, int m, int c, float* tau, float* rdiag, float* red) {
+  const int K = min(m, c);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = 0; k < K; ++k) {
+    float* a = A + (size_t)k * ld;
+    float part = 0.f;
+    for (int i = k + threadIdx.x; i < m; i += blockDim.x) part = fmaf(a[i], a[i], part);
+    const float nrm2 = block_sum(part, red);
+    if (threadIdx.x == 0) {
+      const float x0 = a[k];
+      const float nrm = sqrtf(nrm2);
+      if (nrm == 0.f) {
+        tau[k] = 0.f;
+        rdiag[k] = 0.f;
+      } else {
+        const float alpha = (x0 >= 0.f) ? -nrm : nrm;
+        tau[k] = 1.f / (nrm * (nrm + fabsf(x0)));   // 2 / (v^T v)
+        rdiag[k] = alpha;
+        a[k] = x0 - alpha;
+      }
+    }
+    __syncthreads();
+    const float tk = tau[k];
+    if (tk != 0.f) {
+      for (int j = k + 1 + warp; j < c; j += nw) {
+        float* aj = A + (size_t)j * ld;
+        float w = 0.f;
+        for (int i = k + lane; i < m; i += 32) w = fmaf(a[i], aj[i], w);
+        w = warp_sum(w) * tk;
+        for (int i = k + lane; i < m; i += 32) aj[i] = fmaf(-w, a[i], aj[i]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Qm (column-major, ld) = H_0 ... H_{K-1} [I; 0], then the signs making diag(R) > 0.
+__device__ void hh_form_q(const float* A, float* Qm, int ld, int m, int c, const float* tau,
+                          const float* rdiag, bool fix_sign) {
+  const int K = min(m, c);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
+    const int j = e / m, i = e % m;
+    Qm[(size_t)j * ld + i] = (i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  for (int k = K - 1; k >= 0; --k) {
+    const float tk = tau[k];
+    if (tk != 0.f) {
+      const float* v = A + (size_t)k * ld;
+      for (int j = k + warp; j < c; j += nw) {
+        float* qj = Qm + (size_t)j * ld;
+        float w = 0.f;
+        for (int i = k + lane; i < m; i += 32) w = fmaf(v[i], qj[i], w);
+        w = warp_sum(w) * tk;
+        for (int i = k + lane; i < m; i += 32) qj[i] = fmaf(-w, v[i], qj[i]);
+      }
+    }
+    __syncthreads();
+  }
+  if (fix_sign) {
+    for (int e = threadIdx.x; e < m * K; e += blockDim.x) {
+      const int j = e / m, i = e % m;
+      if (rdiag[j] < 0.f) Qm[(size_t)j * ld + i] = -Qm[(size_t)j * ld + i];
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ int odd_ld(int m) { return m | 1; }
+
+// S5 level 1: QR of one row block of Z (sum of sketch partials).  Single-block
+// problems finish here (signs fixed); tall problems also write R_b.
+// Dynamic smem: A[ld*c] | Qm[ld*c] | tau[CMAX] | rdiag[CMAX] | red[32]
+__global__ void __launch_bounds__(512) k_qr1(const RFProb* __restrict__ P,
+                                             const int64_t* __restrict__ pre, int np) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int b = (int)((int64_t)blockIdx.x - pre[p]);
+  const int c = q.c;
+  const int64_t row0 = (int64_t)b * q.rbrows;
+  const int m = (int)min((int64_t)q.rbrows, q.nS - row0);
+  const int ld = odd_ld(m);
+  float* A = reinterpret_cast<float*>(smem_raw);
+  float* Qm = A + (size_t)ld * c;
+  float* tau = Qm + (size_t)ld * c;
+  float* rdiag = tau + CMAX;
+  float* red = rdiag + CMAX;
+  const int64_t zsz = q.nS * c;
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    const int64_t g = (row0 + i) * c + j;
+    float acc = 0.f;
+    for (int ch = 0; ch < q.nzc; ++ch) acc += q.Zp[ch * zsz + g];
+    A[(size_t)j * ld + i] = acc;
+  }
+  __syncthreads();
+  hh_factor(A, ld, m, c, tau, rdiag, red);
+  const bool single = (q.nrb == 1);
+  if (!single) {  // R_b (c x c, zero below the diagonal and beyond row K)
+    float* Rb = q.Rb + (size_t)b * c * c;
+    for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+      const int k = e / c, j = e % c;
+      float v = 0.f;
+      if (k < m && j >= k) v = (j == k) ? rdiag[k] : A[(size_t)j * ld + k];
+      Rb[e] = v;
+    }
+  }
+  hh_form_q(A, Qm, ld, m, c, tau, rdiag, single);
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    q.Q[(row0 + i) * c + j] = Qm[(size_t)j * ld + i];
+  }
+}
+
+// S5 level 2 (tall Z): QR of the stacked R_b, (nrb c) x c; Q2 with diag(R) > 0.
+__global__ void __launch_bounds__(512) k_qr2(const RFProb* __restrict__ P,
+                                             const int64_t* __restrict__ pre, int np) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int c = q.c;
+  const int m = q.nrb * c;
+  const int ld = odd_ld(m);
+  float* A = reinterpret_cast<float*>(smem_raw);
+  float* Qm = A + (size_t)ld * c;
+  float* tau = Qm + (size_t)ld * c;
+  float* rdiag = tau + CMAX;
+  float* red = rdiag + CMAX;
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    A[(size_t)j * ld + i] = q.Rb[e];
+  }
+  __syncthreads();
+  hh_factor(A, ld, m, c, tau, rdiag, red);
+  hh_form_q(A, Qm, ld, m, c, tau, rdiag, true);
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    q.Q2[e] = Qm[(size_t)j * ld + i];
+  }
+}
+
+// S5 level 3 (tall Z): Q[block b] = Q_b * Q2[b c : b c + c, :].
+// Dynamic smem: Qb[rbrows*c] | Q2b[c*c]
+__global__ void __launch_bounds__(256) k_qr3(const RFProb* __restrict__ P,
+                                             const int64_t* __restrict__ pre, int np) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int b = (int)((int64_t)blockIdx.x - pre[p]);
+  const int c = q.c;
+  const int64_t row0 = (int64_t)b * q.rbrows;
+  const int m = (int)min((int64_t)q.rbrows, q.nS - row0);
+  float* Qb = reinterpret_cast<float*>(smem_raw);
+  float* Q2b = Qb + (size_t)q.rbrows * c;
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) Qb[e] = q.Q[row0 * c + e];
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) Q2b[e] = q.Q2[(size_t)b * c * c + e];
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    float acc = 0.f;
+    for (int t = 0; t < c; ++t) acc = fmaf(Qb[i * c + t], Q2b[t * c + j], acc);
+    q.Q[(row0 + i) * c + j] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ S6: B^T = Y^T Q
+// Partial over rows [ib*BT_IB, ...) for samples [sc*scrows, ...): 4x4 register
+// micro-tiles over (sample, column).
+// Dynamic smem: Ys[32][BT_LDY] (row ii, sample jj) | Qs[32][CMAX]
+constexpr int BT_LDY = BT_SC + 4;
+__global__ void __launch_bounds__(256) k_bt_partial(const RFProb* __restrict__ P,
+                                                    const int64_t* __restrict__ pre, int np) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ys = reinterpret_cast<float*>(smem_raw);
+  float* Qs = Ys + 32 * BT_LDY;
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int64_t local = (int64_t)blockIdx.x - pre[p];
+  const int sc = (int)(local / q.nbi), ib = (int)(local % q.nbi);
+  const int c = q.c, cp = (c + 3) & ~3;
+  const int64_t j0 = (int64_t)sc * q.scrows;
+  const int mj = (int)min((int64_t)q.scrows, q.s - j0);
+  const int64_t iA = (int64_t)ib * BT_IB, iB = min(q.nS, iA + BT_IB);
+  const int ntile = (BT_SC / 4) * (cp / 4);  // <= 32 * 16 = 512: two tiles per thread
+  float acc[2][4][4];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[u][a][b] = 0.f;
+  for (int64_t it = iA; it < iB; it += 32) {
+    const int mi = (int)min((int64_t)32, iB - it);
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * BT_SC; e += 256) {
+      const int jj = e / 32, ii = e % 32;
+      Ys[ii * BT_LDY + jj] = (jj < mj && ii < mi) ? q.Yt[(j0 + jj) * q.nS + it + ii] : 0.f;
+    }
+    for (int e = threadIdx.x; e < 32 * cp; e += 256) {
+      const int ii = e / cp, cc = e % cp;
+      Qs[ii * CMAX + cc] = (ii < mi && cc < c) ? q.Q[(it + ii) * c + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int t = threadIdx.x + 256 * u;
+      if (t < ntile) {
+        const int jg = t % (BT_SC / 4), cg = t / (BT_SC / 4);
+#pragma unroll 8
+        for (int ii = 0; ii < 32; ++ii) {
+          const float4 y = *reinterpret_cast<const float4*>(Ys + ii * BT_LDY + jg * 4);
+          const float4 o = *reinterpret_cast<const float4*>(Qs + ii * CMAX + cg * 4);
+          const float ya[4] = {y.x, y.y, y.z, y.w};
+          const float ob[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[u][a][b] = fmaf(ya[a], ob[b], acc[u][a][b]);
+        }
+      }
+    }
+  }
+  float* out = q.Bp + ((size_t)ib * q.s + j0) * c;
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int t = threadIdx.x + 256 * u;
+    if (t < ntile) {
+      const int jg = t % (BT_SC / 4), cg = t / (BT_SC / 4);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int jj = jg * 4 + a;
+        if (jj >= mj) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int cc = cg * 4 + b;
+          if (cc < c) out[(size_t)jj * c + cc] = acc[u][a][b];
+        }
+      }
+    }
+  }
+}
+
+// S6: QR of one sample chunk of B^T (sum of the row-block partials) -> R_chunk.
+// Dynamic smem: A[ld*c] | tau | rdiag | red
+__global__ void __launch_bounds__(512) k_bt_qr(const RFProb* __restrict__ P,
+                                               const int64_t* __restrict__ pre, int np) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int sc = (int)((int64_t)blockIdx.x - pre[p]);
+  const int c = q.c;
+  const int64_t j0 = (int64_t)sc * q.scrows;
+  const int m = (int)min((int64_t)q.scrows, q.s - j0);
+  const int ld = odd_ld(m);
+  float* A = reinterpret_cast<float*>(smem_raw);
+  float* tau = A + (size_t)ld * c;
+  float* rdiag = tau + CMAX;
+  float* red = rdiag + CMAX;
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    float acc = 0.f;
+    for (int ib = 0; ib < q.nbi; ++ib) acc += q.Bp[((size_t)ib * q.s + j0 + i) * c + j];
+    A[(size_t)j * ld + i] = acc;
+  }
+  __syncthreads();
+  hh_factor(A, ld, m, c, tau, rdiag, red);
+  float* Rc = q.Rc + (size_t)sc * c * c;
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    const int k = e / c, j = e % c;
+    float v = 0.f;
+    if (k < m && j >= k) v = (j == k) ? rdiag[k] : A[(size_t)j * ld + k];
+    Rc[e] = v;
+  }
+}
+
+// S6: R of the stacked chunk factors, then one-sided Jacobi (Hestenes) on the
+// columns of R^T: R^T V = W Sigma, W = left singular vectors of B.  Columns
+// are processed in round-robin order, one warp per pair, until a sweep makes
+// no rotation (or 40 sweeps).  W is stored sorted by descending sigma.
+// Dynamic smem: A[ld*c] | tau | rdiag | red | AT[CMAX*(CMAX+1)] | sig[CMAX] | flag
+__global__ void __launch_bounds__(1024) k_wsvd(const RFProb* __restrict__ P,
+                                               const int64_t* __restrict__ pre, int np,
+                                               int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int c = q.c;
+  const int m = q.nsc * c;
+  const int ld = odd_ld(m);
+  float* A = reinterpret_cast<float*>(smem_raw);
+  float* tau = A + (size_t)ld * c;
+  float* rdiag = tau + CMAX;
+  float* red = rdiag + CMAX;
+  float* AT = red + 32;                  // column q of R^T at AT[q*(CMAX+1) + i]
+  float* sig = AT + CMAX * (CMAX + 1);
+  int* flag = reinterpret_cast<int*>(sig + CMAX);
+  const int LDT = CMAX + 1;
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    A[(size_t)j * ld + i] = q.Rc[e];
+  }
+  if (threadIdx.x < q.r) q.keys[threadIdx.x] = 0ull;
+  __syncthreads();
+  hh_factor(A, ld, m, c, tau, rdiag, red);
+  // AT[qc][i] = R[qc][i]  (column qc of R^T is row qc of R)
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    const int qc = e / c, i = e % c;
+    float v = 0.f;
+    if (qc < m && i >= qc) v = (i == qc) ? rdiag[qc] : A[(size_t)i * ld + qc];
+    AT[qc * LDT + i] = v;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ne = c + (c & 1);           // even number of players (dummy = c)
+  const float tol = 1e-6f;
+  int sweep = 0;
+  for (; sweep < 40; ++sweep) {
+    if (threadIdx.x == 0) *flag = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < ne - 1; ++rnd) {
+      for (int pr = warp; pr < ne / 2; pr += nw) {
+        const int pa = (pr == 0) ? 0 : 1 + (pr - 1 + rnd) % (ne - 1);
+        const int qa = 1 + (ne - 2 - pr + rnd) % (ne - 1);
+        if (pa >= c || qa >= c) continue;
+        float* ap = AT + pa * LDT;
+        float* aq = AT + qa * LDT;
+        float al = 0.f, be = 0.f, ga = 0.f;
+        for (int i = lane; i < c; i += 32) {
+          const float x = ap[i], y = aq[i];
+          al = fmaf(x, x, al);
+          be = fmaf(y, y, be);
+          ga = fmaf(x, y, ga);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga = warp_sum(ga);
+        if (ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
+          const float zeta = (be - al) / (2.f * ga);
+          float t;
+          if (fabsf(zeta) > 1e18f) t = 0.5f / zeta;
+          else t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+          const float cs = rsqrtf(1.f + t * t), sn = cs * t;
+          for (int i = lane; i < c; i += 32) {
+            const float x = ap[i], y = aq[i];
+            ap[i] = cs * x - sn * y;
+            aq[i] = sn * x + cs * y;
+          }
+          if (lane == 0) *flag = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int f = *flag;
+    __syncthreads();
+    if (!f) break;
+  }
+  if (sweep == 40 && threadIdx.x == 0) set_status(status, ST_NUMERIC);
+  // singular values (column norms) and descending order
+  for (int qc = warp; qc < c; qc += nw) {
+    float s2 = 0.f;
+    for (int i = lane; i < c; i += 32) s2 = fmaf(AT[qc * LDT + i], AT[qc * LDT + i], s2);
+    s2 = warp_sum(s2);
+    if (lane == 0) sig[qc] = sqrtf(s2);
+  }
+  __syncthreads();
+  if (threadIdx.x < c) {
+    const int qc = threadIdx.x;
+    const float sq = sig[qc];
+    if (!(sq == sq)) set_status(status, ST_NUMERIC);
+    int rank = 0;
+    for (int t = 0; t < c; ++t) rank += (sig[t] > sq) || (sig[t] == sq && t < qc);
+    q.sigma[rank] = sq;
+    if (q.sigma_out) q.sigma_out[rank] = sq;
+    const float inv = (sq > 0.f) ? 1.f / sq : 0.f;
+    for (int i = 0; i < c; ++i) q.W[i * c + rank] = AT[qc * LDT + i] * inv;
+  }
+}
+
+// ------------------------------------------------------------------ U = Q W(:, :r), sign rule
+__device__ __forceinline__ float qw_entry(const float* __restrict__ Qrow, const float* Ws, int c,
+                                          int col, int ldw) {
+  float acc = 0.f;
+  for (int t = 0; t < c; ++t) acc = fmaf(Qrow[t], Ws[t * ldw + col], acc);
+  return acc;
+}
+
+__device__ __forceinline__ unsigned long long sign_key(float v, int64_t row) {
+  return ((unsigned long long)__float_as_uint(fabsf(v)) << 32) |
+         (unsigned long long)(0xffffffffu - (uint32_t)row);
+}
+
+// Dynamic smem: Ws[CMAX*CMAX] | Qs[QW_TI*CMAX] | keys[CMAX] (u64)
+__global__ void __launch_bounds__(256) k_qw(const RFProb* __restrict__ P,
+                                            const int64_t* __restrict__ pre, int np) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ws = reinterpret_cast<float*>(smem_raw);
+  float* Qs = Ws + CMAX * CMAX;
+  unsigned long long* kb = reinterpret_cast<unsigned long long*>(Qs + QW_TI * CMAX);
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int64_t row0 = ((int64_t)blockIdx.x - pre[p]) * QW_TI;
+  const int m = (int)min((int64_t)QW_TI, q.nS - row0);
+  const int c = q.c, r = q.r;
+  for (int e = threadIdx.x; e < c * r; e += blockDim.x) Ws[(e / r) * CMAX + e % r] = q.W[(e / r) * c + e % r];
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) Qs[e] = q.Q[row0 * c + e];
+  if (threadIdx.x < r) kb[threadIdx.x] = 0ull;
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
+    const int i = e / r, col = e % r;
+    const float u = qw_entry(Qs + i * c, Ws, c, col, CMAX);
+    q.U[(row0 + i) * r + col] = u;
+    atomicMax(&kb[col], sign_key(u, row0 + i));
+  }
+  __syncthreads();
+  if (threadIdx.x < r) atomicMax(&q.keys[threadIdx.x], kb[threadIdx.x]);
+}
+
+__global__ void __launch_bounds__(256) k_flip(const RFProb* __restrict__ P,
+                                              const int64_t* __restrict__ pre, int np) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ws = reinterpret_cast<float*>(smem_raw);
+  float* sg = Ws + CMAX * CMAX;
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int64_t row0 = ((int64_t)blockIdx.x - pre[p]) * QW_TI;
+  const int m = (int)min((int64_t)QW_TI, q.nS - row0);
+  const int c = q.c, r = q.r;
+  for (int e = threadIdx.x; e < c * r; e += blockDim.x) Ws[(e / r) * CMAX + e % r] = q.W[(e / r) * c + e % r];
+  __syncthreads();
+  if (threadIdx.x < r) {
+    const int col = threadIdx.x;
+    const unsigned long long key = q.keys[col];
+    const int64_t rstar = (int64_t)(0xffffffffu - (uint32_t)(key & 0xffffffffull));
+    const float u = qw_entry(q.Q + rstar * c, Ws, c, col, CMAX);
+    sg[col] = (u < 0.f) ? -1.f : 1.f;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
+    const int col = e % r;
+    if (sg[col] < 0.f) q.U[row0 * r + e] = -q.U[row0 * r + e];
+  }
+}
+
+// ------------------------------------------------------------------ host launchers
+static size_t smem_gs() { return (size_t)(SK_TJ * SK_TI + SK_TJ * CMAX) * 4 + SK_TJ * 8; }
+static size_t smem_qr() { return (size_t)(2 * QR_MAXF + 2 * CMAX + 32 + 2 * CMAX) * 4 + 64; }
+static size_t smem_qr2() { return (size_t)(2 * QR2_MAXF + 2 * CMAX + 32 + 2 * CMAX) * 4 + 64; }
+static size_t smem_qr3() { return (size_t)(QR_MAXF + CMAX * CMAX) * 4; }
+static size_t smem_btp() { return (size_t)(32 * BT_LDY + 32 * CMAX) * 4; }
+static size_t smem_btq() { return (size_t)(QR_MAXF + 2 * CMAX + 32 + 2 * CMAX) * 4 + 64; }
+static size_t smem_wsvd() {
+  return (size_t)(WS_MAXF + 2 * CMAX + 32 + CMAX * (CMAX + 1) + CMAX + 8) * 4 + 64;
+}
+static size_t smem_qw() { return (size_t)(CMAX * CMAX + QW_TI * CMAX) * 4 + CMAX * 8; }
+static size_t smem_flip() { return (size_t)(CMAX * CMAX + CMAX) * 4; }
+
+cudaError_t rf_init_attributes() {
+  cudaError_t e;
+#define RT_ATTR(k, sz)                                                                       \
+  if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sz))) != \
+      cudaSuccess)                                                                           \
+    return e;
+  RT_ATTR(k_gather_sketch, smem_gs());
+  RT_ATTR(k_qr1, smem_qr());
+  RT_ATTR(k_qr2, smem_qr2());
+  RT_ATTR(k_qr3, smem_qr3());
+  RT_ATTR(k_bt_partial, smem_btp());
+  RT_ATTR(k_bt_qr, smem_btq());
+  RT_ATTR(k_wsvd, smem_wsvd());
+  RT_ATTR(k_qw, smem_qw());
+  RT_ATTR(k_flip, smem_flip());
+#undef RT_ATTR
+  return cudaSuccess;
+}
+
+static inline unsigned grid_of(int64_t units) { return (unsigned)units; }
+
+int launch_range_finder(const RFGroup& g, cudaStream_t st, int* status) {
+  const int np = g.nprob;
+  const int64_t* pre = g.pre;
+  const int64_t stride = np + 1;
+  int n = 0;
+  if (g.total[STG_SAMPLE] > 0) {
+    k_sample<<<(unsigned)((g.total[STG_SAMPLE] + 255) / 256), 256, 0, st>>>(
+        g.probs, pre + STG_SAMPLE * stride, np, status);
+    ++n;
+  }
+  k_gather_sketch<<<grid_of(g.total[STG_GS]), 256, smem_gs(), st>>>(g.probs, pre + STG_GS * stride, np);
+  ++n;
+  k_qr1<<<grid_of(g.total[STG_QR1]), 512, smem_qr(), st>>>(g.probs, pre + STG_QR1 * stride, np);
+  ++n;
+  if (g.total[STG_QR2] > 0) {
+    k_qr2<<<grid_of(g.total[STG_QR2]), 512, smem_qr2(), st>>>(g.probs, pre + STG_QR2 * stride, np);
+    k_qr3<<<grid_of(g.total[STG_QR3]), 256, smem_qr3(), st>>>(g.probs, pre + STG_QR3 * stride, np);
+    n += 2;
+  }
+  k_bt_partial<<<grid_of(g.total[STG_BTP]), 256, smem_btp(), st>>>(g.probs, pre + STG_BTP * stride, np);
+  k_bt_qr<<<grid_of(g.total[STG_BTQ]), 512, smem_btq(), st>>>(g.probs, pre + STG_BTQ * stride, np);
+  k_wsvd<<<grid_of(g.total[STG_WSVD]), 1024, smem_wsvd(), st>>>(g.probs, pre + STG_WSVD * stride, np,
+                                                                 status);
+  k_qw<<<grid_of(g.total[STG_QW]), 256, smem_qw(), st>>>(g.probs, pre + STG_QW * stride, np);
+  k_flip<<<grid_of(g.total[STG_FLIP]), 256, smem_flip(), st>>>(g.probs, pre + STG_FLIP * stride, np);
+  n += 6;
+  return n;
+}
+
+int launch_sample_only(const RFGroup& g, cudaStream_t st, int* status) {
+  if (g.total[STG_SAMPLE] <= 0) return 0;
+  k_sample<<<(unsigned)((g.total[STG_SAMPLE] + 255) / 256), 256, 0, st>>>(
+      g.probs, g.pre + STG_SAMPLE * (g.nprob + 1), g.nprob, status);
+  return 1;
+}
+
+int launch_sketch_sum(const RFGroup& g, float* const* Zout, cudaStream_t st) {
+  const int64_t stride = g.nprob + 1;
+  k_sketch_sum<<<(unsigned)((g.total[STG_ZSUM] + 255) / 256), 256, 0, st>>>(
+      g.probs, g.pre + STG_ZSUM * stride, g.nprob, Zout);
+  return 1;
+}
+
+}  // namespace rt

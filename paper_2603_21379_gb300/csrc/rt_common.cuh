@@ -1,0 +1,115 @@
+// rt_common.cuh - shared device-side definitions of the rtucker CUDA library.
+//
+// A "range-finder problem" (RFProb) is one application of the loop body of
+// Alg. 1 (one mode k of one tensor) or of the per-node body of Alg. 2 (one
+// node S of the dimension tree): sample w columns of the set unfolding X^(S)
+// for a contiguous mode range S, sketch, orthonormalise, W-step.  Every stage
+// kernel takes the whole table of problems and maps its CTAs onto them, so one
+// launch serves all modes of all tensors (or all nodes of a tree) at once.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace rt {
+
+constexpr int MAXD = 16;
+
+// device status word codes (first error wins)
+enum : int { ST_OK = 0, ST_TIMEOUT = 1, ST_DEVICE = 2, ST_NUMERIC = 3 };
+
+__device__ __forceinline__ void set_status(int* st, int code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+enum : int { DT_F32 = 0, DT_F64 = 1, DT_BF16 = 2 };
+
+struct RFProb {
+  // input tensor and the geometry of the set unfolding X^(S), S = {a..b}
+  const void* X;
+  int32_t dtype;
+  int32_t ncm;             // number of complement modes
+  int64_t nS;              // rows of X^(S)
+  int64_t N;               // columns of X^(S) = n_{notin S}
+  int64_t rowstride;       // element stride in X of the C-order row index over S
+  int64_t csize[MAXD];     // complement mode sizes (natural order)
+  int64_t cstride[MAXD];   // their element strides in X
+  // method parameters
+  int32_t r, c;            // rank and r + p
+  int64_t s;               // number of sampled columns
+  uint64_t seed;
+  uint32_t node;           // stream id (mode k or tree node id)
+  int32_t fh;              // half width of the Feistel domain (bits)
+  // workspace (device pointers) and tiling counts
+  int64_t* idx;            // [s]      sampled column indices pi(j)
+  int64_t* off;            // [s]      element offset in X of column pi(j)
+  float* Om;               // [s][c]   Gaussian test matrix rows
+  float* Yt;               // [s][nS]  sampled columns (fiber j contiguous)
+  float* Zp;               // [nzc][nS][c] partial sketches per sample chunk
+  int32_t nzc;             // number of sample chunks of the sketch
+  int32_t nrb;             // row blocks of the TSQR of Z (1 = single block)
+  int32_t rbrows;          // rows per TSQR row block
+  int32_t nbi;             // row blocks of the reduction B^T = Y^T Q
+  float* Q;                // [nS][c]  orthonormal factor of Z
+  float* Rb;               // [nrb][c][c] TSQR first-level R factors
+  float* Q2;               // [nrb*c][c] TSQR second-level Q
+  float* Bp;               // [nbi][s][c] partial B^T
+  float* Rc;               // [nsc][c][c] R factors of the sample chunks of B^T
+  int32_t nsc;             // number of sample chunks of B^T
+  int32_t scrows;          // rows (samples) per chunk of B^T
+  float* W;                // [c][c]   left singular vectors of R^T, sorted (cols)
+  float* sigma;            // [c]      singular values of Q^T Y, descending
+  unsigned long long* keys;// [r]      sign-rule argmax keys
+  float* U;                // [nS][r]  output factor
+  float* sigma_out;        // optional copy of sigma for the caller (or null)
+};
+
+// Problem lookup: blocks (or threads) are numbered consecutively over the
+// problems; prefix[p] = first unit of problem p, prefix[nprob] = total.
+__device__ __forceinline__ int find_prob(const int64_t* prefix, int nprob, int64_t unit) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= unit) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ float load_x(const void* X, int dtype, int64_t e) {
+  if (dtype == DT_F32) return __ldg(reinterpret_cast<const float*>(X) + e);
+  if (dtype == DT_F64) return (float)__ldg(reinterpret_cast<const double*>(X) + e);
+  return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(X)[e]);
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum; `red` is shared scratch of >= 32 floats.  All threads get the sum.
+__device__ __forceinline__ float block_sum(float v, float* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  float t = (threadIdx.x < (unsigned)nw) ? red[threadIdx.x] : 0.f;
+  if (wid == 0) {
+    t = warp_sum(t);
+    if (lane == 0) red[0] = t;
+  }
+  __syncthreads();
+  float out = red[0];
+  __syncthreads();
+  return out;
+}
+
+}  // namespace rt

@@ -1,0 +1,77 @@
+// rt_host.h - host-side interfaces between the C-ABI layer and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rt_common.cuh"
+
+namespace rt {
+
+// Tile sizes of the range-finder stages (shared by planner and kernels).
+constexpr int SK_TI = 128;         // rows per gather/sketch tile
+constexpr int SK_TJ = 64;          // samples per sketch chunk
+constexpr int CMAX = 64;           // largest r + p supported
+constexpr int QR_MAXF = 12288;     // floats per smem array in the block QR
+constexpr int QR2_MAXF = 24576;    // floats per smem array in the TSQR second level
+constexpr int BT_SC = 128;         // samples per chunk of B^T = Y^T Q
+constexpr int BT_IB = 2048;        // rows per reduction block of B^T
+constexpr int WS_MAXF = 24576;     // floats of the stacked R factors in the W-step
+constexpr int QW_TI = 128;         // rows per tile of U = Q W
+
+enum Stage : int {
+  STG_SAMPLE = 0, STG_GS, STG_QR1, STG_QR2, STG_QR3, STG_BTP, STG_BTQ, STG_WSVD, STG_QW, STG_FLIP,
+  STG_ZSUM, STG_COUNT
+};
+
+// Device-side view of a planned group of range-finder problems.
+struct RFGroup {
+  const RFProb* probs;   // device table [nprob]
+  const int64_t* pre;    // device prefixes [STG_COUNT][nprob + 1]
+  int nprob;
+  int64_t total[STG_COUNT];  // host copy of the unit totals per stage
+};
+
+// Enqueue every stage of the range finder for the group (Alg. 1 loop body /
+// Alg. 2 node body).  Returns the number of kernel launches enqueued.
+int launch_range_finder(const RFGroup& g, cudaStream_t st, int* status);
+// Sampling stage alone (S1), for rtucker_indices.
+int launch_sample_only(const RFGroup& g, cudaStream_t st, int* status);
+// Z = sum of the partial sketches (for rtucker_sketch).
+int launch_sketch_sum(const RFGroup& g, float* const* Zout, cudaStream_t st);
+// Shared-memory opt-ins; call once per device.
+cudaError_t rf_init_attributes();
+
+// ---- multi-TTM (core_kernels.cu)
+// out(L, r, R) = sum_i U[i][a] A(L, n, R): mode contraction with U^T.
+int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, const float* U, int r,
+                 float* out, cudaStream_t st);
+cudaError_t core_init_attributes();
+
+// ---- H-Tucker (ht_kernels.cu)
+struct TransferJob {     // B_S(i, j, k) = sum_{a,b} U_S[a n_r + b][i] U_l[a][j] U_r[b][k]
+  const float* US; const float* Ul; const float* Ur; float* B;
+  int64_t nl, nr; int rS, rl, rr;
+};
+int launch_transfer(const TransferJob* jobs_dev, const TransferJob* jobs_host, int njobs,
+                    cudaStream_t st);
+// B_R(0, j, k) = sum_{a,b} X[a nr + b] Ul[a][j] Ur[b][k]
+int launch_root(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl,
+                const float* Ur, int rr, float* BR, float* scratch, cudaStream_t st);
+size_t root_scratch_floats(int64_t nl, int64_t nr, int rl, int rr);
+
+// ---- evaluators (eval_kernels.cu), float64
+int launch_tucker_relerr(const void* X, int dtype, int d, const int64_t* n, const int32_t* r,
+                         const float* const* U, const float* G, double* scratch, size_t scratch_doubles,
+                         double* result2, cudaStream_t st);
+size_t tucker_relerr_scratch(int d, const int64_t* n, const int32_t* r);
+int launch_ht_relerr(const void* X, int dtype, int64_t nl, int64_t nr, const double* Ul, int rl,
+                     const float* BR, const double* Ur, int rr, double* scratch, double* result2,
+                     cudaStream_t st);
+// Expand U_S = (U_l (x) U_r) B_S^(1)T in float64: Uout[(a nr + b)][i] = sum_jk Ul[a][j] B[i][j][k] Ur[b][k]
+int launch_ht_expand(const double* Ul, int64_t nl, int rl, const double* Ur, int64_t nr, int rr,
+                     const float* B, int rS, double* Uout, cudaStream_t st);
+int launch_f32_to_f64(const float* in, double* out, int64_t n, cudaStream_t st);
+size_t ht_relerr_scratch(int64_t nl, int64_t nr);
+
+}  // namespace rt

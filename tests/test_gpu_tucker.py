@@ -1,0 +1,218 @@
+"""GPU parity of the Sub-R-HOSVD path (S1-S7) against the float64 oracle.
+
+Every call goes through the C ABI (ctypes binding).  Bars: sampled indices
+bit-exact; sketches within 1e-5 of max|Z|; factors equal up to column sign
+within 1e-4 (well-separated columns element-wise, clusters of close singular
+values through their projectors); |relerr_gpu - relerr_oracle| <= 1e-5.
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+from oracle import brute, rng, tucker  # noqa: E402
+from parity_util import (RELERR_TOL, U_TOL, compare_factor, flip_core, orthonormality,  # noqa: E402
+                         to_np)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_21379_gb300 import build
+    build.build()
+    import paper_2603_21379_gb300 as m
+    m.load_library()
+    return m
+
+
+def _run_and_compare(rt, X, r, p, s=None, seed=0, check_core=True, x_for_oracle=None):
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    G, U = rt.rtucker_decompose(Xd, list(r), p, s=s, seed=seed)
+    _, sig = rt.rtucker_factors(Xd, list(r), p, s=s, seed=seed, with_sigma=True)
+    torch.cuda.synchronize()
+    Xo = np.asarray(X if x_for_oracle is None else x_for_oracle, dtype=np.float64)
+    ref = tucker.sub_r_hosvd(Xo, list(r), p, s=s, seed=seed)
+    signs = []
+    for k in range(Xo.ndim):
+        sg, dev, strict = compare_factor(to_np(U[k]), ref["U"][k], ref["modes"][k]["sigma"])
+        assert dev <= U_TOL, ("mode", k, dev)
+        assert orthonormality(to_np(U[k])) < 1e-5
+        s_ref = ref["modes"][k]["sigma"]
+        assert np.abs(to_np(sig[k]) - s_ref).max() <= 1e-5 * s_ref[0] + 1e-30
+        signs.append(sg)
+    err_gpu = rt.rtucker_relerr(Xd, G, U)
+    err_ref = tucker.relerr(Xo, tucker.reconstruct(ref["G"], ref["U"]))
+    assert abs(err_gpu - err_ref) <= RELERR_TOL, (err_gpu, err_ref)
+    if check_core:
+        Gg = flip_core(to_np(G), signs)
+        assert np.abs(Gg - ref["G"]).max() <= 1e-4 * np.abs(ref["G"]).max()
+    return G, U, ref, err_gpu, err_ref
+
+
+def test_indices_bit_exact(rt):
+    for n, s, seed in [((128, 128, 128, 128), (1280,) * 4, 1),
+                       ((64, 64, 64), (640, 640, 640), 0),
+                       ((7, 5, 3), (15, 21, 35), 123456789),
+                       ((2, 3), (3, 2), 2**63 + 5)]:
+        got = rt.rtucker_indices(list(n), list(s), seed=seed)
+        N = int(np.prod(n))
+        for k in range(len(n)):
+            want = rng.fiber_indices(N // n[k], s[k], seed, k)
+            assert np.array_equal(got[k].cpu().numpy(), want), (n, k)
+
+
+def test_sketch_matches_oracle(rt):
+    X = synth.tucker_tensor((40, 36, 150), (4, 5, 6), noise=1e-4, data_seed=5, dtype="f32")
+    Xd = torch.from_numpy(X).cuda()
+    r, p, seed = [4, 5, 6], 3, 11
+    Z = rt.rtucker_sketch(Xd, r, p, seed=seed)
+    ref = tucker.sub_r_hosvd(X.astype(np.float64), r, p, seed=seed, with_core=False)
+    for k in range(3):
+        Zr = ref["modes"][k]["Z"]
+        assert np.abs(to_np(Z[k]) - Zr).max() <= 1e-5 * np.abs(Zr).max()
+
+
+def test_small_order3_ragged_tiles(rt):
+    X = synth.tucker_tensor((40, 36, 150), (4, 5, 6), noise=1e-4, data_seed=5, dtype="f32")
+    _run_and_compare(rt, X, (4, 5, 6), 3, seed=11)
+
+
+def test_order4_ragged(rt):
+    X = synth.tucker_tensor((33, 29, 17, 70), (5, 4, 3, 7), noise=1e-5, data_seed=6, dtype="f32")
+    _run_and_compare(rt, X, (5, 4, 3, 7), 4, seed=3)
+
+
+def test_order3_float64_storage_64cube(rt):
+    cfg = synth.ORDER3_F64
+    X = synth.named(cfg)
+    assert X.dtype == np.float64
+    _, _, _, eg, er = _run_and_compare(rt, X, cfg["ranks"], cfg["p"], seed=cfg["seed"])
+    assert er < 1e-6
+
+
+def test_order4_graded_core_reduced(rt):
+    X = synth.tucker_tensor((48, 48, 48, 48), (12, 12, 12, 12), noise=1e-6, data_seed=7, core="graded")
+    _run_and_compare(rt, X, (12,) * 4, 6, seed=2)
+
+
+def test_matrix_d2(rt):
+    X = synth.tucker_tensor((300, 200), (10, 10), noise=1e-3, data_seed=8)
+    _run_and_compare(rt, X, (10, 10), 5, seed=4)
+
+
+def test_rp_equals_n_and_p_zero(rt):
+    X = synth.tucker_tensor((8, 30, 25), (5, 6, 6), noise=1e-3, data_seed=9)
+    _run_and_compare(rt, X, (5, 6, 6), 3, seed=5)       # r_0 + p = n_0
+    _run_and_compare(rt, X, (5, 6, 6), 0, seed=6)       # no oversampling
+
+
+def test_full_sampling_is_truncated_hosvd(rt):
+    rs = np.random.default_rng(6)
+    X = rs.standard_normal((6, 7, 8)).astype(np.float32)
+    r, p = [2, 3, 4], 4
+    s = [56, 48, 42]
+    G, U, ref, _, _ = _run_and_compare(rt, X, r, p, s=s, seed=3)
+    hs = brute.t_hosvd(X.astype(np.float64), r)
+    for k in range(3):
+        Ug = to_np(U[k])
+        sg = np.sign((Ug * hs["U"][k]).sum(axis=0))
+        assert np.abs(Ug * sg - hs["U"][k]).max() <= U_TOL
+
+
+def test_tall_mode_uses_tsqr(rt):
+    X = synth.tucker_tensor((3000, 8, 9), (6, 3, 3), noise=1e-4, data_seed=10)
+    _run_and_compare(rt, X, (6, 3, 3), 2, seed=8)
+
+
+def test_bf16_storage(rt):
+    X = synth.tucker_tensor((40, 50, 60), (5, 5, 5), noise=1e-3, data_seed=11)
+    Xb = torch.from_numpy(X).to(torch.bfloat16)
+    Xo = Xb.float().numpy()  # the oracle sees the same (rounded) values
+    Xd = Xb.cuda()
+    G, U = rt.rtucker_decompose(Xd, [5, 5, 5], 3, seed=9)
+    ref = tucker.sub_r_hosvd(Xo.astype(np.float64), [5, 5, 5], 3, seed=9)
+    for k in range(3):
+        _, dev, _ = compare_factor(to_np(U[k]), ref["U"][k], ref["modes"][k]["sigma"])
+        assert dev <= U_TOL
+    eg = rt.rtucker_relerr(Xd, G, U)
+    er = tucker.relerr(Xo, tucker.reconstruct(ref["G"], ref["U"]))
+    assert abs(eg - er) <= RELERR_TOL
+
+
+def test_core_entry_point_and_evaluator(rt):
+    X = synth.tucker_tensor((30, 40, 50), (4, 4, 4), noise=1e-3, data_seed=12)
+    Xd = torch.from_numpy(X).cuda()
+    rs = np.random.default_rng(1)
+    U = [np.linalg.qr(rs.standard_normal((n, 4)))[0] for n in X.shape]
+    Ud = [torch.from_numpy(u.astype(np.float32)).cuda() for u in U]
+    G = rt.rtucker_core(Xd, Ud)
+    Uf = [u.astype(np.float32).astype(np.float64) for u in U]
+    Gr = tucker.multi_ttm_t(X.astype(np.float64), Uf)
+    assert np.abs(to_np(G) - Gr).max() <= 1e-5 * np.abs(Gr).max()
+    # evaluator against a host float64 reconstruction of the same G, U
+    eg = rt.rtucker_relerr(Xd, G, Ud)
+    eh = tucker.relerr(X, tucker.reconstruct(to_np(G), Uf))
+    assert abs(eg - eh) <= 1e-9
+
+
+def test_invalid_arguments_raise(rt):
+    X = torch.zeros((4, 5, 6), device="cuda")
+    with pytest.raises(rt.RtError) as e:
+        rt.rtucker_decompose(X, [4, 2, 2], 1)       # r_0 + p > n_0
+    assert e.value.status == 1
+    with pytest.raises(rt.RtError):
+        rt.rtucker_decompose(X, [2, 2, 2], 1, s=[2, 20, 20])  # s < r + p
+    with pytest.raises(rt.RtError):
+        rt.rtucker_decompose(X, [2, 2, 2], 1, s=[31, 20, 20])  # s > n_{!=k}
+    with pytest.raises(rt.RtError) as e:
+        rt.rtucker_decompose(X, [2, 2, 2], 70)     # r + p > 64
+    assert e.value.status in (1, 7)
+
+
+def test_host_memory_entry_point(rt):
+    X = synth.tucker_tensor((40, 36, 50), (4, 5, 6), noise=1e-4, data_seed=13)
+    Xh = torch.from_numpy(X).pin_memory()
+    G, U = rt.rtucker_decompose_host(Xh, [4, 5, 6], 3, seed=2)
+    Gd, Ud = rt.rtucker_decompose(Xh.cuda(), [4, 5, 6], 3, seed=2)
+    torch.cuda.synchronize()
+    assert np.array_equal(G.numpy(), Gd.cpu().numpy())
+    for a, b in zip(U, Ud):
+        assert np.array_equal(a.numpy(), b.cpu().numpy())
+
+
+def test_batched_matches_single_and_oracle(rt):
+    shapes, ranks = synth.batched_shapes(T=12, data_seed=55)
+    Xs = [synth.tucker_tensor(sh, rk, 1e-6, 9000 + t) for t, (sh, rk) in enumerate(zip(shapes, ranks))]
+    Xd = [torch.from_numpy(X).cuda() for X in Xs]
+    seeds = [100 + t for t in range(12)]
+    outs = rt.rtucker_decompose_batched(Xd, [list(r) for r in ranks], 5, seeds)
+    torch.cuda.synchronize()
+    for t in range(12):
+        G1, U1 = rt.rtucker_decompose(Xd[t], list(ranks[t]), 5, seed=seeds[t])
+        Gb, Ub = outs[t]
+        assert np.array_equal(to_np(Gb), to_np(G1))
+        ref = tucker.sub_r_hosvd(Xs[t].astype(np.float64), list(ranks[t]), 5, seed=seeds[t])
+        for k in range(3):
+            _, dev, _ = compare_factor(to_np(Ub[k]), ref["U"][k], ref["modes"][k]["sigma"])
+            assert dev <= U_TOL
+        eg = rt.rtucker_relerr(Xd[t], Gb, Ub)
+        er = tucker.relerr(Xs[t], tucker.reconstruct(ref["G"], ref["U"]))
+        assert abs(eg - er) <= RELERR_TOL
+
+
+def test_order4_96_full_size(rt):
+    cfg = synth.ORDER4_96
+    X = synth.named(cfg)
+    _run_and_compare(rt, X, cfg["ranks"], cfg["p"], seed=cfg["seed"], check_core=False)
+
+
+def test_order4_128_full_size(rt):
+    cfg = synth.ORDER4_128
+    X = synth.named(cfg)
+    G, U, ref, eg, er = _run_and_compare(rt, X, cfg["ranks"], cfg["p"], seed=cfg["seed"], check_core=False)
+    assert 5e-4 < er < 5e-3
