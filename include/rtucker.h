@@ -83,6 +83,17 @@ int rt_version(void);
 int rt_last_launch_count(rt_handle h);
 /* Bytes of device workspace currently held by the handle. */
 size_t rt_workspace_bytes(rt_handle h);
+/* Stage timing.  While enabled, the library records CUDA events on the
+ * handle's stream around the stages of every call and accumulates the elapsed
+ * times.  rt_get_timing synchronises the stream and writes, for stage
+ * i < min(nmax, RT_NSTAGES), the total milliseconds ms[i] and the number of
+ * timed intervals count[i] since the last reset (reset = 1 clears them).
+ * Stages: 0 range finder (S1-S6), 1 first contraction of the core (the pass
+ * over X), 2 remaining core contractions, 3 H-Tucker transfer tensors,
+ * 4 H-Tucker root pass (the pass over X). */
+#define RT_NSTAGES 5
+rt_status rt_set_timing(rt_handle h, int enable);
+rt_status rt_get_timing(rt_handle h, double* ms, int64_t* count, int nmax, int reset);
 
 /* ----------------------------------------------------------- Sub-R-HOSVD
  * Shared arguments (Alg. 1 inputs):

@@ -21,6 +21,7 @@ __all__ = [
     "rtucker_indices", "rtucker_sketch", "rtucker_factors", "rtucker_core", "rtucker_decompose",
     "rtucker_decompose_host", "rtucker_decompose_batched", "rtucker_relerr",
     "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "last_launch_count", "workspace_bytes",
+    "set_timing", "get_timing", "STAGES",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -73,6 +74,8 @@ def load_library():
         "rt_version": (ctypes.c_int, []),
         "rt_last_launch_count": (ctypes.c_int, [vp]),
         "rt_workspace_bytes": (ctypes.c_size_t, [vp]),
+        "rt_set_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "rt_get_timing": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), P64, ctypes.c_int, ctypes.c_int]),
         "rtucker_indices": (ctypes.c_int, [vp, ctypes.c_int, P64, P64, u64, vp]),
         "rtucker_sketch": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64, PO, vp]),
         "rtucker_factors": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64, PO, vp, vp]),
@@ -170,6 +173,24 @@ def last_launch_count(device=None):
 
 def workspace_bytes(device=None):
     return int(load_library().rt_workspace_bytes(_handle(device)))
+
+
+STAGES = ("range_finder", "core_x_pass", "core_rest", "ht_transfer", "ht_root_pass")
+
+
+def set_timing(enable, device=None):
+    """Record CUDA events around the library's stages on the current stream."""
+    h = _handle(device)
+    _check(h, load_library().rt_set_timing(h, 1 if enable else 0))
+
+
+def get_timing(reset=True, device=None):
+    """{stage: (total ms, intervals)} accumulated since the last reset."""
+    h = _handle(device)
+    ms = (ctypes.c_double * len(STAGES))()
+    cnt = (ctypes.c_int64 * len(STAGES))()
+    _check(h, load_library().rt_get_timing(h, ms, cnt, len(STAGES), 1 if reset else 0))
+    return {s: (ms[i], cnt[i]) for i, s in enumerate(STAGES)}
 
 
 # ------------------------------------------------------------------ Sub-R-HOSVD

@@ -36,6 +36,12 @@ struct rt_handle_s {
   int launches = 0;
   char* hc_buf = nullptr;      // device buffers of rtucker_decompose_host
   size_t hc_bytes = 0;
+  // stage timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;              // free events
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;  // recorded intervals
+  double stage_ms[RT_NSTAGES] = {0};
+  int64_t stage_cnt[RT_NSTAGES] = {0};
 };
 
 namespace {
@@ -57,6 +63,50 @@ rt_status cuda_fail(rt_handle h, cudaError_t e, const char* where) {
     cudaError_t _e = (call);                              \
     if (_e != cudaSuccess) return cuda_fail(h, _e, #call); \
   } while (0)
+
+cudaEvent_t pool_event(rt_handle h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets the launches enqueued between begin() and end() with two events.
+struct StageTimer {
+  rt_handle h;
+  int stage;
+  cudaEvent_t a = nullptr;
+  StageTimer(rt_handle hh, int s) : h(hh), stage(s) {
+    if (h->timing) {
+      a = pool_event(h);
+      cudaEventRecord(a, h->stream);
+    }
+  }
+  ~StageTimer() {
+    if (a) {
+      cudaEvent_t b = pool_event(h);
+      cudaEventRecord(b, h->stream);
+      h->ev_open.push_back({stage, {a, b}});
+    }
+  }
+};
+
+void drain_timing(rt_handle h) {
+  for (auto& it : h->ev_open) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, it.second.first, it.second.second) == cudaSuccess) {
+      h->stage_ms[it.first] += ms;
+      h->stage_cnt[it.first] += 1;
+    }
+    h->ev_pool.push_back(it.second.first);
+    h->ev_pool.push_back(it.second.second);
+  }
+  h->ev_open.clear();
+}
 
 int dtype_size(rt_dtype t) { return t == RT_F64 ? 8 : (t == RT_BF16 ? 2 : 4); }
 
@@ -384,8 +434,9 @@ size_t core_buffer_floats(int d, const int64_t* n, const int32_t* r) {
   return best;
 }
 
-int enqueue_core(const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
-                 const float* U, float* G, float* bufA, float* bufB, cudaStream_t st) {
+int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
+                 const float* U, float* G, float* bufA, float* bufB) {
+  cudaStream_t st = h->stream;
   int nl = 0;
   const void* A = X;
   int adt = (int)dtype;
@@ -398,7 +449,10 @@ int enqueue_core(const void* X, rt_dtype dtype, int d, const int64_t* n, const i
     for (int j = 0; j < k; ++j) L *= n[j];
     for (int j = k + 1; j < d; ++j) R *= r[j];
     float* out = (k == 0) ? G : (ping ? bufB : bufA);
-    nl += launch_ttm_t(A, adt, L, n[k], R, U + uoff[k], r[k], out, st);
+    {
+      StageTimer tm(h, k == d - 1 ? 1 : 2);
+      nl += launch_ttm_t(A, adt, L, n[k], R, U + uoff[k], r[k], out, st);
+    }
     A = out;
     adt = DT_F32;
     ping ^= 1;
@@ -492,13 +546,16 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
   }
   RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
   h->stage_pending = true;
-  nl += launch_range_finder(Gp.g, h->stream, h->d_status);
+  {
+    StageTimer tm(h, 0);
+    nl += launch_range_finder(Gp.g, h->stream, h->d_status);
+  }
   if (Zout) nl += launch_sketch_sum(Gp.g, reinterpret_cast<float* const*>(h->ws + o_zp), h->stream);
   if (G) {
     const float* Ucat = U ? U : nullptr;
     if (!Ucat) return fail(h, RT_EINVAL, "U is required with G");
-    nl += enqueue_core(X, dtype, d, n, r, Ucat, G, reinterpret_cast<float*>(h->ws + o_bufA),
-                       reinterpret_cast<float*>(h->ws + o_bufB), h->stream);
+    nl += enqueue_core(h, X, dtype, d, n, r, Ucat, G, reinterpret_cast<float*>(h->ws + o_bufA),
+                       reinterpret_cast<float*>(h->ws + o_bufB));
   }
   return finish(h, nl);
 }
@@ -558,6 +615,8 @@ rt_status rt_destroy(rt_handle h) {
   if (h->h_stage) cudaFreeHost(h->h_stage);
   if (h->ev_status) cudaEventDestroy(h->ev_status);
   if (h->ev_stage) cudaEventDestroy(h->ev_stage);
+  drain_timing(h);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
   return RT_OK;
 }
@@ -585,6 +644,25 @@ rt_status rt_sync(rt_handle h) {
 }
 
 const char* rt_last_error(rt_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+rt_status rt_set_timing(rt_handle h, int enable) {
+  if (!h) return RT_EINVAL;
+  h->timing = enable != 0;
+  return RT_OK;
+}
+
+rt_status rt_get_timing(rt_handle h, double* ms, int64_t* count, int nmax, int reset) {
+  if (!h) return RT_EINVAL;
+  RT_CUDA(h, cudaStreamSynchronize(h->stream));
+  drain_timing(h);
+  for (int i = 0; i < nmax && i < RT_NSTAGES; ++i) {
+    if (ms) ms[i] = h->stage_ms[i];
+    if (count) count[i] = h->stage_cnt[i];
+  }
+  if (reset)
+    for (int i = 0; i < RT_NSTAGES; ++i) { h->stage_ms[i] = 0.0; h->stage_cnt[i] = 0; }
+  return RT_OK;
+}
 int rt_last_launch_count(rt_handle h) { return h ? h->launches : 0; }
 size_t rt_workspace_bytes(rt_handle h) { return h ? h->ws_bytes : 0; }
 
@@ -663,8 +741,8 @@ rt_status rtucker_core(rt_handle h, const void* X, rt_dtype dtype, int d, const 
   const size_t cb = core_buffer_floats(d, n, r);
   const size_t oA = bump.take(cb * 4), oB = bump.take(cb * 4);
   if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
-  const int nl = enqueue_core(X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + oA),
-                              reinterpret_cast<float*>(h->ws + oB), h->stream);
+  const int nl = enqueue_core(h, X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + oA),
+                              reinterpret_cast<float*>(h->ws + oB));
   return finish(h, nl);
 }
 
@@ -740,10 +818,14 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
   if ((st = group_upload(h, Gp, h->h_stage, 0)) != RT_OK) return st;
   RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
   h->stage_pending = true;
-  int nl = launch_range_finder(Gp.g, h->stream, h->d_status);
+  int nl = 0;
+  {
+    StageTimer tm(h, 0);
+    nl += launch_range_finder(Gp.g, h->stream, h->d_status);
+  }
   for (int t = 0; t < T; ++t)
-    nl += enqueue_core(X[t], dtype, d[t], n[t], r[t], U[t], G[t], reinterpret_cast<float*>(h->ws + oA[t]),
-                       reinterpret_cast<float*>(h->ws + oB[t]), h->stream);
+    nl += enqueue_core(h, X[t], dtype, d[t], n[t], r[t], U[t], G[t], reinterpret_cast<float*>(h->ws + oA[t]),
+                       reinterpret_cast<float*>(h->ws + oB[t]));
   return finish(h, nl);
 }
 
@@ -867,17 +949,27 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
                                cudaMemcpyHostToDevice, h->stream));
   RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
   h->stage_pending = true;
-  int nlaunch = launch_range_finder(Gp.g, h->stream, h->d_status);
+  int nlaunch = 0;
+  {
+    StageTimer tm(h, 0);
+    nlaunch += launch_range_finder(Gp.g, h->stream, h->d_status);
+  }
   if (U_nodes) {
     for (int i = 1; i < nn; ++i)
       if (tree[i].a == tree[i].b)
         RT_CUDA(h, cudaMemcpyAsync(U_leaf + o_leaf[i], U_nodes + o_unode[i], (size_t)n[tree[i].a] * rk[i] * 4,
                                    cudaMemcpyDeviceToDevice, h->stream));
   }
-  nlaunch += launch_transfer(reinterpret_cast<const TransferJob*>(h->ws + o_jobs), jobs, (int)internal.size(),
-                             h->stream);
-  nlaunch += launch_root(X, (int)dtype, nl, nr, Uof(root.left), rl, Uof(root.right), rr, B + o_B[0],
-                         reinterpret_cast<float*>(h->ws + o_rootp), h->stream);
+  {
+    StageTimer tm(h, 3);
+    nlaunch += launch_transfer(reinterpret_cast<const TransferJob*>(h->ws + o_jobs), jobs, (int)internal.size(),
+                               h->stream);
+  }
+  {
+    StageTimer tm(h, 4);
+    nlaunch += launch_root(X, (int)dtype, nl, nr, Uof(root.left), rl, Uof(root.right), rr, B + o_B[0],
+                           reinterpret_cast<float*>(h->ws + o_rootp), h->stream);
+  }
   return finish(h, nlaunch);
 }
 
