@@ -1,0 +1,122 @@
+"""GPU parity of the Sub-R-RtL-HT path (S8-S10) against the float64 oracle:
+node bases U_S up to column sign (well-separated columns element-wise,
+clusters through projectors), transfer tensors on the determined columns
+(signs aligned), and the relative error of the whole format."""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+from oracle import brute, htucker, tucker  # noqa: E402
+from parity_util import RELERR_TOL, U_TOL, clusters, compare_factor, orthonormality, to_np  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2603_21379_gb300 import build
+    build.build()
+    import paper_2603_21379_gb300 as m
+    m.load_library()
+    return m
+
+
+def _strict_cols(sigma, r):
+    cl, tail_ok = clusters(sigma, r)
+    out = []
+    for ci, c in enumerate(cl):
+        if ci == len(cl) - 1 and not tail_ok:
+            continue
+        if len(c) == 1:
+            out.append(c[0])
+    return out
+
+
+def _compare_ht(rt, X, rank, p, w=None, seed=0, x_oracle=None):
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    U_leaf, B, Un = rt.rhtucker_decompose(Xd, rank, p, w=w, seed=seed, return_nodes=True)
+    torch.cuda.synchronize()
+    Xo = np.asarray(X if x_oracle is None else x_oracle, dtype=np.float64)
+    ref = htucker.sub_r_rtl_ht(Xo, rank, p, w=w, seed=seed)
+    tree = ref["tree"]
+    signs, strict = {}, {}
+    for nd in tree[1:]:
+        sig = ref["info"][nd.id]["sigma"]
+        Ug = to_np(Un[nd.id])
+        s, dev, _ = compare_factor(Ug, ref["US"][nd.id], sig)
+        assert dev <= U_TOL, (nd.id, dev)
+        assert orthonormality(Ug) < 1e-5
+        signs[nd.id] = s
+        strict[nd.id] = _strict_cols(sig, ref["ranks"][nd.id])
+    for k, nd in enumerate(sorted((n for n in tree if n.is_leaf), key=lambda n: n.a)):
+        assert np.array_equal(to_np(U_leaf[k]), to_np(Un[nd.id]))
+    for nd in tree:
+        if nd.is_leaf:
+            continue
+        Bg = to_np(B[nd.id])
+        Br = ref["B"][nd.id]
+        si = np.ones(1) if nd.id == 0 else signs[nd.id]
+        Bg = Bg * si[:, None, None] * signs[nd.left][None, :, None] * signs[nd.right][None, None, :]
+        ii = [0] if nd.id == 0 else strict[nd.id]
+        jj, kk = strict[nd.left], strict[nd.right]
+        if ii and jj and kk:
+            sub_g = Bg[np.ix_(ii, jj, kk)]
+            sub_r = Br[np.ix_(ii, jj, kk)]
+            assert np.abs(sub_g - sub_r).max() <= 1e-4 * max(1.0, np.abs(Br).max()), nd.id
+    eg = rt.rhtucker_relerr(Xd, U_leaf, B, rank)
+    er = tucker.relerr(Xo, htucker.reconstruct(ref["U"], ref["B"], tree, Xo.shape))
+    assert abs(eg - er) <= RELERR_TOL, (eg, er)
+    return eg, er
+
+
+def test_inv_norm_d6(rt):
+    X = synth.inv_norm_tensor(8, 6)
+    eg, er = _compare_ht(rt, X, 5, 3, seed=3)
+    assert er < 1e-5
+
+
+def test_inv_norm_d8_n6(rt):
+    X = synth.inv_norm_tensor(6, 8)
+    _compare_ht(rt, X, 4, 2, seed=1)
+
+
+def test_exact_hierarchical_rank_recovery(rt):
+    rs = np.random.default_rng(3)
+    shape = (5, 6, 4, 5, 6)
+    tree = htucker.balanced_tree(5)
+    U = [synth.haar(n, 2, rs) for n in shape]
+    B = [None] * len(tree)
+    for nd in tree:
+        if not nd.is_leaf:
+            B[nd.id] = rs.standard_normal((1 if nd.id == 0 else 2, 2, 2))
+    X = htucker.reconstruct(U, B, tree, shape).astype(np.float32)
+    eg, er = _compare_ht(rt, X, 2, 2, seed=7)
+    assert eg < 1e-5
+
+
+def test_full_sampling_matches_rtl_ht(rt):
+    rs = np.random.default_rng(2)
+    X = rs.standard_normal((3, 4, 3, 4)).astype(np.float32)
+    tree = htucker.balanced_tree(4)
+    p = 1
+    ranks = [1] + [htucker.node_rows(X.shape, nd) - p for nd in tree[1:]]
+    w = [1] + [htucker.node_cols(X.shape, nd) for nd in tree[1:]]
+    _compare_ht(rt, X, ranks, p, w=w, seed=5)
+    ref = brute.rtl_ht(X.astype(np.float64), ranks)
+    Xd = torch.from_numpy(X).cuda()
+    _, _, Un = rt.rhtucker_decompose(Xd, ranks, p, w=w, seed=5, return_nodes=True)
+    for nd in tree[1:]:
+        Ug = to_np(Un[nd.id])
+        sg = np.sign((Ug * ref["US"][nd.id]).sum(axis=0))
+        assert np.abs(Ug * sg - ref["US"][nd.id]).max() <= U_TOL
+
+
+def test_tall_node_tsqr_path(rt):
+    # node {0,1,2} of a 16^6 tensor has 4096 rows: two-level TSQR of Z
+    X = synth.inv_norm_tensor(16, 6)
+    _compare_ht(rt, X, 6, 3, seed=2)
