@@ -187,6 +187,33 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
 rt_status rhtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
                           const int32_t* rank, const float* U_leaf, const float* B, double* out);
 
+/* ----------------------------------------------------------- without allocation
+ * rhtucker_root_transfer_noalloc: the root transfer tensor of an H-Tucker
+ * format, BR(0, j, k) = sum_{a,b} X[a nr + b] Ul[a][j] Ur[b][k] (X viewed as an
+ * nl x nr matrix; Ul nl x rl, Ur nr x rr row-major; BR 1 x rl x rr), for
+ * callers that cannot allocate device memory (stream capture in global mode,
+ * frameworks that own all device memory, loops that must avoid the implicit
+ * synchronisation of cudaMalloc/cudaFree).  The paper has no counterpart: it
+ * is this library's allocation-free form of the root pass of
+ * rhtucker_decompose, with the same kernels and results.
+ *   - Allocates nothing: no handle, no workspace.  Its scratch is a static
+ *     device array of RT_ROOT_NOALLOC_MAX_PARTIALS floats (4 MiB) that every
+ *     GPU loading the library holds until the process exits.  The call needs
+ *     ceil(nr / 8192) * ceil(nl / 512) * rl * rr of them; larger problems, or
+ *     rr > 12, return RT_ENOTSUP.  Null pointers or sizes out of range return
+ *     RT_EINVAL.
+ *   - X, Ul, Ur, BR are device pointers owned by the caller; `stream` is a
+ *     cudaStream_t (NULL = legacy default stream).  Asynchronous on `stream`.
+ *   - The first call on a device resolves the device address of the static
+ *     array (cudaGetSymbolAddress) with that device current; make that first
+ *     call before any stream capture.
+ *   - Every call shares the one array: calls whose kernels overlap on the GPU
+ *     (other streams, other host threads) race on it. */
+#define RT_ROOT_NOALLOC_MAX_PARTIALS (1u << 20)
+rt_status rhtucker_root_transfer_noalloc(const void* X, rt_dtype dtype, int64_t nl, int64_t nr,
+                                         const float* Ul, int32_t rl, const float* Ur, int32_t rr,
+                                         float* BR, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

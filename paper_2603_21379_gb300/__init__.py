@@ -21,7 +21,7 @@ __all__ = [
     "rtucker_indices", "rtucker_sketch", "rtucker_factors", "rtucker_core", "rtucker_decompose",
     "rtucker_decompose_host", "rtucker_decompose_batched", "rtucker_relerr",
     "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "last_launch_count", "workspace_bytes",
-    "set_timing", "get_timing", "STAGES",
+    "set_timing", "get_timing", "STAGES", "rhtucker_root_transfer_noalloc",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -91,6 +91,7 @@ def load_library():
         "rhtucker_decompose": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64, PO,
                                               vp, vp, vp]),
         "rhtucker_relerr": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, vp, vp, PD]),
+        "rhtucker_root_transfer_noalloc": (ctypes.c_int, [vp, ctypes.c_int, i64, i64, vp, i32, vp, i32, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -419,3 +420,20 @@ def rhtucker_relerr(X, U_leaf, B, rank):
     h = _handle(X.device.index)
     _check(h, lib.rhtucker_relerr(h, _ptr(X), dt, d, _i64(n), _i32(rk), _ptr(Uc), _ptr(Bc), ctypes.byref(out)))
     return out.value
+
+
+def rhtucker_root_transfer_noalloc(X, Ul, Ur, out=None):
+    """Root transfer tensor U_l^T X_mat U_r (1 x r_l x r_r) without any device
+    allocation by the library (its scratch is a fixed static device array).
+    ``out`` must be preallocated by callers that cannot allocate either."""
+    lib = load_library()
+    dt, _, _ = _tensor_args(X)
+    nl, rl = int(Ul.shape[0]), int(Ul.shape[1])
+    nr, rr = int(Ur.shape[0]), int(Ur.shape[1])
+    if out is None:
+        out = torch.empty((1, rl, rr), dtype=torch.float32, device=X.device)
+    st = lib.rhtucker_root_transfer_noalloc(_ptr(X), dt, nl, nr, _ptr(Ul), rl, _ptr(Ur), rr, _ptr(out),
+                                            ctypes.c_void_p(torch.cuda.current_stream(X.device).cuda_stream))
+    if st != 0:
+        raise RtError(st, lib.rt_status_string(st).decode())
+    return out
