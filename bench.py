@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 METRIC = "input GB/s & decomps/s at fixed rel-err, BF16/batched vs FP32 plain, % roofline"
 WORKLOAD = ("Sub-R-HOSVD, order-4 128x128x128x128 float32 Tucker tensor (graded 32^4 core "
             "10^(-(i1+..+i4)/16) xi, Haar factors, N(0,1e-6^2) noise), r=32, p=10, s_k=1280, seed 1")
-DOMINANT = "k_ttm_t (first core contraction: the pass over X)"
+DOMINANT = "k_core2_tc (tcgen05 pass over X: last two core contractions, 3xBF16)"
 
 
 def measured_peaks():
@@ -45,8 +45,8 @@ def measured_peaks():
 def profile_traffic():
     """dram bytes per launch of the dominant kernel from the committed ncu
     summary, or None when the kernel source changed since the capture."""
-    path = os.path.join(ROOT, "profiles", "ttm_x_pass_128x4.json")
-    src = os.path.join(ROOT, "paper_2603_21379_gb300", "csrc", "core_kernels.cu")
+    path = os.path.join(ROOT, "profiles", "core2_tc_128x4.json")
+    src = os.path.join(ROOT, "paper_2603_21379_gb300", "csrc", "core_tc.cu")
     try:
         with open(path) as f:
             rec = json.load(f)

@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <cstdlib>
 
 #include <algorithm>
 #include <string>
@@ -434,23 +435,54 @@ size_t core_buffer_floats(int d, const int64_t* n, const int32_t* r) {
   return best;
 }
 
+// Core kernel selection: 1 = tensor-core pass over X when the shape allows
+// (default), 0 = FFMA chain only (environment variable RT_CORE_MODE).
+int core_mode() {
+  static int mode = [] {
+    const char* e = getenv("RT_CORE_MODE");
+    return e ? atoi(e) : 1;
+  }();
+  return mode;
+}
+
 int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
                  const float* U, float* G, float* bufA, float* bufB) {
   cudaStream_t st = h->stream;
   int nl = 0;
-  const void* A = X;
-  int adt = (int)dtype;
   size_t uoff[MAXD];
   size_t acc = 0;
   for (int k = 0; k < d; ++k) { uoff[k] = acc; acc += (size_t)n[k] * r[k]; }
+  const void* A = X;
+  int adt = (int)dtype;
   int ping = 0;
-  for (int k = d - 1; k >= 0; --k) {
+  int k = d - 1;
+  // the last two modes in one tensor-core pass over X, when the shape allows
+  const int mode = core_mode();
+  if (mode > 0 && (dtype == RT_F32 || dtype == RT_BF16) && d >= 2) {
+    int64_t S = 1;
+    for (int j = 0; j < d - 2; ++j) S *= n[j];
+    float* out = (d == 2) ? G : bufA;
+    int got = 0;
+    {
+      StageTimer tm(h, 1);
+      got = launch_core2_tc(dtype == RT_BF16 ? 1 : 0, X, S, (int)n[d - 2], (int)n[d - 1], U + uoff[d - 2],
+                            r[d - 2], U + uoff[d - 1], r[d - 1], out, h->d_status, st);
+    }
+    if (got > 0) {
+      nl += got;
+      A = out;
+      adt = DT_F32;
+      ping = 1;
+      k = d - 3;
+    }
+  }
+  for (; k >= 0; --k) {
     int64_t L = 1, R = 1;
     for (int j = 0; j < k; ++j) L *= n[j];
     for (int j = k + 1; j < d; ++j) R *= r[j];
     float* out = (k == 0) ? G : (ping ? bufB : bufA);
     {
-      StageTimer tm(h, k == d - 1 ? 1 : 2);
+      StageTimer tm(h, A == X ? 1 : 2);
       nl += launch_ttm_t(A, adt, L, n[k], R, U + uoff[k], r[k], out, st);
     }
     A = out;
@@ -459,7 +491,6 @@ int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_
   }
   return nl;
 }
-
 
 // --- dimension tree (Sec. 4): node {a..b} splits into its first ceil(len/2)
 // modes and the rest; nodes numbered level by level, left to right.

@@ -1,0 +1,583 @@
+// core_tc.cu - the pass over X of the core projection on the 5th-generation
+// tensor cores (tcgen05, TMEM accumulators, TMA-fed).
+//
+// For X viewed as S slabs of n1 x n2 (the last two modes; S = product of the
+// leading modes) it computes, per slab s,
+//     P_s = U_1^T X_s U_2          (r1 x r2),
+// i.e. the last two contractions of S = X x_1 U_1^T ... x_d U_d^T (Alg. 1,
+// core step) fused in one read of X.  The remaining modes are contracted on
+// P afterwards (core_kernels.cu).
+//
+// Data path per CTA (persistent, one per SM, warp-specialised):
+//   warp 0      TMA producer: 128-row x 32-column float32 boxes of X (one slab,
+//               one K-chunk of 32 columns; 128-byte swizzle) into a ring of
+//               shared-memory stages.
+//   warp 1      TMEM allocator and MMA issuer: per K-chunk, 4 x
+//               tcgen05.mma.kind::tf32 (M = 128, K = 8, N = 2 r2p) with B =
+//               [hi(U_2) | lo(U_2)] (U_2 split into two TF32 terms so the
+//               factor keeps float32 accuracy) resident in shared memory.
+//   warps 2-5   converters: each thread takes one row of the stage, rounds it
+//               to TF32 (round to nearest) and writes it to a TMEM A buffer
+//               (tcgen05.st); the MMA reads A from TMEM.
+//   warps 6-9   epilogue: D (128 x 2 r2p, TMEM) -> registers, T = D_hi + D_lo,
+//               T to shared memory, then P_s = U_1^T T by register-blocked FFMA,
+//               written to global memory.
+// Every mbarrier wait is bounded; on expiry the CTA records RT timeout in the
+// status word, stops issuing work, drains and frees its TMEM, and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "rt_common.cuh"
+#include "rt_host.h"
+
+namespace rt {
+namespace tc {
+
+constexpr int NA = 4;            // TMEM A buffers (32 columns each)
+constexpr int ROWS = 128;        // rows per tile (M)
+constexpr int KC = 32;           // columns per K-chunk (one 128-byte swizzle span)
+constexpr int STAGE_BYTES = ROWS * KC * 4;
+constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+
+__device__ __forceinline__ uint32_t saddr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(saddr(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(saddr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(saddr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: false on timeout or when another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+    if (mbar_test(bar, parity)) return true;
+    if ((it & 255u) == 255u && *abort_flag) return false;
+  }
+  *abort_flag = 1;
+  set_status(status, ST_TIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(saddr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t tf32_rn(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // descriptor version
+  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: D f32, A/B tf32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(
+          d),
+      "r"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
+      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
+      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+struct Core2Args {
+  const void* X;     // only for the element type; data comes through the tensor map
+  const float* U1;   // n1 x r1
+  const float* U2;   // n2 x r2
+  float* P;          // S x r1 x r2
+  int64_t S;
+  int n1, n2, r1, r2;
+  int* status;
+};
+
+// 16-bit MMA operands.  Instruction descriptor for kind::f16 with bf16 A/B, f32 D.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(
+          d),
+      "r"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// (hi, lo) bf16 pairs of two floats packed low = x0, high = x1.
+__device__ __forceinline__ uint32_t pack_bf16(float x0, float x1) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+  return r;
+}
+__device__ __forceinline__ void split_bf16(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  hi = pack_bf16(x0, x1);
+  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+  lo = pack_bf16(x0 - h0, x1 - h1);
+}
+__device__ __forceinline__ void split1_bf16(float x, unsigned short& hi, unsigned short& lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+  hi = *reinterpret_cast<const unsigned short*>(&h);
+  lo = *reinterpret_cast<const unsigned short*>(&l);
+}
+// Byte offset of bf16 element (row, k) in a K-major, 128-byte-swizzled operand
+// whose K range is split into 64-element chunks of `rows` x 128 bytes.
+__device__ __forceinline__ int sw_off16(int row, int k, int rows) {
+  const int kc = k >> 6, kl = k & 63;
+  return kc * rows * 128 + row * 128 + ((((kl >> 3) ^ (row & 7)) << 4) | ((kl & 7) << 1));
+}
+
+constexpr int NCONV = 8;                       // converter warps: two groups of four quadrants
+constexpr int W_CONV0 = 2, W_EPI0 = W_CONV0 + NCONV;
+constexpr int NWARPS = W_EPI0 + 4;
+constexpr int NTHREADS_V2 = NWARPS * 32;       // 448
+constexpr int NS3 = 6;                         // stages of X
+// Converter group g takes the chunks c with c % 2 == g.  Parity waits are only
+// safe when one consumer group owns every use of a barrier (a second group
+// could otherwise test a phase two behind and pass), so the number of stages
+// and of TMEM A buffers must be even: stage c % NS3 and buffer c % NA then
+// always belong to the same group.
+static_assert(NS3 % 2 == 0 && NA % 2 == 0, "stages and A buffers must be even");
+
+template <int R1P, int R2P, bool XBF16>
+struct Layout {
+  static constexpr int N1 = 2 * R2P;           // MMA1: X_s [hi(U2) | lo(U2)]
+  static constexpr int N2 = 2 * R1P;           // MMA2: T^T [hi(U1) | lo(U1)]
+  static constexpr int KCX = XBF16 ? 64 : 32;  // X columns per stage (128 bytes)
+  static constexpr int SPB = 128 / R2P;        // slabs per MMA2 batch (M = 128 rows of T^T)
+  static constexpr int A_COL = 0;              // TMEM: NA A buffers of 32 columns (float32 X only)
+  static constexpr int D1_COL = XBF16 ? 0 : NA * 32;
+  static constexpr int D2_COL = D1_COL + 2 * N1;
+  static constexpr int TMEM_USED = D2_COL + 2 * N2;
+  static constexpr int TMEM_COLS = TMEM_USED <= 128 ? 128 : TMEM_USED <= 256 ? 256 : 512;
+  static constexpr int A2_TERM = 2 * 128 * 128;  // bytes of one term of T^T (K = 128 in two chunks)
+};
+
+// Dynamic shared memory (1024-aligned):
+//   A2[2 terms][2 chunks][128][64 bf16] | B1[nkb][N1][64 bf16] | B2[2][N2][64 bf16] | stages[NS3][16 KB] | bars
+template <int R1P, int R2P, bool XBF16>
+__global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_constant__ CUtensorMap tmap, Core2Args args) {
+  using LY = Layout<R1P, R2P, XBF16>;
+  constexpr int N1 = LY::N1, N2 = LY::N2, KCX = LY::KCX, SPB = LY::SPB;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int nkc = (args.n2 + KCX - 1) / KCX;       // stages per slab
+  const int nkb = (args.n2 + 63) / 64;             // 64-wide K chunks of B1
+  unsigned char* A2 = base;
+  unsigned char* B1 = A2 + 2 * LY::A2_TERM;
+  unsigned char* B2 = B1 + (size_t)nkb * N1 * 128;
+  unsigned char* stages = B2 + 2 * N2 * 128;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stages + NS3 * STAGE_BYTES);
+  uint64_t* full = bars;
+  uint64_t* empty = full + NS3;
+  uint64_t* afull = empty + NS3;
+  uint64_t* aempty = afull + NA;
+  uint64_t* d1full = aempty + NA;
+  uint64_t* d1empty = d1full + 2;
+  uint64_t* tready = d1empty + 2;
+  uint64_t* d2full = tready + 2;
+  uint64_t* d2empty = d2full + 2;
+  uint64_t* fin = d2empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n1 = args.n1, n2 = args.n2, r1 = args.r1, r2 = args.r2;
+  const int64_t S = args.S;
+  const int64_t nmine = (S > blockIdx.x) ? (S - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const int64_t nchunks = nmine * nkc;
+  const int64_t nbatch = (nmine + SPB - 1) / SPB;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NS3; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], XBF16 ? 1 : 4); }
+    for (int i = 0; i < NA; ++i) { mbar_init(&afull[i], 4); mbar_init(&aempty[i], 1); }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&d1full[i], 1); mbar_init(&d1empty[i], 4);
+      mbar_init(&tready[i], 4);
+      mbar_init(&d2full[i], 1); mbar_init(&d2empty[i], 4);
+    }
+    mbar_init(fin, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // B1 = [hi(U2) | lo(U2)] (rows n < R2P: hi), B2 = [hi(U1) | lo(U1)], bf16, K-major, swizzled
+  for (int e = threadIdx.x; e < nkb * 64 * R2P; e += NTHREADS_V2) {
+    const int k = e / R2P, col = e % R2P;
+    unsigned short hi = 0, lo = 0;
+    if (k < n2 && col < r2) split1_bf16(__ldg(args.U2 + (int64_t)k * r2 + col), hi, lo);
+    *reinterpret_cast<unsigned short*>(B1 + sw_off16(col, k, N1)) = hi;
+    *reinterpret_cast<unsigned short*>(B1 + sw_off16(R2P + col, k, N1)) = lo;
+  }
+  for (int e = threadIdx.x; e < 128 * R1P; e += NTHREADS_V2) {
+    const int i = e / R1P, col = e % R1P;
+    unsigned short hi = 0, lo = 0;
+    if (i < n1 && col < r1) split1_bf16(__ldg(args.U1 + (int64_t)i * r1 + col), hi, lo);
+    *reinterpret_cast<unsigned short*>(B2 + sw_off16(col, i, N2)) = hi;
+    *reinterpret_cast<unsigned short*>(B2 + sw_off16(R1P + col, i, N2)) = lo;
+  }
+  // T^T starts at zero: rows of a partial batch and columns i >= n1 stay zero
+  for (int e = threadIdx.x; e < 2 * LY::A2_TERM / 16; e += NTHREADS_V2)
+    reinterpret_cast<uint4*>(A2)[e] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
+                 "r"((uint32_t)LY::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_proxy_async();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t box_bytes = (uint32_t)n1 * 128;
+  constexpr uint32_t idesc1 = idesc_bf16(128, N1);
+  constexpr uint32_t idesc2 = idesc_bf16(128, N2);
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      for (int64_t c = 0; c < nchunks; ++c) {
+        const int st = (int)(c % NS3);
+        if (!mbar_wait(&empty[st], (uint32_t)(((c / NS3) & 1) ^ 1), abort_flag, args.status)) break;
+        const int64_t s = blockIdx.x + (c / nkc) * gridDim.x;
+        const int kc = (int)(c % nkc);
+        mbar_arrive_tx(&full[st], box_bytes);
+        tma_load_2d(saddr(stages + st * STAGE_BYTES), &tmap, kc * KCX, (int)(s * n1), &full[st]);
+      }
+      for (int64_t c = nchunks - 1; c >= 0 && c >= nchunks - NS3; --c)
+        for (uint32_t it = 0; it < (1u << 16); ++it)
+          if (mbar_test(&full[c % NS3], (uint32_t)((c / NS3) & 1))) break;
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      bool ok = true;
+      auto mma2 = [&](int64_t g) -> bool {   // P of batch g: D2 = T^T [hi(U1) | lo(U1)], T^T = hi + lo
+        const int b = (int)(g & 1);
+        const uint32_t ph = (uint32_t)((g >> 1) & 1);
+        if (!mbar_wait(&tready[b], ph, abort_flag, args.status)) return false;
+        if (!mbar_wait(&d2empty[b], ph ^ 1, abort_flag, args.status)) return false;
+        fence_after();
+        const uint32_t dcol = tmem + LY::D2_COL + b * N2;
+#pragma unroll
+        for (int term = 0; term < 2; ++term)
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {   // K = 128 in steps of 16
+            const uint32_t aaddr = saddr(A2 + term * LY::A2_TERM + (kk >> 2) * 128 * 128 + (kk & 3) * 32);
+            const uint32_t baddr = saddr(B2 + (kk >> 2) * N2 * 128 + (kk & 3) * 32);
+            mma_bf16_ss(dcol, sw128_desc(aaddr), sw128_desc(baddr), idesc2, (term | kk) ? 1u : 0u);
+          }
+        mma_commit(&d2full[b]);
+        return true;
+      };
+      int64_t c = 0;
+      for (int64_t t = 0; t < nmine && ok; ++t) {
+        const int db = (int)(t & 1);
+        if (!(ok = mbar_wait(&d1empty[db], (uint32_t)(((t >> 1) & 1) ^ 1), abort_flag, args.status))) break;
+        fence_after();
+        const uint32_t dcol = tmem + LY::D1_COL + db * N1;
+        for (int kc = 0; kc < nkc; ++kc, ++c) {
+          if (XBF16) {
+            const int st = (int)(c % NS3);
+            if (!(ok = mbar_wait(&full[st], (uint32_t)((c / NS3) & 1), abort_flag, args.status))) break;
+            fence_after();
+            const uint32_t sbase = saddr(stages + st * STAGE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+              const int kg = kc * 4 + kk;    // global 16-wide K step
+              const uint32_t baddr = saddr(B1 + (kg >> 2) * N1 * 128 + (kg & 3) * 32);
+              mma_bf16_ss(dcol, sw128_desc(sbase + kk * 32), sw128_desc(baddr), idesc1, (kc | kk) ? 1u : 0u);
+            }
+            mma_commit(&empty[st]);
+          } else {
+            const int ab = (int)(c % NA);
+            if (!(ok = mbar_wait(&afull[ab], (uint32_t)((c / NA) & 1), abort_flag, args.status))) break;
+            fence_after();
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+              const int kg = kc * 2 + kk;
+              const uint64_t bdesc = sw128_desc(saddr(B1 + (kg >> 2) * N1 * 128 + (kg & 3) * 32));
+              const uint32_t a = tmem + LY::A_COL + ab * 32 + kk * 8;
+              mma_bf16_ts(dcol, a, bdesc, idesc1, (kc | kk) ? 1u : 0u);   // hi(X)
+              mma_bf16_ts(dcol, a + 16, bdesc, idesc1, 1u);                // lo(X)
+            }
+            mma_commit(&aempty[ab]);
+          }
+        }
+        if (!ok) break;
+        mma_commit(&d1full[db]);
+        // MMA2 of the previous batch once the first slab of the next batch is queued
+        if (t % SPB == 0 && t >= SPB && !(ok = mma2(t / SPB - 1))) break;
+      }
+      if (ok && nbatch >= 1) mma2(nbatch - 1);
+      mma_commit(fin);
+      for (uint32_t it = 0; it < (1u << 20); ++it)
+        if (mbar_test(fin, 0)) break;
+    }
+  } else if (warp < W_EPI0) {
+    // ---------------------------------------------------------------- converters (float32 X)
+    if (!XBF16) {
+      const int grp = (warp - W_CONV0) >> 2;
+      const int q = warp & 3;
+      const int row = q * 32 + lane;
+      for (int64_t c = grp; c < nchunks; c += 2) {
+        const int st = (int)(c % NS3), ab = (int)(c % NA);
+        bool ok = __all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((c / NS3) & 1), abort_flag, args.status));
+        if (!ok) break;
+        uint32_t v[32];   // 16 columns hi, 16 columns lo
+        const unsigned char* rowp = stages + st * STAGE_BYTES + row * 128;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (row < n1) f = *reinterpret_cast<const float4*>(rowp + ((j ^ (row & 7)) << 4));
+          split_bf16(f.x, f.y, v[2 * j], v[16 + 2 * j]);
+          split_bf16(f.z, f.w, v[2 * j + 1], v[16 + 2 * j + 1]);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+        ok = __all_sync(0xffffffffu, mbar_wait(&aempty[ab], (uint32_t)(((c / NA) & 1) ^ 1), abort_flag, args.status));
+        if (!ok) break;
+        fence_after();
+        tmem_st32(tmem + ((uint32_t)(q * 32) << 16) + LY::A_COL + ab * 32, v);
+        tmem_wait_st();
+        fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&afull[ab]);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int q = warp & 3;
+    const int i = q * 32 + lane;                    // slab row = K index of MMA2
+    auto read_p = [&](int64_t g) -> bool {          // P of the slabs of batch g
+      const int bb = (int)(g & 1);
+      const uint32_t ph = (uint32_t)((g >> 1) & 1);
+      bool ok = __all_sync(0xffffffffu, mbar_wait(&d2full[bb], ph, abort_flag, args.status));
+      if (!ok) return false;
+      fence_after();
+      uint32_t d[N2];
+#pragma unroll
+      for (int cc = 0; cc < N2 / 8; ++cc)
+        tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D2_COL + bb * N2 + cc * 8, d + 8 * cc);
+      tmem_wait_ld();
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d2empty[bb]);
+      const int m = q * 32 + lane;                   // row of D2 = (slab j of the batch, column b of P)
+      const int j = m / R2P, b = m % R2P;
+      const int64_t t = g * SPB + j;
+      if (t < nmine && b < r2) {
+        float* Pout = args.P + (blockIdx.x + t * gridDim.x) * (int64_t)r1 * r2;
+#pragma unroll
+        for (int a = 0; a < R1P; ++a)
+          if (a < r1) Pout[a * r2 + b] = __uint_as_float(d[a]) + __uint_as_float(d[R1P + a]);
+      }
+      return true;
+    };
+    bool ok = true;
+    for (int64_t t = 0; t < nmine && ok; ++t) {
+      const int db = (int)(t & 1);
+      ok = __all_sync(0xffffffffu, mbar_wait(&d1full[db], (uint32_t)((t >> 1) & 1), abort_flag, args.status));
+      if (!ok) break;
+      fence_after();
+      uint32_t d[N1];
+#pragma unroll
+      for (int cc = 0; cc < N1 / 8; ++cc)
+        tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D1_COL + db * N1 + cc * 8, d + 8 * cc);
+      tmem_wait_ld();
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&d1empty[db]);
+      const int j = (int)(t % SPB);
+      const int64_t g = t / SPB;
+      // first slab of a batch: P of the previous batch (frees T^T)
+      if (j == 0 && g >= 1 && !(ok = read_p(g - 1))) break;
+      // T^T rows (j, b), column i: hi and lo terms (rows i >= n1 stay zero)
+      if (i < n1) {
+#pragma unroll
+        for (int b = 0; b < R2P; ++b) {
+          unsigned short hi, lo;
+          split1_bf16(__uint_as_float(d[b]) + __uint_as_float(d[R2P + b]), hi, lo);
+          const int off = sw_off16(j * R2P + b, i, 128);
+          *reinterpret_cast<unsigned short*>(A2 + off) = hi;
+          *reinterpret_cast<unsigned short*>(A2 + LY::A2_TERM + off) = lo;
+        }
+      }
+      if (j == SPB - 1 || t == nmine - 1) {
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tready[g & 1]);
+      }
+    }
+    if (ok && nbatch >= 1) read_p(nbatch - 1);
+  }
+
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)LY::TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ host side
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+template <int R1P, int R2P, bool XBF16>
+static size_t smem_bytes(int nkb) {
+  using LY = Layout<R1P, R2P, XBF16>;
+  return 1024 + 2 * (size_t)LY::A2_TERM + (size_t)nkb * LY::N1 * 128 + 2 * (size_t)LY::N2 * 128 +
+         (size_t)NS3 * STAGE_BYTES + 8 * (2 * NS3 + 2 * NA + 11) + 16;
+}
+
+template <int R1P, int R2P, bool XBF16>
+static int launch_v3(const CUtensorMap& map, const Core2Args& a, int grid, cudaStream_t st) {
+  const int nkb = (a.n2 + 63) / 64;
+  const size_t sm = smem_bytes<R1P, R2P, XBF16>(nkb);
+  if (sm > 227 * 1024) return -1;
+  cudaFuncSetAttribute(k_core2_tc<R1P, R2P, XBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_core2_tc<R1P, R2P, XBF16><<<grid, NTHREADS_V2, sm, st>>>(map, a);
+  return 1;
+}
+
+}  // namespace tc
+
+// Returns the number of launches (1), or 0 when the shape is not supported
+// by the tensor-core path (the caller then uses the FFMA chain).
+// X is float32 (split into two bf16 terms on the fly) or bfloat16 (one term).
+int launch_core2_tc(int xbf16, const void* X, int64_t S, int n1, int n2, const float* U1, int r1, const float* U2,
+                    int r2, float* P, int* status, cudaStream_t st) {
+  using namespace tc;
+  const int esz = xbf16 ? 2 : 4;
+  if (n1 < 1 || n1 > ROWS || n2 < 1 || ((int64_t)n2 * esz) % 16 != 0 || r1 < 1 || r1 > 32 || r2 < 1 || r2 > 32)
+    return 0;
+  if ((reinterpret_cast<uintptr_t>(X) & 15u) != 0) return 0;
+  if (S * (int64_t)n1 >= ((int64_t)1 << 31)) return 0;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return 0;
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {(cuuint64_t)n2, (cuuint64_t)(S * n1)};
+  const cuuint64_t gstride[1] = {(cuuint64_t)n2 * esz};
+  const cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)n1};
+  const cuuint32_t estride[2] = {1, 1};
+  if (enc(&map, xbf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(X),
+          gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return 0;
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = (int)std::min<int64_t>(S, nsm);
+  Core2Args a{X, U1, U2, P, S, n1, n2, r1, r2, status};
+  const int r1p = r1 <= 8 ? 8 : r1 <= 16 ? 16 : 32;
+  const int r2p = r2 <= 8 ? 8 : r2 <= 16 ? 16 : 32;
+  int rc = 0;
+#define RT_TC_CASE(A, B)                                                                   \
+  if (r1p == A && r2p == B) {                                                              \
+    rc = xbf16 ? launch_v3<A, B, true>(map, a, grid, st) : launch_v3<A, B, false>(map, a, grid, st); \
+    return rc < 0 ? 0 : rc;                                                                \
+  }
+  RT_TC_CASE(8, 8) RT_TC_CASE(8, 16) RT_TC_CASE(8, 32)
+  RT_TC_CASE(16, 8) RT_TC_CASE(16, 16) RT_TC_CASE(16, 32)
+  RT_TC_CASE(32, 8) RT_TC_CASE(32, 16) RT_TC_CASE(32, 32)
+#undef RT_TC_CASE
+  return 0;
+}
+
+}  // namespace rt

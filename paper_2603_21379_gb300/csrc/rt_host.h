@@ -47,6 +47,11 @@ cudaError_t rf_init_attributes();
 int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, const float* U, int r,
                  float* out, cudaStream_t st);
 cudaError_t core_init_attributes();
+// Fused pass over X on tensor cores: P[s] = U1^T X[s] U2 for S slabs of
+// n1 x n2.  X float32 (xbf16 = 0: two bf16 terms) or bfloat16 (xbf16 = 1).
+// Returns 0 when the shape is unsupported.
+int launch_core2_tc(int xbf16, const void* X, int64_t S, int n1, int n2, const float* U1, int r1, const float* U2,
+                    int r2, float* P, int* status, cudaStream_t st);
 
 // ---- H-Tucker (ht_kernels.cu)
 struct TransferJob {     // B_S(i, j, k) = sum_{a,b} U_S[a n_r + b][i] U_l[a][j] U_r[b][k]
