@@ -243,6 +243,7 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   pp.units[STG_QW] = (nS + QW_TI - 1) / QW_TI;
   pp.units[STG_FLIP] = pp.units[STG_QW];
   pp.units[STG_ZSUM] = nS * c;
+  pp.units[STG_OMEGA] = s * c;
   return RT_OK;
 }
 

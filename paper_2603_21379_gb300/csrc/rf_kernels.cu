@@ -43,8 +43,19 @@ __global__ void __launch_bounds__(256) k_sample(const RFProb* __restrict__ P,
     rem /= sz;
   }
   q.off[j] = off;
-  float* om = q.Om + j * q.c;
-  for (int c = 0; c < q.c; ++c) om[c] = gauss_entry(m, (uint32_t)c, key, q.node);
+}
+
+// S3: Omega(j, c) = Box-Muller normal of Philox counter (pi(j), c), one thread per entry.
+__global__ void __launch_bounds__(256) k_omega(const RFProb* __restrict__ P,
+                                               const int64_t* __restrict__ pre, int np) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= pre[np]) return;
+  const int p = find_prob(pre, np, t);
+  const RFProb& q = P[p];
+  const int64_t e = t - pre[p];
+  const int64_t j = e / q.c;
+  const int c = (int)(e % q.c);
+  q.Om[e] = gauss_entry((uint64_t)q.idx[j], (uint32_t)c, philox_key(q.seed), q.node);
 }
 
 // ------------------------------------------------------------------ S2 + S4
@@ -67,7 +78,7 @@ __global__ void __launch_bounds__(256) k_gather_sketch(const RFProb* __restrict_
   if (tid < SK_TJ) offs[tid] = (j0 + tid < q.s) ? q.off[j0 + tid] : (int64_t)-1;
   __syncthreads();
   const int64_t nS = q.nS, rs = q.rowstride;
-#pragma unroll 4
+#pragma unroll 8
   for (int e = tid; e < SK_TI * SK_TJ; e += 256) {
     const int jj = e / SK_TI, ii = e % SK_TI;
     const int64_t i = i0 + ii;
@@ -135,37 +146,54 @@ __global__ void k_sketch_sum(const RFProb* __restrict__ P, const int64_t* __rest
 // A is column-major (A[col * ld + row]), m x c.  On exit the columns hold the
 // Householder vectors v_k (v_k[k] stored at A[k*ld+k]), the strict upper part
 // holds R, rdiag[k] = R_kk and tau[k] the reflector scales, H_k = I - tau v v^T.
-__device__ void hh_factor(float* A, int ld, int m, int c, float* tau, float* rdiag, float* red) {
+//
+// Warp w owns the columns j with j % nwarps == w.  In step k every warp applies
+// H_k to its columns j > k; the owner of column k+1 updates that column first
+// and forms H_{k+1} from it right away, so each step needs one block barrier.
+
+// Reflector of column k (rows k..m-1), formed by one warp.
+__device__ __forceinline__ void hh_make(float* A, int ld, int m, int k, float* tau, float* rdiag) {
+  const int lane = threadIdx.x & 31;
+  float* a = A + (size_t)k * ld;
+  float part = 0.f;
+  for (int i = k + lane; i < m; i += 32) part = fmaf(a[i], a[i], part);
+  const float nrm2 = warp_sum(part);
+  if (lane == 0) {
+    const float x0 = a[k];
+    const float nrm = sqrtf(nrm2);
+    if (nrm == 0.f) {
+      tau[k] = 0.f;
+      rdiag[k] = 0.f;
+    } else {
+      const float alpha = (x0 >= 0.f) ? -nrm : nrm;
+      tau[k] = 1.f / (nrm * (nrm + fabsf(x0)));   // 2 / (v^T v)
+      rdiag[k] = alpha;
+      a[k] = x0 - alpha;
+    }
+  }
+  __syncwarp();
+}
+
+__device__ void hh_factor(float* A, int ld, int m, int c, float* tau, float* rdiag, float* /*red*/) {
   const int K = min(m, c);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (K <= 0) return;
+  if (warp == 0) hh_make(A, ld, m, 0, tau, rdiag);
+  __syncthreads();
   for (int k = 0; k < K; ++k) {
-    float* a = A + (size_t)k * ld;
-    float part = 0.f;
-    for (int i = k + threadIdx.x; i < m; i += blockDim.x) part = fmaf(a[i], a[i], part);
-    const float nrm2 = block_sum(part, red);
-    if (threadIdx.x == 0) {
-      const float x0 = a[k];
-      const float nrm = sqrtf(nrm2);
-      if (nrm == 0.f) {
-        tau[k] = 0.f;
-        rdiag[k] = 0.f;
-      } else {
-        const float alpha = (x0 >= 0.f) ? -nrm : nrm;
-        tau[k] = 1.f / (nrm * (nrm + fabsf(x0)));   // 2 / (v^T v)
-        rdiag[k] = alpha;
-        a[k] = x0 - alpha;
-      }
-    }
-    __syncthreads();
     const float tk = tau[k];
-    if (tk != 0.f) {
-      for (int j = k + 1 + warp; j < c; j += nw) {
-        float* aj = A + (size_t)j * ld;
+    const float* v = A + (size_t)k * ld;
+    int j = k + 1 + ((warp - (k + 1)) % nw + nw) % nw;   // smallest owned column > k
+    for (; j < c; j += nw) {
+      float* aj = A + (size_t)j * ld;
+      if (tk != 0.f) {
         float w = 0.f;
-        for (int i = k + lane; i < m; i += 32) w = fmaf(a[i], aj[i], w);
+        for (int i = k + lane; i < m; i += 32) w = fmaf(v[i], aj[i], w);
         w = warp_sum(w) * tk;
-        for (int i = k + lane; i < m; i += 32) aj[i] = fmaf(-w, a[i], aj[i]);
+        for (int i = k + lane; i < m; i += 32) aj[i] = fmaf(-w, v[i], aj[i]);
+        __syncwarp();
       }
+      if (j == k + 1 && k + 1 < K) hh_make(A, ld, m, k + 1, tau, rdiag);
     }
     __syncthreads();
   }
@@ -206,11 +234,211 @@ __device__ void hh_form_q(const float* A, float* Qm, int ld, int m, int c, const
 
 __device__ __forceinline__ int odd_ld(int m) { return m | 1; }
 
+// ------------------------------------------------------------------ register-resident Householder
+// Same factorisation as hh_factor / hh_form_q for m <= 32*MR rows and
+// c <= JPW*nwarps columns, with column j held in the registers of warp
+// j % nwarps (lane l: rows l + 32 t).  Step k: the owner of column k forms
+// H_k and publishes v_k through a double-buffered shared vector; one block
+// barrier; every warp applies H_k to its own columns.  A is read at entry and
+// written back (R above the diagonal, v_k at and below it) at exit.
+template <int MR, int JPW>
+__device__ void hh_factor_reg(float* A, int ld, int m, int c, float* tau, float* rdiag, float* vbuf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int K = min(m, c);
+  float col[JPW][MR];
+#pragma unroll
+  for (int u = 0; u < JPW; ++u) {
+    const int j = warp + u * nw;
+#pragma unroll
+    for (int t = 0; t < MR; ++t) {
+      const int i = lane + 32 * t;
+      col[u][t] = (j < c && i < m) ? A[(size_t)j * ld + i] : 0.f;
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    float* vb = vbuf + (k & 1) * (32 * MR);
+    if (warp == k % nw) {
+      const int uk = k / nw;
+      float s2 = 0.f, xk = 0.f;
+#pragma unroll
+      for (int u = 0; u < JPW; ++u) {
+        if (u != uk) continue;
+#pragma unroll
+        for (int t = 0; t < MR; ++t) {
+          const int i = lane + 32 * t;
+          const float x = col[u][t];
+          if (i >= k && i < m) s2 = fmaf(x, x, s2);
+          if (t == (k >> 5)) xk = x;
+        }
+      }
+      s2 = warp_sum(s2);
+      const float x0 = __shfl_sync(0xffffffffu, xk, k & 31);
+      const float nrm = sqrtf(s2);
+      const float alpha = (x0 >= 0.f) ? -nrm : nrm;
+      const float tk = (nrm == 0.f) ? 0.f : 1.f / (nrm * (nrm + fabsf(x0)));
+#pragma unroll
+      for (int u = 0; u < JPW; ++u) {
+        if (u != uk) continue;
+#pragma unroll
+        for (int t = 0; t < MR; ++t) {
+          const int i = lane + 32 * t;
+          float v = (i > k && i < m) ? col[u][t] : 0.f;
+          if (i == k && nrm != 0.f) {
+            v = x0 - alpha;
+            col[u][t] = v;
+          }
+          vb[i] = (i == k && nrm == 0.f) ? 0.f : v;
+        }
+      }
+      if (lane == 0) {
+        tau[k] = tk;
+        rdiag[k] = (nrm == 0.f) ? 0.f : alpha;
+      }
+    }
+    __syncthreads();
+    const float tk = tau[k];
+    if (tk != 0.f) {
+      float vr[MR];
+#pragma unroll
+      for (int t = 0; t < MR; ++t) vr[t] = vb[lane + 32 * t];
+      float w[JPW];
+#pragma unroll
+      for (int u = 0; u < JPW; ++u) {
+        w[u] = 0.f;
+#pragma unroll
+        for (int t = 0; t < MR; ++t) w[u] = fmaf(vr[t], col[u][t], w[u]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < JPW; ++u) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
+#pragma unroll
+      for (int u = 0; u < JPW; ++u) {
+        const int j = warp + u * nw;
+        if (j > k && j < c) {
+          const float s = w[u] * tk;
+#pragma unroll
+          for (int t = 0; t < MR; ++t) col[u][t] = fmaf(-s, vr[t], col[u][t]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < JPW; ++u) {
+    const int j = warp + u * nw;
+    if (j >= c) continue;
+#pragma unroll
+    for (int t = 0; t < MR; ++t) {
+      const int i = lane + 32 * t;
+      if (i < m) A[(size_t)j * ld + i] = col[u][t];
+    }
+  }
+  __syncthreads();
+}
+
+// Qm = H_0 ... H_{K-1} [I; 0] (signs fixed so that diag(R) > 0 when asked):
+// warp w builds its own columns by applying every reflector, no barriers.
+template <int MR, int JPW>
+__device__ void hh_form_q_reg(const float* A, float* Qm, int ld, int m, int c, const float* tau, const float* rdiag,
+                              bool fix_sign) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int K = min(m, c);
+  float q[JPW][MR];
+#pragma unroll
+  for (int u = 0; u < JPW; ++u) {
+    const int j = warp + u * nw;
+#pragma unroll
+    for (int t = 0; t < MR; ++t) q[u][t] = (lane + 32 * t == j) ? 1.f : 0.f;
+  }
+  const int jmax = min(c - 1, warp + (JPW - 1) * nw);
+  for (int k = min(K - 1, jmax); k >= 0; --k) {
+    const float tk = tau[k];
+    if (tk == 0.f) continue;
+    const float* v = A + (size_t)k * ld;
+    float vr[MR];
+#pragma unroll
+    for (int t = 0; t < MR; ++t) {
+      const int i = lane + 32 * t;
+      vr[t] = (i >= k && i < m) ? v[i] : 0.f;
+    }
+    float w[JPW];
+#pragma unroll
+    for (int u = 0; u < JPW; ++u) {
+      w[u] = 0.f;
+#pragma unroll
+      for (int t = 0; t < MR; ++t) w[u] = fmaf(vr[t], q[u][t], w[u]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int u = 0; u < JPW; ++u) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
+#pragma unroll
+    for (int u = 0; u < JPW; ++u) {
+      const int j = warp + u * nw;
+      if (j >= k && j < c) {
+        const float s = w[u] * tk;
+#pragma unroll
+        for (int t = 0; t < MR; ++t) q[u][t] = fmaf(-s, vr[t], q[u][t]);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < JPW; ++u) {
+    const int j = warp + u * nw;
+    if (j >= c) continue;
+    const float sg = (fix_sign && j < K && rdiag[j] < 0.f) ? -1.f : 1.f;
+#pragma unroll
+    for (int t = 0; t < MR; ++t) {
+      const int i = lane + 32 * t;
+      if (i < m) Qm[(size_t)j * ld + i] = sg * q[u][t];
+    }
+  }
+  __syncthreads();
+}
+
+// Dispatch on the row count (m <= 512: registers; larger: shared memory).
+template <int JPW>
+__device__ void qr_factor(float* A, int ld, int m, int c, float* tau, float* rdiag, float* vbuf) {
+  if (m <= 32) hh_factor_reg<1, JPW>(A, ld, m, c, tau, rdiag, vbuf);
+  else if (m <= 64) hh_factor_reg<2, JPW>(A, ld, m, c, tau, rdiag, vbuf);
+  else if (m <= 128) hh_factor_reg<4, JPW>(A, ld, m, c, tau, rdiag, vbuf);
+  else if (m <= 256) hh_factor_reg<8, JPW>(A, ld, m, c, tau, rdiag, vbuf);
+  else if (m <= 512) hh_factor_reg<16, JPW>(A, ld, m, c, tau, rdiag, vbuf);
+  else hh_factor(A, ld, m, c, tau, rdiag, nullptr);
+}
+template <int JPW>
+__device__ void qr_form_q(const float* A, float* Qm, int ld, int m, int c, const float* tau, const float* rdiag,
+                          bool fix_sign) {
+  if (m <= 32) hh_form_q_reg<1, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
+  else if (m <= 64) hh_form_q_reg<2, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
+  else if (m <= 128) hh_form_q_reg<4, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
+  else if (m <= 256) hh_form_q_reg<8, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
+  else if (m <= 512) hh_form_q_reg<16, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
+  else hh_form_q(A, Qm, ld, m, c, tau, rdiag, fix_sign);
+}
+
+
+
 // S5 level 1: QR of one row block of Z (sum of sketch partials).  Single-block
 // problems finish here (signs fixed); tall problems also write R_b.
-// Dynamic smem: A[ld*c] | Qm[ld*c] | tau[CMAX] | rdiag[CMAX] | red[32]
-__global__ void __launch_bounds__(512) k_qr1(const RFProb* __restrict__ P,
-                                             const int64_t* __restrict__ pre, int np) {
+// Dynamic smem: A[ld*c] | Qm[ld*c] | tau[CMAX] | rdiag[CMAX] | vbuf[1024]
+constexpr int QR_THREADS = 512;
+constexpr int QR_JPW = CMAX / (QR_THREADS / 32);
+__device__ __forceinline__ float sum_partials(const float* __restrict__ base, int64_t stride, int n) {
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  int ch = 0;
+  for (; ch + 4 <= n; ch += 4) {
+    a0 += __ldg(base + (int64_t)ch * stride);
+    a1 += __ldg(base + (int64_t)(ch + 1) * stride);
+    a2 += __ldg(base + (int64_t)(ch + 2) * stride);
+    a3 += __ldg(base + (int64_t)(ch + 3) * stride);
+  }
+  for (; ch < n; ++ch) a0 += __ldg(base + (int64_t)ch * stride);
+  return (a0 + a1) + (a2 + a3);
+}
+
+__global__ void __launch_bounds__(QR_THREADS) k_qr1(const RFProb* __restrict__ P,
+                                                    const int64_t* __restrict__ pre, int np) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = find_prob(pre, np, blockIdx.x);
   const RFProb& q = P[p];
@@ -223,36 +451,34 @@ __global__ void __launch_bounds__(512) k_qr1(const RFProb* __restrict__ P,
   float* Qm = A + (size_t)ld * c;
   float* tau = Qm + (size_t)ld * c;
   float* rdiag = tau + CMAX;
-  float* red = rdiag + CMAX;
+  float* vbuf = rdiag + CMAX;
   const int64_t zsz = q.nS * c;
-  for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
+#pragma unroll 2
+  for (int e = threadIdx.x; e < m * c; e += QR_THREADS) {
     const int i = e / c, j = e % c;
-    const int64_t g = (row0 + i) * c + j;
-    float acc = 0.f;
-    for (int ch = 0; ch < q.nzc; ++ch) acc += q.Zp[ch * zsz + g];
-    A[(size_t)j * ld + i] = acc;
+    A[(size_t)j * ld + i] = sum_partials(q.Zp + (row0 + i) * c + j, zsz, q.nzc);
   }
   __syncthreads();
-  hh_factor(A, ld, m, c, tau, rdiag, red);
+  qr_factor<QR_JPW>(A, ld, m, c, tau, rdiag, vbuf);
   const bool single = (q.nrb == 1);
   if (!single) {  // R_b (c x c, zero below the diagonal and beyond row K)
     float* Rb = q.Rb + (size_t)b * c * c;
-    for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    for (int e = threadIdx.x; e < c * c; e += QR_THREADS) {
       const int k = e / c, j = e % c;
       float v = 0.f;
       if (k < m && j >= k) v = (j == k) ? rdiag[k] : A[(size_t)j * ld + k];
       Rb[e] = v;
     }
   }
-  hh_form_q(A, Qm, ld, m, c, tau, rdiag, single);
-  for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
+  qr_form_q<QR_JPW>(A, Qm, ld, m, c, tau, rdiag, single);
+  for (int e = threadIdx.x; e < m * c; e += QR_THREADS) {
     const int i = e / c, j = e % c;
     q.Q[(row0 + i) * c + j] = Qm[(size_t)j * ld + i];
   }
 }
 
 // S5 level 2 (tall Z): QR of the stacked R_b, (nrb c) x c; Q2 with diag(R) > 0.
-__global__ void __launch_bounds__(512) k_qr2(const RFProb* __restrict__ P,
+__global__ void __launch_bounds__(QR_THREADS) k_qr2(const RFProb* __restrict__ P,
                                              const int64_t* __restrict__ pre, int np) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = find_prob(pre, np, blockIdx.x);
@@ -270,8 +496,8 @@ __global__ void __launch_bounds__(512) k_qr2(const RFProb* __restrict__ P,
     A[(size_t)j * ld + i] = q.Rb[e];
   }
   __syncthreads();
-  hh_factor(A, ld, m, c, tau, rdiag, red);
-  hh_form_q(A, Qm, ld, m, c, tau, rdiag, true);
+  qr_factor<QR_JPW>(A, ld, m, c, tau, rdiag, red + 32);
+  qr_form_q<QR_JPW>(A, Qm, ld, m, c, tau, rdiag, true);
   for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
     const int i = e / c, j = e % c;
     q.Q2[e] = Qm[(size_t)j * ld + i];
@@ -379,9 +605,96 @@ __global__ void __launch_bounds__(256) k_bt_partial(const RFProb* __restrict__ P
   }
 }
 
+// S6 (rows of Y fit one block): B^T chunk = Y_chunk^T Q accumulated over all
+// rows, kept in shared memory and factorised right away -> R_chunk.
+// Dynamic smem: Ys[32][BT_LDY] | Qs[32][CMAX] | A[ld*c] | tau | rdiag
+__global__ void __launch_bounds__(QR_THREADS) k_bt_fused(const RFProb* __restrict__ P,
+                                                  const int64_t* __restrict__ pre, int np) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ys = reinterpret_cast<float*>(smem_raw);
+  float* Qs = Ys + 32 * BT_LDY;
+  float* A = Qs + 32 * CMAX;
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int sc = (int)((int64_t)blockIdx.x - pre[p]);
+  const int c = q.c, cp = (c + 3) & ~3;
+  const int64_t j0 = (int64_t)sc * q.scrows;
+  const int mj = (int)min((int64_t)q.scrows, q.s - j0);
+  const int ld = odd_ld(mj);
+  float* tau = A + (size_t)ld * c;
+  float* rdiag = tau + CMAX;
+  float* vbuf = rdiag + CMAX;
+  const int ntile = (BT_SC / 4) * (cp / 4);
+  float acc[2][4][4];
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[u][a][b] = 0.f;
+  for (int64_t it = 0; it < q.nS; it += 32) {
+    const int mi = (int)min((int64_t)32, q.nS - it);
+    __syncthreads();
+#pragma unroll
+    for (int e = threadIdx.x; e < 32 * BT_SC; e += QR_THREADS) {
+      const int jj = e / 32, ii = e % 32;
+      Ys[ii * BT_LDY + jj] = (jj < mj && ii < mi) ? q.Yt[(j0 + jj) * q.nS + it + ii] : 0.f;
+    }
+    for (int e = threadIdx.x; e < 32 * cp; e += QR_THREADS) {
+      const int ii = e / cp, cc = e % cp;
+      Qs[ii * CMAX + cc] = (ii < mi && cc < c) ? q.Q[(it + ii) * c + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int t = threadIdx.x + QR_THREADS * u;
+      if (t < ntile) {
+        const int jg = t % (BT_SC / 4), cg = t / (BT_SC / 4);
+#pragma unroll 8
+        for (int ii = 0; ii < 32; ++ii) {
+          const float4 y = *reinterpret_cast<const float4*>(Ys + ii * BT_LDY + jg * 4);
+          const float4 o = *reinterpret_cast<const float4*>(Qs + ii * CMAX + cg * 4);
+          const float ya[4] = {y.x, y.y, y.z, y.w};
+          const float ob[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[u][a][b] = fmaf(ya[a], ob[b], acc[u][a][b]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int t = threadIdx.x + QR_THREADS * u;
+    if (t < ntile) {
+      const int jg = t % (BT_SC / 4), cg = t / (BT_SC / 4);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int jj = jg * 4 + a;
+        if (jj >= mj) continue;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int cc = cg * 4 + b;
+          if (cc < c) A[(size_t)cc * ld + jj] = acc[u][a][b];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  qr_factor<QR_JPW>(A, ld, mj, c, tau, rdiag, vbuf);
+  float* Rc = q.Rc + (size_t)sc * c * c;
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    const int k = e / c, j = e % c;
+    float v = 0.f;
+    if (k < mj && j >= k) v = (j == k) ? rdiag[k] : A[(size_t)j * ld + k];
+    Rc[e] = v;
+  }
+}
+
 // S6: QR of one sample chunk of B^T (sum of the row-block partials) -> R_chunk.
 // Dynamic smem: A[ld*c] | tau | rdiag | red
-__global__ void __launch_bounds__(512) k_bt_qr(const RFProb* __restrict__ P,
+__global__ void __launch_bounds__(QR_THREADS) k_bt_qr(const RFProb* __restrict__ P,
                                                const int64_t* __restrict__ pre, int np) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = find_prob(pre, np, blockIdx.x);
@@ -402,7 +715,7 @@ __global__ void __launch_bounds__(512) k_bt_qr(const RFProb* __restrict__ P,
     A[(size_t)j * ld + i] = acc;
   }
   __syncthreads();
-  hh_factor(A, ld, m, c, tau, rdiag, red);
+  qr_factor<QR_JPW>(A, ld, m, c, tau, rdiag, red + 32);
   float* Rc = q.Rc + (size_t)sc * c * c;
   for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
     const int k = e / c, j = e % c;
@@ -417,7 +730,9 @@ __global__ void __launch_bounds__(512) k_bt_qr(const RFProb* __restrict__ P,
 // are processed in round-robin order, one warp per pair, until a sweep makes
 // no rotation (or 40 sweeps).  W is stored sorted by descending sigma.
 // Dynamic smem: A[ld*c] | tau | rdiag | red | AT[CMAX*(CMAX+1)] | sig[CMAX] | flag
-__global__ void __launch_bounds__(1024) k_wsvd(const RFProb* __restrict__ P,
+static_assert(QR_THREADS / 16 >= CMAX / 2, "one 16-lane group per Jacobi pair");
+static_assert(WS_LDT >= CMAX && WS_LDT % 32 == 16, "Jacobi column stride");
+__global__ void __launch_bounds__(QR_THREADS) k_wsvd(const RFProb* __restrict__ P,
                                                const int64_t* __restrict__ pre, int np,
                                                int* status) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -430,70 +745,105 @@ __global__ void __launch_bounds__(1024) k_wsvd(const RFProb* __restrict__ P,
   float* tau = A + (size_t)ld * c;
   float* rdiag = tau + CMAX;
   float* red = rdiag + CMAX;
-  float* AT = red + 32;                  // column q of R^T at AT[q*(CMAX+1) + i]
-  float* sig = AT + CMAX * (CMAX + 1);
+  float* AT = red + 32;                  // column q of R^T at AT[q*WS_LDT + i], zero-padded to CMAX rows
+  float* sig = AT + CMAX * WS_LDT;
   int* flag = reinterpret_cast<int*>(sig + CMAX);
-  const int LDT = CMAX + 1;
+  constexpr int LDT = WS_LDT;
   for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
     const int i = e / c, j = e % c;
     A[(size_t)j * ld + i] = q.Rc[e];
   }
   if (threadIdx.x < q.r) q.keys[threadIdx.x] = 0ull;
+  if (threadIdx.x < 2) flag[threadIdx.x] = 0;
   __syncthreads();
-  hh_factor(A, ld, m, c, tau, rdiag, red);
-  // AT[qc][i] = R[qc][i]  (column qc of R^T is row qc of R)
-  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
-    const int qc = e / c, i = e % c;
+  qr_factor<QR_JPW>(A, ld, m, c, tau, rdiag, sig + CMAX + 8);
+  // AT[qc][i] = R[qc][i]  (column qc of R^T is row qc of R); rows c..CMAX-1 stay zero so
+  // that every pair below runs the same fixed-length, fully unrolled loop.
+  for (int e = threadIdx.x; e < CMAX * CMAX; e += blockDim.x) {
+    const int qc = e / CMAX, i = e % CMAX;
     float v = 0.f;
-    if (qc < m && i >= qc) v = (i == qc) ? rdiag[qc] : A[(size_t)i * ld + qc];
+    if (qc < c && qc < m && i < c && i >= qc) v = (i == qc) ? rdiag[qc] : A[(size_t)i * ld + qc];
     AT[qc * LDT + i] = v;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int ne = c + (c & 1);           // even number of players (dummy = c)
-  const float tol = 1e-6f;
+  // Convergence threshold on |a_p . a_q| / (|a_p| |a_q|): about twice the worst rounding
+  // error of the 16-term tree dot product below, so a converged pair is not rotated again
+  // on noise alone.
+  const float tol = 2e-6f;
+  // Round-robin (circle) ordering: pair pr meets columns pa, qa; each round the players
+  // other than column 0 move one seat.  One pair per 16-lane group; lane l16 holds rows
+  // l16 + 16 k.  Column stride LDT = 80 puts the two groups of a warp on opposite bank
+  // halves (their columns differ in parity).
+  const int pr = threadIdx.x >> 4, l16 = threadIdx.x & 15;
+  const int kc = (c + 15) >> 4;
+  const unsigned gm = 0xffffu << (threadIdx.x & 16);
   int sweep = 0;
-  for (; sweep < 40; ++sweep) {
-    if (threadIdx.x == 0) *flag = 0;
-    __syncthreads();
+  for (; sweep < WS_MAX_SWEEPS; ++sweep) {
+    int t = pr - 1, u = ne - 2 - pr;
+    int rotated = 0;
     for (int rnd = 0; rnd < ne - 1; ++rnd) {
-      for (int pr = warp; pr < ne / 2; pr += nw) {
-        const int pa = (pr == 0) ? 0 : 1 + (pr - 1 + rnd) % (ne - 1);
-        const int qa = 1 + (ne - 2 - pr + rnd) % (ne - 1);
-        if (pa >= c || qa >= c) continue;
-        float* ap = AT + pa * LDT;
-        float* aq = AT + qa * LDT;
-        float al = 0.f, be = 0.f, ga = 0.f;
-        for (int i = lane; i < c; i += 32) {
-          const float x = ap[i], y = aq[i];
-          al = fmaf(x, x, al);
-          be = fmaf(y, y, be);
-          ga = fmaf(x, y, ga);
+      const int pa = (pr == 0) ? 0 : 1 + t;
+      const int qa = 1 + u;
+      if (pr < ne / 2 && pa < c && qa < c) {
+        float* ap = AT + pa * LDT + l16;
+        float* aq = AT + qa * LDT + l16;
+        float x[CMAX / 16], y[CMAX / 16];
+#pragma unroll
+        for (int k = 0; k < CMAX / 16; ++k) {
+          x[k] = (k < kc) ? ap[16 * k] : 0.f;
+          y[k] = (k < kc) ? aq[16 * k] : 0.f;
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (ga != 0.f && fabsf(ga) > tol * sqrtf(al) * sqrtf(be)) {
-          const float zeta = (be - al) / (2.f * ga);
-          float t;
-          if (fabsf(zeta) > 1e18f) t = 0.5f / zeta;
-          else t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-          const float cs = rsqrtf(1.f + t * t), sn = cs * t;
-          for (int i = lane; i < c; i += 32) {
-            const float x = ap[i], y = aq[i];
-            ap[i] = cs * x - sn * y;
-            aq[i] = sn * x + cs * y;
+        float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+        for (int k = 0; k < CMAX / 16; ++k) {
+          al = fmaf(x[k], x[k], al);
+          be = fmaf(y[k], y[k], be);
+          ga = fmaf(x[k], y[k], ga);
+        }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(gm, al, o);
+          be += __shfl_xor_sync(gm, be, o);
+          ga += __shfl_xor_sync(gm, ga, o);
+        }
+        if (ga != 0.f && fabsf(ga) * rsqrt_approx(al) * rsqrt_approx(be) > tol) {
+          // tangent of the angle that makes the pair orthogonal, smaller root
+          const float zeta = (be - al) * rcp_approx(2.f * ga);
+          const float az = fabsf(zeta);
+          float tt;
+          if (az > 1e18f) {
+            tt = 0.5f * rcp_approx(zeta);
+          } else {
+            const float s1 = fmaf(zeta, zeta, 1.f);
+            tt = copysignf(rcp_approx(az + s1 * rsqrt_approx(s1)), zeta);
           }
-          if (lane == 0) *flag = 1;
+          const float cs = rsqrt_approx(fmaf(tt, tt, 1.f)), sn = cs * tt;
+#pragma unroll
+          for (int k = 0; k < CMAX / 16; ++k) {
+            if (k < kc) {
+              ap[16 * k] = cs * x[k] - sn * y[k];
+              aq[16 * k] = sn * x[k] + cs * y[k];
+            }
+          }
+          rotated = 1;
         }
       }
+      if (++t == ne - 1) t = 0;
+      if (++u == ne - 1) u = 0;
       __syncthreads();
     }
-    const int f = *flag;
+    // flag[sweep & 1] is set by any pair that rotated; the other slot is cleared for the
+    // next sweep (it was last read before the previous barrier).
+    if (rotated) flag[sweep & 1] = 1;
+    __syncthreads();
+    const int f = flag[sweep & 1];
+    if (threadIdx.x == 0) flag[(sweep + 1) & 1] = 0;
     __syncthreads();
     if (!f) break;
   }
-  if (sweep == 40 && threadIdx.x == 0) set_status(status, ST_NUMERIC);
+  if (sweep == WS_MAX_SWEEPS && threadIdx.x == 0) set_status(status, ST_NUMERIC);
   // singular values (column norms) and descending order
   for (int qc = warp; qc < c; qc += nw) {
     float s2 = 0.f;
@@ -582,13 +932,16 @@ __global__ void __launch_bounds__(256) k_flip(const RFProb* __restrict__ P,
 
 // ------------------------------------------------------------------ host launchers
 static size_t smem_gs() { return (size_t)(SK_TJ * SK_TI + SK_TJ * CMAX) * 4 + SK_TJ * 8; }
-static size_t smem_qr() { return (size_t)(2 * QR_MAXF + 2 * CMAX + 32 + 2 * CMAX) * 4 + 64; }
-static size_t smem_qr2() { return (size_t)(2 * QR2_MAXF + 2 * CMAX + 32 + 2 * CMAX) * 4 + 64; }
+static size_t smem_qr() { return (size_t)(2 * QR_MAXF + 2 * CMAX + 1024) * 4 + 64; }
+static size_t smem_qr2() { return (size_t)(2 * QR2_MAXF + 2 * CMAX + 32 + 1024) * 4 + 64; }
 static size_t smem_qr3() { return (size_t)(QR_MAXF + CMAX * CMAX) * 4; }
 static size_t smem_btp() { return (size_t)(32 * BT_LDY + 32 * CMAX) * 4; }
-static size_t smem_btq() { return (size_t)(QR_MAXF + 2 * CMAX + 32 + 2 * CMAX) * 4 + 64; }
+static size_t smem_btf() {
+  return (size_t)(32 * BT_LDY + 32 * CMAX + (BT_SC + 1) * CMAX + 2 * CMAX + 1024) * 4 + 64;
+}
+static size_t smem_btq() { return (size_t)(QR_MAXF + 2 * CMAX + 32 + 1024) * 4 + 64; }
 static size_t smem_wsvd() {
-  return (size_t)(WS_MAXF + 2 * CMAX + 32 + CMAX * (CMAX + 1) + CMAX + 8) * 4 + 64;
+  return (size_t)(WS_MAXF + 2 * CMAX + 32 + CMAX * WS_LDT + CMAX + 8 + 1024) * 4 + 64;
 }
 static size_t smem_qw() { return (size_t)(CMAX * CMAX + QW_TI * CMAX) * 4 + CMAX * 8; }
 static size_t smem_flip() { return (size_t)(CMAX * CMAX + CMAX) * 4; }
@@ -605,6 +958,7 @@ cudaError_t rf_init_attributes() {
   RT_ATTR(k_qr3, smem_qr3());
   RT_ATTR(k_bt_partial, smem_btp());
   RT_ATTR(k_bt_qr, smem_btq());
+  RT_ATTR(k_bt_fused, smem_btf());
   RT_ATTR(k_wsvd, smem_wsvd());
   RT_ATTR(k_qw, smem_qw());
   RT_ATTR(k_flip, smem_flip());
@@ -622,24 +976,31 @@ int launch_range_finder(const RFGroup& g, cudaStream_t st, int* status) {
   if (g.total[STG_SAMPLE] > 0) {
     k_sample<<<(unsigned)((g.total[STG_SAMPLE] + 255) / 256), 256, 0, st>>>(
         g.probs, pre + STG_SAMPLE * stride, np, status);
-    ++n;
+    k_omega<<<(unsigned)((g.total[STG_OMEGA] + 255) / 256), 256, 0, st>>>(g.probs, pre + STG_OMEGA * stride, np);
+    n += 2;
   }
   k_gather_sketch<<<grid_of(g.total[STG_GS]), 256, smem_gs(), st>>>(g.probs, pre + STG_GS * stride, np);
   ++n;
-  k_qr1<<<grid_of(g.total[STG_QR1]), 512, smem_qr(), st>>>(g.probs, pre + STG_QR1 * stride, np);
+  k_qr1<<<grid_of(g.total[STG_QR1]), QR_THREADS, smem_qr(), st>>>(g.probs, pre + STG_QR1 * stride, np);
   ++n;
   if (g.total[STG_QR2] > 0) {
-    k_qr2<<<grid_of(g.total[STG_QR2]), 512, smem_qr2(), st>>>(g.probs, pre + STG_QR2 * stride, np);
+    k_qr2<<<grid_of(g.total[STG_QR2]), QR_THREADS, smem_qr2(), st>>>(g.probs, pre + STG_QR2 * stride, np);
     k_qr3<<<grid_of(g.total[STG_QR3]), 256, smem_qr3(), st>>>(g.probs, pre + STG_QR3 * stride, np);
     n += 2;
   }
-  k_bt_partial<<<grid_of(g.total[STG_BTP]), 256, smem_btp(), st>>>(g.probs, pre + STG_BTP * stride, np);
-  k_bt_qr<<<grid_of(g.total[STG_BTQ]), 512, smem_btq(), st>>>(g.probs, pre + STG_BTQ * stride, np);
-  k_wsvd<<<grid_of(g.total[STG_WSVD]), 1024, smem_wsvd(), st>>>(g.probs, pre + STG_WSVD * stride, np,
+  if (g.total[STG_BTP] == g.total[STG_BTQ]) {   // every problem reduces B^T over one row block
+    k_bt_fused<<<grid_of(g.total[STG_BTQ]), QR_THREADS, smem_btf(), st>>>(g.probs, pre + STG_BTQ * stride, np);
+    n += 1;
+  } else {
+    k_bt_partial<<<grid_of(g.total[STG_BTP]), 256, smem_btp(), st>>>(g.probs, pre + STG_BTP * stride, np);
+    k_bt_qr<<<grid_of(g.total[STG_BTQ]), QR_THREADS, smem_btq(), st>>>(g.probs, pre + STG_BTQ * stride, np);
+    n += 2;
+  }
+  k_wsvd<<<grid_of(g.total[STG_WSVD]), QR_THREADS, smem_wsvd(), st>>>(g.probs, pre + STG_WSVD * stride, np,
                                                                  status);
   k_qw<<<grid_of(g.total[STG_QW]), 256, smem_qw(), st>>>(g.probs, pre + STG_QW * stride, np);
   k_flip<<<grid_of(g.total[STG_FLIP]), 256, smem_flip(), st>>>(g.probs, pre + STG_FLIP * stride, np);
-  n += 6;
+  n += 3;
   return n;
 }
 

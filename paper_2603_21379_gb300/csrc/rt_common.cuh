@@ -82,6 +82,21 @@ __device__ __forceinline__ float load_x(const void* X, int dtype, int64_t e) {
   return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(X)[e]);
 }
 
+// Single-instruction approximations (flush-to-zero) used where a few ulp do not matter:
+// the rotation parameters of the Jacobi SVD, whose orthogonality comes from cs^2 + sn^2
+// = 1, not from the exact angle.
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -17,11 +17,13 @@ constexpr int QR2_MAXF = 24576;    // floats per smem array in the TSQR second l
 constexpr int BT_SC = 128;         // samples per chunk of B^T = Y^T Q
 constexpr int BT_IB = 2048;        // rows per reduction block of B^T
 constexpr int WS_MAXF = 24576;     // floats of the stacked R factors in the W-step
-constexpr int QW_TI = 128;         // rows per tile of U = Q W
+constexpr int WS_LDT = 80;         // column stride of R^T in the Jacobi SVD (CMAX + 16)
+constexpr int WS_MAX_SWEEPS = 40;  // one-sided Jacobi sweeps before ST_NUMERIC
+constexpr int QW_TI = 32;          // rows per tile of U = Q W
 
 enum Stage : int {
   STG_SAMPLE = 0, STG_GS, STG_QR1, STG_QR2, STG_QR3, STG_BTP, STG_BTQ, STG_WSVD, STG_QW, STG_FLIP,
-  STG_ZSUM, STG_COUNT
+  STG_ZSUM, STG_OMEGA, STG_COUNT
 };
 
 // Device-side view of a planned group of range-finder problems.
