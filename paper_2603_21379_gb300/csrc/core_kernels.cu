@@ -95,9 +95,140 @@ __global__ void __launch_bounds__(256) k_ttm_t(const T* __restrict__ A, int64_t 
   }
 }
 
+// ---------------------------------------------------------------- FP32, rho-contiguous form
+// out(l, a, rho) = sum_i U[i][a] A(l, i, rho) for float A with R % 4 == 0.  One CTA owns
+// all 32 a (of a 32-row block of U^T) and TN consecutive rho of one l; each thread keeps an
+// 8 x 8 block of outputs in registers: 8 a times two runs of 4 rho, TN/2 apart, so that
+// the 16-byte shared loads of consecutive lanes are consecutive (no bank conflicts).  A and U tiles of TK rows of i are staged in
+// shared memory by 16-byte / 4-byte cp.async in a TS-deep ring, so the loads of tile
+// t + TS - 1 overlap the FMAs of tile t.
+constexpr int TF_TK = 32, TF_TS = 3;
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int TN>
+constexpr size_t ttm_f32_smem() { return (size_t)TF_TS * TF_TK * (TN + 32) * sizeof(float); }
+
+template <int TN>
+__global__ void __launch_bounds__(TN / 2) k_ttm_f32(const float* __restrict__ A, int64_t n, int64_t R,
+                                                    int64_t tiles_per_l, const float* __restrict__ U, int r,
+                                                    float* __restrict__ out) {
+  constexpr int NT = TN / 2;               // threads: 4 a-groups x TN/8 rho-groups
+  extern __shared__ __align__(16) float tsm[];
+  float* As = tsm;                          // [TS][TK][TN]
+  float* Us = tsm + TF_TS * TF_TK * TN;     // [TS][TK][32]
+  const int tid = threadIdx.x;
+  const int64_t l = blockIdx.x / tiles_per_l;
+  const int64_t rho0 = (blockIdx.x - l * tiles_per_l) * TN;
+  const int a0 = blockIdx.y * 32;
+  const int ta = tid / (TN / 8), tr = tid % (TN / 8);
+  const float* Al = A + l * n * R;
+  const int nk = (int)((n + TF_TK - 1) / TF_TK);
+
+  auto issue = [&](int kt) {
+    const int stg = kt % TF_TS;
+    float* as = As + stg * TF_TK * TN;
+    float* us = Us + stg * TF_TK * 32;
+    const int64_t i0 = (int64_t)kt * TF_TK;
+#pragma unroll
+    for (int e = tid; e < TF_TK * TN / 4; e += NT) {
+      const int kk = e / (TN / 4), c4 = (e % (TN / 4)) * 4;
+      const int64_t i = i0 + kk, rho = rho0 + c4;
+      const bool ok = i < n && rho < R;
+      cp_async16(as + kk * TN + c4, ok ? (const void*)(Al + i * R + rho) : (const void*)A, ok ? 16 : 0);
+    }
+#pragma unroll
+    for (int e = tid; e < TF_TK * 32; e += NT) {
+      const int kk = e / 32, aa = e % 32;
+      const int64_t i = i0 + kk;
+      const bool ok = i < n && a0 + aa < r;
+      cp_async4(us + kk * 32 + aa, ok ? (const void*)(U + i * r + a0 + aa) : (const void*)U, ok ? 4 : 0);
+    }
+  };
+
+  float acc[8][8];
+#pragma unroll
+  for (int x = 0; x < 8; ++x)
+#pragma unroll
+    for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+
+#pragma unroll
+  for (int s = 0; s < TF_TS - 1; ++s) {
+    if (s < nk) issue(s);
+    cp_async_commit();
+  }
+  for (int kt = 0; kt < nk; ++kt) {
+    cp_async_wait<TF_TS - 2>();
+    __syncthreads();
+    if (kt + TF_TS - 1 < nk) issue(kt + TF_TS - 1);
+    cp_async_commit();
+    const float* as = As + (kt % TF_TS) * TF_TK * TN + tr * 4;
+    const float* us = Us + (kt % TF_TS) * TF_TK * 32 + ta * 8;
+#pragma unroll 8
+    for (int kk = 0; kk < TF_TK; ++kk) {
+      const float4 u0 = *reinterpret_cast<const float4*>(us + kk * 32);
+      const float4 u1 = *reinterpret_cast<const float4*>(us + kk * 32 + 4);
+      const float4 b0 = *reinterpret_cast<const float4*>(as + kk * TN);
+      const float4 b1 = *reinterpret_cast<const float4*>(as + kk * TN + TN / 2);
+      const float ua[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+      const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int x = 0; x < 8; ++x)
+#pragma unroll
+        for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(ua[x], bb[y], acc[x][y]);
+    }
+  }
+  cp_async_wait<0>();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t rho = rho0 + h * (TN / 2) + tr * 4;
+    if (rho >= R) continue;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      const int a = a0 + ta * 8 + x;
+      if (a >= r) continue;
+      float* o = out + (l * r + a) * R + rho;
+      if (rho + 4 <= R) {
+        *reinterpret_cast<float4*>(o) = make_float4(acc[x][4 * h], acc[x][4 * h + 1], acc[x][4 * h + 2], acc[x][4 * h + 3]);
+      } else {
+#pragma unroll
+        for (int y = 0; y < 4; ++y)
+          if (rho + y < R) o[y] = acc[x][4 * h + y];
+      }
+    }
+  }
+}
+
+static int g_num_sms = 0;
+
 int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, const float* U, int r,
                  float* out, cudaStream_t st) {
   const int64_t ncol = L * R;
+  if (dtype == DT_F32 && R >= 128 && R % 4 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
+      (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+    // rho-contiguous FP32 form; the narrower tile when the wide one leaves SMs idle
+    const int64_t t256 = (R + 255) / 256;
+    const unsigned gy = (unsigned)((r + 31) / 32);
+    if (L * t256 * gy >= 2 * (int64_t)g_num_sms) {
+      dim3 grid((unsigned)(L * t256), gy);
+      k_ttm_f32<256><<<grid, 128, ttm_f32_smem<256>(), st>>>(static_cast<const float*>(A), n, R, t256, U, r, out);
+    } else {
+      const int64_t t128 = (R + 127) / 128;
+      dim3 grid((unsigned)(L * t128), gy);
+      k_ttm_f32<128><<<grid, 64, ttm_f32_smem<128>(), st>>>(static_cast<const float*>(A), n, R, t128, U, r, out);
+    }
+    return 1;
+  }
   dim3 grid((unsigned)((ncol + TT_BN - 1) / TT_BN), (unsigned)((r + TT_BM - 1) / TT_BM));
   if (dtype == DT_F32)
     k_ttm_t<float><<<grid, 256, 0, st>>>(static_cast<const float*>(A), L, n, R, U, r, out);
@@ -108,6 +239,15 @@ int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, cons
   return 1;
 }
 
-cudaError_t core_init_attributes() { return cudaSuccess; }
+cudaError_t core_init_attributes() {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ttm_f32<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ttm_f32_smem<256>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_ttm_f32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ttm_f32_smem<128>());
+  return e;
+}
 
 }  // namespace rt

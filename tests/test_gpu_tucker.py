@@ -160,6 +160,22 @@ def test_core_entry_point_and_evaluator(rt):
     assert abs(eg - eh) <= 1e-9
 
 
+def test_core_wide_rho_ragged_tiles(rt):
+    # order 4: the tensor-core pass contracts modes 3, 4 (P has 12*12 = 144 trailing
+    # entries per slab), then the register-tiled FP32 contraction runs twice with ragged
+    # rho tiles (144 and 7*144 = 1008), ragged i (45, 37) and a-blocks of 5 and 7 rows
+    rs = np.random.default_rng(5)
+    shape, ranks = (37, 45, 24, 20), (5, 7, 12, 12)
+    X = rs.standard_normal(shape).astype(np.float32)
+    U = [np.linalg.qr(rs.standard_normal((n, k)))[0] for n, k in zip(shape, ranks)]
+    Ud = [torch.from_numpy(u.astype(np.float32)).cuda() for u in U]
+    G = rt.rtucker_core(torch.from_numpy(X).cuda(), Ud)
+    Uf = [u.astype(np.float32).astype(np.float64) for u in U]
+    Gr = tucker.multi_ttm_t(X.astype(np.float64), Uf)
+    assert G.shape == tuple(ranks)
+    assert np.abs(to_np(G) - Gr).max() <= 1e-4 * np.abs(Gr).max()
+
+
 def test_invalid_arguments_raise(rt):
     X = torch.zeros((4, 5, 6), device="cuda")
     with pytest.raises(rt.RtError) as e:
