@@ -54,16 +54,21 @@ typedef enum {
 typedef enum { RT_F32 = 0, RT_F64 = 1, RT_BF16 = 2 } rt_dtype; /* storage type of X */
 
 typedef enum {
-  RT_PREC_FP32 = 0, /* float32 arithmetic throughout (default)                 */
-  RT_PREC_BF16 = 1  /* bfloat16 sketch / multi-TTM operands, float32 accumulate */
+  RT_PREC_FP32 = 0, /* float32-accurate arithmetic throughout (default)         */
+  RT_PREC_BF16 = 1  /* BF16 compute form: in the tensor-core pass over a float32
+                       X, X is rounded to one bfloat16 term (the factors and the
+                       intermediate keep two terms; float32 accumulate).  The
+                       range finder still computes in float32.  Tucker entry
+                       points only; shapes the tensor-core pass cannot take run
+                       in float32.  rhtucker_* return RT_ENOTSUP.             */
 } rt_prec;
 
 typedef struct rt_handle_s* rt_handle;
 
 typedef struct {
   int32_t prec;        /* rt_prec                                              */
-  int32_t use_graph;   /* 1: capture the launch sequence in a CUDA graph once per
-                          shape and replay it (pointers must stay the same)      */
+  int32_t use_graph;   /* must be 0: CUDA-graph replay is not provided yet
+                          (nonzero returns RT_ENOTSUP)                           */
   int32_t reserved[6]; /* must be zero                                          */
 } rt_options;
 

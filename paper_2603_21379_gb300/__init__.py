@@ -245,24 +245,40 @@ def rtucker_factors(X, r, p, s=None, seed=0, with_sigma=False):
     return Us
 
 
+_PREC = {"fp32": 0, "bf16": 1}
+
+
+def _opts(prec):
+    """rt_options for a precision form, or None (defaults) for "fp32"."""
+    if prec not in _PREC:
+        raise ValueError("prec must be 'fp32' or 'bf16'")
+    if prec == "fp32":
+        return None
+    o = _Options()
+    o.prec = _PREC[prec]
+    return ctypes.byref(o)
+
+
 def _cat_u(U):
     return torch.cat([u.reshape(-1).to(torch.float32) for u in U]).contiguous()
 
 
-def rtucker_core(X, U):
-    """S7: core G = X x_1 U_1^T ... x_d U_d^T (float32)."""
+def rtucker_core(X, U, prec="fp32"):
+    """S7: core G = X x_1 U_1^T ... x_d U_d^T (float32 result; prec="bf16" rounds a
+    float32 X to one bfloat16 term in the tensor-core pass)."""
     lib = load_library()
     dt, d, n = _tensor_args(X)
     r = [int(u.shape[1]) for u in U]
     Uc = _cat_u(U)
     G = torch.empty(r, dtype=torch.float32, device=X.device)
     h = _handle(X.device.index)
-    _check(h, lib.rtucker_core(h, _ptr(X), dt, d, _i64(n), _i32(r), _ptr(Uc), None, _ptr(G)))
+    _check(h, lib.rtucker_core(h, _ptr(X), dt, d, _i64(n), _i32(r), _ptr(Uc), _opts(prec), _ptr(G)))
     return G
 
 
-def rtucker_decompose(X, r, p, s=None, seed=0, out=None):
-    """S1-S7: Sub-R-HOSVD; returns (G, [U_k]).  ``out`` = (Uflat, G) reuses buffers."""
+def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32"):
+    """S1-S7: Sub-R-HOSVD; returns (G, [U_k]).  ``out`` = (Uflat, G) reuses buffers;
+    ``prec`` "fp32" (default) or "bf16" (the BF16 compute form of the core pass)."""
     lib = load_library()
     dt, d, n = _tensor_args(X)
     r = _as_list(r, d)
@@ -273,12 +289,12 @@ def rtucker_decompose(X, r, p, s=None, seed=0, out=None):
         U, G = out
     h = _handle(X.device.index)
     sp = _i64(_as_list(s, d)) if s is not None else None
-    _check(h, lib.rtucker_decompose(h, _ptr(X), dt, d, _i64(n), _i32(r), int(p), sp, ctypes.c_uint64(seed), None,
-                                    _ptr(U), _ptr(G)))
+    _check(h, lib.rtucker_decompose(h, _ptr(X), dt, d, _i64(n), _i32(r), int(p), sp, ctypes.c_uint64(seed),
+                                    _opts(prec), _ptr(U), _ptr(G)))
     return G, _split(U, n, r)
 
 
-def rtucker_decompose_host(X, r, p, s=None, seed=0, out=None):
+def rtucker_decompose_host(X, r, p, s=None, seed=0, out=None, prec="fp32"):
     """Sub-R-HOSVD of a HOST tensor (pinned memory recommended); copies in,
     decomposes, copies U and G back to host tensors; synchronous."""
     lib = load_library()
@@ -294,11 +310,11 @@ def rtucker_decompose_host(X, r, p, s=None, seed=0, out=None):
     h = _handle()
     sp = _i64(_as_list(s, d)) if s is not None else None
     _check(h, lib.rtucker_decompose_host(h, _ptr(X), _DT[X.dtype], d, _i64(n), _i32(r), int(p), sp,
-                                         ctypes.c_uint64(seed), None, _ptr(U), _ptr(G)))
+                                         ctypes.c_uint64(seed), _opts(prec), _ptr(U), _ptr(G)))
     return G, _split(U, n, r)
 
 
-def rtucker_decompose_batched(Xs, ranks, p, seeds, s=None):
+def rtucker_decompose_batched(Xs, ranks, p, seeds, s=None, prec="fp32"):
     """Batched Sub-R-HOSVD: one grouped launch per stage for all (tensor, mode)
     problems.  Returns a list of (G, [U_k])."""
     lib = load_library()
@@ -330,7 +346,8 @@ def rtucker_decompose_batched(Xs, ranks, p, seeds, s=None):
     G_arr = (ctypes.c_void_p * T)(*[g.data_ptr() for g in Gs])
     h = _handle(dev.index)
     _check(h, lib.rtucker_decompose_batched(h, T, X_arr, dt, _i32(ds), n_arr, r_arr, int(p), s_arr,
-                                            (ctypes.c_uint64 * T)(*[int(v) for v in seeds]), None, U_arr, G_arr))
+                                            (ctypes.c_uint64 * T)(*[int(v) for v in seeds]), _opts(prec), U_arr,
+                                            G_arr))
     out = []
     for X, r, U, G in zip(Xs, ranks, Us, Gs):
         n = list(X.shape)

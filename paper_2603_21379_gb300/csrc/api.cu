@@ -382,7 +382,8 @@ rt_status check_tensor(rt_handle h, const void* X, rt_dtype dtype, int d, const 
 
 rt_status check_opts(rt_handle h, const rt_options* opt) {
   if (!opt) return RT_OK;
-  if (opt->prec != RT_PREC_FP32) return fail(h, RT_ENOTSUP, "only RT_PREC_FP32 is available");
+  if (opt->prec != RT_PREC_FP32 && opt->prec != RT_PREC_BF16) return fail(h, RT_EINVAL, "unknown precision");
+  if (opt->use_graph) return fail(h, RT_ENOTSUP, "CUDA-graph replay is not provided");
   for (int i = 0; i < 6; ++i)
     if (opt->reserved[i]) return fail(h, RT_EINVAL, "reserved option fields must be zero");
   return RT_OK;
@@ -446,8 +447,13 @@ int core_mode() {
   return mode;
 }
 
+int prec_of(const rt_options* opt) { return opt ? opt->prec : RT_PREC_FP32; }
+
+// prec RT_PREC_BF16 rounds float32 X to one bf16 term in the tensor-core pass (the
+// factors and the intermediate keep two terms); shapes that pass cannot take run the
+// float32 chain instead.
 int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
-                 const float* U, float* G, float* bufA, float* bufB) {
+                 const float* U, float* G, float* bufA, float* bufB, int prec) {
   cudaStream_t st = h->stream;
   int nl = 0;
   size_t uoff[MAXD];
@@ -466,7 +472,8 @@ int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_
     int got = 0;
     {
       StageTimer tm(h, 1);
-      got = launch_core2_tc(dtype == RT_BF16 ? 1 : 0, X, S, (int)n[d - 2], (int)n[d - 1], U + uoff[d - 2],
+      const int xmode = (dtype == RT_BF16) ? 1 : (prec == RT_PREC_BF16 ? 2 : 0);
+      got = launch_core2_tc(xmode, X, S, (int)n[d - 2], (int)n[d - 1], U + uoff[d - 2],
                             r[d - 2], U + uoff[d - 1], r[d - 1], out, h->d_status, st);
     }
     if (got > 0) {
@@ -587,7 +594,7 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
     const float* Ucat = U ? U : nullptr;
     if (!Ucat) return fail(h, RT_EINVAL, "U is required with G");
     nl += enqueue_core(h, X, dtype, d, n, r, Ucat, G, reinterpret_cast<float*>(h->ws + o_bufA),
-                       reinterpret_cast<float*>(h->ws + o_bufB));
+                       reinterpret_cast<float*>(h->ws + o_bufB), prec_of(opt));
   }
   return finish(h, nl);
 }
@@ -774,7 +781,7 @@ rt_status rtucker_core(rt_handle h, const void* X, rt_dtype dtype, int d, const 
   const size_t oA = bump.take(cb * 4), oB = bump.take(cb * 4);
   if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
   const int nl = enqueue_core(h, X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + oA),
-                              reinterpret_cast<float*>(h->ws + oB));
+                              reinterpret_cast<float*>(h->ws + oB), prec_of(opt));
   return finish(h, nl);
 }
 
@@ -857,7 +864,7 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
   }
   for (int t = 0; t < T; ++t)
     nl += enqueue_core(h, X[t], dtype, d[t], n[t], r[t], U[t], G[t], reinterpret_cast<float*>(h->ws + oA[t]),
-                       reinterpret_cast<float*>(h->ws + oB[t]));
+                       reinterpret_cast<float*>(h->ws + oB[t]), prec_of(opt));
   return finish(h, nl);
 }
 
@@ -894,6 +901,7 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
   int64_t total = 0;
   if ((st = check_tensor(h, X, dtype, d, n, &total)) != RT_OK) return st;
   if ((st = check_opts(h, opt)) != RT_OK) return st;
+  if (prec_of(opt) != RT_PREC_FP32) return fail(h, RT_ENOTSUP, "the H-Tucker path computes in float32 only");
   if (!rank || !U_leaf || !B) return fail(h, RT_EINVAL, "rank, U_leaf and B are required");
   if ((st = check_prior_status(h)) != RT_OK) return st;
   if ((st = init_device_attrs(h)) != RT_OK) return st;

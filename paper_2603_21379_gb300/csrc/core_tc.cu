@@ -8,21 +8,29 @@
 // core step) fused in one read of X.  The remaining modes are contracted on
 // P afterwards (core_kernels.cu).
 //
-// Data path per CTA (persistent, one per SM, warp-specialised):
-//   warp 0      TMA producer: 128-row x 32-column float32 boxes of X (one slab,
-//               one K-chunk of 32 columns; 128-byte swizzle) into a ring of
-//               shared-memory stages.
-//   warp 1      TMEM allocator and MMA issuer: per K-chunk, 4 x
-//               tcgen05.mma.kind::tf32 (M = 128, K = 8, N = 2 r2p) with B =
-//               [hi(U_2) | lo(U_2)] (U_2 split into two TF32 terms so the
-//               factor keeps float32 accuracy) resident in shared memory.
-//   warps 2-5   converters: each thread takes one row of the stage, rounds it
-//               to TF32 (round to nearest) and writes it to a TMEM A buffer
-//               (tcgen05.st); the MMA reads A from TMEM.
-//   warps 6-9   epilogue: D (128 x 2 r2p, TMEM) -> registers, T = D_hi + D_lo,
-//               T to shared memory, then P_s = U_1^T T by register-blocked FFMA,
-//               written to global memory.
-// Every mbarrier wait is bounded; on expiry the CTA records RT timeout in the
+// Arithmetic: every operand is split into bf16 terms, x = hi(x) + lo(x), and
+// the MMAs (kind::f16, float32 accumulate) form the products of all terms, so
+// the result carries float32-level accuracy (about 2^-16 relative per
+// product).  X modes: 0 = float32 X split into hi + lo (default); 1 = bfloat16
+// X as stored (one term); 2 = float32 X rounded to one bf16 term (the BF16
+// compute form).  U_1, U_2 and the intermediate T are always split in two.
+//
+// Data path per CTA (persistent, one per SM, warp-specialised, 14 warps):
+//   warp 0      TMA producer: 128-byte-wide boxes (32 float32 or 64 bf16
+//               columns) of one slab into a ring of NS3 shared-memory stages,
+//               128-byte swizzle.
+//   warp 1      TMEM allocator and MMA issuer.  MMA1 per K step:
+//               D1 (n1 x 2 r2p) += X_s [hi(U_2) | lo(U_2)], A = X terms from
+//               TMEM (float32 X) or from the stage (bf16 X).  MMA2 per batch
+//               of 128 / r2p slabs: D2 (128 x 2 r1p) = T^T [hi(U_1) | lo(U_1)]
+//               with T^T terms in shared memory.
+//   warps 2-9   converters (float32 X): two groups of four quadrant warps take
+//               alternate stages; each thread splits one row into bf16 terms
+//               and stores them to a TMEM A buffer (tcgen05.st).
+//   warps 10-13 epilogue: T = D1_hi + D1_lo from TMEM, split into the two
+//               bf16 terms of T^T in shared memory; after MMA2, P_s = D2_hi +
+//               D2_lo to global memory.
+// Every mbarrier wait is bounded; on expiry the CTA records the timeout in the
 // status word, stops issuing work, drains and frees its TMEM, and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -141,6 +149,13 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
       "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
       : "memory");
 }
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
@@ -217,10 +232,11 @@ constexpr int NS3 = 6;                         // stages of X
 // always belong to the same group.
 static_assert(NS3 % 2 == 0 && NA % 2 == 0, "stages and A buffers must be even");
 
-template <int R1P, int R2P, bool XBF16>
+template <int R1P, int R2P, int XM>
 struct Layout {
   static constexpr int N1 = 2 * R2P;           // MMA1: X_s [hi(U2) | lo(U2)]
   static constexpr int N2 = 2 * R1P;           // MMA2: T^T [hi(U1) | lo(U1)]
+  static constexpr bool XBF16 = (XM == 1);      // X stored as bf16: MMA1 reads the stage
   static constexpr int KCX = XBF16 ? 64 : 32;  // X columns per stage (128 bytes)
   static constexpr int SPB = 128 / R2P;        // slabs per MMA2 batch (M = 128 rows of T^T)
   static constexpr int A_COL = 0;              // TMEM: NA A buffers of 32 columns (float32 X only)
@@ -233,9 +249,11 @@ struct Layout {
 
 // Dynamic shared memory (1024-aligned):
 //   A2[2 terms][2 chunks][128][64 bf16] | B1[nkb][N1][64 bf16] | B2[2][N2][64 bf16] | stages[NS3][16 KB] | bars
-template <int R1P, int R2P, bool XBF16>
+template <int R1P, int R2P, int XM>
 __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_constant__ CUtensorMap tmap, Core2Args args) {
-  using LY = Layout<R1P, R2P, XBF16>;
+  using LY = Layout<R1P, R2P, XM>;
+  constexpr bool XBF16 = LY::XBF16;
+  constexpr bool XLO = (XM == 0);                  // float32 X keeps its lo term
   constexpr int N1 = LY::N1, N2 = LY::N2, KCX = LY::KCX, SPB = LY::SPB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -377,7 +395,7 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
               const uint64_t bdesc = sw128_desc(saddr(B1 + (kg >> 2) * N1 * 128 + (kg & 3) * 32));
               const uint32_t a = tmem + LY::A_COL + ab * 32 + kk * 8;
               mma_bf16_ts(dcol, a, bdesc, idesc1, (kc | kk) ? 1u : 0u);   // hi(X)
-              mma_bf16_ts(dcol, a + 16, bdesc, idesc1, 1u);                // lo(X)
+              if (XLO) mma_bf16_ts(dcol, a + 16, bdesc, idesc1, 1u);       // lo(X)
             }
             mma_commit(&aempty[ab]);
           }
@@ -408,15 +426,21 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
         for (int j = 0; j < 8; ++j) {
           float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
           if (row < n1) f = *reinterpret_cast<const float4*>(rowp + ((j ^ (row & 7)) << 4));
-          split_bf16(f.x, f.y, v[2 * j], v[16 + 2 * j]);
-          split_bf16(f.z, f.w, v[2 * j + 1], v[16 + 2 * j + 1]);
+          if (XLO) {
+            split_bf16(f.x, f.y, v[2 * j], v[16 + 2 * j]);
+            split_bf16(f.z, f.w, v[2 * j + 1], v[16 + 2 * j + 1]);
+          } else {
+            v[2 * j] = pack_bf16(f.x, f.y);
+            v[2 * j + 1] = pack_bf16(f.z, f.w);
+          }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
         ok = __all_sync(0xffffffffu, mbar_wait(&aempty[ab], (uint32_t)(((c / NA) & 1) ^ 1), abort_flag, args.status));
         if (!ok) break;
         fence_after();
-        tmem_st32(tmem + ((uint32_t)(q * 32) << 16) + LY::A_COL + ab * 32, v);
+        if (XLO) tmem_st32(tmem + ((uint32_t)(q * 32) << 16) + LY::A_COL + ab * 32, v);
+        else tmem_st16(tmem + ((uint32_t)(q * 32) << 16) + LY::A_COL + ab * 32, v);
         tmem_wait_st();
         fence_before();
         __syncwarp();
@@ -519,20 +543,20 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-template <int R1P, int R2P, bool XBF16>
+template <int R1P, int R2P, int XM>
 static size_t smem_bytes(int nkb) {
-  using LY = Layout<R1P, R2P, XBF16>;
+  using LY = Layout<R1P, R2P, XM>;
   return 1024 + 2 * (size_t)LY::A2_TERM + (size_t)nkb * LY::N1 * 128 + 2 * (size_t)LY::N2 * 128 +
          (size_t)NS3 * STAGE_BYTES + 8 * (2 * NS3 + 2 * NA + 11) + 16;
 }
 
-template <int R1P, int R2P, bool XBF16>
+template <int R1P, int R2P, int XM>
 static int launch_v3(const CUtensorMap& map, const Core2Args& a, int grid, cudaStream_t st) {
   const int nkb = (a.n2 + 63) / 64;
-  const size_t sm = smem_bytes<R1P, R2P, XBF16>(nkb);
+  const size_t sm = smem_bytes<R1P, R2P, XM>(nkb);
   if (sm > 227 * 1024) return -1;
-  cudaFuncSetAttribute(k_core2_tc<R1P, R2P, XBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_core2_tc<R1P, R2P, XBF16><<<grid, NTHREADS_V2, sm, st>>>(map, a);
+  cudaFuncSetAttribute(k_core2_tc<R1P, R2P, XM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_core2_tc<R1P, R2P, XM><<<grid, NTHREADS_V2, sm, st>>>(map, a);
   return 1;
 }
 
@@ -540,10 +564,13 @@ static int launch_v3(const CUtensorMap& map, const Core2Args& a, int grid, cudaS
 
 // Returns the number of launches (1), or 0 when the shape is not supported
 // by the tensor-core path (the caller then uses the FFMA chain).
-// X is float32 (split into two bf16 terms on the fly) or bfloat16 (one term).
-int launch_core2_tc(int xbf16, const void* X, int64_t S, int n1, int n2, const float* U1, int r1, const float* U2,
+// xmode: 0 float32 X split into two bf16 terms, 1 bfloat16 X, 2 float32 X
+// rounded to one bf16 term.
+int launch_core2_tc(int xmode, const void* X, int64_t S, int n1, int n2, const float* U1, int r1, const float* U2,
                     int r2, float* P, int* status, cudaStream_t st) {
   using namespace tc;
+  if (xmode < 0 || xmode > 2) return 0;
+  const bool xbf16 = (xmode == 1);
   const int esz = xbf16 ? 2 : 4;
   if (n1 < 1 || n1 > ROWS || n2 < 1 || ((int64_t)n2 * esz) % 16 != 0 || r1 < 1 || r1 > 32 || r2 < 1 || r2 > 32)
     return 0;
@@ -568,10 +595,12 @@ int launch_core2_tc(int xbf16, const void* X, int64_t S, int n1, int n2, const f
   const int r1p = r1 <= 8 ? 8 : r1 <= 16 ? 16 : 32;
   const int r2p = r2 <= 8 ? 8 : r2 <= 16 ? 16 : 32;
   int rc = 0;
-#define RT_TC_CASE(A, B)                                                                   \
-  if (r1p == A && r2p == B) {                                                              \
-    rc = xbf16 ? launch_v3<A, B, true>(map, a, grid, st) : launch_v3<A, B, false>(map, a, grid, st); \
-    return rc < 0 ? 0 : rc;                                                                \
+#define RT_TC_CASE(A, B)                                                       \
+  if (r1p == A && r2p == B) {                                                  \
+    rc = xmode == 1   ? launch_v3<A, B, 1>(map, a, grid, st)                   \
+         : xmode == 2 ? launch_v3<A, B, 2>(map, a, grid, st)                   \
+                      : launch_v3<A, B, 0>(map, a, grid, st);                  \
+    return rc < 0 ? 0 : rc;                                                    \
   }
   RT_TC_CASE(8, 8) RT_TC_CASE(8, 16) RT_TC_CASE(8, 32)
   RT_TC_CASE(16, 8) RT_TC_CASE(16, 16) RT_TC_CASE(16, 32)

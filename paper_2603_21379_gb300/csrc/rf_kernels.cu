@@ -78,17 +78,24 @@ __global__ void __launch_bounds__(256) k_gather_sketch(const RFProb* __restrict_
   if (tid < SK_TJ) offs[tid] = (j0 + tid < q.s) ? q.off[j0 + tid] : (int64_t)-1;
   __syncthreads();
   const int64_t nS = q.nS, rs = q.rowstride;
-#pragma unroll 8
-  for (int e = tid; e < SK_TI * SK_TJ; e += 256) {
-    const int jj = e / SK_TI, ii = e % SK_TI;
-    const int64_t i = i0 + ii;
-    float v = 0.f;
+  // All loads of this thread are issued before any store, so the strided gathers (one
+  // DRAM sector each for all but the last mode) overlap instead of waiting on one another.
+  constexpr int PER = SK_TI * SK_TJ / 256;
+  static_assert(SK_TI * SK_TJ % 256 == 0 && 256 % SK_TI == 0, "gather tiling");
+  const int ii = tid % SK_TI;
+  const int64_t i = i0 + ii;
+  float v[PER];
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int jj = tid / SK_TI + t * (256 / SK_TI);
     const int64_t o = offs[jj];
-    if (i < nS && o >= 0) {
-      v = load_x(q.X, q.dtype, o + i * rs);
-      q.Yt[(j0 + jj) * nS + i] = v;
-    }
-    Ys[jj * SK_TI + ii] = v;
+    v[t] = (i < nS && o >= 0) ? load_x(q.X, q.dtype, o + i * rs) : 0.f;
+  }
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int jj = tid / SK_TI + t * (256 / SK_TI);
+    if (i < nS && offs[jj] >= 0) q.Yt[(j0 + jj) * nS + i] = v[t];
+    Ys[jj * SK_TI + ii] = v[t];
   }
   for (int e = tid; e < SK_TJ * cp; e += 256) {
     const int jj = e / cp, cc = e % cp;

@@ -52,7 +52,7 @@ cudaError_t core_init_attributes();
 // Fused pass over X on tensor cores: P[s] = U1^T X[s] U2 for S slabs of
 // n1 x n2.  X float32 (xbf16 = 0: two bf16 terms) or bfloat16 (xbf16 = 1).
 // Returns 0 when the shape is unsupported.
-int launch_core2_tc(int xbf16, const void* X, int64_t S, int n1, int n2, const float* U1, int r1, const float* U2,
+int launch_core2_tc(int xmode, const void* X, int64_t S, int n1, int n2, const float* U1, int r1, const float* U2,
                     int r2, float* P, int* status, cudaStream_t st);
 
 // ---- H-Tucker (ht_kernels.cu)

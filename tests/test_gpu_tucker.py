@@ -144,6 +144,44 @@ def test_bf16_storage(rt):
     assert abs(eg - er) <= RELERR_TOL
 
 
+def test_bf16_compute_form(rt):
+    # float32 X rounded to one bfloat16 term in the tensor-core pass (factors keep two
+    # terms): the factors are those of the float32 form (the range finder is float32)
+    # and the relative error still meets the float32 criterion against the oracle
+    X = synth.tucker_tensor((48, 40, 64, 32), (6, 5, 8, 8), noise=1e-3, data_seed=13)
+    Xd = torch.from_numpy(X).cuda()
+    r, p, seed = [6, 5, 8, 8], 4, 21
+    G32, U32 = rt.rtucker_decompose(Xd, r, p, seed=seed)
+    G16, U16 = rt.rtucker_decompose(Xd, r, p, seed=seed, prec="bf16")
+    for a, b in zip(U32, U16):
+        assert torch.equal(a, b)
+    ref = tucker.sub_r_hosvd(X.astype(np.float64), r, p, seed=seed)
+    er = tucker.relerr(X.astype(np.float64), tucker.reconstruct(ref["G"], ref["U"]))
+    e16 = rt.rtucker_relerr(Xd, G16, U16)
+    assert abs(e16 - er) <= RELERR_TOL, (e16, er)
+    # the bf16 rounding of X is visible in G, at the level of its 2^-9 relative step
+    dg = (G16 - G32).abs().max().item() / G32.abs().max().item()
+    assert 0 < dg < 4e-3
+    Gc = rt.rtucker_core(Xd, U32, prec="bf16")
+    assert torch.equal(Gc, G16)
+
+
+def test_bf16_storage_tensor_core_pass(rt):
+    # bfloat16 X through the tensor-core pass (MMA1 reads X from the TMA stage) must
+    # give the core of its exact float32 copy (whose lo terms are then zero)
+    rs = np.random.default_rng(14)
+    shape, ranks = (6, 40, 96, 64), (4, 6, 12, 16)
+    Xb = torch.from_numpy(rs.standard_normal(shape).astype(np.float32)).to(torch.bfloat16).cuda()
+    U = [np.linalg.qr(rs.standard_normal((n, k)))[0].astype(np.float32) for n, k in zip(shape, ranks)]
+    Ud = [torch.from_numpy(u).cuda() for u in U]
+    Gb = rt.rtucker_core(Xb, Ud)
+    Gf = rt.rtucker_core(Xb.float(), Ud)
+    Gr = tucker.multi_ttm_t(Xb.float().cpu().numpy().astype(np.float64), [u.astype(np.float64) for u in U])
+    scale = np.abs(Gr).max()
+    assert np.abs(to_np(Gf) - Gr).max() <= 1e-5 * scale
+    assert np.abs(to_np(Gb) - Gr).max() <= 1e-5 * scale
+
+
 def test_core_entry_point_and_evaluator(rt):
     X = synth.tucker_tensor((30, 40, 50), (4, 4, 4), noise=1e-3, data_seed=12)
     Xd = torch.from_numpy(X).cuda()
@@ -232,3 +270,20 @@ def test_order4_128_full_size(rt):
     X = synth.named(cfg)
     G, U, ref, eg, er = _run_and_compare(rt, X, cfg["ranks"], cfg["p"], seed=cfg["seed"], check_core=False)
     assert 5e-4 < er < 5e-3
+    # BF16 compute form and bfloat16-stored X on the same tensor meet the same criterion
+    Xd = torch.from_numpy(X).cuda()
+    G16, U16 = rt.rtucker_decompose(Xd, cfg["ranks"], cfg["p"], seed=cfg["seed"], prec="bf16")
+    assert abs(rt.rtucker_relerr(Xd, G16, U16) - er) <= RELERR_TOL
+    del G16, U16
+    # bfloat16-stored X: the factors are fitted to the rounded data, which moves the
+    # error against the float32 X well beyond 1e-5 on this tensor (the rounding, 1.7e-3
+    # relative, is above the noise under the smallest kept directions); parity is with
+    # the oracle run on the same rounded tensor, both measured against the float32 X
+    Xb = Xd.to(torch.bfloat16)
+    Gb, Ub = rt.rtucker_decompose(Xb, cfg["ranks"], cfg["p"], seed=cfg["seed"])
+    eb = rt.rtucker_relerr(Xd, Gb, Ub)
+    Xbo = Xb.float().cpu().numpy().astype(np.float64)
+    refb = tucker.sub_r_hosvd(Xbo, cfg["ranks"], cfg["p"], seed=cfg["seed"])
+    del Xbo
+    ebr = tucker.relerr(np.asarray(X, dtype=np.float64), tucker.reconstruct(refb["G"], refb["U"]))
+    assert abs(eb - ebr) <= RELERR_TOL, (eb, ebr)
