@@ -96,7 +96,7 @@ def default_w(shape, nodes):
     return [0 if nd.id == 0 else min(20 * n, node_cols(shape, nd)) for nd in nodes]
 
 
-def sub_r_rtl_ht(X, rank, p, w=None, seed=0, tree=None):
+def sub_r_rtl_ht(X, rank, p, w=None, seed=0, tree=None, with_root=True):
     """[{U_k}, {B_S}] = Sub-R-RtL-HT(X, T, r, w, p) (Alg. 2).
 
     Every non-root node S (leaves included) gets U_S from the range finder on
@@ -105,8 +105,11 @@ def sub_r_rtl_ht(X, rank, p, w=None, seed=0, tree=None):
     the root transfer tensor is taken from vec X.  ``rank`` is one rank per
     node (the root's is 1) or a scalar.  Returns leaf factors, transfer tensors
     (indexed by node id; None for leaves), the node bases U_S and intermediates.
+    X keeps its stored precision here: the sampled columns and the root are
+    promoted to float64 where they are formed.  ``with_root=False`` leaves
+    B[0] = None (for callers that form the root from X themselves).
     """
-    X = np.asarray(X, dtype=np.float64)
+    X = np.asarray(X)
     shape = X.shape
     nodes = balanced_tree(X.ndim) if tree is None else tree
     ranks = default_ranks(nodes, rank) if np.ndim(rank) == 0 else [int(v) for v in rank]
@@ -131,7 +134,8 @@ def sub_r_rtl_ht(X, rank, p, w=None, seed=0, tree=None):
         if nd.is_leaf:
             continue
         if nd.id == 0:
-            B[0] = root_transfer(X, US[nd.left], US[nd.right])
+            if with_root:
+                B[0] = root_transfer(X, US[nd.left], US[nd.right])
         else:
             B[nd.id] = transfer_tensor(US[nd.id], US[nd.left], US[nd.right])
     leaves = sorted((nd for nd in nodes if nd.is_leaf), key=lambda nd: nd.a)

@@ -158,7 +158,7 @@ struct ProbSpec {
 
 struct ProbPlan {
   RFProb q;
-  size_t o_idx, o_off, o_Om, o_Yt, o_Zp, o_Q, o_Rb, o_Q2, o_Bp, o_Rc, o_W, o_sig, o_keys, o_U;
+  size_t o_idx, o_off, o_Om, o_Yt, o_Zp, o_zcnt, o_Q, o_Rb, o_Q2, o_Bp, o_Rc, o_W, o_sig, o_keys, o_U;
   int64_t units[STG_COUNT];
 };
 
@@ -219,6 +219,7 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   pp.o_Om = bump.take(s * c * 4);
   pp.o_Yt = bump.take((size_t)s * nS * 4);
   pp.o_Zp = bump.take((size_t)q.nzc * nS * c * 4);
+  pp.o_zcnt = bump.take((size_t)((nS + SK_TI - 1) / SK_TI) * 4);
   pp.o_Q = bump.take((size_t)nS * c * 4);
   pp.o_Rb = bump.take(q.nrb > 1 ? (size_t)q.nrb * c * c * 4 : 4);
   pp.o_Q2 = bump.take(q.nrb > 1 ? (size_t)q.nrb * c * c * 4 : 4);
@@ -254,6 +255,7 @@ void bind_problem(ProbPlan& pp, char* ws) {
   q.Om = reinterpret_cast<float*>(ws + pp.o_Om);
   q.Yt = reinterpret_cast<float*>(ws + pp.o_Yt);
   q.Zp = reinterpret_cast<float*>(ws + pp.o_Zp);
+  q.zcnt = reinterpret_cast<int32_t*>(ws + pp.o_zcnt);
   q.Q = reinterpret_cast<float*>(ws + pp.o_Q);
   q.Rb = reinterpret_cast<float*>(ws + pp.o_Rb);
   q.Q2 = reinterpret_cast<float*>(ws + pp.o_Q2);

@@ -56,6 +56,9 @@ __global__ void __launch_bounds__(256) k_omega(const RFProb* __restrict__ P,
   const int64_t j = e / q.c;
   const int c = (int)(e % q.c);
   q.Om[e] = gauss_entry((uint64_t)q.idx[j], (uint32_t)c, philox_key(q.seed), q.node);
+  // the sketch's per-row-tile counters start at zero (this kernel precedes it)
+  const int64_t nrt = (q.nS + SK_TI - 1) / SK_TI;
+  for (int64_t e2 = e; e2 < nrt; e2 += pre[p + 1] - pre[p]) q.zcnt[e2] = 0;
 }
 
 // ------------------------------------------------------------------ S2 + S4
@@ -133,9 +136,34 @@ __global__ void __launch_bounds__(256) k_gather_sketch(const RFProb* __restrict_
       }
     }
   }
+  if (q.nzc == 1) return;
+  // The last CTA of this row tile to finish sums the nzc partial sketches of the tile,
+  // in chunk order, into the chunk-0 slot (deterministic; no second pass over Zp).
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(q.zcnt + rtile, 1) == q.nzc - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int64_t zsz = nS * c;
+  const int rows = (int)min((int64_t)SK_TI, nS - i0);
+  for (int e = tid; e < rows * c; e += 256) {
+    const float* src = q.Zp + i0 * c + e;
+    float acc = 0.f;
+    for (int ch0 = 0; ch0 < q.nzc; ch0 += 16) {
+      float v[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) v[u] = (ch0 + u < q.nzc) ? __ldcg(src + (int64_t)(ch0 + u) * zsz) : 0.f;
+#pragma unroll
+      for (int u = 0; u < 16; ++u) acc += v[u];
+    }
+    q.Zp[i0 * c + e] = acc;
+  }
+  if (tid == 0) q.zcnt[rtile] = 0;
 }
 
-// Z = sum over sample chunks of the partial sketches (test/inspection path).
+// Z (reduced into the chunk-0 slot by the gather/sketch kernel) to the caller (test path).
 __global__ void k_sketch_sum(const RFProb* __restrict__ P, const int64_t* __restrict__ pre, int np,
                              float* const* __restrict__ Zout) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -143,10 +171,7 @@ __global__ void k_sketch_sum(const RFProb* __restrict__ P, const int64_t* __rest
   const int p = find_prob(pre, np, t);
   const RFProb& q = P[p];
   const int64_t e = t - pre[p];
-  const int64_t sz = q.nS * q.c;
-  float acc = 0.f;
-  for (int ch = 0; ch < q.nzc; ++ch) acc += q.Zp[ch * sz + e];
-  Zout[p][e] = acc;
+  Zout[p][e] = q.Zp[e];
 }
 
 // ------------------------------------------------------------------ Householder QR in smem
@@ -431,19 +456,6 @@ __device__ void qr_form_q(const float* A, float* Qm, int ld, int m, int c, const
 // Dynamic smem: A[ld*c] | Qm[ld*c] | tau[CMAX] | rdiag[CMAX] | vbuf[1024]
 constexpr int QR_THREADS = 512;
 constexpr int QR_JPW = CMAX / (QR_THREADS / 32);
-__device__ __forceinline__ float sum_partials(const float* __restrict__ base, int64_t stride, int n) {
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-  int ch = 0;
-  for (; ch + 4 <= n; ch += 4) {
-    a0 += __ldg(base + (int64_t)ch * stride);
-    a1 += __ldg(base + (int64_t)(ch + 1) * stride);
-    a2 += __ldg(base + (int64_t)(ch + 2) * stride);
-    a3 += __ldg(base + (int64_t)(ch + 3) * stride);
-  }
-  for (; ch < n; ++ch) a0 += __ldg(base + (int64_t)ch * stride);
-  return (a0 + a1) + (a2 + a3);
-}
-
 __global__ void __launch_bounds__(QR_THREADS) k_qr1(const RFProb* __restrict__ P,
                                                     const int64_t* __restrict__ pre, int np) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -459,11 +471,10 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr1(const RFProb* __restrict__ P
   float* tau = Qm + (size_t)ld * c;
   float* rdiag = tau + CMAX;
   float* vbuf = rdiag + CMAX;
-  const int64_t zsz = q.nS * c;
 #pragma unroll 2
   for (int e = threadIdx.x; e < m * c; e += QR_THREADS) {
     const int i = e / c, j = e % c;
-    A[(size_t)j * ld + i] = sum_partials(q.Zp + (row0 + i) * c + j, zsz, q.nzc);
+    A[(size_t)j * ld + i] = q.Zp[(row0 + i) * c + j];
   }
   __syncthreads();
   qr_factor<QR_JPW>(A, ld, m, c, tau, rdiag, vbuf);

@@ -46,7 +46,9 @@ struct RFProb {
   int64_t* off;            // [s]      element offset in X of column pi(j)
   float* Om;               // [s][c]   Gaussian test matrix rows
   float* Yt;               // [s][nS]  sampled columns (fiber j contiguous)
-  float* Zp;               // [nzc][nS][c] partial sketches per sample chunk
+  float* Zp;               // [nzc][nS][c] partial sketches per sample chunk; chunk 0
+                           // holds Z itself once the gather/sketch kernel is done
+  int32_t* zcnt;           // [nrt] finished-chunk counters per row tile of the sketch
   int32_t nzc;             // number of sample chunks of the sketch
   int32_t nrb;             // row blocks of the TSQR of Z (1 = single block)
   int32_t rbrows;          // rows per TSQR row block

@@ -9,8 +9,9 @@
 namespace rt {
 
 // Tile sizes of the range-finder stages (shared by planner and kernels).
-constexpr int SK_TI = 128;         // rows per gather/sketch tile
-constexpr int SK_TJ = 64;          // samples per sketch chunk
+constexpr int SK_TI = 32;          // rows per gather/sketch tile (small: spreads the
+                                   // scattered fiber loads over many SMs)
+constexpr int SK_TJ = 128;         // samples per sketch chunk
 constexpr int CMAX = 64;           // largest r + p supported
 constexpr int QR_MAXF = 12288;     // floats per smem array in the block QR
 constexpr int QR2_MAXF = 24576;    // floats per smem array in the TSQR second level

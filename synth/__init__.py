@@ -15,6 +15,10 @@ and the function f(x) = 1/||x|| on a uniform grid, Sec. 4.2.1):
 * ``inv_norm_tensor``    X(i) = 1 / sqrt(sum_j x_{i_j}^2), x_i = lo + i (hi-lo)/(n-1),
                          evaluated in float64 with plain IEEE +, *, /, sqrt in a
                          fixed order, then rounded to float32 (bit-reproducible).
+* ``inv_norm_tensor_torch``  the same tensor built with torch (float64 elementwise
+                         ops, one kernel per operation, so no fused multiply-add),
+                         slab by slab over the first mode, on any device: the
+                         way to make the 16^8 (17 GB) tensor without a host copy.
 * ``batched_shapes``     sizes/ranks of the batched workload (n_k ~ U{32..160},
                          r_k ~ U{4..min(24, n_k // 4)}).
 """
@@ -99,6 +103,27 @@ def inv_norm_tensor(n, d, lo=1.0, hi=2.0):
     """Full n^d tensor of f(x) = 1/||x|| on the grid (host; small d or n only)."""
     grids = np.meshgrid(*[np.arange(n)] * d, indexing="ij", sparse=True)
     return np.ascontiguousarray(inv_norm_entries(tuple(grids), n, lo, hi))
+
+
+def inv_norm_tensor_torch(n, d, lo=1.0, hi=2.0, device="cpu"):
+    """``inv_norm_tensor(n, d, lo, hi)`` as a contiguous torch float32 tensor on
+    ``device``, bit-identical to the numpy version: the same float64 grid, the
+    sum of squares accumulated mode 0 first with separate multiply and add
+    kernels, then sqrt and 1/(.) in float64 (IEEE-rounded), then one rounding
+    to float32.  Built one slab of the first mode at a time."""
+    import torch
+    x = torch.from_numpy(inv_norm_grid(n, lo, hi)).to(device)
+    sq = x * x                                      # x_i^2, float64, rounded once
+    out = torch.empty((n,) * d, dtype=torch.float32, device=device)
+    rest = (n,) * (d - 1)
+    for i0 in range(n):
+        acc = sq[i0].expand(rest).clone()           # mode 0 term first
+        for j in range(1, d):
+            shape = [1] * (d - 1)
+            shape[j - 1] = n
+            acc = acc + sq.view(shape)              # modes 1..d-1 in order
+        out[i0] = (1.0 / torch.sqrt(acc)).to(torch.float32)
+    return out
 
 
 def batched_shapes(T=256, nmin=32, nmax=160, rmin=4, rmax=24, data_seed=102):

@@ -37,12 +37,10 @@ def _strict_cols(sigma, r):
     return out
 
 
-def _compare_ht(rt, X, rank, p, w=None, seed=0, x_oracle=None):
-    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
-    U_leaf, B, Un = rt.rhtucker_decompose(Xd, rank, p, w=w, seed=seed, return_nodes=True)
-    torch.cuda.synchronize()
-    Xo = np.asarray(X if x_oracle is None else x_oracle, dtype=np.float64)
-    ref = htucker.sub_r_rtl_ht(Xo, rank, p, w=w, seed=seed)
+def _check_nodes(ref, U_leaf, B, Un, root_ref=None):
+    """Node bases, leaf factors and transfer tensors of a GPU result against an
+    oracle result ``ref``; the root transfer tensor against ``root_ref`` (default
+    ref["B"][0])."""
     tree = ref["tree"]
     signs, strict = {}, {}
     for nd in tree[1:]:
@@ -59,7 +57,7 @@ def _compare_ht(rt, X, rank, p, w=None, seed=0, x_oracle=None):
         if nd.is_leaf:
             continue
         Bg = to_np(B[nd.id])
-        Br = ref["B"][nd.id]
+        Br = (ref["B"][0] if root_ref is None else root_ref) if nd.id == 0 else ref["B"][nd.id]
         si = np.ones(1) if nd.id == 0 else signs[nd.id]
         Bg = Bg * si[:, None, None] * signs[nd.left][None, :, None] * signs[nd.right][None, None, :]
         ii = [0] if nd.id == 0 else strict[nd.id]
@@ -68,8 +66,17 @@ def _compare_ht(rt, X, rank, p, w=None, seed=0, x_oracle=None):
             sub_g = Bg[np.ix_(ii, jj, kk)]
             sub_r = Br[np.ix_(ii, jj, kk)]
             assert np.abs(sub_g - sub_r).max() <= 1e-4 * max(1.0, np.abs(Br).max()), nd.id
+
+
+def _compare_ht(rt, X, rank, p, w=None, seed=0, x_oracle=None):
+    Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+    U_leaf, B, Un = rt.rhtucker_decompose(Xd, rank, p, w=w, seed=seed, return_nodes=True)
+    torch.cuda.synchronize()
+    Xo = np.asarray(X if x_oracle is None else x_oracle, dtype=np.float64)
+    ref = htucker.sub_r_rtl_ht(Xo, rank, p, w=w, seed=seed)
+    _check_nodes(ref, U_leaf, B, Un)
     eg = rt.rhtucker_relerr(Xd, U_leaf, B, rank)
-    er = tucker.relerr(Xo, htucker.reconstruct(ref["U"], ref["B"], tree, Xo.shape))
+    er = tucker.relerr(Xo, htucker.reconstruct(ref["U"], ref["B"], ref["tree"], Xo.shape))
     assert abs(eg - er) <= RELERR_TOL, (eg, er)
     return eg, er
 
@@ -120,3 +127,29 @@ def test_tall_node_tsqr_path(rt):
     # node {0,1,2} of a 16^6 tensor has 4096 rows: two-level TSQR of Z
     X = synth.inv_norm_tensor(16, 6)
     _compare_ht(rt, X, 6, 3, seed=2)
+
+
+def test_inv_norm_16_8_full_size(rt):
+    # the paper's H-Tucker workload at full size: f = 1/||x|| on a 16^8 grid (17.2 GB
+    # float32), balanced tree, rank 10 at every node, p = 5, w = 320 columns per node.
+    # All 14 node bases and 6 transfer tensors are compared with the oracle (which
+    # needs only the sampled columns); the root, B_R = U_l^T X^(R_l) U_r, with the
+    # oracle's root transfer summed over row blocks of X^(R_l).
+    cfg = synth.INVNORM_16_8
+    n, d = cfg["n"], cfg["d"]
+    Xd = synth.inv_norm_tensor_torch(n, d, cfg["lo"], cfg["hi"], device="cuda")
+    rs = np.random.default_rng(0)
+    idx = tuple(rs.integers(0, n, size=2000) for _ in range(d))
+    assert np.array_equal(Xd[idx].cpu().numpy(), synth.inv_norm_entries(idx, n, cfg["lo"], cfg["hi"]))
+    U_leaf, B, Un = rt.rhtucker_decompose(Xd, cfg["rank"], cfg["p"], w=cfg["w"], seed=cfg["seed"],
+                                          return_nodes=True)
+    torch.cuda.synchronize()
+    Xh = Xd.cpu().numpy()
+    del Xd
+    ref = htucker.sub_r_rtl_ht(Xh, cfg["rank"], cfg["p"], w=cfg["w"], seed=cfg["seed"], with_root=False)
+    root = ref["tree"][0]
+    Ul, Ur = ref["US"][root.left], ref["US"][root.right]
+    Xm = Xh.reshape(Ul.shape[0], Ur.shape[0])
+    blk = 4096
+    BR = sum(htucker.root_transfer(Xm[a:a + blk], Ul[a:a + blk], Ur) for a in range(0, Xm.shape[0], blk))
+    _check_nodes(ref, U_leaf, B, Un, root_ref=BR)

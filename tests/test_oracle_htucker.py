@@ -8,6 +8,7 @@ import itertools
 import os
 
 import numpy as np
+import pytest
 
 import synth
 from oracle import brute, htucker, tucker
@@ -129,6 +130,38 @@ def test_inv_norm_generator_matches_definition():
     rs = np.random.default_rng(0)
     idx = tuple(rs.integers(0, n, size=50) for _ in range(d))
     assert np.array_equal(synth.inv_norm_entries(idx, n), X[idx])
+
+
+def test_inv_norm_torch_generator_is_bit_identical():
+    # the torch generator (used for the 17 GB 16^8 tensor on the device) makes the
+    # same bytes as the numpy definition above
+    torch = pytest.importorskip("torch")
+    for n, d in [(5, 4), (16, 3), (3, 7)]:
+        a = synth.inv_norm_tensor(n, d)
+        b = synth.inv_norm_tensor_torch(n, d)
+        assert b.dtype == torch.float32 and tuple(b.shape) == (n,) * d
+        assert np.array_equal(a, b.numpy())
+
+
+def test_root_transfer_is_linear_in_row_blocks():
+    # the full-size H-Tucker test forms B_R from row blocks of X^(R_l); the sum of
+    # the blocks' root transfers is the root transfer of the whole matrix
+    rs = np.random.default_rng(4)
+    X = rs.standard_normal((12, 10))
+    Ul, Ur = rs.standard_normal((12, 3)), rs.standard_normal((10, 2))
+    whole = htucker.root_transfer(X, Ul, Ur)
+    parts = sum(htucker.root_transfer(X[a:a + 5], Ul[a:a + 5], Ur) for a in range(0, 12, 5))
+    assert np.allclose(whole, parts, rtol=1e-14, atol=1e-14)
+    assert whole.shape == (1, 3, 2)
+
+
+def test_sub_r_rtl_ht_without_root_matches():
+    X = synth.inv_norm_tensor(5, 4)
+    a = htucker.sub_r_rtl_ht(X, 2, 1, seed=3)
+    b = htucker.sub_r_rtl_ht(X, 2, 1, seed=3, with_root=False)
+    assert b["B"][0] is None
+    for nd in a["tree"][1:]:
+        assert np.array_equal(a["US"][nd.id], b["US"][nd.id])
 
 
 def test_inv_norm_workload_ht_runs_and_is_accurate():
