@@ -8,6 +8,12 @@ flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+After the timed region, rank 0 also measures (CUDA events; extra keys of the
+same JSON line, skipped with --no-extras): the BF16 compute form and bfloat16-
+stored X of the same workload ("forms"), 256 order-3 tensors in one batched call
+against a loop of plain calls ("batched"), and the H-Tucker decomposition of
+the 17.2 GB 16^8 tensor with its root-pass roofline ("ht").
+
 N > 1 runs under torchrun: each rank decomposes its own copy (independent
 problems, no data-path collective: weak scaling).  ``--impl reference`` times
 the float64 oracle on the host cores instead (a bounded sample of the same
@@ -171,6 +177,110 @@ def run_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------- other forms and workloads
+def _event_time(fn, steps, warmup):
+    """ms per call of ``fn`` on the current stream, CUDA events, after warm-up."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def measure_forms(rt, X, r, p, seed, relerr_fp32, steps):
+    """BF16 compute form and bfloat16-stored X on the 128^4 workload, against the
+    float32 plain form: time per decomposition and the error of the result
+    measured against the float32 X (the fixed-error bar is |delta relerr| <= 1e-5)."""
+    import torch
+    nbytes32 = X.numel() * 4
+    out = {}
+    ms = _event_time(lambda: rt.rtucker_decompose(X, r, p, seed=seed, prec="bf16"), steps, 3)
+    G, U = rt.rtucker_decompose(X, r, p, seed=seed, prec="bf16")
+    e = rt.rtucker_relerr(X, G, U)
+    out["bf16_compute"] = {"ms_per_decomp": ms, "input_gbs": nbytes32 / (ms * 1e-3) / 1e9, "relerr": e,
+                           "delta_relerr": e - relerr_fp32, "meets_fixed_relerr": abs(e - relerr_fp32) <= 1e-5}
+    Xb = X.to(torch.bfloat16)
+    ms = _event_time(lambda: rt.rtucker_decompose(Xb, r, p, seed=seed), steps, 3)
+    G, U = rt.rtucker_decompose(Xb, r, p, seed=seed)
+    e = rt.rtucker_relerr(X, G, U)
+    out["bf16_stored"] = {"ms_per_decomp": ms, "input_gbs": Xb.numel() * 2 / (ms * 1e-3) / 1e9,
+                          "relerr": e, "delta_relerr": e - relerr_fp32,
+                          "meets_fixed_relerr": abs(e - relerr_fp32) <= 1e-5}
+    del Xb
+    return out
+
+
+def measure_batched(rt, steps):
+    """256 order-3 float32 tensors (n_k ~ U{32..160}): one batched call against a
+    loop of plain calls; tensors/s, input GB/s and the largest relerr difference."""
+    import torch
+    import synth
+    cfg = synth.BATCHED_256
+    Xh, shapes, ranks = synth.batched_tensors(cfg["T"], cfg["nmin"], cfg["nmax"], cfg["rmin"], cfg["rmax"],
+                                              cfg["noise"], cfg["data_seed"])
+    Xs = [torch.from_numpy(x).cuda() for x in Xh]
+    nbytes = sum(x.nbytes for x in Xh)
+    seeds = [cfg["seed"] + t for t in range(cfg["T"])]
+    p = cfg["p"]
+    ms_b = _event_time(lambda: rt.rtucker_decompose_batched(Xs, ranks, p, seeds), steps, 2)
+
+    def plain():
+        for X, rk, sd in zip(Xs, ranks, seeds):
+            rt.rtucker_decompose(X, list(rk), p, seed=sd)
+    ms_p = _event_time(plain, max(1, steps // 2), 1)
+    res = rt.rtucker_decompose_batched(Xs, ranks, p, seeds)
+    dmax = 0.0
+    for t in range(0, cfg["T"], 16):
+        Gb, Ub = res[t]
+        Gp, Up = rt.rtucker_decompose(Xs[t], list(ranks[t]), p, seed=seeds[t])
+        dmax = max(dmax, abs(rt.rtucker_relerr(Xs[t], Gb, Ub) - rt.rtucker_relerr(Xs[t], Gp, Up)))
+    return {"workload": "256 order-3 float32 Tucker tensors, n_k ~ U{32..160}, r_k ~ U{4..min(24, n_k/4)}, "
+                        "p=5, Gaussian cores, Haar factors, 1e-6 noise, %.3f GB" % (nbytes / 1e9),
+            "ms_per_batch": ms_b, "tensors_per_s": cfg["T"] / (ms_b * 1e-3),
+            "input_gbs": nbytes / (ms_b * 1e-3) / 1e9,
+            "plain_loop_ms": ms_p, "plain_loop_tensors_per_s": cfg["T"] / (ms_p * 1e-3),
+            "max_delta_relerr_vs_plain": dmax}
+
+
+def measure_ht(rt, steps, peak):
+    """Sub-R-RtL-HT of f = 1/||x|| on the 16^8 grid (17.2 GB float32), rank 10,
+    p = 5, w = 320: time per decomposition, input GB/s, the root pass (one read of
+    X) against the HBM roofline, and the relative error of the format."""
+    import torch
+    import synth
+    cfg = synth.INVNORM_16_8
+    X = synth.inv_norm_tensor_torch(cfg["n"], cfg["d"], cfg["lo"], cfg["hi"], device="cuda")
+    nbytes = X.numel() * 4
+
+    def step():
+        return rt.rhtucker_decompose(X, cfg["rank"], cfg["p"], w=cfg["w"], seed=cfg["seed"])
+    step()
+    rt.set_timing(True)
+    rt.get_timing(reset=True)
+    ms = _event_time(step, steps, 1)
+    stg = rt.get_timing(reset=True)
+    rt.set_timing(False)
+    root_ms = stg["ht_root_pass"][0] / max(1, stg["ht_root_pass"][1])
+    U_leaf, B = step()
+    e = rt.rhtucker_relerr(X, U_leaf, B, cfg["rank"])
+    del X
+    torch.cuda.empty_cache()
+    return {"workload": "Sub-R-RtL-HT, f=1/||x|| on a 16^8 grid over [1,2]^8 (17.18 GB float32), balanced "
+                        "tree, rank 10, p=5, w=320 columns per node, seed 3",
+            "ms_per_decomp": ms, "input_gbs": nbytes / (ms * 1e-3) / 1e9, "relerr": e,
+            "stage_ms": {k: v[0] / max(1, v[1]) for k, v in stg.items() if v[1]},
+            "root_roofline": {"bound": "hbm", "kernel": "k_root (B_R = U_l^T X U_r, one read of X)",
+                              "achieved": nbytes / (root_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                              "frac": nbytes / (root_ms * 1e-3) / 1e9 / peak}}
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -256,6 +366,15 @@ def run_ours(args):
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         t_e2e = float(tt.item())
 
+    extra = {}
+    if rank == 0 and not args.no_extras:
+        peak0, _ = measured_peaks()
+        xs = min(args.steps, 20)
+        extra["forms"] = measure_forms(rt, X, r, p, seed, relerr, xs)
+        extra["batched"] = measure_batched(rt, max(2, min(args.steps, 5)))
+        del Xpin, Uh, Gh
+        extra["ht"] = measure_ht(rt, max(2, min(args.steps, 5)), peak0)
+
     if rank == 0:
         peak, peak_src = measured_peaks()
         x_ms, x_cnt = stages["core_x_pass"]
@@ -287,6 +406,7 @@ def run_ours(args):
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }
+        line.update(extra)
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -300,6 +420,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the BF16 forms, the batched and the H-Tucker workloads (untimed extras)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -959,7 +959,7 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
   const int64_t nl = range_prod(n, root.a, tree[root.left].b), nr = total / nl;
   const int rl = rk[root.left], rr = rk[root.right];
   if (rr > 12) return fail(h, RT_ENOTSUP, "rank of the root's right child above 12");
-  const size_t o_rootp = bump.take(root_scratch_floats(nl, nr, rl, rr) * 4);
+  const size_t o_rootp = bump.take(root_pass_scratch_floats(nl, nr, rl, rr) * 4);
   for (int i : internal) {
     const int64_t nlc = range_prod(n, tree[tree[i].left].a, tree[tree[i].left].b);
     if ((size_t)nlc * rk[tree[i].right] * 4 > 200 * 1024)
@@ -1010,7 +1010,7 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
   {
     StageTimer tm(h, 4);
     nlaunch += launch_root(X, (int)dtype, nl, nr, Uof(root.left), rl, Uof(root.right), rr, B + o_B[0],
-                           reinterpret_cast<float*>(h->ws + o_rootp), h->stream);
+                           reinterpret_cast<float*>(h->ws + o_rootp), h->d_status, h->stream);
   }
   return finish(h, nlaunch);
 }

@@ -11,6 +11,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "rt_common.cuh"
 #include "rt_host.h"
 
@@ -191,15 +193,32 @@ static void root_dispatch(const T* X, int64_t nl, int64_t nr, const float* Ul, i
   }
 }
 
-int launch_root(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl,
-                const float* Ur, int rr, float* BR, float* scratch, cudaStream_t st) {
+void launch_root_reduce(const float* part, int64_t nblk, int rl, int rr, float* BR, cudaStream_t st) {
+  k_root_reduce<<<(unsigned)(rl * rr), 256, 0, st>>>(part, nblk, rl, rr, BR);
+}
+
+int launch_root_tiled(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl,
+                      const float* Ur, int rr, float* BR, float* scratch, cudaStream_t st) {
   const int64_t gx = (nr + RT_CB - 1) / RT_CB, gy = (nl + RT_RA - 1) / RT_RA;
   dim3 grid((unsigned)gx, (unsigned)gy);
   if (dtype == DT_F32) root_dispatch(static_cast<const float*>(X), nl, nr, Ul, rl, Ur, rr, scratch, grid, st);
   else if (dtype == DT_F64) root_dispatch(static_cast<const double*>(X), nl, nr, Ul, rl, Ur, rr, scratch, grid, st);
   else root_dispatch(static_cast<const __nv_bfloat16*>(X), nl, nr, Ul, rl, Ur, rr, scratch, grid, st);
-  k_root_reduce<<<(unsigned)(rl * rr), 256, 0, st>>>(scratch, gx * gy, rl, rr, BR);
+  launch_root_reduce(scratch, gx * gy, rl, rr, BR, st);
   return 2;
+}
+
+size_t root_pass_scratch_floats(int64_t nl, int64_t nr, int rl, int rr) {
+  return std::max(root_scratch_floats(nl, nr, rl, rr), root_stream_scratch_floats(nl, rl, rr));
+}
+
+int launch_root(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur, int rr,
+                float* BR, float* scratch, int* status, cudaStream_t st) {
+  if (dtype == DT_F32) {
+    const int n = launch_root_stream(static_cast<const float*>(X), nl, nr, Ul, rl, Ur, rr, BR, scratch, status, st);
+    if (n > 0) return n;
+  }
+  return launch_root_tiled(X, dtype, nl, nr, Ul, rl, Ur, rr, BR, scratch, st);
 }
 
 }  // namespace rt

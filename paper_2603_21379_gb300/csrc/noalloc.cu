@@ -11,8 +11,10 @@
 //
 // rhtucker_root_transfer_noalloc computes the root transfer tensor of an
 // H-Tucker format, B_R(0, j, k) = sum_{a,b} X[a nr + b] U_l[a][j] U_r[b][k],
-// with the same two kernels rhtucker_decompose uses, but its scratch (one
-// partial r_l x r_r block per CTA) lives in the file-scope device array below
+// with the tiled root kernel (the one rhtucker_decompose uses for shapes the
+// streaming kernel does not take; it has no waits and so needs no status word),
+// but its scratch (one partial r_l x r_r block per CTA) lives in the file-scope
+// device array below
 // instead of a workspace.  The array has a fixed capacity; every GPU that
 // loads the library holds it until the process exits.
 #include <cuda_runtime.h>
@@ -73,7 +75,7 @@ extern "C" rt_status rhtucker_root_transfer_noalloc(const void* X, rt_dtype dtyp
   if (st != RT_OK) return st;
   // The partial blocks are all overwritten by the first kernel; nothing in the
   // scratch has to start at zero.
-  rt::launch_root(X, (int)dtype, nl, nr, Ul, rl, Ur, rr, BR, scratch, static_cast<cudaStream_t>(stream));
+  rt::launch_root_tiled(X, (int)dtype, nl, nr, Ul, rl, Ur, rr, BR, scratch, static_cast<cudaStream_t>(stream));
   if (cudaGetLastError() != cudaSuccess) return RT_ECUDA;
   return RT_OK;
 }

@@ -1,0 +1,244 @@
+// root_tma.cu - the root pass of Sub-R-RtL-HT (Alg. 2, root transfer tensor),
+//     B_R(0, j, k) = sum_{a, b} U_l(a, j) X(a, b) U_r(b, k),
+// X = X^(R_l) the n_l x n_r matricization of the whole tensor (row-major), as
+// one streaming read of X:
+//
+//   k_root_rows   T(a, k) = sum_b X(a, b) U_r(b, k) for every row a.
+//                 Persistent, two CTAs per SM.  In each CTA a producer warp
+//                 streams 64-row x 32-column boxes of X (TMA, 128-byte swizzle)
+//                 and the matching 32 x r_r rows of U_r (bulk copy) through a
+//                 ring of RS_NS shared-memory stages; four consumer warps own the
+//                 64 rows of the current block, each thread 4 rows x 4 columns of
+//                 every stage (so one read of its 4 x r_r slice of U_r serves 4
+//                 rows), accumulating in registers over 4 stages and adding those
+//                 sums with Kahan compensation; the eight column groups of a row
+//                 are combined with warp shuffles at the end of the block.
+//   k_root_left   per CTA of 256 rows: sum_a U_l(a, j) T(a, k) in float64.
+//   k_root_reduce (ht_kernels.cu): fixed-order float64 sum of the partials.
+//
+// The bytes that count are X's (17.2 GB for the 16^8 tensor): U_r (n_r r_r
+// floats) is re-read from L2 once per 64-row block, T and the partials are
+// n_l r_r and (n_l / 256) r_l r_r floats.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "rt_common.cuh"
+#include "rt_host.h"
+#include "tma_util.cuh"
+
+namespace rt {
+namespace {
+
+using namespace tma;
+
+constexpr int RS_ROWS = 64;                  // rows of X per work item
+constexpr int RS_COLS = 32;                  // columns per stage (128 bytes of float32)
+constexpr int RS_NS = 8;                     // stages in the ring (8 KB of X each)
+constexpr int RS_CONS = 4;                   // consumer warps
+constexpr int RS_THREADS = (RS_CONS + 1) * 32;
+constexpr int RS_CTAS_PER_SM = 2;
+constexpr int RS_XBYTES = RS_ROWS * RS_COLS * 4;
+constexpr int RS_UMAX = 12;                  // largest r_r
+constexpr int RS_UBYTES = RS_COLS * RS_UMAX * 4;
+
+constexpr int RS_KAHAN = 4;                  // stages summed in plain float32 between Kahan steps
+constexpr int RL_ROWS = 256;                 // rows per CTA of k_root_left
+
+constexpr size_t rs_smem() { return 1024 + (size_t)RS_NS * (RS_XBYTES + RS_UBYTES) + 8 * (2 * RS_NS) + 16; }
+
+template <int RR>
+__global__ void __launch_bounds__(RS_THREADS, RS_CTAS_PER_SM) k_root_rows(const __grid_constant__ CUtensorMap tmap,
+                                                             const float* __restrict__ Ur, int64_t nl, int64_t nr,
+                                                             float* __restrict__ T, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* xs = base;                                   // [RS_NS][64 rows][128 B], swizzled
+  float* us = reinterpret_cast<float*>(base + RS_NS * RS_XBYTES);  // [RS_NS][32][RR]
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + RS_NS * (RS_XBYTES + RS_UBYTES));
+  uint64_t* empty = full + RS_NS;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + RS_NS);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nitems = (nl + RS_ROWS - 1) / RS_ROWS;
+  const int64_t nst = nr / RS_COLS;                           // stages per item (nr % 32 == 0)
+  const uint32_t ubytes = (uint32_t)(RS_COLS * RR * 4);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < RS_NS; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], RS_CONS); }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == RS_CONS) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int64_t c = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+        for (int64_t s = 0; s < nst; ++s, ++c) {
+          const int slot = (int)(c % RS_NS);
+          if (!(ok = mbar_wait(&empty[slot], (uint32_t)(((c / RS_NS) & 1) ^ 1), abort_flag, status))) break;
+          mbar_arrive_tx(&full[slot], (uint32_t)RS_XBYTES + ubytes);
+          tma_load_2d(saddr(xs + slot * RS_XBYTES), &tmap, (int)(s * RS_COLS), (int)(it * RS_ROWS), &full[slot]);
+          bulk_load(saddr(us + slot * (RS_UBYTES / 4)), Ur + s * RS_COLS * RR, ubytes, &full[slot]);
+        }
+      }
+      // the CTA may exit only when no copy into its shared memory is in flight
+      for (int64_t q = c - 1; q >= 0 && q >= c - RS_NS; --q)
+        for (uint32_t w = 0; w < (1u << 22); ++w)
+          if (mbar_test(&full[q % RS_NS], (uint32_t)((q / RS_NS) & 1))) break;
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- consumers
+  // thread = (row group rs, column group g): rows rs + 16 h (h < 4), columns 4g..4g+3
+  constexpr int NCG = 8;                                        // column groups
+  constexpr int CPT = RS_COLS / NCG;                            // columns per thread
+  constexpr int RPT = RS_ROWS * NCG / (RS_CONS * 32);           // rows per thread
+  constexpr int RSTEP = RS_ROWS / RPT;
+  const int rs = threadIdx.x / NCG, g = threadIdx.x % NCG;
+  int64_t c = 0;
+  for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
+    float acc[RPT][RR], tot[RPT][RR], cmp[RPT][RR];
+#pragma unroll
+    for (int h = 0; h < RPT; ++h)
+#pragma unroll
+      for (int k = 0; k < RR; ++k) acc[h][k] = tot[h][k] = cmp[h][k] = 0.f;
+    bool ok = true;
+    for (int64_t s = 0; s < nst; ++s, ++c) {
+      const int slot = (int)(c % RS_NS);
+      if (!(ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], (uint32_t)((c / RS_NS) & 1), abort_flag, status))))
+        break;
+      float u[CPT * RR];
+      const float4* u4 = reinterpret_cast<const float4*>(us + slot * (RS_UBYTES / 4) + CPT * g * RR);
+#pragma unroll
+      for (int v = 0; v < CPT * RR / 4; ++v) {
+        const float4 w = u4[v];
+        u[4 * v] = w.x; u[4 * v + 1] = w.y; u[4 * v + 2] = w.z; u[4 * v + 3] = w.w;
+      }
+#pragma unroll
+      for (int h = 0; h < RPT; ++h) {
+        const int row = rs + RSTEP * h;
+        const unsigned char* rp = xs + slot * RS_XBYTES + row * 128;
+        float x[CPT];
+#pragma unroll
+        for (int q = 0; q < CPT / 4; ++q) {
+          const float4 xv = *reinterpret_cast<const float4*>(rp + ((((CPT / 4) * g + q) ^ (row & 7)) << 4));
+          x[4 * q] = xv.x; x[4 * q + 1] = xv.y; x[4 * q + 2] = xv.z; x[4 * q + 3] = xv.w;
+        }
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc)
+#pragma unroll
+          for (int k = 0; k < RR; ++k) acc[h][k] = fmaf(x[cc], u[cc * RR + k], acc[h][k]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);
+      if ((s % RS_KAHAN) == RS_KAHAN - 1 || s == nst - 1) {
+#pragma unroll
+        for (int h = 0; h < RPT; ++h)
+#pragma unroll
+          for (int k = 0; k < RR; ++k) {
+            const float y = acc[h][k] - cmp[h][k];
+            const float t = tot[h][k] + y;
+            cmp[h][k] = (t - tot[h][k]) - y;
+            tot[h][k] = t;
+            acc[h][k] = 0.f;
+          }
+      }
+    }
+    if (!ok) break;
+    // T(a, k): sum over the column groups (consecutive lanes)
+#pragma unroll
+    for (int h = 0; h < RPT; ++h) {
+      const int64_t a = it * RS_ROWS + rs + RSTEP * h;
+#pragma unroll
+      for (int k = 0; k < RR; ++k) {
+        float v = tot[h][k] - cmp[h][k];
+#pragma unroll
+        for (int o = 1; o < NCG; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (g == 0 && a < nl) T[a * RR + k] = v;
+      }
+    }
+  }
+}
+
+// part[blk](j, k) = sum over the CTA's rows a of U_l(a, j) T(a, k), float64.
+__global__ void __launch_bounds__(RL_ROWS) k_root_left(const float* __restrict__ Ul, int rl,
+                                                       const float* __restrict__ T, int rr, int64_t nl,
+                                                       float* __restrict__ part) {
+  __shared__ float ul[RL_ROWS * RS_UMAX], ts[RL_ROWS * RS_UMAX];
+  const int64_t a0 = (int64_t)blockIdx.x * RL_ROWS;
+  const int rows = (int)min((int64_t)RL_ROWS, nl - a0);
+  for (int e = threadIdx.x; e < rows * rl; e += blockDim.x) ul[e] = Ul[a0 * rl + e];
+  for (int e = threadIdx.x; e < rows * rr; e += blockDim.x) ts[e] = T[a0 * rr + e];
+  __syncthreads();
+  const int p = threadIdx.x;
+  if (p < rl * rr) {
+    const int j = p / rr, k = p % rr;
+    double acc = 0.0;
+    for (int a = 0; a < rows; ++a) acc += (double)ul[a * rl + j] * (double)ts[a * rr + k];
+    part[(size_t)blockIdx.x * rl * rr + p] = (float)acc;
+  }
+}
+
+template <int RR>
+int launch_rows(const CUtensorMap& map, const float* Ur, int64_t nl, int64_t nr, float* T, int* status,
+                cudaStream_t st) {
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t nitems = (nl + RS_ROWS - 1) / RS_ROWS;
+  const int grid = (int)std::min<int64_t>(nitems, (int64_t)nsm * RS_CTAS_PER_SM);
+  cudaFuncSetAttribute(k_root_rows<RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem());
+  k_root_rows<RR><<<grid, RS_THREADS, rs_smem(), st>>>(map, Ur, nl, nr, T, status);
+  return 1;
+}
+
+}  // namespace
+
+size_t root_stream_scratch_floats(int64_t nl, int rl, int rr) {
+  return (size_t)nl * rr + (size_t)((nl + RL_ROWS - 1) / RL_ROWS) * rl * rr;
+}
+
+// Streaming root pass for float32 X with n_r % 32 == 0, 16-byte aligned X and U_r
+// and r_l, r_r <= 12.  Returns the number of launches, or 0 when the shape does not
+// qualify (the caller then uses the tiled kernel).  `scratch` holds
+// root_stream_scratch_floats() floats; `reduce` launches the final float64 sum.
+int launch_root_stream(const float* X, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur, int rr,
+                       float* BR, float* scratch, int* status, cudaStream_t st) {
+  if (nr % RS_COLS != 0 || rr < 1 || rr > RS_UMAX || rl < 1 || rl > RS_UMAX) return 0;
+  if (nl < 1 || nl >= ((int64_t)1 << 31) || nr >= ((int64_t)1 << 31)) return 0;
+  if ((reinterpret_cast<uintptr_t>(X) & 15u) || (reinterpret_cast<uintptr_t>(Ur) & 15u)) return 0;
+  EncodeTiledFn enc = encode_tiled_fn();
+  if (!enc) return 0;
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {(cuuint64_t)nr, (cuuint64_t)nl};
+  const cuuint64_t gstride[1] = {(cuuint64_t)nr * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)RS_COLS, (cuuint32_t)RS_ROWS};
+  const cuuint32_t estride[2] = {1, 1};
+  if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(X), gdim, gstride, box, estride,
+          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return 0;
+  float* T = scratch;
+  float* part = scratch + (size_t)nl * rr;
+  int n = 0;
+  switch (rr) {
+#define RS_CASE(K) \
+  case K: n = launch_rows<K>(map, Ur, nl, nr, T, status, st); break;
+    RS_CASE(1) RS_CASE(2) RS_CASE(3) RS_CASE(4) RS_CASE(5) RS_CASE(6)
+    RS_CASE(7) RS_CASE(8) RS_CASE(9) RS_CASE(10) RS_CASE(11) RS_CASE(12)
+#undef RS_CASE
+    default: return 0;
+  }
+  const int64_t nblk = (nl + RL_ROWS - 1) / RL_ROWS;
+  k_root_left<<<(unsigned)nblk, RL_ROWS, 0, st>>>(Ul, rl, T, rr, nl, part);
+  launch_root_reduce(part, nblk, rl, rr, BR, st);
+  return n + 2;
+}
+
+}  // namespace rt

@@ -64,8 +64,18 @@ struct TransferJob {     // B_S(i, j, k) = sum_{a,b} U_S[a n_r + b][i] U_l[a][j]
 int launch_transfer(const TransferJob* jobs_dev, const TransferJob* jobs_host, int njobs,
                     cudaStream_t st);
 // B_R(0, j, k) = sum_{a,b} X[a nr + b] Ul[a][j] Ur[b][k]
-int launch_root(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl,
-                const float* Ur, int rr, float* BR, float* scratch, cudaStream_t st);
+// Root pass B_R = U_l^T X^(R_l) U_r: the streaming (TMA) kernel for float32 X when the
+// shape allows, else the tiled kernel; scratch holds root_pass_scratch_floats().
+int launch_root(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur, int rr,
+                float* BR, float* scratch, int* status, cudaStream_t st);
+// The tiled kernel alone (no waits, no status word); scratch of root_scratch_floats().
+int launch_root_tiled(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl,
+                      const float* Ur, int rr, float* BR, float* scratch, cudaStream_t st);
+int launch_root_stream(const float* X, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur, int rr,
+                       float* BR, float* scratch, int* status, cudaStream_t st);
+void launch_root_reduce(const float* part, int64_t nblk, int rl, int rr, float* BR, cudaStream_t st);
+size_t root_stream_scratch_floats(int64_t nl, int rl, int rr);
+size_t root_pass_scratch_floats(int64_t nl, int64_t nr, int rl, int rr);
 size_t root_scratch_floats(int64_t nl, int64_t nr, int rl, int rr);
 
 // ---- evaluators (eval_kernels.cu), float64

@@ -92,6 +92,21 @@ def test_inv_norm_d8_n6(rt):
     _compare_ht(rt, X, 4, 2, seed=1)
 
 
+def test_root_stream_ragged_rows(rt):
+    # root of a (5, 7, 8, 8) tensor: X^(R_l) is 35 x 64, so the streaming root pass
+    # runs one partial 64-row block over two 32-column stages
+    rs = np.random.default_rng(8)
+    X = rs.standard_normal((5, 7, 8, 8)).astype(np.float32)
+    _compare_ht(rt, X, 3, 2, seed=4)
+
+
+def test_root_stream_wide(rt):
+    # 12 x 10 x 16 x 40: X^(R_l) is 120 x 640 (two row blocks, 20 column stages), ranks 7
+    rs = np.random.default_rng(9)
+    X = rs.standard_normal((12, 10, 16, 40)).astype(np.float32)
+    _compare_ht(rt, X, 7, 3, seed=6)
+
+
 def test_exact_hierarchical_rank_recovery(rt):
     rs = np.random.default_rng(3)
     shape = (5, 6, 4, 5, 6)
