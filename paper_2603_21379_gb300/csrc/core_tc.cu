@@ -423,12 +423,15 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
       // T^T rows (j, b), column i: hi and lo terms (rows i >= n1 stay zero)
       if (i < n1) {
 #pragma unroll
-        for (int b = 0; b < R2P; ++b) {
-          unsigned short hi, lo;
-          split1_bf16(__uint_as_float(d[b]) + __uint_as_float(d[R2P + b]), hi, lo);
-          const int off = sw_off16(j * R2P + b, i, 128);
-          *reinterpret_cast<unsigned short*>(A2 + off) = hi;
-          *reinterpret_cast<unsigned short*>(A2 + LY::A2_TERM + off) = lo;
+        for (int b = 0; b < R2P; b += 2) {
+          uint32_t hi, lo;
+          split_bf16(__uint_as_float(d[b]) + __uint_as_float(d[R2P + b]),
+                     __uint_as_float(d[b + 1]) + __uint_as_float(d[R2P + b + 1]), hi, lo);
+          const int off0 = sw_off16(j * R2P + b, i, 128), off1 = sw_off16(j * R2P + b + 1, i, 128);
+          *reinterpret_cast<unsigned short*>(A2 + off0) = (unsigned short)(hi & 0xffffu);
+          *reinterpret_cast<unsigned short*>(A2 + off1) = (unsigned short)(hi >> 16);
+          *reinterpret_cast<unsigned short*>(A2 + LY::A2_TERM + off0) = (unsigned short)(lo & 0xffffu);
+          *reinterpret_cast<unsigned short*>(A2 + LY::A2_TERM + off1) = (unsigned short)(lo >> 16);
         }
       }
       if (j == SPB - 1 || t == nmine - 1) {

@@ -166,11 +166,12 @@ def test_bf16_compute_form(rt):
     assert torch.equal(Gc, G16)
 
 
-def test_bf16_storage_tensor_core_pass(rt):
+@pytest.mark.parametrize("shape,ranks", [((6, 40, 96, 64), (4, 6, 12, 16)), ((5, 9, 33, 16), (3, 4, 7, 5))])
+def test_bf16_storage_tensor_core_pass(rt, shape, ranks):
     # bfloat16 X through the tensor-core pass (MMA1 reads X from the TMA stage) must
-    # give the core of its exact float32 copy (whose lo terms are then zero)
+    # give the core of its exact float32 copy (whose lo terms are then zero); the
+    # second shape has an odd slab height (33 rows of the 128-row MMA tile)
     rs = np.random.default_rng(14)
-    shape, ranks = (6, 40, 96, 64), (4, 6, 12, 16)
     Xb = torch.from_numpy(rs.standard_normal(shape).astype(np.float32)).to(torch.bfloat16).cuda()
     U = [np.linalg.qr(rs.standard_normal((n, k)))[0].astype(np.float32) for n, k in zip(shape, ranks)]
     Ud = [torch.from_numpy(u).cuda() for u in U]
@@ -196,6 +197,17 @@ def test_core_entry_point_and_evaluator(rt):
     eg = rt.rtucker_relerr(Xd, G, Ud)
     eh = tucker.relerr(X, tucker.reconstruct(to_np(G), Uf))
     assert abs(eg - eh) <= 1e-9
+
+
+def test_core_tensor_core_pass_odd_slab_height(rt):
+    # float32 X, slabs of 33 x 12: odd n_{d-1} on the tensor-core pass, r = 5 and 7
+    rs = np.random.default_rng(15)
+    shape, ranks = (7, 6, 33, 12), (3, 4, 5, 7)
+    X = rs.standard_normal(shape).astype(np.float32)
+    U = [np.linalg.qr(rs.standard_normal((n, k)))[0].astype(np.float32) for n, k in zip(shape, ranks)]
+    G = rt.rtucker_core(torch.from_numpy(X).cuda(), [torch.from_numpy(u).cuda() for u in U])
+    Gr = tucker.multi_ttm_t(X.astype(np.float64), [u.astype(np.float64) for u in U])
+    assert np.abs(to_np(G) - Gr).max() <= 1e-5 * np.abs(Gr).max()
 
 
 def test_core_wide_rho_ragged_tiles(rt):
