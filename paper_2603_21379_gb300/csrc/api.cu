@@ -849,14 +849,70 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
   group_layout(Gp, bump);
   // per-tensor core buffers
   std::vector<size_t> oA(T), oB(T);
+  int dmax = 0;
   for (int t = 0; t < T; ++t) {
     const size_t cb = core_buffer_floats(d[t], n[t], r[t]);
     oA[t] = bump.take(cb * 4);
     oB[t] = bump.take(cb * 4);
+    dmax = std::max(dmax, (int)d[t]);
+  }
+  // The core of every tensor as grouped contractions: level k contracts mode
+  // d_t - 1 - k of every tensor with d_t > k, last mode first, one launch per level.
+  std::vector<int> njob(dmax, 0);
+  for (int t = 0; t < T; ++t)
+    for (int k = 0; k < d[t]; ++k) ++njob[k];
+  std::vector<size_t> o_jobs(dmax), o_lpre(dmax);
+  size_t job_bytes = 0;
+  for (int k = 0; k < dmax; ++k) {
+    o_jobs[k] = bump.take(sizeof(TTMJob) * njob[k]);
+    o_lpre[k] = bump.take(sizeof(int64_t) * (njob[k] + 1));
+    job_bytes += align_up(sizeof(TTMJob) * njob[k]) + align_up(sizeof(int64_t) * (njob[k] + 1));
   }
   if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
-  if ((st = ensure_stage(h, group_stage_bytes(Gp))) != RT_OK) return st;
+  const size_t gsb = group_stage_bytes(Gp);
+  if ((st = ensure_stage(h, gsb + job_bytes)) != RT_OK) return st;
   if ((st = group_upload(h, Gp, h->h_stage, 0)) != RT_OK) return st;
+  // job tables (workspace addresses are final once it is sized), staged after the
+  // range-finder tables and uploaded with them
+  std::vector<int64_t> ltiles(dmax, 0);
+  {
+    size_t so = gsb;
+    for (int k = 0; k < dmax; ++k) {
+      TTMJob* js = reinterpret_cast<TTMJob*>(h->h_stage + so);
+      so += align_up(sizeof(TTMJob) * njob[k]);
+      int64_t* ps = reinterpret_cast<int64_t*>(h->h_stage + so);
+      so += align_up(sizeof(int64_t) * (njob[k] + 1));
+      int q_i = 0;
+      int64_t acc = 0;
+      for (int t = 0; t < T; ++t) {
+        if (d[t] <= k) continue;
+        const int m = d[t] - 1 - k;
+        float* bufA = reinterpret_cast<float*>(h->ws + oA[t]);
+        float* bufB = reinterpret_cast<float*>(h->ws + oB[t]);
+        TTMJob q{};
+        q.A = (k == 0) ? X[t] : static_cast<const void*>((k & 1) ? bufA : bufB);
+        q.out = (m == 0) ? G[t] : ((k & 1) ? bufB : bufA);
+        q.L = 1;
+        q.R = 1;
+        for (int j = 0; j < m; ++j) q.L *= n[t][j];
+        for (int j = m + 1; j < d[t]; ++j) q.R *= r[t][j];
+        q.n = n[t][m];
+        q.r = r[t][m];
+        int64_t uo = 0;
+        for (int j = 0; j < m; ++j) uo += n[t][j] * r[t][j];
+        q.U = U[t] + uo;
+        ps[q_i] = acc;
+        acc += ttm_job_tiles(q);
+        js[q_i++] = q;
+      }
+      ps[q_i] = acc;
+      ltiles[k] = acc;
+      RT_CUDA(h, cudaMemcpyAsync(h->ws + o_jobs[k], js, sizeof(TTMJob) * njob[k], cudaMemcpyHostToDevice,
+                                 h->stream));
+      RT_CUDA(h, cudaMemcpyAsync(h->ws + o_lpre[k], ps, sizeof(int64_t) * (njob[k] + 1), cudaMemcpyHostToDevice,
+                                 h->stream));
+    }
+  }
   RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
   h->stage_pending = true;
   int nl = 0;
@@ -864,9 +920,12 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
     StageTimer tm(h, 0);
     nl += launch_range_finder(Gp.g, h->stream, h->d_status);
   }
-  for (int t = 0; t < T; ++t)
-    nl += enqueue_core(h, X[t], dtype, d[t], n[t], r[t], U[t], G[t], reinterpret_cast<float*>(h->ws + oA[t]),
-                       reinterpret_cast<float*>(h->ws + oB[t]), prec_of(opt));
+  for (int k = 0; k < dmax; ++k) {
+    StageTimer tm(h, k == 0 ? 1 : 2);
+    nl += launch_ttm_grouped(reinterpret_cast<const TTMJob*>(h->ws + o_jobs[k]),
+                             reinterpret_cast<const int64_t*>(h->ws + o_lpre[k]), njob[k], ltiles[k],
+                             k == 0 ? (int)dtype : DT_F32, h->stream);
+  }
   return finish(h, nl);
 }
 

@@ -26,16 +26,16 @@ template <> __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloa
   return __bfloat162float(p[e]);
 }
 
+// One 32 (a) x 128 (col) output tile of out(l, a, rho) = sum_i U[i][a] A(l, i, rho),
+// col = l R + rho, starting at column n0 and row a0 of U^T.
 template <typename T>
-__global__ void __launch_bounds__(256) k_ttm_t(const T* __restrict__ A, int64_t L, int64_t n, int64_t R,
-                                               const float* __restrict__ U, int r,
-                                               float* __restrict__ out) {
+__device__ __forceinline__ void ttm_tile(const T* __restrict__ A, int64_t L, int64_t n, int64_t R,
+                                         const float* __restrict__ U, int r, float* __restrict__ out, int64_t n0,
+                                         int a0) {
   __shared__ __align__(16) float Us[TT_BK][TT_BM];
   __shared__ __align__(16) float Bs[TT_BK][TT_BN];
   const int tid = threadIdx.x;
   const int64_t ncol = L * R;
-  const int64_t n0 = (int64_t)blockIdx.x * TT_BN;
-  const int a0 = blockIdx.y * TT_BM;
   const int tm = tid >> 5, tn = tid & 31;
   float acc[4][4];
 #pragma unroll
@@ -93,6 +93,25 @@ __global__ void __launch_bounds__(256) k_ttm_t(const T* __restrict__ A, int64_t 
       if (a < r) out[(l * r + a) * R + rho] = acc[x][y];
     }
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ttm_t(const T* __restrict__ A, int64_t L, int64_t n, int64_t R,
+                                               const float* __restrict__ U, int r,
+                                               float* __restrict__ out) {
+  ttm_tile<T>(A, L, n, R, U, r, out, (int64_t)blockIdx.x * TT_BN, blockIdx.y * TT_BM);
+}
+
+// Many contractions (one per tensor of a batch) in one launch: CTA b works on job
+// j with pre[j] <= b < pre[j + 1], tile (b - pre[j]) of its tiles_x x tiles_y grid.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ttm_grouped(const TTMJob* __restrict__ jobs, const int64_t* __restrict__ pre,
+                                                     int njobs) {
+  const int j = find_prob(pre, njobs, blockIdx.x);
+  const TTMJob& q = jobs[j];
+  const int64_t local = (int64_t)blockIdx.x - pre[j];
+  const int64_t tx = local % q.tiles_x, ty = local / q.tiles_x;
+  ttm_tile<T>(static_cast<const T*>(q.A), q.L, q.n, q.R, q.U, q.r, q.out, tx * TT_BN, (int)ty * TT_BM);
 }
 
 // ---------------------------------------------------------------- FP32, rho-contiguous form
@@ -236,6 +255,21 @@ int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, cons
     k_ttm_t<double><<<grid, 256, 0, st>>>(static_cast<const double*>(A), L, n, R, U, r, out);
   else
     k_ttm_t<__nv_bfloat16><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(A), L, n, R, U, r, out);
+  return 1;
+}
+
+int64_t ttm_job_tiles(TTMJob& q) {
+  q.tiles_x = (q.L * q.R + TT_BN - 1) / TT_BN;
+  return q.tiles_x * ((q.r + TT_BM - 1) / TT_BM);
+}
+
+int launch_ttm_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs, int64_t total_tiles, int dtype,
+                       cudaStream_t st) {
+  if (njobs < 1 || total_tiles < 1) return 0;
+  const unsigned grid = (unsigned)total_tiles;
+  if (dtype == DT_F32) k_ttm_grouped<float><<<grid, 256, 0, st>>>(jobs_dev, pre_dev, njobs);
+  else if (dtype == DT_F64) k_ttm_grouped<double><<<grid, 256, 0, st>>>(jobs_dev, pre_dev, njobs);
+  else k_ttm_grouped<__nv_bfloat16><<<grid, 256, 0, st>>>(jobs_dev, pre_dev, njobs);
   return 1;
 }
 

@@ -49,6 +49,19 @@ cudaError_t rf_init_attributes();
 // out(L, r, R) = sum_i U[i][a] A(L, n, R): mode contraction with U^T.
 int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, const float* U, int r,
                  float* out, cudaStream_t st);
+// One mode contraction out(l, a, rho) = sum_i U[i][a] A(l, i, rho) of a grouped launch
+// (A's element type is the launch's dtype).
+struct TTMJob {
+  const void* A;
+  int64_t L, n, R;
+  const float* U;
+  int32_t r;
+  float* out;
+  int64_t tiles_x;
+};
+int64_t ttm_job_tiles(TTMJob& q);  // sets tiles_x, returns the job's CTA count
+int launch_ttm_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs, int64_t total_tiles, int dtype,
+                       cudaStream_t st);
 cudaError_t core_init_attributes();
 // Fused pass over X on tensor cores: P[s] = U1^T X[s] U2 for S slabs of
 // n1 x n2.  X float32 (xbf16 = 0: two bf16 terms) or bfloat16 (xbf16 = 1).

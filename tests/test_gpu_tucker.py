@@ -261,7 +261,11 @@ def test_batched_matches_single_and_oracle(rt):
     for t in range(12):
         G1, U1 = rt.rtucker_decompose(Xd[t], list(ranks[t]), 5, seed=seeds[t])
         Gb, Ub = outs[t]
-        assert np.array_equal(to_np(Gb), to_np(G1))
+        # same range finder (grouped) -> identical factors; the core takes the grouped
+        # FFMA contractions in the batch and per-shape kernels alone
+        for k in range(3):
+            assert torch.equal(Ub[k], U1[k])
+        assert np.abs(to_np(Gb) - to_np(G1)).max() <= 1e-5 * np.abs(to_np(G1)).max()
         ref = tucker.sub_r_hosvd(Xs[t].astype(np.float64), list(ranks[t]), 5, seed=seeds[t])
         for k in range(3):
             _, dev, _ = compare_factor(to_np(Ub[k]), ref["U"][k], ref["modes"][k]["sigma"])
