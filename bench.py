@@ -229,13 +229,14 @@ def measure_batched(rt, steps):
     nbytes = sum(x.nbytes for x in Xh)
     seeds = [cfg["seed"] + t for t in range(cfg["T"])]
     p = cfg["p"]
-    ms_b = _event_time(lambda: rt.rtucker_decompose_batched(Xs, ranks, p, seeds), steps, 2)
+    plan = rt.BatchedDecomposition(Xs, ranks, p, seeds)
+    ms_b = _event_time(plan.run, steps, 2)
 
     def plain():
         for X, rk, sd in zip(Xs, ranks, seeds):
             rt.rtucker_decompose(X, list(rk), p, seed=sd)
     ms_p = _event_time(plain, max(1, steps // 2), 1)
-    res = rt.rtucker_decompose_batched(Xs, ranks, p, seeds)
+    res = plan.run().results()
     dmax = 0.0
     for t in range(0, cfg["T"], 16):
         Gb, Ub = res[t]

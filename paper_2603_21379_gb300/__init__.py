@@ -21,7 +21,7 @@ __all__ = [
     "rtucker_indices", "rtucker_sketch", "rtucker_factors", "rtucker_core", "rtucker_decompose",
     "rtucker_decompose_host", "rtucker_decompose_batched", "rtucker_relerr",
     "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "last_launch_count", "workspace_bytes",
-    "set_timing", "get_timing", "STAGES", "rhtucker_root_transfer_noalloc",
+    "set_timing", "get_timing", "STAGES", "rhtucker_root_transfer_noalloc", "BatchedDecomposition",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -314,45 +314,84 @@ def rtucker_decompose_host(X, r, p, s=None, seed=0, out=None, prec="fp32"):
     return G, _split(U, n, r)
 
 
+class BatchedDecomposition:
+    """A batch of Sub-R-HOSVD problems with its argument arrays and outputs set up
+    once: ``run()`` is a single call of ``rtucker_decompose_batched`` (one grouped
+    launch per stage for all (tensor, mode) problems, one per contraction level of
+    the cores), so repeated batches of the same shapes pay no per-call Python
+    marshalling.  The tensors in ``Xs`` may be overwritten between runs.  U and G
+    of all tensors live in two flat float32 buffers (``U_flat``, ``G_flat``);
+    ``results()`` gives the per-tensor (G, [U_k]) views."""
+
+    def __init__(self, Xs, ranks, p, seeds, s=None, prec="fp32"):
+        self.lib = load_library()
+        T = len(Xs)
+        dts = {X.dtype for X in Xs}
+        if len(dts) != 1:
+            raise ValueError("all tensors of a batch share one dtype")
+        self.dt = _DT[Xs[0].dtype]
+        dev = Xs[0].device
+        self.Xs = list(Xs)
+        self.T, self.p = T, int(p)
+        ds, ns, rs, shapes, rks = [], [], [], [], []
+        for X, r in zip(Xs, ranks):
+            _, d, n = _tensor_args(X)
+            r = _as_list(r, d)
+            ds.append(d)
+            ns.append(_i64(n))
+            rs.append(_i32(r))
+            shapes.append(n)
+            rks.append(r)
+        self.shapes, self.ranks = shapes, rks
+        usz = [sum(nk * rk for nk, rk in zip(n, r)) for n, r in zip(shapes, rks)]
+        gsz = [_prod(r) for r in rks]
+        self.U_flat = torch.empty(sum(usz), dtype=torch.float32, device=dev)
+        self.G_flat = torch.empty(sum(gsz), dtype=torch.float32, device=dev)
+        uoff = [0]
+        for v in usz:
+            uoff.append(uoff[-1] + v)
+        goff = [0]
+        for v in gsz:
+            goff.append(goff[-1] + v)
+        self._uoff, self._goff = uoff, goff
+        P64 = ctypes.POINTER(ctypes.c_int64)
+        P32 = ctypes.POINTER(ctypes.c_int32)
+        self._keep = (ns, rs)
+        self.n_arr = (P64 * T)(*[ctypes.cast(a, P64) for a in ns])
+        self.r_arr = (P32 * T)(*[ctypes.cast(a, P32) for a in rs])
+        self.s_arr = None
+        if s is not None:
+            self._s_keep = [_i64(_as_list(sv, dd)) for sv, dd in zip(s, ds)]
+            self.s_arr = (P64 * T)(*[ctypes.cast(a, P64) for a in self._s_keep])
+        self.d_arr = _i32(ds)
+        self.X_arr = (ctypes.c_void_p * T)(*[X.data_ptr() for X in Xs])
+        ub, gb = self.U_flat.data_ptr(), self.G_flat.data_ptr()
+        self.U_arr = (ctypes.c_void_p * T)(*[ub + 4 * uoff[t] for t in range(T)])
+        self.G_arr = (ctypes.c_void_p * T)(*[gb + 4 * goff[t] for t in range(T)])
+        self.seed_arr = (ctypes.c_uint64 * T)(*[int(v) for v in seeds])
+        self._opt_keep = _opts(prec)
+        self.h = _handle(dev.index)
+
+    def run(self):
+        _check(self.h, self.lib.rtucker_decompose_batched(self.h, self.T, self.X_arr, self.dt, self.d_arr, self.n_arr,
+                                                          self.r_arr, self.p, self.s_arr, self.seed_arr,
+                                                          self._opt_keep, self.U_arr, self.G_arr))
+        return self
+
+    def results(self):
+        out = []
+        for t in range(self.T):
+            n, r = self.shapes[t], self.ranks[t]
+            G = self.G_flat[self._goff[t]:self._goff[t + 1]].view(r)
+            U = self.U_flat[self._uoff[t]:self._uoff[t + 1]]
+            out.append((G, _split(U, n, r)))
+        return out
+
+
 def rtucker_decompose_batched(Xs, ranks, p, seeds, s=None, prec="fp32"):
     """Batched Sub-R-HOSVD: one grouped launch per stage for all (tensor, mode)
     problems.  Returns a list of (G, [U_k])."""
-    lib = load_library()
-    T = len(Xs)
-    dts = {X.dtype for X in Xs}
-    if len(dts) != 1:
-        raise ValueError("all tensors of a batch share one dtype")
-    dt = _DT[Xs[0].dtype]
-    dev = Xs[0].device
-    ds, ns, rs, Us, Gs = [], [], [], [], []
-    for X, r in zip(Xs, ranks):
-        _, d, n = _tensor_args(X)
-        r = _as_list(r, d)
-        ds.append(d)
-        ns.append(_i64(n))
-        rs.append(_i32(r))
-        Us.append(torch.empty(sum(nk * rk for nk, rk in zip(n, r)), dtype=torch.float32, device=dev))
-        Gs.append(torch.empty(r, dtype=torch.float32, device=dev))
-    P64 = ctypes.POINTER(ctypes.c_int64)
-    P32 = ctypes.POINTER(ctypes.c_int32)
-    n_arr = (P64 * T)(*[ctypes.cast(a, P64) for a in ns])
-    r_arr = (P32 * T)(*[ctypes.cast(a, P32) for a in rs])
-    s_arr = None
-    if s is not None:
-        s_keep = [_i64(_as_list(sv, dd)) for sv, dd in zip(s, ds)]
-        s_arr = (P64 * T)(*[ctypes.cast(a, P64) for a in s_keep])
-    X_arr = (ctypes.c_void_p * T)(*[X.data_ptr() for X in Xs])
-    U_arr = (ctypes.c_void_p * T)(*[u.data_ptr() for u in Us])
-    G_arr = (ctypes.c_void_p * T)(*[g.data_ptr() for g in Gs])
-    h = _handle(dev.index)
-    _check(h, lib.rtucker_decompose_batched(h, T, X_arr, dt, _i32(ds), n_arr, r_arr, int(p), s_arr,
-                                            (ctypes.c_uint64 * T)(*[int(v) for v in seeds]), _opts(prec), U_arr,
-                                            G_arr))
-    out = []
-    for X, r, U, G in zip(Xs, ranks, Us, Gs):
-        n = list(X.shape)
-        out.append((G, _split(U, n, _as_list(r, X.dim()))))
-    return out
+    return BatchedDecomposition(Xs, ranks, p, seeds, s=s, prec=prec).run().results()
 
 
 def rtucker_relerr(X, G, U):
