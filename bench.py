@@ -250,13 +250,18 @@ def measure_batched(rt, steps):
             "max_delta_relerr_vs_plain": dmax}
 
 
-def measure_ht(rt, steps, peak):
+def measure_ht(rt, steps, peak, n=None, d=None):
     """Sub-R-RtL-HT of f = 1/||x|| on the 16^8 grid (17.2 GB float32), rank 10,
     p = 5, w = 320: time per decomposition, input GB/s, the root pass (one read of
-    X) against the HBM roofline, and the relative error of the format."""
+    X) against the HBM roofline, and the relative error of the format.  ``n`` and
+    ``d`` replace the grid size and order (profiling runs use a smaller tensor)."""
     import torch
     import synth
-    cfg = synth.INVNORM_16_8
+    cfg = dict(synth.INVNORM_16_8)
+    if n is not None:
+        cfg["n"] = n
+    if d is not None:
+        cfg["d"] = d
     X = synth.inv_norm_tensor_torch(cfg["n"], cfg["d"], cfg["lo"], cfg["hi"], device="cuda")
     nbytes = X.numel() * 4
 
@@ -273,8 +278,9 @@ def measure_ht(rt, steps, peak):
     e = rt.rhtucker_relerr(X, U_leaf, B, cfg["rank"])
     del X
     torch.cuda.empty_cache()
-    return {"workload": "Sub-R-RtL-HT, f=1/||x|| on a 16^8 grid over [1,2]^8 (17.18 GB float32), balanced "
-                        "tree, rank 10, p=5, w=320 columns per node, seed 3",
+    return {"workload": "Sub-R-RtL-HT, f=1/||x|| on a %d^%d grid over [1,2]^%d (%.2f GB float32), balanced "
+                        "tree, rank 10, p=5, w=320 columns per node, seed 3"
+                        % (cfg["n"], cfg["d"], cfg["d"], nbytes / 1e9),
             "ms_per_decomp": ms, "input_gbs": nbytes / (ms * 1e-3) / 1e9, "relerr": e,
             "stage_ms": {k: v[0] / max(1, v[1]) for k, v in stg.items() if v[1]},
             "root_roofline": {"bound": "hbm", "kernel": "k_root (B_R = U_l^T X U_r, one read of X)",
@@ -414,6 +420,23 @@ def run_ours(args):
     return 0
 
 
+def run_only(args):
+    """One workload alone (for profiling): prints its JSON object."""
+    import torch
+    import paper_2603_21379_gb300 as rt
+    from paper_2603_21379_gb300 import build
+    torch.cuda.set_device(0)
+    build.build()
+    rt.load_library()
+    peak, _ = measured_peaks()
+    if args.only == "ht":
+        out = measure_ht(rt, args.steps, peak, n=args.ht_n, d=args.ht_d)
+    else:
+        out = measure_batched(rt, args.steps)
+    print(json.dumps({"only": args.only, **out}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,6 +444,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["ht", "batched"], default=None,
+                    help="run one extra workload alone (profiling), not the benchmark line")
+    ap.add_argument("--ht-n", type=int, default=None, help="grid size of the H-Tucker workload with --only ht")
+    ap.add_argument("--ht-d", type=int, default=None, help="order of the H-Tucker workload with --only ht")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the BF16 forms, the batched and the H-Tucker workloads (untimed extras)")
     args = ap.parse_args()
@@ -428,6 +455,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
     return run_ours(args)
 
 

@@ -182,7 +182,10 @@ rt_status rtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, cons
  *               first (1 x r_{R_l} x r_{R_r});
  *   U_nodes     device or NULL: concat over non-root nodes in id order of the
  *               node bases U_S (n_S x r_S).
- * Rules: r_S + p <= min(n_S, n_{notin S}), r_S + p <= w_S <= n_{notin S}. */
+ * Rules: r_S + p <= min(n_S, n_{notin S}), r_S + p <= w_S <= n_{notin S}
+ * (RT_EINVAL otherwise); ranks of internal nodes and of their children at
+ * most 12 (RT_ENOTSUP otherwise: the transfer-tensor and root kernels keep
+ * r x r x r blocks in registers and shared memory; the paper uses 10). */
 rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
                              const int32_t* rank, int32_t p, const int64_t* w, uint64_t seed,
                              const rt_options* opt, float* U_leaf, float* B, float* U_nodes);

@@ -1019,11 +1019,13 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
   const int rl = rk[root.left], rr = rk[root.right];
   if (rr > 12) return fail(h, RT_ENOTSUP, "rank of the root's right child above 12");
   const size_t o_rootp = bump.take(root_pass_scratch_floats(nl, nr, rl, rr) * 4);
+  int64_t tr_ctas = 0;
   for (int i : internal) {
-    const int64_t nlc = range_prod(n, tree[tree[i].left].a, tree[tree[i].left].b);
-    if ((size_t)nlc * rk[tree[i].right] * 4 > 200 * 1024)
-      return fail(h, RT_ENOTSUP, "child basis too large for the transfer-tensor kernel");
+    if (rk[i] > 12 || rk[tree[i].left] > 12 || rk[tree[i].right] > 12)
+      return fail(h, RT_ENOTSUP, "internal-node ranks above 12");
+    tr_ctas += transfer_ctas(range_prod(n, tree[tree[i].left].a, tree[tree[i].left].b));
   }
+  const size_t o_tpart = bump.take(transfer_part_floats(std::max<int64_t>(1, tr_ctas)) * 4);
   if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
   const size_t sb = group_stage_bytes(Gp) + align_up(sizeof(TransferJob) * std::max<size_t>(1, internal.size()));
   if ((st = ensure_stage(h, sb)) != RT_OK) return st;
@@ -1043,6 +1045,7 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
     jb.rS = rk[i];
     jb.rl = rk[nd.left];
     jb.rr = rk[nd.right];
+    jb.cta0 = q == 0 ? 0 : jobs[q - 1].cta0 + transfer_ctas(jobs[q - 1].nl);
     jobs[q] = jb;
   }
   if (!internal.empty())
@@ -1064,7 +1067,7 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
   {
     StageTimer tm(h, 3);
     nlaunch += launch_transfer(reinterpret_cast<const TransferJob*>(h->ws + o_jobs), jobs, (int)internal.size(),
-                               h->stream);
+                               reinterpret_cast<float*>(h->ws + o_tpart), h->stream);
   }
   {
     StageTimer tm(h, 4);

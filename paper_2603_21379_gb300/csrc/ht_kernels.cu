@@ -19,44 +19,87 @@
 namespace rt {
 
 // ------------------------------------------------------------------ internal nodes
-// grid: (job, i).  Dynamic smem: T[nl][rr] (float)
-__global__ void __launch_bounds__(256) k_transfer(const TransferJob* __restrict__ jobs) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* T = reinterpret_cast<float*>(smem_raw);
-  const TransferJob jb = jobs[blockIdx.y];
-  const int i = blockIdx.x;
-  if (i >= jb.rS) return;
-  // T(a, k) = sum_b M_i(a, b) U_r(b, k)
-  for (int64_t e = threadIdx.x; e < jb.nl * jb.rr; e += blockDim.x) {
-    const int64_t a = e / jb.rr;
-    const int k = (int)(e % jb.rr);
-    float acc = 0.f;
-    for (int64_t b = 0; b < jb.nr; ++b)
-      acc = fmaf(__ldg(jb.US + (a * jb.nr + b) * jb.rS + i), __ldg(jb.Ur + b * jb.rr + k), acc);
-    T[e] = acc;
+// k_transfer_part: CTA c of job q (q.cta0 <= c < q.cta0 + ceil(n_l / TR_A)) takes the
+// left-child rows a in [a0, a0 + TR_A):
+//     T(a, i, k) = sum_b U_S(a n_r + b, i) U_r(b, k)      (rows of U_S read contiguously)
+//     part_c(i, j, k) = sum_a U_l(a, j) T(a, i, k)
+// k_transfer_sum: B_S = sum over the job's CTAs of part_c, fixed order, float64.
+constexpr int TR_A = 4, TR_B = 64, TR_MAX = 12, TR_TH = 256;
+
+__global__ void __launch_bounds__(TR_TH) k_transfer_part(const TransferJob* __restrict__ jobs, int njobs,
+                                                         float* __restrict__ part) {
+  __shared__ float us[TR_A * TR_B * TR_MAX];
+  __shared__ float ur[TR_B * TR_MAX];
+  __shared__ float tt[TR_A * TR_MAX * TR_MAX];
+  int q = 0;
+  while (q + 1 < njobs && (int64_t)blockIdx.x >= jobs[q + 1].cta0) ++q;
+  const TransferJob jb = jobs[q];
+  const int64_t a0 = ((int64_t)blockIdx.x - jb.cta0) * TR_A;
+  const int na = (int)min((int64_t)TR_A, jb.nl - a0);
+  const int rS = jb.rS, rl = jb.rl, rr = jb.rr;
+  const int nT = TR_A * rS * rr;                 // outputs T(a, i, k), a < TR_A
+  float acc[(TR_A * TR_MAX * TR_MAX + TR_TH - 1) / TR_TH];
+#pragma unroll
+  for (int u = 0; u < (int)(sizeof(acc) / sizeof(float)); ++u) acc[u] = 0.f;
+  for (int64_t b0 = 0; b0 < jb.nr; b0 += TR_B) {
+    const int nb = (int)min((int64_t)TR_B, jb.nr - b0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < TR_A * nb * rS; e += TR_TH) {
+      const int a = e / (nb * rS), rem = e % (nb * rS);
+      us[e] = (a < na) ? __ldg(jb.US + ((a0 + a) * jb.nr + b0) * rS + rem) : 0.f;
+    }
+    for (int e = threadIdx.x; e < nb * rr; e += TR_TH) ur[e] = __ldg(jb.Ur + b0 * rr + e);
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < (int)(sizeof(acc) / sizeof(float)); ++u) {
+      const int o = threadIdx.x + u * TR_TH;
+      if (o < nT) {
+        const int a = o / (rS * rr), i = (o / rr) % rS, k = o % rr;
+        const float* up = us + a * nb * rS + i;
+        float v = acc[u];
+        for (int b = 0; b < nb; ++b) v = fmaf(up[b * rS], ur[b * rr + k], v);
+        acc[u] = v;
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < (int)(sizeof(acc) / sizeof(float)); ++u) {
+    const int o = threadIdx.x + u * TR_TH;
+    if (o < nT) tt[o] = acc[u];
   }
   __syncthreads();
-  // B(i, j, k) = sum_a U_l(a, j) T(a, k)
-  for (int e = threadIdx.x; e < jb.rl * jb.rr; e += blockDim.x) {
-    const int j = e / jb.rr, k = e % jb.rr;
-    float acc = 0.f;
-    for (int64_t a = 0; a < jb.nl; ++a) acc = fmaf(__ldg(jb.Ul + a * jb.rl + j), T[a * jb.rr + k], acc);
-    jb.B[((int64_t)i * jb.rl + j) * jb.rr + k] = acc;
+  float* pc = part + (size_t)blockIdx.x * TR_MAX * TR_MAX * TR_MAX;
+  for (int o = threadIdx.x; o < rS * rl * rr; o += TR_TH) {
+    const int i = o / (rl * rr), j = (o / rr) % rl, k = o % rr;
+    float v = 0.f;
+    for (int a = 0; a < na; ++a) v = fmaf(__ldg(jb.Ul + (a0 + a) * rl + j), tt[(a * rS + i) * rr + k], v);
+    pc[o] = v;
   }
 }
 
-int launch_transfer(const TransferJob* jobs_dev, const TransferJob* jobs_host, int njobs, cudaStream_t st) {
-  if (njobs <= 0) return 0;
-  int rmax = 1;
-  size_t smax = 0;
-  for (int q = 0; q < njobs; ++q) {
-    rmax = rmax > jobs_host[q].rS ? rmax : jobs_host[q].rS;
-    const size_t sz = (size_t)jobs_host[q].nl * jobs_host[q].rr * sizeof(float);
-    smax = smax > sz ? smax : sz;
-  }
-  cudaFuncSetAttribute(k_transfer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smax);
-  k_transfer<<<dim3((unsigned)rmax, (unsigned)njobs), 256, smax, st>>>(jobs_dev);
-  return 1;
+__global__ void __launch_bounds__(TR_TH) k_transfer_sum(const TransferJob* __restrict__ jobs,
+                                                        const float* __restrict__ part) {
+  const TransferJob jb = jobs[blockIdx.y];
+  const int o = blockIdx.x * TR_TH + threadIdx.x;
+  if (o >= jb.rS * jb.rl * jb.rr) return;
+  const int64_t nc = (jb.nl + TR_A - 1) / TR_A;
+  double v = 0.0;
+  for (int64_t c = 0; c < nc; ++c) v += (double)part[(size_t)(jb.cta0 + c) * TR_MAX * TR_MAX * TR_MAX + o];
+  jb.B[o] = (float)v;
+}
+
+int64_t transfer_ctas(int64_t nl) { return (nl + TR_A - 1) / TR_A; }
+size_t transfer_part_floats(int64_t total_ctas) { return (size_t)total_ctas * TR_MAX * TR_MAX * TR_MAX; }
+
+int launch_transfer(const TransferJob* jobs_dev, const TransferJob* jobs_host, int njobs, float* part,
+                    cudaStream_t st) {
+  if (njobs < 1) return 0;
+  const int64_t total = jobs_host[njobs - 1].cta0 + transfer_ctas(jobs_host[njobs - 1].nl);
+  int omax = 1;
+  for (int q = 0; q < njobs; ++q) omax = std::max(omax, jobs_host[q].rS * jobs_host[q].rl * jobs_host[q].rr);
+  k_transfer_part<<<(unsigned)total, TR_TH, 0, st>>>(jobs_dev, njobs, part);
+  k_transfer_sum<<<dim3((unsigned)((omax + TR_TH - 1) / TR_TH), (unsigned)njobs), TR_TH, 0, st>>>(jobs_dev, part);
+  return 2;
 }
 
 // ------------------------------------------------------------------ root pass

@@ -11,14 +11,15 @@
 //                 64 rows of the current block, each thread 4 rows x 4 columns of
 //                 every stage (so one read of its 4 x r_r slice of U_r serves 4
 //                 rows), accumulating in registers over 4 stages and adding those
-//                 sums with Kahan compensation; the eight column groups of a row
-//                 are combined with warp shuffles at the end of the block.
-//   k_root_left   per CTA of 256 rows: sum_a U_l(a, j) T(a, k) in float64.
+//                 sums with Kahan compensation.  Each warp holds half of the
+//                 columns of 32 rows; at the end of the block its 4 column groups
+//                 are combined with warp shuffles and the half is written to T.
+//   k_root_left   per CTA of 256 rows: sum_a U_l(a, j) T(a, k).
 //   k_root_reduce (ht_kernels.cu): fixed-order float64 sum of the partials.
 //
 // The bytes that count are X's (17.2 GB for the 16^8 tensor): U_r (n_r r_r
-// floats) is re-read from L2 once per 64-row block, T and the partials are
-// n_l r_r and (n_l / 256) r_l r_r floats.
+// floats) is re-read from L2 once per 64-row block, T (two column halves) and
+// the partials are 2 n_l r_r and (n_l / 256) r_l r_r floats.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -33,6 +34,7 @@ namespace rt {
 namespace {
 
 using namespace tma;
+
 
 constexpr int RS_ROWS = 64;                  // rows of X per work item
 constexpr int RS_COLS = 32;                  // columns per stage (128 bytes of float32)
@@ -95,12 +97,16 @@ __global__ void __launch_bounds__(RS_THREADS, RS_CTAS_PER_SM) k_root_rows(const 
   }
 
   // -------------------------------------------------------------- consumers
-  // thread = (row group rs, column group g): rows rs + 16 h (h < 4), columns 4g..4g+3
+  // thread = (row group rs, column group g): rows rs + 16 h (h < 4), columns 4g..4g+3.
+  // Warp w covers row groups 8 (w & 1) .. + 7 and column groups 4 (w >> 1) .. + 3, so
+  // the four U_r slices a warp reads start 40 floats apart (distinct banks) and its X
+  // reads are 8 rows x 64 bytes (4 wavefronts under the 128-byte swizzle).
   constexpr int NCG = 8;                                        // column groups
   constexpr int CPT = RS_COLS / NCG;                            // columns per thread
   constexpr int RPT = RS_ROWS * NCG / (RS_CONS * 32);           // rows per thread
   constexpr int RSTEP = RS_ROWS / RPT;
-  const int rs = threadIdx.x / NCG, g = threadIdx.x % NCG;
+  static_assert(RS_CONS == 4 && RPT == 4 && RSTEP == 16, "lane map below assumes 4 warps of 8 x 4 threads");
+  const int rs = 8 * (warp & 1) + (lane >> 2), g = 4 * (warp >> 1) + (lane & 3);
   int64_t c = 0;
   for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
     float acc[RPT][RR], tot[RPT][RR], cmp[RPT][RR];
@@ -151,22 +157,26 @@ __global__ void __launch_bounds__(RS_THREADS, RS_CTAS_PER_SM) k_root_rows(const 
       }
     }
     if (!ok) break;
-    // T(a, k): sum over the column groups (consecutive lanes)
+    // T(a, half, k): sum over the 4 column groups of this warp (lanes 4m .. 4m + 3); the
+    // other half of the columns is in warp w ^ 2 and has its own slot (k_root_left adds
+    // the two), so the consumer warps never wait on one another
+    const int half = warp >> 1;
 #pragma unroll
     for (int h = 0; h < RPT; ++h) {
       const int64_t a = it * RS_ROWS + rs + RSTEP * h;
 #pragma unroll
       for (int k = 0; k < RR; ++k) {
         float v = tot[h][k] - cmp[h][k];
-#pragma unroll
-        for (int o = 1; o < NCG; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (g == 0 && a < nl) T[a * RR + k] = v;
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        if ((lane & 3) == 0 && a < nl) T[(a * 2 + half) * RR + k] = v;
       }
     }
   }
 }
 
-// part[blk](j, k) = sum over the CTA's rows a of U_l(a, j) T(a, k), float64.
+// part[blk](j, k) = sum over the CTA's rows a of U_l(a, j) T(a, k), with T(a, k) the
+// sum of the two column halves written by k_root_rows.
 __global__ void __launch_bounds__(RL_ROWS) k_root_left(const float* __restrict__ Ul, int rl,
                                                        const float* __restrict__ T, int rr, int64_t nl,
                                                        float* __restrict__ part) {
@@ -174,14 +184,19 @@ __global__ void __launch_bounds__(RL_ROWS) k_root_left(const float* __restrict__
   const int64_t a0 = (int64_t)blockIdx.x * RL_ROWS;
   const int rows = (int)min((int64_t)RL_ROWS, nl - a0);
   for (int e = threadIdx.x; e < rows * rl; e += blockDim.x) ul[e] = Ul[a0 * rl + e];
-  for (int e = threadIdx.x; e < rows * rr; e += blockDim.x) ts[e] = T[a0 * rr + e];
+  for (int e = threadIdx.x; e < rows * rr; e += blockDim.x) {
+    const int a = e / rr, k = e % rr;
+    ts[e] = T[((a0 + a) * 2) * rr + k] + T[((a0 + a) * 2 + 1) * rr + k];
+  }
   __syncthreads();
   const int p = threadIdx.x;
   if (p < rl * rr) {
+    // four interleaved float32 partial sums of 64 products each; the partials of all
+    // CTAs are added in float64 by k_root_reduce
     const int j = p / rr, k = p % rr;
-    double acc = 0.0;
-    for (int a = 0; a < rows; ++a) acc += (double)ul[a * rl + j] * (double)ts[a * rr + k];
-    part[(size_t)blockIdx.x * rl * rr + p] = (float)acc;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int a = 0; a < rows; ++a) acc[a & 3] = fmaf(ul[a * rl + j], ts[a * rr + k], acc[a & 3]);
+    part[(size_t)blockIdx.x * rl * rr + p] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
   }
 }
 
@@ -201,7 +216,7 @@ int launch_rows(const CUtensorMap& map, const float* Ur, int64_t nl, int64_t nr,
 }  // namespace
 
 size_t root_stream_scratch_floats(int64_t nl, int rl, int rr) {
-  return (size_t)nl * rr + (size_t)((nl + RL_ROWS - 1) / RL_ROWS) * rl * rr;
+  return (size_t)nl * 2 * rr + (size_t)((nl + RL_ROWS - 1) / RL_ROWS) * rl * rr;
 }
 
 // Streaming root pass for float32 X with n_r % 32 == 0, 16-byte aligned X and U_r
@@ -225,7 +240,7 @@ int launch_root_stream(const float* X, int64_t nl, int64_t nr, const float* Ul, 
           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return 0;
   float* T = scratch;
-  float* part = scratch + (size_t)nl * rr;
+  float* part = scratch + (size_t)nl * 2 * rr;
   int n = 0;
   switch (rr) {
 #define RS_CASE(K) \

@@ -73,8 +73,12 @@ int launch_core2_tc(int xmode, const void* X, int64_t S, int n1, int n2, const f
 struct TransferJob {     // B_S(i, j, k) = sum_{a,b} U_S[a n_r + b][i] U_l[a][j] U_r[b][k]
   const float* US; const float* Ul; const float* Ur; float* B;
   int64_t nl, nr; int rS, rl, rr;
+  int64_t cta0;          // first CTA of this job in the partial-sum launch
 };
-int launch_transfer(const TransferJob* jobs_dev, const TransferJob* jobs_host, int njobs,
+int64_t transfer_ctas(int64_t nl);               // CTAs of one job
+size_t transfer_part_floats(int64_t total_ctas); // partial-sum scratch
+// ranks up to 12; part holds transfer_part_floats(total CTAs of all jobs)
+int launch_transfer(const TransferJob* jobs_dev, const TransferJob* jobs_host, int njobs, float* part,
                     cudaStream_t st);
 // B_R(0, j, k) = sum_{a,b} X[a nr + b] Ul[a][j] Ur[b][k]
 // Root pass B_R = U_l^T X^(R_l) U_r: the streaming (TMA) kernel for float32 X when the
