@@ -745,9 +745,10 @@ __global__ void __launch_bounds__(QR_THREADS) k_bt_qr(const RFProb* __restrict__
 
 // S6: R of the stacked chunk factors, then one-sided Jacobi (Hestenes) on the
 // columns of R^T: R^T V = W Sigma, W = left singular vectors of B.  Columns
-// are processed in round-robin order, one warp per pair, until a sweep makes
-// no rotation (or 40 sweeps).  W is stored sorted by descending sigma.
-// Dynamic smem: A[ld*c] | tau | rdiag | red | AT[CMAX*(CMAX+1)] | sig[CMAX] | flag
+// are processed in round-robin order, one 16-lane group per pair, until a sweep
+// makes no rotation or leaves every pair below sqrt(tol) / 2 before rotation (at
+// most WS_MAX_SWEEPS, else ST_NUMERIC).  W is stored sorted by descending sigma.
+// Dynamic smem: A[ld*c] | tau | rdiag | red | AT[CMAX*WS_LDT] | sig[CMAX] | flag[2], dmax[2] | vbuf
 static_assert(QR_THREADS / 16 >= CMAX / 2, "one 16-lane group per Jacobi pair");
 static_assert(WS_LDT >= CMAX && WS_LDT % 32 == 16, "Jacobi column stride");
 __global__ void __launch_bounds__(QR_THREADS) k_wsvd(const RFProb* __restrict__ P,
@@ -797,10 +798,19 @@ __global__ void __launch_bounds__(QR_THREADS) k_wsvd(const RFProb* __restrict__ 
   const int pr = threadIdx.x >> 4, l16 = threadIdx.x & 15;
   const int kc = (c + 15) >> 4;
   const unsigned gm = 0xffffu << (threadIdx.x & 16);
-  int sweep = 0;
-  for (; sweep < WS_MAX_SWEEPS; ++sweep) {
+  // Stop after a sweep in which no pair rotated, or in which every pair's relative
+  // off-diagonal |a_p.a_q| / (|a_p||a_q|) was below sqrt(tol) / 2: cyclic Jacobi
+  // converges quadratically, so such a sweep leaves every pair below tol and the next
+  // sweep would rotate nothing.
+  const float quad_stop = 0.5f * sqrtf(tol);
+  unsigned* dmax = reinterpret_cast<unsigned*>(flag + 2);   // per sweep, as float bits (>= 0)
+  if (threadIdx.x < 2) dmax[threadIdx.x] = 0u;
+  __syncthreads();
+  bool converged = false;
+  for (int sweep = 0; sweep < WS_MAX_SWEEPS && !converged; ++sweep) {
     int t = pr - 1, u = ne - 2 - pr;
     int rotated = 0;
+    float dloc = 0.f;
     for (int rnd = 0; rnd < ne - 1; ++rnd) {
       const int pa = (pr == 0) ? 0 : 1 + t;
       const int qa = 1 + u;
@@ -826,7 +836,9 @@ __global__ void __launch_bounds__(QR_THREADS) k_wsvd(const RFProb* __restrict__ 
           be += __shfl_xor_sync(gm, be, o);
           ga += __shfl_xor_sync(gm, ga, o);
         }
-        if (ga != 0.f && fabsf(ga) * rsqrt_approx(al) * rsqrt_approx(be) > tol) {
+        const float rel = (ga != 0.f) ? fabsf(ga) * rsqrt_approx(al) * rsqrt_approx(be) : 0.f;
+        dloc = fmaxf(dloc, rel);
+        if (ga != 0.f && rel > tol) {
           // tangent of the angle that makes the pair orthogonal, smaller root
           const float zeta = (be - al) * rcp_approx(2.f * ga);
           const float az = fabsf(zeta);
@@ -855,13 +867,16 @@ __global__ void __launch_bounds__(QR_THREADS) k_wsvd(const RFProb* __restrict__ 
     // flag[sweep & 1] is set by any pair that rotated; the other slot is cleared for the
     // next sweep (it was last read before the previous barrier).
     if (rotated) flag[sweep & 1] = 1;
+    const unsigned dw = __reduce_max_sync(0xffffffffu, __float_as_uint(dloc));
+    if ((threadIdx.x & 31) == 0 && dw) atomicMax(&dmax[sweep & 1], dw);
     __syncthreads();
     const int f = flag[sweep & 1];
-    if (threadIdx.x == 0) flag[(sweep + 1) & 1] = 0;
+    const float dm = __uint_as_float(dmax[sweep & 1]);
+    if (threadIdx.x == 0) { flag[(sweep + 1) & 1] = 0; dmax[(sweep + 1) & 1] = 0u; }
     __syncthreads();
-    if (!f) break;
+    converged = !f || dm < quad_stop;
   }
-  if (sweep == WS_MAX_SWEEPS && threadIdx.x == 0) set_status(status, ST_NUMERIC);
+  if (!converged && threadIdx.x == 0) set_status(status, ST_NUMERIC);
   // singular values (column norms) and descending order
   for (int qc = warp; qc < c; qc += nw) {
     float s2 = 0.f;
