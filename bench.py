@@ -130,6 +130,30 @@ def dist_info():
     return ws, rank, local
 
 
+def max_over_ranks(value, device=None):
+    """The largest ``value`` over all ranks of the default process group (the
+    identity without one).  Timing lines report the slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.barrier()
+
+
+def whole_job_rate(bytes_per_rank, steps, world, ms):
+    """Whole-job input rate (GB/s): every rank decomposes its own tensor each step
+    (independent problems, weak scaling), timed by the slowest rank."""
+    return world * bytes_per_rank * steps / (ms * 1e-3) / 1e9
+
+
 # ---------------------------------------------------------------- oracle arm
 def oracle_sample(X, cfg):
     """Bounded sample of the workload on the float64 oracle: the whole factor
@@ -331,8 +355,7 @@ def run_ours(args):
         time.sleep(0.3)
     rt.set_timing(True)
     rt.get_timing(reset=True)
-    if ws > 1:
-        torch.distributed.barrier()
+    rank_barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -340,16 +363,12 @@ def run_ours(args):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
+    rank_barrier()
     ms = e0.elapsed_time(e1)
     stages = rt.get_timing(reset=True)
     rt.set_timing(False)
     clocks = sampler.stop() if sampler else None
-    if ws > 1:
-        tt = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, device="cuda")
 
     # fixed-error report (untimed): relative reconstruction error of this result
     Us = [u for u in torch.split(U, [nk * rk for nk, rk in zip(n, r)])]
@@ -362,16 +381,12 @@ def run_ours(args):
     Gh = torch.empty(r, dtype=torch.float32).pin_memory()
     rt.rtucker_decompose_host(Xpin, r, p, seed=seed, out=(Uh, Gh))
     e2e_steps = max(3, min(args.steps, 10))
-    if ws > 1:
-        torch.distributed.barrier()
+    rank_barrier()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         rt.rtucker_decompose_host(Xpin, r, p, seed=seed, out=(Uh, Gh))
     t_e2e = time.perf_counter() - t0
-    if ws > 1:
-        tt = torch.tensor([t_e2e], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(t_e2e, device="cuda")
 
     extra = {}
     if rank == 0 and not args.no_extras:
@@ -387,7 +402,7 @@ def run_ours(args):
         x_ms, x_cnt = stages["core_x_pass"]
         avg_x = x_ms / max(1, x_cnt)
         achieved = nbytes / (avg_x * 1e-3) / 1e9
-        value = ws * nbytes * args.steps / (ms * 1e-3) / 1e9
+        value = whole_job_rate(nbytes, args.steps, ws, ms)
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
             t_cpu = oracle_sample(Xh, cfg)
