@@ -241,10 +241,11 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   pp.units[STG_BTP] = (int64_t)q.nsc * q.nbi;
   pp.units[STG_BTQ] = q.nsc;
   pp.units[STG_WSVD] = 1;
-  pp.units[STG_QW] = (nS + QW_TI - 1) / QW_TI;
+  const bool qw_fused = nS <= QWF_MAX;
+  pp.units[STG_QW] = qw_fused ? 0 : (nS + QW_TI - 1) / QW_TI;
   pp.units[STG_FLIP] = pp.units[STG_QW];
+  pp.units[STG_QWF] = qw_fused ? 1 : 0;
   pp.units[STG_ZSUM] = nS * c;
-  pp.units[STG_OMEGA] = s * c;
   return RT_OK;
 }
 

@@ -45,22 +45,6 @@ __global__ void __launch_bounds__(256) k_sample(const RFProb* __restrict__ P,
   q.off[j] = off;
 }
 
-// S3: Omega(j, c) = Box-Muller normal of Philox counter (pi(j), c), one thread per entry.
-__global__ void __launch_bounds__(256) k_omega(const RFProb* __restrict__ P,
-                                               const int64_t* __restrict__ pre, int np) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= pre[np]) return;
-  const int p = find_prob(pre, np, t);
-  const RFProb& q = P[p];
-  const int64_t e = t - pre[p];
-  const int64_t j = e / q.c;
-  const int c = (int)(e % q.c);
-  q.Om[e] = gauss_entry((uint64_t)q.idx[j], (uint32_t)c, philox_key(q.seed), q.node);
-  // the sketch's per-row-tile counters start at zero (this kernel precedes it)
-  const int64_t nrt = (q.nS + SK_TI - 1) / SK_TI;
-  for (int64_t e2 = e; e2 < nrt; e2 += pre[p + 1] - pre[p]) q.zcnt[e2] = 0;
-}
-
 // ------------------------------------------------------------------ S2 + S4
 // One CTA: rows [i0, i0+TI) x samples [j0, j0+TJ) of Y = X^(S) E.
 // Dynamic smem: Ys[TJ][TI] | Os[TJ][CMAX] | offs[TJ] (int64)
@@ -963,6 +947,69 @@ __global__ void __launch_bounds__(256) k_flip(const RFProb* __restrict__ P,
   }
 }
 
+// U = Q W(:, :r) and the sign rule in one CTA per problem with n_S <= QWF_MAX rows:
+// U in shared memory, per-column keys (|u|, lowest row) by shared atomics, then the
+// flipped U written once.  Dynamic smem: Ws[CMAX*CMAX] | Qs[QWF_MAX*CMAX] |
+// Us[QWF_MAX*CMAX] | keys[CMAX] (u64) | sg[CMAX]
+__global__ void __launch_bounds__(512) k_qwf(const RFProb* __restrict__ P, const int64_t* __restrict__ pre,
+                                             int np) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ws = reinterpret_cast<float*>(smem_raw);
+  float* Qs = Ws + CMAX * CMAX;
+  float* Us = Qs + QWF_MAX * CMAX;
+  unsigned long long* kb = reinterpret_cast<unsigned long long*>(Us + QWF_MAX * CMAX);
+  float* sg = reinterpret_cast<float*>(kb + CMAX);
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int m = (int)q.nS;
+  const int c = q.c, r = q.r;
+  for (int e = threadIdx.x; e < c * r; e += blockDim.x) Ws[(e / r) * CMAX + e % r] = q.W[(e / r) * c + e % r];
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) Qs[e] = q.Q[e];
+  if (threadIdx.x < r) kb[threadIdx.x] = 0ull;
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
+    const int i = e / r, col = e % r;
+    const float u = qw_entry(Qs + i * c, Ws, c, col, CMAX);
+    Us[e] = u;
+    atomicMax(&kb[col], sign_key(u, i));
+  }
+  __syncthreads();
+  if (threadIdx.x < r) {
+    const int col = threadIdx.x;
+    const int rstar = (int)(0xffffffffu - (uint32_t)(kb[col] & 0xffffffffull));
+    sg[col] = (Us[rstar * r + col] < 0.f) ? -1.f : 1.f;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * r; e += blockDim.x) q.U[e] = sg[e % r] * Us[e];
+}
+
+// S1 + S3 for the grouped range finder: thread j computes pi(j) and its fiber offset,
+// then row j of Omega (Box-Muller of Philox counters (pi(j), c)); it also clears the
+// sketch's per-row-tile counters.
+__global__ void __launch_bounds__(128) k_sample_omega(const RFProb* __restrict__ P,
+                                                      const int64_t* __restrict__ pre, int np, int* status) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= pre[np]) return;
+  const int p = find_prob(pre, np, t);
+  const RFProb& q = P[p];
+  const int64_t j = t - pre[p];
+  const PhiloxKey key = philox_key(q.seed);
+  const uint64_t m = sample_index((uint64_t)j, (uint64_t)q.N, q.fh, key, q.node, status);
+  q.idx[j] = (int64_t)m;
+  uint64_t rem = m;
+  int64_t off = 0;
+  for (int t2 = q.ncm - 1; t2 >= 0; --t2) {
+    const uint64_t sz = (uint64_t)q.csize[t2];
+    off += (int64_t)(rem % sz) * q.cstride[t2];
+    rem /= sz;
+  }
+  q.off[j] = off;
+  float* om = q.Om + j * q.c;
+  for (int c = 0; c < q.c; ++c) om[c] = gauss_entry(m, (uint32_t)c, key, q.node);
+  const int64_t nrt = (q.nS + SK_TI - 1) / SK_TI;
+  for (int64_t e2 = j; e2 < nrt; e2 += q.s) q.zcnt[e2] = 0;
+}
+
 // ------------------------------------------------------------------ host launchers
 static size_t smem_gs() { return (size_t)(SK_TJ * SK_TI + SK_TJ * CMAX) * 4 + SK_TJ * 8; }
 static size_t smem_qr() { return (size_t)(2 * QR_MAXF + 2 * CMAX + 1024) * 4 + 64; }
@@ -978,6 +1025,7 @@ static size_t smem_wsvd() {
 }
 static size_t smem_qw() { return (size_t)(CMAX * CMAX + QW_TI * CMAX) * 4 + CMAX * 8; }
 static size_t smem_flip() { return (size_t)(CMAX * CMAX + CMAX) * 4; }
+static size_t smem_qwf() { return (size_t)(CMAX * CMAX + 2 * QWF_MAX * CMAX) * 4 + CMAX * 8 + CMAX * 4; }
 
 cudaError_t rf_init_attributes() {
   cudaError_t e;
@@ -995,6 +1043,7 @@ cudaError_t rf_init_attributes() {
   RT_ATTR(k_wsvd, smem_wsvd());
   RT_ATTR(k_qw, smem_qw());
   RT_ATTR(k_flip, smem_flip());
+  RT_ATTR(k_qwf, smem_qwf());
 #undef RT_ATTR
   return cudaSuccess;
 }
@@ -1007,10 +1056,9 @@ int launch_range_finder(const RFGroup& g, cudaStream_t st, int* status) {
   const int64_t stride = np + 1;
   int n = 0;
   if (g.total[STG_SAMPLE] > 0) {
-    k_sample<<<(unsigned)((g.total[STG_SAMPLE] + 255) / 256), 256, 0, st>>>(
+    k_sample_omega<<<(unsigned)((g.total[STG_SAMPLE] + 127) / 128), 128, 0, st>>>(
         g.probs, pre + STG_SAMPLE * stride, np, status);
-    k_omega<<<(unsigned)((g.total[STG_OMEGA] + 255) / 256), 256, 0, st>>>(g.probs, pre + STG_OMEGA * stride, np);
-    n += 2;
+    n += 1;
   }
   k_gather_sketch<<<grid_of(g.total[STG_GS]), 256, smem_gs(), st>>>(g.probs, pre + STG_GS * stride, np);
   ++n;
@@ -1031,9 +1079,16 @@ int launch_range_finder(const RFGroup& g, cudaStream_t st, int* status) {
   }
   k_wsvd<<<grid_of(g.total[STG_WSVD]), QR_THREADS, smem_wsvd(), st>>>(g.probs, pre + STG_WSVD * stride, np,
                                                                  status);
-  k_qw<<<grid_of(g.total[STG_QW]), 256, smem_qw(), st>>>(g.probs, pre + STG_QW * stride, np);
-  k_flip<<<grid_of(g.total[STG_FLIP]), 256, smem_flip(), st>>>(g.probs, pre + STG_FLIP * stride, np);
-  n += 3;
+  n += 1;
+  if (g.total[STG_QWF] > 0) {
+    k_qwf<<<grid_of(g.total[STG_QWF]), 512, smem_qwf(), st>>>(g.probs, pre + STG_QWF * stride, np);
+    ++n;
+  }
+  if (g.total[STG_QW] > 0) {
+    k_qw<<<grid_of(g.total[STG_QW]), 256, smem_qw(), st>>>(g.probs, pre + STG_QW * stride, np);
+    k_flip<<<grid_of(g.total[STG_FLIP]), 256, smem_flip(), st>>>(g.probs, pre + STG_FLIP * stride, np);
+    n += 2;
+  }
   return n;
 }
 

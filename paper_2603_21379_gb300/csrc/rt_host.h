@@ -21,10 +21,11 @@ constexpr int WS_MAXF = 24576;     // floats of the stacked R factors in the W-s
 constexpr int WS_LDT = 80;         // column stride of R^T in the Jacobi SVD (CMAX + 16)
 constexpr int WS_MAX_SWEEPS = 40;  // one-sided Jacobi sweeps before ST_NUMERIC
 constexpr int QW_TI = 32;          // rows per tile of U = Q W
+constexpr int QWF_MAX = 256;       // rows up to which U = Q W and its signs take one CTA
 
 enum Stage : int {
   STG_SAMPLE = 0, STG_GS, STG_QR1, STG_QR2, STG_QR3, STG_BTP, STG_BTQ, STG_WSVD, STG_QW, STG_FLIP,
-  STG_ZSUM, STG_OMEGA, STG_COUNT
+  STG_ZSUM, STG_QWF, STG_COUNT
 };
 
 // Device-side view of a planned group of range-finder problems.
