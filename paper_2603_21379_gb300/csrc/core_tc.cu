@@ -22,14 +22,15 @@
 //   warp 1      TMEM allocator and MMA issuer.  MMA1 per K step:
 //               D1 (n1 x 2 r2p) += X_s [hi(U_2) | lo(U_2)], A = X terms from
 //               TMEM (float32 X) or from the stage (bf16 X).  MMA2 per batch
-//               of 128 / r2p slabs: D2 (128 x 2 r1p) = T^T [hi(U_1) | lo(U_1)]
-//               with T^T terms in shared memory.
+//               of 128 / r2p slabs: D2 (64 x 128, rows a < r1) = U_1^T T with
+//               U_1^T (K-major A) and T of the batch (MN-major B, 128 columns)
+//               as bf16 terms in shared memory, three term products.
 //   warps 2-9   converters (float32 X): two groups of four quadrant warps take
 //               alternate stages; each thread splits one row into bf16 terms
 //               and stores them to a TMEM A buffer (tcgen05.st).
-//   warps 10-13 epilogue: T = D1_hi + D1_lo from TMEM, split into the two
-//               bf16 terms of T^T in shared memory; after MMA2, P_s = D2_hi +
-//               D2_lo to global memory.
+//   warps 10-13 epilogue: T = D1_hi + D1_lo from TMEM, each thread writes its
+//               row of T as bf16 hi/lo terms with 16-byte stores; after MMA2,
+//               P_s rows from the M = 64 accumulator to global memory.
 // Every mbarrier wait is bounded; on expiry the CTA records the timeout in the
 // status word, stops issuing work, drains and frees its TMEM, and returns.
 #include <cuda.h>
@@ -60,6 +61,18 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
   d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
   d |= (uint64_t)1 << 46;              // descriptor version
   d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+
+// Shared-memory matrix descriptor: MN-major, 128-byte swizzle (atoms of 8 K-rows x 128
+// bytes of MN); lbo = bytes between atoms along MN, sbo = bytes between 8-row groups
+// along K.
+__device__ __forceinline__ uint64_t mn128_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
   return d;
 }
 
@@ -160,21 +173,29 @@ static_assert(NS3 % 2 == 0 && NA % 2 == 0, "stages and A buffers must be even");
 
 template <int R1P, int R2P, int XM>
 struct Layout {
-  static constexpr int N1 = 2 * R2P;           // MMA1: X_s [hi(U2) | lo(U2)]
-  static constexpr int N2 = 2 * R1P;           // MMA2: T^T [hi(U1) | lo(U1)]
+  static constexpr int N1 = 2 * R2P;           // MMA1: X_s [hi(U2) | lo(U2)], M = 128 rows of the slab
   static constexpr bool XBF16 = (XM == 1);      // X stored as bf16: MMA1 reads the stage
   static constexpr int KCX = XBF16 ? 64 : 32;  // X columns per stage (128 bytes)
-  static constexpr int SPB = 128 / R2P;        // slabs per MMA2 batch (M = 128 rows of T^T)
+  static constexpr int SPB = 128 / R2P;        // slabs per MMA2 batch (N = 128 columns of T)
+  static constexpr int N2 = 128;               // MMA2: U_1^T [T of SPB slabs], M = 64 (rows a < r1)
   static constexpr int A_COL = 0;              // TMEM: NA A buffers of 32 columns (float32 X only)
   static constexpr int D1_COL = XBF16 ? 0 : NA * 32;
   static constexpr int D2_COL = D1_COL + 2 * N1;
   static constexpr int TMEM_USED = D2_COL + 2 * N2;
   static constexpr int TMEM_COLS = TMEM_USED <= 128 ? 128 : TMEM_USED <= 256 ? 256 : 512;
-  static constexpr int A2_TERM = 2 * 128 * 128;  // bytes of one term of T^T (K = 128 in two chunks)
+  // T of a batch as the MN-major B operand of MMA2: K = 128 rows (i) x N = 128 columns
+  // (slab j, column b), 128-byte swizzle, atoms of 8 rows x 64 columns; the 16 row
+  // atoms of a 64-column group are contiguous (1 KB apart), the two groups 16 KB apart.
+  static constexpr int BT_TERM = 128 * 128 * 2;
+  static constexpr int BT_NATOM = 16 * 1024;
+  // U_1^T as the K-major A operand of MMA2: 64 rows (a) x K = 128 (i), two 64-wide K chunks
+  static constexpr int AU_TERM = 64 * 128 * 2;
+  static_assert(TMEM_USED <= 512, "TMEM columns");
 };
 
 // Dynamic shared memory (1024-aligned):
-//   A2[2 terms][2 chunks][128][64 bf16] | B1[nkb][N1][64 bf16] | B2[2][N2][64 bf16] | stages[NS3][16 KB] | bars
+//   BT[2 terms][2 groups][16 atoms][8][64 bf16] | B1[nkb][N1][64 bf16] | AU[2 terms][2 chunks][64][64 bf16] |
+//   stages[NS3][16 KB] | bars
 template <int R1P, int R2P, int XM>
 __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_constant__ CUtensorMap tmap, Core2Args args) {
   using LY = Layout<R1P, R2P, XM>;
@@ -185,10 +206,10 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int nkc = (args.n2 + KCX - 1) / KCX;       // stages per slab
   const int nkb = (args.n2 + 63) / 64;             // 64-wide K chunks of B1
-  unsigned char* A2 = base;
-  unsigned char* B1 = A2 + 2 * LY::A2_TERM;
-  unsigned char* B2 = B1 + (size_t)nkb * N1 * 128;
-  unsigned char* stages = B2 + 2 * N2 * 128;
+  unsigned char* BT = base;
+  unsigned char* B1 = BT + 2 * LY::BT_TERM;
+  unsigned char* AU = B1 + (size_t)nkb * N1 * 128;
+  unsigned char* stages = AU + 2 * LY::AU_TERM;
   uint64_t* bars = reinterpret_cast<uint64_t*>(stages + NS3 * STAGE_BYTES);
   uint64_t* full = bars;
   uint64_t* empty = full + NS3;
@@ -222,7 +243,8 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // B1 = [hi(U2) | lo(U2)] (rows n < R2P: hi), B2 = [hi(U1) | lo(U1)], bf16, K-major, swizzled
+  // B1 = [hi(U2) | lo(U2)] (rows n < R2P: hi), AU = hi(U1)^T, lo(U1)^T (rows a >= r1 zero),
+  // bf16, K-major, swizzled
   for (int e = threadIdx.x; e < nkb * 64 * R2P; e += NTHREADS_V2) {
     const int k = e / R2P, col = e % R2P;
     unsigned short hi = 0, lo = 0;
@@ -230,16 +252,16 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
     *reinterpret_cast<unsigned short*>(B1 + sw_off16(col, k, N1)) = hi;
     *reinterpret_cast<unsigned short*>(B1 + sw_off16(R2P + col, k, N1)) = lo;
   }
-  for (int e = threadIdx.x; e < 128 * R1P; e += NTHREADS_V2) {
-    const int i = e / R1P, col = e % R1P;
+  for (int e = threadIdx.x; e < 128 * 64; e += NTHREADS_V2) {
+    const int i = e / 64, a = e % 64;
     unsigned short hi = 0, lo = 0;
-    if (i < n1 && col < r1) split1_bf16(__ldg(args.U1 + (int64_t)i * r1 + col), hi, lo);
-    *reinterpret_cast<unsigned short*>(B2 + sw_off16(col, i, N2)) = hi;
-    *reinterpret_cast<unsigned short*>(B2 + sw_off16(R1P + col, i, N2)) = lo;
+    if (i < n1 && a < r1) split1_bf16(__ldg(args.U1 + (int64_t)i * r1 + a), hi, lo);
+    *reinterpret_cast<unsigned short*>(AU + sw_off16(a, i, 64)) = hi;
+    *reinterpret_cast<unsigned short*>(AU + LY::AU_TERM + sw_off16(a, i, 64)) = lo;
   }
-  // T^T starts at zero: rows of a partial batch and columns i >= n1 stay zero
-  for (int e = threadIdx.x; e < 2 * LY::A2_TERM / 16; e += NTHREADS_V2)
-    reinterpret_cast<uint4*>(A2)[e] = make_uint4(0u, 0u, 0u, 0u);
+  // T starts at zero: rows i >= n1 and the columns of a partial batch stay zero
+  for (int e = threadIdx.x; e < 2 * LY::BT_TERM / 16; e += NTHREADS_V2)
+    reinterpret_cast<uint4*>(BT)[e] = make_uint4(0u, 0u, 0u, 0u);
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tmem_slot)),
                  "r"((uint32_t)LY::TMEM_COLS)
@@ -253,7 +275,7 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
   const uint32_t tmem = *tmem_slot;
   const uint32_t box_bytes = (uint32_t)n1 * 128;
   constexpr uint32_t idesc1 = idesc_bf16(128, N1);
-  constexpr uint32_t idesc2 = idesc_bf16(128, N2);
+  constexpr uint32_t idesc2 = idesc_bf16(64, N2) | (1u << 16);   // B (T) MN-major
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
@@ -274,7 +296,7 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       bool ok = true;
-      auto mma2 = [&](int64_t g) -> bool {   // P of batch g: D2 = T^T [hi(U1) | lo(U1)], T^T = hi + lo
+      auto mma2 = [&](int64_t g) -> bool {   // P of batch g: D2 = U1^T T (three products of the bf16 terms)
         const int b = (int)(g & 1);
         const uint32_t ph = (uint32_t)((g >> 1) & 1);
         if (!mbar_wait(&tready[b], ph, abort_flag, args.status)) return false;
@@ -282,13 +304,16 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
         fence_after();
         const uint32_t dcol = tmem + LY::D2_COL + b * N2;
 #pragma unroll
-        for (int term = 0; term < 2; ++term)
+        for (int kk = 0; kk < 8; ++kk) {     // K = 128 in steps of 16
 #pragma unroll
-          for (int kk = 0; kk < 8; ++kk) {   // K = 128 in steps of 16
-            const uint32_t aaddr = saddr(A2 + term * LY::A2_TERM + (kk >> 2) * 128 * 128 + (kk & 3) * 32);
-            const uint32_t baddr = saddr(B2 + (kk >> 2) * N2 * 128 + (kk & 3) * 32);
-            mma_bf16_ss(dcol, sw128_desc(aaddr), sw128_desc(baddr), idesc2, (term | kk) ? 1u : 0u);
+          for (int pr = 0; pr < 3; ++pr) {   // (hi U1, hi T), (hi U1, lo T), (lo U1, hi T)
+            const int ta = pr == 2 ? 1 : 0, tb = pr == 1 ? 1 : 0;
+            const uint32_t aaddr = saddr(AU + ta * LY::AU_TERM + (kk >> 2) * 64 * 128 + (kk & 3) * 32);
+            const uint32_t baddr = saddr(BT + tb * LY::BT_TERM + kk * 2048);
+            mma_bf16_ss(dcol, sw128_desc(aaddr), mn128_desc(baddr, LY::BT_NATOM, 1024), idesc2,
+                        (kk | pr) ? 1u : 0u);
           }
+        }
         mma_commit(&d2full[b]);
         return true;
       };
@@ -383,23 +408,37 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
       bool ok = __all_sync(0xffffffffu, mbar_wait(&d2full[bb], ph, abort_flag, args.status));
       if (!ok) return false;
       fence_after();
-      uint32_t d[N2];
+      // M = 64 accumulator: row a in TMEM lane 32 (a / 16) + a % 16, so warp q holds rows
+      // a = 16 q + lane (lane < 16); column n = j R2P + b of slab j
+      if (16 * q < r1) {
+        const int a = 16 * q + lane;
 #pragma unroll
-      for (int cc = 0; cc < N2 / 8; ++cc)
-        tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D2_COL + bb * N2 + cc * 8, d + 8 * cc);
-      tmem_wait_ld();
+        for (int j = 0; j < SPB; ++j) {
+          uint32_t d[R2P];
+#pragma unroll
+          for (int cc = 0; cc < R2P / 8; ++cc)
+            tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D2_COL + bb * N2 + j * R2P + cc * 8, d + 8 * cc);
+          tmem_wait_ld();
+          const int64_t t = g * SPB + j;
+          if (lane < 16 && a < r1 && t < nmine) {
+            float* Pout = args.P + ((blockIdx.x + t * gridDim.x) * (int64_t)r1 + a) * r2;
+            if ((r2 & 3) == 0) {
+#pragma unroll
+              for (int b = 0; b < R2P; b += 4)
+                if (b < r2)
+                  *reinterpret_cast<float4*>(Pout + b) = make_float4(__uint_as_float(d[b]), __uint_as_float(d[b + 1]),
+                                                                      __uint_as_float(d[b + 2]), __uint_as_float(d[b + 3]));
+            } else {
+#pragma unroll
+              for (int b = 0; b < R2P; ++b)
+                if (b < r2) Pout[b] = __uint_as_float(d[b]);
+            }
+          }
+        }
+      }
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&d2empty[bb]);
-      const int m = q * 32 + lane;                   // row of D2 = (slab j of the batch, column b of P)
-      const int j = m / R2P, b = m % R2P;
-      const int64_t t = g * SPB + j;
-      if (t < nmine && b < r2) {
-        float* Pout = args.P + (blockIdx.x + t * gridDim.x) * (int64_t)r1 * r2;
-#pragma unroll
-        for (int a = 0; a < R1P; ++a)
-          if (a < r1) Pout[a * r2 + b] = __uint_as_float(d[a]) + __uint_as_float(d[R1P + a]);
-      }
       return true;
     };
     bool ok = true;
@@ -420,18 +459,22 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
       const int64_t g = t / SPB;
       // first slab of a batch: P of the previous batch (frees T^T)
       if (j == 0 && g >= 1 && !(ok = read_p(g - 1))) break;
-      // T^T rows (j, b), column i: hi and lo terms (rows i >= n1 stay zero)
+      // row i of T (columns b of slab j) into the MN-major B operand: 8 consecutive
+      // columns per 16-byte store, hi and lo terms.  Rows i >= n1 stay zero (for bf16 X
+      // those D1 rows come from stage rows the TMA box does not cover).
       if (i < n1) {
+        const int atom = (i >> 3) * 1024 + (i & 7) * 128;
 #pragma unroll
-        for (int b = 0; b < R2P; b += 2) {
-          uint32_t hi, lo;
-          split_bf16(__uint_as_float(d[b]) + __uint_as_float(d[R2P + b]),
-                     __uint_as_float(d[b + 1]) + __uint_as_float(d[R2P + b + 1]), hi, lo);
-          const int off0 = sw_off16(j * R2P + b, i, 128), off1 = sw_off16(j * R2P + b + 1, i, 128);
-          *reinterpret_cast<unsigned short*>(A2 + off0) = (unsigned short)(hi & 0xffffu);
-          *reinterpret_cast<unsigned short*>(A2 + off1) = (unsigned short)(hi >> 16);
-          *reinterpret_cast<unsigned short*>(A2 + LY::A2_TERM + off0) = (unsigned short)(lo & 0xffffu);
-          *reinterpret_cast<unsigned short*>(A2 + LY::A2_TERM + off1) = (unsigned short)(lo >> 16);
+        for (int b0 = 0; b0 < R2P; b0 += 8) {
+          uint32_t hi[4], lo[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            split_bf16(__uint_as_float(d[b0 + 2 * e]) + __uint_as_float(d[R2P + b0 + 2 * e]),
+                       __uint_as_float(d[b0 + 2 * e + 1]) + __uint_as_float(d[R2P + b0 + 2 * e + 1]), hi[e], lo[e]);
+          const int n = j * R2P + b0;
+          const int off = (n >> 6) * LY::BT_NATOM + atom + ((((n & 63) >> 3) ^ (i & 7)) << 4);
+          *reinterpret_cast<uint4*>(BT + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+          *reinterpret_cast<uint4*>(BT + LY::BT_TERM + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
         }
       }
       if (j == SPB - 1 || t == nmine - 1) {
@@ -456,7 +499,7 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
 template <int R1P, int R2P, int XM>
 static size_t smem_bytes(int nkb) {
   using LY = Layout<R1P, R2P, XM>;
-  return 1024 + 2 * (size_t)LY::A2_TERM + (size_t)nkb * LY::N1 * 128 + 2 * (size_t)LY::N2 * 128 +
+  return 1024 + 2 * (size_t)LY::BT_TERM + (size_t)nkb * LY::N1 * 128 + 2 * (size_t)LY::AU_TERM +
          (size_t)NS3 * STAGE_BYTES + 8 * (2 * NS3 + 2 * NA + 11) + 16;
 }
 
