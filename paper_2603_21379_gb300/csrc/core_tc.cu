@@ -163,15 +163,14 @@ constexpr int NCONV = 8;                       // converter warps: two groups of
 constexpr int W_CONV0 = 2, W_EPI0 = W_CONV0 + NCONV;
 constexpr int NWARPS = W_EPI0 + 4;
 constexpr int NTHREADS_V2 = NWARPS * 32;       // 448
-constexpr int NS3 = 6;                         // stages of X
 // Converter group g takes the chunks c with c % 2 == g.  Parity waits are only
 // safe when one consumer group owns every use of a barrier (a second group
 // could otherwise test a phase two behind and pass), so the number of stages
-// and of TMEM A buffers must be even: stage c % NS3 and buffer c % NA then
+// and of TMEM A buffers must be even: stage c % NS and buffer c % NA then
 // always belong to the same group.
-static_assert(NS3 % 2 == 0 && NA % 2 == 0, "stages and A buffers must be even");
+static_assert(NA % 2 == 0, "A buffers must be even");
 
-template <int R1P, int R2P, int XM>
+template <int R2P, int XM>
 struct Layout {
   static constexpr int N1 = 2 * R2P;           // MMA1: X_s [hi(U2) | lo(U2)], M = 128 rows of the slab
   static constexpr bool XBF16 = (XM == 1);      // X stored as bf16: MMA1 reads the stage
@@ -181,7 +180,11 @@ struct Layout {
   static constexpr int A_COL = 0;              // TMEM: NA A buffers of 32 columns (float32 X only)
   static constexpr int D1_COL = XBF16 ? 0 : NA * 32;
   static constexpr int D2_COL = D1_COL + 2 * N1;
-  static constexpr int TMEM_USED = D2_COL + 2 * N2;
+  static constexpr int ND2 = (D2_COL + 2 * N2 <= 512) ? 2 : 1;   // D2 buffers
+  static constexpr int TMEM_USED = D2_COL + ND2 * N2;
+  static constexpr int NS = (R2P == 64) ? 4 : 6;                 // X stages (shared-memory budget)
+  static_assert(NS % 2 == 0, "stages must be even");
+  static constexpr int TCH = R2P < 32 ? R2P : 32;                // T columns per epilogue round
   static constexpr int TMEM_COLS = TMEM_USED <= 128 ? 128 : TMEM_USED <= 256 ? 256 : 512;
   // T of a batch as the MN-major B operand of MMA2: K = 128 rows (i) x N = 128 columns
   // (slab j, column b), 128-byte swizzle, atoms of 8 rows x 64 columns; the 16 row
@@ -196,9 +199,10 @@ struct Layout {
 // Dynamic shared memory (1024-aligned):
 //   BT[2 terms][2 groups][16 atoms][8][64 bf16] | B1[nkb][N1][64 bf16] | AU[2 terms][2 chunks][64][64 bf16] |
 //   stages[NS3][16 KB] | bars
-template <int R1P, int R2P, int XM>
+template <int R2P, int XM>
 __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_constant__ CUtensorMap tmap, Core2Args args) {
-  using LY = Layout<R1P, R2P, XM>;
+  using LY = Layout<R2P, XM>;
+  constexpr int NS3 = LY::NS, ND2 = LY::ND2;
   constexpr bool XBF16 = LY::XBF16;
   constexpr bool XLO = (XM == 0);                  // float32 X keeps its lo term
   constexpr int N1 = LY::N1, N2 = LY::N2, KCX = LY::KCX, SPB = LY::SPB;
@@ -297,8 +301,8 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
     if (lane == 0) {
       bool ok = true;
       auto mma2 = [&](int64_t g) -> bool {   // P of batch g: D2 = U1^T T (three products of the bf16 terms)
-        const int b = (int)(g & 1);
-        const uint32_t ph = (uint32_t)((g >> 1) & 1);
+        const int b = (int)(g % ND2);
+        const uint32_t ph = (uint32_t)((g / ND2) & 1);
         if (!mbar_wait(&tready[b], ph, abort_flag, args.status)) return false;
         if (!mbar_wait(&d2empty[b], ph ^ 1, abort_flag, args.status)) return false;
         fence_after();
@@ -403,8 +407,8 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
     const int q = warp & 3;
     const int i = q * 32 + lane;                    // slab row = K index of MMA2
     auto read_p = [&](int64_t g) -> bool {          // P of the slabs of batch g
-      const int bb = (int)(g & 1);
-      const uint32_t ph = (uint32_t)((g >> 1) & 1);
+      const int bb = (int)(g % ND2);
+      const uint32_t ph = (uint32_t)((g / ND2) & 1);
       bool ok = __all_sync(0xffffffffu, mbar_wait(&d2full[bb], ph, abort_flag, args.status));
       if (!ok) return false;
       fence_after();
@@ -414,24 +418,28 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
         const int a = 16 * q + lane;
 #pragma unroll
         for (int j = 0; j < SPB; ++j) {
-          uint32_t d[R2P];
-#pragma unroll
-          for (int cc = 0; cc < R2P / 8; ++cc)
-            tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D2_COL + bb * N2 + j * R2P + cc * 8, d + 8 * cc);
-          tmem_wait_ld();
           const int64_t t = g * SPB + j;
-          if (lane < 16 && a < r1 && t < nmine) {
-            float* Pout = args.P + ((blockIdx.x + t * gridDim.x) * (int64_t)r1 + a) * r2;
-            if ((r2 & 3) == 0) {
 #pragma unroll
-              for (int b = 0; b < R2P; b += 4)
-                if (b < r2)
-                  *reinterpret_cast<float4*>(Pout + b) = make_float4(__uint_as_float(d[b]), __uint_as_float(d[b + 1]),
-                                                                      __uint_as_float(d[b + 2]), __uint_as_float(d[b + 3]));
-            } else {
+          for (int b0 = 0; b0 < R2P; b0 += LY::TCH) {
+            uint32_t d[LY::TCH];
 #pragma unroll
-              for (int b = 0; b < R2P; ++b)
-                if (b < r2) Pout[b] = __uint_as_float(d[b]);
+            for (int cc = 0; cc < LY::TCH / 8; ++cc)
+              tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D2_COL + bb * N2 + j * R2P + b0 + cc * 8, d + 8 * cc);
+            tmem_wait_ld();
+            if (lane < 16 && a < r1 && t < nmine) {
+              float* Pout = args.P + ((blockIdx.x + t * gridDim.x) * (int64_t)r1 + a) * r2 + b0;
+              if ((r2 & 3) == 0) {
+#pragma unroll
+                for (int b = 0; b < LY::TCH; b += 4)
+                  if (b0 + b < r2)
+                    *reinterpret_cast<float4*>(Pout + b) =
+                        make_float4(__uint_as_float(d[b]), __uint_as_float(d[b + 1]), __uint_as_float(d[b + 2]),
+                                    __uint_as_float(d[b + 3]));
+              } else {
+#pragma unroll
+                for (int b = 0; b < LY::TCH; ++b)
+                  if (b0 + b < r2) Pout[b] = __uint_as_float(d[b]);
+              }
             }
           }
         }
@@ -447,36 +455,49 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
       ok = __all_sync(0xffffffffu, mbar_wait(&d1full[db], (uint32_t)((t >> 1) & 1), abort_flag, args.status));
       if (!ok) break;
       fence_after();
-      uint32_t d[N1];
-#pragma unroll
-      for (int cc = 0; cc < N1 / 8; ++cc)
-        tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D1_COL + db * N1 + cc * 8, d + 8 * cc);
-      tmem_wait_ld();
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&d1empty[db]);
       const int j = (int)(t % SPB);
       const int64_t g = t / SPB;
-      // first slab of a batch: P of the previous batch (frees T^T)
-      if (j == 0 && g >= 1 && !(ok = read_p(g - 1))) break;
-      // row i of T (columns b of slab j) into the MN-major B operand: 8 consecutive
-      // columns per 16-byte store, hi and lo terms.  Rows i >= n1 stay zero (for bf16 X
-      // those D1 rows come from stage rows the TMA box does not cover).
-      if (i < n1) {
-        const int atom = (i >> 3) * 1024 + (i & 7) * 128;
+      // Row i of T (columns b of slab j) into the MN-major B operand, TCH columns per
+      // round: T = D1_hi + D1_lo, 8 consecutive columns per 16-byte store, hi and lo
+      // terms.  Rows i >= n1 stay zero (for bf16 X those D1 rows come from stage rows
+      // the TMA box does not cover).  The first slab of a batch first reads P of the
+      // previous batch (which frees T).
+      bool first = true;
 #pragma unroll
-        for (int b0 = 0; b0 < R2P; b0 += 8) {
-          uint32_t hi[4], lo[4];
+      for (int h0 = 0; h0 < R2P; h0 += LY::TCH) {
+        uint32_t dh[LY::TCH], dl[LY::TCH];
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            split_bf16(__uint_as_float(d[b0 + 2 * e]) + __uint_as_float(d[R2P + b0 + 2 * e]),
-                       __uint_as_float(d[b0 + 2 * e + 1]) + __uint_as_float(d[R2P + b0 + 2 * e + 1]), hi[e], lo[e]);
-          const int n = j * R2P + b0;
-          const int off = (n >> 6) * LY::BT_NATOM + atom + ((((n & 63) >> 3) ^ (i & 7)) << 4);
-          *reinterpret_cast<uint4*>(BT + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-          *reinterpret_cast<uint4*>(BT + LY::BT_TERM + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        for (int cc = 0; cc < LY::TCH / 8; ++cc) {
+          tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D1_COL + db * N1 + h0 + cc * 8, dh + 8 * cc);
+          tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D1_COL + db * N1 + R2P + h0 + cc * 8, dl + 8 * cc);
+        }
+        tmem_wait_ld();
+        if (h0 + LY::TCH >= R2P) {
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&d1empty[db]);
+        }
+        if (first) {
+          first = false;
+          if (j == 0 && g >= 1 && !(ok = read_p(g - 1))) break;
+        }
+        if (i < n1) {
+          const int atom = (i >> 3) * 1024 + (i & 7) * 128;
+#pragma unroll
+          for (int b0 = 0; b0 < LY::TCH; b0 += 8) {
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              split_bf16(__uint_as_float(dh[b0 + 2 * e]) + __uint_as_float(dl[b0 + 2 * e]),
+                         __uint_as_float(dh[b0 + 2 * e + 1]) + __uint_as_float(dl[b0 + 2 * e + 1]), hi[e], lo[e]);
+            const int n = j * R2P + h0 + b0;
+            const int off = (n >> 6) * LY::BT_NATOM + atom + ((((n & 63) >> 3) ^ (i & 7)) << 4);
+            *reinterpret_cast<uint4*>(BT + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(BT + LY::BT_TERM + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+          }
         }
       }
+      if (!ok) break;
       if (j == SPB - 1 || t == nmine - 1) {
         fence_proxy_async();
         __syncwarp();
@@ -496,20 +517,20 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
 }
 
 // ------------------------------------------------------------------ host side
-template <int R1P, int R2P, int XM>
+template <int R2P, int XM>
 static size_t smem_bytes(int nkb) {
-  using LY = Layout<R1P, R2P, XM>;
+  using LY = Layout<R2P, XM>;
   return 1024 + 2 * (size_t)LY::BT_TERM + (size_t)nkb * LY::N1 * 128 + 2 * (size_t)LY::AU_TERM +
-         (size_t)NS3 * STAGE_BYTES + 8 * (2 * NS3 + 2 * NA + 11) + 16;
+         (size_t)LY::NS * STAGE_BYTES + 8 * (2 * LY::NS + 2 * NA + 11) + 16;
 }
 
-template <int R1P, int R2P, int XM>
+template <int R2P, int XM>
 static int launch_v3(const CUtensorMap& map, const Core2Args& a, int grid, cudaStream_t st) {
   const int nkb = (a.n2 + 63) / 64;
-  const size_t sm = smem_bytes<R1P, R2P, XM>(nkb);
+  const size_t sm = smem_bytes<R2P, XM>(nkb);
   if (sm > 227 * 1024) return -1;
-  cudaFuncSetAttribute(k_core2_tc<R1P, R2P, XM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_core2_tc<R1P, R2P, XM><<<grid, NTHREADS_V2, sm, st>>>(map, a);
+  cudaFuncSetAttribute(k_core2_tc<R2P, XM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_core2_tc<R2P, XM><<<grid, NTHREADS_V2, sm, st>>>(map, a);
   return 1;
 }
 
@@ -520,16 +541,16 @@ static int launch_v3(const CUtensorMap& map, const Core2Args& a, int grid, cudaS
 // xmode: 0 float32 X split into two bf16 terms, 1 bfloat16 X, 2 float32 X
 // rounded to one bf16 term.
 int launch_core2_tc(int xmode, const void* X, int64_t S, int n1, int n2, const float* U1, int r1, const float* U2,
-                    int r2, float* P, int* status, cudaStream_t st) {
+                    int r2, float* P, int* status, cudaStream_t st, int max_ctas) {
   using namespace tc;
   if (xmode < 0 || xmode > 2) return 0;
   const bool xbf16 = (xmode == 1);
   const int esz = xbf16 ? 2 : 4;
-  if (n1 < 1 || n1 > ROWS || n2 < 1 || ((int64_t)n2 * esz) % 16 != 0 || r1 < 1 || r1 > 32 || r2 < 1 || r2 > 32)
+  if (n1 < 1 || n1 > ROWS || n2 < 1 || ((int64_t)n2 * esz) % 16 != 0 || r1 < 1 || r1 > 64 || r2 < 1 || r2 > 64)
     return 0;
   if ((reinterpret_cast<uintptr_t>(X) & 15u) != 0) return 0;
   if (S * (int64_t)n1 >= ((int64_t)1 << 31)) return 0;
-  tma::EncodeTiledFn enc = tma::encode_tiled_fn();
+  EncodeTiledFn enc = encode_tiled_fn();
   if (!enc) return 0;
   CUtensorMap map;
   const cuuint64_t gdim[2] = {(cuuint64_t)n2, (cuuint64_t)(S * n1)};
@@ -543,21 +564,19 @@ int launch_core2_tc(int xmode, const void* X, int64_t S, int n1, int n2, const f
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = (int)std::min<int64_t>(S, nsm);
+  int64_t grid = std::min<int64_t>(S, nsm);
+  if (max_ctas > 0) grid = std::min<int64_t>(grid, max_ctas);
   Core2Args a{X, U1, U2, P, S, n1, n2, r1, r2, status};
-  const int r1p = r1 <= 8 ? 8 : r1 <= 16 ? 16 : 32;
-  const int r2p = r2 <= 8 ? 8 : r2 <= 16 ? 16 : 32;
+  const int r2p = r2 <= 8 ? 8 : r2 <= 16 ? 16 : r2 <= 32 ? 32 : 64;
   int rc = 0;
-#define RT_TC_CASE(A, B)                                                       \
-  if (r1p == A && r2p == B) {                                                  \
-    rc = xmode == 1   ? launch_v3<A, B, 1>(map, a, grid, st)                   \
-         : xmode == 2 ? launch_v3<A, B, 2>(map, a, grid, st)                   \
-                      : launch_v3<A, B, 0>(map, a, grid, st);                  \
-    return rc < 0 ? 0 : rc;                                                    \
+#define RT_TC_CASE(B)                                                            \
+  if (r2p == B) {                                                                \
+    rc = xmode == 1   ? launch_v3<B, 1>(map, a, (int)grid, st)                   \
+         : xmode == 2 ? launch_v3<B, 2>(map, a, (int)grid, st)                   \
+                      : launch_v3<B, 0>(map, a, (int)grid, st);                  \
+    return rc < 0 ? 0 : rc;                                                      \
   }
-  RT_TC_CASE(8, 8) RT_TC_CASE(8, 16) RT_TC_CASE(8, 32)
-  RT_TC_CASE(16, 8) RT_TC_CASE(16, 16) RT_TC_CASE(16, 32)
-  RT_TC_CASE(32, 8) RT_TC_CASE(32, 16) RT_TC_CASE(32, 32)
+  RT_TC_CASE(8) RT_TC_CASE(16) RT_TC_CASE(32) RT_TC_CASE(64)
 #undef RT_TC_CASE
   return 0;
 }

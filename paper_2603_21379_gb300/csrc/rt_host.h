@@ -68,7 +68,7 @@ cudaError_t core_init_attributes();
 // n1 x n2.  X float32 (xbf16 = 0: two bf16 terms) or bfloat16 (xbf16 = 1).
 // Returns 0 when the shape is unsupported.
 int launch_core2_tc(int xmode, const void* X, int64_t S, int n1, int n2, const float* U1, int r1, const float* U2,
-                    int r2, float* P, int* status, cudaStream_t st);
+                    int r2, float* P, int* status, cudaStream_t st, int max_ctas = 0);
 
 // ---- H-Tucker (ht_kernels.cu)
 struct TransferJob {     // B_S(i, j, k) = sum_{a,b} U_S[a n_r + b][i] U_l[a][j] U_r[b][k]

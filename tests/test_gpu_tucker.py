@@ -210,6 +210,23 @@ def test_core_tensor_core_pass_odd_slab_height(rt):
     assert np.abs(to_np(G) - Gr).max() <= 1e-5 * np.abs(Gr).max()
 
 
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_core_tensor_core_pass_ranks_up_to_64(rt, dtype):
+    # the tensor-core pass with r_{d-1} = 50 (M = 64 accumulator rows) and r_d = 60
+    # (64-column T, one D2 buffer, four X stages)
+    rs = np.random.default_rng(16)
+    shape, ranks = (3, 4, 100, 96), (3, 4, 50, 60)
+    X = rs.standard_normal(shape).astype(np.float32)
+    Xd = torch.from_numpy(X).cuda()
+    if dtype == "bf16":
+        Xd = Xd.to(torch.bfloat16)
+        X = Xd.float().cpu().numpy()
+    U = [np.linalg.qr(rs.standard_normal((n, k)))[0].astype(np.float32) for n, k in zip(shape, ranks)]
+    G = rt.rtucker_core(Xd, [torch.from_numpy(u).cuda() for u in U])
+    Gr = tucker.multi_ttm_t(X.astype(np.float64), [u.astype(np.float64) for u in U])
+    assert np.abs(to_np(G) - Gr).max() <= 1e-5 * np.abs(Gr).max()
+
+
 def test_core_wide_rho_ragged_tiles(rt):
     # order 4: the tensor-core pass contracts modes 3, 4 (P has 12*12 = 144 trailing
     # entries per slab), then the register-tiled FP32 contraction runs twice with ragged
