@@ -69,7 +69,14 @@ typedef struct {
   int32_t prec;        /* rt_prec                                              */
   int32_t use_graph;   /* must be 0: CUDA-graph replay is not provided yet
                           (nonzero returns RT_ENOTSUP)                           */
-  int32_t reserved[6]; /* must be zero                                          */
+  int32_t overlap;     /* rtucker_decompose only: 1 runs the pass over X on the
+                          QR factors Q of the last two modes (U_k = Q_k W_k) on
+                          the tensor cores while the SVD / W / U part of their
+                          range finder runs beside it on a second stream, then
+                          contracts with W; 0 (default) waits for U.  Same
+                          result up to rounding.  Shapes the tensor-core pass
+                          cannot take ignore it.                                 */
+  int32_t reserved[5]; /* must be zero                                          */
 } rt_options;
 
 /* ----------------------------------------------------------- handle
@@ -93,10 +100,12 @@ size_t rt_workspace_bytes(rt_handle h);
  * times.  rt_get_timing synchronises the stream and writes, for stage
  * i < min(nmax, RT_NSTAGES), the total milliseconds ms[i] and the number of
  * timed intervals count[i] since the last reset (reset = 1 clears them).
- * Stages: 0 range finder (S1-S6), 1 first contraction of the core (the pass
- * over X), 2 remaining core contractions, 3 H-Tucker transfer tensors,
- * 4 H-Tucker root pass (the pass over X). */
-#define RT_NSTAGES 5
+ * Stages: 0 range finder (S1-S6; S1-S5 and the B-step of S6 when stage 5 is
+ * split off), 1 first contraction of the core (the pass over X), 2 remaining
+ * core contractions, 3 H-Tucker transfer tensors, 4 H-Tucker root pass (the
+ * pass over X), 5 SVD/W/U part of S6 when it runs on the handle's second stream
+ * beside the pass over X (timed on that stream; overlaps stage 1). */
+#define RT_NSTAGES 6
 rt_status rt_set_timing(rt_handle h, int enable);
 rt_status rt_get_timing(rt_handle h, double* ms, int64_t* count, int nmax, int reset);
 

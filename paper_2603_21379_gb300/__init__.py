@@ -17,7 +17,7 @@ import os
 import torch
 
 __all__ = [
-    "load_library", "library_path", "RtError",
+    "load_library", "library_path", "RtError", "sync",
     "rtucker_indices", "rtucker_sketch", "rtucker_factors", "rtucker_core", "rtucker_decompose",
     "rtucker_decompose_host", "rtucker_decompose_batched", "rtucker_relerr",
     "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "last_launch_count", "workspace_bytes",
@@ -38,7 +38,8 @@ class RtError(RuntimeError):
 
 
 class _Options(ctypes.Structure):
-    _fields_ = [("prec", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+    _fields_ = [("prec", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("overlap", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
 
 
 _lib = None
@@ -129,6 +130,14 @@ def _check(h, st):
         raise RtError(st, load_library().rt_last_error(h).decode())
 
 
+def sync(device=None):
+    """Wait for the library's work on the current stream and raise RtError if a
+    kernel reported a device-side failure (bounded wait ran out, numerical
+    breakdown, failed check) since the last sync."""
+    h = _handle(device)
+    _check(h, load_library().rt_sync(h))
+
+
 def _i64(vals):
     vals = [int(v) for v in vals]
     return (ctypes.c_int64 * len(vals))(*vals)
@@ -176,7 +185,7 @@ def workspace_bytes(device=None):
     return int(load_library().rt_workspace_bytes(_handle(device)))
 
 
-STAGES = ("range_finder", "core_x_pass", "core_rest", "ht_transfer", "ht_root_pass")
+STAGES = ("range_finder", "core_x_pass", "core_rest", "ht_transfer", "ht_root_pass", "range_finder_tail")
 
 
 def set_timing(enable, device=None):
@@ -248,14 +257,16 @@ def rtucker_factors(X, r, p, s=None, seed=0, with_sigma=False):
 _PREC = {"fp32": 0, "bf16": 1}
 
 
-def _opts(prec):
-    """rt_options for a precision form, or None (defaults) for "fp32"."""
+def _opts(prec, overlap=False):
+    """rt_options for a precision form (and the overlapped core schedule), or None
+    (defaults)."""
     if prec not in _PREC:
         raise ValueError("prec must be 'fp32' or 'bf16'")
-    if prec == "fp32":
+    if prec == "fp32" and not overlap:
         return None
     o = _Options()
     o.prec = _PREC[prec]
+    o.overlap = 1 if overlap else 0
     return ctypes.byref(o)
 
 
@@ -276,9 +287,11 @@ def rtucker_core(X, U, prec="fp32"):
     return G
 
 
-def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32"):
+def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32", overlap=False):
     """S1-S7: Sub-R-HOSVD; returns (G, [U_k]).  ``out`` = (Uflat, G) reuses buffers;
-    ``prec`` "fp32" (default) or "bf16" (the BF16 compute form of the core pass)."""
+    ``prec`` "fp32" (default) or "bf16" (the BF16 compute form of the core pass);
+    ``overlap`` runs the pass over X on the QR factors beside the SVD part of the
+    range finder (see rt_options.overlap)."""
     lib = load_library()
     dt, d, n = _tensor_args(X)
     r = _as_list(r, d)
@@ -290,7 +303,7 @@ def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32"):
     h = _handle(X.device.index)
     sp = _i64(_as_list(s, d)) if s is not None else None
     _check(h, lib.rtucker_decompose(h, _ptr(X), dt, d, _i64(n), _i32(r), int(p), sp, ctypes.c_uint64(seed),
-                                    _opts(prec), _ptr(U), _ptr(G)))
+                                    _opts(prec, overlap), _ptr(U), _ptr(G)))
     return G, _split(U, n, r)
 
 

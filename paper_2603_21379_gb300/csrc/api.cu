@@ -37,6 +37,9 @@ struct rt_handle_s {
   int launches = 0;
   char* hc_buf = nullptr;      // device buffers of rtucker_decompose_host
   size_t hc_bytes = 0;
+  // second stream for work that overlaps the pass over X, with fork/join events
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // stage timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;              // free events
@@ -80,17 +83,18 @@ cudaEvent_t pool_event(rt_handle h) {
 struct StageTimer {
   rt_handle h;
   int stage;
+  cudaStream_t st;
   cudaEvent_t a = nullptr;
-  StageTimer(rt_handle hh, int s) : h(hh), stage(s) {
+  StageTimer(rt_handle hh, int s, cudaStream_t stream = nullptr) : h(hh), stage(s), st(stream ? stream : hh->stream) {
     if (h->timing) {
       a = pool_event(h);
-      cudaEventRecord(a, h->stream);
+      cudaEventRecord(a, st);
     }
   }
   ~StageTimer() {
     if (a) {
       cudaEvent_t b = pool_event(h);
-      cudaEventRecord(b, h->stream);
+      cudaEventRecord(b, st);
       h->ev_open.push_back({stage, {a, b}});
     }
   }
@@ -158,7 +162,7 @@ struct ProbSpec {
 
 struct ProbPlan {
   RFProb q;
-  size_t o_idx, o_off, o_Om, o_Yt, o_Zp, o_zcnt, o_Q, o_Rb, o_Q2, o_Bp, o_Rc, o_W, o_sig, o_keys, o_U;
+  size_t o_idx, o_off, o_Om, o_Yt, o_Zp, o_zcnt, o_Q, o_Rb, o_Q2, o_Bp, o_Rc, o_W, o_Wsg, o_sig, o_keys, o_U;
   int64_t units[STG_COUNT];
 };
 
@@ -226,6 +230,7 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   pp.o_Bp = bump.take((size_t)q.nbi * s * c * 4);
   pp.o_Rc = bump.take((size_t)q.nsc * c * c * 4);
   pp.o_W = bump.take((size_t)c * c * 4);
+  pp.o_Wsg = bump.take((size_t)c * ps.r * 4);
   pp.o_sig = bump.take((size_t)c * 4);
   pp.o_keys = bump.take((size_t)ps.r * 8);
   pp.o_U = ps.U ? (size_t)-1 : bump.take((size_t)nS * ps.r * 4);
@@ -263,6 +268,7 @@ void bind_problem(ProbPlan& pp, char* ws) {
   q.Bp = reinterpret_cast<float*>(ws + pp.o_Bp);
   q.Rc = reinterpret_cast<float*>(ws + pp.o_Rc);
   q.W = reinterpret_cast<float*>(ws + pp.o_W);
+  q.Wsg = reinterpret_cast<float*>(ws + pp.o_Wsg);
   q.sigma = reinterpret_cast<float*>(ws + pp.o_sig);
   q.keys = reinterpret_cast<unsigned long long*>(ws + pp.o_keys);
   if (!q.U) q.U = reinterpret_cast<float*>(ws + pp.o_U);
@@ -387,7 +393,7 @@ rt_status check_opts(rt_handle h, const rt_options* opt) {
   if (!opt) return RT_OK;
   if (opt->prec != RT_PREC_FP32 && opt->prec != RT_PREC_BF16) return fail(h, RT_EINVAL, "unknown precision");
   if (opt->use_graph) return fail(h, RT_ENOTSUP, "CUDA-graph replay is not provided");
-  for (int i = 0; i < 6; ++i)
+  for (int i = 0; i < 5; ++i)
     if (opt->reserved[i]) return fail(h, RT_EINVAL, "reserved option fields must be zero");
   return RT_OK;
 }
@@ -440,8 +446,8 @@ size_t core_buffer_floats(int d, const int64_t* n, const int32_t* r) {
   return best;
 }
 
-// Core kernel selection: 1 = tensor-core pass over X when the shape allows
-// (default), 0 = FFMA chain only (environment variable RT_CORE_MODE).
+// Core kernel selection (environment variable RT_CORE_MODE): 1 = tensor-core pass
+// over X when the shape allows (default), 0 = FFMA chain only.
 int core_mode() {
   static int mode = [] {
     const char* e = getenv("RT_CORE_MODE");
@@ -500,6 +506,77 @@ int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_
     adt = DT_F32;
     ping ^= 1;
   }
+  return nl;
+}
+
+rt_status ensure_side(rt_handle h) {
+  if (h->side) return RT_OK;
+  RT_CUDA(h, cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+  RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  return RT_OK;
+}
+
+// The pass over X can run on the QR factors Q_{d-2}, Q_{d-1} (c = r + p columns):
+// U_k = Q_k W_k (W_k with the sign rule's signs), so
+//     X x_{d-2} U^T x_{d-1} U^T = (X x_{d-2} Q^T x_{d-1} Q^T) x_{d-2} W^T x_{d-1} W^T,
+// and the SVD/W/U part of the range finder runs beside it on a second stream.
+bool overlap_core_ok(const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r, int32_t p) {
+  if (core_mode() < 1 || d < 2) return false;
+  if (dtype != RT_F32 && dtype != RT_BF16) return false;
+  const int esz = dtype == RT_BF16 ? 2 : 4;
+  const int64_t n1 = n[d - 2], n2 = n[d - 1];
+  const int c1 = r[d - 2] + p, c2 = r[d - 1] + p;
+  int64_t S = 1;
+  for (int j = 0; j < d - 2; ++j) S *= n[j];
+  if (n1 > 128 || (n2 * esz) % 16 != 0 || c1 > 64 || c2 > 64) return false;
+  if ((reinterpret_cast<uintptr_t>(X) & 15u) != 0) return false;
+  return S * n1 < ((int64_t)1 << 31);
+}
+
+// Buffer floats of the overlapped core: P' (S c1 c2) and every later intermediate.
+size_t overlap_buffer_floats(int d, const int64_t* n, const int32_t* r, int32_t p) {
+  const size_t c1 = r[d - 2] + p, c2 = r[d - 1] + p;
+  size_t L = 1;
+  for (int j = 0; j < d - 2; ++j) L *= (size_t)n[j];
+  size_t best = L * c1 * c2;
+  size_t R = c1 * c2;
+  for (int k = d - 3; k >= 0; --k) {   // output of the mode-k contraction
+    L /= (size_t)n[k];
+    R *= (size_t)r[k];
+    best = std::max(best, L * R);
+  }
+  best = std::max(best, R / c2 * (size_t)r[d - 1]);   // after W_{d-1}
+  return best;
+}
+
+// Core on the overlapped path: the X pass on Q (already launched by the caller) left
+// P' in bufA; contract the leading modes with U, then the last two with W (signed).
+int enqueue_core_rest_overlap(rt_handle h, int d, const int64_t* n, const int32_t* r, int32_t p, const float* U,
+                              const float* Wsg1, const float* Wsg2, float* G, float* bufA, float* bufB) {
+  cudaStream_t st = h->stream;
+  int nl = 0;
+  size_t uoff[MAXD];
+  size_t acc = 0;
+  for (int k = 0; k < d; ++k) { uoff[k] = acc; acc += (size_t)n[k] * r[k]; }
+  const int64_t c1 = r[d - 2] + p, c2 = r[d - 1] + p;
+  const float* A = bufA;
+  float* bufs[2] = {bufB, bufA};
+  int ping = 0;
+  int64_t R = c1 * c2;
+  for (int k = d - 3; k >= 0; --k) {
+    int64_t L = 1;
+    for (int j = 0; j < k; ++j) L *= n[j];
+    float* out = bufs[ping];
+    nl += launch_ttm_t(A, DT_F32, L, n[k], R, U + uoff[k], r[k], out, st);
+    A = out;
+    ping ^= 1;
+    R *= r[k];
+  }
+  int64_t Lr = R / (c1 * c2);     // product of r_0 .. r_{d-3}
+  float* out = bufs[ping];
+  nl += launch_ttm_t(A, DT_F32, Lr * c1, c2, 1, Wsg2, r[d - 1], out, st);   // mode d-1
+  nl += launch_ttm_t(out, DT_F32, Lr, c1, r[d - 1], Wsg1, r[d - 2], G, st);  // mode d-2
   return nl;
 }
 
@@ -570,8 +647,10 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
   size_t o_zp = 0;
   if (Zout) o_zp = bump.take(sizeof(float*) * d);
   size_t o_bufA = 0, o_bufB = 0;
+  const bool overlap = opt && opt->overlap && G && U && !Zout && overlap_core_ok(X, dtype, d, n, r, p);
   if (G) {
-    const size_t cb = core_buffer_floats(d, n, r);
+    size_t cb = core_buffer_floats(d, n, r);
+    if (overlap) cb = std::max(cb, overlap_buffer_floats(d, n, r, p));
     o_bufA = bump.take(cb * 4);
     o_bufB = bump.take(cb * 4);
   }
@@ -588,6 +667,45 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
   }
   RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
   h->stage_pending = true;
+  if (overlap) {
+    if ((st = ensure_side(h)) != RT_OK) return st;
+    {
+      StageTimer tm(h, 0);
+      nl += launch_rf_head(Gp.g, h->stream, h->d_status);
+    }
+    RT_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+    RT_CUDA(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+    {
+      StageTimer tm(h, 5, h->side);
+      nl += launch_rf_tail(Gp.g, h->side, h->d_status);
+    }
+    RT_CUDA(h, cudaEventRecord(h->ev_join, h->side));
+    const RFProb& q1 = Gp.pp[d - 2].q;
+    const RFProb& q2 = Gp.pp[d - 1].q;
+    int64_t S = 1;
+    for (int j = 0; j < d - 2; ++j) S *= n[j];
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+    const int xmode = (dtype == RT_BF16) ? 1 : (prec_of(opt) == RT_PREC_BF16 ? 2 : 0);
+    float* bufA = reinterpret_cast<float*>(h->ws + o_bufA);
+    float* bufB = reinterpret_cast<float*>(h->ws + o_bufB);
+    int got = 0;
+    {
+      StageTimer tm(h, 1);
+      // leave one SM per problem to the SVD part running beside the pass
+      got = launch_core2_tc(xmode, X, S, (int)n[d - 2], (int)n[d - 1], q1.Q, q1.c, q2.Q, q2.c, bufA, h->d_status,
+                            h->stream, std::max(1, nsm - d));
+    }
+    RT_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+    if (got > 0) {
+      nl += got;
+      StageTimer tm(h, 2);
+      nl += enqueue_core_rest_overlap(h, d, n, r, p, U, q1.Wsg, q2.Wsg, G, bufA, bufB);
+    } else {
+      nl += enqueue_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec_of(opt));
+    }
+    return finish(h, nl);
+  }
   {
     StageTimer tm(h, 0);
     nl += launch_range_finder(Gp.g, h->stream, h->d_status);
@@ -657,6 +775,12 @@ rt_status rt_destroy(rt_handle h) {
   if (h->h_stage) cudaFreeHost(h->h_stage);
   if (h->ev_status) cudaEventDestroy(h->ev_status);
   if (h->ev_stage) cudaEventDestroy(h->ev_stage);
+  if (h->side) {
+    cudaStreamSynchronize(h->side);
+    cudaStreamDestroy(h->side);
+  }
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   drain_timing(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;

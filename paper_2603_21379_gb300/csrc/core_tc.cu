@@ -301,9 +301,11 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
     if (lane == 0) {
       bool ok = true;
       auto mma2 = [&](int64_t g) -> bool {   // P of batch g: D2 = U1^T T (three products of the bf16 terms)
+        // T of batch g is announced on tready[g & 1] (two barriers, by batch parity); the
+        // accumulator uses buffer g % ND2
+        if (!mbar_wait(&tready[g & 1], (uint32_t)((g >> 1) & 1), abort_flag, args.status)) return false;
         const int b = (int)(g % ND2);
         const uint32_t ph = (uint32_t)((g / ND2) & 1);
-        if (!mbar_wait(&tready[b], ph, abort_flag, args.status)) return false;
         if (!mbar_wait(&d2empty[b], ph ^ 1, abort_flag, args.status)) return false;
         fence_after();
         const uint32_t dcol = tmem + LY::D2_COL + b * N2;

@@ -945,6 +945,8 @@ __global__ void __launch_bounds__(256) k_flip(const RFProb* __restrict__ P,
     const int col = e % r;
     if (sg[col] < 0.f) q.U[row0 * r + e] = -q.U[row0 * r + e];
   }
+  if (row0 == 0)
+    for (int e = threadIdx.x; e < c * r; e += blockDim.x) q.Wsg[e] = sg[e % r] * Ws[(e / r) * CMAX + e % r];
 }
 
 // U = Q W(:, :r) and the sign rule in one CTA per problem with n_S <= QWF_MAX rows:
@@ -981,6 +983,7 @@ __global__ void __launch_bounds__(512) k_qwf(const RFProb* __restrict__ P, const
   }
   __syncthreads();
   for (int e = threadIdx.x; e < m * r; e += blockDim.x) q.U[e] = sg[e % r] * Us[e];
+  for (int e = threadIdx.x; e < c * r; e += blockDim.x) q.Wsg[e] = sg[e % r] * Ws[(e / r) * CMAX + e % r];
 }
 
 // S1 + S3 for the grouped range finder: thread j computes pi(j) and its fiber offset,
@@ -1050,7 +1053,8 @@ cudaError_t rf_init_attributes() {
 
 static inline unsigned grid_of(int64_t units) { return (unsigned)units; }
 
-int launch_range_finder(const RFGroup& g, cudaStream_t st, int* status) {
+// S1-S5 and the B-step of S6 (up to the R factors of B^T).
+int launch_rf_head(const RFGroup& g, cudaStream_t st, int* status) {
   const int np = g.nprob;
   const int64_t* pre = g.pre;
   const int64_t stride = np + 1;
@@ -1077,6 +1081,15 @@ int launch_range_finder(const RFGroup& g, cudaStream_t st, int* status) {
     k_bt_qr<<<grid_of(g.total[STG_BTQ]), QR_THREADS, smem_btq(), st>>>(g.probs, pre + STG_BTQ * stride, np);
     n += 2;
   }
+  return n;
+}
+
+// S6 after the B-step: the SVD of R, W, U = Q W and the sign rule (also W with signs).
+int launch_rf_tail(const RFGroup& g, cudaStream_t st, int* status) {
+  const int np = g.nprob;
+  const int64_t* pre = g.pre;
+  const int64_t stride = np + 1;
+  int n = 0;
   k_wsvd<<<grid_of(g.total[STG_WSVD]), QR_THREADS, smem_wsvd(), st>>>(g.probs, pre + STG_WSVD * stride, np,
                                                                  status);
   n += 1;
@@ -1090,6 +1103,10 @@ int launch_range_finder(const RFGroup& g, cudaStream_t st, int* status) {
     n += 2;
   }
   return n;
+}
+
+int launch_range_finder(const RFGroup& g, cudaStream_t st, int* status) {
+  return launch_rf_head(g, st, status) + launch_rf_tail(g, st, status);
 }
 
 int launch_sample_only(const RFGroup& g, cudaStream_t st, int* status) {

@@ -61,6 +61,7 @@ struct RFProb {
   int32_t nsc;             // number of sample chunks of B^T
   int32_t scrows;          // rows (samples) per chunk of B^T
   float* W;                // [c][c]   left singular vectors of R^T, sorted (cols)
+  float* Wsg;              // [c][r]   W(:, :r) with the sign rule's column signs (U = Q Wsg)
   float* sigma;            // [c]      singular values of Q^T Y, descending
   unsigned long long* keys;// [r]      sign-rule argmax keys
   float* U;                // [nS][r]  output factor

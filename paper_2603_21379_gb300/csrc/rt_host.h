@@ -39,6 +39,8 @@ struct RFGroup {
 // Enqueue every stage of the range finder for the group (Alg. 1 loop body /
 // Alg. 2 node body).  Returns the number of kernel launches enqueued.
 int launch_range_finder(const RFGroup& g, cudaStream_t st, int* status);
+int launch_rf_head(const RFGroup& g, cudaStream_t st, int* status);   // S1-S5, B-step of S6
+int launch_rf_tail(const RFGroup& g, cudaStream_t st, int* status);   // SVD of R, W, U = Q W, signs
 // Sampling stage alone (S1), for rtucker_indices.
 int launch_sample_only(const RFGroup& g, cudaStream_t st, int* status);
 // Z = sum of the partial sketches (for rtucker_sketch).
