@@ -548,10 +548,11 @@ __global__ void __launch_bounds__(256) k_bt_partial(const RFProb* __restrict__ P
   const int64_t j0 = (int64_t)sc * q.scrows;
   const int mj = (int)min((int64_t)q.scrows, q.s - j0);
   const int64_t iA = (int64_t)ib * BT_IB, iB = min(q.nS, iA + BT_IB);
-  const int ntile = (BT_SC / 4) * (cp / 4);  // <= 32 * 16 = 512: two tiles per thread
-  float acc[2][4][4];
+  const int ntile = (BT_SC / 4) * (cp / 4);
+  constexpr int TPT = (BT_SC / 4) * (CMAX / 4) / 256;   // 4x4 tiles per thread (at most)
+  float acc[TPT][4][4];
 #pragma unroll
-  for (int u = 0; u < 2; ++u)
+  for (int u = 0; u < TPT; ++u)
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -569,7 +570,7 @@ __global__ void __launch_bounds__(256) k_bt_partial(const RFProb* __restrict__ P
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < TPT; ++u) {
       const int t = threadIdx.x + 256 * u;
       if (t < ntile) {
         const int jg = t % (BT_SC / 4), cg = t / (BT_SC / 4);
@@ -589,7 +590,7 @@ __global__ void __launch_bounds__(256) k_bt_partial(const RFProb* __restrict__ P
   }
   float* out = q.Bp + ((size_t)ib * q.s + j0) * c;
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
+  for (int u = 0; u < TPT; ++u) {
     const int t = threadIdx.x + 256 * u;
     if (t < ntile) {
       const int jg = t % (BT_SC / 4), cg = t / (BT_SC / 4);
@@ -627,9 +628,10 @@ __global__ void __launch_bounds__(QR_THREADS) k_bt_fused(const RFProb* __restric
   float* rdiag = tau + CMAX;
   float* vbuf = rdiag + CMAX;
   const int ntile = (BT_SC / 4) * (cp / 4);
-  float acc[2][4][4];
+  constexpr int TPT = (BT_SC / 4) * (CMAX / 4) / QR_THREADS;   // 4x4 tiles per thread (at most)
+  float acc[TPT][4][4];
 #pragma unroll
-  for (int u = 0; u < 2; ++u)
+  for (int u = 0; u < TPT; ++u)
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -648,7 +650,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_bt_fused(const RFProb* __restric
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 2; ++u) {
+    for (int u = 0; u < TPT; ++u) {
       const int t = threadIdx.x + QR_THREADS * u;
       if (t < ntile) {
         const int jg = t % (BT_SC / 4), cg = t / (BT_SC / 4);
@@ -667,7 +669,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_bt_fused(const RFProb* __restric
     }
   }
 #pragma unroll
-  for (int u = 0; u < 2; ++u) {
+  for (int u = 0; u < TPT; ++u) {
     const int t = threadIdx.x + QR_THREADS * u;
     if (t < ntile) {
       const int jg = t % (BT_SC / 4), cg = t / (BT_SC / 4);
