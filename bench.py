@@ -385,8 +385,18 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         rt.rtucker_decompose_host(Xpin, r, p, seed=seed, out=(Uh, Gh))
-    t_e2e = time.perf_counter() - t0
-    t_e2e = max_over_ranks(t_e2e, device="cuda")
+    t_sync = max_over_ranks(time.perf_counter() - t0, device="cuda")
+    # pipelined host call: each step's copy of X overlaps the previous step's
+    # decomposition; every step's copies in and out are inside the timed region
+    rt.rtucker_decompose_host_async(Xpin, r, p, seed=seed, out=(Uh, Gh))
+    rt.sync()
+    e2e_pipe = max(3, min(args.steps, 20))
+    rank_barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_pipe):
+        rt.rtucker_decompose_host_async(Xpin, r, p, seed=seed, out=(Uh, Gh))
+    rt.sync()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, device="cuda")
 
     extra = {}
     if rank == 0 and not args.no_extras:
@@ -423,8 +433,10 @@ def run_ours(args):
                          "traffic": profile_traffic(),
                          "step_frac": (nbytes / (ms / args.steps * 1e-3) / 1e9) / peak},
             "cpu_baseline": cpu,
-            "e2e": {"value": ws * nbytes * e2e_steps / t_e2e / 1e9, "unit": "GB/s",
-                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": (U.numel() + G.numel()) * 4},
+            "e2e": {"value": ws * nbytes * e2e_pipe / t_e2e / 1e9, "unit": "GB/s",
+                    "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": (U.numel() + G.numel()) * 4,
+                    "api": "rtucker_decompose_host_async x%d + sync (pinned host X)" % e2e_pipe,
+                    "synchronous_value": ws * nbytes * e2e_steps / t_sync / 1e9},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
         }

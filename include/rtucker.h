@@ -159,6 +159,23 @@ rt_status rtucker_decompose_host(rt_handle h, const void* X_host, rt_dtype dtype
                                  const int64_t* n, const int32_t* r, int32_t p, const int64_t* s,
                                  uint64_t seed, const rt_options* opt, float* U_host, float* G_host);
 
+/* Pipelined form of rtucker_decompose_host for a stream of tensors.  The call
+ * enqueues the copy of X_host into one of two device input slots on the
+ * handle's copy stream, the decomposition on the handle's stream after that
+ * copy, and the copies of U and G into U_host / G_host after it, and returns
+ * without waiting, so the copy of the next call's X runs while this call
+ * decomposes.  X_host, U_host and G_host must stay allocated and X_host
+ * unmodified until rt_sync(h) returns (after an error return X_host is no
+ * longer read); with pageable memory the copies are
+ * correct but do not overlap (pinned memory recommended).  Argument checks
+ * are those of rtucker_decompose; device-side failures are reported by
+ * rt_sync.  The two slots (2 x the tensor's bytes) and the outputs live in a
+ * handle-owned device allocation that grows on demand (RT_ENOMEM if it
+ * cannot). */
+rt_status rtucker_decompose_host_async(rt_handle h, const void* X_host, rt_dtype dtype, int d,
+                                       const int64_t* n, const int32_t* r, int32_t p, const int64_t* s,
+                                       uint64_t seed, const rt_options* opt, float* U_host, float* G_host);
+
 /* Batched Sub-R-HOSVD: T independent tensors (tensor t: X[t], order d[t],
  * sizes n[t][.], ranks r[t][.], samples s[t] or s == NULL / s[t] == NULL for
  * the default, seed seeds[t]) decomposed with one grouped launch per stage for

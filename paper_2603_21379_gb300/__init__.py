@@ -19,7 +19,7 @@ import torch
 __all__ = [
     "load_library", "library_path", "RtError", "sync",
     "rtucker_indices", "rtucker_sketch", "rtucker_factors", "rtucker_core", "rtucker_decompose",
-    "rtucker_decompose_host", "rtucker_decompose_batched", "rtucker_relerr",
+    "rtucker_decompose_host", "rtucker_decompose_host_async", "rtucker_decompose_batched", "rtucker_relerr",
     "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "last_launch_count", "workspace_bytes",
     "set_timing", "get_timing", "STAGES", "rhtucker_root_transfer_noalloc", "BatchedDecomposition",
 ]
@@ -84,6 +84,8 @@ def load_library():
         "rtucker_decompose": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64, PO, vp, vp]),
         "rtucker_decompose_host": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64, PO,
                                                   vp, vp]),
+        "rtucker_decompose_host_async": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64,
+                                                        PO, vp, vp]),
         "rtucker_decompose_batched": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ctypes.c_int, P32,
                                                      ctypes.POINTER(P64), ctypes.POINTER(P32), i32,
                                                      ctypes.POINTER(P64), PU64, PO, ctypes.POINTER(vp),
@@ -135,7 +137,10 @@ def sync(device=None):
     kernel reported a device-side failure (bounded wait ran out, numerical
     breakdown, failed check) since the last sync."""
     h = _handle(device)
-    _check(h, load_library().rt_sync(h))
+    try:
+        _check(h, load_library().rt_sync(h))
+    finally:
+        _in_flight.pop(h.value, None)
 
 
 def _i64(vals):
@@ -324,6 +329,35 @@ def rtucker_decompose_host(X, r, p, s=None, seed=0, out=None, prec="fp32"):
     sp = _i64(_as_list(s, d)) if s is not None else None
     _check(h, lib.rtucker_decompose_host(h, _ptr(X), _DT[X.dtype], d, _i64(n), _i32(r), int(p), sp,
                                          ctypes.c_uint64(seed), _opts(prec), _ptr(U), _ptr(G)))
+    return G, _split(U, n, r)
+
+
+# host tensors of rtucker_decompose_host_async calls not yet synchronised, per handle
+_in_flight = {}
+
+
+def rtucker_decompose_host_async(X, r, p, s=None, seed=0, out=None, prec="fp32"):
+    """Pipelined Sub-R-HOSVD of a HOST tensor: enqueues the copy of X into one of
+    two device slots, the decomposition and the copies of U and G back to host
+    tensors, and returns (G, [U_k]) before they are written.  The copy of the
+    next call's X overlaps this call's decomposition; the results are valid
+    after ``sync()``, and X must not be modified until then.  X and the outputs
+    are kept alive here until that ``sync()``."""
+    lib = load_library()
+    if X.is_cuda or X.dtype not in _DT or not X.is_contiguous():
+        raise ValueError("X must be a contiguous host tensor of float32/float64/bfloat16")
+    d, n = X.dim(), list(X.shape)
+    r = _as_list(r, d)
+    if out is None:
+        U = torch.empty(sum(nk * rk for nk, rk in zip(n, r)), dtype=torch.float32, pin_memory=True)
+        G = torch.empty(r, dtype=torch.float32, pin_memory=True)
+    else:
+        U, G = out
+    h = _handle()
+    sp = _i64(_as_list(s, d)) if s is not None else None
+    _check(h, lib.rtucker_decompose_host_async(h, _ptr(X), _DT[X.dtype], d, _i64(n), _i32(r), int(p), sp,
+                                               ctypes.c_uint64(seed), _opts(prec), _ptr(U), _ptr(G)))
+    _in_flight.setdefault(h.value, []).append((X, U, G))
     return G, _split(U, n, r)
 
 

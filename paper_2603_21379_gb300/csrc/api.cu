@@ -20,6 +20,52 @@
 
 using namespace rt;
 
+// One table upload: `words` 8-byte words from staging offset `src` to `dst`.
+struct StageSeg {
+  uint64_t* dst;
+  size_t src;
+  int64_t words;
+};
+
+namespace {
+
+// Table uploads are read by a kernel straight from the mapped pinned staging
+// buffer instead of being copied by the copy engine: a decomposition that
+// waits behind a large host-to-device copy of the next tensor (the pipelined
+// host call) would otherwise wait for that copy before its first kernel.
+constexpr int UP_MAX = 16;            // segments per launch
+constexpr int UP_CHUNK = 256 * 4;     // words per CTA (4 independent loads per thread)
+
+struct UploadBatch {
+  int nseg;
+  int cta0[UP_MAX + 1];               // first CTA of each segment
+  uint64_t* dst[UP_MAX];
+  const uint64_t* src[UP_MAX];
+  int64_t words[UP_MAX];
+};
+
+__global__ void __launch_bounds__(256) k_stage_copy(const UploadBatch b) {
+  int sg = 0;
+  while (sg + 1 < b.nseg && (int)blockIdx.x >= b.cta0[sg + 1]) ++sg;
+  const int64_t w0 = (int64_t)(blockIdx.x - b.cta0[sg]) * UP_CHUNK;
+  const int64_t nw = b.words[sg];
+  const uint64_t* __restrict__ src = b.src[sg];
+  uint64_t* __restrict__ dst = b.dst[sg];
+  uint64_t v[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t w = w0 + j * 256 + threadIdx.x;
+    v[j] = w < nw ? __ldcv(src + w) : 0;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int64_t w = w0 + j * 256 + threadIdx.x;
+    if (w < nw) dst[w] = v[j];
+  }
+}
+
+}  // namespace
+
 struct rt_handle_s {
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -30,13 +76,23 @@ struct rt_handle_s {
   cudaEvent_t ev_status = nullptr;
   bool status_pending = false;
   char* h_stage = nullptr;     // pinned staging of the problem tables
+  char* d_stage = nullptr;     // the same buffer as the device addresses it
   size_t h_stage_bytes = 0;
+  std::vector<StageSeg> stage_segs;  // uploads not yet enqueued
   cudaEvent_t ev_stage = nullptr;
   bool stage_pending = false;
   std::string err;
   int launches = 0;
   char* hc_buf = nullptr;      // device buffers of rtucker_decompose_host
   size_t hc_bytes = 0;
+  // rtucker_decompose_host_async: two device input slots filled on a copy
+  // stream (slot k is reused once the decomposition that read it has run),
+  // one device output area read back on the handle's stream
+  cudaStream_t cstream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+  char* pipe_buf = nullptr;
+  size_t pipe_slot = 0, pipe_out = 0;
+  int pipe_next = 0;
   // second stream for work that overlaps the pass over X, with fork/join events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -293,6 +349,7 @@ rt_status ensure_ws(rt_handle h, size_t bytes) {
 }
 
 rt_status ensure_stage(rt_handle h, size_t bytes) {
+  h->stage_segs.clear();  // left over from a call that failed before its commit
   if (h->stage_pending) {
     RT_CUDA(h, cudaEventSynchronize(h->ev_stage));
     h->stage_pending = false;
@@ -301,9 +358,49 @@ rt_status ensure_stage(rt_handle h, size_t bytes) {
   if (h->h_stage) cudaFreeHost(h->h_stage);
   h->h_stage = nullptr;
   h->h_stage_bytes = 0;
+  h->d_stage = nullptr;
   const size_t want = align_up(bytes * 2);
   RT_CUDA(h, cudaMallocHost(&h->h_stage, want));
+  void* dv = nullptr;
+  RT_CUDA(h, cudaHostGetDevicePointer(&dv, h->h_stage, 0));
+  h->d_stage = static_cast<char*>(dv);
   h->h_stage_bytes = want;
+  return RT_OK;
+}
+
+// Queues the upload of `bytes` (a multiple of 8) from `src` inside the staging
+// buffer to device address `dst` (8-byte aligned).
+rt_status stage_put(rt_handle h, void* dst, const void* src, size_t bytes) {
+  const size_t off = static_cast<size_t>(static_cast<const char*>(src) - h->h_stage);
+  if (bytes % 8 || off % 8 || reinterpret_cast<uintptr_t>(dst) % 8 || off + bytes > h->h_stage_bytes)
+    return fail(h, RT_EINVAL, "internal: misaligned table upload");
+  if (bytes) h->stage_segs.push_back({static_cast<uint64_t*>(dst), off, (int64_t)(bytes / 8)});
+  return RT_OK;
+}
+
+// Enqueues the queued uploads on the handle's stream (one launch per UP_MAX
+// segments, counted in *nl) and marks the staging buffer busy until they ran.
+rt_status stage_commit(rt_handle h, int* nl) {
+  std::vector<StageSeg> segs;
+  segs.swap(h->stage_segs);
+  for (size_t i0 = 0; i0 < segs.size(); i0 += UP_MAX) {
+    UploadBatch b{};
+    b.nseg = (int)std::min<size_t>(UP_MAX, segs.size() - i0);
+    int ctas = 0;
+    for (int j = 0; j < b.nseg; ++j) {
+      const StageSeg& g = segs[i0 + j];
+      b.cta0[j] = ctas;
+      b.dst[j] = g.dst;
+      b.src[j] = reinterpret_cast<const uint64_t*>(h->d_stage + g.src);
+      b.words[j] = g.words;
+      ctas += (int)((g.words + UP_CHUNK - 1) / UP_CHUNK);
+    }
+    b.cta0[b.nseg] = ctas;
+    k_stage_copy<<<ctas, 256, 0, h->stream>>>(b);
+    ++*nl;
+  }
+  RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
+  h->stage_pending = true;
   return RT_OK;
 }
 
@@ -341,7 +438,7 @@ void group_layout(Group& G, Bump& bump) {
   G.o_pre = bump.take(sizeof(int64_t) * STG_COUNT * (np + 1));
 }
 
-// Writes the tables into staging and enqueues the upload; fills G.g.
+// Writes the tables into staging and queues their upload; fills G.g.
 rt_status group_upload(rt_handle h, Group& G, char* stage, size_t stage_off) {
   const int np = (int)G.pp.size();
   RFProb* tab = reinterpret_cast<RFProb*>(stage + stage_off);
@@ -359,9 +456,9 @@ rt_status group_upload(rt_handle h, Group& G, char* stage, size_t stage_off) {
     pre[st * (np + 1) + np] = acc;
     G.g.total[st] = acc;
   }
-  RT_CUDA(h, cudaMemcpyAsync(h->ws + G.o_tab, tab, sizeof(RFProb) * np, cudaMemcpyHostToDevice, h->stream));
-  RT_CUDA(h, cudaMemcpyAsync(h->ws + G.o_pre, pre, sizeof(int64_t) * STG_COUNT * (np + 1),
-                             cudaMemcpyHostToDevice, h->stream));
+  rt_status st;
+  if ((st = stage_put(h, h->ws + G.o_tab, tab, sizeof(RFProb) * np)) != RT_OK) return st;
+  if ((st = stage_put(h, h->ws + G.o_pre, pre, sizeof(int64_t) * STG_COUNT * (np + 1))) != RT_OK) return st;
   G.g.probs = reinterpret_cast<const RFProb*>(h->ws + G.o_tab);
   G.g.pre = reinterpret_cast<const int64_t*>(h->ws + G.o_pre);
   G.g.nprob = np;
@@ -663,10 +760,9 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
     float** zp = reinterpret_cast<float**>(h->h_stage + group_stage_bytes(Gp));
     size_t off = 0;
     for (int k = 0; k < d; ++k) { zp[k] = Zout + off; off += (size_t)n[k] * (r[k] + p); }
-    RT_CUDA(h, cudaMemcpyAsync(h->ws + o_zp, zp, sizeof(float*) * d, cudaMemcpyHostToDevice, h->stream));
+    if ((st = stage_put(h, h->ws + o_zp, zp, sizeof(float*) * d)) != RT_OK) return st;
   }
-  RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
-  h->stage_pending = true;
+  if ((st = stage_commit(h, &nl)) != RT_OK) return st;
   if (overlap) {
     if ((st = ensure_side(h)) != RT_OK) return st;
     {
@@ -781,6 +877,15 @@ rt_status rt_destroy(rt_handle h) {
   }
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->cstream) {
+    cudaStreamSynchronize(h->cstream);
+    cudaStreamDestroy(h->cstream);
+  }
+  for (int k = 0; k < 2; ++k) {
+    if (h->ev_copied[k]) cudaEventDestroy(h->ev_copied[k]);
+    if (h->ev_used[k]) cudaEventDestroy(h->ev_used[k]);
+  }
+  if (h->pipe_buf) cudaFree(h->pipe_buf);
   drain_timing(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
@@ -865,9 +970,9 @@ rt_status rtucker_indices(rt_handle h, int d, const int64_t* n, const int64_t* s
   if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
   if ((st = ensure_stage(h, group_stage_bytes(Gp))) != RT_OK) return st;
   if ((st = group_upload(h, Gp, h->h_stage, 0)) != RT_OK) return st;
-  RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
-  h->stage_pending = true;
-  const int nl = launch_sample_only(Gp.g, h->stream, h->d_status);
+  int nl = 0;
+  if ((st = stage_commit(h, &nl)) != RT_OK) return st;
+  nl += launch_sample_only(Gp.g, h->stream, h->d_status);
   return finish(h, nl);
 }
 
@@ -952,6 +1057,62 @@ rt_status rtucker_decompose_host(rt_handle h, const void* X_host, rt_dtype dtype
   return st;
 }
 
+rt_status rtucker_decompose_host_async(rt_handle h, const void* X_host, rt_dtype dtype, int d, const int64_t* n,
+                                       const int32_t* r, int32_t p, const int64_t* s, uint64_t seed,
+                                       const rt_options* opt, float* U_host, float* G_host) {
+  if (!h) return RT_EINVAL;
+  int64_t total = 0;
+  rt_status st = check_tensor(h, X_host, dtype, d, n, &total);
+  if (st != RT_OK) return st;
+  if (!r || !U_host || !G_host) return fail(h, RT_EINVAL, "r, U and G are required");
+  size_t usz = 0, gsz = 1;
+  for (int k = 0; k < d; ++k) { usz += (size_t)n[k] * r[k]; gsz *= (size_t)r[k]; }
+  const size_t xbytes = (size_t)total * dtype_size(dtype);
+  const size_t xb = align_up(xbytes), ob = align_up(usz * 4) + align_up(gsz * 4);
+  if (!h->cstream) {
+    RT_CUDA(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+    for (int k = 0; k < 2; ++k) {
+      RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_copied[k], cudaEventDisableTiming));
+      RT_CUDA(h, cudaEventCreateWithFlags(&h->ev_used[k], cudaEventDisableTiming));
+    }
+  }
+  if (xb > h->pipe_slot || ob > h->pipe_out) {
+    // both streams idle before the buffers move
+    RT_CUDA(h, cudaStreamSynchronize(h->cstream));
+    RT_CUDA(h, cudaStreamSynchronize(h->stream));
+    if (h->pipe_buf) cudaFree(h->pipe_buf);
+    h->pipe_buf = nullptr;
+    h->pipe_slot = h->pipe_out = 0;
+    const size_t slot = std::max(xb, h->pipe_slot), out = std::max(ob, h->pipe_out);
+    if (cudaMalloc(&h->pipe_buf, 2 * slot + out) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, RT_ENOMEM, "device buffers for the pipelined host-memory call");
+    }
+    h->pipe_slot = slot;
+    h->pipe_out = out;
+  }
+  const int k = h->pipe_next;
+  char* dX = h->pipe_buf + (size_t)k * h->pipe_slot;
+  float* dU = reinterpret_cast<float*>(h->pipe_buf + 2 * h->pipe_slot);
+  float* dG = reinterpret_cast<float*>(h->pipe_buf + 2 * h->pipe_slot + align_up(usz * 4));
+  // copy stream: slot k is free once the decomposition that last read it ran
+  RT_CUDA(h, cudaStreamWaitEvent(h->cstream, h->ev_used[k], 0));
+  RT_CUDA(h, cudaMemcpyAsync(dX, X_host, xbytes, cudaMemcpyHostToDevice, h->cstream));
+  RT_CUDA(h, cudaEventRecord(h->ev_copied[k], h->cstream));
+  RT_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_copied[k], 0));
+  st = rtucker_decompose(h, dX, dtype, d, n, r, p, s, seed, opt, dU, dG);
+  if (st != RT_OK) {
+    cudaStreamSynchronize(h->cstream);  // X_host is no longer read when the call returns
+    return st;
+  }
+  RT_CUDA(h, cudaEventRecord(h->ev_used[k], h->stream));
+  // the next call's decomposition writes dU/dG after these reads on the same stream
+  RT_CUDA(h, cudaMemcpyAsync(U_host, dU, usz * 4, cudaMemcpyDeviceToHost, h->stream));
+  RT_CUDA(h, cudaMemcpyAsync(G_host, dG, gsz * 4, cudaMemcpyDeviceToHost, h->stream));
+  h->pipe_next = k ^ 1;
+  return RT_OK;
+}
+
 rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt_dtype dtype, const int32_t* d,
                                     const int64_t* const* n, const int32_t* const* r, int32_t p,
                                     const int64_t* const* s, const uint64_t* seeds, const rt_options* opt,
@@ -1032,15 +1193,12 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
       }
       ps[q_i] = acc;
       ltiles[k] = acc;
-      RT_CUDA(h, cudaMemcpyAsync(h->ws + o_jobs[k], js, sizeof(TTMJob) * njob[k], cudaMemcpyHostToDevice,
-                                 h->stream));
-      RT_CUDA(h, cudaMemcpyAsync(h->ws + o_lpre[k], ps, sizeof(int64_t) * (njob[k] + 1), cudaMemcpyHostToDevice,
-                                 h->stream));
+      if ((st = stage_put(h, h->ws + o_jobs[k], js, sizeof(TTMJob) * njob[k])) != RT_OK) return st;
+      if ((st = stage_put(h, h->ws + o_lpre[k], ps, sizeof(int64_t) * (njob[k] + 1))) != RT_OK) return st;
     }
   }
-  RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
-  h->stage_pending = true;
   int nl = 0;
+  if ((st = stage_commit(h, &nl)) != RT_OK) return st;
   {
     StageTimer tm(h, 0);
     nl += launch_range_finder(Gp.g, h->stream, h->d_status);
@@ -1173,12 +1331,9 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
     jb.cta0 = q == 0 ? 0 : jobs[q - 1].cta0 + transfer_ctas(jobs[q - 1].nl);
     jobs[q] = jb;
   }
-  if (!internal.empty())
-    RT_CUDA(h, cudaMemcpyAsync(h->ws + o_jobs, jobs, sizeof(TransferJob) * internal.size(),
-                               cudaMemcpyHostToDevice, h->stream));
-  RT_CUDA(h, cudaEventRecord(h->ev_stage, h->stream));
-  h->stage_pending = true;
+  if ((st = stage_put(h, h->ws + o_jobs, jobs, sizeof(TransferJob) * internal.size())) != RT_OK) return st;
   int nlaunch = 0;
+  if ((st = stage_commit(h, &nlaunch)) != RT_OK) return st;
   {
     StageTimer tm(h, 0);
     nlaunch += launch_range_finder(Gp.g, h->stream, h->d_status);

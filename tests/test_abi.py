@@ -29,7 +29,7 @@ def lib():
 def test_header_declares_the_path_entry_points():
     names = declared_functions()
     for must in ["rtucker_indices", "rtucker_sketch", "rtucker_factors", "rtucker_core", "rtucker_decompose",
-                 "rtucker_decompose_host", "rtucker_decompose_batched", "rtucker_relerr", "rhtucker_decompose",
+                 "rtucker_decompose_host", "rtucker_decompose_host_async", "rtucker_decompose_batched", "rtucker_relerr", "rhtucker_decompose",
                  "rhtucker_relerr", "rt_create", "rt_destroy", "rt_sync", "rt_last_error"]:
         assert must in names
 

@@ -272,6 +272,30 @@ def test_host_memory_entry_point(rt):
         assert np.array_equal(a.numpy(), b.cpu().numpy())
 
 
+def test_pipelined_host_entry_point(rt):
+    # a stream of tensors (two shapes, so the device slots grow once; one
+    # pageable input) through the pipelined host call: each result equals the
+    # synchronous device call on the same tensor
+    shapes = [(40, 36, 50), (40, 36, 50), (64, 48, 40), (40, 36, 50), (64, 48, 40)]
+    ranks = [4, 5, 6]
+    Xs = [torch.from_numpy(synth.tucker_tensor(sh, ranks, 1e-4, 300 + i)) for i, sh in enumerate(shapes)]
+    Xs = [x.pin_memory() if i != 3 else x for i, x in enumerate(Xs)]
+    outs = [rt.rtucker_decompose_host_async(x, ranks, 3, seed=10 + i) for i, x in enumerate(Xs)]
+    rt.sync()
+    for i, (x, (G, U)) in enumerate(zip(Xs, outs)):
+        Gd, Ud = rt.rtucker_decompose(x.cuda(), ranks, 3, seed=10 + i)
+        torch.cuda.synchronize()
+        assert np.array_equal(G.numpy(), Gd.cpu().numpy()), i
+        for a, b in zip(U, Ud):
+            assert np.array_equal(a.numpy(), b.cpu().numpy()), i
+    # an argument error leaves the pipeline usable
+    with pytest.raises(rt.RtError):
+        rt.rtucker_decompose_host_async(Xs[0], ranks, 70)
+    G, U = rt.rtucker_decompose_host_async(Xs[1], ranks, 3, seed=11)
+    rt.sync()
+    assert np.array_equal(G.numpy(), outs[1][0].numpy())
+
+
 def test_batched_matches_single_and_oracle(rt):
     shapes, ranks = synth.batched_shapes(T=12, data_seed=55)
     Xs = [synth.tucker_tensor(sh, rk, 1e-6, 9000 + t) for t, (sh, rk) in enumerate(zip(shapes, ranks))]
