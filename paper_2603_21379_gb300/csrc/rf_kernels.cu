@@ -352,6 +352,108 @@ __device__ void hh_factor_reg(float* A, int ld, int m, int c, float* tau, float*
   __syncthreads();
 }
 
+// As hh_factor_reg, with the owner of column k tracked by counters instead of k % nw
+// and warps whose columns are all finished skipping the update.  Faster where the
+// block holds only the QR (k_qr1, k_wsvd); inside k_bt_fused the original schedules
+// better.
+template <int MR, int JPW>
+__device__ void hh_factor_reg_ct(float* A, int ld, int m, int c, float* tau, float* rdiag, float* vbuf) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int K = min(m, c);
+  float col[JPW][MR];
+#pragma unroll
+  for (int u = 0; u < JPW; ++u) {
+    const int j = warp + u * nw;
+#pragma unroll
+    for (int t = 0; t < MR; ++t) {
+      const int i = lane + 32 * t;
+      col[u][t] = (j < c && i < m) ? A[(size_t)j * ld + i] : 0.f;
+    }
+  }
+  int kw = 0, ku = 0;                  // k = ku * nw + kw: owner warp and register slot of column k
+  for (int k = 0; k < K; ++k) {
+    float* vb = vbuf + (k & 1) * (32 * MR);
+    if (warp == kw) {
+      const int uk = ku;
+      float s2 = 0.f, xk = 0.f;
+#pragma unroll
+      for (int u = 0; u < JPW; ++u) {
+        if (u != uk) continue;
+#pragma unroll
+        for (int t = 0; t < MR; ++t) {
+          const int i = lane + 32 * t;
+          const float x = col[u][t];
+          if (i >= k && i < m) s2 = fmaf(x, x, s2);
+          if (t == (k >> 5)) xk = x;
+        }
+      }
+      s2 = warp_sum(s2);
+      const float x0 = __shfl_sync(0xffffffffu, xk, k & 31);
+      const float nrm = sqrtf(s2);
+      const float alpha = (x0 >= 0.f) ? -nrm : nrm;
+      const float tk = (nrm == 0.f) ? 0.f : 1.f / (nrm * (nrm + fabsf(x0)));
+#pragma unroll
+      for (int u = 0; u < JPW; ++u) {
+        if (u != uk) continue;
+#pragma unroll
+        for (int t = 0; t < MR; ++t) {
+          const int i = lane + 32 * t;
+          float v = (i > k && i < m) ? col[u][t] : 0.f;
+          if (i == k && nrm != 0.f) {
+            v = x0 - alpha;
+            col[u][t] = v;
+          }
+          vb[i] = (i == k && nrm == 0.f) ? 0.f : v;
+        }
+      }
+      if (lane == 0) {
+        tau[k] = tk;
+        rdiag[k] = (nrm == 0.f) ? 0.f : alpha;
+      }
+    }
+    if (++kw == nw) { kw = 0; ++ku; }
+    __syncthreads();
+    const float tk = tau[k];
+    // a warp whose columns are all done skips the step
+    if (tk != 0.f && warp + (JPW - 1) * nw > k) {
+      float vr[MR];
+#pragma unroll
+      for (int t = 0; t < MR; ++t) vr[t] = vb[lane + 32 * t];
+      float w[JPW];
+#pragma unroll
+      for (int u = 0; u < JPW; ++u) {
+        w[u] = 0.f;
+#pragma unroll
+        for (int t = 0; t < MR; ++t) w[u] = fmaf(vr[t], col[u][t], w[u]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int u = 0; u < JPW; ++u) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
+#pragma unroll
+      for (int u = 0; u < JPW; ++u) {
+        const int j = warp + u * nw;
+        if (j > k && j < c) {
+          const float s = w[u] * tk;
+#pragma unroll
+          for (int t = 0; t < MR; ++t) col[u][t] = fmaf(-s, vr[t], col[u][t]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < JPW; ++u) {
+    const int j = warp + u * nw;
+    if (j >= c) continue;
+#pragma unroll
+    for (int t = 0; t < MR; ++t) {
+      const int i = lane + 32 * t;
+      if (i < m) A[(size_t)j * ld + i] = col[u][t];
+    }
+  }
+  __syncthreads();
+}
+
 // Qm = H_0 ... H_{K-1} [I; 0] (signs fixed so that diag(R) > 0 when asked):
 // warp w builds its own columns by applying every reflector, no barriers.
 template <int MR, int JPW>
@@ -412,9 +514,60 @@ __device__ void hh_form_q_reg(const float* A, float* Qm, int ld, int m, int c, c
   __syncthreads();
 }
 
+// Qm = H_0 ... H_{K-1} [I; 0] with one 8-lane group per column: group g (needs
+// blockDim >= 8 c) holds column g of Q in registers (lane l: rows l + 8 t, m <= 8 RPL)
+// and applies H_k for k = min(K-1, g) .. 0 (H_k leaves e_g alone for k > g); the
+// groups never wait for one another, and each reflector costs one 3-level reduction.
+template <int RPL>
+__device__ void hh_form_q_g8(const float* A, float* Qm, int ld, int m, int c, const float* tau, const float* rdiag,
+                             bool fix_sign) {
+  const int g = threadIdx.x >> 3, l8 = threadIdx.x & 7;
+  const unsigned gm = 0xffu << (threadIdx.x & 24);
+  const int K = min(m, c);
+  if (g < c) {
+    float q[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) q[t] = (l8 + 8 * t == g) ? 1.f : 0.f;
+    for (int k = min(K - 1, g); k >= 0; --k) {
+      const float tk = tau[k];
+      if (tk == 0.f) continue;
+      const float* vc = A + (size_t)k * ld;
+      float v[RPL];
+      float d = 0.f;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) {
+        const int i = l8 + 8 * t;
+        v[t] = (i >= k && i < m) ? vc[i] : 0.f;
+        d = fmaf(v[t], q[t], d);
+      }
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) d += __shfl_xor_sync(gm, d, o);
+      const float sc = d * tk;
+#pragma unroll
+      for (int t = 0; t < RPL; ++t) q[t] = fmaf(-sc, v[t], q[t]);
+    }
+    const float sg = (fix_sign && g < K && rdiag[g] < 0.f) ? -1.f : 1.f;
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+      const int i = l8 + 8 * t;
+      if (i < m) Qm[(size_t)g * ld + i] = sg * q[t];
+    }
+  }
+  __syncthreads();
+}
+
 // Dispatch on the row count (m <= 512: registers; larger: shared memory).
-template <int JPW>
+template <int JPW, bool CT = true>
 __device__ void qr_factor(float* A, int ld, int m, int c, float* tau, float* rdiag, float* vbuf) {
+  if (CT) {
+    if (m <= 32) hh_factor_reg_ct<1, JPW>(A, ld, m, c, tau, rdiag, vbuf);
+    else if (m <= 64) hh_factor_reg_ct<2, JPW>(A, ld, m, c, tau, rdiag, vbuf);
+    else if (m <= 128) hh_factor_reg_ct<4, JPW>(A, ld, m, c, tau, rdiag, vbuf);
+    else if (m <= 256) hh_factor_reg_ct<8, JPW>(A, ld, m, c, tau, rdiag, vbuf);
+    else if (m <= 512) hh_factor_reg_ct<16, JPW>(A, ld, m, c, tau, rdiag, vbuf);
+    else hh_factor(A, ld, m, c, tau, rdiag, nullptr);
+    return;
+  }
   if (m <= 32) hh_factor_reg<1, JPW>(A, ld, m, c, tau, rdiag, vbuf);
   else if (m <= 64) hh_factor_reg<2, JPW>(A, ld, m, c, tau, rdiag, vbuf);
   else if (m <= 128) hh_factor_reg<4, JPW>(A, ld, m, c, tau, rdiag, vbuf);
@@ -425,7 +578,11 @@ __device__ void qr_factor(float* A, int ld, int m, int c, float* tau, float* rdi
 template <int JPW>
 __device__ void qr_form_q(const float* A, float* Qm, int ld, int m, int c, const float* tau, const float* rdiag,
                           bool fix_sign) {
-  if (m <= 32) hh_form_q_reg<1, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
+  if ((int)blockDim.x >= 8 * c && m <= 128) {
+    if (m <= 32) hh_form_q_g8<4>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
+    else if (m <= 64) hh_form_q_g8<8>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
+    else hh_form_q_g8<16>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
+  } else if (m <= 32) hh_form_q_reg<1, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
   else if (m <= 64) hh_form_q_reg<2, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
   else if (m <= 128) hh_form_q_reg<4, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
   else if (m <= 256) hh_form_q_reg<8, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
@@ -686,7 +843,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_bt_fused(const RFProb* __restric
     }
   }
   __syncthreads();
-  qr_factor<QR_JPW>(A, ld, mj, c, tau, rdiag, vbuf);
+  qr_factor<QR_JPW, false>(A, ld, mj, c, tau, rdiag, vbuf);
   float* Rc = q.Rc + (size_t)sc * c * c;
   for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
     const int k = e / c, j = e % c;
@@ -951,48 +1108,84 @@ __global__ void __launch_bounds__(256) k_flip(const RFProb* __restrict__ P,
     for (int e = threadIdx.x; e < c * r; e += blockDim.x) q.Wsg[e] = sg[e % r] * Ws[(e / r) * CMAX + e % r];
 }
 
-// U = Q W(:, :r) and the sign rule in one CTA per problem with n_S <= QWF_MAX rows:
-// U in shared memory, per-column keys (|u|, lowest row) by shared atomics, then the
-// flipped U written once.  Dynamic smem: Ws[CMAX*CMAX] | Qs[QWF_MAX*CMAX] |
-// Us[QWF_MAX*CMAX] | keys[CMAX] (u64) | sg[CMAX]
+// U = Q W(:, :r) and the sign rule in one CTA per problem with n_S <= QWF_MAX rows.
+// Q is staged transposed (Qt[t][i], rows padded to a multiple of 4) so that a thread's
+// 4 x 4 tile of U takes one 16-byte load of Q and one of W per t; every entry is the
+// same sequential fma chain over t as qw_entry.  The sign rule's key (|u|, lowest row)
+// of each column is a warp max-reduction over the U tile in shared memory.
+// Dynamic smem: Ws[CMAX*CMAX] | Qt[CMAX*QWF_MAX] | Us[QWF_MAX*CMAX] | sg[CMAX]
 __global__ void __launch_bounds__(512) k_qwf(const RFProb* __restrict__ P, const int64_t* __restrict__ pre,
                                              int np) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* Ws = reinterpret_cast<float*>(smem_raw);
-  float* Qs = Ws + CMAX * CMAX;
-  float* Us = Qs + QWF_MAX * CMAX;
-  unsigned long long* kb = reinterpret_cast<unsigned long long*>(Us + QWF_MAX * CMAX);
-  float* sg = reinterpret_cast<float*>(kb + CMAX);
+  float* Qt = Ws + CMAX * CMAX;
+  float* Us = Qt + QWF_MAX * CMAX;
+  float* sg = Us + QWF_MAX * CMAX;
   const int p = find_prob(pre, np, blockIdx.x);
   const RFProb& q = P[p];
   const int m = (int)q.nS;
   const int c = q.c, r = q.r;
-  for (int e = threadIdx.x; e < c * r; e += blockDim.x) Ws[(e / r) * CMAX + e % r] = q.W[(e / r) * c + e % r];
-  for (int e = threadIdx.x; e < m * c; e += blockDim.x) Qs[e] = q.Q[e];
-  if (threadIdx.x < r) kb[threadIdx.x] = 0ull;
-  __syncthreads();
-  for (int e = threadIdx.x; e < m * r; e += blockDim.x) {
-    const int i = e / r, col = e % r;
-    const float u = qw_entry(Qs + i * c, Ws, c, col, CMAX);
-    Us[e] = u;
-    atomicMax(&kb[col], sign_key(u, i));
+  const int mp = (m + 3) & ~3, rp = (r + 3) & ~3;
+  for (int e = threadIdx.x; e < c * rp; e += blockDim.x) {
+    const int t = e / rp, col = e % rp;
+    Ws[t * CMAX + col] = col < r ? q.W[t * c + col] : 0.f;
+  }
+  for (int e = threadIdx.x; e < mp * c; e += blockDim.x) {
+    const int i = e / c, t = e % c;
+    Qt[t * QWF_MAX + i] = i < m ? q.Q[e] : 0.f;
   }
   __syncthreads();
-  if (threadIdx.x < r) {
-    const int col = threadIdx.x;
-    const int rstar = (int)(0xffffffffu - (uint32_t)(kb[col] & 0xffffffffull));
-    sg[col] = (Us[rstar * r + col] < 0.f) ? -1.f : 1.f;
+  const int nrg = mp >> 2, ncg = rp >> 2;
+  for (int tile = threadIdx.x; tile < nrg * ncg; tile += blockDim.x) {
+    const int rg = tile % nrg, cg = tile / nrg;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int t = 0; t < c; ++t) {
+      const float4 qv = *reinterpret_cast<const float4*>(Qt + t * QWF_MAX + 4 * rg);
+      const float4 wv = *reinterpret_cast<const float4*>(Ws + t * CMAX + 4 * cg);
+      const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
+      const float wb[4] = {wv.x, wv.y, wv.z, wv.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(qa[a], wb[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) Us[(4 * rg + a) * CMAX + 4 * cg + b] = acc[a][b];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < m * r; e += blockDim.x) q.U[e] = sg[e % r] * Us[e];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int col = warp; col < r; col += nw) {
+    unsigned long long best = 0ull;
+    for (int i = lane; i < m; i += 32) {
+      const unsigned long long k = sign_key(Us[i * CMAX + col], i);
+      best = k > best ? k : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long k = __shfl_xor_sync(0xffffffffu, best, o);
+      best = k > best ? k : best;
+    }
+    if (lane == 0) {
+      const int rstar = (int)(0xffffffffu - (uint32_t)(best & 0xffffffffull));
+      sg[col] = (Us[rstar * CMAX + col] < 0.f) ? -1.f : 1.f;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < m * r; e += blockDim.x) q.U[e] = sg[e % r] * Us[(e / r) * CMAX + e % r];
   for (int e = threadIdx.x; e < c * r; e += blockDim.x) q.Wsg[e] = sg[e % r] * Ws[(e / r) * CMAX + e % r];
 }
 
-// S1 + S3 for the grouped range finder: thread j computes pi(j) and its fiber offset,
-// then row j of Omega (Box-Muller of Philox counters (pi(j), c)); it also clears the
-// sketch's per-row-tile counters.
-__global__ void __launch_bounds__(128) k_sample_omega(const RFProb* __restrict__ P,
-                                                      const int64_t* __restrict__ pre, int np, int* status) {
+// S1 + S3 with one thread per sample (pi(j), its fiber offset and row j of Omega):
+// the form for many samples (batches), where one thread per sample already fills
+// the GPU and the warp form below would walk each Feistel cycle 32 times.
+__global__ void __launch_bounds__(128) k_sample_omega_t(const RFProb* __restrict__ P,
+                                                        const int64_t* __restrict__ pre, int np, int* status) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= pre[np]) return;
   const int p = find_prob(pre, np, t);
@@ -1015,7 +1208,43 @@ __global__ void __launch_bounds__(128) k_sample_omega(const RFProb* __restrict__
   for (int64_t e2 = j; e2 < nrt; e2 += q.s) q.zcnt[e2] = 0;
 }
 
+// S1 + S3 with one warp per sample, the form for few samples (a single tensor), where
+// spreading the Gaussians over lanes and SMs shortens the stage: warp j computes pi(j)
+// (every lane walks the same Feistel cycle, so the value is warp-uniform) and lane 0 its
+// fiber offset; the lanes then share row j of Omega (Box-Muller of Philox counters
+// (pi(j), c), one entry per lane and column).  Lane 0 also clears the sketch's
+// per-row-tile counters.  Both forms write the same values.
+__global__ void __launch_bounds__(128) k_sample_omega(const RFProb* __restrict__ P,
+                                                      const int64_t* __restrict__ pre, int np, int* status) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= pre[np]) return;
+  const int p = find_prob(pre, np, w);
+  const RFProb& q = P[p];
+  const int64_t j = w - pre[p];
+  const PhiloxKey key = philox_key(q.seed);
+  const uint64_t m = sample_index((uint64_t)j, (uint64_t)q.N, q.fh, key, q.node, status);
+  float* om = q.Om + j * q.c;
+  for (int c = lane; c < q.c; c += 32) om[c] = gauss_entry(m, (uint32_t)c, key, q.node);
+  if (lane == 0) {
+    q.idx[j] = (int64_t)m;
+    uint64_t rem = m;
+    int64_t off = 0;
+    for (int t2 = q.ncm - 1; t2 >= 0; --t2) {
+      const uint64_t sz = (uint64_t)q.csize[t2];
+      off += (int64_t)(rem % sz) * q.cstride[t2];
+      rem /= sz;
+    }
+    q.off[j] = off;
+    const int64_t nrt = (q.nS + SK_TI - 1) / SK_TI;
+    for (int64_t e2 = j; e2 < nrt; e2 += q.s) q.zcnt[e2] = 0;
+  }
+}
+
 // ------------------------------------------------------------------ host launchers
+// Samples up to which S1 + S3 take one warp per sample (beyond: one thread per sample).
+constexpr int64_t SO_WARP_MAX = 32768;
+
 static size_t smem_gs() { return (size_t)(SK_TJ * SK_TI + SK_TJ * CMAX) * 4 + SK_TJ * 8; }
 static size_t smem_qr() { return (size_t)(2 * QR_MAXF + 2 * CMAX + 1024) * 4 + 64; }
 static size_t smem_qr2() { return (size_t)(2 * QR2_MAXF + 2 * CMAX + 32 + 1024) * 4 + 64; }
@@ -1030,7 +1259,7 @@ static size_t smem_wsvd() {
 }
 static size_t smem_qw() { return (size_t)(CMAX * CMAX + QW_TI * CMAX) * 4 + CMAX * 8; }
 static size_t smem_flip() { return (size_t)(CMAX * CMAX + CMAX) * 4; }
-static size_t smem_qwf() { return (size_t)(CMAX * CMAX + 2 * QWF_MAX * CMAX) * 4 + CMAX * 8 + CMAX * 4; }
+static size_t smem_qwf() { return (size_t)(CMAX * CMAX + 2 * QWF_MAX * CMAX + CMAX) * 4; }
 
 cudaError_t rf_init_attributes() {
   cudaError_t e;
@@ -1062,8 +1291,12 @@ int launch_rf_head(const RFGroup& g, cudaStream_t st, int* status) {
   const int64_t stride = np + 1;
   int n = 0;
   if (g.total[STG_SAMPLE] > 0) {
-    k_sample_omega<<<(unsigned)((g.total[STG_SAMPLE] + 127) / 128), 128, 0, st>>>(
-        g.probs, pre + STG_SAMPLE * stride, np, status);
+    if (g.total[STG_SAMPLE] <= SO_WARP_MAX)
+      k_sample_omega<<<(unsigned)((g.total[STG_SAMPLE] * 32 + 127) / 128), 128, 0, st>>>(
+          g.probs, pre + STG_SAMPLE * stride, np, status);
+    else
+      k_sample_omega_t<<<(unsigned)((g.total[STG_SAMPLE] + 127) / 128), 128, 0, st>>>(
+          g.probs, pre + STG_SAMPLE * stride, np, status);
     n += 1;
   }
   k_gather_sketch<<<grid_of(g.total[STG_GS]), 256, smem_gs(), st>>>(g.probs, pre + STG_GS * stride, np);

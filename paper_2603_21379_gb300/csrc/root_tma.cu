@@ -10,7 +10,7 @@
 //                 ring of RS_NS shared-memory stages; four consumer warps own the
 //                 64 rows of the current block, each thread 4 rows x 4 columns of
 //                 every stage (so one read of its 4 x r_r slice of U_r serves 4
-//                 rows), accumulating in registers over 4 stages and adding those
+//                 rows), accumulating in registers over 8 stages and adding those
 //                 sums with Kahan compensation.  Each warp holds half of the
 //                 columns of 32 rows; at the end of the block its 4 column groups
 //                 are combined with warp shuffles and the half is written to T.
@@ -46,7 +46,7 @@ constexpr int RS_XBYTES = RS_ROWS * RS_COLS * 4;
 constexpr int RS_UMAX = 12;                  // largest r_r
 constexpr int RS_UBYTES = RS_COLS * RS_UMAX * 4;
 
-constexpr int RS_KAHAN = 4;                  // stages summed in plain float32 between Kahan steps
+constexpr int RS_KAHAN = 8;                  // stages summed in plain float32 between Kahan steps
 constexpr int RL_ROWS = 256;                 // rows per CTA of k_root_left
 
 constexpr size_t rs_smem() { return 1024 + (size_t)RS_NS * (RS_XBYTES + RS_UBYTES) + 8 * (2 * RS_NS) + 16; }
