@@ -20,9 +20,12 @@ randomization") that it follows:
                  transfer tensors (Eqs. 4.1/4.2), H-Tucker reconstruction.
 * ``brute``    - deterministic T-HOSVD (Sec. 3) and RtL-HT (Sec. 4) by full
                  SVDs, used only to pin the randomized oracle on tiny inputs.
+* ``tucker_grad`` - gradients of the Tucker misfit 1/2 ||X - G x_k U_k||^2 and
+                 the adjoint of the core projection (Sec. 3 format, Alg. 1
+                 core step); the differentiable extension, not in the paper.
 
 Precision: every floating-point step runs in float64 (the paper's NumPy
 implementation does not state a precision; float64 is NumPy's default).
 """
 
-from . import rng, tucker, htucker, brute  # noqa: F401
+from . import rng, tucker, htucker, brute, tucker_grad  # noqa: F401
