@@ -406,6 +406,7 @@ def run_ours(args):
         extra["batched"] = measure_batched(rt, max(2, min(args.steps, 5)))
         del Xpin, Uh, Gh
         extra["ht"] = measure_ht(rt, max(2, min(args.steps, 5)), peak0)
+        extra["grad"] = measure_grad(rt, max(3, min(args.steps, 10)), peak0)
 
     if rank == 0:
         peak, peak_src = measured_peaks()
@@ -447,6 +448,38 @@ def run_ours(args):
     return 0
 
 
+def measure_grad(rt, steps, peak):
+    """Differentiable Tucker on the order-4 96 workload (96^4 float32, Gaussian 16^4
+    core, Haar factors, 1e-4 noise): the misfit 1/2 ||X - G x_k U_k||^2 and all its
+    gradients (dX, dG, dU) at the Sub-R-HOSVD result (r = 16, p = 8), one
+    rtucker_loss_grad call per step.  Rate against the minimal traffic of the
+    step (X read twice, the residual dX written once: 3 x 0.34 GB)."""
+    import torch
+    import synth
+    cfg = synth.ORDER4_96
+    X = torch.from_numpy(synth.named(cfg)).cuda()
+    r, p = list(cfg["ranks"]), cfg["p"]
+    G, U = rt.rtucker_decompose(X, r, p, seed=cfg["seed"])
+    Uf = torch.cat([u.reshape(-1) for u in U])
+    Ul = list(torch.split(Uf, [u.numel() for u in U]))
+    Ul = [u.view(t.shape) for u, t in zip(Ul, U)]
+    nbytes = X.numel() * 4
+
+    def step():
+        return rt.rtucker_loss_grad(X, G, Ul)
+    ms = _event_time(step, steps, 3)
+    loss = step()[0].item()
+    launches = rt.last_launch_count()
+    floor_bytes = 3 * nbytes
+    del X
+    torch.cuda.empty_cache()
+    return {"workload": "misfit and gradients (dX, dG, dU) of a Tucker model of a 96^4 float32 tensor "
+                        "(Gaussian 16^4 core, Haar factors, 1e-4 noise) at its Sub-R-HOSVD result, r=16, p=8",
+            "ms_per_step": ms, "input_gbs": nbytes / (ms * 1e-3) / 1e9, "loss": loss, "launches": launches,
+            "floor": {"bytes": floor_bytes, "ms_at_peak": floor_bytes / (peak * 1e9) * 1e3,
+                      "frac": (floor_bytes / (ms * 1e-3) / 1e9) / peak, "peak_gbs": peak}}
+
+
 def run_only(args):
     """One workload alone (for profiling): prints its JSON object."""
     import torch
@@ -458,6 +491,8 @@ def run_only(args):
     peak, _ = measured_peaks()
     if args.only == "ht":
         out = measure_ht(rt, args.steps, peak, n=args.ht_n, d=args.ht_d)
+    elif args.only == "grad":
+        out = measure_grad(rt, args.steps, peak)
     else:
         out = measure_batched(rt, args.steps)
     print(json.dumps({"only": args.only, **out}))
@@ -471,12 +506,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["ht", "batched"], default=None,
+    ap.add_argument("--only", choices=["ht", "batched", "grad"], default=None,
                     help="run one extra workload alone (profiling), not the benchmark line")
     ap.add_argument("--ht-n", type=int, default=None, help="grid size of the H-Tucker workload with --only ht")
     ap.add_argument("--ht-d", type=int, default=None, help="order of the H-Tucker workload with --only ht")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the BF16 forms, the batched and the H-Tucker workloads (untimed extras)")
+                    help="skip the BF16 forms, the batched, H-Tucker and gradient workloads (untimed extras)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

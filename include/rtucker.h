@@ -186,6 +186,35 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
                                     const int64_t* const* s, const uint64_t* seeds,
                                     const rt_options* opt, float* const* U, float* const* G);
 
+/* ----------------------------------------------------- differentiable Tucker
+ * Gradients of the Tucker format (Sec. 3: X ~ Xhat = G x_1 U_1 ... x_d U_d) for
+ * training through a decomposition; an extension of the paper (not in it).
+ *
+ * rtucker_loss_grad: the misfit L = 1/2 ||X - Xhat||_F^2 and its gradients
+ *   dX = R = X - Xhat                          (n_1 x ... x n_d, C order)
+ *   dG = -R x_1 U_1^T ... x_d U_d^T            (r_1 x ... x r_d, C order)
+ *   dU = concat_n -[R x_{m != n} U_m^T]_(n) G_(n)^T   (n_n x r_n row-major each)
+ * X: DEVICE tensor (float32 / float64 / bfloat16); U (concat n_k x r_k) and G:
+ * DEVICE float32, e.g. the outputs of rtucker_decompose.  Outputs (DEVICE,
+ * caller-owned, each may be NULL): loss (one float64), dX, dG, dU (float32).
+ * Without dX the residual lives in handle workspace (prod n floats) while dG
+ * or dU are formed.  1 <= r_k <= 64.  Asynchronous on the handle's stream.
+ * Arithmetic: float32 with the residual's squared norm summed in float32 per
+ * thread and tile and in float64 across tiles and CTAs. */
+rt_status rtucker_loss_grad(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                            const int32_t* r, const float* U, const float* G, double* loss, float* dX,
+                            float* dG, float* dU);
+
+/* Adjoint of the core projection G = X x_1 U_1^T ... x_d U_d^T (the core step of
+ * Alg. 1): for an upstream gradient Gbar (r_1 x ... x r_d, DEVICE float32),
+ *   Xbar = Gbar x_1 U_1 ... x_d U_d                    (n_1 x ... x n_d)
+ *   Ubar = concat_n [X x_{m != n} U_m^T]_(n) Gbar_(n)^T  (n_n x r_n each)
+ * Xbar and Ubar: DEVICE float32, caller-owned, either may be NULL.  Other
+ * arguments and conventions as rtucker_loss_grad. */
+rt_status rtucker_core_adjoint(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                               const int32_t* r, const float* U, const float* Gbar, float* Xbar,
+                               float* Ubar);
+
 /* Relative reconstruction error ||X - (U_1..U_d) G||_F / ||X||_F computed on
  * the device in float64 (evaluator; not part of the decomposition).  The
  * result is written to *out (HOST) after the call synchronises the stream. */

@@ -22,6 +22,7 @@ __all__ = [
     "rtucker_decompose_host", "rtucker_decompose_host_async", "rtucker_decompose_batched", "rtucker_relerr",
     "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "last_launch_count", "workspace_bytes",
     "set_timing", "get_timing", "STAGES", "rhtucker_root_transfer_noalloc", "BatchedDecomposition",
+    "rtucker_loss_grad", "rtucker_core_adjoint",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -91,6 +92,9 @@ def load_library():
                                                      ctypes.POINTER(P64), PU64, PO, ctypes.POINTER(vp),
                                                      ctypes.POINTER(vp)]),
         "rtucker_relerr": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, vp, vp, PD]),
+        "rtucker_loss_grad": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, vp, vp, vp, vp, vp,
+                                             vp]),
+        "rtucker_core_adjoint": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, vp, vp, vp, vp]),
         "rhtucker_decompose": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64, PO,
                                               vp, vp, vp]),
         "rhtucker_relerr": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, vp, vp, PD]),
@@ -359,6 +363,57 @@ def rtucker_decompose_host_async(X, r, p, s=None, seed=0, out=None, prec="fp32")
                                                ctypes.c_uint64(seed), _opts(prec), _ptr(U), _ptr(G)))
     _in_flight.setdefault(h.value, []).append((X, U, G))
     return G, _split(U, n, r)
+
+
+def _flat_factors(U, n, r, device):
+    if len(U) != len(n):
+        raise ValueError("one factor per mode")
+    for u, nk, rk in zip(U, n, r):
+        if tuple(u.shape) != (nk, rk) or u.dtype != torch.float32 or u.device != device:
+            raise ValueError("U_k must be float32 n_k x r_k tensors on X's device")
+    return torch.cat([u.reshape(-1) for u in U])
+
+
+def rtucker_loss_grad(X, G, U, dX=True, dG=True, dU=True):
+    """Misfit L = 1/2 ||X - G x_1 U_1 ... x_d U_d||_F^2 of a Tucker model and its
+    gradients (device float32): returns (loss as a 0-d float64 device tensor, dL/dX,
+    dL/dG, [dL/dU_k]); a gradient not asked for is None."""
+    lib = load_library()
+    if not X.is_cuda or X.dtype not in _DT or not X.is_contiguous():
+        raise ValueError("X must be a contiguous CUDA tensor of float32/float64/bfloat16")
+    d, n = X.dim(), list(X.shape)
+    r = list(G.shape)
+    if len(r) != d or G.dtype != torch.float32 or not G.is_contiguous() or G.device != X.device:
+        raise ValueError("G must be a contiguous float32 r_1 x ... x r_d tensor on X's device")
+    Uf = _flat_factors(U, n, r, X.device)
+    loss = torch.empty((), dtype=torch.float64, device=X.device)
+    gX = torch.empty_like(X, dtype=torch.float32) if dX else None
+    gG = torch.empty_like(G) if dG else None
+    gU = torch.empty_like(Uf) if dU else None
+    h = _handle()
+    _check(h, lib.rtucker_loss_grad(h, _ptr(X), _DT[X.dtype], d, _i64(n), _i32(r), _ptr(Uf), _ptr(G), _ptr(loss),
+                                    _ptr(gX), _ptr(gG), _ptr(gU)))
+    return loss, gX, gG, (_split(gU, n, r) if dU else None)
+
+
+def rtucker_core_adjoint(X, U, Gbar, Xbar=True, Ubar=True):
+    """Adjoint of the core projection G = X x_1 U_1^T ... x_d U_d^T for an upstream
+    gradient Gbar: returns (Xbar = Gbar x_k U_k, [Ubar_k]) (device float32); a result
+    not asked for is None."""
+    lib = load_library()
+    if not X.is_cuda or X.dtype not in _DT or not X.is_contiguous():
+        raise ValueError("X must be a contiguous CUDA tensor of float32/float64/bfloat16")
+    d, n = X.dim(), list(X.shape)
+    r = list(Gbar.shape)
+    if len(r) != d or Gbar.dtype != torch.float32 or not Gbar.is_contiguous() or Gbar.device != X.device:
+        raise ValueError("Gbar must be a contiguous float32 r_1 x ... x r_d tensor on X's device")
+    Uf = _flat_factors(U, n, r, X.device)
+    xb = torch.empty(n, dtype=torch.float32, device=X.device) if Xbar else None
+    ub = torch.empty_like(Uf) if Ubar else None
+    h = _handle()
+    _check(h, lib.rtucker_core_adjoint(h, _ptr(X), _DT[X.dtype], d, _i64(n), _i32(r), _ptr(Uf), _ptr(Gbar),
+                                       _ptr(xb), _ptr(ub)))
+    return xb, (_split(ub, n, r) if Ubar else None)
 
 
 class BatchedDecomposition:

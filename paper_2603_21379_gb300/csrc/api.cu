@@ -1017,6 +1017,242 @@ rt_status rtucker_core(rt_handle h, const void* X, rt_dtype dtype, int d, const 
   return finish(h, nl);
 }
 
+// --- differentiable Tucker ----------------------------------------------------
+namespace {
+
+// Largest intermediate of the expansion of the leading d-2 modes of an
+// r_0 x ... x r_{d-1} core (mode k: r_k -> n_k, k < d-2).
+size_t expand_buffer_floats(int d, const int64_t* n, const int32_t* r) {
+  size_t cur = 1;
+  for (int k = 0; k < d; ++k) cur *= (size_t)r[k];
+  size_t best = cur;
+  for (int k = 0; k + 2 < d; ++k) {
+    cur = cur / (size_t)r[k] * (size_t)n[k];
+    best = std::max(best, cur);
+  }
+  return best;
+}
+
+// out = alpha X + beta C x_0 U_0 ... x_{d-1} U_{d-1} (X may be null): the leading
+// d-2 modes of C expanded into H (two ping-pong buffers), then the last two per
+// slab of H; sumsq (device, may be null) receives scale * ||out||_F^2.
+int enqueue_expand(rt_handle h, const float* C, int d, const int64_t* n, const int32_t* r, const float* U,
+                   const size_t* uoff, const void* X, int dtype, float alpha, float beta, float* out, float* bufA,
+                   float* bufB, double* part, double* sumsq, double scale) {
+  cudaStream_t st = h->stream;
+  const float* A = C;
+  int64_t L = 1;
+  int nl = 0;
+  for (int k = 0; k + 2 < d; ++k) {
+    int64_t R = 1;
+    for (int j = k + 1; j < d; ++j) R *= r[j];
+    float* o = (k % 2 == 0) ? bufA : bufB;
+    nl += launch_expand_f32(A, L, r[k], R, U + uoff[k], n[k], o, st);
+    A = o;
+    L *= n[k];
+  }
+  nl += launch_tucker_slab_out(X, dtype, alpha, beta, A, L, n[d - 2], r[d - 2], n[d - 1], r[d - 1],
+                               U + uoff[d - 2], U + uoff[d - 1], out, part, sumsq, scale, st);
+  return nl;
+}
+
+// Plan of the partial projections Y_n = T x_{m != n} U_m^T of an n_0 x ... x n_{d-1}
+// tensor T: the prefixes P_k = T x_0 U_0^T ... x_{k-1} U_{k-1}^T (k = 1 .. d-1) are
+// kept, and Y_n continues from P_n (P_0 = T) over modes n+1 .. d-1.  Leading modes
+// go first so that every contraction of a large tensor has a long contiguous
+// trailing extent (the fast TTM form); only reduced tensors see a last-mode step.
+struct PartialPlan {
+  size_t prefix_floats[MAXD + 1] = {0};  // size of P_k
+  size_t chain_floats = 1;               // largest intermediate of a continuation
+  size_t y_floats = 1;                   // largest Y_n
+};
+
+PartialPlan plan_partials(int d, const int64_t* n, const int32_t* r) {
+  PartialPlan pl;
+  for (int k = 1; k < d; ++k) {
+    size_t s = 1;
+    for (int j = 0; j < k; ++j) s *= (size_t)r[j];
+    for (int j = k; j < d; ++j) s *= (size_t)n[j];
+    pl.prefix_floats[k] = s;
+  }
+  for (int m = 0; m < d; ++m) {
+    int64_t sh[MAXD];
+    for (int j = 0; j < d; ++j) sh[j] = (j < m) ? r[j] : n[j];
+    for (int j = m + 1; j < d; ++j) {
+      sh[j] = r[j];
+      size_t s = 1;
+      for (int q = 0; q < d; ++q) s *= (size_t)sh[q];
+      if (j < d - 1) pl.chain_floats = std::max(pl.chain_floats, s);
+      else pl.y_floats = std::max(pl.y_floats, s);
+    }
+  }
+  return pl;
+}
+
+// outU (concatenated n_n x r_n, may be null) = scale [T x_{m != n} U_m^T]_(n) C_(n)^T
+// for every n, and outCore (may be null) = scale T x_k U_k^T.  T has element type
+// dtype; prefix[k] hold P_k, chainA/B the continuations, ybuf the finished Y_n.
+int enqueue_partials(rt_handle h, const void* T, int dtype, int d, const int64_t* n, const int32_t* r,
+                     const float* U, const size_t* uoff, const float* C, float scale, float* outU, float* outCore,
+                     float* const* prefix, float* chainA, float* chainB, float* ybuf, float* uscratch) {
+  cudaStream_t st = h->stream;
+  int nl = 0;
+  const void* A = T;
+  int adt = dtype;
+  for (int k = 1; k < d; ++k) {        // P_k = P_{k-1} x_{k-1} U_{k-1}^T
+    int64_t L = 1, R = 1;
+    for (int j = 0; j < k - 1; ++j) L *= r[j];
+    for (int j = k; j < d; ++j) R *= n[j];
+    nl += launch_ttm_t(A, adt, L, n[k - 1], R, U + uoff[k - 1], r[k - 1], prefix[k], st);
+    A = prefix[k];
+    adt = DT_F32;
+  }
+  if (outCore) {                       // P_{d-1} x_{d-1} U_{d-1}^T
+    int64_t L = 1;
+    for (int j = 0; j < d - 1; ++j) L *= r[j];
+    nl += launch_ttm_t(prefix[d - 1], DT_F32, L, n[d - 1], 1, U + uoff[d - 1], r[d - 1], outCore, st);
+    if (scale != 1.f) nl += launch_scale_f32(outCore, L * r[d - 1], scale, st);
+  }
+  if (!outU) return nl;
+  for (int m = 0; m < d; ++m) {
+    const void* Y = (m == 0) ? T : (const void*)prefix[m];
+    int ydt = (m == 0) ? dtype : DT_F32;
+    int64_t sh[MAXD];
+    for (int j = 0; j < d; ++j) sh[j] = (j < m) ? r[j] : n[j];
+    int ping = 0;
+    for (int j = m + 1; j < d; ++j) {
+      int64_t L = 1, R = 1;
+      for (int q = 0; q < j; ++q) L *= sh[q];
+      for (int q = j + 1; q < d; ++q) R *= sh[q];
+      float* o = (j == d - 1) ? ybuf : (ping ? chainB : chainA);
+      nl += launch_ttm_t(Y, ydt, L, sh[j], R, U + uoff[j], r[j], o, st);
+      sh[j] = r[j];
+      Y = o;
+      ydt = DT_F32;
+      ping ^= 1;
+    }
+    if (ydt != DT_F32) return -1;      // only for d = 1, excluded by the argument checks
+    int64_t P = 1, Q = 1;
+    for (int j = 0; j < m; ++j) P *= r[j];
+    for (int j = m + 1; j < d; ++j) Q *= r[j];
+    const int got = launch_unfold_contract(static_cast<const float*>(Y), C, P, n[m], r[m], Q, scale,
+                                           outU + uoff[m], uscratch, st);
+    if (got <= 0) return -1;
+    nl += got;
+  }
+  return nl;
+}
+
+rt_status check_grad_args(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
+                          const float* U, const float* C, int64_t* total) {
+  rt_status st;
+  if ((st = check_tensor(h, X, dtype, d, n, total)) != RT_OK) return st;
+  if (!r || !U || !C) return fail(h, RT_EINVAL, "r, U and the core are required");
+  for (int k = 0; k < d; ++k)
+    if (r[k] < 1 || r[k] > CMAX) return fail(h, RT_EINVAL, "need 1 <= r_k <= 64");
+  if ((st = check_prior_status(h)) != RT_OK) return st;
+  return init_device_attrs(h);
+}
+
+}  // namespace
+
+rt_status rtucker_loss_grad(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
+                            const float* U, const float* G, double* loss, float* dX, float* dG, float* dU) {
+  int64_t total = 0;
+  rt_status st = check_grad_args(h, X, dtype, d, n, r, U, G, &total);
+  if (st != RT_OK) return st;
+  size_t uoff[MAXD];
+  size_t acc = 0;
+  for (int k = 0; k < d; ++k) { uoff[k] = acc; acc += (size_t)n[k] * r[k]; }
+  const bool grads = dG || dU;
+  Bump bump;
+  const size_t eb = expand_buffer_floats(d, n, r);
+  const size_t oEA = bump.take(eb * 4), oEB = bump.take(eb * 4);
+  const size_t oPart = bump.take(expand_partial_doubles() * 8);
+  const size_t oR = (!dX && grads) ? bump.take((size_t)total * 4) : 0;
+  PartialPlan pl = plan_partials(d, n, r);
+  size_t oS[MAXD + 1] = {0};
+  size_t oCA = 0, oCB = 0, oY = 0, oUS = 0;
+  if (grads) {
+    for (int k = 1; k < d; ++k) oS[k] = bump.take(pl.prefix_floats[k] * 4);
+    oCA = bump.take(pl.chain_floats * 4);
+    oCB = bump.take(pl.chain_floats * 4);
+    oY = bump.take(pl.y_floats * 4);
+    size_t us = 1;
+    for (int m = 0; m < d; ++m) us = std::max(us, unfold_scratch_floats(n[m], r[m]));
+    oUS = bump.take(us * 4);
+  }
+  if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
+  char* ws = h->ws;
+  float* R = dX ? dX : reinterpret_cast<float*>(ws + oR);
+  int nl = 0;
+  if (dX || grads || loss) {
+    float* out = (dX || grads) ? R : nullptr;   // loss only: the residual is not stored
+    const int got = enqueue_expand(h, G, d, n, r, U, uoff, X, dtype, 1.f, -1.f, out,
+                                   reinterpret_cast<float*>(ws + oEA), reinterpret_cast<float*>(ws + oEB),
+                                   reinterpret_cast<double*>(ws + oPart), loss, 0.5);
+    if (got <= 0) return fail(h, RT_ENOTSUP, "ranks too large for the reconstruction kernel");
+    nl += got;
+    R = out;
+  }
+  if (grads) {
+    float* prefix[MAXD + 1] = {nullptr};
+    for (int k = 1; k < d; ++k) prefix[k] = reinterpret_cast<float*>(ws + oS[k]);
+    const int got = enqueue_partials(h, R, DT_F32, d, n, r, U, uoff, G, -1.f, dU, dG, prefix,
+                                     reinterpret_cast<float*>(ws + oCA), reinterpret_cast<float*>(ws + oCB),
+                                     reinterpret_cast<float*>(ws + oY), reinterpret_cast<float*>(ws + oUS));
+    if (got < 0) return fail(h, RT_EINVAL, "internal: partial projection plan");
+    nl += got;
+  }
+  return finish(h, nl);
+}
+
+rt_status rtucker_core_adjoint(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                               const int32_t* r, const float* U, const float* Gbar, float* Xbar, float* Ubar) {
+  int64_t total = 0;
+  rt_status st = check_grad_args(h, X, dtype, d, n, r, U, Gbar, &total);
+  if (st != RT_OK) return st;
+  size_t uoff[MAXD];
+  size_t acc = 0;
+  for (int k = 0; k < d; ++k) { uoff[k] = acc; acc += (size_t)n[k] * r[k]; }
+  Bump bump;
+  const size_t eb = expand_buffer_floats(d, n, r);
+  const size_t oEA = bump.take(eb * 4), oEB = bump.take(eb * 4);
+  const size_t oPart = bump.take(expand_partial_doubles() * 8);
+  PartialPlan pl = plan_partials(d, n, r);
+  size_t oS[MAXD + 1] = {0};
+  size_t oCA = 0, oCB = 0, oY = 0, oUS = 0;
+  if (Ubar) {
+    for (int k = 1; k < d; ++k) oS[k] = bump.take(pl.prefix_floats[k] * 4);
+    oCA = bump.take(pl.chain_floats * 4);
+    oCB = bump.take(pl.chain_floats * 4);
+    oY = bump.take(pl.y_floats * 4);
+    size_t us = 1;
+    for (int m = 0; m < d; ++m) us = std::max(us, unfold_scratch_floats(n[m], r[m]));
+    oUS = bump.take(us * 4);
+  }
+  if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
+  char* ws = h->ws;
+  int nl = 0;
+  if (Xbar) {
+    const int got = enqueue_expand(h, Gbar, d, n, r, U, uoff, nullptr, (int)dtype, 0.f, 1.f, Xbar,
+                                   reinterpret_cast<float*>(ws + oEA), reinterpret_cast<float*>(ws + oEB),
+                                   reinterpret_cast<double*>(ws + oPart), nullptr, 1.0);
+    if (got <= 0) return fail(h, RT_ENOTSUP, "ranks too large for the reconstruction kernel");
+    nl += got;
+  }
+  if (Ubar) {
+    float* prefix[MAXD + 1] = {nullptr};
+    for (int k = 1; k < d; ++k) prefix[k] = reinterpret_cast<float*>(ws + oS[k]);
+    const int got = enqueue_partials(h, X, (int)dtype, d, n, r, U, uoff, Gbar, 1.f, Ubar, nullptr, prefix,
+                                     reinterpret_cast<float*>(ws + oCA), reinterpret_cast<float*>(ws + oCB),
+                                     reinterpret_cast<float*>(ws + oY), reinterpret_cast<float*>(ws + oUS));
+    if (got < 0) return fail(h, RT_EINVAL, "internal: partial projection plan");
+    nl += got;
+  }
+  return finish(h, nl);
+}
+
 rt_status rtucker_decompose_host(rt_handle h, const void* X_host, rt_dtype dtype, int d, const int64_t* n,
                                  const int32_t* r, int32_t p, const int64_t* s, uint64_t seed,
                                  const rt_options* opt, float* U_host, float* G_host) {

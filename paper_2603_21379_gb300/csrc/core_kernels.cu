@@ -135,43 +135,46 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int TN>
-constexpr size_t ttm_f32_smem() { return (size_t)TF_TS * TF_TK * (TN + 32) * sizeof(float); }
+// AW: width of the block's slice of a (32, or 16 for r <= 16, which halves the products
+// and, with a K stage of AW rows, the shared memory).
+template <int TN, int AW>
+constexpr size_t ttm_f32_smem() { return (size_t)TF_TS * AW * (TN + AW) * sizeof(float); }
 
-template <int TN>
-__global__ void __launch_bounds__(TN / 2) k_ttm_f32(const float* __restrict__ A, int64_t n, int64_t R,
+template <int TN, int AW>
+__global__ void __launch_bounds__(AW * TN / 64) k_ttm_f32(const float* __restrict__ A, int64_t n, int64_t R,
                                                     int64_t tiles_per_l, const float* __restrict__ U, int r,
                                                     float* __restrict__ out) {
-  constexpr int NT = TN / 2;               // threads: 4 a-groups x TN/8 rho-groups
+  constexpr int NT = AW * TN / 64;         // threads: AW/8 a-groups x TN/8 rho-groups
+  constexpr int TK = AW;                   // rows of A and U per stage
   extern __shared__ __align__(16) float tsm[];
   float* As = tsm;                          // [TS][TK][TN]
-  float* Us = tsm + TF_TS * TF_TK * TN;     // [TS][TK][32]
+  float* Us = tsm + TF_TS * TK * TN;        // [TS][TK][AW]
   const int tid = threadIdx.x;
   const int64_t l = blockIdx.x / tiles_per_l;
   const int64_t rho0 = (blockIdx.x - l * tiles_per_l) * TN;
-  const int a0 = blockIdx.y * 32;
+  const int a0 = blockIdx.y * AW;
   const int ta = tid / (TN / 8), tr = tid % (TN / 8);
   const float* Al = A + l * n * R;
-  const int nk = (int)((n + TF_TK - 1) / TF_TK);
+  const int nk = (int)((n + TK - 1) / TK);
 
   auto issue = [&](int kt) {
     const int stg = kt % TF_TS;
-    float* as = As + stg * TF_TK * TN;
-    float* us = Us + stg * TF_TK * 32;
-    const int64_t i0 = (int64_t)kt * TF_TK;
+    float* as = As + stg * TK * TN;
+    float* us = Us + stg * TK * AW;
+    const int64_t i0 = (int64_t)kt * TK;
 #pragma unroll
-    for (int e = tid; e < TF_TK * TN / 4; e += NT) {
+    for (int e = tid; e < TK * TN / 4; e += NT) {
       const int kk = e / (TN / 4), c4 = (e % (TN / 4)) * 4;
       const int64_t i = i0 + kk, rho = rho0 + c4;
       const bool ok = i < n && rho < R;
       cp_async16(as + kk * TN + c4, ok ? (const void*)(Al + i * R + rho) : (const void*)A, ok ? 16 : 0);
     }
 #pragma unroll
-    for (int e = tid; e < TF_TK * 32; e += NT) {
-      const int kk = e / 32, aa = e % 32;
+    for (int e = tid; e < TK * AW; e += NT) {
+      const int kk = e / AW, aa = e % AW;
       const int64_t i = i0 + kk;
       const bool ok = i < n && a0 + aa < r;
-      cp_async4(us + kk * 32 + aa, ok ? (const void*)(U + i * r + a0 + aa) : (const void*)U, ok ? 4 : 0);
+      cp_async4(us + kk * AW + aa, ok ? (const void*)(U + i * r + a0 + aa) : (const void*)U, ok ? 4 : 0);
     }
   };
 
@@ -191,12 +194,12 @@ __global__ void __launch_bounds__(TN / 2) k_ttm_f32(const float* __restrict__ A,
     __syncthreads();
     if (kt + TF_TS - 1 < nk) issue(kt + TF_TS - 1);
     cp_async_commit();
-    const float* as = As + (kt % TF_TS) * TF_TK * TN + tr * 4;
-    const float* us = Us + (kt % TF_TS) * TF_TK * 32 + ta * 8;
+    const float* as = As + (kt % TF_TS) * TK * TN + tr * 4;
+    const float* us = Us + (kt % TF_TS) * TK * AW + ta * 8;
 #pragma unroll 8
-    for (int kk = 0; kk < TF_TK; ++kk) {
-      const float4 u0 = *reinterpret_cast<const float4*>(us + kk * 32);
-      const float4 u1 = *reinterpret_cast<const float4*>(us + kk * 32 + 4);
+    for (int kk = 0; kk < TK; ++kk) {
+      const float4 u0 = *reinterpret_cast<const float4*>(us + kk * AW);
+      const float4 u1 = *reinterpret_cast<const float4*>(us + kk * AW + 4);
       const float4 b0 = *reinterpret_cast<const float4*>(as + kk * TN);
       const float4 b1 = *reinterpret_cast<const float4*>(as + kk * TN + TN / 2);
       const float ua[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
@@ -233,19 +236,28 @@ static int g_num_sms = 0;
 int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, const float* U, int r,
                  float* out, cudaStream_t st) {
   const int64_t ncol = L * R;
-  if (dtype == DT_F32 && R >= 128 && R % 4 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
+  if (dtype == DT_F32 && R >= 64 && R % 4 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
       (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
-    // rho-contiguous FP32 form; the narrower tile when the wide one leaves SMs idle
-    const int64_t t256 = (R + 255) / 256;
-    const unsigned gy = (unsigned)((r + 31) / 32);
-    if (L * t256 * gy >= 2 * (int64_t)g_num_sms) {
-      dim3 grid((unsigned)(L * t256), gy);
-      k_ttm_f32<256><<<grid, 128, ttm_f32_smem<256>(), st>>>(static_cast<const float*>(A), n, R, t256, U, r, out);
-    } else {
-      const int64_t t128 = (R + 127) / 128;
-      dim3 grid((unsigned)(L * t128), gy);
-      k_ttm_f32<128><<<grid, 64, ttm_f32_smem<128>(), st>>>(static_cast<const float*>(A), n, R, t128, U, r, out);
+    // rho-contiguous FP32 form; the narrower tile when the wide one leaves SMs idle or
+    // R is shorter than it (the tail of a tile is masked)
+    const int64_t t256 = (R + 255) / 256, t128 = (R + 127) / 128;
+    const float* Af = static_cast<const float*>(A);
+    if (r <= 16) {
+      if (R >= 256 && L * t256 >= 2 * (int64_t)g_num_sms)
+        k_ttm_f32<256, 16><<<dim3((unsigned)(L * t256), 1), 64, ttm_f32_smem<256, 16>(), st>>>(Af, n, R, t256, U, r,
+                                                                                               out);
+      else
+        k_ttm_f32<128, 16><<<dim3((unsigned)(L * t128), 1), 32, ttm_f32_smem<128, 16>(), st>>>(Af, n, R, t128, U, r,
+                                                                                               out);
+      return 1;
     }
+    const unsigned gy = (unsigned)((r + 31) / 32);
+    if (R >= 256 && L * t256 * gy >= 2 * (int64_t)g_num_sms)
+      k_ttm_f32<256, 32><<<dim3((unsigned)(L * t256), gy), 128, ttm_f32_smem<256, 32>(), st>>>(Af, n, R, t256, U, r,
+                                                                                               out);
+    else
+      k_ttm_f32<128, 32><<<dim3((unsigned)(L * t128), gy), 64, ttm_f32_smem<128, 32>(), st>>>(Af, n, R, t128, U, r,
+                                                                                              out);
     return 1;
   }
   dim3 grid((unsigned)((ncol + TT_BN - 1) / TT_BN), (unsigned)((r + TT_BM - 1) / TT_BM));
@@ -277,10 +289,12 @@ cudaError_t core_init_attributes() {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ttm_f32<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ttm_f32_smem<256>());
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_ttm_f32<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ttm_f32_smem<128>());
+#define RT_TTM_ATTR(TN, AW)                                                                              \
+  if (e == cudaSuccess)                                                                                    \
+    e = cudaFuncSetAttribute(k_ttm_f32<TN, AW>, cudaFuncAttributeMaxDynamicSharedMemorySize,                \
+                             (int)ttm_f32_smem<TN, AW>());
+  RT_TTM_ATTR(256, 32) RT_TTM_ATTR(128, 32) RT_TTM_ATTR(256, 16) RT_TTM_ATTR(128, 16)
+#undef RT_TTM_ATTR
   return e;
 }
 

@@ -66,6 +66,23 @@ int64_t ttm_job_tiles(TTMJob& q);  // sets tiles_x, returns the job's CTA count
 int launch_ttm_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs, int64_t total_tiles, int dtype,
                        cudaStream_t st);
 cudaError_t core_init_attributes();
+// ---- differentiable Tucker (grad_kernels.cu)
+// out(l, i, rho) = sum_a U[i][a] A(l, a, rho) (one core mode expanded, float32).
+int launch_expand_f32(const float* A, int64_t L, int r, int64_t R, const float* U, int64_t n, float* out,
+                      cudaStream_t st);
+// out(s, i, j) = alpha X(s, i, j) + beta (U1 H_s U2^T)(i, j) for nslab slabs (X may be
+// null); when sumsq_scaled is non-null it receives scale * ||out||_F^2 (part: per-CTA
+// float64 partials, expand_partial_doubles() entries).  Returns 0 if r1, r2 are too large.
+size_t expand_partial_doubles();
+int launch_tucker_slab_out(const void* X, int dtype, float alpha, float beta, const float* H, int64_t nslab,
+                           int64_t n1, int r1, int64_t n2, int r2, const float* U1, const float* U2, float* out,
+                           double* part, double* sumsq_scaled, double scale, cudaStream_t st);
+// out[i][a] = scale * sum_{p,q} Y(p, i, q) C(p, a, q) (Y of P x n x Q, C of P x r x Q);
+// scratch: unfold_scratch_floats(n, r) floats.
+size_t unfold_scratch_floats(int64_t n, int r);
+int launch_unfold_contract(const float* Y, const float* C, int64_t P, int64_t n, int r, int64_t Q, float scale,
+                           float* out, float* scratch, cudaStream_t st);
+int launch_scale_f32(float* x, int64_t n, float s, cudaStream_t st);
 // Fused pass over X on tensor cores: P[s] = U1^T X[s] U2 for S slabs of
 // n1 x n2.  X float32 (xbf16 = 0: two bf16 terms) or bfloat16 (xbf16 = 1).
 // Returns 0 when the shape is unsupported.
