@@ -1179,7 +1179,12 @@ rt_status rtucker_loss_grad(rt_handle h, const void* X, rt_dtype dtype, int d, c
     oCB = bump.take(pl.chain_floats * 4);
     oY = bump.take(pl.y_floats * 4);
     size_t us = 1;
-    for (int m = 0; m < d; ++m) us = std::max(us, unfold_scratch_floats(n[m], r[m]));
+    for (int m = 0; m < d; ++m) {
+      int64_t K = 1;
+      for (int j = 0; j < d; ++j)
+        if (j != m) K *= r[j];
+      us = std::max(us, unfold_scratch_floats(n[m], r[m], K));
+    }
     oUS = bump.take(us * 4);
   }
   if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
@@ -1228,7 +1233,12 @@ rt_status rtucker_core_adjoint(rt_handle h, const void* X, rt_dtype dtype, int d
     oCB = bump.take(pl.chain_floats * 4);
     oY = bump.take(pl.y_floats * 4);
     size_t us = 1;
-    for (int m = 0; m < d; ++m) us = std::max(us, unfold_scratch_floats(n[m], r[m]));
+    for (int m = 0; m < d; ++m) {
+      int64_t K = 1;
+      for (int j = 0; j < d; ++j)
+        if (j != m) K *= r[j];
+      us = std::max(us, unfold_scratch_floats(n[m], r[m], K));
+    }
     oUS = bump.take(us * 4);
   }
   if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;

@@ -231,11 +231,70 @@ __global__ void __launch_bounds__(AW * TN / 64) k_ttm_f32(const float* __restric
   }
 }
 
+// Last-mode contraction out(l, a) = sum_i U[i][a] A(l, i) (R = 1): one thread per row
+// l reads its n contiguous floats (16-byte loads when n % 4 == 0), U sits in shared
+// memory and is read as 16-byte broadcasts along a; RW >= r partial sums per thread.
+constexpr int TL_THREADS = 128;
+template <int RW>
+__global__ void __launch_bounds__(TL_THREADS) k_ttm_last(const float* __restrict__ A, int64_t L, int n,
+                                                         const float* __restrict__ U, int r,
+                                                         float* __restrict__ out) {
+  extern __shared__ __align__(16) float us[];   // [n][RW], zero beyond r
+  for (int e = threadIdx.x; e < n * RW; e += TL_THREADS) {
+    const int i = e / RW, a = e % RW;
+    us[e] = a < r ? U[i * r + a] : 0.f;
+  }
+  __syncthreads();
+  const int64_t l = (int64_t)blockIdx.x * TL_THREADS + threadIdx.x;
+  if (l >= L) return;
+  const float* row = A + l * n;
+  float acc[RW];
+#pragma unroll
+  for (int a = 0; a < RW; ++a) acc[a] = 0.f;
+  const bool v4 = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  for (int i0 = 0; i0 < n; i0 += 4) {
+    float x[4];
+    if (v4) {
+      const float4 f = __ldg(reinterpret_cast<const float4*>(row + i0));
+      x[0] = f.x; x[1] = f.y; x[2] = f.z; x[3] = f.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x[q] = i0 + q < n ? __ldg(row + i0 + q) : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (i0 + q >= n) break;
+      const float* ui = us + (i0 + q) * RW;
+#pragma unroll
+      for (int a = 0; a < RW; a += 4) {
+        const float4 u = *reinterpret_cast<const float4*>(ui + a);
+        acc[a] = fmaf(x[q], u.x, acc[a]);
+        acc[a + 1] = fmaf(x[q], u.y, acc[a + 1]);
+        acc[a + 2] = fmaf(x[q], u.z, acc[a + 2]);
+        acc[a + 3] = fmaf(x[q], u.w, acc[a + 3]);
+      }
+    }
+  }
+  float* o = out + l * r;
+#pragma unroll
+  for (int a = 0; a < RW; ++a)
+    if (a < r) o[a] = acc[a];
+}
+
 static int g_num_sms = 0;
 
 int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, const float* U, int r,
                  float* out, cudaStream_t st) {
   const int64_t ncol = L * R;
+  if (dtype == DT_F32 && R == 1 && n <= 256 && r <= 32 && L <= ((int64_t)1 << 40)) {
+    const unsigned blocks = (unsigned)((L + TL_THREADS - 1) / TL_THREADS);
+    const float* Af = static_cast<const float*>(A);
+    if (r <= 16)
+      k_ttm_last<16><<<blocks, TL_THREADS, (size_t)n * 16 * 4, st>>>(Af, L, (int)n, U, r, out);
+    else
+      k_ttm_last<32><<<blocks, TL_THREADS, (size_t)n * 32 * 4, st>>>(Af, L, (int)n, U, r, out);
+    return 1;
+  }
   if (dtype == DT_F32 && R >= 64 && R % 4 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0 &&
       (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
     // rho-contiguous FP32 form; the narrower tile when the wide one leaves SMs idle or

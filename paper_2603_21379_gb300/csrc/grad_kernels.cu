@@ -36,102 +36,113 @@ __global__ void k_expand_f32(const float* __restrict__ A, int64_t L, int r, int6
 }
 
 constexpr int SO_THREADS = 256;
-constexpr int SO_TR = 32, SO_TC = 64;            // output tile: 32 rows x 64 columns, 2 x 4 per thread
 
 // Per slab s of the leading d-2 modes (H_s = H[s], r1 x r2):
 //   out(s, i, j) = alpha X(s, i, j) + beta sum_a U1[i][a] sum_b H_s[a][b] U2[j][b].
-// U1 and U2 (transposed) stay in shared memory for the whole kernel; per slab T = H_s U2^T
-// (r1 x n2) goes to shared memory, then out = U1 T by 32 x 64 tiles, each thread a
-// 2 x 4 register tile (rows ty + 16 u, columns 4 tx .. + 3), T read as float4.
+// U1 and U2 stay in shared memory, transposed (U1t[a][i], U2t[b][j]), for the whole
+// kernel.  Per slab: T = H_s U2^T (r1 x n2) in shared memory, one thread per column
+// j computing all r1 entries (U2t read along j, H_s^T as 16-byte broadcasts); then
+// out = U1 T by 4 x 4 groups (one 16-byte load of T and one of U1t per a feed 16
+// products), X prefetched and out stored as 16-byte accesses on the float32 path.
 // part[blockIdx.x] = the CTA's sum of out^2 (float per thread and slab, float64
 // across slabs and threads).  X may be null (alpha ignored); out may be null (only
-// the sum of squares).  Dynamic smem: U1[n1*r1] | U2^T[r2*n2] | H_s[r1*r2] | T[r1*n2p],
-// n2p = n2 rounded up to a multiple of SO_TC.
+// the sum of squares).  Row and column extents are padded to multiples of 4 (p
+// suffix).  Dynamic smem: U1t[r1*n1p] | U2t[r2*n2p] | HsT[r2*r1p] | T[r1*n2p].
 __global__ void __launch_bounds__(SO_THREADS) k_tucker_slab_out(
     const void* __restrict__ X, int dtype, float alpha, float beta, const float* __restrict__ H, int64_t nslab,
     int n1, int r1, int n2, int r2, const float* __restrict__ U1, const float* __restrict__ U2,
     float* __restrict__ out, double* __restrict__ part) {
   extern __shared__ __align__(16) float sm[];
-  const int n2p = (n2 + SO_TC - 1) / SO_TC * SO_TC;
-  float* U1s = sm;
-  float* U2s = U1s + ((n1 * r1 + 3) & ~3);
-  float* Hs = U2s + ((n2 * r2 + 3) & ~3);
-  float* T = Hs + ((r1 * r2 + 3) & ~3);
+  const int n1p = (n1 + 3) & ~3, n2p = (n2 + 3) & ~3, r1p = (r1 + 3) & ~3;
+  float* U1t = sm;                      // [r1][n1p]
+  float* U2t = U1t + r1 * n1p;          // [r2][n2p]
+  float* HsT = U2t + r2 * n2p;          // [r2][r1p]
+  float* T = HsT + r2 * r1p;            // [r1][n2p]
   __shared__ double red[SO_THREADS / 32];
-  for (int e = threadIdx.x; e < n1 * r1; e += SO_THREADS) U1s[e] = U1[e];
-  // U2 transposed (U2s[b][j]): the T products below read it along j, conflict-free
-  for (int e = threadIdx.x; e < n2 * r2; e += SO_THREADS) U2s[(e % r2) * n2 + e / r2] = U2[e];
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  // float32 fast path: 16-byte X loads and out stores (rows of n2 % 4 == 0 floats,
-  // 16-byte aligned bases; column groups of 4 never straddle n2)
+  for (int e = threadIdx.x; e < r1 * n1p; e += SO_THREADS) {
+    const int a = e / n1p, i = e % n1p;
+    U1t[e] = i < n1 ? U1[i * r1 + a] : 0.f;
+  }
+  for (int e = threadIdx.x; e < r2 * n2p; e += SO_THREADS) {
+    const int b = e / n2p, j = e % n2p;
+    U2t[e] = j < n2 ? U2[j * r2 + b] : 0.f;
+  }
+  // float32 fast path: 16-byte X loads and out stores (n2 % 4 == 0, aligned bases)
   const bool vec = (X == nullptr || dtype == DT_F32) && (n2 % 4) == 0 &&
                    (reinterpret_cast<uintptr_t>(X) & 15) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+  const int nrg = n1p / 4, ncg = n2p / 4;
   double sqd = 0.0;
   for (int64_t s = blockIdx.x; s < nslab; s += gridDim.x) {
     __syncthreads();
-    for (int e = threadIdx.x; e < r1 * r2; e += SO_THREADS) Hs[e] = H[s * r1 * r2 + e];
+    for (int e = threadIdx.x; e < r2 * r1p; e += SO_THREADS) {
+      const int b = e / r1p, a = e % r1p;
+      HsT[e] = a < r1 ? H[(s * r1 + a) * r2 + b] : 0.f;
+    }
     __syncthreads();
-    for (int e = threadIdx.x; e < r1 * n2p; e += SO_THREADS) {
-      const int a = e / n2p, j = e % n2p;
-      float acc = 0.f;
-      if (j < n2)
-        for (int b = 0; b < r2; ++b) acc = fmaf(Hs[a * r2 + b], U2s[b * n2 + j], acc);
-      T[e] = acc;
+    for (int j = threadIdx.x; j < n2p; j += SO_THREADS) {
+      for (int a0 = 0; a0 < r1; a0 += 4) {
+        float t4[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int b = 0; b < r2; ++b) {
+          const float u = U2t[b * n2p + j];
+          const float4 hv = *reinterpret_cast<const float4*>(HsT + b * r1p + a0);
+          t4[0] = fmaf(hv.x, u, t4[0]); t4[1] = fmaf(hv.y, u, t4[1]);
+          t4[2] = fmaf(hv.z, u, t4[2]); t4[3] = fmaf(hv.w, u, t4[3]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (a0 + q < r1) T[(a0 + q) * n2p + j] = t4[q];
+      }
     }
     __syncthreads();
     float sq = 0.f;
     const int64_t base = s * (int64_t)n1 * n2;
-    for (int i0 = 0; i0 < n1; i0 += SO_TR) {
-      for (int j0 = 0; j0 < n2; j0 += SO_TC) {
-        float acc[2][4], xv[2][4];
-        const int ia = i0 + ty, ib = i0 + ty + 16;
-        const int ja = ia < n1 ? ia : 0, jb = ib < n1 ? ib : 0;
-        // X of the thread's 2 x 4 outputs, loaded before the products so that the
-        // DRAM latency overlaps them (16-byte loads on the float32 fast path)
+    for (int g = threadIdx.x; g < nrg * ncg; g += SO_THREADS) {
+      const int rg = g / ncg, cg = g % ncg;
+      const int i0 = 4 * rg, j0 = 4 * cg;
+      float xv[4][4], acc[4][4];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int i = u ? ib : ia;
-          const int j = j0 + 4 * tx;
-          const int64_t e = base + (int64_t)i * n2 + j;
-          if (vec) {
-            float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (X && i < n1 && j < n2) f = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(X) + e));
-            xv[u][0] = f.x; xv[u][1] = f.y; xv[u][2] = f.z; xv[u][3] = f.w;
-          } else {
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u;
+        const int64_t e = base + (int64_t)i * n2 + j0;
+        if (vec) {
+          float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (X && i < n1) f = __ldg(reinterpret_cast<const float4*>(static_cast<const float*>(X) + e));
+          xv[u][0] = f.x; xv[u][1] = f.y; xv[u][2] = f.z; xv[u][3] = f.w;
+        } else {
 #pragma unroll
-            for (int v = 0; v < 4; ++v) xv[u][v] = (X && i < n1 && j + v < n2) ? ldx(X, dtype, e + v) : 0.f;
-          }
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-        }
-        for (int a = 0; a < r1; ++a) {
-          const float4 t = *reinterpret_cast<const float4*>(T + a * n2p + j0 + 4 * tx);
-          const float ua = U1s[ja * r1 + a], ub = U1s[jb * r1 + a];
-          acc[0][0] = fmaf(ua, t.x, acc[0][0]); acc[0][1] = fmaf(ua, t.y, acc[0][1]);
-          acc[0][2] = fmaf(ua, t.z, acc[0][2]); acc[0][3] = fmaf(ua, t.w, acc[0][3]);
-          acc[1][0] = fmaf(ub, t.x, acc[1][0]); acc[1][1] = fmaf(ub, t.y, acc[1][1]);
-          acc[1][2] = fmaf(ub, t.z, acc[1][2]); acc[1][3] = fmaf(ub, t.w, acc[1][3]);
+          for (int v = 0; v < 4; ++v) xv[u][v] = (X && i < n1 && j0 + v < n2) ? ldx(X, dtype, e + v) : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int i = u ? ib : ia;
-          if (i >= n1) continue;
-          float val[4];
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+      }
+      for (int a = 0; a < r1; ++a) {
+        const float4 t = *reinterpret_cast<const float4*>(T + a * n2p + j0);
+        const float4 uu = *reinterpret_cast<const float4*>(U1t + a * n1p + i0);
+        const float ur[4] = {uu.x, uu.y, uu.z, uu.w};
+        const float tc[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
-          for (int v = 0; v < 4; ++v) val[v] = X ? fmaf(alpha, xv[u][v], beta * acc[u][v]) : beta * acc[u][v];
-          const int j = j0 + 4 * tx;
-          const int64_t e = base + (int64_t)i * n2 + j;
-          if (vec && j < n2) {
-            if (out) *reinterpret_cast<float4*>(out + e) = make_float4(val[0], val[1], val[2], val[3]);
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) sq = fmaf(val[v], val[v], sq);
-          } else {
+          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ur[u], tc[v], acc[u][v]);
+      }
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              if (j + v >= n2) continue;
-              if (out) out[e + v] = val[v];
-              sq = fmaf(val[v], val[v], sq);
-            }
+      for (int u = 0; u < 4; ++u) {
+        const int i = i0 + u;
+        if (i >= n1) continue;
+        float val[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) val[v] = X ? fmaf(alpha, xv[u][v], beta * acc[u][v]) : beta * acc[u][v];
+        const int64_t e = base + (int64_t)i * n2 + j0;
+        if (vec) {
+          if (out) *reinterpret_cast<float4*>(out + e) = make_float4(val[0], val[1], val[2], val[3]);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) sq = fmaf(val[v], val[v], sq);
+        } else {
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            if (j0 + v >= n2) continue;
+            if (out) out[e + v] = val[v];
+            sq = fmaf(val[v], val[v], sq);
           }
         }
       }
@@ -164,43 +175,54 @@ __global__ void k_sum_parts(const double* __restrict__ part, int nblk, double sc
 }
 
 // out[i][a] = scale * sum_{p, q} Y(p, i, q) C(p, a, q) for Y of (P, n, Q) and C of
-// (P, r, Q): the mode-n unfoldings' product [Y]_(n) [C]_(n)^T.  CTA (i, ks) takes
-// the ks-th chunk of the P Q terms (q fastest, so Y and C are read along q); its
-// threads keep r <= 64 partial sums, reduced across the CTA into part[i][ks][a];
-// k_unfold_reduce then adds the chunks in order (deterministic).
-constexpr int UC_THREADS = 256;
+// (P, r, Q): the mode-n unfoldings' product [Y]_(n) [C]_(n)^T.  CTA (ib, ks) takes
+// rows ib*UC_ROWS .. + UC_ROWS and the ks-th chunk of UC_K terms k = p Q + q: the
+// chunk of C (UC_K x r) is staged in shared memory once and serves all its rows;
+// thread (row, k-lane) keeps r <= 64 partial sums over its terms, reduced across
+// the k-lanes of the row into part[i][ks][a]; k_unfold_reduce adds the chunks in
+// order (deterministic).
+constexpr int UC_THREADS = 256, UC_K = 128, UC_ROWS = 8, UC_LANES = UC_THREADS / UC_ROWS;
 __global__ void __launch_bounds__(UC_THREADS) k_unfold_contract(const float* __restrict__ Y,
                                                                 const float* __restrict__ C, int64_t P,
-                                                                int64_t n, int r, int64_t Q, int64_t kchunk,
+                                                                int64_t n, int r, int64_t Q,
                                                                 float* __restrict__ part) {
-  __shared__ float red[UC_THREADS / 32][CMAX];
-  const int64_t i = blockIdx.x;
-  const int ks = blockIdx.y, KS = gridDim.y;
+  __shared__ __align__(16) float cs[CMAX * UC_K];    // [a][kk]
+  const int KS = gridDim.y;
+  const int64_t K = P * Q, nchunk = (K + UC_K - 1) / UC_K;
+  const int row = threadIdx.x / UC_LANES, kl = threadIdx.x % UC_LANES;
+  const int64_t i = (int64_t)blockIdx.x * UC_ROWS + row;
   float acc[CMAX];
 #pragma unroll
   for (int a = 0; a < CMAX; ++a) acc[a] = 0.f;
-  const int64_t K = P * Q;
-  const int64_t k1 = min(K, (int64_t)(ks + 1) * kchunk);
-  for (int64_t k = (int64_t)ks * kchunk + threadIdx.x; k < k1; k += UC_THREADS) {
-    const int64_t p = k / Q, q = k % Q;
-    const float y = __ldg(Y + (p * n + i) * Q + q);
-    const float* c = C + p * r * Q + q;
+  for (int64_t ch = blockIdx.y; ch < nchunk; ch += KS) {   // chunks ks, ks + KS, ...
+    const int64_t k0 = ch * UC_K;
+    const int kn = (int)min((int64_t)UC_K, K - k0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kn * r; e += UC_THREADS) {
+      // C(p, a, q) for k = k0 + kk: consecutive threads take consecutive q (then a)
+      const int kk = e % kn, a = e / kn;
+      const int64_t k = k0 + kk, p = k / Q, q = k % Q;
+      cs[a * UC_K + kk] = C[(p * r + a) * Q + q];
+    }
+    __syncthreads();
+    if (i < n) {
+      for (int kk = kl; kk < kn; kk += UC_LANES) {
+        const int64_t k = k0 + kk, p = k / Q, q = k % Q;
+        const float y = __ldg(Y + (p * n + i) * Q + q);
+        const float* c = cs + kk;
 #pragma unroll
-    for (int a = 0; a < CMAX; ++a)
-      if (a < r) acc[a] = fmaf(y, __ldg(c + (int64_t)a * Q), acc[a]);
+        for (int a = 0; a < CMAX; ++a)
+          if (a < r) acc[a] = fmaf(y, c[a * UC_K], acc[a]);
+      }
+    }
   }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ks = blockIdx.y;
+  // the UC_LANES (= 32) k-lanes of a row are one warp
 #pragma unroll
   for (int a = 0; a < CMAX; ++a) {
     if (a >= r) break;
     const float v = warp_sum(acc[a]);
-    if (lane == 0) red[w][a] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < r) {
-    float t = 0.f;
-    for (int q = 0; q < UC_THREADS / 32; ++q) t += red[q][threadIdx.x];
-    part[(i * KS + ks) * r + threadIdx.x] = t;
+    if (kl == 0 && i < n) part[(i * KS + ks) * r + a] = v;
   }
 }
 
@@ -240,10 +262,9 @@ int launch_expand_f32(const float* A, int64_t L, int r, int64_t R, const float* 
 int launch_tucker_slab_out(const void* X, int dtype, float alpha, float beta, const float* H, int64_t nslab,
                            int64_t n1, int r1, int64_t n2, int r2, const float* U1, const float* U2, float* out,
                            double* part, double* sumsq_scaled, double scale, cudaStream_t st) {
-  if (n1 > 4096 || n2 > 4096) return 0;
-  const int64_t n2p = (n2 + SO_TC - 1) / SO_TC * SO_TC;
-  auto up4 = [](int64_t x) { return (x + 3) & ~(int64_t)3; };
-  const size_t smem = (size_t)(up4(n1 * r1) + up4(n2 * r2) + up4((int64_t)r1 * r2) + (int64_t)r1 * n2p) * 4;
+  if (n1 > 65536 || n2 > 65536) return 0;
+  const int64_t n1p = (n1 + 3) & ~(int64_t)3, n2p = (n2 + 3) & ~(int64_t)3, r1p = (r1 + 3) & ~3;
+  const size_t smem = (size_t)(r1 * n1p + r2 * n2p + r2 * r1p + r1 * n2p) * 4;
   if (smem > 200 * 1024) return 0;
   cudaFuncSetAttribute(k_tucker_slab_out, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int nb = (int)(nslab < GR_SLAB_BLOCKS ? nslab : GR_SLAB_BLOCKS);
@@ -257,19 +278,21 @@ int launch_tucker_slab_out(const void* X, int dtype, float alpha, float beta, co
   return nl;
 }
 
-constexpr int UC_MAX_SPLIT = 64;
+constexpr int UC_MAX_SPLIT = 4096;   // CTAs per row group along K
 
-size_t unfold_scratch_floats(int64_t n, int r) { return (size_t)n * UC_MAX_SPLIT * r; }
+size_t unfold_scratch_floats(int64_t n, int r, int64_t K) {
+  const int64_t ks = (K + UC_K - 1) / UC_K;
+  return (size_t)n * (ks < UC_MAX_SPLIT ? ks : UC_MAX_SPLIT) * r;
+}
 
 int launch_unfold_contract(const float* Y, const float* C, int64_t P, int64_t n, int r, int64_t Q, float scale,
                            float* out, float* scratch, cudaStream_t st) {
   if (r > CMAX || n < 1 || n > (int64_t)0x7fffffff) return 0;
   const int64_t K = P * Q;
-  int64_t KS = (K + 2047) / 2048;                  // about 8 terms per thread per chunk
-  if (KS < 1) KS = 1;
-  if (KS > UC_MAX_SPLIT) KS = UC_MAX_SPLIT;
-  const int64_t kchunk = (K + KS - 1) / KS;
-  k_unfold_contract<<<dim3((unsigned)n, (unsigned)KS), UC_THREADS, 0, st>>>(Y, C, P, n, r, Q, kchunk, scratch);
+  int64_t KS = (K + UC_K - 1) / UC_K;
+  if (KS > UC_MAX_SPLIT) KS = UC_MAX_SPLIT;     // a CTA then takes every KS-th chunk
+  k_unfold_contract<<<dim3((unsigned)((n + UC_ROWS - 1) / UC_ROWS), (unsigned)KS), UC_THREADS, 0, st>>>(
+      Y, C, P, n, r, Q, scratch);
   k_unfold_reduce<<<grid_for(n * r, 256), 256, 0, st>>>(scratch, n, r, (int)KS, scale, out);
   return 2;
 }

@@ -78,8 +78,8 @@ int launch_tucker_slab_out(const void* X, int dtype, float alpha, float beta, co
                            int64_t n1, int r1, int64_t n2, int r2, const float* U1, const float* U2, float* out,
                            double* part, double* sumsq_scaled, double scale, cudaStream_t st);
 // out[i][a] = scale * sum_{p,q} Y(p, i, q) C(p, a, q) (Y of P x n x Q, C of P x r x Q);
-// scratch: unfold_scratch_floats(n, r) floats.
-size_t unfold_scratch_floats(int64_t n, int r);
+// scratch: unfold_scratch_floats(n, r, P * Q) floats.
+size_t unfold_scratch_floats(int64_t n, int r, int64_t K);
 int launch_unfold_contract(const float* Y, const float* C, int64_t P, int64_t n, int r, int64_t Q, float scale,
                            float* out, float* scratch, cudaStream_t st);
 int launch_scale_f32(float* x, int64_t n, float s, cudaStream_t st);
