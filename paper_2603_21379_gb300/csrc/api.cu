@@ -79,6 +79,11 @@ struct rt_handle_s {
   char* d_stage = nullptr;     // the same buffer as the device addresses it
   size_t h_stage_bytes = 0;
   std::vector<StageSeg> stage_segs;  // uploads not yet enqueued
+  // the last table upload: skipped when the next one is identical and nothing else
+  // used the workspace in between (ws_epoch counts workspace users)
+  uint64_t ws_epoch = 0, commit_epoch = ~0ull;
+  std::vector<StageSeg> last_segs;
+  std::vector<uint64_t> last_words;
   cudaEvent_t ev_stage = nullptr;
   bool stage_pending = false;
   std::string err;
@@ -332,6 +337,7 @@ void bind_problem(ProbPlan& pp, char* ws) {
 
 // Grows the workspace to at least `bytes` (synchronising the stream first).
 rt_status ensure_ws(rt_handle h, size_t bytes) {
+  ++h->ws_epoch;
   if (bytes <= h->ws_bytes) return RT_OK;
   RT_CUDA(h, cudaStreamSynchronize(h->stream));
   if (h->ws) cudaFree(h->ws);
@@ -383,6 +389,22 @@ rt_status stage_put(rt_handle h, void* dst, const void* src, size_t bytes) {
 rt_status stage_commit(rt_handle h, int* nl) {
   std::vector<StageSeg> segs;
   segs.swap(h->stage_segs);
+  // identical tables into an untouched workspace: the device copy is still current
+  std::vector<uint64_t> words;
+  for (const StageSeg& g : segs) {
+    const uint64_t* src = reinterpret_cast<const uint64_t*>(h->h_stage + g.src);
+    words.insert(words.end(), src, src + g.words);
+  }
+  bool same = h->commit_epoch == h->ws_epoch - 1 && segs.size() == h->last_segs.size() && words == h->last_words;
+  for (size_t i = 0; same && i < segs.size(); ++i)
+    same = segs[i].dst == h->last_segs[i].dst && segs[i].words == h->last_segs[i].words;
+  h->commit_epoch = h->ws_epoch;
+  if (same) {
+    h->stage_pending = false;   // nothing reads the staging buffer
+    return RT_OK;
+  }
+  h->last_segs = segs;
+  h->last_words.swap(words);
   for (size_t i0 = 0; i0 < segs.size(); i0 += UP_MAX) {
     UploadBatch b{};
     b.nseg = (int)std::min<size_t>(UP_MAX, segs.size() - i0);

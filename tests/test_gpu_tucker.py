@@ -373,3 +373,26 @@ def test_order4_128_full_size(rt):
     del Xbo
     ebr = tucker.relerr(np.asarray(X, dtype=np.float64), tucker.reconstruct(refb["G"], refb["U"]))
     assert abs(eb - ebr) <= RELERR_TOL, (eb, ebr)
+
+
+def test_repeated_calls_reuse_tables_safely(rt):
+    # identical calls may skip re-uploading the problem tables; any other use of the
+    # workspace in between (another decomposition, a core or gradient call) must not
+    # leave stale tables behind
+    X = synth.tucker_tensor((48, 40, 56), (5, 4, 6), 1e-4, 21)
+    Xd = torch.from_numpy(X).cuda()
+    r = [5, 4, 6]
+    G0, U0 = rt.rtucker_decompose(Xd, r, 3, seed=7)
+    G1, U1 = rt.rtucker_decompose(Xd, r, 3, seed=7)           # same tables
+    Gs, _ = rt.rtucker_decompose(Xd, r, 3, seed=8)            # other seed: other tables
+    G2, U2 = rt.rtucker_decompose(Xd, r, 3, seed=7)
+    Y = torch.from_numpy(synth.tucker_tensor((30, 33, 31), (3, 3, 3), 1e-4, 22)).cuda()
+    rt.rtucker_core(Y, [u[:m, :3].contiguous() for u, m in zip(U0, (30, 33, 31))])
+    rt.rtucker_loss_grad(Xd, G0, U0)
+    G3, U3 = rt.rtucker_decompose(Xd, r, 3, seed=7)
+    rt.sync()
+    for G, U in ((G1, U1), (G2, U2), (G3, U3)):
+        assert torch.equal(G, G0)
+        for a, b in zip(U, U0):
+            assert torch.equal(a, b)
+    assert not torch.equal(Gs, G0)
