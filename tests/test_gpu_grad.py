@@ -168,3 +168,26 @@ def test_order4_96_at_the_decomposition(rt):
         _check(dU[n].cpu().numpy(), dUr[n], sU[n], "dU%d" % n)
     # the core from the projection is (to float32 rounding) the best core for these U
     assert np.abs(dGr).max() <= 1e-4 * np.abs(Gn).max()
+
+
+def test_loss_grad_bf16_and_f64_input(rt):
+    # X stored as bfloat16 / float64 (read through the scalar path of the residual
+    # kernel); the oracle gets the values the kernels read
+    rs = np.random.default_rng(13)
+    shape, ranks = (18, 21, 15), (4, 3, 5)
+    X64 = rs.standard_normal(shape)
+    G = rs.standard_normal(ranks).astype(np.float32)
+    U = [(rs.standard_normal((n, r)) / np.sqrt(n)).astype(np.float32) for n, r in zip(shape, ranks)]
+    Gd = torch.from_numpy(G).cuda()
+    Ud = [torch.from_numpy(u).cuda() for u in U]
+    for Xd in (torch.from_numpy(X64).cuda(), torch.from_numpy(X64).to(torch.bfloat16).cuda()):
+        loss, dX, dG, dU = rt.rtucker_loss_grad(Xd, Gd, Ud)
+        rt.sync()
+        Xo = Xd.double().cpu().numpy()
+        Lr, dXr, dGr, dUr = tg.misfit_grads(Xo, G, U)
+        A, sG, sU = _scales(Xo, G, U)
+        _check(dX.cpu().numpy(), dXr, A, "dX")
+        _check(dG.cpu().numpy(), dGr, sG, "dG")
+        for n in range(3):
+            _check(dU[n].cpu().numpy(), dUr[n], sU[n], "dU%d" % n)
+        assert abs(loss.item() - Lr) <= 1e-6 * Lr + REL * float(np.sum(A * np.abs(dXr)))
