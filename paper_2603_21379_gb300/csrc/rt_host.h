@@ -16,7 +16,7 @@ constexpr int CMAX = 64;           // largest r + p supported
 constexpr int QR_MAXF = 12288;     // floats per smem array in the block QR
 constexpr int QR2_MAXF = 24576;    // floats per smem array in the TSQR second level
 constexpr int BT_SC = 256;         // samples per chunk of B^T = Y^T Q
-constexpr int BT_IB = 2048;        // rows per reduction block of B^T
+constexpr int BT_IB = 512;         // rows per reduction block of B^T (more, shorter CTAs for tall nodes)
 constexpr int WS_MAXF = 24576;     // floats of the stacked R factors in the W-step
 constexpr int WS_LDT = 80;         // column stride of R^T in the Jacobi SVD (CMAX + 16)
 constexpr int WS_MAX_SWEEPS = 40;  // one-sided Jacobi sweeps before ST_NUMERIC
