@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_ttm_grouped(const TTMJob* __restrict__ 
 // the 16-byte shared loads of consecutive lanes are consecutive (no bank conflicts).  A and U tiles of TK rows of i are staged in
 // shared memory by 16-byte / 4-byte cp.async in a TS-deep ring, so the loads of tile
 // t + TS - 1 overlap the FMAs of tile t.
-constexpr int TF_TK = 32, TF_TS = 3;
+constexpr int TF_TS = 3;
 
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -135,17 +135,17 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// AW: width of the block's slice of a (32, or 16 for r <= 16, which halves the products
-// and, with a K stage of AW rows, the shared memory).
-template <int TN, int AW>
-constexpr size_t ttm_f32_smem() { return (size_t)TF_TS * AW * (TN + AW) * sizeof(float); }
+// AW: width of the block's slice of a (32, or 16 for r <= 16, which halves the
+// products); TK: rows of A and U per pipeline stage (16 with the narrow slice, which
+// halves the shared memory; for AW = 32, TK = 16 measured slower than 32).
+template <int TN, int AW, int TK>
+constexpr size_t ttm_f32_smem() { return (size_t)TF_TS * TK * (TN + AW) * sizeof(float); }
 
-template <int TN, int AW>
+template <int TN, int AW, int TK>
 __global__ void __launch_bounds__(AW * TN / 64) k_ttm_f32(const float* __restrict__ A, int64_t n, int64_t R,
                                                     int64_t tiles_per_l, const float* __restrict__ U, int r,
                                                     float* __restrict__ out) {
   constexpr int NT = AW * TN / 64;         // threads: AW/8 a-groups x TN/8 rho-groups
-  constexpr int TK = AW;                   // rows of A and U per stage
   extern __shared__ __align__(16) float tsm[];
   float* As = tsm;                          // [TS][TK][TN]
   float* Us = tsm + TF_TS * TK * TN;        // [TS][TK][AW]
@@ -303,19 +303,19 @@ int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, cons
     const float* Af = static_cast<const float*>(A);
     if (r <= 16) {
       if (R >= 256 && L * t256 >= 2 * (int64_t)g_num_sms)
-        k_ttm_f32<256, 16><<<dim3((unsigned)(L * t256), 1), 64, ttm_f32_smem<256, 16>(), st>>>(Af, n, R, t256, U, r,
+        k_ttm_f32<256, 16, 16><<<dim3((unsigned)(L * t256), 1), 64, ttm_f32_smem<256, 16, 16>(), st>>>(Af, n, R, t256, U, r,
                                                                                                out);
       else
-        k_ttm_f32<128, 16><<<dim3((unsigned)(L * t128), 1), 32, ttm_f32_smem<128, 16>(), st>>>(Af, n, R, t128, U, r,
+        k_ttm_f32<128, 16, 16><<<dim3((unsigned)(L * t128), 1), 32, ttm_f32_smem<128, 16, 16>(), st>>>(Af, n, R, t128, U, r,
                                                                                                out);
       return 1;
     }
     const unsigned gy = (unsigned)((r + 31) / 32);
     if (R >= 256 && L * t256 * gy >= 2 * (int64_t)g_num_sms)
-      k_ttm_f32<256, 32><<<dim3((unsigned)(L * t256), gy), 128, ttm_f32_smem<256, 32>(), st>>>(Af, n, R, t256, U, r,
+      k_ttm_f32<256, 32, 32><<<dim3((unsigned)(L * t256), gy), 128, ttm_f32_smem<256, 32, 32>(), st>>>(Af, n, R, t256, U, r,
                                                                                                out);
     else
-      k_ttm_f32<128, 32><<<dim3((unsigned)(L * t128), gy), 64, ttm_f32_smem<128, 32>(), st>>>(Af, n, R, t128, U, r,
+      k_ttm_f32<128, 32, 32><<<dim3((unsigned)(L * t128), gy), 64, ttm_f32_smem<128, 32, 32>(), st>>>(Af, n, R, t128, U, r,
                                                                                               out);
     return 1;
   }
@@ -348,11 +348,11 @@ cudaError_t core_init_attributes() {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-#define RT_TTM_ATTR(TN, AW)                                                                              \
+#define RT_TTM_ATTR(TN, AW, TK)                                                                          \
   if (e == cudaSuccess)                                                                                    \
-    e = cudaFuncSetAttribute(k_ttm_f32<TN, AW>, cudaFuncAttributeMaxDynamicSharedMemorySize,                \
-                             (int)ttm_f32_smem<TN, AW>());
-  RT_TTM_ATTR(256, 32) RT_TTM_ATTR(128, 32) RT_TTM_ATTR(256, 16) RT_TTM_ATTR(128, 16)
+    e = cudaFuncSetAttribute(k_ttm_f32<TN, AW, TK>, cudaFuncAttributeMaxDynamicSharedMemorySize,            \
+                             (int)ttm_f32_smem<TN, AW, TK>());
+  RT_TTM_ATTR(256, 32, 32) RT_TTM_ATTR(128, 32, 32) RT_TTM_ATTR(256, 16, 16) RT_TTM_ATTR(128, 16, 16)
 #undef RT_TTM_ATTR
   return e;
 }
