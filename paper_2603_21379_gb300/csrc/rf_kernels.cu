@@ -557,7 +557,7 @@ __device__ void hh_form_q_g8(const float* A, float* Qm, int ld, int m, int c, co
 }
 
 // Dispatch on the row count (m <= 512: registers; larger: shared memory).
-template <int JPW, bool CT = true>
+template <int JPW, bool CT = true, bool TALL = false>
 __device__ void qr_factor(float* A, int ld, int m, int c, float* tau, float* rdiag, float* vbuf) {
   if (CT) {
     if (m <= 32) hh_factor_reg_ct<1, JPW>(A, ld, m, c, tau, rdiag, vbuf);
@@ -565,6 +565,9 @@ __device__ void qr_factor(float* A, int ld, int m, int c, float* tau, float* rdi
     else if (m <= 128) hh_factor_reg_ct<4, JPW>(A, ld, m, c, tau, rdiag, vbuf);
     else if (m <= 256) hh_factor_reg_ct<8, JPW>(A, ld, m, c, tau, rdiag, vbuf);
     else if (m <= 512) hh_factor_reg_ct<16, JPW>(A, ld, m, c, tau, rdiag, vbuf);
+    // tall stacks with at most one column per warp (small r + p): 48 rows per lane;
+    // vbuf must then hold 2 x 32 x 48 floats
+    else if (TALL && m <= 1536 && c <= (int)(blockDim.x >> 5)) hh_factor_reg_ct<48, 1>(A, ld, m, c, tau, rdiag, vbuf);
     else hh_factor(A, ld, m, c, tau, rdiag, nullptr);
     return;
   }
@@ -575,7 +578,7 @@ __device__ void qr_factor(float* A, int ld, int m, int c, float* tau, float* rdi
   else if (m <= 512) hh_factor_reg<16, JPW>(A, ld, m, c, tau, rdiag, vbuf);
   else hh_factor(A, ld, m, c, tau, rdiag, nullptr);
 }
-template <int JPW>
+template <int JPW, bool TALL = false>
 __device__ void qr_form_q(const float* A, float* Qm, int ld, int m, int c, const float* tau, const float* rdiag,
                           bool fix_sign) {
   if ((int)blockDim.x >= 8 * c && m <= 128) {
@@ -587,6 +590,7 @@ __device__ void qr_form_q(const float* A, float* Qm, int ld, int m, int c, const
   else if (m <= 128) hh_form_q_reg<4, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
   else if (m <= 256) hh_form_q_reg<8, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
   else if (m <= 512) hh_form_q_reg<16, JPW>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
+  else if (TALL && m <= 1536 && c <= (int)(blockDim.x >> 5)) hh_form_q_reg<48, 1>(A, Qm, ld, m, c, tau, rdiag, fix_sign);
   else hh_form_q(A, Qm, ld, m, c, tau, rdiag, fix_sign);
 }
 
@@ -655,8 +659,8 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr2(const RFProb* __restrict__ P
     A[(size_t)j * ld + i] = q.Rb[e];
   }
   __syncthreads();
-  qr_factor<QR_JPW>(A, ld, m, c, tau, rdiag, red + 32);
-  qr_form_q<QR_JPW>(A, Qm, ld, m, c, tau, rdiag, true);
+  qr_factor<QR_JPW, true, true>(A, ld, m, c, tau, rdiag, red + 32);
+  qr_form_q<QR_JPW, true>(A, Qm, ld, m, c, tau, rdiag, true);
   for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
     const int i = e / c, j = e % c;
     q.Q2[e] = Qm[(size_t)j * ld + i];
@@ -1247,7 +1251,7 @@ constexpr int64_t SO_WARP_MAX = 32768;
 
 static size_t smem_gs() { return (size_t)(SK_TJ * SK_TI + SK_TJ * CMAX) * 4 + SK_TJ * 8; }
 static size_t smem_qr() { return (size_t)(2 * QR_MAXF + 2 * CMAX + 1024) * 4 + 64; }
-static size_t smem_qr2() { return (size_t)(2 * QR2_MAXF + 2 * CMAX + 32 + 1024) * 4 + 64; }
+static size_t smem_qr2() { return (size_t)(2 * QR2_MAXF + 2 * CMAX + 32 + 3072) * 4 + 64; }
 static size_t smem_qr3() { return (size_t)(QR_MAXF + CMAX * CMAX) * 4; }
 static size_t smem_btp() { return (size_t)(32 * BT_LDY + 32 * CMAX) * 4; }
 static size_t smem_btf() {
