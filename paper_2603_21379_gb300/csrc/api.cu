@@ -1429,6 +1429,8 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
   // job tables (workspace addresses are final once it is sized), staged after the
   // range-finder tables and uploaded with them
   std::vector<int64_t> ltiles(dmax, 0);
+  std::vector<char> last_rows(dmax, 0);
+  std::vector<int> lnmax(dmax, 0), lrmax(dmax, 0);
   {
     size_t so = gsb;
     for (int k = 0; k < dmax; ++k) {
@@ -1438,6 +1440,17 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
       so += align_up(sizeof(int64_t) * (njob[k] + 1));
       int q_i = 0;
       int64_t acc = 0;
+      // a level whose jobs all contract a last mode of <= 256 rows into <= 32 columns
+      // takes the one-thread-per-row form (CTAs counted per job by rows)
+      bool rows = true;
+      for (int t = 0; t < T && rows; ++t)
+        if (d[t] > k) {
+          const int m = d[t] - 1 - k;
+          int64_t R = 1;
+          for (int j = m + 1; j < d[t]; ++j) R *= r[t][j];
+          rows = R == 1 && n[t][m] <= 256 && r[t][m] <= 32;
+        }
+      last_rows[k] = rows;
       for (int t = 0; t < T; ++t) {
         if (d[t] <= k) continue;
         const int m = d[t] - 1 - k;
@@ -1456,7 +1469,14 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
         for (int j = 0; j < m; ++j) uo += n[t][j] * r[t][j];
         q.U = U[t] + uo;
         ps[q_i] = acc;
-        acc += ttm_job_tiles(q);
+        const int64_t tiles = ttm_job_tiles(q);   // also sets tiles_x
+        if (rows) {
+          acc += ttm_last_job_ctas(q);
+          lnmax[k] = std::max<int>(lnmax[k], (int)q.n);
+          lrmax[k] = std::max<int>(lrmax[k], q.r);
+        } else {
+          acc += tiles;
+        }
         js[q_i++] = q;
       }
       ps[q_i] = acc;
@@ -1473,9 +1493,14 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
   }
   for (int k = 0; k < dmax; ++k) {
     StageTimer tm(h, k == 0 ? 1 : 2);
-    nl += launch_ttm_grouped(reinterpret_cast<const TTMJob*>(h->ws + o_jobs[k]),
-                             reinterpret_cast<const int64_t*>(h->ws + o_lpre[k]), njob[k], ltiles[k],
-                             k == 0 ? (int)dtype : DT_F32, h->stream);
+    if (last_rows[k])
+      nl += launch_ttm_last_grouped(reinterpret_cast<const TTMJob*>(h->ws + o_jobs[k]),
+                                    reinterpret_cast<const int64_t*>(h->ws + o_lpre[k]), njob[k], ltiles[k],
+                                    k == 0 ? (int)dtype : DT_F32, lnmax[k], lrmax[k], h->stream);
+    else
+      nl += launch_ttm_grouped(reinterpret_cast<const TTMJob*>(h->ws + o_jobs[k]),
+                               reinterpret_cast<const int64_t*>(h->ws + o_lpre[k]), njob[k], ltiles[k],
+                               k == 0 ? (int)dtype : DT_F32, h->stream);
   }
   return finish(h, nl);
 }

@@ -281,6 +281,58 @@ __global__ void __launch_bounds__(TL_THREADS) k_ttm_last(const float* __restrict
     if (a < r) o[a] = acc[a];
 }
 
+// Grouped last-mode contractions (R = 1) of a batch: job q contracts the last mode of
+// its L x n tensor with U_q (n x r <= RW), one thread per row.  pre[j] counts CTAs of
+// TL_THREADS rows before job j.  A's element type T (the batch's X type at the first
+// level); 16-byte loads for float rows with n % 4 == 0.
+template <typename T, int RW>
+__global__ void __launch_bounds__(TL_THREADS) k_ttm_last_grouped(const TTMJob* __restrict__ jobs,
+                                                                 const int64_t* __restrict__ pre, int njobs) {
+  extern __shared__ __align__(16) float us[];   // [n][RW], zero beyond r
+  const int j = find_prob(pre, njobs, blockIdx.x);
+  const TTMJob& q = jobs[j];
+  const int n = (int)q.n, r = q.r;
+  for (int e = threadIdx.x; e < n * RW; e += TL_THREADS) {
+    const int i = e / RW, a = e % RW;
+    us[e] = a < r ? q.U[i * r + a] : 0.f;
+  }
+  __syncthreads();
+  const int64_t l = ((int64_t)blockIdx.x - pre[j]) * TL_THREADS + threadIdx.x;
+  if (l >= q.L) return;
+  const T* row = static_cast<const T*>(q.A) + l * n;
+  float acc[RW];
+#pragma unroll
+  for (int a = 0; a < RW; ++a) acc[a] = 0.f;
+  const bool v4 = sizeof(T) == 4 && (n % 4) == 0 && (reinterpret_cast<uintptr_t>(q.A) & 15) == 0;
+  for (int i0 = 0; i0 < n; i0 += 4) {
+    float x[4];
+    if (v4) {
+      const float4 f = __ldg(reinterpret_cast<const float4*>(row + i0));
+      x[0] = f.x; x[1] = f.y; x[2] = f.z; x[3] = f.w;
+    } else {
+#pragma unroll
+      for (int t = 0; t < 4; ++t) x[t] = i0 + t < n ? ldf<T>(row, i0 + t) : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (i0 + t >= n) break;
+      const float* ui = us + (i0 + t) * RW;
+#pragma unroll
+      for (int a = 0; a < RW; a += 4) {
+        const float4 u = *reinterpret_cast<const float4*>(ui + a);
+        acc[a] = fmaf(x[t], u.x, acc[a]);
+        acc[a + 1] = fmaf(x[t], u.y, acc[a + 1]);
+        acc[a + 2] = fmaf(x[t], u.z, acc[a + 2]);
+        acc[a + 3] = fmaf(x[t], u.w, acc[a + 3]);
+      }
+    }
+  }
+  float* o = q.out + l * r;
+#pragma unroll
+  for (int a = 0; a < RW; ++a)
+    if (a < r) o[a] = acc[a];
+}
+
 static int g_num_sms = 0;
 
 int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, const float* U, int r,
@@ -326,6 +378,26 @@ int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, cons
     k_ttm_t<double><<<grid, 256, 0, st>>>(static_cast<const double*>(A), L, n, R, U, r, out);
   else
     k_ttm_t<__nv_bfloat16><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(A), L, n, R, U, r, out);
+  return 1;
+}
+
+int64_t ttm_last_job_ctas(const TTMJob& q) { return (q.L + TL_THREADS - 1) / TL_THREADS; }
+
+int launch_ttm_last_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs, int64_t total_ctas,
+                            int dtype, int nmax, int rmax, cudaStream_t st) {
+  if (njobs < 1 || total_ctas < 1 || nmax > 256 || rmax > 32) return 0;
+  const int rw = rmax <= 8 ? 8 : rmax <= 16 ? 16 : rmax <= 24 ? 24 : 32;
+  const size_t smem = (size_t)nmax * rw * 4;
+  const unsigned grid = (unsigned)total_ctas;
+#define RT_TLG(T, RWV)                                                                       \
+  k_ttm_last_grouped<T, RWV><<<grid, TL_THREADS, smem, st>>>(jobs_dev, pre_dev, njobs)
+#define RT_TLG_RW(T)                                                                          \
+  if (rw == 8) RT_TLG(T, 8); else if (rw == 16) RT_TLG(T, 16); else if (rw == 24) RT_TLG(T, 24); else RT_TLG(T, 32)
+  if (dtype == DT_F32) { RT_TLG_RW(float); }
+  else if (dtype == DT_F64) { RT_TLG_RW(double); }
+  else { RT_TLG_RW(__nv_bfloat16); }
+#undef RT_TLG_RW
+#undef RT_TLG
   return 1;
 }
 

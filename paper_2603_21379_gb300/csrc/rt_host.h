@@ -65,6 +65,11 @@ struct TTMJob {
 int64_t ttm_job_tiles(TTMJob& q);  // sets tiles_x, returns the job's CTA count
 int launch_ttm_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs, int64_t total_tiles, int dtype,
                        cudaStream_t st);
+// Grouped last-mode contractions (every job R = 1, n <= 256, r <= 32): pre counts
+// ttm_last_job_ctas per job; returns 0 when a job does not fit.
+int64_t ttm_last_job_ctas(const TTMJob& q);
+int launch_ttm_last_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs, int64_t total_ctas,
+                            int dtype, int nmax, int rmax, cudaStream_t st);
 cudaError_t core_init_attributes();
 // ---- differentiable Tucker (grad_kernels.cu)
 // out(l, i, rho) = sum_a U[i][a] A(l, a, rho) (one core mode expanded, float32).
