@@ -1257,7 +1257,10 @@ static size_t smem_btp() { return (size_t)(32 * BT_LDY + 32 * CMAX) * 4; }
 static size_t smem_btf() {
   return (size_t)(32 * BT_LDY + 32 * CMAX + (BT_SC + 1) * CMAX + 2 * CMAX + 1024) * 4 + 64;
 }
-static size_t smem_btq() { return (size_t)(QR_MAXF + 2 * CMAX + 32 + 1024) * 4 + 64; }
+// k_bt_qr factors one whole chunk: up to (BT_SC | 1) x CMAX floats, then the register
+// Householder's two 32 x MR vectors (MR = 16 rows per lane covers chunks up to 512).
+static_assert(BT_SC <= 512, "B^T chunk must stay within the register Householder");
+static size_t smem_btq() { return (size_t)((BT_SC | 1) * CMAX + 2 * CMAX + 32 + 1024) * 4 + 64; }
 static size_t smem_wsvd() {
   return (size_t)(WS_MAXF + 2 * CMAX + 32 + CMAX * WS_LDT + CMAX + 8 + 1024) * 4 + 64;
 }

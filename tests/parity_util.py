@@ -40,12 +40,12 @@ def clusters(sigma, r, gap_min=GAP_MIN):
     return out, tail_ok
 
 
-def compare_factor(Ug, Ur, sigma_ref, tol=U_TOL):
+def compare_factor(Ug, Ur, sigma_ref, tol=U_TOL, gap_min=GAP_MIN):
     """Returns (signs, max-abs deviation over determined columns, #strict columns)."""
     Ug = np.asarray(Ug, dtype=np.float64)
     r = Ur.shape[1]
     Ua, s = align_signs(Ug, Ur)
-    cl, tail_ok = clusters(sigma_ref, r)
+    cl, tail_ok = clusters(sigma_ref, r, gap_min)
     worst, strict = 0.0, 0
     for ci, c in enumerate(cl):
         if ci == len(cl) - 1 and not tail_ok:

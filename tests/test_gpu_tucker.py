@@ -106,6 +106,33 @@ def test_matrix_d2(rt):
     _run_and_compare(rt, X, (10, 10), 5, seed=4)
 
 
+def test_widest_sketch_on_tall_unfoldings(rt):
+    # r + p = 64, the largest supported width, on a mode whose unfolding (48 x 48 = 2304
+    # rows) spans several row blocks of B^T = Y^T Q, so every chunk of 256 samples is
+    # factored from the reduced row-block partials.  The 54 sampled singular values sit
+    # ~1e-3 of sigma_1 apart, so columns closer than 5e-3 are compared as subspaces and
+    # the core is checked as the projection of X on the returned factors.
+    X = synth.tucker_tensor((70, 48, 48), (54, 8, 8), noise=1e-4, data_seed=10)
+    r, p, seed = [54, 8, 8], 10, 12
+    Xd = torch.from_numpy(X).cuda()
+    G, U = rt.rtucker_decompose(Xd, r, p, seed=seed)
+    _, sig = rt.rtucker_factors(Xd, r, p, seed=seed, with_sigma=True)
+    rt.sync()
+    Xo = X.astype(np.float64)
+    ref = tucker.sub_r_hosvd(Xo, r, p, seed=seed, with_core=False)
+    Un = [to_np(u) for u in U]
+    for k in range(3):
+        s_ref = ref["modes"][k]["sigma"]
+        _, dev, _ = compare_factor(Un[k], ref["U"][k], s_ref, gap_min=5e-3)
+        assert dev <= U_TOL, ("mode", k, dev)
+        assert orthonormality(Un[k]) < 1e-5
+        assert np.abs(to_np(sig[k]) - s_ref).max() <= 1e-5 * s_ref[0]
+    Gp = tucker.multi_ttm_t(Xo, Un)
+    assert np.abs(to_np(G) - Gp).max() <= 1e-5 * np.abs(Gp).max()
+    er = tucker.relerr(Xo, tucker.reconstruct(tucker.multi_ttm_t(Xo, ref["U"]), ref["U"]))
+    assert abs(rt.rtucker_relerr(Xd, G, U) - er) <= RELERR_TOL
+
+
 def test_rp_equals_n_and_p_zero(rt):
     X = synth.tucker_tensor((8, 30, 25), (5, 6, 6), noise=1e-3, data_seed=9)
     _run_and_compare(rt, X, (5, 6, 6), 3, seed=5)       # r_0 + p = n_0
