@@ -1043,21 +1043,28 @@ rt_status rtucker_core(rt_handle h, const void* X, rt_dtype dtype, int d, const 
 namespace {
 
 // Largest intermediate of the expansion of the leading d-2 modes of an
-// r_0 x ... x r_{d-1} core (mode k: r_k -> n_k, k < d-2).
+// r_0 x ... x r_{d-1} core (mode k: r_k -> n_k, k < d-2), and of mode d-2 as well
+// when the last two modes take the general form.
 size_t expand_buffer_floats(int d, const int64_t* n, const int32_t* r) {
   size_t cur = 1;
   for (int k = 0; k < d; ++k) cur *= (size_t)r[k];
   size_t best = cur;
+  int64_t L = 1;
   for (int k = 0; k + 2 < d; ++k) {
     cur = cur / (size_t)r[k] * (size_t)n[k];
     best = std::max(best, cur);
+    L *= n[k];
   }
+  if (last_modes_general(L, n[d - 2], r[d - 2], n[d - 1], r[d - 1]))
+    best = std::max(best, cur / (size_t)r[d - 2] * (size_t)n[d - 2]);
   return best;
 }
 
 // out = alpha X + beta C x_0 U_0 ... x_{d-1} U_{d-1} (X may be null): the leading
 // d-2 modes of C expanded into H (two ping-pong buffers), then the last two per
-// slab of H; sumsq (device, may be null) receives scale * ||out||_F^2.
+// slab of H, or (slabs too large or too few) mode d-2 expanded as well and the
+// last mode by rows; sumsq (device, may be null) receives scale * ||out||_F^2.
+// Returns the launches made, 0 if the shape is unsupported.
 int enqueue_expand(rt_handle h, const float* C, int d, const int64_t* n, const int32_t* r, const float* U,
                    const size_t* uoff, const void* X, int dtype, float alpha, float beta, float* out, float* bufA,
                    float* bufB, double* part, double* sumsq, double scale) {
@@ -1073,9 +1080,17 @@ int enqueue_expand(rt_handle h, const float* C, int d, const int64_t* n, const i
     A = o;
     L *= n[k];
   }
-  nl += launch_tucker_slab_out(X, dtype, alpha, beta, A, L, n[d - 2], r[d - 2], n[d - 1], r[d - 1],
-                               U + uoff[d - 2], U + uoff[d - 1], out, part, sumsq, scale, st);
-  return nl;
+  int got;
+  if (last_modes_general(L, n[d - 2], r[d - 2], n[d - 1], r[d - 1])) {
+    float* o = (A == bufA) ? bufB : bufA;
+    nl += launch_expand_f32(A, L, r[d - 2], r[d - 1], U + uoff[d - 2], n[d - 2], o, st);
+    got = launch_last_out(X, dtype, alpha, beta, o, L * n[d - 2], r[d - 1], n[d - 1], U + uoff[d - 1], out, part,
+                          sumsq, scale, st);
+  } else {
+    got = launch_tucker_slab_out(X, dtype, alpha, beta, A, L, n[d - 2], r[d - 2], n[d - 1], r[d - 1],
+                                 U + uoff[d - 2], U + uoff[d - 1], out, part, sumsq, scale, st);
+  }
+  return got > 0 ? nl + got : 0;
 }
 
 // Plan of the partial projections Y_n = T x_{m != n} U_m^T of an n_0 x ... x n_{d-1}

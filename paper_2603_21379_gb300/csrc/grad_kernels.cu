@@ -159,6 +159,78 @@ __global__ void __launch_bounds__(SO_THREADS) k_tucker_slab_out(
   }
 }
 
+// General form of the last two modes, for slabs too large for shared memory or too
+// few to fill the GPU: Hp = H x_{d-2} U1 is expanded beforehand (M = L n1 rows of
+// r2), and here
+//   out(l, j) = alpha X(l, j) + beta sum_b Hp[l][b] U2[j][b],   l < M, j < n2.
+// Tiles of LO_R rows x LO_J columns; tile g = tj * ntr + tr, so that a CTA walking
+// g, g + gridDim.x, ... keeps its column chunk of U2 (transposed in shared memory,
+// reloaded only when tj changes) over many row tiles.  Thread (rh, j): column j of
+// the chunk for LO_R / 2 rows.  part[blockIdx.x] = the CTA's sum of out^2 (float
+// per thread and tile, float64 across tiles and threads).
+constexpr int LO_THREADS = 256, LO_J = 128, LO_R = 32, LO_RT = LO_R / (LO_THREADS / LO_J);
+constexpr int LO_LDU = LO_J + 1;     // odd stride: the transposing store is conflict-free
+__global__ void __launch_bounds__(LO_THREADS) k_last_out(const void* __restrict__ X, int dtype, float alpha,
+                                                         float beta, const float* __restrict__ Hp, int64_t M,
+                                                         int r2, int64_t n2, const float* __restrict__ U2,
+                                                         float* __restrict__ out, double* __restrict__ part) {
+  __shared__ float U2t[CMAX * LO_LDU];               // [b][jj]
+  __shared__ __align__(16) float Hs[LO_R * CMAX];    // [row][b]
+  __shared__ double red[LO_THREADS / 32];
+  const int64_t ntr = (M + LO_R - 1) / LO_R, ntj = (n2 + LO_J - 1) / LO_J;
+  const int jj = threadIdx.x % LO_J, rh = threadIdx.x / LO_J;
+  int64_t cur_tj = -1;
+  double sqd = 0.0;
+  for (int64_t g = blockIdx.x; g < ntr * ntj; g += gridDim.x) {
+    const int64_t tj = g / ntr, tr = g % ntr;
+    const int64_t j0 = tj * LO_J, l0 = tr * LO_R;
+    __syncthreads();
+    if (tj != cur_tj) {
+      for (int e = threadIdx.x; e < r2 * LO_J; e += LO_THREADS) {
+        const int b = e % r2, c = e / r2;     // consecutive threads read consecutive b of row j0 + c
+        U2t[b * LO_LDU + c] = (j0 + c < n2) ? __ldg(U2 + (j0 + c) * r2 + b) : 0.f;
+      }
+      cur_tj = tj;
+    }
+    for (int e = threadIdx.x; e < LO_R * r2; e += LO_THREADS) {
+      const int rr = e / r2, b = e % r2;
+      Hs[rr * CMAX + b] = (l0 + rr < M) ? Hp[(l0 + rr) * r2 + b] : 0.f;
+    }
+    __syncthreads();
+    float acc[LO_RT];
+#pragma unroll
+    for (int u = 0; u < LO_RT; ++u) acc[u] = 0.f;
+    const float* hrow = Hs + rh * LO_RT * CMAX;
+    for (int b = 0; b < r2; ++b) {
+      const float u2 = U2t[b * LO_LDU + jj];
+#pragma unroll
+      for (int u = 0; u < LO_RT; ++u) acc[u] = fmaf(hrow[u * CMAX + b], u2, acc[u]);
+    }
+    const int64_t j = j0 + jj;
+    float sq = 0.f;
+    if (j < n2) {
+#pragma unroll
+      for (int u = 0; u < LO_RT; ++u) {
+        const int64_t l = l0 + rh * LO_RT + u;
+        if (l >= M) break;
+        const int64_t e = l * n2 + j;
+        const float val = X ? fmaf(alpha, ldx(X, dtype, e), beta * acc[u]) : beta * acc[u];
+        if (out) out[e] = val;
+        sq = fmaf(val, val, sq);
+      }
+    }
+    sqd += (double)sq;
+  }
+  sqd = warp_sum_d(sqd);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sqd;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < LO_THREADS / 32; ++q) t += red[q];
+    part[blockIdx.x] = t;
+  }
+}
+
 // out[0] = scale * sum of part[0..nblk) in a fixed order.
 __global__ void k_sum_parts(const double* __restrict__ part, int nblk, double scale, double* __restrict__ out) {
   __shared__ double red[32];
@@ -262,14 +334,38 @@ int launch_expand_f32(const float* A, int64_t L, int r, int64_t R, const float* 
 int launch_tucker_slab_out(const void* X, int dtype, float alpha, float beta, const float* H, int64_t nslab,
                            int64_t n1, int r1, int64_t n2, int r2, const float* U1, const float* U2, float* out,
                            double* part, double* sumsq_scaled, double scale, cudaStream_t st) {
-  if (n1 > 65536 || n2 > 65536) return 0;
+  if (!slab_out_fits(n1, r1, n2, r2)) return 0;
   const int64_t n1p = (n1 + 3) & ~(int64_t)3, n2p = (n2 + 3) & ~(int64_t)3, r1p = (r1 + 3) & ~3;
   const size_t smem = (size_t)(r1 * n1p + r2 * n2p + r2 * r1p + r1 * n2p) * 4;
-  if (smem > 200 * 1024) return 0;
   cudaFuncSetAttribute(k_tucker_slab_out, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int nb = (int)(nslab < GR_SLAB_BLOCKS ? nslab : GR_SLAB_BLOCKS);
   k_tucker_slab_out<<<nb, SO_THREADS, smem, st>>>(X, dtype, alpha, beta, H, nslab, (int)n1, r1, (int)n2, r2, U1,
                                                    U2, out, part);
+  int nl = 1;
+  if (sumsq_scaled) {
+    k_sum_parts<<<1, 1024, 0, st>>>(part, nb, scale, sumsq_scaled);
+    ++nl;
+  }
+  return nl;
+}
+
+bool slab_out_fits(int64_t n1, int r1, int64_t n2, int r2) {
+  if (n1 > 65536 || n2 > 65536) return false;
+  const int64_t n1p = (n1 + 3) & ~(int64_t)3, n2p = (n2 + 3) & ~(int64_t)3, r1p = (r1 + 3) & ~3;
+  return (r1 * n1p + r2 * n2p + r2 * r1p + r1 * n2p) * 4 <= 200 * 1024;
+}
+
+bool last_modes_general(int64_t L, int64_t n1, int r1, int64_t n2, int r2) {
+  return !slab_out_fits(n1, r1, n2, r2) || (L < GR_SLAB_BLOCKS / 8 && n1 * n2 > 65536);
+}
+
+int launch_last_out(const void* X, int dtype, float alpha, float beta, const float* Hp, int64_t M, int r2,
+                    int64_t n2, const float* U2, float* out, double* part, double* sumsq_scaled, double scale,
+                    cudaStream_t st) {
+  if (r2 < 1 || r2 > CMAX || M < 1 || n2 < 1) return 0;
+  const int64_t tiles = ((M + LO_R - 1) / LO_R) * ((n2 + LO_J - 1) / LO_J);
+  const int nb = (int)(tiles < GR_SLAB_BLOCKS ? tiles : GR_SLAB_BLOCKS);
+  k_last_out<<<nb, LO_THREADS, 0, st>>>(X, dtype, alpha, beta, Hp, M, r2, n2, U2, out, part);
   int nl = 1;
   if (sumsq_scaled) {
     k_sum_parts<<<1, 1024, 0, st>>>(part, nb, scale, sumsq_scaled);

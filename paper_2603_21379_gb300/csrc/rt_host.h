@@ -82,6 +82,17 @@ size_t expand_partial_doubles();
 int launch_tucker_slab_out(const void* X, int dtype, float alpha, float beta, const float* H, int64_t nslab,
                            int64_t n1, int r1, int64_t n2, int r2, const float* U1, const float* U2, float* out,
                            double* part, double* sumsq_scaled, double scale, cudaStream_t st);
+// Whether launch_tucker_slab_out takes slabs of n1 x n2 with ranks r1, r2.
+bool slab_out_fits(int64_t n1, int r1, int64_t n2, int r2);
+// Whether the last two modes of L slabs take the general form (launch_last_out after
+// one more expansion): slabs too large for launch_tucker_slab_out, or large slabs
+// fewer than the SMs.
+bool last_modes_general(int64_t L, int64_t n1, int r1, int64_t n2, int r2);
+// out(l, j) = alpha X(l, j) + beta sum_b Hp[l][b] U2[j][b] for M rows of n2 (the last
+// mode; Hp holds the other modes already expanded), with the same sum of squares.
+int launch_last_out(const void* X, int dtype, float alpha, float beta, const float* Hp, int64_t M, int r2,
+                    int64_t n2, const float* U2, float* out, double* part, double* sumsq_scaled, double scale,
+                    cudaStream_t st);
 // out[i][a] = scale * sum_{p,q} Y(p, i, q) C(p, a, q) (Y of P x n x Q, C of P x r x Q);
 // scratch: unfold_scratch_floats(n, r, P * Q) floats.
 size_t unfold_scratch_floats(int64_t n, int r, int64_t K);

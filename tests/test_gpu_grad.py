@@ -81,6 +81,58 @@ def test_loss_grad_random_model(rt, shape, ranks):
     assert abs(L - Lr) <= 1e-6 * Lr + REL * float(np.sum(A * np.abs(dXr)))
 
 
+# Shapes whose last two modes take the general form (mode d-2 expanded, then the last
+# mode by rows): one large slab (d = 2); slabs too large for shared memory.
+GENERAL = [((600, 500), (8, 12)), ((3, 700, 1100), (2, 20, 30))]
+
+
+@pytest.mark.parametrize("shape,ranks", GENERAL)
+def test_loss_grad_general_last_modes(rt, shape, ranks):
+    rs = np.random.default_rng(sum(shape))
+    X = rs.standard_normal(shape).astype(np.float32)
+    G = rs.standard_normal(ranks).astype(np.float32)
+    U = [(rs.standard_normal((n, r)) / np.sqrt(n)).astype(np.float32) for n, r in zip(shape, ranks)]
+    L, dX, dG, dU = _run_grad(rt, X, G, U)
+    Lr, dXr, dGr, dUr = tg.misfit_grads(X, G, U)
+    A, sG, sU = _scales(X, G, U)
+    _check(dX, dXr, A, "dX")
+    _check(dG, dGr, sG, "dG")
+    for n in range(len(U)):
+        _check(dU[n], dUr[n], sU[n], "dU%d" % n)
+    bound = REL * float(np.sum(A * np.abs(dXr)))
+    assert abs(L - Lr) <= 1e-6 * Lr + bound
+    # the loss alone (no residual stored) and the core adjoint's Xbar (no X) on the same path
+    Xd = torch.from_numpy(X).cuda()
+    Gd = torch.from_numpy(G).cuda()
+    Ud = [torch.from_numpy(u).cuda() for u in U]
+    only = rt.rtucker_loss_grad(Xd, Gd, Ud, dX=False, dG=False, dU=False)
+    xb, _ = rt.rtucker_core_adjoint(Xd, Ud, Gd, Ubar=False)
+    rt.sync()
+    assert abs(only[0].item() - Lr) <= 1e-6 * Lr + bound
+    Xbr, _ = tg.core_projection_adjoint(X, U, G)
+    _check(xb.cpu().numpy(), Xbr, np.abs(reconstruct(np.abs(G).astype(np.float64), [np.abs(u) for u in U])),
+           "Xbar")
+
+
+def test_loss_grad_general_many_large_slabs(rt):
+    # 152 slabs of 260 x 300 with r = 64 in the last two modes: more slabs than SMs,
+    # each too large for shared memory; dX compared on sampled entries
+    shape, ranks = (19, 8, 260, 300), (2, 2, 64, 64)
+    rs = np.random.default_rng(21)
+    X = rs.standard_normal(shape).astype(np.float32)
+    G = rs.standard_normal(ranks).astype(np.float32)
+    U = [(rs.standard_normal((n, r)) / np.sqrt(n)).astype(np.float32) for n, r in zip(shape, ranks)]
+    L, dX, dG, dU = _run_grad(rt, X, G, U)
+    Lr, dXr, dGr, dUr = tg.misfit_grads(X, G, U)
+    A, sG, sU = _scales(X, G, U)
+    idx = tuple(rs.integers(0, n, size=20000) for n in shape)
+    _check(dX[idx], dXr[idx], A[idx], "dX")
+    _check(dG, dGr, sG, "dG")
+    for n in range(4):
+        _check(dU[n], dUr[n], sU[n], "dU%d" % n)
+    assert abs(L - Lr) <= 1e-6 * Lr + REL * float(np.sum(A * np.abs(dXr)))
+
+
 def test_loss_only_and_partial_outputs(rt):
     rs = np.random.default_rng(3)
     shape, ranks = (20, 17, 19), (4, 3, 5)
