@@ -238,15 +238,17 @@ rt_status rtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, cons
  *   U_nodes     device or NULL: concat over non-root nodes in id order of the
  *               node bases U_S (n_S x r_S).
  * Rules: r_S + p <= min(n_S, n_{notin S}), r_S + p <= w_S <= n_{notin S}
- * (RT_EINVAL otherwise); ranks of internal nodes and of their children at
- * most 12 (RT_ENOTSUP otherwise: the transfer-tensor and root kernels keep
- * r x r x r blocks in registers and shared memory; the paper uses 10). */
+ * and r_S + p <= 64 (RT_EINVAL / RT_ENOTSUP otherwise).  Transfer tensors whose
+ * ranks are all at most 12 (the paper uses 10) take one grouped kernel that
+ * keeps r x r x r blocks on chip; wider ones take two mode contractions and a
+ * permutation.  A root right-child rank above 12 costs one pass over X per
+ * chunk of at most 12 columns of U_{R_r} (ceil(r / 12) passes). */
 rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
                              const int32_t* rank, int32_t p, const int64_t* w, uint64_t seed,
                              const rt_options* opt, float* U_leaf, float* B, float* U_nodes);
 
 /* Relative error of the H-Tucker format (U_leaf, B) against X, float64 on the
- * device; *out (HOST) written after the call synchronises. */
+ * device; *out (HOST) written after the call synchronises.  Ranks 1..64. */
 rt_status rhtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
                           const int32_t* rank, const float* U_leaf, const float* B, double* out);
 

@@ -223,13 +223,15 @@ struct ProbSpec {
 
 struct ProbPlan {
   RFProb q;
-  size_t o_idx, o_off, o_Om, o_Yt, o_Zp, o_zcnt, o_Q, o_Rb, o_Q2, o_Bp, o_Rc, o_W, o_Wsg, o_sig, o_keys, o_U;
-  int64_t units[STG_COUNT];
+  size_t o_idx, o_off, o_Om, o_Yt, o_Zp, o_zcnt, o_Q, o_Rb, o_Q2, o_tsR, o_tsQ, o_Bp, o_Rc, o_W, o_Wsg, o_sig,
+      o_keys, o_U, o_wsR;
+  int64_t units[STG_ALL];
 };
 
 rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp) {
   RFProb& q = pp.q;
   memset(&q, 0, sizeof(q));
+  for (int64_t& u : pp.units) u = 0;
   const int d = ps.d;
   int64_t stride[MAXD];
   stride[d - 1] = 1;
@@ -270,14 +272,37 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
     q.rbrows = (int)nS;
   } else {
     q.rbrows = rb;
+    if ((nS + rb - 1) / rb > (1 << 30)) return fail(h, RT_ENOTSUP, "unfolding too tall for the TSQR");
     q.nrb = (int)((nS + rb - 1) / rb);
-    if ((int64_t)odd(q.nrb * c) * c > QR2_MAXF)
-      return fail(h, RT_ENOTSUP, "unfolding too tall for the two-level TSQR");
+    // TSQR tree: groups of up to `fan` stacked R factors per level (the largest
+    // stack the level kernel holds), until one group is left
+    int fan = 1;
+    while ((int64_t)odd((fan + 1) * c) * c <= QR2_MAXF) ++fan;
+    q.fan = fan;
+    q.lev_n[0] = q.nrb;
+    int64_t cnt = q.nrb;
+    while (cnt > 1) {
+      if (q.nlev == TS_MAXLEV) return fail(h, RT_ENOTSUP, "unfolding too tall for the TSQR tree");
+      cnt = (cnt + fan - 1) / fan;
+      q.lev_n[++q.nlev] = (int)cnt;
+    }
   }
   q.scrows = BT_SC;
   q.nsc = (int)((ps.s + BT_SC - 1) / BT_SC);
   q.nbi = (int)((nS + BT_IB - 1) / BT_IB);
-  if ((int64_t)odd(q.nsc * c) * c > WS_MAXF) return fail(h, RT_ENOTSUP, "too many samples for the W-step");
+  // more chunk factors than the W-step stacks: an R tree over them first
+  int wf = 1, tf = 1;
+  while ((int64_t)odd((wf + 1) * c) * c <= WS_MAXF) ++wf;
+  while ((int64_t)odd((tf + 1) * c) * c <= QR2_MAXF) ++tf;
+  q.wfan = tf;
+  q.wn[0] = q.nsc;
+  int64_t wcnt = q.nsc;
+  while (wcnt > wf) {
+    if (q.wlev == TS_MAXLEV) return fail(h, RT_ENOTSUP, "too many samples for the W-step");
+    wcnt = (wcnt + tf - 1) / tf;
+    q.wn[++q.wlev] = (int)wcnt;
+  }
+  q.nrw = (int)wcnt;
   const int64_t s = ps.s;
   pp.o_idx = ps.idx_out ? (size_t)-1 : bump.take(s * 8);
   pp.o_off = bump.take(s * 8);
@@ -288,8 +313,15 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   pp.o_Q = bump.take((size_t)nS * c * 4);
   pp.o_Rb = bump.take(q.nrb > 1 ? (size_t)q.nrb * c * c * 4 : 4);
   pp.o_Q2 = bump.take(q.nrb > 1 ? (size_t)q.nrb * c * c * 4 : 4);
+  size_t upper = 0;   // factors entering levels 1 .. nlev-1
+  for (int j = 1; j < q.nlev; ++j) upper += (size_t)q.lev_n[j];
+  pp.o_tsR = bump.take(upper ? upper * c * c * 4 : 4);
+  pp.o_tsQ = bump.take(upper ? upper * c * c * 4 : 4);
   pp.o_Bp = bump.take((size_t)q.nbi * s * c * 4);
   pp.o_Rc = bump.take((size_t)q.nsc * c * c * 4);
+  size_t wup = 0;   // factors produced by the R tree's levels
+  for (int j = 1; j <= q.wlev; ++j) wup += (size_t)q.wn[j];
+  pp.o_wsR = bump.take(wup ? wup * c * c * 4 : 4);
   pp.o_W = bump.take((size_t)c * c * 4);
   pp.o_Wsg = bump.take((size_t)c * ps.r * 4);
   pp.o_sig = bump.take((size_t)c * 4);
@@ -302,7 +334,9 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   pp.units[STG_SAMPLE] = s;
   pp.units[STG_GS] = nrt * q.nzc;
   pp.units[STG_QR1] = q.nrb;
-  pp.units[STG_QR2] = q.nrb > 1 ? 1 : 0;
+  for (int j = 0; j < q.nlev; ++j) pp.units[stg_qr2(j)] = q.lev_n[j + 1];      // groups of level j
+  for (int t = 0; t + 1 < q.nlev; ++t) pp.units[stg_qrc(t)] = q.lev_n[q.nlev - 2 - t];   // members
+  for (int j = 0; j < q.wlev; ++j) pp.units[stg_wt(j)] = q.wn[j + 1];                    // groups
   pp.units[STG_QR3] = q.nrb > 1 ? q.nrb : 0;
   pp.units[STG_BTP] = (int64_t)q.nsc * q.nbi;
   pp.units[STG_BTQ] = q.nsc;
@@ -326,8 +360,18 @@ void bind_problem(ProbPlan& pp, char* ws) {
   q.Q = reinterpret_cast<float*>(ws + pp.o_Q);
   q.Rb = reinterpret_cast<float*>(ws + pp.o_Rb);
   q.Q2 = reinterpret_cast<float*>(ws + pp.o_Q2);
+  q.tsR = reinterpret_cast<float*>(ws + pp.o_tsR);
+  q.tsQ = reinterpret_cast<float*>(ws + pp.o_tsQ);
   q.Bp = reinterpret_cast<float*>(ws + pp.o_Bp);
   q.Rc = reinterpret_cast<float*>(ws + pp.o_Rc);
+  q.wsR = reinterpret_cast<float*>(ws + pp.o_wsR);
+  if (q.wlev == 0) {
+    q.Rw = q.Rc;
+  } else {
+    size_t o = 0;
+    for (int j = 1; j < q.wlev; ++j) o += (size_t)q.wn[j];
+    q.Rw = q.wsR + o * q.c * q.c;
+  }
   q.W = reinterpret_cast<float*>(ws + pp.o_W);
   q.Wsg = reinterpret_cast<float*>(ws + pp.o_Wsg);
   q.sigma = reinterpret_cast<float*>(ws + pp.o_sig);
@@ -454,10 +498,23 @@ struct Group {
   RFGroup g{};
 };
 
+// Prefix rows a group needs: the fixed stages, plus the tree stages when one of its
+// problems has a TSQR tree of two or more levels or an R tree before its W-step.
+int group_rows(const Group& G, int* lmax, int* wmax = nullptr) {
+  int l = 0, w = 0;
+  for (const ProbPlan& p : G.pp) {
+    l = std::max(l, (int)p.q.nlev);
+    w = std::max(w, (int)p.q.wlev);
+  }
+  if (lmax) *lmax = l;
+  if (wmax) *wmax = w;
+  return (l > 1 || w > 0) ? STG_ALL : STG_COUNT;
+}
+
 void group_layout(Group& G, Bump& bump) {
   const int np = (int)G.pp.size();
   G.o_tab = bump.take(sizeof(RFProb) * np);
-  G.o_pre = bump.take(sizeof(int64_t) * STG_COUNT * (np + 1));
+  G.o_pre = bump.take(sizeof(int64_t) * group_rows(G, nullptr) * (np + 1));
 }
 
 // Writes the tables into staging and queues their upload; fills G.g.
@@ -469,18 +526,23 @@ rt_status group_upload(rt_handle h, Group& G, char* stage, size_t stage_off) {
     bind_problem(G.pp[i], h->ws);
     tab[i] = G.pp[i].q;
   }
-  for (int st = 0; st < STG_COUNT; ++st) {
+  int lmax = 0, wmax = 0;
+  const int nst = group_rows(G, &lmax, &wmax);
+  for (int st = 0; st < STG_ALL; ++st) {
     int64_t acc = 0;
     for (int i = 0; i < np; ++i) {
-      pre[st * (np + 1) + i] = acc;
+      if (st < nst) pre[st * (np + 1) + i] = acc;
       acc += G.pp[i].units[st];
     }
-    pre[st * (np + 1) + np] = acc;
-    G.g.total[st] = acc;
+    if (st < nst) pre[st * (np + 1) + np] = acc;
+    G.g.total[st] = st < nst ? acc : 0;
   }
+  G.g.nst = nst;
+  G.g.lmax = lmax;
+  G.g.wmax = wmax;
   rt_status st;
   if ((st = stage_put(h, h->ws + G.o_tab, tab, sizeof(RFProb) * np)) != RT_OK) return st;
-  if ((st = stage_put(h, h->ws + G.o_pre, pre, sizeof(int64_t) * STG_COUNT * (np + 1))) != RT_OK) return st;
+  if ((st = stage_put(h, h->ws + G.o_pre, pre, sizeof(int64_t) * nst * (np + 1))) != RT_OK) return st;
   G.g.probs = reinterpret_cast<const RFProb*>(h->ws + G.o_tab);
   G.g.pre = reinterpret_cast<const int64_t*>(h->ws + G.o_pre);
   G.g.nprob = np;
@@ -489,7 +551,7 @@ rt_status group_upload(rt_handle h, Group& G, char* stage, size_t stage_off) {
 
 size_t group_stage_bytes(const Group& G) {
   const int np = (int)G.pp.size();
-  return align_up(sizeof(RFProb) * np) + align_up(sizeof(int64_t) * STG_COUNT * (np + 1));
+  return align_up(sizeof(RFProb) * np) + align_up(sizeof(int64_t) * group_rows(G, nullptr) * (np + 1));
 }
 
 rt_status check_tensor(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, int64_t* total) {
@@ -1600,22 +1662,30 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
     Gp.pp.push_back(pp);
   }
   group_layout(Gp, bump);
-  // transfer jobs (internal non-root nodes) and the root
-  std::vector<int> internal;
-  for (int i = 1; i < nn; ++i)
-    if (tree[i].a != tree[i].b) internal.push_back(i);
+  // transfer jobs (internal non-root nodes): ranks up to TRANSFER_RMAX in one grouped
+  // launch, wider ones one by one in the general form; and the root
+  std::vector<int> internal, wide;
+  size_t gen_floats = 4;
+  for (int i = 1; i < nn; ++i) {
+    if (tree[i].a == tree[i].b) continue;
+    const int rl_i = rk[tree[i].left], rr_i = rk[tree[i].right];
+    if (rk[i] <= TRANSFER_RMAX && rl_i <= TRANSFER_RMAX && rr_i <= TRANSFER_RMAX) {
+      internal.push_back(i);
+    } else {
+      wide.push_back(i);
+      gen_floats = std::max(gen_floats, transfer_general_floats(range_prod(n, tree[tree[i].left].a,
+                                                                           tree[tree[i].left].b),
+                                                                rk[i], rl_i, rr_i));
+    }
+  }
   const size_t o_jobs = bump.take(sizeof(TransferJob) * std::max<size_t>(1, internal.size()));
+  const size_t o_tgen = bump.take(gen_floats * 4);
   const TNode& root = tree[0];
   const int64_t nl = range_prod(n, root.a, tree[root.left].b), nr = total / nl;
   const int rl = rk[root.left], rr = rk[root.right];
-  if (rr > 12) return fail(h, RT_ENOTSUP, "rank of the root's right child above 12");
-  const size_t o_rootp = bump.take(root_pass_scratch_floats(nl, nr, rl, rr) * 4);
+  const size_t o_rootp = bump.take(root_any_scratch_floats(nl, nr, rl, rr) * 4);
   int64_t tr_ctas = 0;
-  for (int i : internal) {
-    if (rk[i] > 12 || rk[tree[i].left] > 12 || rk[tree[i].right] > 12)
-      return fail(h, RT_ENOTSUP, "internal-node ranks above 12");
-    tr_ctas += transfer_ctas(range_prod(n, tree[tree[i].left].a, tree[tree[i].left].b));
-  }
+  for (int i : internal) tr_ctas += transfer_ctas(range_prod(n, tree[tree[i].left].a, tree[tree[i].left].b));
   const size_t o_tpart = bump.take(transfer_part_floats(std::max<int64_t>(1, tr_ctas)) * 4);
   if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
   const size_t sb = group_stage_bytes(Gp) + align_up(sizeof(TransferJob) * std::max<size_t>(1, internal.size()));
@@ -1656,11 +1726,25 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
     StageTimer tm(h, 3);
     nlaunch += launch_transfer(reinterpret_cast<const TransferJob*>(h->ws + o_jobs), jobs, (int)internal.size(),
                                reinterpret_cast<float*>(h->ws + o_tpart), h->stream);
+    for (int i : wide) {
+      const TNode& nd = tree[i];
+      TransferJob jb{};
+      jb.US = Uof(i);
+      jb.Ul = Uof(nd.left);
+      jb.Ur = Uof(nd.right);
+      jb.B = B + o_B[i];
+      jb.nl = range_prod(n, tree[nd.left].a, tree[nd.left].b);
+      jb.nr = range_prod(n, tree[nd.right].a, tree[nd.right].b);
+      jb.rS = rk[i];
+      jb.rl = rk[nd.left];
+      jb.rr = rk[nd.right];
+      nlaunch += launch_transfer_general(jb, reinterpret_cast<float*>(h->ws + o_tgen), h->stream);
+    }
   }
   {
     StageTimer tm(h, 4);
-    nlaunch += launch_root(X, (int)dtype, nl, nr, Uof(root.left), rl, Uof(root.right), rr, B + o_B[0],
-                           reinterpret_cast<float*>(h->ws + o_rootp), h->d_status, h->stream);
+    nlaunch += launch_root_any(X, (int)dtype, nl, nr, Uof(root.left), rl, Uof(root.right), rr, B + o_B[0],
+                               reinterpret_cast<float*>(h->ws + o_rootp), h->d_status, h->stream);
   }
   return finish(h, nlaunch);
 }
@@ -1676,7 +1760,8 @@ rt_status rhtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, con
   std::vector<int> rk(nn);
   for (int i = 0; i < nn; ++i) rk[i] = (i == 0) ? 1 : rank[i];
   const TNode& root = tree[0];
-  if (rk[root.right] > 16) return fail(h, RT_ENOTSUP, "rank of the root's right child above 16");
+  for (int i = 1; i < nn; ++i)
+    if (rk[i] < 1 || rk[i] > CMAX) return fail(h, RT_EINVAL, "need 1 <= rank <= 64 at every node");
   std::vector<size_t> o_u(nn, 0), o_leaf(nn, 0), o_B(nn, 0);
   Bump bump;
   for (int i = 1; i < nn; ++i) o_u[i] = bump.take((size_t)range_prod(n, tree[i].a, tree[i].b) * rk[i] * 8);

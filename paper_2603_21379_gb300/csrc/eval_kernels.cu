@@ -208,12 +208,12 @@ __global__ void k_ht_v(const double* __restrict__ Ul, int64_t nl, int rl, const 
   }
 }
 
-// xhat(a, b) = sum_k V[a][k] Ur[b][k]; tiles of 32 rows x 256 columns
+// xhat(a, b) = sum_k V[a][k] Ur[b][k]; tiles of 32 rows x 256 columns; r_r <= CMAX
 constexpr int HE_RA = 32, HE_CB = 256;
 __global__ void __launch_bounds__(256) k_ht_err(const void* __restrict__ X, int dtype, int64_t nl, int64_t nr,
                                                 const double* __restrict__ V, const double* __restrict__ Ur,
                                                 int rr, double* __restrict__ part) {
-  __shared__ double Vs[HE_RA * 16];
+  __shared__ double Vs[HE_RA * CMAX];
   __shared__ double red[64];
   double se = 0.0, sx = 0.0;
   const int64_t ntr = (nl + HE_RA - 1) / HE_RA, ntc = (nr + HE_CB - 1) / HE_CB;
@@ -222,15 +222,15 @@ __global__ void __launch_bounds__(256) k_ht_err(const void* __restrict__ X, int 
     __syncthreads();
     for (int e = threadIdx.x; e < HE_RA * rr; e += blockDim.x) {
       const int64_t a = a0 + e / rr;
-      Vs[(e / rr) * 16 + e % rr] = (a < nl) ? V[a * rr + e % rr] : 0.0;
+      Vs[(e / rr) * CMAX + e % rr] = (a < nl) ? V[a * rr + e % rr] : 0.0;
     }
     __syncthreads();
     if (b < nr) {
-      double u[16];
+      double u[CMAX];
       for (int k = 0; k < rr; ++k) u[k] = Ur[b * rr + k];
       for (int ra = 0; ra < HE_RA && a0 + ra < nl; ++ra) {
         double xh = 0.0;
-        for (int k = 0; k < rr; ++k) xh = fma(Vs[ra * 16 + k], u[k], xh);
+        for (int k = 0; k < rr; ++k) xh = fma(Vs[ra * CMAX + k], u[k], xh);
         const double x = ldxd(X, dtype, (a0 + ra) * nr + b);
         se = fma(x - xh, x - xh, se);
         sx = fma(x, x, sx);
@@ -250,13 +250,13 @@ __global__ void __launch_bounds__(256) k_ht_err(const void* __restrict__ X, int 
   }
 }
 
-size_t ht_relerr_scratch(int64_t nl, int64_t nr) { (void)nr; return (size_t)nl * 16 + 2 * EV_BLOCKS + 16; }
+size_t ht_relerr_scratch(int64_t nl, int64_t nr) { (void)nr; return (size_t)nl * CMAX + 2 * EV_BLOCKS + 16; }
 
 int launch_ht_relerr(const void* X, int dtype, int64_t nl, int64_t nr, const double* Ul, int rl,
                      const float* BR, const double* Ur, int rr, double* scratch, double* result2,
                      cudaStream_t st) {
   double* V = scratch;
-  double* part = scratch + (size_t)nl * 16;
+  double* part = scratch + (size_t)nl * CMAX;
   k_ht_v<<<1024, 256, 0, st>>>(Ul, nl, rl, BR, rr, V);
   k_ht_err<<<EV_BLOCKS, 256, 0, st>>>(X, dtype, nl, nr, V, Ur, rr, part);
   k_reduce_pairs<<<1, 1024, 0, st>>>(part, EV_BLOCKS, result2);

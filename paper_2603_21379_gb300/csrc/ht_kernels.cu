@@ -25,6 +25,7 @@ namespace rt {
 //     part_c(i, j, k) = sum_a U_l(a, j) T(a, i, k)
 // k_transfer_sum: B_S = sum over the job's CTAs of part_c, fixed order, float64.
 constexpr int TR_A = 4, TR_B = 64, TR_MAX = 12, TR_TH = 256;
+static_assert(TR_MAX == TRANSFER_RMAX, "grouped transfer kernel width");
 
 __global__ void __launch_bounds__(TR_TH) k_transfer_part(const TransferJob* __restrict__ jobs, int njobs,
                                                          float* __restrict__ part) {
@@ -86,6 +87,31 @@ __global__ void __launch_bounds__(TR_TH) k_transfer_sum(const TransferJob* __res
   double v = 0.0;
   for (int64_t c = 0; c < nc; ++c) v += (double)part[(size_t)(jb.cta0 + c) * TR_MAX * TR_MAX * TR_MAX + o];
   jb.B[o] = (float)v;
+}
+
+// General form of one transfer tensor, for ranks above TR_MAX (up to 64): two mode
+// contractions, T1(a, k, i) = sum_b U_r(b, k) U_S(a n_r + b, i) and
+// T2(j, k, i) = sum_a U_l(a, j) T1(a, k, i), then B_S(i, j, k) = T2(j, k, i).
+__global__ void k_perm_jki(const float* __restrict__ T2, int rS, int rl, int rr, float* __restrict__ B) {
+  const int tot = rS * rl * rr;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {
+    const int i = e / (rl * rr), j = (e / rr) % rl, k = e % rr;
+    B[e] = T2[((size_t)j * rr + k) * rS + i];
+  }
+}
+
+size_t transfer_general_floats(int64_t nl, int rS, int rl, int rr) {
+  return (size_t)nl * rr * rS + (size_t)rl * rr * rS + 4;
+}
+
+int launch_transfer_general(const TransferJob& jb, float* scratch, cudaStream_t st) {
+  float* T1 = scratch;
+  float* T2 = scratch + (((size_t)jb.nl * jb.rr * jb.rS + 3) & ~(size_t)3);
+  int n = launch_ttm_t(jb.US, DT_F32, jb.nl, jb.nr, jb.rS, jb.Ur, jb.rr, T1, st);
+  n += launch_ttm_t(T1, DT_F32, 1, jb.nl, (int64_t)jb.rr * jb.rS, jb.Ul, jb.rl, T2, st);
+  const int tot = jb.rS * jb.rl * jb.rr;
+  k_perm_jki<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(T2, jb.rS, jb.rl, jb.rr, jb.B);
+  return n + 1;
 }
 
 int64_t transfer_ctas(int64_t nl) { return (nl + TR_A - 1) / TR_A; }
@@ -253,6 +279,50 @@ int launch_root_tiled(const void* X, int dtype, int64_t nl, int64_t nr, const fl
 
 size_t root_pass_scratch_floats(int64_t nl, int64_t nr, int rl, int rr) {
   return std::max(root_scratch_floats(nl, nr, rl, rr), root_stream_scratch_floats(nl, rl, rr));
+}
+
+// dst[row][d0 + c] = src[row][c0 + c], c < nc (column blocks of row-major matrices).
+__global__ void k_copy_cols(const float* __restrict__ src, int64_t rows, int lds, int c0, int nc,
+                            float* __restrict__ dst, int ldd, int d0) {
+  const int64_t tot = rows * nc;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e / nc;
+    const int c = (int)(e % nc);
+    dst[r * ldd + d0 + c] = src[r * lds + c0 + c];
+  }
+}
+
+static unsigned copy_grid(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+static size_t pad4(size_t n) { return (n + 3) & ~(size_t)3; }
+
+size_t root_any_scratch_floats(int64_t nl, int64_t nr, int rl, int rr) {
+  if (rr <= RT_KMAX) return root_pass_scratch_floats(nl, nr, rl, rr);
+  return pad4((size_t)nr * RT_KMAX) + pad4((size_t)rl * RT_KMAX) + root_pass_scratch_floats(nl, nr, rl, RT_KMAX);
+}
+
+int launch_root_any(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur,
+                    int rr, float* BR, float* scratch, int* status, cudaStream_t st) {
+  if (rr <= RT_KMAX) return launch_root(X, dtype, nl, nr, Ul, rl, Ur, rr, BR, scratch, status, st);
+  // r_r above the root kernels' register width: one pass over X per chunk of at most
+  // RT_KMAX columns of U_r (chunks of near-equal width), each on the root pass above.
+  float* Urc = scratch;
+  float* BRc = Urc + pad4((size_t)nr * RT_KMAX);
+  float* rs = BRc + pad4((size_t)rl * RT_KMAX);
+  const int nch = (rr + RT_KMAX - 1) / RT_KMAX;
+  int n = 0;
+  for (int ch = 0, k0 = 0; ch < nch; ++ch) {
+    const int kc = (rr - k0) / (nch - ch);
+    k_copy_cols<<<copy_grid(nr * kc), 256, 0, st>>>(Ur, nr, rr, k0, kc, Urc, kc, 0);
+    n += 1 + launch_root(X, dtype, nl, nr, Ul, rl, Urc, kc, BRc, rs, status, st);
+    k_copy_cols<<<copy_grid((int64_t)rl * kc), 256, 0, st>>>(BRc, rl, kc, 0, kc, BR, rr, k0);
+    ++n;
+    k0 += kc;
+  }
+  return n;
 }
 
 int launch_root(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur, int rr,

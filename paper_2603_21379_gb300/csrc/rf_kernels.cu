@@ -640,30 +640,87 @@ __global__ void __launch_bounds__(QR_THREADS) k_qr1(const RFProb* __restrict__ P
   }
 }
 
-// S5 level 2 (tall Z): QR of the stacked R_b, (nrb c) x c; Q2 with diag(R) > 0.
+// TSQR tree of a tall Z: level l stacks the R factors entering it (lev_n[l] of
+// them, c x c each; level 0 takes the row blocks' R_b) in groups of `fan`.  Level
+// l's R inputs and Q member slices:
+__device__ __forceinline__ size_t ts_level_off(const RFProb& q, int l) {
+  size_t o = 0;
+  for (int j = 1; j < l; ++j) o += (size_t)q.lev_n[j];
+  return o * q.c * q.c;
+}
+__device__ __forceinline__ const float* ts_rin(const RFProb& q, int l) {
+  return l == 0 ? q.Rb : q.tsR + ts_level_off(q, l);
+}
+__device__ __forceinline__ float* ts_q(const RFProb& q, int l) { return l == 0 ? q.Q2 : q.tsQ + ts_level_off(q, l); }
+
+// S5, level `lev` of the TSQR tree: QR of one group's stacked R factors, (cnt c) x c.
+// Below the top its R goes to the next level's inputs (signs as they come, matching
+// its Q); at the top Q has diag(R) > 0, which fixes the overall factor.
 __global__ void __launch_bounds__(QR_THREADS) k_qr2(const RFProb* __restrict__ P,
-                                             const int64_t* __restrict__ pre, int np) {
+                                             const int64_t* __restrict__ pre, int np, int lev) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int p = find_prob(pre, np, blockIdx.x);
   const RFProb& q = P[p];
+  const int g = (int)((int64_t)blockIdx.x - pre[p]);
   const int c = q.c;
-  const int m = q.nrb * c;
+  const int b0 = g * q.fan;
+  const int cnt = min(q.fan, q.lev_n[lev] - b0);
+  const int m = cnt * c;
   const int ld = odd_ld(m);
+  const bool top = (lev == q.nlev - 1);
   float* A = reinterpret_cast<float*>(smem_raw);
   float* Qm = A + (size_t)ld * c;
   float* tau = Qm + (size_t)ld * c;
   float* rdiag = tau + CMAX;
   float* red = rdiag + CMAX;
+  const float* Rin = ts_rin(q, lev) + (size_t)b0 * c * c;
   for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
     const int i = e / c, j = e % c;
-    A[(size_t)j * ld + i] = q.Rb[e];
+    A[(size_t)j * ld + i] = Rin[e];
   }
   __syncthreads();
   qr_factor<QR_JPW, true, true>(A, ld, m, c, tau, rdiag, red + 32);
-  qr_form_q<QR_JPW, true>(A, Qm, ld, m, c, tau, rdiag, true);
+  if (!top) {
+    float* Rout = const_cast<float*>(ts_rin(q, lev + 1)) + (size_t)g * c * c;
+    for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+      const int k = e / c, j = e % c;
+      float v = 0.f;
+      if (j >= k) v = (j == k) ? rdiag[k] : A[(size_t)j * ld + k];
+      Rout[e] = v;
+    }
+  }
+  qr_form_q<QR_JPW, true>(A, Qm, ld, m, c, tau, rdiag, top);
+  float* Qout = ts_q(q, lev) + (size_t)b0 * c * c;
   for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
     const int i = e / c, j = e % c;
-    q.Q2[e] = Qm[(size_t)j * ld + i];
+    Qout[e] = Qm[(size_t)j * ld + i];
+  }
+}
+
+// S5, combine pass t of the TSQR tree (top-down): at level l = nlev - 2 - t, member
+// b's Q slice times its group's slice one level up (already combined), in place,
+// so that level 0 ends with the slices of the whole tree's Q.
+// Static smem: two c x c slices.
+__global__ void __launch_bounds__(256) k_qrc(const RFProb* __restrict__ P, const int64_t* __restrict__ pre,
+                                             int np, int t) {
+  __shared__ float Sb[CMAX * CMAX], Sg[CMAX * CMAX];
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int b = (int)((int64_t)blockIdx.x - pre[p]);
+  const int c = q.c;
+  const int l = q.nlev - 2 - t;
+  float* Qb = ts_q(q, l) + (size_t)b * c * c;
+  const float* Qg = ts_q(q, l + 1) + (size_t)(b / q.fan) * c * c;
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    Sb[e] = Qb[e];
+    Sg[e] = Qg[e];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    float acc = 0.f;
+    for (int k = 0; k < c; ++k) acc = fmaf(Sb[i * c + k], Sg[k * c + j], acc);
+    Qb[e] = acc;
   }
 }
 
@@ -890,6 +947,47 @@ __global__ void __launch_bounds__(QR_THREADS) k_bt_qr(const RFProb* __restrict__
   }
 }
 
+// S6, many sample chunks: level `lev` of an R tree over the chunk factors R_c.  A
+// group of up to wfan stacked c x c factors is replaced by the R of its QR.  Only R
+// is kept: the W-step needs the left singular vectors of R^T, which an orthogonal
+// factor applied to R from the left leaves unchanged.
+// Dynamic smem: A[ld*c] | tau | rdiag | red | vbuf[3072]
+__device__ __forceinline__ size_t wt_off(const RFProb& q, int l) {
+  size_t o = 0;
+  for (int j = 1; j < l; ++j) o += (size_t)q.wn[j];
+  return o * q.c * q.c;
+}
+__global__ void __launch_bounds__(QR_THREADS) k_wtree(const RFProb* __restrict__ P,
+                                               const int64_t* __restrict__ pre, int np, int lev) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int g = (int)((int64_t)blockIdx.x - pre[p]);
+  const int c = q.c;
+  const int b0 = g * q.wfan;
+  const int cnt = min(q.wfan, q.wn[lev] - b0);
+  const int m = cnt * c;
+  const int ld = odd_ld(m);
+  float* A = reinterpret_cast<float*>(smem_raw);
+  float* tau = A + (size_t)ld * c;
+  float* rdiag = tau + CMAX;
+  float* red = rdiag + CMAX;
+  const float* Rin = (lev == 0 ? q.Rc : q.wsR + wt_off(q, lev)) + (size_t)b0 * c * c;
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    A[(size_t)j * ld + i] = Rin[e];
+  }
+  __syncthreads();
+  qr_factor<QR_JPW, true, true>(A, ld, m, c, tau, rdiag, red + 32);
+  float* Rout = q.wsR + wt_off(q, lev + 1) + (size_t)g * c * c;
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    const int k = e / c, j = e % c;
+    float v = 0.f;
+    if (j >= k) v = (j == k) ? rdiag[k] : A[(size_t)j * ld + k];
+    Rout[e] = v;
+  }
+}
+
 // S6: R of the stacked chunk factors, then one-sided Jacobi (Hestenes) on the
 // columns of R^T: R^T V = W Sigma, W = left singular vectors of B.  Columns
 // are processed in round-robin order, one 16-lane group per pair, until a sweep
@@ -905,7 +1003,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_wsvd(const RFProb* __restrict__ 
   const int p = find_prob(pre, np, blockIdx.x);
   const RFProb& q = P[p];
   const int c = q.c;
-  const int m = q.nsc * c;
+  const int m = q.nrw * c;
   const int ld = odd_ld(m);
   float* A = reinterpret_cast<float*>(smem_raw);
   float* tau = A + (size_t)ld * c;
@@ -917,7 +1015,7 @@ __global__ void __launch_bounds__(QR_THREADS) k_wsvd(const RFProb* __restrict__ 
   constexpr int LDT = WS_LDT;
   for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
     const int i = e / c, j = e % c;
-    A[(size_t)j * ld + i] = q.Rc[e];
+    A[(size_t)j * ld + i] = q.Rw[e];
   }
   if (threadIdx.x < q.r) q.keys[threadIdx.x] = 0ull;
   if (threadIdx.x < 2) flag[threadIdx.x] = 0;
@@ -1260,6 +1358,7 @@ static size_t smem_btf() {
 // k_bt_qr factors one whole chunk: up to (BT_SC | 1) x CMAX floats, then the register
 // Householder's two 32 x MR vectors (MR = 16 rows per lane covers chunks up to 512).
 static_assert(BT_SC <= 512, "B^T chunk must stay within the register Householder");
+static size_t smem_wt() { return (size_t)(QR2_MAXF + 2 * CMAX + 32 + 3072) * 4 + 64; }
 static size_t smem_btq() { return (size_t)((BT_SC | 1) * CMAX + 2 * CMAX + 32 + 1024) * 4 + 64; }
 static size_t smem_wsvd() {
   return (size_t)(WS_MAXF + 2 * CMAX + 32 + CMAX * WS_LDT + CMAX + 8 + 1024) * 4 + 64;
@@ -1280,6 +1379,7 @@ cudaError_t rf_init_attributes() {
   RT_ATTR(k_qr3, smem_qr3());
   RT_ATTR(k_bt_partial, smem_btp());
   RT_ATTR(k_bt_qr, smem_btq());
+  RT_ATTR(k_wtree, smem_wt());
   RT_ATTR(k_bt_fused, smem_btf());
   RT_ATTR(k_wsvd, smem_wsvd());
   RT_ATTR(k_qw, smem_qw());
@@ -1311,9 +1411,20 @@ int launch_rf_head(const RFGroup& g, cudaStream_t st, int* status) {
   k_qr1<<<grid_of(g.total[STG_QR1]), QR_THREADS, smem_qr(), st>>>(g.probs, pre + STG_QR1 * stride, np);
   ++n;
   if (g.total[STG_QR2] > 0) {
-    k_qr2<<<grid_of(g.total[STG_QR2]), QR_THREADS, smem_qr2(), st>>>(g.probs, pre + STG_QR2 * stride, np);
+    for (int j = 0; j < g.lmax; ++j) {          // the tree's levels, bottom-up
+      const int sj = stg_qr2(j);
+      if (g.total[sj] == 0) continue;
+      k_qr2<<<grid_of(g.total[sj]), QR_THREADS, smem_qr2(), st>>>(g.probs, pre + sj * stride, np, j);
+      ++n;
+    }
+    for (int t = 0; t + 1 < g.lmax; ++t) {      // Q slices combined top-down
+      const int stc = stg_qrc(t);
+      if (g.total[stc] == 0) continue;
+      k_qrc<<<grid_of(g.total[stc]), 256, 0, st>>>(g.probs, pre + stc * stride, np, t);
+      ++n;
+    }
     k_qr3<<<grid_of(g.total[STG_QR3]), 256, smem_qr3(), st>>>(g.probs, pre + STG_QR3 * stride, np);
-    n += 2;
+    ++n;
   }
   if (g.total[STG_BTP] == g.total[STG_BTQ]) {   // every problem reduces B^T over one row block
     k_bt_fused<<<grid_of(g.total[STG_BTQ]), QR_THREADS, smem_btf(), st>>>(g.probs, pre + STG_BTQ * stride, np);
@@ -1322,6 +1433,12 @@ int launch_rf_head(const RFGroup& g, cudaStream_t st, int* status) {
     k_bt_partial<<<grid_of(g.total[STG_BTP]), 256, smem_btp(), st>>>(g.probs, pre + STG_BTP * stride, np);
     k_bt_qr<<<grid_of(g.total[STG_BTQ]), QR_THREADS, smem_btq(), st>>>(g.probs, pre + STG_BTQ * stride, np);
     n += 2;
+  }
+  for (int j = 0; j < g.wmax; ++j) {            // R tree over many chunk factors
+    const int sj = stg_wt(j);
+    if (g.total[sj] == 0) continue;
+    k_wtree<<<grid_of(g.total[sj]), QR_THREADS, smem_wt(), st>>>(g.probs, pre + sj * stride, np, j);
+    ++n;
   }
   return n;
 }

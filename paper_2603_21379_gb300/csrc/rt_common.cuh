@@ -15,6 +15,7 @@
 namespace rt {
 
 constexpr int MAXD = 16;
+constexpr int TS_MAXLEV = 6;   // stack levels of the TSQR tree of Z above its row blocks
 
 // device status word codes (first error wins)
 enum : int { ST_OK = 0, ST_TIMEOUT = 1, ST_DEVICE = 2, ST_NUMERIC = 3 };
@@ -55,11 +56,22 @@ struct RFProb {
   int32_t nbi;             // row blocks of the reduction B^T = Y^T Q
   float* Q;                // [nS][c]  orthonormal factor of Z
   float* Rb;               // [nrb][c][c] TSQR first-level R factors
-  float* Q2;               // [nrb*c][c] TSQR second-level Q
+  float* Q2;               // [nrb*c][c] TSQR level-0 Q (member slices; combined in place)
+  int32_t nlev;            // stack levels of the TSQR tree (0: one row block)
+  int32_t fan;             // R factors stacked per group at every level
+  int32_t lev_n[TS_MAXLEV + 1];  // factors entering level l (lev_n[0] = nrb); lev_n[nlev] = 1
+  float* tsR;              // R of the groups of levels 0 .. nlev-2 (inputs of levels 1 ..)
+  float* tsQ;              // Q member slices of levels 1 .. nlev-1
   float* Bp;               // [nbi][s][c] partial B^T
   float* Rc;               // [nsc][c][c] R factors of the sample chunks of B^T
   int32_t nsc;             // number of sample chunks of B^T
   int32_t scrows;          // rows (samples) per chunk of B^T
+  int32_t wlev;            // levels of the R tree over the chunk factors before the W-step
+  int32_t wfan;            // chunk factors stacked per group in that tree
+  int32_t wn[TS_MAXLEV + 1];  // factors entering level l (wn[0] = nsc)
+  float* wsR;              // R of the tree's groups (levels 1 .. wlev)
+  const float* Rw;         // the stack the W-step factors: Rc, or the tree's last level
+  int32_t nrw;             // number of c x c factors in it
   float* W;                // [c][c]   left singular vectors of R^T, sorted (cols)
   float* Wsg;              // [c][r]   W(:, :r) with the sign rule's column signs (U = Q Wsg)
   float* sigma;            // [c]      singular values of Q^T Y, descending

@@ -27,13 +27,25 @@ enum Stage : int {
   STG_SAMPLE = 0, STG_GS, STG_QR1, STG_QR2, STG_QR3, STG_BTP, STG_BTQ, STG_WSVD, STG_QW, STG_FLIP,
   STG_ZSUM, STG_QWF, STG_COUNT
 };
+// Stages of the TSQR tree beyond its first level: the QR of level j >= 1 and the
+// combine passes t = 0 .. (top-down); their prefix rows follow the fixed ones and
+// are uploaded only for groups with a problem of two or more levels (or an R tree
+// in front of its W-step).
+// The levels j of the R tree in front of the W-step follow them.
+constexpr int STG_ALL = STG_COUNT + 2 * (TS_MAXLEV - 1) + TS_MAXLEV;
+inline int stg_qr2(int j) { return j == 0 ? (int)STG_QR2 : STG_COUNT + j - 1; }
+inline int stg_qrc(int t) { return STG_COUNT + TS_MAXLEV - 1 + t; }
+inline int stg_wt(int j) { return STG_COUNT + 2 * (TS_MAXLEV - 1) + j; }
 
 // Device-side view of a planned group of range-finder problems.
 struct RFGroup {
   const RFProb* probs;   // device table [nprob]
-  const int64_t* pre;    // device prefixes [STG_COUNT][nprob + 1]
+  const int64_t* pre;    // device prefixes [nst][nprob + 1]
   int nprob;
-  int64_t total[STG_COUNT];  // host copy of the unit totals per stage
+  int nst;               // prefix rows: STG_COUNT, or STG_ALL when lmax > 1 or wmax > 0
+  int lmax;              // largest TSQR tree depth of the group's problems
+  int wmax;              // largest W-step R tree depth
+  int64_t total[STG_ALL];  // host copy of the unit totals per stage (0 beyond nst)
 };
 
 // Enqueue every stage of the range finder for the group (Alg. 1 loop body /
@@ -113,14 +125,24 @@ struct TransferJob {     // B_S(i, j, k) = sum_{a,b} U_S[a n_r + b][i] U_l[a][j]
 };
 int64_t transfer_ctas(int64_t nl);               // CTAs of one job
 size_t transfer_part_floats(int64_t total_ctas); // partial-sum scratch
-// ranks up to 12; part holds transfer_part_floats(total CTAs of all jobs)
+// ranks up to TRANSFER_RMAX; part holds transfer_part_floats(total CTAs of all jobs)
+constexpr int TRANSFER_RMAX = 12;
 int launch_transfer(const TransferJob* jobs_dev, const TransferJob* jobs_host, int njobs, float* part,
                     cudaStream_t st);
+// One job with any ranks up to 64 (host-side job; cta0 unused): two mode contractions
+// and a permutation; scratch holds transfer_general_floats() floats.
+size_t transfer_general_floats(int64_t nl, int rS, int rl, int rr);
+int launch_transfer_general(const TransferJob& jb, float* scratch, cudaStream_t st);
 // B_R(0, j, k) = sum_{a,b} X[a nr + b] Ul[a][j] Ur[b][k]
 // Root pass B_R = U_l^T X^(R_l) U_r: the streaming (TMA) kernel for float32 X when the
 // shape allows, else the tiled kernel; scratch holds root_pass_scratch_floats().
 int launch_root(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur, int rr,
                 float* BR, float* scratch, int* status, cudaStream_t st);
+// Any r_r up to 64: above the root kernels' width, one root pass per chunk of U_r's
+// columns; scratch holds root_any_scratch_floats().
+size_t root_any_scratch_floats(int64_t nl, int64_t nr, int rl, int rr);
+int launch_root_any(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur,
+                    int rr, float* BR, float* scratch, int* status, cudaStream_t st);
 // The tiled kernel alone (no waits, no status word); scratch of root_scratch_floats().
 int launch_root_tiled(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl,
                       const float* Ur, int rr, float* BR, float* scratch, cudaStream_t st);

@@ -10,7 +10,7 @@ torch = pytest.importorskip("torch")
 
 import synth  # noqa: E402
 from oracle import brute, htucker, tucker  # noqa: E402
-from parity_util import RELERR_TOL, U_TOL, clusters, compare_factor, orthonormality, to_np  # noqa: E402
+from parity_util import GAP_MIN, RELERR_TOL, U_TOL, clusters, compare_factor, orthonormality, to_np  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -26,8 +26,8 @@ def rt():
     return m
 
 
-def _strict_cols(sigma, r):
-    cl, tail_ok = clusters(sigma, r)
+def _strict_cols(sigma, r, gap_min=GAP_MIN):
+    cl, tail_ok = clusters(sigma, r, gap_min)
     out = []
     for ci, c in enumerate(cl):
         if ci == len(cl) - 1 and not tail_ok:
@@ -37,7 +37,7 @@ def _strict_cols(sigma, r):
     return out
 
 
-def _check_nodes(ref, U_leaf, B, Un, root_ref=None):
+def _check_nodes(ref, U_leaf, B, Un, root_ref=None, gap_min=GAP_MIN):
     """Node bases, leaf factors and transfer tensors of a GPU result against an
     oracle result ``ref``; the root transfer tensor against ``root_ref`` (default
     ref["B"][0])."""
@@ -46,11 +46,11 @@ def _check_nodes(ref, U_leaf, B, Un, root_ref=None):
     for nd in tree[1:]:
         sig = ref["info"][nd.id]["sigma"]
         Ug = to_np(Un[nd.id])
-        s, dev, _ = compare_factor(Ug, ref["US"][nd.id], sig)
+        s, dev, _ = compare_factor(Ug, ref["US"][nd.id], sig, gap_min=gap_min)
         assert dev <= U_TOL, (nd.id, dev)
         assert orthonormality(Ug) < 1e-5
         signs[nd.id] = s
-        strict[nd.id] = _strict_cols(sig, ref["ranks"][nd.id])
+        strict[nd.id] = _strict_cols(sig, ref["ranks"][nd.id], gap_min)
     for k, nd in enumerate(sorted((n for n in tree if n.is_leaf), key=lambda n: n.a)):
         assert np.array_equal(to_np(U_leaf[k]), to_np(Un[nd.id]))
     for nd in tree:
@@ -68,13 +68,13 @@ def _check_nodes(ref, U_leaf, B, Un, root_ref=None):
             assert np.abs(sub_g - sub_r).max() <= 1e-4 * max(1.0, np.abs(Br).max()), nd.id
 
 
-def _compare_ht(rt, X, rank, p, w=None, seed=0, x_oracle=None):
+def _compare_ht(rt, X, rank, p, w=None, seed=0, x_oracle=None, gap_min=GAP_MIN):
     Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
     U_leaf, B, Un = rt.rhtucker_decompose(Xd, rank, p, w=w, seed=seed, return_nodes=True)
     torch.cuda.synchronize()
     Xo = np.asarray(X if x_oracle is None else x_oracle, dtype=np.float64)
     ref = htucker.sub_r_rtl_ht(Xo, rank, p, w=w, seed=seed)
-    _check_nodes(ref, U_leaf, B, Un)
+    _check_nodes(ref, U_leaf, B, Un, gap_min=gap_min)
     eg = rt.rhtucker_relerr(Xd, U_leaf, B, rank)
     er = tucker.relerr(Xo, htucker.reconstruct(ref["U"], ref["B"], ref["tree"], Xo.shape))
     assert abs(eg - er) <= RELERR_TOL, (eg, er)
@@ -119,6 +119,46 @@ def test_exact_hierarchical_rank_recovery(rt):
     X = htucker.reconstruct(U, B, tree, shape).astype(np.float32)
     eg, er = _compare_ht(rt, X, 2, 2, seed=7)
     assert eg < 1e-5
+
+
+def test_wide_ranks(rt):
+    # hierarchical ranks 54 at the two inner nodes (r + p = 64, the largest supported
+    # width; 1600-row node unfoldings: a two-level TSQR tree of Z, and B^T chunks
+    # factored from row-block partials) and 30 at the leaves of a 40^4 tensor built in the format (Gaussian
+    # transfer tensors, Haar leaves) plus 1e-4 noise: 54 x 30 x 30 transfer tensors and
+    # a 54 x 54 root.  Sampled singular values ~1e-3 of sigma_1 apart: columns closer
+    # than 5e-3 are compared as subspaces.
+    rs = np.random.default_rng(34)
+    shape, ranks, p = (40, 40, 40, 40), [1, 54, 54, 30, 30, 30, 30], 10
+    tree = htucker.balanced_tree(4)
+    U = [synth.haar(n, 30, rs) for n in shape]
+    B = [None] * len(tree)
+    for nd in tree:
+        if not nd.is_leaf:
+            B[nd.id] = rs.standard_normal((1 if nd.id == 0 else 54, ranks[nd.left], ranks[nd.right]))
+    X = htucker.reconstruct(U, B, tree, shape)
+    X = (X / np.abs(X).max() + 1e-4 * rs.standard_normal(shape)).astype(np.float32)
+    eg, er = _compare_ht(rt, X, ranks, p, seed=5, gap_min=5e-3)
+    assert er < 5e-3
+
+
+def test_mixed_transfer_forms_and_chunked_root(rt):
+    # node {0,1} rank 8 (grouped transfer kernel) beside node {2,3} rank 20 with rank-14
+    # children (general form), and a root right-child rank of 20: two chunks of 10
+    # columns of U_r, each a streaming root pass (n_r = 1024).  The format is built with
+    # these ranks, so node {2,3} has 8 determined directions (the root's two children
+    # share one rank); its other 12 are noise and not compared column by column.
+    rs = np.random.default_rng(55)
+    shape, ranks, p = (8, 9, 32, 32), [1, 8, 20, 3, 3, 14, 14], 3
+    tree = htucker.balanced_tree(4)
+    U = [synth.haar(n, r, rs) for n, r in zip(shape, ranks[3:])]
+    B = [None] * len(tree)
+    for nd in tree:
+        if not nd.is_leaf:
+            B[nd.id] = rs.standard_normal((1 if nd.id == 0 else ranks[nd.id], ranks[nd.left], ranks[nd.right]))
+    X = htucker.reconstruct(U, B, tree, shape)
+    X = (X / np.abs(X).max() + 1e-4 * rs.standard_normal(shape)).astype(np.float32)
+    _compare_ht(rt, X, ranks, p, seed=5, gap_min=5e-3)
 
 
 def test_full_sampling_matches_rtl_ht(rt):

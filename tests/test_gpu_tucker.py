@@ -106,20 +106,25 @@ def test_matrix_d2(rt):
     _run_and_compare(rt, X, (10, 10), 5, seed=4)
 
 
-def test_widest_sketch_on_tall_unfoldings(rt):
-    # r + p = 64, the largest supported width, on a mode whose unfolding (48 x 48 = 2304
-    # rows) spans several row blocks of B^T = Y^T Q, so every chunk of 256 samples is
-    # factored from the reduced row-block partials.  The 54 sampled singular values sit
-    # ~1e-3 of sigma_1 apart, so columns closer than 5e-3 are compared as subspaces and
-    # the core is checked as the projection of X on the returned factors.
-    X = synth.tucker_tensor((70, 48, 48), (54, 8, 8), noise=1e-4, data_seed=10)
+@pytest.mark.parametrize("shape,data_seed,s", [((70, 48, 48), 10, None), ((20000, 18, 18), 42, None),
+                                                ((120, 90, 90), 65, [8000, 900, 900])])
+def test_widest_sketch(rt, shape, data_seed, s):
+    # r + p = 64, the largest supported width.  70 rows: one QR block, B^T formed and
+    # factored in one kernel.  20000 rows: 125 row blocks of 160, so the TSQR of Z
+    # runs a three-level tree (fan-in 5) with two combine passes, and B^T is reduced
+    # over 40 row blocks before each 256-sample chunk is factored.  8000 samples: 32
+    # chunk factors, more than the W-step stacks (5), reduced by a two-level R tree
+    # (32 -> 7 -> 2) first.  The 54 sampled singular values sit ~1e-3 of sigma_1
+    # apart, so columns closer than 5e-3 are compared as subspaces and the core is
+    # checked as the projection of X on the returned factors.
+    X = synth.tucker_tensor(shape, (54, 8, 8), noise=1e-4, data_seed=data_seed)
     r, p, seed = [54, 8, 8], 10, 12
     Xd = torch.from_numpy(X).cuda()
-    G, U = rt.rtucker_decompose(Xd, r, p, seed=seed)
-    _, sig = rt.rtucker_factors(Xd, r, p, seed=seed, with_sigma=True)
+    G, U = rt.rtucker_decompose(Xd, r, p, s=s, seed=seed)
+    _, sig = rt.rtucker_factors(Xd, r, p, s=s, seed=seed, with_sigma=True)
     rt.sync()
     Xo = X.astype(np.float64)
-    ref = tucker.sub_r_hosvd(Xo, r, p, seed=seed, with_core=False)
+    ref = tucker.sub_r_hosvd(Xo, r, p, s=s, seed=seed, with_core=False)
     Un = [to_np(u) for u in U]
     for k in range(3):
         s_ref = ref["modes"][k]["sigma"]
