@@ -67,8 +67,19 @@ typedef struct rt_handle_s* rt_handle;
 
 typedef struct {
   int32_t prec;        /* rt_prec                                              */
-  int32_t use_graph;   /* must be 0: CUDA-graph replay is not provided yet
-                          (nonzero returns RT_ENOTSUP)                           */
+  int32_t use_graph;   /* 1: run the call's kernel sequence as a CUDA graph.
+                          The sequence is captured on a stream of the handle's
+                          own (so the caller's stream may be the legacy default
+                          stream), instantiated and launched on the handle's
+                          stream; later calls whose launch-shaping arguments
+                          match (pointers, shapes, ranks, p, sample counts,
+                          workspace) replay it.  The problem tables, seeds
+                          included, are uploaded by every call.  Up to 4
+                          sequences are cached per handle; stage timing
+                          (rt_set_timing) turns capture off.  rtucker_decompose,
+                          rtucker_factors, rtucker_decompose_batched,
+                          rhtucker_decompose.  0 (default): direct launches.
+                          Other values: RT_EINVAL.                              */
   int32_t overlap;     /* rtucker_decompose only: 1 runs the pass over X on the
                           QR factors Q of the last two modes (U_k = Q_k W_k) on
                           the tensor cores while the SVD / W / U part of their

@@ -266,16 +266,17 @@ def rtucker_factors(X, r, p, s=None, seed=0, with_sigma=False):
 _PREC = {"fp32": 0, "bf16": 1}
 
 
-def _opts(prec, overlap=False):
-    """rt_options for a precision form (and the overlapped core schedule), or None
-    (defaults)."""
+def _opts(prec, overlap=False, graph=False):
+    """rt_options for a precision form (the overlapped core schedule, CUDA-graph
+    replay), or None (defaults)."""
     if prec not in _PREC:
         raise ValueError("prec must be 'fp32' or 'bf16'")
-    if prec == "fp32" and not overlap:
+    if prec == "fp32" and not overlap and not graph:
         return None
     o = _Options()
     o.prec = _PREC[prec]
     o.overlap = 1 if overlap else 0
+    o.use_graph = 1 if graph else 0
     return ctypes.byref(o)
 
 
@@ -296,11 +297,13 @@ def rtucker_core(X, U, prec="fp32"):
     return G
 
 
-def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32", overlap=False):
+def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32", overlap=False, graph=False):
     """S1-S7: Sub-R-HOSVD; returns (G, [U_k]).  ``out`` = (Uflat, G) reuses buffers;
     ``prec`` "fp32" (default) or "bf16" (the BF16 compute form of the core pass);
     ``overlap`` runs the pass over X on the QR factors beside the SVD part of the
-    range finder (see rt_options.overlap)."""
+    range finder (see rt_options.overlap); ``graph`` replays the kernel sequence as
+    a CUDA graph for repeated calls with the same buffers and shapes
+    (rt_options.use_graph; pass ``out`` so that the output pointers repeat)."""
     lib = load_library()
     dt, d, n = _tensor_args(X)
     r = _as_list(r, d)
@@ -312,7 +315,7 @@ def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32", overlap=Fa
     h = _handle(X.device.index)
     sp = _i64(_as_list(s, d)) if s is not None else None
     _check(h, lib.rtucker_decompose(h, _ptr(X), dt, d, _i64(n), _i32(r), int(p), sp, ctypes.c_uint64(seed),
-                                    _opts(prec, overlap), _ptr(U), _ptr(G)))
+                                    _opts(prec, overlap, graph), _ptr(U), _ptr(G)))
     return G, _split(U, n, r)
 
 
@@ -340,7 +343,7 @@ def rtucker_decompose_host(X, r, p, s=None, seed=0, out=None, prec="fp32"):
 _in_flight = {}
 
 
-def rtucker_decompose_host_async(X, r, p, s=None, seed=0, out=None, prec="fp32"):
+def rtucker_decompose_host_async(X, r, p, s=None, seed=0, out=None, prec="fp32", graph=False):
     """Pipelined Sub-R-HOSVD of a HOST tensor: enqueues the copy of X into one of
     two device slots, the decomposition and the copies of U and G back to host
     tensors, and returns (G, [U_k]) before they are written.  The copy of the
@@ -360,7 +363,7 @@ def rtucker_decompose_host_async(X, r, p, s=None, seed=0, out=None, prec="fp32")
     h = _handle()
     sp = _i64(_as_list(s, d)) if s is not None else None
     _check(h, lib.rtucker_decompose_host_async(h, _ptr(X), _DT[X.dtype], d, _i64(n), _i32(r), int(p), sp,
-                                               ctypes.c_uint64(seed), _opts(prec), _ptr(U), _ptr(G)))
+                                               ctypes.c_uint64(seed), _opts(prec, graph=graph), _ptr(U), _ptr(G)))
     _in_flight.setdefault(h.value, []).append((X, U, G))
     return G, _split(U, n, r)
 
@@ -425,7 +428,7 @@ class BatchedDecomposition:
     of all tensors live in two flat float32 buffers (``U_flat``, ``G_flat``);
     ``results()`` gives the per-tensor (G, [U_k]) views."""
 
-    def __init__(self, Xs, ranks, p, seeds, s=None, prec="fp32"):
+    def __init__(self, Xs, ranks, p, seeds, s=None, prec="fp32", graph=False):
         self.lib = load_library()
         T = len(Xs)
         dts = {X.dtype for X in Xs}
@@ -471,7 +474,7 @@ class BatchedDecomposition:
         self.U_arr = (ctypes.c_void_p * T)(*[ub + 4 * uoff[t] for t in range(T)])
         self.G_arr = (ctypes.c_void_p * T)(*[gb + 4 * goff[t] for t in range(T)])
         self.seed_arr = (ctypes.c_uint64 * T)(*[int(v) for v in seeds])
-        self._opt_keep = _opts(prec)
+        self._opt_keep = _opts(prec, graph=graph)
         self.h = _handle(dev.index)
 
     def run(self):
@@ -492,7 +495,8 @@ class BatchedDecomposition:
 
 def rtucker_decompose_batched(Xs, ranks, p, seeds, s=None, prec="fp32"):
     """Batched Sub-R-HOSVD: one grouped launch per stage for all (tensor, mode)
-    problems.  Returns a list of (G, [U_k])."""
+    problems.  Returns a list of (G, [U_k]).  For repeated batches (and CUDA-graph
+    replay, ``graph=True``) keep a ``BatchedDecomposition``."""
     return BatchedDecomposition(Xs, ranks, p, seeds, s=s, prec=prec).run().results()
 
 
@@ -533,9 +537,12 @@ def _ht_ranks(d, rank):
     return rk
 
 
-def rhtucker_decompose(X, rank, p, w=None, seed=0, return_nodes=False):
+def rhtucker_decompose(X, rank, p, w=None, seed=0, return_nodes=False, graph=False, out=None):
     """Sub-R-RtL-HT on the balanced tree.  Returns (U_leaf list, B dict node->
-    transfer tensor) and, with ``return_nodes``, the node bases U_S."""
+    transfer tensor) and, with ``return_nodes``, the node bases U_S.  ``graph``
+    replays the kernel sequence as a CUDA graph for repeated calls with the same
+    buffers and shapes (rt_options.use_graph); ``out`` = (U_leaf flat, B flat[,
+    U_nodes flat]) reuses output buffers so that their pointers repeat."""
     lib = load_library()
     dt, d, n = _tensor_args(X)
     tree = ht_tree(d)
@@ -543,17 +550,22 @@ def rhtucker_decompose(X, rank, p, w=None, seed=0, return_nodes=False):
     nrows = [_prod(n[a:b + 1]) for (a, b, _, _, _) in tree]
     leaves = sorted((i for i, t in enumerate(tree) if t[0] == t[1]), key=lambda i: tree[i][0])
     internal = [i for i, t in enumerate(tree) if t[0] != t[1]]
-    Ul = torch.empty(sum(n[tree[i][0]] * rk[i] for i in leaves), dtype=torch.float32, device=X.device)
     Bsz = [rk[i] * rk[tree[i][2]] * rk[tree[i][3]] for i in internal]
-    B = torch.empty(sum(Bsz), dtype=torch.float32, device=X.device)
     Un = None
-    if return_nodes:
-        Un = torch.empty(sum(nrows[i] * rk[i] for i in range(1, len(tree))), dtype=torch.float32,
-                         device=X.device)
+    if out is not None:
+        Ul, B = out[0], out[1]
+        if return_nodes:
+            Un = out[2]
+    else:
+        Ul = torch.empty(sum(n[tree[i][0]] * rk[i] for i in leaves), dtype=torch.float32, device=X.device)
+        B = torch.empty(sum(Bsz), dtype=torch.float32, device=X.device)
+        if return_nodes:
+            Un = torch.empty(sum(nrows[i] * rk[i] for i in range(1, len(tree))), dtype=torch.float32,
+                             device=X.device)
     h = _handle(X.device.index)
     wp = _i64(_as_list(w, len(tree))) if w is not None else None
-    _check(h, lib.rhtucker_decompose(h, _ptr(X), dt, d, _i64(n), _i32(rk), int(p), wp, ctypes.c_uint64(seed), None,
-                                     _ptr(Ul), _ptr(B), _ptr(Un)))
+    _check(h, lib.rhtucker_decompose(h, _ptr(X), dt, d, _i64(n), _i32(rk), int(p), wp, ctypes.c_uint64(seed),
+                                     _opts("fp32", graph=graph), _ptr(Ul), _ptr(B), _ptr(Un)))
     U_leaf = _split(Ul, [n[tree[i][0]] for i in leaves], [rk[i] for i in leaves])
     Bd, off = {}, 0
     for i, sz in zip(internal, Bsz):

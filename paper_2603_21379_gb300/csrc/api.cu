@@ -66,6 +66,24 @@ __global__ void __launch_bounds__(256) k_stage_copy(const UploadBatch b) {
 
 }  // namespace
 
+// A captured kernel sequence (rt_options.use_graph) and the launch-shaping arguments
+// it was captured for.  Stage-timing intervals recorded during the capture are event
+// record nodes of the graph; each launch points them at fresh events.
+struct TimedNodes {
+  int stage;
+  cudaGraphNode_t na, nb;
+  cudaEvent_t a0, b0;    // the events recorded at capture (owned by the entry)
+};
+struct GraphEntry {
+  std::vector<uint64_t> key;
+  cudaGraph_t graph = nullptr;      // kept: its nodes address the executable's event nodes
+  cudaGraphExec_t exec = nullptr;
+  std::vector<TimedNodes> timed;
+  int launches = 0;
+  uint64_t used = 0;
+};
+constexpr size_t GRAPH_CACHE = 4;   // captured sequences kept per handle (least recently used replaced)
+
 struct rt_handle_s {
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -101,6 +119,11 @@ struct rt_handle_s {
   // second stream for work that overlaps the pass over X, with fork/join events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // CUDA-graph replay: capture stream and cache
+  cudaStream_t gstream = nullptr;
+  bool capturing = false;            // a graph capture is running (stage timing records nodes)
+  std::vector<GraphEntry> graphs;
+  uint64_t graph_tick = 0;
   // stage timing
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;              // free events
@@ -149,15 +172,20 @@ struct StageTimer {
   StageTimer(rt_handle hh, int s, cudaStream_t stream = nullptr) : h(hh), stage(s), st(stream ? stream : hh->stream) {
     if (h->timing) {
       a = pool_event(h);
-      cudaEventRecord(a, st);
+      record(a);
     }
   }
   ~StageTimer() {
     if (a) {
       cudaEvent_t b = pool_event(h);
-      cudaEventRecord(b, st);
+      record(b);
       h->ev_open.push_back({stage, {a, b}});
     }
+  }
+  // under graph capture the record becomes an event-record node of the graph
+  void record(cudaEvent_t e) {
+    if (h->capturing) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
   }
 };
 
@@ -573,7 +601,7 @@ rt_status check_tensor(rt_handle h, const void* X, rt_dtype dtype, int d, const 
 rt_status check_opts(rt_handle h, const rt_options* opt) {
   if (!opt) return RT_OK;
   if (opt->prec != RT_PREC_FP32 && opt->prec != RT_PREC_BF16) return fail(h, RT_EINVAL, "unknown precision");
-  if (opt->use_graph) return fail(h, RT_ENOTSUP, "CUDA-graph replay is not provided");
+  if (opt->use_graph != 0 && opt->use_graph != 1) return fail(h, RT_EINVAL, "use_graph must be 0 or 1");
   for (int i = 0; i < 5; ++i)
     if (opt->reserved[i]) return fail(h, RT_EINVAL, "reserved option fields must be zero");
   return RT_OK;
@@ -810,6 +838,143 @@ rt_status finish(rt_handle h, int launches) {
   return RT_OK;
 }
 
+// Launch-shaping arguments of a call, as words: a captured sequence is replayed only
+// for calls whose words match (pointers, shapes, stage unit totals, workspace base
+// and layout).  Everything else the kernels read (the problem tables: seeds, sample
+// indices' parameters) is uploaded by each call before its sequence runs.
+struct GraphKey {
+  std::vector<uint64_t> w;
+  void add(uint64_t v) { w.push_back(v); }
+  void ptr(const void* p) { w.push_back((uint64_t)(uintptr_t)p); }
+  template <typename T>
+  void arr(const T* a, int n) {
+    w.push_back((uint64_t)n);
+    for (int i = 0; i < n; ++i) w.push_back((uint64_t)a[i]);
+  }
+  void group(const RFGroup& g) {
+    add((uint64_t)g.nprob);
+    add((uint64_t)g.nst);
+    add((uint64_t)g.lmax);
+    add((uint64_t)g.wmax);
+    ptr(g.probs);
+    ptr(g.pre);
+    for (int i = 0; i < STG_ALL; ++i) add((uint64_t)g.total[i]);
+  }
+};
+
+void release_graph(rt_handle h, GraphEntry& ge) {
+  if (ge.exec) cudaGraphExecDestroy(ge.exec);
+  if (ge.graph) cudaGraphDestroy(ge.graph);
+  for (TimedNodes& t : ge.timed) {
+    h->ev_pool.push_back(t.a0);
+    h->ev_pool.push_back(t.b0);
+  }
+  ge = GraphEntry{};
+}
+
+rt_status launch_graph(rt_handle h, GraphEntry& ge) {
+  for (const TimedNodes& t : ge.timed) {
+    cudaEvent_t a = pool_event(h), b = pool_event(h);
+    RT_CUDA(h, cudaGraphExecEventRecordNodeSetEvent(ge.exec, t.na, a));
+    RT_CUDA(h, cudaGraphExecEventRecordNodeSetEvent(ge.exec, t.nb, b));
+    h->ev_open.push_back({t.stage, {a, b}});
+  }
+  RT_CUDA(h, cudaGraphLaunch(ge.exec, h->stream));
+  ge.used = ++h->graph_tick;
+  return RT_OK;
+}
+
+// Runs enqueue(&launches) on the handle's stream, directly or (use_graph) as a CUDA
+// graph: a cached one when the key matches, else captured on a private stream (so
+// that the caller's stream may be the legacy default stream), instantiated and
+// launched on the handle's stream.
+template <class F>
+rt_status run_kernels(rt_handle h, bool use_graph, GraphKey key, int* nl, F&& enqueue) {
+  if (!use_graph) {
+    int n = 0;
+    const rt_status st = enqueue(&n);
+    *nl += n;
+    return st;
+  }
+  key.add(h->timing ? 1 : 0);
+  for (GraphEntry& ge : h->graphs)
+    if (ge.key == key.w) {
+      rt_status st;
+      if ((st = launch_graph(h, ge)) != RT_OK) return st;
+      *nl += ge.launches;
+      return RT_OK;
+    }
+  if (!h->gstream) RT_CUDA(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+  const size_t ev0 = h->ev_open.size();
+  RT_CUDA(h, cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeRelaxed));
+  cudaStream_t user = h->stream;
+  h->stream = h->gstream;
+  h->capturing = true;
+  int n = 0;
+  const rt_status st = enqueue(&n);
+  h->capturing = false;
+  h->stream = user;
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(h->gstream, &g);
+  // the stage intervals opened during the capture belong to the graph
+  GraphEntry ne;
+  for (size_t i = ev0; i < h->ev_open.size(); ++i)
+    ne.timed.push_back({h->ev_open[i].first, nullptr, nullptr, h->ev_open[i].second.first,
+                        h->ev_open[i].second.second});
+  h->ev_open.resize(ev0);
+  ne.graph = g;
+  if (st != RT_OK || ec != cudaSuccess || !g) {
+    release_graph(h, ne);
+    cudaGetLastError();
+    return st != RT_OK ? st : cuda_fail(h, ec != cudaSuccess ? ec : cudaErrorUnknown, "graph capture");
+  }
+  if (!ne.timed.empty()) {
+    size_t cnt = 0;
+    RT_CUDA(h, cudaGraphGetNodes(g, nullptr, &cnt));
+    std::vector<cudaGraphNode_t> nodes(cnt);
+    RT_CUDA(h, cudaGraphGetNodes(g, nodes.data(), &cnt));
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType ty;
+      RT_CUDA(h, cudaGraphNodeGetType(nd, &ty));
+      if (ty != cudaGraphNodeTypeEventRecord) continue;
+      cudaEvent_t ev = nullptr;
+      RT_CUDA(h, cudaGraphEventRecordNodeGetEvent(nd, &ev));
+      for (TimedNodes& t : ne.timed) {
+        if (t.a0 == ev) t.na = nd;
+        if (t.b0 == ev) t.nb = nd;
+      }
+    }
+    for (const TimedNodes& t : ne.timed)
+      if (!t.na || !t.nb) {
+        release_graph(h, ne);
+        return fail(h, RT_ECUDA, "graph capture: stage-timing events not found");
+      }
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&ne.exec, g, 0);
+  if (ei != cudaSuccess) {
+    ne.exec = nullptr;
+    release_graph(h, ne);
+    return cuda_fail(h, ei, "graph instantiate");
+  }
+  ne.key = key.w;
+  ne.launches = n;
+  GraphEntry* slot = nullptr;
+  if (h->graphs.size() < GRAPH_CACHE) {
+    h->graphs.push_back(GraphEntry{});
+    slot = &h->graphs.back();
+  } else {
+    slot = &h->graphs[0];
+    for (GraphEntry& ge : h->graphs)
+      if (ge.used < slot->used) slot = &ge;
+    release_graph(h, *slot);
+  }
+  *slot = std::move(ne);
+  rt_status sl;
+  if ((sl = launch_graph(h, *slot)) != RT_OK) return sl;
+  *nl += n;
+  return RT_OK;
+}
+
 // Full Tucker pipeline for one tensor: tables, range finder, optional core.
 rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
                      int32_t p, const int64_t* s, uint64_t seed, const rt_options* opt, float* U,
@@ -847,56 +1012,81 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
     if ((st = stage_put(h, h->ws + o_zp, zp, sizeof(float*) * d)) != RT_OK) return st;
   }
   if ((st = stage_commit(h, &nl)) != RT_OK) return st;
-  if (overlap) {
-    if ((st = ensure_side(h)) != RT_OK) return st;
+  if (overlap && (st = ensure_side(h)) != RT_OK) return st;
+  if (G && !U) return fail(h, RT_EINVAL, "U is required with G");
+  const bool graph = opt && opt->use_graph;
+  GraphKey key;
+  if (graph) {
+    key.add(1);
+    key.add((uint64_t)h->device);
+    key.ptr(h->ws);
+    key.add(bump.off);
+    key.ptr(X);
+    key.add((uint64_t)dtype);
+    key.arr(n, d);
+    key.arr(r, d);
+    key.add((uint64_t)p);
+    key.ptr(U);
+    key.ptr(sigma);
+    key.ptr(G);
+    key.ptr(Zout);
+    key.add((uint64_t)prec_of(opt));
+    key.add(overlap ? 1 : 0);
+    key.add(o_zp);
+    key.add(o_bufA);
+    key.add(o_bufB);
+    key.group(Gp.g);
+  }
+  st = run_kernels(h, graph, key, &nl, [&](int* nk) -> rt_status {
+    if (overlap) {
+      {
+        StageTimer tm(h, 0);
+        *nk += launch_rf_head(Gp.g, h->stream, h->d_status);
+      }
+      RT_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
+      RT_CUDA(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+      {
+        StageTimer tm(h, 5, h->side);
+        *nk += launch_rf_tail(Gp.g, h->side, h->d_status);
+      }
+      RT_CUDA(h, cudaEventRecord(h->ev_join, h->side));
+      const RFProb& q1 = Gp.pp[d - 2].q;
+      const RFProb& q2 = Gp.pp[d - 1].q;
+      int64_t S = 1;
+      for (int j = 0; j < d - 2; ++j) S *= n[j];
+      int nsm = 148;
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+      const int xmode = (dtype == RT_BF16) ? 1 : (prec_of(opt) == RT_PREC_BF16 ? 2 : 0);
+      float* bufA = reinterpret_cast<float*>(h->ws + o_bufA);
+      float* bufB = reinterpret_cast<float*>(h->ws + o_bufB);
+      int got = 0;
+      {
+        StageTimer tm(h, 1);
+        // leave one SM per problem to the SVD part running beside the pass
+        got = launch_core2_tc(xmode, X, S, (int)n[d - 2], (int)n[d - 1], q1.Q, q1.c, q2.Q, q2.c, bufA,
+                              h->d_status, h->stream, std::max(1, nsm - d));
+      }
+      RT_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+      if (got > 0) {
+        *nk += got;
+        StageTimer tm(h, 2);
+        *nk += enqueue_core_rest_overlap(h, d, n, r, p, U, q1.Wsg, q2.Wsg, G, bufA, bufB);
+      } else {
+        *nk += enqueue_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec_of(opt));
+      }
+      return RT_OK;
+    }
     {
       StageTimer tm(h, 0);
-      nl += launch_rf_head(Gp.g, h->stream, h->d_status);
+      *nk += launch_range_finder(Gp.g, h->stream, h->d_status);
     }
-    RT_CUDA(h, cudaEventRecord(h->ev_fork, h->stream));
-    RT_CUDA(h, cudaStreamWaitEvent(h->side, h->ev_fork, 0));
-    {
-      StageTimer tm(h, 5, h->side);
-      nl += launch_rf_tail(Gp.g, h->side, h->d_status);
-    }
-    RT_CUDA(h, cudaEventRecord(h->ev_join, h->side));
-    const RFProb& q1 = Gp.pp[d - 2].q;
-    const RFProb& q2 = Gp.pp[d - 1].q;
-    int64_t S = 1;
-    for (int j = 0; j < d - 2; ++j) S *= n[j];
-    int nsm = 148;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
-    const int xmode = (dtype == RT_BF16) ? 1 : (prec_of(opt) == RT_PREC_BF16 ? 2 : 0);
-    float* bufA = reinterpret_cast<float*>(h->ws + o_bufA);
-    float* bufB = reinterpret_cast<float*>(h->ws + o_bufB);
-    int got = 0;
-    {
-      StageTimer tm(h, 1);
-      // leave one SM per problem to the SVD part running beside the pass
-      got = launch_core2_tc(xmode, X, S, (int)n[d - 2], (int)n[d - 1], q1.Q, q1.c, q2.Q, q2.c, bufA, h->d_status,
-                            h->stream, std::max(1, nsm - d));
-    }
-    RT_CUDA(h, cudaStreamWaitEvent(h->stream, h->ev_join, 0));
-    if (got > 0) {
-      nl += got;
-      StageTimer tm(h, 2);
-      nl += enqueue_core_rest_overlap(h, d, n, r, p, U, q1.Wsg, q2.Wsg, G, bufA, bufB);
-    } else {
-      nl += enqueue_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec_of(opt));
-    }
-    return finish(h, nl);
-  }
-  {
-    StageTimer tm(h, 0);
-    nl += launch_range_finder(Gp.g, h->stream, h->d_status);
-  }
-  if (Zout) nl += launch_sketch_sum(Gp.g, reinterpret_cast<float* const*>(h->ws + o_zp), h->stream);
-  if (G) {
-    const float* Ucat = U ? U : nullptr;
-    if (!Ucat) return fail(h, RT_EINVAL, "U is required with G");
-    nl += enqueue_core(h, X, dtype, d, n, r, Ucat, G, reinterpret_cast<float*>(h->ws + o_bufA),
-                       reinterpret_cast<float*>(h->ws + o_bufB), prec_of(opt));
-  }
+    if (Zout) *nk += launch_sketch_sum(Gp.g, reinterpret_cast<float* const*>(h->ws + o_zp), h->stream);
+    if (G)
+      *nk += enqueue_core(h, X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + o_bufA),
+                          reinterpret_cast<float*>(h->ws + o_bufB), prec_of(opt));
+    return RT_OK;
+  });
+  if (st != RT_OK) return st;
   return finish(h, nl);
 }
 
@@ -970,6 +1160,8 @@ rt_status rt_destroy(rt_handle h) {
     if (h->ev_used[k]) cudaEventDestroy(h->ev_used[k]);
   }
   if (h->pipe_buf) cudaFree(h->pipe_buf);
+  for (GraphEntry& ge : h->graphs) release_graph(h, ge);
+  if (h->gstream) cudaStreamDestroy(h->gstream);
   drain_timing(h);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   delete h;
@@ -1564,21 +1756,53 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
   }
   int nl = 0;
   if ((st = stage_commit(h, &nl)) != RT_OK) return st;
-  {
-    StageTimer tm(h, 0);
-    nl += launch_range_finder(Gp.g, h->stream, h->d_status);
+  const bool graph = opt && opt->use_graph;
+  GraphKey key;
+  if (graph) {
+    key.add(2);
+    key.add((uint64_t)h->device);
+    key.ptr(h->ws);
+    key.add(bump.off);
+    key.add((uint64_t)T);
+    key.add((uint64_t)dtype);
+    key.add((uint64_t)p);
+    for (int t = 0; t < T; ++t) {   // the job tables are uploaded per call; their launch shapes:
+      key.ptr(X[t]);
+      key.arr(n[t], d[t]);
+      key.arr(r[t], d[t]);
+      key.ptr(U[t]);
+      key.ptr(G[t]);
+    }
+    for (int k = 0; k < dmax; ++k) {
+      key.add((uint64_t)njob[k]);
+      key.add((uint64_t)ltiles[k]);
+      key.add((uint64_t)last_rows[k]);
+      key.add((uint64_t)lnmax[k]);
+      key.add((uint64_t)lrmax[k]);
+      key.add(o_jobs[k]);
+      key.add(o_lpre[k]);
+    }
+    key.group(Gp.g);
   }
-  for (int k = 0; k < dmax; ++k) {
-    StageTimer tm(h, k == 0 ? 1 : 2);
-    if (last_rows[k])
-      nl += launch_ttm_last_grouped(reinterpret_cast<const TTMJob*>(h->ws + o_jobs[k]),
-                                    reinterpret_cast<const int64_t*>(h->ws + o_lpre[k]), njob[k], ltiles[k],
-                                    k == 0 ? (int)dtype : DT_F32, lnmax[k], lrmax[k], h->stream);
-    else
-      nl += launch_ttm_grouped(reinterpret_cast<const TTMJob*>(h->ws + o_jobs[k]),
-                               reinterpret_cast<const int64_t*>(h->ws + o_lpre[k]), njob[k], ltiles[k],
-                               k == 0 ? (int)dtype : DT_F32, h->stream);
-  }
+  st = run_kernels(h, graph, key, &nl, [&](int* nk) -> rt_status {
+    {
+      StageTimer tm(h, 0);
+      *nk += launch_range_finder(Gp.g, h->stream, h->d_status);
+    }
+    for (int k = 0; k < dmax; ++k) {
+      StageTimer tm(h, k == 0 ? 1 : 2);
+      if (last_rows[k])
+        *nk += launch_ttm_last_grouped(reinterpret_cast<const TTMJob*>(h->ws + o_jobs[k]),
+                                       reinterpret_cast<const int64_t*>(h->ws + o_lpre[k]), njob[k], ltiles[k],
+                                       k == 0 ? (int)dtype : DT_F32, lnmax[k], lrmax[k], h->stream);
+      else
+        *nk += launch_ttm_grouped(reinterpret_cast<const TTMJob*>(h->ws + o_jobs[k]),
+                                  reinterpret_cast<const int64_t*>(h->ws + o_lpre[k]), njob[k], ltiles[k],
+                                  k == 0 ? (int)dtype : DT_F32, h->stream);
+    }
+    return RT_OK;
+  });
+  if (st != RT_OK) return st;
   return finish(h, nl);
 }
 
@@ -1712,40 +1936,66 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
   if ((st = stage_put(h, h->ws + o_jobs, jobs, sizeof(TransferJob) * internal.size())) != RT_OK) return st;
   int nlaunch = 0;
   if ((st = stage_commit(h, &nlaunch)) != RT_OK) return st;
-  {
-    StageTimer tm(h, 0);
-    nlaunch += launch_range_finder(Gp.g, h->stream, h->d_status);
+  const bool graph = opt && opt->use_graph;
+  GraphKey key;
+  if (graph) {
+    key.add(3);
+    key.add((uint64_t)h->device);
+    key.ptr(h->ws);
+    key.add(bump.off);
+    key.ptr(X);
+    key.add((uint64_t)dtype);
+    key.arr(n, d);
+    key.arr(rk.data(), nn);
+    key.add((uint64_t)p);
+    if (w) key.arr(w, nn);
+    key.ptr(U_leaf);
+    key.ptr(B);
+    key.ptr(U_nodes);
+    key.add(o_jobs);
+    key.add(o_tgen);
+    key.add(o_tpart);
+    key.add(o_rootp);
+    key.group(Gp.g);
   }
-  if (U_nodes) {
-    for (int i = 1; i < nn; ++i)
-      if (tree[i].a == tree[i].b)
-        RT_CUDA(h, cudaMemcpyAsync(U_leaf + o_leaf[i], U_nodes + o_unode[i], (size_t)n[tree[i].a] * rk[i] * 4,
-                                   cudaMemcpyDeviceToDevice, h->stream));
-  }
-  {
-    StageTimer tm(h, 3);
-    nlaunch += launch_transfer(reinterpret_cast<const TransferJob*>(h->ws + o_jobs), jobs, (int)internal.size(),
-                               reinterpret_cast<float*>(h->ws + o_tpart), h->stream);
-    for (int i : wide) {
-      const TNode& nd = tree[i];
-      TransferJob jb{};
-      jb.US = Uof(i);
-      jb.Ul = Uof(nd.left);
-      jb.Ur = Uof(nd.right);
-      jb.B = B + o_B[i];
-      jb.nl = range_prod(n, tree[nd.left].a, tree[nd.left].b);
-      jb.nr = range_prod(n, tree[nd.right].a, tree[nd.right].b);
-      jb.rS = rk[i];
-      jb.rl = rk[nd.left];
-      jb.rr = rk[nd.right];
-      nlaunch += launch_transfer_general(jb, reinterpret_cast<float*>(h->ws + o_tgen), h->stream);
+  st = run_kernels(h, graph, key, &nlaunch, [&](int* nk) -> rt_status {
+    {
+      StageTimer tm(h, 0);
+      *nk += launch_range_finder(Gp.g, h->stream, h->d_status);
     }
-  }
-  {
-    StageTimer tm(h, 4);
-    nlaunch += launch_root_any(X, (int)dtype, nl, nr, Uof(root.left), rl, Uof(root.right), rr, B + o_B[0],
-                               reinterpret_cast<float*>(h->ws + o_rootp), h->d_status, h->stream);
-  }
+    if (U_nodes) {
+      for (int i = 1; i < nn; ++i)
+        if (tree[i].a == tree[i].b)
+          RT_CUDA(h, cudaMemcpyAsync(U_leaf + o_leaf[i], U_nodes + o_unode[i], (size_t)n[tree[i].a] * rk[i] * 4,
+                                     cudaMemcpyDeviceToDevice, h->stream));
+    }
+    {
+      StageTimer tm(h, 3);
+      *nk += launch_transfer(reinterpret_cast<const TransferJob*>(h->ws + o_jobs), jobs, (int)internal.size(),
+                             reinterpret_cast<float*>(h->ws + o_tpart), h->stream);
+      for (int i : wide) {
+        const TNode& nd = tree[i];
+        TransferJob jb{};
+        jb.US = Uof(i);
+        jb.Ul = Uof(nd.left);
+        jb.Ur = Uof(nd.right);
+        jb.B = B + o_B[i];
+        jb.nl = range_prod(n, tree[nd.left].a, tree[nd.left].b);
+        jb.nr = range_prod(n, tree[nd.right].a, tree[nd.right].b);
+        jb.rS = rk[i];
+        jb.rl = rk[nd.left];
+        jb.rr = rk[nd.right];
+        *nk += launch_transfer_general(jb, reinterpret_cast<float*>(h->ws + o_tgen), h->stream);
+      }
+    }
+    {
+      StageTimer tm(h, 4);
+      *nk += launch_root_any(X, (int)dtype, nl, nr, Uof(root.left), rl, Uof(root.right), rr, B + o_B[0],
+                             reinterpret_cast<float*>(h->ws + o_rootp), h->d_status, h->stream);
+    }
+    return RT_OK;
+  });
+  if (st != RT_OK) return st;
   return finish(h, nlaunch);
 }
 

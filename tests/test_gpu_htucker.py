@@ -208,3 +208,20 @@ def test_inv_norm_16_8_full_size(rt):
     blk = 4096
     BR = sum(htucker.root_transfer(Xm[a:a + blk], Ul[a:a + blk], Ur) for a in range(0, Xm.shape[0], blk))
     _check_nodes(ref, U_leaf, B, Un, root_ref=BR)
+
+
+def test_graph_replay_matches_direct_launches(rt):
+    rs = np.random.default_rng(10)
+    X = torch.from_numpy(rs.standard_normal((6, 7, 8, 9, 5)).astype(np.float32)).cuda()
+    Ul0, B0 = rt.rhtucker_decompose(X, 3, 2, seed=4)
+    Ul1, B1 = rt.rhtucker_decompose(X, 3, 2, seed=5)
+    flat_u = torch.cat([u.reshape(-1) for u in Ul0]).clone()
+    flat_b = torch.cat([b.reshape(-1) for b in B0.values()]).clone()
+    out = (torch.empty_like(flat_u), torch.empty_like(flat_b))
+    for seed, (Ul, B) in ((4, (Ul0, B0)), (4, (Ul0, B0)), (5, (Ul1, B1))):   # capture, replay, other seed
+        Ug, Bg = rt.rhtucker_decompose(X, 3, 2, seed=seed, graph=True, out=out)
+        torch.cuda.synchronize()
+        for a, b in zip(Ug, Ul):
+            assert torch.equal(a, b)
+        for k in B:
+            assert torch.equal(Bg[k], B[k])

@@ -428,3 +428,65 @@ def test_repeated_calls_reuse_tables_safely(rt):
         for a, b in zip(U, U0):
             assert torch.equal(a, b)
     assert not torch.equal(Gs, G0)
+
+
+def _clone(G, U):
+    return G.clone(), [u.clone() for u in U]
+
+
+def _same(a, b):
+    assert torch.equal(a[0], b[0])
+    for x, y in zip(a[1], b[1]):
+        assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("overlap", [False, True])
+def test_graph_replay_matches_direct_launches(rt, overlap):
+    # rt_options.use_graph: the first call captures the kernel sequence, later calls
+    # with the same buffers and shapes replay it; each call still uploads its own
+    # tables, so another seed or new contents of X give that call's result.  Same
+    # kernels, same launch shapes: bit-identical to direct launches.
+    shape, r, p = (40, 36, 64), [5, 4, 6], 3
+    Xd = torch.from_numpy(synth.tucker_tensor(shape, tuple(r), 1e-4, 23)).cuda()
+    out = (torch.empty(sum(n * k for n, k in zip(shape, r)), device="cuda"), torch.empty(r, device="cuda"))
+    direct = {sd: _clone(*rt.rtucker_decompose(Xd, r, p, seed=sd, overlap=overlap)) for sd in (7, 8)}
+    g1 = _clone(*rt.rtucker_decompose(Xd, r, p, seed=7, out=out, overlap=overlap, graph=True))   # capture
+    g2 = _clone(*rt.rtucker_decompose(Xd, r, p, seed=7, out=out, overlap=overlap, graph=True))   # replay
+    g3 = _clone(*rt.rtucker_decompose(Xd, r, p, seed=8, out=out, overlap=overlap, graph=True))   # other tables
+    rt.sync()
+    _same(g1, direct[7])
+    _same(g2, direct[7])
+    _same(g3, direct[8])
+    # new contents of X, replayed; then another shape (captured anew) and back
+    Xd.copy_(torch.from_numpy(synth.tucker_tensor(shape, tuple(r), 1e-4, 24)).cuda())
+    d2 = _clone(*rt.rtucker_decompose(Xd, r, p, seed=7, overlap=overlap))
+    g4 = _clone(*rt.rtucker_decompose(Xd, r, p, seed=7, out=out, overlap=overlap, graph=True))
+    Y = torch.from_numpy(synth.tucker_tensor((30, 33, 31), (3, 3, 3), 1e-4, 25)).cuda()
+    dy = _clone(*rt.rtucker_decompose(Y, [3, 3, 3], 2, seed=1))
+    gy = _clone(*rt.rtucker_decompose(Y, [3, 3, 3], 2, seed=1, graph=True))
+    g5 = _clone(*rt.rtucker_decompose(Xd, r, p, seed=7, out=out, overlap=overlap, graph=True))
+    rt.sync()
+    _same(g4, d2)
+    _same(gy, dy)
+    _same(g5, d2)
+    # stage timing turns capture off; the result is the same
+    rt.set_timing(True)
+    g6 = _clone(*rt.rtucker_decompose(Xd, r, p, seed=7, out=out, overlap=overlap, graph=True))
+    rt.sync()
+    rt.get_timing(reset=True)
+    rt.set_timing(False)
+    _same(g6, d2)
+
+
+def test_graph_replay_batched(rt):
+    shapes = [(20, 24, 28), (33, 17, 40), (16, 16, 16, 16)]
+    ranks = [(3, 4, 5), (4, 3, 6), (3, 3, 3, 3)]
+    Xs = [torch.from_numpy(synth.tucker_tensor(s, k, 1e-4, 30 + i)).cuda() for i, (s, k) in enumerate(zip(shapes, ranks))]
+    direct = rt.BatchedDecomposition(Xs, ranks, 3, [5, 6, 7]).run().results()
+    want = [_clone(G, U) for G, U in direct]
+    bd = rt.BatchedDecomposition(Xs, ranks, 3, [5, 6, 7], graph=True)
+    for _ in range(3):                       # capture, then replays
+        got = bd.run().results()
+        rt.sync()
+        for a, b in zip(got, want):
+            _same(a, b)
