@@ -1,8 +1,9 @@
 """Pins of the Sub-R-RtL-HT oracle (Alg. 2): the paper's order-8 dimension tree
 (tests/golden), the transfer-tensor and root definitions written with explicit
-Kronecker products, the full-sampling case that reduces to deterministic RtL-HT,
-exact recovery of tensors of known hierarchical rank, nestedness, and the
-float32 input generator of the 1/||x|| workload."""
+Kronecker products, the full-sampling case that reduces to deterministic RtL-HT
+and its error window (Sec. 4 quasi-optimality), exact recovery of tensors of
+known hierarchical rank, nestedness, and the float32 input generator of the
+1/||x|| workload."""
 
 import itertools
 import os
@@ -74,6 +75,39 @@ def test_full_sampling_reduces_to_deterministic_rtl_ht():
     for nd in tree:
         if not nd.is_leaf:
             assert np.abs(out["B"][nd.id] - ref["B"][nd.id]).max() < 1e-10
+
+
+def test_full_sampling_error_within_rtl_ht_bounds():
+    # Sec. 4 (RtL-HT quasi-optimality, sqrt(2d-3) times the best error): with every
+    # column sampled and r_S + p = min(n_S, n_notin_S), each U_S is the dominant left
+    # singular basis of X^(S) and the format is the RtL-HT truncation, whose error
+    # squared is at most the sum over the non-root nodes but one child of the root of
+    # the discarded squared singular values of X^(S); no format of these ranks does
+    # better than the largest single-node tail.  Low hierarchical rank plus noise, so
+    # a wrong transfer tensor or reconstruction step lands far outside the window.
+    for trial in range(12):
+        rs = np.random.default_rng(300 + trial)
+        shape = tuple(int(v) for v in rs.integers(3, 7, size=int(rs.integers(3, 6))))
+        X = _random_ht_tensor(shape, 2, 300 + trial)
+        X = X / np.linalg.norm(X) + 1e-2 * rs.standard_normal(shape) / np.sqrt(X.size)
+        tree = htucker.balanced_tree(len(shape))
+        p = int(rs.integers(1, 3))
+        ranks = [1] + [min(htucker.node_rows(shape, nd), htucker.node_cols(shape, nd)) - p for nd in tree[1:]]
+        if min(ranks[1:]) < 2:
+            continue
+        w = [0] + [htucker.node_cols(shape, nd) for nd in tree[1:]]
+        out = htucker.sub_r_rtl_ht(X, ranks, p, w=w, seed=trial)
+        err = np.linalg.norm(X - htucker.reconstruct(out["U"], out["B"], out["tree"], shape))
+        tails = {}
+        for nd in tree[1:]:
+            rows = int(np.prod(shape[nd.a:nd.b + 1]))
+            M = np.moveaxis(X, list(range(nd.a, nd.b + 1)), list(range(nd.b - nd.a + 1))).reshape(rows, -1)
+            sv = np.linalg.svd(M, compute_uv=False)
+            tails[nd.id] = float(np.sum(sv[ranks[nd.id]:] ** 2))
+        lo = np.sqrt(max(tails.values()))
+        hi = np.sqrt(sum(v for k, v in tails.items() if k != tree[0].right))
+        assert lo * (1 - 1e-12) <= err <= hi * (1 + 1e-12), (shape, lo, err, hi)
+        assert len(tails) == 2 * len(shape) - 2
 
 
 def _random_ht_tensor(shape, r, seed):
