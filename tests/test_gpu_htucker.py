@@ -161,6 +161,13 @@ def test_mixed_transfer_forms_and_chunked_root(rt):
     _compare_ht(rt, X, ranks, p, seed=5, gap_min=5e-3)
 
 
+def test_order_16_balanced_tree(rt):
+    # d = 16: 31 nodes (16 leaves of 2 rows, 4 levels of internal nodes), a 256 x 256
+    # root unfolding; rank 1 at every node of a rank-one tensor plus noise
+    X = synth.tucker_tensor((2,) * 16, (1,) * 16, noise=1e-3, data_seed=41)
+    _compare_ht(rt, X, 1, 1, seed=2)
+
+
 def test_full_sampling_matches_rtl_ht(rt):
     rs = np.random.default_rng(2)
     X = rs.standard_normal((3, 4, 3, 4)).astype(np.float32)

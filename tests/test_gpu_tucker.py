@@ -293,6 +293,27 @@ def test_invalid_arguments_raise(rt):
     assert e.value.status in (1, 7)
 
 
+def test_order_16_the_largest_supported(rt):
+    # d = 16: every per-problem mode array is full; ragged last modes (3, 4) keep the
+    # core on the FFMA chain
+    X = synth.tucker_tensor((2,) * 14 + (3, 4), (1,) * 16, noise=1e-3, data_seed=40)
+    _run_and_compare(rt, X, (1,) * 16, 1, seed=3)
+
+
+def test_degenerate_shapes_are_rejected(rt):
+    with pytest.raises(rt.RtError) as e:
+        rt.rtucker_decompose(torch.zeros((4, 0, 6), device="cuda"), [1, 1, 1], 0)   # empty mode
+    assert e.value.status == 1
+    with pytest.raises(rt.RtError) as e:
+        rt.rtucker_decompose(torch.zeros((1,) * 17, device="cuda"), [1] * 17, 0)    # d > 16
+    assert e.value.status == 1
+    with pytest.raises((rt.RtError, ValueError)):
+        rt.rtucker_decompose(torch.zeros((8,), device="cuda"), [1], 0)              # d < 2
+    with pytest.raises(rt.RtError) as e:
+        rt.rtucker_decompose(torch.zeros((4, 5, 6), device="cuda"), [0, 1, 1], 1)   # r_k = 0
+    assert e.value.status == 1
+
+
 def test_host_memory_entry_point(rt):
     X = synth.tucker_tensor((40, 36, 50), (4, 5, 6), noise=1e-4, data_seed=13)
     Xh = torch.from_numpy(X).pin_memory()
