@@ -312,6 +312,67 @@ def measure_ht(rt, steps, peak, n=None, d=None):
                               "frac": nbytes / (root_ms * 1e-3) / 1e9 / peak}}
 
 
+def measure_scaling(rt, steps):
+    """The paper's scaling workloads on one GPU (its parallel experiments):
+    Sub-R-HOSVD of order-8 low-rank tensors (rank 5, n = 16, 18, 20: 17 to 102 GB
+    float32, s = 10^4 fibers per mode) and Sub-R-RtL-HT of f = 1/||x|| on n^8 grids
+    (rank 6, 20 n fibers per node).  Each: graph replay, CUDA events, stage times,
+    input GB/s and the relative error of the result."""
+    import torch
+    import synth
+    out = {"tucker": [], "ht": []}
+    ct = synth.SCALING_TUCKER
+    for n in ct["ns"]:
+        shape, r = (n,) * ct["d"], [ct["rank"]] * ct["d"]
+        X = synth.tucker_tensor_torch(shape, tuple(r), noise=ct["noise"], data_seed=n, device="cuda")
+        nbytes = X.numel() * 4
+        U = torch.empty(sum(n * k for k in r), dtype=torch.float32, device="cuda")
+        G = torch.empty(r, dtype=torch.float32, device="cuda")
+        s = [ct["s"]] * ct["d"]
+
+        def step():
+            rt.rtucker_decompose(X, r, ct["p"], s=s, seed=ct["seed"], out=(U, G), graph=True)
+        rt.set_timing(True)
+        ms = _event_time(step, steps, 2)
+        stg = rt.get_timing(reset=True)
+        rt.set_timing(False)
+        Us = [u.view(n, k) for u, k in zip(torch.split(U, [n * k for k in r]), r)]
+        e = rt.rtucker_relerr(X, G, Us)
+        calls = steps + 2
+        out["tucker"].append({"n": n, "gb": nbytes / 1e9, "ms_per_decomp": ms,
+                              "input_gbs": nbytes / (ms * 1e-3) / 1e9, "relerr": e,
+                              "stage_ms_per_decomp": {k: v[0] / calls for k, v in stg.items() if v[1]}})
+        del X, U, G, Us
+        torch.cuda.empty_cache()
+    ch = synth.SCALING_HT
+    for n in ch["ns"]:
+        X = synth.inv_norm_tensor_torch(n, ch["d"], ch["lo"], ch["hi"], device="cuda")
+        nbytes = X.numel() * 4
+        w = ch["w_per_n"] * n
+
+        def step():
+            return rt.rhtucker_decompose(X, ch["rank"], ch["p"], w=w, seed=ch["seed"])
+        step()
+        rt.set_timing(True)
+        rt.get_timing(reset=True)
+        ms = _event_time(step, steps, 1)
+        stg = rt.get_timing(reset=True)
+        rt.set_timing(False)
+        U_leaf, B = step()
+        e = rt.rhtucker_relerr(X, U_leaf, B, ch["rank"])
+        calls = steps + 1
+        out["ht"].append({"n": n, "gb": nbytes / 1e9, "ms_per_decomp": ms,
+                          "input_gbs": nbytes / (ms * 1e-3) / 1e9, "relerr": e,
+                          "stage_ms_per_decomp": {k: v[0] / calls for k, v in stg.items() if v[1]}})
+        del X, U_leaf, B
+        torch.cuda.empty_cache()
+    out["workload"] = ("Sub-R-HOSVD: order-8 float32 tensors n^8, n = %s (Gaussian 5^8 core, Q-of-Gaussian "
+                       "factors, 1e-6 noise, built on the device), r = 5, p = 5, s = 10^4 per mode; "
+                       "Sub-R-RtL-HT: f = 1/||x|| on n^8 grids over [1,2]^8, rank 6, p = 5, w = 20 n"
+                       % (list(ct["ns"]),))
+    return out
+
+
 # ---------------------------------------------------------------- our arm
 def run_ours(args):
     import numpy as np
@@ -500,6 +561,8 @@ def run_only(args):
         out = measure_ht(rt, args.steps, peak, n=args.ht_n, d=args.ht_d)
     elif args.only == "grad":
         out = measure_grad(rt, args.steps, peak)
+    elif args.only == "scaling":
+        out = measure_scaling(rt, args.steps)
     else:
         out = measure_batched(rt, args.steps)
     print(json.dumps({"only": args.only, **out}))
@@ -513,7 +576,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["ht", "batched", "grad"], default=None,
+    ap.add_argument("--only", choices=["ht", "batched", "grad", "scaling"], default=None,
                     help="run one extra workload alone (profiling), not the benchmark line")
     ap.add_argument("--ht-n", type=int, default=None, help="grid size of the H-Tucker workload with --only ht")
     ap.add_argument("--ht-d", type=int, default=None, help="order of the H-Tucker workload with --only ht")

@@ -87,7 +87,14 @@ typedef struct {
                           contracts with W; 0 (default) waits for U.  Same
                           result up to rounding.  Shapes the tensor-core pass
                           cannot take ignore it.                                 */
-  int32_t reserved[5]; /* must be zero                                          */
+  int32_t core;        /* kernels of the core contraction (rtucker_decompose,
+                          rtucker_core): 0 (default) auto: the tensor-core pass
+                          over X for slabs of at least 64 x 64 (last two modes),
+                          two-mode FFMA passes over small slabs that fit shared
+                          memory, one-mode FFMA contractions otherwise; 1 the
+                          tensor-core pass whenever the shape allows it; 2 FFMA
+                          kernels only.  Same result up to rounding.           */
+  int32_t reserved[4]; /* must be zero                                          */
 } rt_options;
 
 /* ----------------------------------------------------------- handle

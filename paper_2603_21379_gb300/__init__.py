@@ -40,7 +40,7 @@ class RtError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("overlap", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("core", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 _lib = None
@@ -264,19 +264,23 @@ def rtucker_factors(X, r, p, s=None, seed=0, with_sigma=False):
 
 
 _PREC = {"fp32": 0, "bf16": 1}
+_CORE = {"auto": 0, "tc": 1, "ffma": 2}
 
 
-def _opts(prec, overlap=False, graph=False):
+def _opts(prec, overlap=False, graph=False, core="auto"):
     """rt_options for a precision form (the overlapped core schedule, CUDA-graph
-    replay), or None (defaults)."""
+    replay, the core kernels: "auto", "tc" or "ffma"), or None (defaults)."""
     if prec not in _PREC:
         raise ValueError("prec must be 'fp32' or 'bf16'")
-    if prec == "fp32" and not overlap and not graph:
+    if core not in _CORE:
+        raise ValueError("core must be 'auto', 'tc' or 'ffma'")
+    if prec == "fp32" and not overlap and not graph and core == "auto":
         return None
     o = _Options()
     o.prec = _PREC[prec]
     o.overlap = 1 if overlap else 0
     o.use_graph = 1 if graph else 0
+    o.core = _CORE[core]
     return ctypes.byref(o)
 
 
@@ -284,20 +288,21 @@ def _cat_u(U):
     return torch.cat([u.reshape(-1).to(torch.float32) for u in U]).contiguous()
 
 
-def rtucker_core(X, U, prec="fp32"):
+def rtucker_core(X, U, prec="fp32", core="auto"):
     """S7: core G = X x_1 U_1^T ... x_d U_d^T (float32 result; prec="bf16" rounds a
-    float32 X to one bfloat16 term in the tensor-core pass)."""
+    float32 X to one bfloat16 term in the tensor-core pass; ``core`` selects the
+    kernels, see rt_options.core)."""
     lib = load_library()
     dt, d, n = _tensor_args(X)
     r = [int(u.shape[1]) for u in U]
     Uc = _cat_u(U)
     G = torch.empty(r, dtype=torch.float32, device=X.device)
     h = _handle(X.device.index)
-    _check(h, lib.rtucker_core(h, _ptr(X), dt, d, _i64(n), _i32(r), _ptr(Uc), _opts(prec), _ptr(G)))
+    _check(h, lib.rtucker_core(h, _ptr(X), dt, d, _i64(n), _i32(r), _ptr(Uc), _opts(prec, core=core), _ptr(G)))
     return G
 
 
-def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32", overlap=False, graph=False):
+def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32", overlap=False, graph=False, core="auto"):
     """S1-S7: Sub-R-HOSVD; returns (G, [U_k]).  ``out`` = (Uflat, G) reuses buffers;
     ``prec`` "fp32" (default) or "bf16" (the BF16 compute form of the core pass);
     ``overlap`` runs the pass over X on the QR factors beside the SVD part of the
@@ -315,7 +320,7 @@ def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32", overlap=Fa
     h = _handle(X.device.index)
     sp = _i64(_as_list(s, d)) if s is not None else None
     _check(h, lib.rtucker_decompose(h, _ptr(X), dt, d, _i64(n), _i32(r), int(p), sp, ctypes.c_uint64(seed),
-                                    _opts(prec, overlap, graph), _ptr(U), _ptr(G)))
+                                    _opts(prec, overlap, graph, core), _ptr(U), _ptr(G)))
     return G, _split(U, n, r)
 
 

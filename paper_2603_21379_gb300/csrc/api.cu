@@ -602,7 +602,8 @@ rt_status check_opts(rt_handle h, const rt_options* opt) {
   if (!opt) return RT_OK;
   if (opt->prec != RT_PREC_FP32 && opt->prec != RT_PREC_BF16) return fail(h, RT_EINVAL, "unknown precision");
   if (opt->use_graph != 0 && opt->use_graph != 1) return fail(h, RT_EINVAL, "use_graph must be 0 or 1");
-  for (int i = 0; i < 5; ++i)
+  if (opt->core < 0 || opt->core > 2) return fail(h, RT_EINVAL, "core must be 0, 1 or 2");
+  for (int i = 0; i < 4; ++i)
     if (opt->reserved[i]) return fail(h, RT_EINVAL, "reserved option fields must be zero");
   return RT_OK;
 }
@@ -667,11 +668,20 @@ int core_mode() {
 
 int prec_of(const rt_options* opt) { return opt ? opt->prec : RT_PREC_FP32; }
 
-// prec RT_PREC_BF16 rounds float32 X to one bf16 term in the tensor-core pass (the
-// factors and the intermediate keep two terms); shapes that pass cannot take run the
-// float32 chain instead.
+int core_of(const rt_options* opt) { return opt ? opt->core : 0; }
+
+// Contractions of the core G = X x_1 U_1^T ... x_d U_d^T, last modes first.  core
+// (rt_options.core): 0 auto, 1 tensor-core pass whenever the shape allows, 2 FFMA only
+// (also RT_CORE_MODE=0).  Auto takes the tensor-core pass over X for slabs of at least
+// TC_MIN_SIDE x TC_MIN_SIDE (its MMA tiles are 128 rows; smaller slabs leave most of
+// each tile empty); then, from the last remaining modes down, two modes at a time
+// with k_slab2 where a slab fits shared memory, else one mode.  prec RT_PREC_BF16
+// rounds float32 X to one bf16 term in the tensor-core pass (the factors and the
+// intermediate keep two terms); the FFMA kernels compute in float32.
+constexpr int64_t TC_MIN_SIDE = 64;
+
 int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
-                 const float* U, float* G, float* bufA, float* bufB, int prec) {
+                 const float* U, float* G, float* bufA, float* bufB, int prec, int core) {
   cudaStream_t st = h->stream;
   int nl = 0;
   size_t uoff[MAXD];
@@ -681,9 +691,11 @@ int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_
   int adt = (int)dtype;
   int ping = 0;
   int k = d - 1;
+  if (core_mode() == 0) core = 2;
   // the last two modes in one tensor-core pass over X, when the shape allows
-  const int mode = core_mode();
-  if (mode > 0 && (dtype == RT_F32 || dtype == RT_BF16) && d >= 2) {
+  const bool tc_pref = core == 1 || (core == 0 && n[d - 2] >= TC_MIN_SIDE && n[d - 1] >= TC_MIN_SIDE) ||
+                       (core == 0 && !slab2_fits(n[d - 2], n[d - 1], 1, r[d - 2], r[d - 1]));
+  if (core != 2 && tc_pref && (dtype == RT_F32 || dtype == RT_BF16) && d >= 2) {
     int64_t S = 1;
     for (int j = 0; j < d - 2; ++j) S *= n[j];
     float* out = (d == 2) ? G : bufA;
@@ -702,10 +714,44 @@ int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_
       k = d - 3;
     }
   }
-  for (; k >= 0; --k) {
-    int64_t L = 1, R = 1;
-    for (int j = 0; j < k; ++j) L *= n[j];
+  if (A == X && k == d - 1 && dtype == RT_F32 && last2_fits(n[d - 2], n[d - 1], r[d - 2], r[d - 1])) {
+    // the last two modes of float32 X with small slabs: one thread per row, one read
+    int64_t S = 1;
+    for (int j = 0; j < d - 2; ++j) S *= n[j];
+    float* out = (d == 2) ? G : bufA;
+    int got = 0;
+    {
+      StageTimer tm(h, 1);
+      got = launch_last2(static_cast<const float*>(X), S, n[d - 2], n[d - 1], U + uoff[d - 2], r[d - 2],
+                         U + uoff[d - 1], r[d - 1], out, st);
+    }
+    if (got > 0) {
+      nl += got;
+      A = out;
+      adt = DT_F32;
+      ping = 1;
+      k = d - 3;
+    }
+  }
+  while (k >= 0) {
+    int64_t R = 1;
     for (int j = k + 1; j < d; ++j) R *= r[j];
+    if (k >= 1 && slab2_fits(n[k - 1], n[k], R, r[k - 1], r[k])) {   // modes k-1 and k together
+      int64_t L = 1;
+      for (int j = 0; j < k - 1; ++j) L *= n[j];
+      float* out = (k == 1) ? G : (ping ? bufB : bufA);
+      {
+        StageTimer tm(h, A == X ? 1 : 2);
+        nl += launch_slab2(A, adt, L, n[k - 1], n[k], R, U + uoff[k - 1], r[k - 1], U + uoff[k], r[k], out, st);
+      }
+      A = out;
+      adt = DT_F32;
+      ping ^= 1;
+      k -= 2;
+      continue;
+    }
+    int64_t L = 1;
+    for (int j = 0; j < k; ++j) L *= n[j];
     float* out = (k == 0) ? G : (ping ? bufB : bufA);
     {
       StageTimer tm(h, A == X ? 1 : 2);
@@ -714,6 +760,7 @@ int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_
     A = out;
     adt = DT_F32;
     ping ^= 1;
+    --k;
   }
   return nl;
 }
@@ -1031,6 +1078,7 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
     key.ptr(G);
     key.ptr(Zout);
     key.add((uint64_t)prec_of(opt));
+    key.add((uint64_t)core_of(opt));
     key.add(overlap ? 1 : 0);
     key.add(o_zp);
     key.add(o_bufA);
@@ -1072,7 +1120,7 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
         StageTimer tm(h, 2);
         *nk += enqueue_core_rest_overlap(h, d, n, r, p, U, q1.Wsg, q2.Wsg, G, bufA, bufB);
       } else {
-        *nk += enqueue_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec_of(opt));
+        *nk += enqueue_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec_of(opt), core_of(opt));
       }
       return RT_OK;
     }
@@ -1083,7 +1131,7 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
     if (Zout) *nk += launch_sketch_sum(Gp.g, reinterpret_cast<float* const*>(h->ws + o_zp), h->stream);
     if (G)
       *nk += enqueue_core(h, X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + o_bufA),
-                          reinterpret_cast<float*>(h->ws + o_bufB), prec_of(opt));
+                          reinterpret_cast<float*>(h->ws + o_bufB), prec_of(opt), core_of(opt));
     return RT_OK;
   });
   if (st != RT_OK) return st;
@@ -1289,7 +1337,7 @@ rt_status rtucker_core(rt_handle h, const void* X, rt_dtype dtype, int d, const 
   const size_t oA = bump.take(cb * 4), oB = bump.take(cb * 4);
   if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
   const int nl = enqueue_core(h, X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + oA),
-                              reinterpret_cast<float*>(h->ws + oB), prec_of(opt));
+                              reinterpret_cast<float*>(h->ws + oB), prec_of(opt), core_of(opt));
   return finish(h, nl);
 }
 

@@ -11,6 +11,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "rt_common.cuh"
 #include "rt_host.h"
 
@@ -281,6 +283,77 @@ __global__ void __launch_bounds__(TL_THREADS) k_ttm_last(const float* __restrict
     if (a < r) o[a] = acc[a];
 }
 
+// The last two modes of float32 X in one read, for small slabs (n1 <= TL_THREADS rows
+// of n2 values): a CTA owns spc = TL_THREADS / n1 whole slabs.  Thread per row l:
+// T(l, b) = sum_j U2[j][b] X(l, j) in registers (as k_ttm_last, U2 zero-padded to RW
+// columns in shared memory), written to shared memory; then the slabs' outputs
+// P(s, a, b) = sum_i U1[i][a] T(s n1 + i, b), one per thread and step, written
+// contiguously.  float32 products and sums, j then i in order.
+// Dynamic smem: us[n2][RW] | Ts[spc n1][RW + 1] | U1s[n1][r1]
+template <int RW>
+__global__ void __launch_bounds__(TL_THREADS) k_last2(const float* __restrict__ A, int64_t S, int n1, int n2,
+                                                      const float* __restrict__ U1, int r1,
+                                                      const float* __restrict__ U2, int r2,
+                                                      float* __restrict__ out) {
+  extern __shared__ __align__(16) float l2m[];
+  constexpr int LDT = RW + 1;                    // odd stride: row-wise stores are conflict-free
+  const int spc = TL_THREADS / n1;
+  float* us = l2m;
+  float* Ts = us + n2 * RW;
+  float* U1s = Ts + spc * n1 * LDT;
+  for (int e = threadIdx.x; e < n2 * RW; e += TL_THREADS) {
+    const int j = e / RW, b = e % RW;
+    us[e] = b < r2 ? U2[j * r2 + b] : 0.f;
+  }
+  for (int e = threadIdx.x; e < n1 * r1; e += TL_THREADS) U1s[e] = U1[e];
+  __syncthreads();
+  const int64_t s0 = (int64_t)blockIdx.x * spc;
+  const int nsl = (int)min((int64_t)spc, S - s0);
+  const int t = threadIdx.x;
+  if (t < nsl * n1) {
+    const float* row = A + (s0 * n1 + t) * n2;
+    float acc[RW];
+#pragma unroll
+    for (int b = 0; b < RW; ++b) acc[b] = 0.f;
+    const bool v4 = (n2 % 4) == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+    for (int j0 = 0; j0 < n2; j0 += 4) {
+      float x[4];
+      if (v4) {
+        const float4 f = __ldg(reinterpret_cast<const float4*>(row + j0));
+        x[0] = f.x; x[1] = f.y; x[2] = f.z; x[3] = f.w;
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = j0 + q < n2 ? __ldg(row + j0 + q) : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        if (j0 + q >= n2) break;
+        const float* uj = us + (j0 + q) * RW;
+#pragma unroll
+        for (int b = 0; b < RW; b += 4) {
+          const float4 u = *reinterpret_cast<const float4*>(uj + b);
+          acc[b] = fmaf(x[q], u.x, acc[b]);
+          acc[b + 1] = fmaf(x[q], u.y, acc[b + 1]);
+          acc[b + 2] = fmaf(x[q], u.z, acc[b + 2]);
+          acc[b + 3] = fmaf(x[q], u.w, acc[b + 3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < RW; ++b) Ts[t * LDT + b] = acc[b];
+  }
+  __syncthreads();
+  const int osz = r1 * r2;
+  float* dst = out + s0 * osz;
+  for (int o = t; o < nsl * osz; o += TL_THREADS) {
+    const int b = o % r2, a = (o / r2) % r1, s = o / osz;
+    const float* tp = Ts + s * n1 * LDT + b;
+    float acc = 0.f;
+    for (int i = 0; i < n1; ++i) acc = fmaf(U1s[i * r1 + a], tp[i * LDT], acc);
+    dst[o] = acc;
+  }
+}
+
 // Grouped last-mode contractions (R = 1) of a batch: job q contracts the last mode of
 // its L x n tensor with U_q (n x r <= RW), one thread per row.  pre[j] counts CTAs of
 // TL_THREADS rows before job j.  A's element type T (the batch's X type at the first
@@ -333,7 +406,162 @@ __global__ void __launch_bounds__(TL_THREADS) k_ttm_last_grouped(const TTMJob* _
     if (a < r) o[a] = acc[a];
 }
 
+// ---------------------------------------------------------------- two modes of small slabs
+// out(l, a, b, rho) = sum_{i,j} U1[i][a] U2[j][b] A(l, i, j, rho) for A of (L, n1, n2, R):
+// two neighbouring modes contracted in one read of A when a slab (n1 n2 R values) fits
+// in shared memory, for the small slabs that the tensor-core pass tiles poorly (its
+// M = 128 rows per slab).  A CTA takes batches of nb consecutive slabs (contiguous in
+// A): it forms T(s, i, b, rho) = sum_j U2[j][b] A(s, i, j, rho), then the outputs, one
+// output per thread and step, and writes the batch's outputs (contiguous in out).
+// float32 A is staged by cp.async into two buffers, the next batch's copies in flight
+// while the current one is contracted; other dtypes are converted on a plain load.
+// float32 products and sums, j then i in order.
+// Dynamic smem: As[2][nb n1 n2 R] (one buffer for non-float32 A) | Ts[nb n1 r2 R] |
+//               U1s[n1 r1] | U2s[n2 r2]
+constexpr int S2_THREADS = 256, S2_MAXA = 12288, S2_FILL = 6144, S2_MAXT = 4096, S2_MAXU = 2048;
+
+__device__ __forceinline__ void slab2_contract(const float* __restrict__ As, float* __restrict__ Ts,
+                                               const float* __restrict__ U1s, const float* __restrict__ U2s,
+                                               int cnt, int n1, int n2, int R, int r1, int r2,
+                                               float* __restrict__ dst) {
+  const int tsz = n1 * r2 * R, osz = r1 * r2 * R;
+  for (int o = threadIdx.x; o < cnt * tsz; o += S2_THREADS) {   // o = ((s n1 + i) r2 + b) R + rho
+    const int rho = o % R, b = (o / R) % r2, si = o / (R * r2);
+    const float* a = As + (size_t)si * n2 * R + rho;
+    float acc = 0.f;
+    for (int j = 0; j < n2; ++j) acc = fmaf(U2s[j * r2 + b], a[j * R], acc);
+    Ts[o] = acc;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < cnt * osz; o += S2_THREADS) {   // o = ((s r1 + a) r2 + b) R + rho
+    const int rho = o % R, b = (o / R) % r2, a = (o / (R * r2)) % r1, s = o / osz;
+    const float* t = Ts + (size_t)s * tsz + b * R + rho;
+    float acc = 0.f;
+    for (int i = 0; i < n1; ++i) acc = fmaf(U1s[i * r1 + a], t[i * r2 * R], acc);
+    dst[o] = acc;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(S2_THREADS) k_slab2(const T* __restrict__ A, int64_t L, int n1, int n2, int R,
+                                                      int nb, const float* __restrict__ U1, int r1,
+                                                      const float* __restrict__ U2, int r2, float* __restrict__ out) {
+  extern __shared__ __align__(16) float s2m[];
+  constexpr bool F32 = sizeof(T) == 4;
+  const int slab = n1 * n2 * R, osz = r1 * r2 * R;
+  float* As = s2m;
+  float* Ts = As + (F32 ? 2 : 1) * nb * slab;
+  float* U1s = Ts + nb * n1 * r2 * R;
+  float* U2s = U1s + n1 * r1;
+  for (int e = threadIdx.x; e < n1 * r1; e += S2_THREADS) U1s[e] = U1[e];
+  for (int e = threadIdx.x; e < n2 * r2; e += S2_THREADS) U2s[e] = U2[e];
+  const int64_t nbatch = (L + nb - 1) / nb;
+  if constexpr (F32) {
+    const float* Af = reinterpret_cast<const float*>(A);
+    const bool v4 = (slab % 4) == 0 && (reinterpret_cast<uintptr_t>(Af) & 15) == 0;
+    // copies of batch bt into buffer q, one commit group per batch (empty past the end)
+    auto issue = [&](int64_t bt, int q) {
+      if (bt < nbatch) {
+        const int64_t l0 = bt * nb;
+        const int tot = (int)min((int64_t)nb, L - l0) * slab;
+        const float* src = Af + l0 * slab;
+        float* dst = As + q * nb * slab;
+        if (v4) {
+          for (int e = threadIdx.x; e < tot / 4; e += S2_THREADS) cp_async16(dst + 4 * e, src + 4 * e, 16);
+        } else {
+          for (int e = threadIdx.x; e < tot; e += S2_THREADS) cp_async4(dst + e, src + e, 4);
+        }
+      }
+      cp_async_commit();
+    };
+    int q = 0;
+    issue(blockIdx.x, 0);
+    for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x, q ^= 1) {
+      issue(bt + gridDim.x, q ^ 1);          // the next batch streams in meanwhile
+      cp_async_wait<1>();                    // this batch's copies (all but the newest group)
+      __syncthreads();
+      const int64_t l0 = bt * nb;
+      const int cnt = (int)min((int64_t)nb, L - l0);
+      slab2_contract(As + q * nb * slab, Ts, U1s, U2s, cnt, n1, n2, R, r1, r2, out + l0 * osz);
+      __syncthreads();                       // buffer q and Ts are free for the next round
+    }
+    cp_async_wait<0>();
+  } else {
+    for (int64_t bt = blockIdx.x; bt < nbatch; bt += gridDim.x) {
+      const int64_t l0 = bt * nb;
+      const int cnt = (int)min((int64_t)nb, L - l0);
+      const T* src = A + l0 * slab;
+      __syncthreads();
+      for (int e = threadIdx.x; e < cnt * slab; e += S2_THREADS) As[e] = ldf<T>(src, e);
+      __syncthreads();
+      slab2_contract(As, Ts, U1s, U2s, cnt, n1, n2, R, r1, r2, out + l0 * osz);
+    }
+  }
+}
+
+static int slab2_batch(int n1, int n2, int64_t R, int r1, int r2) {
+  if (n1 < 1 || n2 < 1 || R < 1 || r1 < 1 || r2 < 1) return 0;
+  const int64_t slab = (int64_t)n1 * n2 * R, tsz = (int64_t)n1 * r2 * R;
+  if (slab > S2_MAXA || tsz > S2_MAXT || (int64_t)n1 * r1 + (int64_t)n2 * r2 > S2_MAXU) return 0;
+  return (int)std::max<int64_t>(1, std::min(S2_FILL / slab, S2_MAXT / tsz));
+}
+
+static size_t slab2_smem() { return (size_t)(2 * S2_MAXA + S2_MAXT + S2_MAXU) * 4; }
+
 static int g_num_sms = 0;
+
+constexpr int L2_MAXN2 = 256, L2_MAXR1 = 32;
+template <int RW>
+static size_t last2_smem_max() {
+  return ((size_t)L2_MAXN2 * RW + (size_t)TL_THREADS * (RW + 1) + (size_t)TL_THREADS * L2_MAXR1) * 4;
+}
+
+bool last2_fits(int64_t n1, int64_t n2, int r1, int r2) {
+  return n1 >= 1 && n1 <= TL_THREADS && n2 >= 1 && n2 <= L2_MAXN2 && r1 >= 1 && r1 <= L2_MAXR1 && r2 >= 1 &&
+         r2 <= 32;
+}
+
+int launch_last2(const float* X, int64_t S, int64_t n1, int64_t n2, const float* U1, int r1, const float* U2, int r2,
+                 float* out, cudaStream_t st) {
+  if (!last2_fits(n1, n2, r1, r2) || S < 1) return 0;
+  const int spc = TL_THREADS / (int)n1;
+  const int64_t blocks = (S + spc - 1) / spc;
+  if (blocks >= ((int64_t)1 << 31)) return 0;
+  const int rw = r2 <= 8 ? 8 : r2 <= 16 ? 16 : 32;
+  const size_t sm = ((size_t)n2 * rw + (size_t)spc * n1 * (rw + 1) + (size_t)n1 * r1) * 4;
+  if (rw == 8)
+    k_last2<8><<<(unsigned)blocks, TL_THREADS, sm, st>>>(X, S, (int)n1, (int)n2, U1, r1, U2, r2, out);
+  else if (rw == 16)
+    k_last2<16><<<(unsigned)blocks, TL_THREADS, sm, st>>>(X, S, (int)n1, (int)n2, U1, r1, U2, r2, out);
+  else
+    k_last2<32><<<(unsigned)blocks, TL_THREADS, sm, st>>>(X, S, (int)n1, (int)n2, U1, r1, U2, r2, out);
+  return 1;
+}
+
+bool slab2_fits(int64_t n1, int64_t n2, int64_t R, int r1, int r2) {
+  return n1 <= 65536 && n2 <= 65536 && slab2_batch((int)n1, (int)n2, R, r1, r2) > 0;
+}
+
+int launch_slab2(const void* A, int dtype, int64_t L, int64_t n1, int64_t n2, int64_t R, const float* U1, int r1,
+                 const float* U2, int r2, float* out, cudaStream_t st) {
+  if (!slab2_fits(n1, n2, R, r1, r2) || L < 1) return 0;
+  const int nb = slab2_batch((int)n1, (int)n2, R, r1, r2);
+  const int64_t nbatch = (L + nb - 1) / nb;
+  const int64_t cap = (int64_t)std::max(1, g_num_sms) * 8;
+  const unsigned grid = (unsigned)std::min(nbatch, cap);
+  const size_t sm = ((size_t)(dtype == DT_F32 ? 2 : 1) * nb * n1 * n2 * R + (size_t)nb * n1 * r2 * R + n1 * r1 +
+                     n2 * r2) * 4;
+  if (dtype == DT_F32)
+    k_slab2<float><<<grid, S2_THREADS, sm, st>>>(static_cast<const float*>(A), L, (int)n1, (int)n2, (int)R, nb, U1,
+                                                 r1, U2, r2, out);
+  else if (dtype == DT_F64)
+    k_slab2<double><<<grid, S2_THREADS, sm, st>>>(static_cast<const double*>(A), L, (int)n1, (int)n2, (int)R, nb,
+                                                  U1, r1, U2, r2, out);
+  else
+    k_slab2<__nv_bfloat16><<<grid, S2_THREADS, sm, st>>>(static_cast<const __nv_bfloat16*>(A), L, (int)n1,
+                                                         (int)n2, (int)R, nb, U1, r1, U2, r2, out);
+  return 1;
+}
 
 int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, const float* U, int r,
                  float* out, cudaStream_t st) {
@@ -426,6 +654,19 @@ cudaError_t core_init_attributes() {
                              (int)ttm_f32_smem<TN, AW, TK>());
   RT_TTM_ATTR(256, 32, 32) RT_TTM_ATTR(128, 32, 32) RT_TTM_ATTR(256, 16, 16) RT_TTM_ATTR(128, 16, 16)
 #undef RT_TTM_ATTR
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_last2<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)last2_smem_max<8>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_last2<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)last2_smem_max<16>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_last2<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)last2_smem_max<32>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_slab2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab2_smem());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_slab2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)slab2_smem());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_slab2<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)slab2_smem());
   return e;
 }
 

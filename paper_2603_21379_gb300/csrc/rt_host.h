@@ -80,6 +80,18 @@ int launch_ttm_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs
 // Grouped last-mode contractions (every job R = 1, n <= 256, r <= 32): pre counts
 // ttm_last_job_ctas per job; returns 0 when a job does not fit.
 int64_t ttm_last_job_ctas(const TTMJob& q);
+// Two neighbouring modes of small slabs in one read: out(l, a, b, rho) =
+// sum_{i,j} U1[i][a] U2[j][b] A(l, i, j, rho), A (L, n1, n2, R) of the launch's dtype.
+// slab2_fits: whether a slab (n1 n2 R values) and its partial products fit shared
+// memory; launch_slab2 returns 0 when they do not.
+bool slab2_fits(int64_t n1, int64_t n2, int64_t R, int r1, int r2);
+// The last two modes of float32 X (R = 1) of S slabs n1 x n2 (n1 <= 128, n2 <= 256,
+// r1, r2 <= 32): one thread per row, then the slab outputs; 0 when not applicable.
+bool last2_fits(int64_t n1, int64_t n2, int r1, int r2);
+int launch_last2(const float* X, int64_t S, int64_t n1, int64_t n2, const float* U1, int r1, const float* U2, int r2,
+                 float* out, cudaStream_t st);
+int launch_slab2(const void* A, int dtype, int64_t L, int64_t n1, int64_t n2, int64_t R, const float* U1, int r1,
+                 const float* U2, int r2, float* out, cudaStream_t st);
 int launch_ttm_last_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs, int64_t total_ctas,
                             int dtype, int nmax, int rmax, cudaStream_t st);
 cudaError_t core_init_attributes();

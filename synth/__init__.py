@@ -35,6 +35,11 @@ ORDER4_96 = dict(shape=(96, 96, 96, 96), ranks=(16, 16, 16, 16), p=8, seed=4, da
 INVNORM_16_8 = dict(n=16, d=8, lo=1.0, hi=2.0, rank=10, p=5, w=320, seed=3)
 BATCHED_256 = dict(T=256, nmin=32, nmax=160, rmin=4, rmax=24, p=5, seed=2, data_seed=102,
                    noise=1e-6)
+# The paper's single-node scaling workloads (its parallel experiments), one GPU:
+# Tucker of order-8 low-rank tensors, rank 5, n = 16..20, s = 10^4 fibers per mode;
+# H-Tucker of f = 1/||x|| on n^8 grids, rank 6, 20 n fibers per node.
+SCALING_TUCKER = dict(d=8, ns=(16, 18, 20), rank=5, p=5, s=10000, seed=1, noise=1e-6)
+SCALING_HT = dict(d=8, ns=(16, 18, 20), lo=1.0, hi=2.0, rank=6, p=5, w_per_n=20, seed=3)
 
 
 def haar(n, r, rs):
@@ -124,6 +129,33 @@ def inv_norm_tensor_torch(n, d, lo=1.0, hi=2.0, device="cpu"):
             acc = acc + sq.view(shape)              # modes 1..d-1 in order
         out[i0] = (1.0 / torch.sqrt(acc)).to(torch.float32)
     return out
+
+
+def tucker_tensor_torch(shape, core_ranks, noise=0.0, data_seed=0, device="cpu"):
+    """X = C x_1 A_1 ... x_d A_d + noise * N(0,1) as a contiguous float32 torch tensor
+    built on ``device`` (for tensors too large for the host): Gaussian core, factors
+    the Q of Gaussian n x r matrices, drawn from torch's generator seeded with
+    ``data_seed``; the modes are expanded last to first, one batched matrix product
+    each, and the noise is added one slab of the first mode at a time."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(data_seed))
+    d = len(shape)
+    Y = torch.randn(tuple(core_ranks), generator=g, device=device, dtype=torch.float32)
+    A = [torch.linalg.qr(torch.randn((n, r), generator=g, device=device, dtype=torch.float64))[0].float()
+         for n, r in zip(shape, core_ranks)]
+    for k in range(d - 1, -1, -1):     # Y(..., a_k, i_{k+1}, ...) -> Y(..., i_k, i_{k+1}, ...)
+        left = 1
+        for j in range(k):
+            left *= core_ranks[j]
+        right = Y.numel() // (left * core_ranks[k])
+        Y = torch.matmul(A[k], Y.reshape(left, core_ranks[k], right))
+    X = Y.reshape(tuple(shape))
+    if noise:
+        for i0 in range(shape[0]):
+            X[i0].add_(torch.randn(tuple(shape[1:]), generator=g, device=device, dtype=torch.float32),
+                       alpha=noise)
+    return X.contiguous()
 
 
 def batched_shapes(T=256, nmin=32, nmax=160, rmin=4, rmax=24, data_seed=102):

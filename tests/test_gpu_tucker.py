@@ -184,8 +184,8 @@ def test_bf16_compute_form(rt):
     X = synth.tucker_tensor((48, 40, 64, 32), (6, 5, 8, 8), noise=1e-3, data_seed=13)
     Xd = torch.from_numpy(X).cuda()
     r, p, seed = [6, 5, 8, 8], 4, 21
-    G32, U32 = rt.rtucker_decompose(Xd, r, p, seed=seed)
-    G16, U16 = rt.rtucker_decompose(Xd, r, p, seed=seed, prec="bf16")
+    G32, U32 = rt.rtucker_decompose(Xd, r, p, seed=seed, core="tc")
+    G16, U16 = rt.rtucker_decompose(Xd, r, p, seed=seed, prec="bf16", core="tc")
     for a, b in zip(U32, U16):
         assert torch.equal(a, b)
     ref = tucker.sub_r_hosvd(X.astype(np.float64), r, p, seed=seed)
@@ -197,7 +197,7 @@ def test_bf16_compute_form(rt):
     assert 0 < dg < 4e-3
     # the core entry point (pass over X on the final factors) and the decomposition
     # (pass on the QR factors, then the W contractions) round differently
-    Gc = rt.rtucker_core(Xd, U32, prec="bf16")
+    Gc = rt.rtucker_core(Xd, U32, prec="bf16", core="tc")
     assert (Gc - G16).abs().max().item() <= 2e-5 * G16.abs().max().item()
 
 
@@ -210,8 +210,8 @@ def test_bf16_storage_tensor_core_pass(rt, shape, ranks):
     Xb = torch.from_numpy(rs.standard_normal(shape).astype(np.float32)).to(torch.bfloat16).cuda()
     U = [np.linalg.qr(rs.standard_normal((n, k)))[0].astype(np.float32) for n, k in zip(shape, ranks)]
     Ud = [torch.from_numpy(u).cuda() for u in U]
-    Gb = rt.rtucker_core(Xb, Ud)
-    Gf = rt.rtucker_core(Xb.float(), Ud)
+    Gb = rt.rtucker_core(Xb, Ud, core="tc")
+    Gf = rt.rtucker_core(Xb.float(), Ud, core="tc")
     Gr = tucker.multi_ttm_t(Xb.float().cpu().numpy().astype(np.float64), [u.astype(np.float64) for u in U])
     scale = np.abs(Gr).max()
     assert np.abs(to_np(Gf) - Gr).max() <= 1e-5 * scale
@@ -240,7 +240,7 @@ def test_core_tensor_core_pass_odd_slab_height(rt):
     shape, ranks = (7, 6, 33, 12), (3, 4, 5, 7)
     X = rs.standard_normal(shape).astype(np.float32)
     U = [np.linalg.qr(rs.standard_normal((n, k)))[0].astype(np.float32) for n, k in zip(shape, ranks)]
-    G = rt.rtucker_core(torch.from_numpy(X).cuda(), [torch.from_numpy(u).cuda() for u in U])
+    G = rt.rtucker_core(torch.from_numpy(X).cuda(), [torch.from_numpy(u).cuda() for u in U], core="tc")
     Gr = tucker.multi_ttm_t(X.astype(np.float64), [u.astype(np.float64) for u in U])
     assert np.abs(to_np(G) - Gr).max() <= 1e-5 * np.abs(Gr).max()
 
@@ -257,7 +257,7 @@ def test_core_tensor_core_pass_ranks_up_to_64(rt, dtype):
         Xd = Xd.to(torch.bfloat16)
         X = Xd.float().cpu().numpy()
     U = [np.linalg.qr(rs.standard_normal((n, k)))[0].astype(np.float32) for n, k in zip(shape, ranks)]
-    G = rt.rtucker_core(Xd, [torch.from_numpy(u).cuda() for u in U])
+    G = rt.rtucker_core(Xd, [torch.from_numpy(u).cuda() for u in U], core="tc")
     rt.sync()
     Gr = tucker.multi_ttm_t(X.astype(np.float64), [u.astype(np.float64) for u in U])
     assert np.abs(to_np(G) - Gr).max() <= 1e-5 * np.abs(Gr).max()
@@ -272,11 +272,35 @@ def test_core_wide_rho_ragged_tiles(rt):
     X = rs.standard_normal(shape).astype(np.float32)
     U = [np.linalg.qr(rs.standard_normal((n, k)))[0] for n, k in zip(shape, ranks)]
     Ud = [torch.from_numpy(u.astype(np.float32)).cuda() for u in U]
-    G = rt.rtucker_core(torch.from_numpy(X).cuda(), Ud)
+    G = rt.rtucker_core(torch.from_numpy(X).cuda(), Ud, core="tc")
     Uf = [u.astype(np.float32).astype(np.float64) for u in U]
     Gr = tucker.multi_ttm_t(X.astype(np.float64), Uf)
     assert G.shape == tuple(ranks)
     assert np.abs(to_np(G) - Gr).max() <= 1e-4 * np.abs(Gr).max()
+
+
+@pytest.mark.parametrize("shape,ranks,dtype", [
+    ((7, 6, 33, 12), (3, 4, 5, 7), "f32"),      # two two-mode passes (R = 1, then R = 35)
+    ((3,) * 8, (2,) * 8, "f32"),                 # four two-mode passes
+    ((5, 6, 7), (2, 3, 4), "f64"),               # two-mode pass on float64 X, then one mode
+    ((9, 10, 11, 13), (4, 5, 6, 7), "bf16"),     # bfloat16 X
+    ((4, 5, 150, 90), (3, 3, 9, 8), "f32"),      # slab 150 x 90 > shared memory: one-mode chain
+])
+def test_core_two_mode_ffma_passes(rt, shape, ranks, dtype):
+    # small slabs take k_slab2 (two modes per read); its results against the float64
+    # definition for every kernel choice
+    rs = np.random.default_rng(sum(shape))
+    X = rs.standard_normal(shape)
+    Xd = torch.from_numpy(X).cuda()
+    Xd = Xd.to({"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16}[dtype])
+    Xo = Xd.double().cpu().numpy()
+    U = [np.linalg.qr(rs.standard_normal((n, k)))[0].astype(np.float32) for n, k in zip(shape, ranks)]
+    Ud = [torch.from_numpy(u).cuda() for u in U]
+    Gr = tucker.multi_ttm_t(Xo, [u.astype(np.float64) for u in U])
+    for core in ("auto", "ffma", "tc"):
+        G = rt.rtucker_core(Xd, Ud, core=core)
+        rt.sync()
+        assert np.abs(to_np(G) - Gr).max() <= 1e-5 * np.abs(Gr).max(), core
 
 
 def test_invalid_arguments_raise(rt):
