@@ -278,7 +278,7 @@ int launch_root_tiled(const void* X, int dtype, int64_t nl, int64_t nr, const fl
 }
 
 size_t root_pass_scratch_floats(int64_t nl, int64_t nr, int rl, int rr) {
-  return std::max(root_scratch_floats(nl, nr, rl, rr), root_stream_scratch_floats(nl, rl, rr));
+  return std::max(root_scratch_floats(nl, nr, rl, rr), root_stream_scratch_floats(nl, nr, rl, rr));
 }
 
 // dst[row][d0 + c] = src[row][c0 + c], c < nc (column blocks of row-major matrices).

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(RS_THREADS, RS_CTAS_PER_SM) k_root_rows(const 
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nitems = (nl + RS_ROWS - 1) / RS_ROWS;
-  const int64_t nst = nr / RS_COLS;                           // stages per item (nr % 32 == 0)
+  const int64_t nst = nr / RS_COLS;        // stages per item (nr: columns padded to a multiple of 32)
   const uint32_t ubytes = (uint32_t)(RS_COLS * RR * 4);
   if (threadIdx.x == 0) {
     for (int i = 0; i < RS_NS; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], RS_CONS); }
@@ -215,18 +215,30 @@ int launch_rows(const CUtensorMap& map, const float* Ur, int64_t nl, int64_t nr,
 
 }  // namespace
 
-size_t root_stream_scratch_floats(int64_t nl, int rl, int rr) {
-  return (size_t)nl * 2 * rr + (size_t)((nl + RL_ROWS - 1) / RL_ROWS) * rl * rr;
+static int64_t cols_padded(int64_t nr) { return (nr + RS_COLS - 1) / RS_COLS * RS_COLS; }
+
+// T and the partial sums, then (ragged n_r) the padded U_r at a 16-byte boundary
+static size_t stream_base_floats(int64_t nl, int rl, int rr) {
+  return ((size_t)nl * 2 * rr + (size_t)((nl + RL_ROWS - 1) / RL_ROWS) * rl * rr + 3) & ~(size_t)3;
 }
 
-// Streaming root pass for float32 X with n_r % 32 == 0, 16-byte aligned X and U_r
-// and r_l, r_r <= 12.  Returns the number of launches, or 0 when the shape does not
-// qualify (the caller then uses the tiled kernel).  `scratch` holds
-// root_stream_scratch_floats() floats; `reduce` launches the final float64 sum.
+size_t root_stream_scratch_floats(int64_t nl, int64_t nr, int rl, int rr) {
+  const size_t upad = nr % RS_COLS ? (size_t)cols_padded(nr) * rr : 0;
+  return stream_base_floats(nl, rl, rr) + upad;
+}
+
+// Streaming root pass for float32 X with n_r % 4 == 0 (16-byte row stride), 16-byte
+// aligned X and U_r and r_l, r_r <= 12.  When n_r is not a multiple of the 32-column
+// stage, the last stage's TMA box overhangs the rows (the copy fills those columns
+// with zeros) and U_r is first copied into a zero-padded buffer of ceil(n_r / 32) * 32
+// rows, so that every stage's bulk copy of U_r stays inside it.  Returns the number
+// of launches, or 0 when the shape does not qualify (the caller then uses the tiled
+// kernel).  `scratch` holds root_stream_scratch_floats() floats; `reduce` launches the
+// final float64 sum.
 int launch_root_stream(const float* X, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur, int rr,
                        float* BR, float* scratch, int* status, cudaStream_t st) {
-  if (nr % RS_COLS != 0 || rr < 1 || rr > RS_UMAX || rl < 1 || rl > RS_UMAX) return 0;
-  if (nl < 1 || nl >= ((int64_t)1 << 31) || nr >= ((int64_t)1 << 31)) return 0;
+  if (nr % 4 != 0 || rr < 1 || rr > RS_UMAX || rl < 1 || rl > RS_UMAX) return 0;
+  if (nl < 1 || nl >= ((int64_t)1 << 31) || cols_padded(nr) >= ((int64_t)1 << 31)) return 0;
   if ((reinterpret_cast<uintptr_t>(X) & 15u) || (reinterpret_cast<uintptr_t>(Ur) & 15u)) return 0;
   EncodeTiledFn enc = encode_tiled_fn();
   if (!enc) return 0;
@@ -241,10 +253,20 @@ int launch_root_stream(const float* X, int64_t nl, int64_t nr, const float* Ul, 
     return 0;
   float* T = scratch;
   float* part = scratch + (size_t)nl * 2 * rr;
+  const int64_t ncols = cols_padded(nr);
+  const float* Urs = Ur;
   int n = 0;
+  if (ncols != nr) {
+    float* Urp = scratch + stream_base_floats(nl, rl, rr);
+    if ((reinterpret_cast<uintptr_t>(Urp) & 15u) ||
+        cudaMemcpyAsync(Urp, Ur, (size_t)nr * rr * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(Urp + (size_t)nr * rr, 0, (size_t)(ncols - nr) * rr * 4, st) != cudaSuccess)
+      return 0;
+    Urs = Urp;
+  }
   switch (rr) {
 #define RS_CASE(K) \
-  case K: n = launch_rows<K>(map, Ur, nl, nr, T, status, st); break;
+  case K: n = launch_rows<K>(map, Urs, nl, ncols, T, status, st); break;
     RS_CASE(1) RS_CASE(2) RS_CASE(3) RS_CASE(4) RS_CASE(5) RS_CASE(6)
     RS_CASE(7) RS_CASE(8) RS_CASE(9) RS_CASE(10) RS_CASE(11) RS_CASE(12)
 #undef RS_CASE

@@ -161,7 +161,7 @@ int launch_root_tiled(const void* X, int dtype, int64_t nl, int64_t nr, const fl
 int launch_root_stream(const float* X, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur, int rr,
                        float* BR, float* scratch, int* status, cudaStream_t st);
 void launch_root_reduce(const float* part, int64_t nblk, int rl, int rr, float* BR, cudaStream_t st);
-size_t root_stream_scratch_floats(int64_t nl, int rl, int rr);
+size_t root_stream_scratch_floats(int64_t nl, int64_t nr, int rl, int rr);
 size_t root_pass_scratch_floats(int64_t nl, int64_t nr, int rl, int rr);
 size_t root_scratch_floats(int64_t nl, int64_t nr, int rl, int rr);
 

@@ -100,6 +100,15 @@ def test_root_stream_ragged_rows(rt):
     _compare_ht(rt, X, 3, 2, seed=4)
 
 
+def test_root_stream_ragged_columns(rt):
+    # 6 x 5 x 6 x 6: X^(R_l) is 30 x 36, so the streaming root pass runs two 32-column
+    # stages, the second overhanging the rows by 28 zero-filled columns, against a copy
+    # of U_r padded to 64 rows
+    rs = np.random.default_rng(12)
+    X = rs.standard_normal((6, 5, 6, 6)).astype(np.float32)
+    _compare_ht(rt, X, 3, 2, seed=8)
+
+
 def test_root_stream_wide(rt):
     # 12 x 10 x 16 x 40: X^(R_l) is 120 x 640 (two row blocks, 20 column stages), ranks 7
     rs = np.random.default_rng(9)
