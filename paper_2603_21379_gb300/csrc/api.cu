@@ -1867,7 +1867,7 @@ rt_status rtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, cons
   const float* Uk[MAXD];
   size_t off = 0;
   for (int k = 0; k < d; ++k) { Uk[k] = U + off; off += (size_t)n[k] * r[k]; }
-  if ((size_t)r[d - 2] * n[d - 1] * 8 > 200 * 1024) return fail(h, RT_ENOTSUP, "evaluator slab too large");
+  if (!tucker_relerr_supported(d, n, r)) return fail(h, RT_ENOTSUP, "evaluator: r_d above 64 with a large slab");
   double* res = reinterpret_cast<double*>(h->ws + o_res);
   const int nl = launch_tucker_relerr(X, (int)dtype, d, n, r, Uk, G, reinterpret_cast<double*>(h->ws + o), sd, res,
                                       h->stream);

@@ -12,6 +12,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "rt_common.cuh"
 #include "rt_host.h"
 
@@ -106,26 +108,45 @@ __global__ void k_reduce_pairs(const double* __restrict__ part, int nblk, double
 
 constexpr int EV_BLOCKS = 1216;  // 8 x 152 SMs
 
-size_t tucker_relerr_scratch(int d, const int64_t* n, const int32_t* r) {
-  // two ping-pong buffers for the expansions + per-CTA partials
-  size_t best = 1;
+// The last two modes per slab in shared memory (r_{d-2} x n_{d-1} doubles), else the
+// general form: mode d-2 expanded as well, then the rows of n_{d-1} against U_{d-1}.
+static bool relerr_slab_fits(int d, const int64_t* n, const int32_t* r) {
+  return (size_t)r[d - 2] * n[d - 1] * 8 <= 200 * 1024;
+}
+
+bool tucker_relerr_supported(int d, const int64_t* n, const int32_t* r) {
+  return relerr_slab_fits(d, n, r) || r[d - 1] <= CMAX;
+}
+
+// largest expansion buffer (doubles): the leading d-2 modes, and mode d-2 as well in
+// the general form
+static size_t relerr_half(int d, const int64_t* n, const int32_t* r) {
   size_t cur = 1;
   for (int k = 0; k < d; ++k) cur *= (size_t)r[k];
-  best = cur;
+  size_t best = cur;
   for (int k = 0; k + 2 < d; ++k) {
     cur = cur / (size_t)r[k] * (size_t)n[k];
     if (cur > best) best = cur;
   }
-  return 2 * best + 2 * EV_BLOCKS + 16;
+  if (!relerr_slab_fits(d, n, r)) best = std::max(best, cur / (size_t)r[d - 2] * (size_t)n[d - 2]);
+  return best;
 }
+
+size_t tucker_relerr_scratch(int d, const int64_t* n, const int32_t* r) {
+  // two ping-pong buffers for the expansions + per-CTA partials (+ U_{d-1} in float64)
+  const size_t extra = relerr_slab_fits(d, n, r) ? 0 : (size_t)n[d - 1] * r[d - 1];
+  return 2 * relerr_half(d, n, r) + 2 * EV_BLOCKS + 16 + extra;
+}
+
+static int launch_rows_err(const void* X, int dtype, int64_t M, int64_t n2, const double* V, const float* U2,
+                           double* U64, int r2, double* part, double* result2, cudaStream_t st);
 
 int launch_tucker_relerr(const void* X, int dtype, int d, const int64_t* n, const int32_t* r,
                          const float* const* U, const float* G, double* scratch, size_t scratch_doubles,
                          double* result2, cudaStream_t st) {
+  (void)scratch_doubles;
   int nl = 0;
-  size_t cur = 1;
-  for (int k = 0; k < d; ++k) cur *= (size_t)r[k];
-  const size_t half = (scratch_doubles - 2 * EV_BLOCKS - 16) / 2;
+  const size_t half = relerr_half(d, n, r);
   double* bufA = scratch;
   double* bufB = scratch + half;
   double* part = scratch + 2 * half;
@@ -144,6 +165,14 @@ int launch_tucker_relerr(const void* X, int dtype, int d, const int64_t* n, cons
     H = out;
     Hf = nullptr;
     L *= n[k];
+  }
+  if (!relerr_slab_fits(d, n, r)) {
+    double* out = (H == bufA) ? bufB : bufA;
+    const int64_t R = r[d - 1], tot = L * n[d - 2] * R;
+    const unsigned blocks = (unsigned)((tot + 255) / 256 < 65535 * 8 ? (tot + 255) / 256 : 65535 * 8);
+    k_expand_f64<<<blocks, 256, 0, st>>>(H, Hf, L, r[d - 2], R, U[d - 2], n[d - 2], out);
+    return nl + 1 + launch_rows_err(X, dtype, L * n[d - 2], n[d - 1], out, U[d - 1], part + 2 * EV_BLOCKS + 16,
+                                    r[d - 1], part, result2, st);
   }
   const int64_t n1 = n[d - 2], n2 = n[d - 1];
   const int r1 = r[d - 2], r2 = r[d - 1];
@@ -248,6 +277,16 @@ __global__ void __launch_bounds__(256) k_ht_err(const void* __restrict__ X, int 
     part[2 * blockIdx.x] = a;
     part[2 * blockIdx.x + 1] = c;
   }
+}
+
+// err over the M x n2 matrix X against V U2^T (V: M x r2 float64; U2 converted first)
+static int launch_rows_err(const void* X, int dtype, int64_t M, int64_t n2, const double* V, const float* U2,
+                           double* U64, int r2, double* part, double* result2, cudaStream_t st) {
+  const int64_t nu = n2 * r2;
+  k_f32_to_f64<<<(unsigned)((nu + 255) / 256 < 4096 ? (nu + 255) / 256 : 4096), 256, 0, st>>>(U2, U64, nu);
+  k_ht_err<<<EV_BLOCKS, 256, 0, st>>>(X, dtype, M, n2, V, U64, r2, part);
+  k_reduce_pairs<<<1, 1024, 0, st>>>(part, EV_BLOCKS, result2);
+  return 3;
 }
 
 size_t ht_relerr_scratch(int64_t nl, int64_t nr) { (void)nr; return (size_t)nl * CMAX + 2 * EV_BLOCKS + 16; }

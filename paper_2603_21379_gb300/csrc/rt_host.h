@@ -169,6 +169,7 @@ size_t root_scratch_floats(int64_t nl, int64_t nr, int rl, int rr);
 int launch_tucker_relerr(const void* X, int dtype, int d, const int64_t* n, const int32_t* r,
                          const float* const* U, const float* G, double* scratch, size_t scratch_doubles,
                          double* result2, cudaStream_t st);
+bool tucker_relerr_supported(int d, const int64_t* n, const int32_t* r);
 size_t tucker_relerr_scratch(int d, const int64_t* n, const int32_t* r);
 int launch_ht_relerr(const void* X, int dtype, int64_t nl, int64_t nr, const double* Ul, int rl,
                      const float* BR, const double* Ur, int rr, double* scratch, double* result2,

@@ -234,6 +234,19 @@ def test_core_entry_point_and_evaluator(rt):
     assert abs(eg - eh) <= 1e-9
 
 
+@pytest.mark.parametrize("shape,ranks", [((300, 20000), (5, 12)), ((30, 40, 8000), (3, 4, 5))])
+def test_evaluator_general_form(rt, shape, ranks):
+    # r_{d-2} n_{d-1} doubles above 200 KB: mode d-2 expanded as well, then rows of
+    # n_{d-1} against U_{d-1}; against a host float64 reconstruction of the same G, U
+    rs = np.random.default_rng(len(shape))
+    X = rs.standard_normal(shape).astype(np.float32)
+    G = rs.standard_normal(ranks).astype(np.float32)
+    U = [(rs.standard_normal((n, k)) / np.sqrt(n)).astype(np.float32) for n, k in zip(shape, ranks)]
+    eg = rt.rtucker_relerr(torch.from_numpy(X).cuda(), torch.from_numpy(G).cuda(), [torch.from_numpy(u).cuda() for u in U])
+    eh = tucker.relerr(X.astype(np.float64), tucker.reconstruct(G.astype(np.float64), [u.astype(np.float64) for u in U]))
+    assert abs(eg - eh) <= 1e-9, (eg, eh)
+
+
 def test_core_tensor_core_pass_odd_slab_height(rt):
     # float32 X, slabs of 33 x 12: odd n_{d-1} on the tensor-core pass, r = 5 and 7
     rs = np.random.default_rng(15)
