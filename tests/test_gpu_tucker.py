@@ -410,6 +410,32 @@ def test_batched_matches_single_and_oracle(rt):
         assert abs(eg - er) <= RELERR_TOL
 
 
+def test_batched_full_size_256(rt):
+    # the batch the benchmark times (256 order-3 tensors, n_k ~ U{32..160}, one grouped
+    # call): every 32nd tensor against the oracle (factors as subspaces where sampled
+    # singular values sit within 5e-3 of sigma_1, the error of the format), and every
+    # factor of the batch orthonormal
+    cfg = synth.BATCHED_256
+    Xh, shapes, ranks = synth.batched_tensors(cfg["T"], cfg["nmin"], cfg["nmax"], cfg["rmin"], cfg["rmax"],
+                                              cfg["noise"], cfg["data_seed"])
+    Xd = [torch.from_numpy(x).cuda() for x in Xh]
+    seeds = [cfg["seed"] + t for t in range(cfg["T"])]
+    outs = rt.BatchedDecomposition(Xd, ranks, cfg["p"], seeds).run().results()
+    rt.sync()
+    for t in range(cfg["T"]):
+        for u in outs[t][1]:
+            assert orthonormality(to_np(u)) < 1e-5, t
+    for t in range(0, cfg["T"], 32):
+        Gb, Ub = outs[t]
+        ref = tucker.sub_r_hosvd(Xh[t].astype(np.float64), list(ranks[t]), cfg["p"], seed=seeds[t])
+        for k in range(3):
+            _, dev, _ = compare_factor(to_np(Ub[k]), ref["U"][k], ref["modes"][k]["sigma"], gap_min=5e-3)
+            assert dev <= U_TOL, (t, k, dev)
+        eg = rt.rtucker_relerr(Xd[t], Gb, Ub)
+        er = tucker.relerr(Xh[t].astype(np.float64), tucker.reconstruct(ref["G"], ref["U"]))
+        assert abs(eg - er) <= RELERR_TOL, (t, eg, er)
+
+
 @pytest.mark.parametrize("shape,r,p", [((40, 36, 48, 64), (6, 5, 12, 20), 4), ((128, 128, 128, 128), None, None)])
 def test_overlapped_core_schedule(rt, shape, r, p):
     # the pass over X on the QR factors beside the SVD part of the range finder,
