@@ -65,3 +65,31 @@ def test_product_path_never_touches_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"\boracle\b", src), f
+
+
+def test_options_struct_matches_the_header():
+    # the binding's rt_options: same int32 fields, same order, same size as the header
+    import paper_2603_21379_gb300 as rt
+    text = open(HEADER).read()
+    body = re.search(r"typedef struct \{(.*?)\} rt_options;", text, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"int32_t\s+(\w+)(?:\[(\d+)\])?;", body)
+    header = [(name, int(count) if count else 1) for name, count in fields]
+    ours = []
+    for name, ctype in rt._Options._fields_:
+        ours.append((name, getattr(ctype, "_length_", 1)))
+    assert header == ours
+    assert ctypes.sizeof(rt._Options) == 4 * sum(c for _, c in header)
+
+
+def test_option_marshalling():
+    import paper_2603_21379_gb300 as rt
+    assert rt._opts("fp32") is None                      # defaults: no struct
+    o = rt._opts("bf16", overlap=True, graph=True, core="ffma")._obj
+    assert (o.prec, o.overlap, o.use_graph, o.core) == (1, 1, 1, 2)
+    assert list(o.reserved) == [0] * len(o.reserved)
+    assert rt._opts("fp32", core="tc")._obj.core == 1
+    with pytest.raises(ValueError):
+        rt._opts("fp16")
+    with pytest.raises(ValueError):
+        rt._opts("fp32", core="wmma")
