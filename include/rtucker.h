@@ -93,7 +93,12 @@ typedef struct {
                           two-mode FFMA passes over small slabs that fit shared
                           memory, one-mode FFMA contractions otherwise; 1 the
                           tensor-core pass whenever the shape allows it; 2 FFMA
-                          kernels only.  Same result up to rounding.           */
+                          kernels only; 3 tune: on the first call for a shape
+                          (d, n, r, dtype, prec) choices 1 and 2 are each timed
+                          with CUDA events on the call's own buffers (the call
+                          synchronises its stream once) and the faster is kept
+                          in the handle for later calls.  Same result up to
+                          rounding.                                            */
   int32_t reserved[4]; /* must be zero                                          */
 } rt_options;
 

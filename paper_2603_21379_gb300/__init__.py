@@ -264,16 +264,16 @@ def rtucker_factors(X, r, p, s=None, seed=0, with_sigma=False):
 
 
 _PREC = {"fp32": 0, "bf16": 1}
-_CORE = {"auto": 0, "tc": 1, "ffma": 2}
+_CORE = {"auto": 0, "tc": 1, "ffma": 2, "tune": 3}
 
 
 def _opts(prec, overlap=False, graph=False, core="auto"):
     """rt_options for a precision form (the overlapped core schedule, CUDA-graph
-    replay, the core kernels: "auto", "tc" or "ffma"), or None (defaults)."""
+    replay, the core kernels: "auto", "tc", "ffma" or "tune"), or None (defaults)."""
     if prec not in _PREC:
         raise ValueError("prec must be 'fp32' or 'bf16'")
     if core not in _CORE:
-        raise ValueError("core must be 'auto', 'tc' or 'ffma'")
+        raise ValueError("core must be 'auto', 'tc', 'ffma' or 'tune'")
     if prec == "fp32" and not overlap and not graph and core == "auto":
         return None
     o = _Options()

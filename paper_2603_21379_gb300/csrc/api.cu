@@ -11,6 +11,7 @@
 #include <cstdlib>
 
 #include <algorithm>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -119,6 +120,8 @@ struct rt_handle_s {
   // second stream for work that overlaps the pass over X, with fork/join events
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // core kernels picked by timing (rt_options.core = 3), per shape
+  std::map<std::vector<int64_t>, int> core_tuned;
   // CUDA-graph replay: capture stream and cache
   cudaStream_t gstream = nullptr;
   bool capturing = false;            // a graph capture is running (stage timing records nodes)
@@ -602,7 +605,7 @@ rt_status check_opts(rt_handle h, const rt_options* opt) {
   if (!opt) return RT_OK;
   if (opt->prec != RT_PREC_FP32 && opt->prec != RT_PREC_BF16) return fail(h, RT_EINVAL, "unknown precision");
   if (opt->use_graph != 0 && opt->use_graph != 1) return fail(h, RT_EINVAL, "use_graph must be 0 or 1");
-  if (opt->core < 0 || opt->core > 2) return fail(h, RT_EINVAL, "core must be 0, 1 or 2");
+  if (opt->core < 0 || opt->core > 3) return fail(h, RT_EINVAL, "core must be 0, 1, 2 or 3");
   for (int i = 0; i < 4; ++i)
     if (opt->reserved[i]) return fail(h, RT_EINVAL, "reserved option fields must be zero");
   return RT_OK;
@@ -763,6 +766,57 @@ int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_
     --k;
   }
   return nl;
+}
+
+// rt_options.core = 3: the core kernels for this shape picked by timing.  On the
+// first call for (d, n, r, dtype, prec) each fixed choice (1 tensor-core pass where
+// the shape allows, 2 FFMA kernels) runs once to warm up and twice timed with CUDA
+// events on the call's own buffers (U may hold anything then: only the time counts;
+// G is rewritten by the call itself afterwards); the faster is kept for the handle.
+// Stage timing is paused meanwhile.  Returns the choice to use (1 or 2).
+rt_status tune_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
+                    const float* U, float* G, float* bufA, float* bufB, int prec, int* choice) {
+  std::vector<int64_t> key = {d, (int64_t)dtype, prec};
+  for (int k = 0; k < d; ++k) key.push_back(n[k]);
+  for (int k = 0; k < d; ++k) key.push_back(r[k]);
+  auto it = h->core_tuned.find(key);
+  if (it != h->core_tuned.end()) {
+    *choice = it->second;
+    return RT_OK;
+  }
+  const bool timing = h->timing;
+  h->timing = false;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float best = 0.f;
+  int pick = 2;
+  rt_status st = RT_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    st = fail(h, RT_ECUDA, "core tuning: event creation");
+  } else {
+    for (int cand = 1; cand <= 2 && st == RT_OK; ++cand) {
+      enqueue_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec, cand);
+      cudaEventRecord(e0, h->stream);
+      for (int rep = 0; rep < 2; ++rep) enqueue_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec, cand);
+      cudaEventRecord(e1, h->stream);
+      float ms = 0.f;
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        st = cuda_fail(h, e, "core tuning");
+      } else if (cand == 1 || ms < best) {
+        best = ms;
+        pick = cand;
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  h->timing = timing;
+  if (st != RT_OK) return st;
+  h->core_tuned[key] = pick;
+  *choice = pick;
+  return RT_OK;
 }
 
 rt_status ensure_side(rt_handle h) {
@@ -1061,6 +1115,16 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
   if ((st = stage_commit(h, &nl)) != RT_OK) return st;
   if (overlap && (st = ensure_side(h)) != RT_OK) return st;
   if (G && !U) return fail(h, RT_EINVAL, "U is required with G");
+  int core = core_of(opt);
+  if (core == 3) {
+    if (G && !overlap) {
+      if ((st = tune_core(h, X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + o_bufA),
+                          reinterpret_cast<float*>(h->ws + o_bufB), prec_of(opt), &core)) != RT_OK)
+        return st;
+    } else {
+      core = 0;
+    }
+  }
   const bool graph = opt && opt->use_graph;
   GraphKey key;
   if (graph) {
@@ -1120,7 +1184,7 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
         StageTimer tm(h, 2);
         *nk += enqueue_core_rest_overlap(h, d, n, r, p, U, q1.Wsg, q2.Wsg, G, bufA, bufB);
       } else {
-        *nk += enqueue_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec_of(opt), core_of(opt));
+        *nk += enqueue_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec_of(opt), core);
       }
       return RT_OK;
     }
@@ -1131,7 +1195,7 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
     if (Zout) *nk += launch_sketch_sum(Gp.g, reinterpret_cast<float* const*>(h->ws + o_zp), h->stream);
     if (G)
       *nk += enqueue_core(h, X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + o_bufA),
-                          reinterpret_cast<float*>(h->ws + o_bufB), prec_of(opt), core_of(opt));
+                          reinterpret_cast<float*>(h->ws + o_bufB), prec_of(opt), core);
     return RT_OK;
   });
   if (st != RT_OK) return st;
@@ -1332,12 +1396,17 @@ rt_status rtucker_core(rt_handle h, const void* X, rt_dtype dtype, int d, const 
   for (int k = 0; k < d; ++k)
     if (r[k] < 1) return fail(h, RT_EINVAL, "need r_k >= 1");
   if ((st = check_prior_status(h)) != RT_OK) return st;
+  if ((st = init_device_attrs(h)) != RT_OK) return st;
   Bump bump;
   const size_t cb = core_buffer_floats(d, n, r);
   const size_t oA = bump.take(cb * 4), oB = bump.take(cb * 4);
   if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
-  const int nl = enqueue_core(h, X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + oA),
-                              reinterpret_cast<float*>(h->ws + oB), prec_of(opt), core_of(opt));
+  float* bufA = reinterpret_cast<float*>(h->ws + oA);
+  float* bufB = reinterpret_cast<float*>(h->ws + oB);
+  int core = core_of(opt);
+  if (core == 3 && (st = tune_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec_of(opt), &core)) != RT_OK)
+    return st;
+  const int nl = enqueue_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec_of(opt), core);
   return finish(h, nl);
 }
 

@@ -91,5 +91,6 @@ def test_option_marshalling():
     assert rt._opts("fp32", core="tc")._obj.core == 1
     with pytest.raises(ValueError):
         rt._opts("fp16")
+    assert rt._opts("fp32", core="tune")._obj.core == 3
     with pytest.raises(ValueError):
         rt._opts("fp32", core="wmma")

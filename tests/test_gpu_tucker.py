@@ -316,6 +316,29 @@ def test_core_two_mode_ffma_passes(rt, shape, ranks, dtype):
         assert np.abs(to_np(G) - Gr).max() <= 1e-5 * np.abs(Gr).max(), core
 
 
+@pytest.mark.parametrize("shape,ranks", [((7, 6, 33, 12), (3, 4, 5, 7)), ((6, 40, 96, 64), (4, 6, 12, 16))])
+def test_core_tuned_choice(rt, shape, ranks):
+    # core="tune" times the tensor-core pass and the FFMA kernels on the first call for
+    # a shape and keeps the faster: its core is bit-identical to one of the two, on the
+    # core entry point and inside a decomposition, and stays so on later calls
+    rs = np.random.default_rng(sum(shape) + 1)
+    X = synth.tucker_tensor(shape, ranks, 1e-3, 77)
+    Xd = torch.from_numpy(X).cuda()
+    U = [torch.from_numpy(np.linalg.qr(rs.standard_normal((n, k)))[0].astype(np.float32)).cuda()
+         for n, k in zip(shape, ranks)]
+    fixed = [rt.rtucker_core(Xd, U, core=c) for c in ("tc", "ffma")]
+    for _ in range(2):
+        Gt = rt.rtucker_core(Xd, U, core="tune")
+        rt.sync()
+        assert any(torch.equal(Gt, f) for f in fixed)
+    p = 2
+    dec = [rt.rtucker_decompose(Xd, list(ranks), p, seed=5, core=c)[0] for c in ("tc", "ffma")]
+    for _ in range(2):
+        Gd, _ = rt.rtucker_decompose(Xd, list(ranks), p, seed=5, core="tune")
+        rt.sync()
+        assert any(torch.equal(Gd, f) for f in dec)
+
+
 def test_invalid_arguments_raise(rt):
     X = torch.zeros((4, 5, 6), device="cuda")
     with pytest.raises(rt.RtError) as e:
