@@ -94,3 +94,23 @@ def test_option_marshalling():
     assert rt._opts("fp32", core="tune")._obj.core == 3
     with pytest.raises(ValueError):
         rt._opts("fp32", core="wmma")
+
+
+def test_product_never_uses_the_scratch_folder():
+    # nothing tracked imports, reads or runs a file of the untracked working folder
+    import subprocess
+    try:
+        files = subprocess.run(["git", "ls-files"], cwd=ROOT, capture_output=True, text=True,
+                               check=True).stdout.split()
+    except (OSError, subprocess.CalledProcessError):
+        pytest.skip("not a git checkout")
+    pat = re.compile(r"(?<![\w.])_work[/\\.]|import\s+_work|['\"]_work['\"]")
+    hits = []
+    for f in files:
+        if f == ".gitignore" or not f.endswith((".py", ".cu", ".cuh", ".h", ".cpp", ".sh", ".toml", ".cfg")):
+            continue
+        with open(os.path.join(ROOT, f), errors="ignore") as fh:
+            for i, line in enumerate(fh, 1):
+                if pat.search(line):
+                    hits.append("%s:%d" % (f, i))
+    assert not hits, hits
