@@ -239,8 +239,13 @@ rt_status rtucker_core_adjoint(rt_handle h, const void* X, rt_dtype dtype, int d
                                float* Ubar);
 
 /* Relative reconstruction error ||X - (U_1..U_d) G||_F / ||X||_F computed on
- * the device in float64 (evaluator; not part of the decomposition).  The
- * result is written to *out (HOST) after the call synchronises the stream. */
+ * the device in float64 (evaluator; not part of the decomposition; Sec. 3.3
+ * reports this measure).  G (r_1 x ... x r_d, C order) and the concatenated
+ * U_k (n_k x r_k row-major) are device float32.  The last two modes are formed
+ * per slab when r_{d-1} n_d doubles fit 200 KB, else mode d-1 is expanded as
+ * well and the rows of n_d are measured against U_d (r_d <= 64; RT_ENOTSUP
+ * beyond).  The result is written to *out (HOST) after the call synchronises
+ * the stream. */
 rt_status rtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
                          const int32_t* r, const float* U, const float* G, double* out);
 
