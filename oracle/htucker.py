@@ -96,6 +96,16 @@ def default_w(shape, nodes):
     return [0 if nd.id == 0 else min(20 * n, node_cols(shape, nd)) for nd in nodes]
 
 
+def alpha_w(shape, nodes, alpha):
+    """w_S = min(floor(alpha^(d-2) n_S), n_{notin S}) at every non-root node: the
+    sampling rule of the paper's serial H-Tucker tests (Sec. 4.2), n_S the rows of
+    the node's unfolding; the root takes none (0)."""
+    d = len(shape)
+    scale = float(alpha) ** (d - 2)
+    return [0 if nd.id == 0 else min(int(np.floor(scale * node_rows(shape, nd))), node_cols(shape, nd))
+            for nd in nodes]
+
+
 def sub_r_rtl_ht(X, rank, p, w=None, seed=0, tree=None, with_root=True):
     """[{U_k}, {B_S}] = Sub-R-RtL-HT(X, T, r, w, p) (Alg. 2).
 

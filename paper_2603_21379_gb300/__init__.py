@@ -20,7 +20,7 @@ __all__ = [
     "load_library", "library_path", "RtError", "sync",
     "rtucker_indices", "rtucker_sketch", "rtucker_factors", "rtucker_core", "rtucker_decompose",
     "rtucker_decompose_host", "rtucker_decompose_host_async", "rtucker_decompose_batched", "rtucker_relerr",
-    "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "last_launch_count", "workspace_bytes",
+    "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "ht_alpha_w", "last_launch_count", "workspace_bytes",
     "set_timing", "get_timing", "STAGES", "rhtucker_root_transfer_noalloc", "BatchedDecomposition",
     "rtucker_loss_grad", "rtucker_core_adjoint",
 ]
@@ -533,6 +533,20 @@ def ht_tree(d):
             nodes.append([mid, b, -1, -1, lev + 1])
         q += 1
     return [tuple(x) for x in nodes]
+
+
+def ht_alpha_w(shape, alpha):
+    """Samples per node of the balanced tree by the alpha rule,
+    w_S = min(floor(alpha^(d-2) n_S), n_{notin S}) (n_S rows of the node's unfolding;
+    the root entry is 0), for the ``w`` argument of ``rhtucker_decompose``."""
+    d = len(shape)
+    total = _prod(shape)
+    scale = float(alpha) ** (d - 2)
+    out = []
+    for i, (a, b, _, _, _) in enumerate(ht_tree(d)):
+        rows = _prod(shape[a:b + 1])
+        out.append(0 if i == 0 else min(int(scale * rows), total // rows))
+    return out
 
 
 def _ht_ranks(d, rank):

@@ -205,3 +205,18 @@ def test_inv_norm_workload_ht_runs_and_is_accurate():
     out = htucker.sub_r_rtl_ht(X, 5, p=3, seed=3)
     Xh = htucker.reconstruct(out["U"], out["B"], out["tree"], X.shape)
     assert tucker.relerr(X, Xh) < 1e-2
+
+
+def test_alpha_sampling_rule():
+    # Sec. 4.2: min(alpha^(d-2) n_S, n_notin_S) fibers at node S, n_S its unfolding's rows.
+    # 3 x 4 x 5 x 6, alpha = 2 (scale 4), worked by hand: {0,1} 12 rows -> min(48, 30);
+    # {2,3} 30 rows -> min(120, 12); leaves 3, 4, 5, 6 rows -> 12, 16, 20, 24
+    shape = (3, 4, 5, 6)
+    nodes = htucker.balanced_tree(4)
+    assert htucker.alpha_w(shape, nodes, 2) == [0, 30, 12, 12, 16, 20, 24]
+    # the binding's helper (host arithmetic, no GPU) follows the same rule on the same tree
+    import paper_2603_21379_gb300 as rt
+    assert rt.ht_alpha_w(shape, 2) == [0, 30, 12, 12, 16, 20, 24]
+    for shape, alpha in [((2, 3, 4, 5, 6), 1.5), ((16,) * 8, 1.2), ((7, 5, 9), 3.0)]:
+        nodes = htucker.balanced_tree(len(shape))
+        assert rt.ht_alpha_w(shape, alpha) == htucker.alpha_w(shape, nodes, alpha)
