@@ -104,9 +104,12 @@ typedef struct {
 
 /* ----------------------------------------------------------- handle
  * rt_create: new handle bound to `stream` (a cudaStream_t; NULL = legacy
- * default stream) on the current device.  rt_destroy frees the workspace.
- * rt_sync waits for the stream and returns the device status word (then
- * clears it).  rt_last_error: message of the last failure on this handle. */
+ * default stream) on the current device.  rt_destroy waits for the handle's
+ * work and frees its workspace, staging buffers and captured graphs.
+ * rt_set_stream: later calls enqueue on `stream` (the caller orders it after
+ * any earlier work of the handle).  rt_sync waits for the stream and returns
+ * the device status word (then clears it).  rt_last_error: message of the last
+ * failure on this handle (owned by the handle, valid until its next call). */
 rt_status rt_create(rt_handle* h, void* stream);
 rt_status rt_destroy(rt_handle h);
 rt_status rt_set_stream(rt_handle h, void* stream);
@@ -175,9 +178,10 @@ rt_status rtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, c
                             const int32_t* r, int32_t p, const int64_t* s, uint64_t seed,
                             const rt_options* opt, float* U, float* G);
 
-/* Same as rtucker_decompose with X, U and G in HOST memory (pinned memory
- * recommended): X is copied to device workspace, the decomposition runs, and
- * U and G are copied back; the call returns after the copies completed. */
+/* Same as rtucker_decompose (Alg. 1) with X, U and G in HOST memory (pinned
+ * memory recommended): X is copied to device workspace, the decomposition
+ * runs, and U and G are copied back; the call returns after the copies
+ * completed. */
 rt_status rtucker_decompose_host(rt_handle h, const void* X_host, rt_dtype dtype, int d,
                                  const int64_t* n, const int32_t* r, int32_t p, const int64_t* s,
                                  uint64_t seed, const rt_options* opt, float* U_host, float* G_host);
@@ -199,10 +203,14 @@ rt_status rtucker_decompose_host_async(rt_handle h, const void* X_host, rt_dtype
                                        const int64_t* n, const int32_t* r, int32_t p, const int64_t* s,
                                        uint64_t seed, const rt_options* opt, float* U_host, float* G_host);
 
-/* Batched Sub-R-HOSVD: T independent tensors (tensor t: X[t], order d[t],
- * sizes n[t][.], ranks r[t][.], samples s[t] or s == NULL / s[t] == NULL for
- * the default, seed seeds[t]) decomposed with one grouped launch per stage for
- * all (tensor, mode) problems.  X, U, G: HOST arrays of DEVICE pointers. */
+/* Batched Sub-R-HOSVD (Alg. 1 for each tensor; the modes of all tensors are
+ * independent problems, as the modes of one are in Sec. 3.3): T independent
+ * tensors (tensor t: X[t], order d[t], sizes n[t][.], ranks r[t][.], samples
+ * s[t] or s == NULL / s[t] == NULL for the default, seed seeds[t]) decomposed
+ * with one grouped launch per stage for all (tensor, mode) problems and one per
+ * contraction level of the cores.  X, U, G: HOST arrays of DEVICE pointers
+ * (U[t] and G[t] laid out as for rtucker_decompose); argument errors of any
+ * tensor fail the whole call before anything is enqueued. */
 rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt_dtype dtype,
                                     const int32_t* d, const int64_t* const* n,
                                     const int32_t* const* r, int32_t p,
@@ -275,8 +283,10 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
                              const int32_t* rank, int32_t p, const int64_t* w, uint64_t seed,
                              const rt_options* opt, float* U_leaf, float* B, float* U_nodes);
 
-/* Relative error of the H-Tucker format (U_leaf, B) against X, float64 on the
- * device; *out (HOST) written after the call synchronises.  Ranks 1..64. */
+/* Relative error ||X - X_hat||_F / ||X||_F of the H-Tucker format (U_leaf, B,
+ * laid out as rhtucker_decompose writes them) against X, with X_hat rebuilt
+ * through the nested node bases (Sec. 4); float64 on the device; *out (HOST)
+ * written after the call synchronises.  Ranks 1..64. */
 rt_status rhtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
                           const int32_t* rank, const float* U_leaf, const float* B, double* out);
 
