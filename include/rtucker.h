@@ -135,6 +135,29 @@ size_t rt_workspace_bytes(rt_handle h);
 rt_status rt_set_timing(rt_handle h, int enable);
 rt_status rt_get_timing(rt_handle h, double* ms, int64_t* count, int nmax, int reset);
 
+/* ----------------------------------------------------------- failure handling
+ * Not part of the paper's method: the library's own failure paths, made
+ * testable without faulting or hanging a GPU.
+ *
+ * rt_set_wait_limit: poll limit of every bounded mbarrier wait in the library's
+ * TMA pipelines (the tensor-core pass over X, the streaming root pass), for the
+ * device of `h` and every handle on it (0 = the default, 2^22 polls).  A wait
+ * that runs out records RT_ETIMEOUT in the handle's status word (returned by
+ * rt_sync or the next call), its CTA stops and frees what it holds, and the
+ * context stays usable.  Synchronous; not while a call of another handle on
+ * the device is running.
+ * rt_selftest_wait: enqueues one CTA that waits, through that bounded wait, on a
+ * barrier nothing arrives on: rt_sync(h) then returns RT_ETIMEOUT (after the
+ * limit's polls; use a small limit) and clears the status word.
+ * rt_inject_fault(h, RT_FAULT_ALLOC, count): the handle's next `count` device
+ * workspace growths fail exactly as a failed cudaMalloc does (RT_ENOMEM, the
+ * outputs untouched, nothing enqueued); count 0 clears.  The environment
+ * variable RT_FAULT=alloc[:count] sets the same for every new handle. */
+#define RT_FAULT_ALLOC 1
+rt_status rt_set_wait_limit(rt_handle h, uint32_t polls);
+rt_status rt_selftest_wait(rt_handle h);
+rt_status rt_inject_fault(rt_handle h, int kind, int count);
+
 /* ----------------------------------------------------------- Sub-R-HOSVD
  * Shared arguments (Alg. 1 inputs):
  *   X      device, d-way C-order tensor of sizes n[0..d-1], storage `dtype`;
@@ -258,10 +281,22 @@ rt_status rtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, cons
                          const int32_t* r, const float* U, const float* G, double* out);
 
 /* ----------------------------------------------------------- Sub-R-RtL-HT
- * rhtucker_decompose (Alg. 2) on the balanced dimension tree (the node {a..b}
- * splits into its first ceil(len/2) modes and the rest; nodes numbered level
- * by level, left to right: for d = 8 the paper's heap numbering, root 0,
- * leaves 7..14).  The tree has 2d-1 nodes.
+ * rhtucker_decompose: Sub-R-RtL-HT(X, T, r, w, p) (Alg. 2) on the dimension
+ * tree T (Sec. 4: a binary tree whose root holds every mode, whose leaves are
+ * single modes, and whose internal nodes are the disjoint union of their two
+ * children).  The tree has 2d-1 nodes.
+ *   tree        host child table of 2 (2d-1) int32: tree[2i], tree[2i+1] are the
+ *               left and right child ids of node i, both -1 for a leaf; node 0 is
+ *               the root.  The leaves hold the modes 0..d-1 in left-to-right
+ *               order, so every node is a contiguous mode range {a..b} whose left
+ *               child holds the first modes (natural order: the rows of the set
+ *               unfolding X^(S) and of U_{S_l} (x) U_{S_r} are C-order with the
+ *               left child slower).  Node ids are free otherwise; the id is the
+ *               node's random-stream id.  RT_EINVAL for a table that is not such
+ *               a tree.  NULL: the balanced tree (node {a..b} splits into its
+ *               first ceil(len/2) modes and the rest; nodes numbered level by
+ *               level, left to right: for d = 8 the paper's heap numbering, root
+ *               0, leaves 7..14).
  *   rank[node]  rank per node (host, 2d-1 entries; rank[0] is ignored: the
  *               root rank is 1);  p oversampling;
  *   w[node]     samples per node (host) or NULL for
@@ -280,15 +315,17 @@ rt_status rtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, cons
  * permutation.  A root right-child rank above 12 costs one pass over X per
  * chunk of at most 12 columns of U_{R_r} (ceil(r / 12) passes). */
 rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
-                             const int32_t* rank, int32_t p, const int64_t* w, uint64_t seed,
-                             const rt_options* opt, float* U_leaf, float* B, float* U_nodes);
+                             const int32_t* tree, const int32_t* rank, int32_t p, const int64_t* w,
+                             uint64_t seed, const rt_options* opt, float* U_leaf, float* B, float* U_nodes);
 
 /* Relative error ||X - X_hat||_F / ||X||_F of the H-Tucker format (U_leaf, B,
- * laid out as rhtucker_decompose writes them) against X, with X_hat rebuilt
- * through the nested node bases (Sec. 4); float64 on the device; *out (HOST)
- * written after the call synchronises.  Ranks 1..64. */
+ * laid out as rhtucker_decompose writes them for the same `tree`, NULL =
+ * balanced) against X, with X_hat rebuilt through the nested node bases
+ * (Sec. 4); float64 on the device; *out (HOST) written after the call
+ * synchronises.  Ranks 1..64. */
 rt_status rhtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
-                          const int32_t* rank, const float* U_leaf, const float* B, double* out);
+                          const int32_t* tree, const int32_t* rank, const float* U_leaf, const float* B,
+                          double* out);
 
 /* ----------------------------------------------------------- without allocation
  * rhtucker_root_transfer_noalloc: the root transfer tensor of an H-Tucker
@@ -298,15 +335,20 @@ rt_status rhtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, con
  * frameworks that own all device memory, loops that must avoid the implicit
  * synchronisation of cudaMalloc/cudaFree).  The paper has no counterpart: it
  * is this library's allocation-free form of the root pass of
- * rhtucker_decompose, with the same kernels and results.
+ * rhtucker_decompose.  It runs the tiled root kernel of rhtucker_decompose (which
+ * streams float32 X through TMA where the shape allows); results agree with
+ * rhtucker_decompose to float32 rounding.
  *   - Allocates nothing: no handle, no workspace.  Its scratch is a static
  *     device array of RT_ROOT_NOALLOC_MAX_PARTIALS floats (4 MiB) that every
  *     GPU loading the library holds until the process exits.  The call needs
  *     ceil(nr / 8192) * ceil(nl / 512) * rl * rr of them; larger problems, or
- *     rr > 12, return RT_ENOTSUP.  Null pointers or sizes out of range return
- *     RT_EINVAL.
- *   - X, Ul, Ur, BR are device pointers owned by the caller; `stream` is a
+ *     rr > 12, return RT_ENOTSUP.  Null pointers, an unknown dtype or sizes out
+ *     of range (nl, nr, rl, rr < 1; nl > 2^31; nr > 2^40) return RT_EINVAL.
+ *   - X (nl * nr elements of `dtype`, C order), Ul, Ur (float32) and BR
+ *     (float32, rl * rr) are device pointers owned by the caller; `stream` is a
  *     cudaStream_t (NULL = legacy default stream).  Asynchronous on `stream`.
+ *   - RT_ECUDA if a CUDA call of its own fails (the error stays pending in the
+ *     runtime; errors pending before the call are neither reported nor cleared).
  *   - The first call on a device resolves the device address of the static
  *     array (cudaGetSymbolAddress) with that device current; make that first
  *     call before any stream capture.

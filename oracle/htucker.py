@@ -56,6 +56,40 @@ def balanced_tree(d):
     return nodes
 
 
+def tree_from_children(children):
+    """Dimension tree from a child table: children[i] = (left, right) node ids of
+    node i, (-1, -1) for a leaf, node 0 the root.  The leaves are the single modes
+    0..d-1 taken left to right, so each node is the contiguous range of the leaves
+    below it, its left child's modes first (any binary tree over the modes in
+    their natural order, Sec. 4's definition of a dimension tree with natural
+    unfolding order).  Node ids are the table's indices."""
+    nn = len(children)
+    nodes = [None] * nn
+    leaves = []
+
+    def visit(i, parent, level):
+        l, r = children[i]
+        if l < 0:
+            nodes[i] = Node(i, len(leaves), len(leaves), parent, level)
+            leaves.append(i)
+            return
+        visit(l, i, level + 1)
+        visit(r, i, level + 1)
+        nd = Node(i, nodes[l].a, nodes[r].b, parent, level)
+        nd.left, nd.right = l, r
+        nodes[i] = nd
+
+    visit(0, -1, 0)
+    if any(nd is None for nd in nodes) or nn != 2 * len(leaves) - 1:
+        raise ValueError("not a binary dimension tree")
+    return nodes
+
+
+def children_of(tree):
+    """Child table [(left, right), ...] of a tree given as a list of Nodes."""
+    return [(-1, -1) if nd.is_leaf else (nd.left, nd.right) for nd in tree]
+
+
 def node_rows(shape, nd):
     return int(np.prod(shape[nd.a:nd.b + 1]))
 

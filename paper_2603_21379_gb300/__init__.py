@@ -20,9 +20,9 @@ __all__ = [
     "load_library", "library_path", "RtError", "sync",
     "rtucker_indices", "rtucker_sketch", "rtucker_factors", "rtucker_core", "rtucker_decompose",
     "rtucker_decompose_host", "rtucker_decompose_host_async", "rtucker_decompose_batched", "rtucker_relerr",
-    "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "ht_alpha_w", "last_launch_count", "workspace_bytes",
+    "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "ht_tree_from_children", "ht_alpha_w", "last_launch_count", "workspace_bytes",
     "set_timing", "get_timing", "STAGES", "rhtucker_root_transfer_noalloc", "BatchedDecomposition",
-    "rtucker_loss_grad", "rtucker_core_adjoint",
+    "rtucker_loss_grad", "rtucker_core_adjoint", "set_wait_limit", "selftest_wait", "inject_fault",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -95,10 +95,13 @@ def load_library():
         "rtucker_loss_grad": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, vp, vp, vp, vp, vp,
                                              vp]),
         "rtucker_core_adjoint": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, vp, vp, vp, vp]),
-        "rhtucker_decompose": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, i32, P64, u64, PO,
-                                              vp, vp, vp]),
-        "rhtucker_relerr": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, vp, vp, PD]),
+        "rhtucker_decompose": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, P32, i32, P64, u64,
+                                              PO, vp, vp, vp]),
+        "rhtucker_relerr": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, P32, vp, vp, PD]),
         "rhtucker_root_transfer_noalloc": (ctypes.c_int, [vp, ctypes.c_int, i64, i64, vp, i32, vp, i32, vp, vp]),
+        "rt_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_uint32]),
+        "rt_selftest_wait": (ctypes.c_int, [vp]),
+        "rt_inject_fault": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -535,15 +538,60 @@ def ht_tree(d):
     return [tuple(x) for x in nodes]
 
 
-def ht_alpha_w(shape, alpha):
-    """Samples per node of the balanced tree by the alpha rule,
-    w_S = min(floor(alpha^(d-2) n_S), n_{notin S}) (n_S rows of the node's unfolding;
-    the root entry is 0), for the ``w`` argument of ``rhtucker_decompose``."""
+def ht_tree_from_children(children):
+    """Dimension tree from a child table [(left, right), ...] (node 0 the root, (-1, -1)
+    for a leaf), as the C ABI takes it: list of (a, b, left, right, level), the leaves
+    holding the modes 0..d-1 in left-to-right order.  Raises ValueError for a table
+    that is not a binary tree over 2d-1 nodes."""
+    nn = len(children)
+    if nn < 3 or nn % 2 == 0:
+        raise ValueError("a dimension tree has 2d-1 >= 3 nodes")
+    out = [[-1, -1, int(l), int(r), 0] for (l, r) in children]
+    seen = set()
+
+    def walk(i, lev, mode):
+        if i in seen or not 0 <= i < nn:
+            raise ValueError("not a tree")
+        seen.add(i)
+        out[i][4] = lev
+        l, r = out[i][2], out[i][3]
+        if (l < 0) != (r < 0):
+            raise ValueError("node %d has one child" % i)
+        if l < 0:
+            out[i][0] = out[i][1] = mode
+            return mode + 1
+        m = walk(l, lev + 1, mode)
+        m = walk(r, lev + 1, m)
+        out[i][0], out[i][1] = out[l][0], out[r][1]
+        return m
+
+    walk(0, 0, 0)
+    if len(seen) != nn:
+        raise ValueError("not every node is reachable from the root")
+    return [tuple(x) for x in out]
+
+
+def _tree_args(d, tree):
+    """(node tuples, child-table pointer for the C ABI or None) of ``tree``: None for
+    the balanced tree, else a child table [(left, right), ...]."""
+    if tree is None:
+        return ht_tree(d), None
+    nodes = ht_tree_from_children(tree)
+    if len(nodes) != 2 * d - 1:
+        raise ValueError("the tree must have 2d-1 = %d nodes" % (2 * d - 1))
+    return nodes, _i32([v for lr in tree for v in lr])
+
+
+def ht_alpha_w(shape, alpha, tree=None):
+    """Samples per node by the alpha rule, w_S = min(floor(alpha^(d-2) n_S), n_{notin S})
+    (n_S rows of the node's unfolding; the root entry is 0), for the ``w`` argument of
+    ``rhtucker_decompose`` (balanced tree, or the child table ``tree``)."""
     d = len(shape)
     total = _prod(shape)
     scale = float(alpha) ** (d - 2)
     out = []
-    for i, (a, b, _, _, _) in enumerate(ht_tree(d)):
+    nodes, _ = _tree_args(d, tree)
+    for i, (a, b, _, _, _) in enumerate(nodes):
         rows = _prod(shape[a:b + 1])
         out.append(0 if i == 0 else min(int(scale * rows), total // rows))
     return out
@@ -556,73 +604,112 @@ def _ht_ranks(d, rank):
     return rk
 
 
-def rhtucker_decompose(X, rank, p, w=None, seed=0, return_nodes=False, graph=False, out=None):
-    """Sub-R-RtL-HT on the balanced tree.  Returns (U_leaf list, B dict node->
-    transfer tensor) and, with ``return_nodes``, the node bases U_S.  ``graph``
-    replays the kernel sequence as a CUDA graph for repeated calls with the same
-    buffers and shapes (rt_options.use_graph); ``out`` = (U_leaf flat, B flat[,
-    U_nodes flat]) reuses output buffers so that their pointers repeat."""
+def rhtucker_decompose(X, rank, p, w=None, seed=0, return_nodes=False, graph=False, out=None, tree=None):
+    """Sub-R-RtL-HT (Alg. 2) on the dimension tree ``tree`` (a child table
+    [(left, right), ...], node 0 the root, (-1, -1) for leaves; None = the balanced
+    tree).  Returns (U_leaf list, B dict node -> transfer tensor) and, with
+    ``return_nodes``, the node bases U_S.  ``graph`` replays the kernel sequence as a
+    CUDA graph for repeated calls with the same buffers and shapes
+    (rt_options.use_graph); ``out`` = (U_leaf flat, B flat[, U_nodes flat]) reuses
+    output buffers so that their pointers repeat."""
     lib = load_library()
     dt, d, n = _tensor_args(X)
-    tree = ht_tree(d)
+    nodes, tab = _tree_args(d, tree)
     rk = _ht_ranks(d, rank)
-    nrows = [_prod(n[a:b + 1]) for (a, b, _, _, _) in tree]
-    leaves = sorted((i for i, t in enumerate(tree) if t[0] == t[1]), key=lambda i: tree[i][0])
-    internal = [i for i, t in enumerate(tree) if t[0] != t[1]]
-    Bsz = [rk[i] * rk[tree[i][2]] * rk[tree[i][3]] for i in internal]
+    nrows = [_prod(n[a:b + 1]) for (a, b, _, _, _) in nodes]
+    leaves = sorted((i for i, t in enumerate(nodes) if t[0] == t[1]), key=lambda i: nodes[i][0])
+    internal = [i for i, t in enumerate(nodes) if t[0] != t[1]]
+    Bsz = [rk[i] * rk[nodes[i][2]] * rk[nodes[i][3]] for i in internal]
     Un = None
     if out is not None:
         Ul, B = out[0], out[1]
         if return_nodes:
             Un = out[2]
     else:
-        Ul = torch.empty(sum(n[tree[i][0]] * rk[i] for i in leaves), dtype=torch.float32, device=X.device)
+        Ul = torch.empty(sum(n[nodes[i][0]] * rk[i] for i in leaves), dtype=torch.float32, device=X.device)
         B = torch.empty(sum(Bsz), dtype=torch.float32, device=X.device)
         if return_nodes:
-            Un = torch.empty(sum(nrows[i] * rk[i] for i in range(1, len(tree))), dtype=torch.float32,
+            Un = torch.empty(sum(nrows[i] * rk[i] for i in range(1, len(nodes))), dtype=torch.float32,
                              device=X.device)
     h = _handle(X.device.index)
-    wp = _i64(_as_list(w, len(tree))) if w is not None else None
-    _check(h, lib.rhtucker_decompose(h, _ptr(X), dt, d, _i64(n), _i32(rk), int(p), wp, ctypes.c_uint64(seed),
-                                     _opts("fp32", graph=graph), _ptr(Ul), _ptr(B), _ptr(Un)))
-    U_leaf = _split(Ul, [n[tree[i][0]] for i in leaves], [rk[i] for i in leaves])
+    wp = _i64(_as_list(w, len(nodes))) if w is not None else None
+    _check(h, lib.rhtucker_decompose(h, _ptr(X), dt, d, _i64(n), tab, _i32(rk), int(p), wp,
+                                     ctypes.c_uint64(seed), _opts("fp32", graph=graph), _ptr(Ul), _ptr(B),
+                                     _ptr(Un)))
+    U_leaf = _split(Ul, [n[nodes[i][0]] for i in leaves], [rk[i] for i in leaves])
     Bd, off = {}, 0
     for i, sz in zip(internal, Bsz):
-        Bd[i] = B[off:off + sz].view(rk[i], rk[tree[i][2]], rk[tree[i][3]])
+        Bd[i] = B[off:off + sz].view(rk[i], rk[nodes[i][2]], rk[nodes[i][3]])
         off += sz
     if return_nodes:
-        Ud = dict(zip(range(1, len(tree)), _split(Un, nrows[1:], rk[1:])))
+        Ud = dict(zip(range(1, len(nodes)), _split(Un, nrows[1:], rk[1:])))
         return U_leaf, Bd, Ud
     return U_leaf, Bd
 
 
-def rhtucker_relerr(X, U_leaf, B, rank):
-    """Relative error of an H-Tucker result against X, float64 on the device."""
+def rhtucker_relerr(X, U_leaf, B, rank, tree=None):
+    """Relative error of an H-Tucker result (on the same ``tree`` as its
+    decomposition) against X, float64 on the device."""
     lib = load_library()
     dt, d, n = _tensor_args(X)
-    tree = ht_tree(d)
+    nodes, tab = _tree_args(d, tree)
     rk = _ht_ranks(d, rank)
-    internal = [i for i, t in enumerate(tree) if t[0] != t[1]]
+    internal = [i for i, t in enumerate(nodes) if t[0] != t[1]]
     Uc = _cat_u(U_leaf)
     Bc = torch.cat([B[i].reshape(-1) for i in internal]).to(torch.float32).contiguous()
     out = ctypes.c_double()
     h = _handle(X.device.index)
-    _check(h, lib.rhtucker_relerr(h, _ptr(X), dt, d, _i64(n), _i32(rk), _ptr(Uc), _ptr(Bc), ctypes.byref(out)))
+    _check(h, lib.rhtucker_relerr(h, _ptr(X), dt, d, _i64(n), tab, _i32(rk), _ptr(Uc), _ptr(Bc),
+                                  ctypes.byref(out)))
     return out.value
 
 
 def rhtucker_root_transfer_noalloc(X, Ul, Ur, out=None):
     """Root transfer tensor U_l^T X_mat U_r (1 x r_l x r_r) without any device
     allocation by the library (its scratch is a fixed static device array).
-    ``out`` must be preallocated by callers that cannot allocate either."""
+    ``out`` must be preallocated by callers that cannot allocate either.  X is
+    viewed as an n_l x n_r matrix (n_l, n_r the rows of Ul and Ur)."""
     lib = load_library()
     dt, _, _ = _tensor_args(X)
+    if Ul.dim() != 2 or Ur.dim() != 2:
+        raise ValueError("Ul and Ur must be matrices")
     nl, rl = int(Ul.shape[0]), int(Ul.shape[1])
     nr, rr = int(Ur.shape[0]), int(Ur.shape[1])
+    if X.numel() != nl * nr:
+        raise ValueError("X has %d elements, Ul and Ur need n_l * n_r = %d" % (X.numel(), nl * nr))
+    for name, t in (("Ul", Ul), ("Ur", Ur)):
+        if t.dtype != torch.float32 or not t.is_contiguous() or t.device != X.device:
+            raise ValueError("%s must be a contiguous float32 tensor on X's device" % name)
     if out is None:
         out = torch.empty((1, rl, rr), dtype=torch.float32, device=X.device)
+    elif (out.dtype != torch.float32 or not out.is_contiguous() or out.device != X.device
+          or tuple(out.shape) != (1, rl, rr)):
+        raise ValueError("out must be a contiguous float32 tensor of shape (1, %d, %d) on X's device" % (rl, rr))
     st = lib.rhtucker_root_transfer_noalloc(_ptr(X), dt, nl, nr, _ptr(Ul), rl, _ptr(Ur), rr, _ptr(out),
                                             ctypes.c_void_p(torch.cuda.current_stream(X.device).cuda_stream))
     if st != 0:
         raise RtError(st, lib.rt_status_string(st).decode())
     return out
+
+
+# ----------------------------------------------------------------- failure handling
+FAULT_ALLOC = 1
+
+
+def set_wait_limit(polls=0, device=None):
+    """Poll limit of the library's bounded mbarrier waits on ``device`` (0 = default)."""
+    h = _handle(device)
+    _check(h, load_library().rt_set_wait_limit(h, int(polls)))
+
+
+def selftest_wait(device=None):
+    """Enqueue the bounded-wait self-test (a wait nothing ends); ``sync()`` then
+    raises RtError with status RT_ETIMEOUT once the poll limit has run out."""
+    h = _handle(device)
+    _check(h, load_library().rt_selftest_wait(h))
+
+
+def inject_fault(kind=FAULT_ALLOC, count=1, device=None):
+    """The handle's next ``count`` workspace growths fail as a failed cudaMalloc."""
+    h = _handle(device)
+    _check(h, load_library().rt_inject_fault(h, int(kind), int(count)))

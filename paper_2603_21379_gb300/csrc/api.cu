@@ -133,6 +133,8 @@ struct rt_handle_s {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_open;  // recorded intervals
   double stage_ms[RT_NSTAGES] = {0};
   int64_t stage_cnt[RT_NSTAGES] = {0};
+  // injected host-side failures (rt_inject_fault, environment RT_FAULT=alloc[:count])
+  int fault_alloc = 0;         // the next this many workspace growths fail as a failed cudaMalloc
 };
 
 namespace {
@@ -419,9 +421,13 @@ rt_status ensure_ws(rt_handle h, size_t bytes) {
   h->ws = nullptr;
   h->ws_bytes = 0;
   const size_t want = align_up(bytes + bytes / 8);
-  cudaError_t e = cudaMalloc(&h->ws, want);
+  cudaError_t e = cudaErrorMemoryAllocation;
+  if (h->fault_alloc > 0)
+    --h->fault_alloc;      // injected: fails like cudaMalloc, with the old workspace already freed
+  else
+    e = cudaMalloc(&h->ws, want);
   if (e != cudaSuccess) {
-    cudaGetLastError();
+    if (h->ws) cudaGetLastError();   // a real failure: clear its sticky-free error state
     h->ws = nullptr;
     return fail(h, RT_ENOMEM, "device workspace allocation of " + std::to_string(want) + " bytes failed");
   }
@@ -913,6 +919,68 @@ std::vector<TNode> balanced_tree(int d) {
   return t;
 }
 
+// A dimension tree given as a child table (Alg. 2's input T): tab[2i], tab[2i+1] are
+// the left and right children of node i (both -1 for a leaf), node 0 is the root,
+// 2d - 1 nodes.  Leaves take the modes 0..d-1 in left-to-right order, so every node
+// is a contiguous mode range with its left child's modes first (the row order of
+// the set unfoldings and of the Kronecker products in the nestedness relation,
+// Sec. 4).  NULL gives the balanced tree.
+rt_status tree_of(rt_handle h, int d, const int32_t* tab, std::vector<TNode>& out) {
+  if (!tab) {
+    out = balanced_tree(d);
+    return RT_OK;
+  }
+  const int nn = 2 * d - 1;
+  std::vector<int> parents(nn, 0);
+  int nleaf = 0;
+  for (int i = 0; i < nn; ++i) {
+    const int l = tab[2 * i], r = tab[2 * i + 1];
+    if ((l < 0) != (r < 0)) return fail(h, RT_EINVAL, "tree: node " + std::to_string(i) + " has one child");
+    if (l < 0) {
+      if (l != -1 || r != -1) return fail(h, RT_EINVAL, "tree: a leaf's children must be -1");
+      ++nleaf;
+      continue;
+    }
+    if (l >= nn || r >= nn || l == 0 || r == 0 || l == r)
+      return fail(h, RT_EINVAL, "tree: children of node " + std::to_string(i) + " out of range");
+    ++parents[l];
+    ++parents[r];
+  }
+  if (nleaf != d) return fail(h, RT_EINVAL, "tree: need d leaves");
+  for (int i = 1; i < nn; ++i)
+    if (parents[i] != 1) return fail(h, RT_EINVAL, "tree: node " + std::to_string(i) + " needs one parent");
+  if (d == 1 || tab[0] < 0) return fail(h, RT_EINVAL, "tree: the root must have two children");
+  // in-order walk from the root: leaves numbered by mode, ranges and levels
+  out.assign(nn, TNode{-1, -1, -1, -1, 0});
+  std::vector<int> state(nn, 0), stack{0};
+  int mode = 0, visited = 0;
+  while (!stack.empty()) {
+    const int i = stack.back();
+    const int l = tab[2 * i], r = tab[2 * i + 1];
+    if (state[i] == 0) {
+      ++visited;
+      out[i].left = l;
+      out[i].right = r;
+      if (l < 0) {
+        out[i].a = out[i].b = mode++;
+        stack.pop_back();
+        continue;
+      }
+      state[i] = 1;
+      out[l].level = out[r].level = out[i].level + 1;
+      stack.push_back(r);
+      stack.push_back(l);
+    } else {
+      out[i].a = out[l].a;
+      out[i].b = out[r].b;
+      stack.pop_back();
+    }
+    if ((int)stack.size() > nn) break;
+  }
+  if (visited != nn || mode != d) return fail(h, RT_EINVAL, "tree: not every node is reachable from the root");
+  return RT_OK;
+}
+
 int64_t range_prod(const int64_t* n, int a, int b) {
   int64_t v = 1;
   for (int j = a; j <= b; ++j) v *= n[j];
@@ -1207,7 +1275,7 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
 // ============================================================================ C ABI
 extern "C" {
 
-int rt_version(void) { return 1; }
+int rt_version(void) { return 2; }
 
 const char* rt_status_string(rt_status s) {
   switch (s) {
@@ -1243,8 +1311,39 @@ rt_status rt_create(rt_handle* out, void* stream) {
     return RT_ECUDA;
   }
   *h->h_status = 0;
+  // RT_FAULT=alloc[:count]: the handle's next `count` (default 1) workspace growths fail
+  if (const char* f = std::getenv("RT_FAULT")) {
+    if (strncmp(f, "alloc", 5) == 0) h->fault_alloc = (f[5] == ':') ? std::max(0, atoi(f + 6)) : 1;
+  }
   *out = h;
   return RT_OK;
+}
+
+rt_status rt_inject_fault(rt_handle h, int kind, int count) {
+  if (!h || count < 0) return RT_EINVAL;
+  if (kind != RT_FAULT_ALLOC) return fail(h, RT_EINVAL, "unknown fault kind");
+  h->fault_alloc = count;
+  return RT_OK;
+}
+
+rt_status rt_set_wait_limit(rt_handle h, uint32_t polls) {
+  if (!h) return RT_EINVAL;
+  int cur = 0;
+  RT_CUDA(h, cudaGetDevice(&cur));
+  if (cur != h->device) RT_CUDA(h, cudaSetDevice(h->device));
+  cudaError_t e = core_tc_set_wait_limit(polls);
+  if (e == cudaSuccess) e = root_tma_set_wait_limit(polls);
+  if (e == cudaSuccess) e = diag_set_wait_limit(polls);
+  if (cur != h->device) cudaSetDevice(cur);
+  if (e != cudaSuccess) return cuda_fail(h, e, "rt_set_wait_limit");
+  return RT_OK;
+}
+
+rt_status rt_selftest_wait(rt_handle h) {
+  if (!h) return RT_EINVAL;
+  rt_status st;
+  if ((st = check_prior_status(h)) != RT_OK) return st;
+  return finish(h, launch_wait_selftest(h->d_status, h->stream));
 }
 
 rt_status rt_destroy(rt_handle h) {
@@ -1950,8 +2049,8 @@ rt_status rtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, cons
 }
 
 rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
-                             const int32_t* rank, int32_t p, const int64_t* w, uint64_t seed,
-                             const rt_options* opt, float* U_leaf, float* B, float* U_nodes) {
+                             const int32_t* tree_tab, const int32_t* rank, int32_t p, const int64_t* w,
+                             uint64_t seed, const rt_options* opt, float* U_leaf, float* B, float* U_nodes) {
   rt_status st;
   int64_t total = 0;
   if ((st = check_tensor(h, X, dtype, d, n, &total)) != RT_OK) return st;
@@ -1960,7 +2059,8 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
   if (!rank || !U_leaf || !B) return fail(h, RT_EINVAL, "rank, U_leaf and B are required");
   if ((st = check_prior_status(h)) != RT_OK) return st;
   if ((st = init_device_attrs(h)) != RT_OK) return st;
-  const std::vector<TNode> tree = balanced_tree(d);
+  std::vector<TNode> tree;
+  if ((st = tree_of(h, d, tree_tab, tree)) != RT_OK) return st;
   const int nn = (int)tree.size();
   std::vector<int> rk(nn);
   for (int i = 0; i < nn; ++i) rk[i] = (i == 0) ? 1 : rank[i];
@@ -2064,6 +2164,10 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
     key.add((uint64_t)dtype);
     key.arr(n, d);
     key.arr(rk.data(), nn);
+    for (const TNode& t : tree) {
+      key.add((uint64_t)(uint32_t)t.left);
+      key.add((uint64_t)(uint32_t)t.right);
+    }
     key.add((uint64_t)p);
     if (w) key.arr(w, nn);
     key.ptr(U_leaf);
@@ -2117,12 +2221,14 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
 }
 
 rt_status rhtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
-                          const int32_t* rank, const float* U_leaf, const float* B, double* out) {
+                          const int32_t* tree_tab, const int32_t* rank, const float* U_leaf, const float* B,
+                          double* out) {
   rt_status st;
   int64_t total = 0;
   if ((st = check_tensor(h, X, dtype, d, n, &total)) != RT_OK) return st;
   if (!rank || !U_leaf || !B || !out) return fail(h, RT_EINVAL, "rank, U_leaf, B and out are required");
-  const std::vector<TNode> tree = balanced_tree(d);
+  std::vector<TNode> tree;
+  if ((st = tree_of(h, d, tree_tab, tree)) != RT_OK) return st;
   const int nn = (int)tree.size();
   std::vector<int> rk(nn);
   for (int i = 0; i < nn; ++i) rk[i] = (i == 0) ? 1 : rank[i];

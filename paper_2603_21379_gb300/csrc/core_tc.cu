@@ -542,6 +542,8 @@ static int launch_v3(const CUtensorMap& map, const Core2Args& a, int grid, cudaS
 // by the tensor-core path (the caller then uses the FFMA chain).
 // xmode: 0 float32 X split into two bf16 terms, 1 bfloat16 X, 2 float32 X
 // rounded to one bf16 term.
+cudaError_t core_tc_set_wait_limit(uint32_t polls) { return tma::set_wait_limit(polls); }
+
 int launch_core2_tc(int xmode, const void* X, int64_t S, int n1, int n2, const float* U1, int r1, const float* U2,
                     int r2, float* P, int* status, cudaStream_t st, int max_ctas) {
   using namespace tc;

@@ -133,7 +133,10 @@ int launch_transfer(const TransferJob* jobs_dev, const TransferJob* jobs_host, i
 // a0 + t + RT_TH*q (q < 4).  X tiles of RT_CBT columns are staged in shared
 // memory (row stride RT_CBT + 1), U_r rows in shared memory (padded to 12).
 // Row sums t(a, k) accumulate per stage, then Kahan-add into the totals.
-// Output: partial P[blk](j, k) = sum_{a in block} U_l(a, j) t(a, k).
+// Output: partial P[blk](j, k) = sum_{a in block} U_l(a, j) t(a, k), blk =
+// by * gridDim.x + bx.  There are gy = ceil(nl / RT_RA) row blocks; a grid of
+// fewer than gy rows of CTAs (grid.y is limited to 65535) walks them with
+// stride gridDim.y.
 constexpr int RT_TH = 128, RT_RPT = 4, RT_RA = RT_TH * RT_RPT, RT_CBT = 32, RT_CB = 8192, RT_KMAX = 12;
 constexpr int RT_SMEM = RT_RA * (RT_CBT + 1) * 4;
 
@@ -153,7 +156,9 @@ __global__ void __launch_bounds__(RT_TH) k_root(const T* __restrict__ X, int64_t
   __shared__ __align__(16) float Us[RT_CBT * RT_KMAX];
   __shared__ float red[RT_TH];
   const int tid = threadIdx.x;
-  const int64_t a0 = (int64_t)blockIdx.y * RT_RA;
+  const int64_t gy = (nl + RT_RA - 1) / RT_RA;
+  for (int64_t by = blockIdx.y; by < gy; by += gridDim.y) {
+  const int64_t a0 = by * RT_RA;
   const int64_t b0 = (int64_t)blockIdx.x * RT_CB;
   const int64_t b1 = min(nr, b0 + RT_CB);
   float tot[RT_RPT][RR], cmp[RT_RPT][RR];
@@ -220,8 +225,9 @@ __global__ void __launch_bounds__(RT_TH) k_root(const T* __restrict__ X, int64_t
 #pragma unroll
       for (int q = 0; q < RT_RPT; ++q) v = fmaf(ul[q], tot[q][k], v);
       v = block_sum(v, red);
-      if (tid == 0) part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * rl * RR + j * RR + k] = v;
+      if (tid == 0) part[((size_t)by * gridDim.x + blockIdx.x) * rl * RR + j * RR + k] = v;
     }
+  }
   }
 }
 
@@ -246,34 +252,50 @@ size_t root_scratch_floats(int64_t nl, int64_t nr, int rl, int rr) {
   return (size_t)(gx * gy) * rl * rr;
 }
 
+// Launches return their error directly (cudaLaunchKernel), so that a caller can tell
+// a failure of these launches from an earlier error pending in the runtime.
 template <typename T>
-static void root_dispatch(const T* X, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur,
-                          int rr, float* part, dim3 grid, cudaStream_t st) {
+static cudaError_t root_dispatch(const T* X, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur,
+                                 int rr, float* part, dim3 grid, cudaStream_t st) {
+  void* args[] = {&X, &nl, &nr, &Ul, &rl, &Ur, &part};
+  const void* fn = nullptr;
   switch (rr) {
-#define RT_CASE(K)                                                                          \
-  case K:                                                                                   \
-    cudaFuncSetAttribute(k_root<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, RT_SMEM); \
-    k_root<T, K><<<grid, RT_TH, RT_SMEM, st>>>(X, nl, nr, Ul, rl, Ur, part);                 \
+#define RT_CASE(K)                                    \
+  case K:                                             \
+    fn = reinterpret_cast<const void*>(k_root<T, K>); \
     break;
     RT_CASE(1) RT_CASE(2) RT_CASE(3) RT_CASE(4) RT_CASE(5) RT_CASE(6)
     RT_CASE(7) RT_CASE(8) RT_CASE(9) RT_CASE(10) RT_CASE(11) RT_CASE(12)
 #undef RT_CASE
-    default: break;
+    default: return cudaErrorInvalidValue;
   }
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, RT_SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchKernel(fn, grid, dim3(RT_TH), args, RT_SMEM, st);
 }
 
 void launch_root_reduce(const float* part, int64_t nblk, int rl, int rr, float* BR, cudaStream_t st) {
   k_root_reduce<<<(unsigned)(rl * rr), 256, 0, st>>>(part, nblk, rl, rr, BR);
 }
 
+constexpr int64_t RT_GRID_Y_MAX = 65535;
+
 int launch_root_tiled(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl,
-                      const float* Ur, int rr, float* BR, float* scratch, cudaStream_t st) {
+                      const float* Ur, int rr, float* BR, float* scratch, cudaStream_t st, cudaError_t* err) {
   const int64_t gx = (nr + RT_CB - 1) / RT_CB, gy = (nl + RT_RA - 1) / RT_RA;
-  dim3 grid((unsigned)gx, (unsigned)gy);
-  if (dtype == DT_F32) root_dispatch(static_cast<const float*>(X), nl, nr, Ul, rl, Ur, rr, scratch, grid, st);
-  else if (dtype == DT_F64) root_dispatch(static_cast<const double*>(X), nl, nr, Ul, rl, Ur, rr, scratch, grid, st);
-  else root_dispatch(static_cast<const __nv_bfloat16*>(X), nl, nr, Ul, rl, Ur, rr, scratch, grid, st);
-  launch_root_reduce(scratch, gx * gy, rl, rr, BR, st);
+  dim3 grid((unsigned)gx, (unsigned)std::min(gy, RT_GRID_Y_MAX));
+  cudaError_t e;
+  if (dtype == DT_F32) e = root_dispatch(static_cast<const float*>(X), nl, nr, Ul, rl, Ur, rr, scratch, grid, st);
+  else if (dtype == DT_F64) e = root_dispatch(static_cast<const double*>(X), nl, nr, Ul, rl, Ur, rr, scratch, grid, st);
+  else e = root_dispatch(static_cast<const __nv_bfloat16*>(X), nl, nr, Ul, rl, Ur, rr, scratch, grid, st);
+  if (e == cudaSuccess) {
+    int64_t nblk = gx * gy;
+    int irl = rl, irr = rr;
+    void* args[] = {&scratch, &nblk, &irl, &irr, &BR};
+    e = cudaLaunchKernel(reinterpret_cast<const void*>(k_root_reduce), dim3((unsigned)(rl * rr)), dim3(256), args,
+                         0, st);
+  }
+  if (err) *err = e;
   return 2;
 }
 

@@ -12,7 +12,9 @@
 // rhtucker_root_transfer_noalloc computes the root transfer tensor of an
 // H-Tucker format, B_R(0, j, k) = sum_{a,b} X[a nr + b] U_l[a][j] U_r[b][k],
 // with the tiled root kernel (the one rhtucker_decompose uses for shapes the
-// streaming kernel does not take; it has no waits and so needs no status word),
+// streaming kernel does not take; it has no waits and so needs no status word;
+// rhtucker_decompose takes the streaming kernel where it can, and the two agree to
+// float32 rounding),
 // but its scratch (one partial r_l x r_r block per CTA) lives in the file-scope
 // device array below
 // instead of a workspace.  The array has a fixed capacity; every GPU that
@@ -42,18 +44,14 @@ float* g_addr[MAX_DEVICES] = {nullptr};
 
 rt_status scratch_for_current_device(float** out) {
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
-    cudaGetLastError();
-    return RT_ECUDA;
-  }
+  // Failures are returned as RT_ECUDA and left in the runtime's error state (no
+  // cudaGetLastError here: it would also clear an error the caller had pending).
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return RT_ECUDA;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_addr[dev]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_root_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return RT_ECUDA;
-    }
+    if (e != cudaSuccess || !p) return RT_ECUDA;
     g_addr[dev] = static_cast<float*>(p);
   }
   *out = g_addr[dev];
@@ -74,8 +72,10 @@ extern "C" rt_status rhtucker_root_transfer_noalloc(const void* X, rt_dtype dtyp
   const rt_status st = scratch_for_current_device(&scratch);
   if (st != RT_OK) return st;
   // The partial blocks are all overwritten by the first kernel; nothing in the
-  // scratch has to start at zero.
-  rt::launch_root_tiled(X, (int)dtype, nl, nr, Ul, rl, Ur, rr, BR, scratch, static_cast<cudaStream_t>(stream));
-  if (cudaGetLastError() != cudaSuccess) return RT_ECUDA;
-  return RT_OK;
+  // scratch has to start at zero.  The launch errors come back from the launches
+  // themselves, so an error the caller left pending in the runtime is neither
+  // reported as ours nor cleared.
+  cudaError_t e = cudaSuccess;
+  rt::launch_root_tiled(X, (int)dtype, nl, nr, Ul, rl, Ur, rr, BR, scratch, static_cast<cudaStream_t>(stream), &e);
+  return e == cudaSuccess ? RT_OK : RT_ECUDA;
 }

@@ -222,6 +222,8 @@ static size_t stream_base_floats(int64_t nl, int rl, int rr) {
   return ((size_t)nl * 2 * rr + (size_t)((nl + RL_ROWS - 1) / RL_ROWS) * rl * rr + 3) & ~(size_t)3;
 }
 
+cudaError_t root_tma_set_wait_limit(uint32_t polls) { return tma::set_wait_limit(polls); }
+
 size_t root_stream_scratch_floats(int64_t nl, int64_t nr, int rl, int rr) {
   const size_t upad = nr % RS_COLS ? (size_t)cols_padded(nr) * rr : 0;
   return stream_base_floats(nl, rl, rr) + upad;

@@ -95,6 +95,13 @@ int launch_slab2(const void* A, int dtype, int64_t L, int64_t n1, int64_t n2, in
 int launch_ttm_last_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs, int64_t total_ctas,
                             int dtype, int nmax, int rmax, cudaStream_t st);
 cudaError_t core_init_attributes();
+// Poll limit of the bounded mbarrier waits (0 = default) in each unit that has them.
+cudaError_t core_tc_set_wait_limit(uint32_t polls);
+cudaError_t root_tma_set_wait_limit(uint32_t polls);
+cudaError_t diag_set_wait_limit(uint32_t polls);
+// One CTA waiting on an mbarrier that nothing arrives on: the bounded wait runs out
+// and records ST_TIMEOUT in *status (the bounded-wait failure path, exercised).
+int launch_wait_selftest(int* status, cudaStream_t st);
 // ---- differentiable Tucker (grad_kernels.cu)
 // out(l, i, rho) = sum_a U[i][a] A(l, a, rho) (one core mode expanded, float32).
 int launch_expand_f32(const float* A, int64_t L, int r, int64_t R, const float* U, int64_t n, float* out,
@@ -156,8 +163,12 @@ size_t root_any_scratch_floats(int64_t nl, int64_t nr, int rl, int rr);
 int launch_root_any(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur,
                     int rr, float* BR, float* scratch, int* status, cudaStream_t st);
 // The tiled kernel alone (no waits, no status word); scratch of root_scratch_floats().
+// Any n_l: row blocks beyond the grid's y limit are folded onto the CTAs.  *err (if
+// given) receives the first error of its own launches, without touching errors that
+// were pending in the runtime before the call.
 int launch_root_tiled(const void* X, int dtype, int64_t nl, int64_t nr, const float* Ul, int rl,
-                      const float* Ur, int rr, float* BR, float* scratch, cudaStream_t st);
+                      const float* Ur, int rr, float* BR, float* scratch, cudaStream_t st,
+                      cudaError_t* err = nullptr);
 int launch_root_stream(const float* X, int64_t nl, int64_t nr, const float* Ul, int rl, const float* Ur, int rr,
                        float* BR, float* scratch, int* status, cudaStream_t st);
 void launch_root_reduce(const float* part, int64_t nblk, int rl, int rr, float* BR, cudaStream_t st);

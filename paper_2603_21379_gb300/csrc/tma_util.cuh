@@ -2,9 +2,10 @@
 // stream X through shared memory: the tensor-core core pass (core_tc.cu) and the
 // H-Tucker root pass (root_tma.cu).
 //
-// Every wait is bounded: after WAIT_LIMIT polls the waiter records a timeout in
-// the status word, raises the CTA's abort flag and returns false, so that a
-// missing arrival ends the kernel with an error status instead of a hang.
+// Every wait is bounded: after c_wait_limit polls (WAIT_LIMIT unless changed at run
+// time) the waiter records a timeout in the status word, raises the CTA's abort
+// flag and returns false, so that a missing arrival ends the kernel with an error
+// status instead of a hang.
 #pragma once
 
 #include <cuda.h>
@@ -19,6 +20,15 @@ namespace rt {
 namespace tma {
 
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
+
+// Poll limit of the bounded waits of this translation unit (each unit that includes
+// this header has its own copy, set through set_wait_limit from that unit).
+static __constant__ uint32_t c_wait_limit = WAIT_LIMIT;
+
+static inline cudaError_t set_wait_limit(uint32_t polls) {
+  const uint32_t v = polls ? polls : WAIT_LIMIT;
+  return cudaMemcpyToSymbol(c_wait_limit, &v, sizeof(v));
+}
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -46,7 +56,8 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait: false on timeout or when another role aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
-  for (uint32_t it = 0; it < WAIT_LIMIT; ++it) {
+  const uint32_t lim = c_wait_limit;
+  for (uint32_t it = 0; it < lim; ++it) {
     if (mbar_test(bar, parity)) return true;
     if ((it & 255u) == 255u && *abort_flag) return false;
   }

@@ -40,16 +40,21 @@ def clusters(sigma, r, gap_min=GAP_MIN):
     return out, tail_ok
 
 
-def compare_factor(Ug, Ur, sigma_ref, tol=U_TOL, gap_min=GAP_MIN):
-    """Returns (signs, max-abs deviation over determined columns, #strict columns)."""
+def compare_factor(Ug, Ur, sigma_ref, tol=U_TOL, gap_min=GAP_MIN, min_covered=1):
+    """Returns (signs, max-abs deviation over determined columns, #strict columns,
+    #covered columns).  Strict columns are compared element by element, columns of
+    a cluster of close singular values through the cluster's projector; a trailing
+    cluster that is not separated from sigma_r is undetermined and not covered.
+    Fails unless at least ``min_covered`` columns were compared."""
     Ug = np.asarray(Ug, dtype=np.float64)
     r = Ur.shape[1]
     Ua, s = align_signs(Ug, Ur)
     cl, tail_ok = clusters(sigma_ref, r, gap_min)
-    worst, strict = 0.0, 0
+    worst, strict, covered = 0.0, 0, 0
     for ci, c in enumerate(cl):
         if ci == len(cl) - 1 and not tail_ok:
             continue
+        covered += len(c)
         if len(c) == 1:
             worst = max(worst, np.abs(Ua[:, c[0]] - Ur[:, c[0]]).max())
             strict += 1
@@ -57,7 +62,8 @@ def compare_factor(Ug, Ur, sigma_ref, tol=U_TOL, gap_min=GAP_MIN):
             Pg = Ua[:, c] @ Ua[:, c].T
             Pr = Ur[:, c] @ Ur[:, c].T
             worst = max(worst, np.abs(Pg - Pr).max())
-    return s, worst, strict
+    assert covered >= min_covered, ("compared %d of %d columns" % (covered, r), min_covered)
+    return s, worst, strict, covered
 
 
 def orthonormality(U):

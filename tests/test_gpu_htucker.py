@@ -46,7 +46,7 @@ def _check_nodes(ref, U_leaf, B, Un, root_ref=None, gap_min=GAP_MIN):
     for nd in tree[1:]:
         sig = ref["info"][nd.id]["sigma"]
         Ug = to_np(Un[nd.id])
-        s, dev, _ = compare_factor(Ug, ref["US"][nd.id], sig, gap_min=gap_min)
+        s, dev, _, _ = compare_factor(Ug, ref["US"][nd.id], sig, gap_min=gap_min)
         assert dev <= U_TOL, (nd.id, dev)
         assert orthonormality(Ug) < 1e-5
         signs[nd.id] = s
@@ -68,14 +68,17 @@ def _check_nodes(ref, U_leaf, B, Un, root_ref=None, gap_min=GAP_MIN):
             assert np.abs(sub_g - sub_r).max() <= 1e-4 * max(1.0, np.abs(Br).max()), nd.id
 
 
-def _compare_ht(rt, X, rank, p, w=None, seed=0, x_oracle=None, gap_min=GAP_MIN):
+def _compare_ht(rt, X, rank, p, w=None, seed=0, x_oracle=None, gap_min=GAP_MIN, tree=None):
+    """GPU against oracle on the dimension tree ``tree`` (child table; None =
+    balanced), through rhtucker_decompose and rhtucker_relerr."""
     Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
-    U_leaf, B, Un = rt.rhtucker_decompose(Xd, rank, p, w=w, seed=seed, return_nodes=True)
+    U_leaf, B, Un = rt.rhtucker_decompose(Xd, rank, p, w=w, seed=seed, return_nodes=True, tree=tree)
     torch.cuda.synchronize()
     Xo = np.asarray(X if x_oracle is None else x_oracle, dtype=np.float64)
-    ref = htucker.sub_r_rtl_ht(Xo, rank, p, w=w, seed=seed)
+    otree = None if tree is None else htucker.tree_from_children(tree)
+    ref = htucker.sub_r_rtl_ht(Xo, rank, p, w=w, seed=seed, tree=otree)
     _check_nodes(ref, U_leaf, B, Un, gap_min=gap_min)
-    eg = rt.rhtucker_relerr(Xd, U_leaf, B, rank)
+    eg = rt.rhtucker_relerr(Xd, U_leaf, B, rank, tree=tree)
     er = tucker.relerr(Xo, htucker.reconstruct(ref["U"], ref["B"], ref["tree"], Xo.shape))
     assert abs(eg - er) <= RELERR_TOL, (eg, er)
     return eg, er
@@ -241,3 +244,60 @@ def test_graph_replay_matches_direct_launches(rt):
             assert torch.equal(a, b)
         for k in B:
             assert torch.equal(Bg[k], B[k])
+
+
+# ----------------------------------------------------------------- other dimension trees
+def _caterpillar(d):
+    ch = []
+    for j in range(d - 1):
+        ch.append((2 * j + 1, 2 * j + 2))
+        ch.append((-1, -1))
+    ch.append((-1, -1))
+    return ch
+
+
+def test_caterpillar_tree_d5(rt):
+    # Alg. 2 on the caterpillar tree {0..4} -> {0}, {1..4} -> {1}, ...: node bases of
+    # 8, 8^4 = 4096 ... rows, four transfer tensors, the root's left child a leaf
+    X = synth.inv_norm_tensor(8, 5)
+    _compare_ht(rt, X, 4, 3, seed=6, tree=_caterpillar(5))
+
+
+def test_tree_with_leaf_right_child_of_root(rt):
+    # root {0..4} -> {0..3}, {4}: the root pass takes X as 4096 x 8 (U_{R_r} of a leaf);
+    # ids below the left child are the balanced tree of 4 modes shifted by one
+    ch = [(1, 8), (2, 3), (4, 5), (6, 7), (-1, -1), (-1, -1), (-1, -1), (-1, -1), (-1, -1)]
+    rs = np.random.default_rng(21)
+    X = (synth.inv_norm_tensor(8, 5) + 1e-3 * rs.standard_normal((8,) * 5)).astype(np.float32)
+    _compare_ht(rt, X, 4, 2, seed=7, tree=ch)
+
+
+def test_alpha_sampling_rule_on_the_gpu(rt):
+    # w_S = min(floor(alpha^(d-2) n_S), n_notin_S) at every node (Sec. 4.2), from the
+    # binding's helper; the oracle takes its own restatement of the rule
+    X = synth.inv_norm_tensor(6, 6)
+    shape = X.shape
+    w = rt.ht_alpha_w(shape, 1.5)
+    wo = htucker.alpha_w(shape, htucker.balanced_tree(6), 1.5)
+    assert w == wo
+    _compare_ht(rt, X, 4, 2, w=w, seed=9)
+
+
+def test_bad_trees_are_rejected(rt):
+    X = torch.from_numpy(synth.inv_norm_tensor(4, 4)).cuda()
+    lib = rt.load_library()
+    import ctypes
+    h = rt._handle(X.device.index)
+    n = (ctypes.c_int64 * 4)(4, 4, 4, 4)
+    rk = (ctypes.c_int32 * 7)(*([2] * 7))
+    U = torch.empty(64, device="cuda")
+    B = torch.empty(64, device="cuda")
+    for tab in ([(1, 2), (3, 4), (5, 6), (-1, -1), (-1, -1), (-1, -1), (1, -1)],     # one child
+                [(1, 2), (3, 4), (3, 6), (-1, -1), (-1, -1), (-1, -1), (-1, -1)],    # node 3 twice
+                [(1, 2), (3, 4), (5, 0), (-1, -1), (-1, -1), (-1, -1), (-1, -1)],    # root as a child
+                [(1, 2), (-1, -1), (-1, -1), (-1, -1), (-1, -1), (-1, -1), (-1, -1)]):  # too many leaves
+        flat = (ctypes.c_int32 * 14)(*[v for lr in tab for v in lr])
+        st = lib.rhtucker_decompose(h, ctypes.c_void_p(X.data_ptr()), 0, 4, n, flat, rk, 1, None,
+                                    ctypes.c_uint64(1), None, ctypes.c_void_p(U.data_ptr()),
+                                    ctypes.c_void_p(B.data_ptr()), None)
+        assert st == 1, tab

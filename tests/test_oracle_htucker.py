@@ -110,10 +110,10 @@ def test_full_sampling_error_within_rtl_ht_bounds():
         assert len(tails) == 2 * len(shape) - 2
 
 
-def _random_ht_tensor(shape, r, seed):
+def _random_ht_tensor(shape, r, seed, tree=None):
     """Tensor built from a random H-Tucker format of hierarchical rank <= r."""
     rs = np.random.default_rng(seed)
-    tree = htucker.balanced_tree(len(shape))
+    tree = htucker.balanced_tree(len(shape)) if tree is None else tree
     U = [synth.haar(n, r, rs) for n in shape]
     B = [None] * len(tree)
     for nd in tree:
@@ -220,3 +220,104 @@ def test_alpha_sampling_rule():
     for shape, alpha in [((2, 3, 4, 5, 6), 1.5), ((16,) * 8, 1.2), ((7, 5, 9), 3.0)]:
         nodes = htucker.balanced_tree(len(shape))
         assert rt.ht_alpha_w(shape, alpha) == htucker.alpha_w(shape, nodes, alpha)
+
+
+# ----------------------------------------------------------------- general trees
+def caterpillar(d):
+    """Child table of the caterpillar tree {0..d-1} -> {0}, {1..d-1} -> {1}, {2..d-1} ...:
+    node 0 the root, internal node 2j has children 2j+1 (the leaf {j}) and 2j+2."""
+    ch = []
+    for j in range(d - 1):
+        ch.append((2 * j + 1, 2 * j + 2))
+        ch.append((-1, -1))
+    ch.append((-1, -1))
+    return ch
+
+
+def left_heavy(d):
+    """Child table with the root's right child a leaf: {0..d-2} on the left (balanced
+    below it, ids shifted), {d-1} on the right."""
+    sub = htucker.children_of(htucker.balanced_tree(d - 1))
+    ch = [(1, 2 * d - 2)]
+    for (l, r) in sub:
+        ch.append((-1, -1) if l < 0 else (l + 1, r + 1))
+    ch.append((-1, -1))
+    return ch
+
+
+def test_tree_from_children_reproduces_balanced_tree():
+    for d in range(2, 12):
+        a = htucker.balanced_tree(d)
+        b = htucker.tree_from_children(htucker.children_of(a))
+        assert [(n.id, n.a, n.b, n.left, n.right, n.level) for n in a] == \
+            [(n.id, n.a, n.b, n.left, n.right, n.level) for n in b]
+
+
+def test_tree_from_children_general_shapes():
+    t = htucker.tree_from_children(caterpillar(5))
+    # the leaves hold modes 0..4 in order; internal node 2j is {j..4}
+    assert [(n.a, n.b) for n in t] == [(0, 4), (0, 0), (1, 4), (1, 1), (2, 4), (2, 2), (3, 4), (3, 3), (4, 4)]
+    assert max(n.level for n in t) == 4
+    t = htucker.tree_from_children(left_heavy(5))
+    root = t[0]
+    assert (t[root.left].a, t[root.left].b, t[root.right].a, t[root.right].b) == (0, 3, 4, 4)
+    for bad in ([(1, 2), (-1, -1)], [(1, 1), (-1, -1), (-1, -1)], [(1, 2), (-1, -1), (0, 1)]):
+        with pytest.raises((ValueError, RecursionError, IndexError, TypeError)):
+            htucker.tree_from_children(bad)
+
+
+@pytest.mark.parametrize("make", [caterpillar, left_heavy])
+def test_general_tree_full_sampling_error_within_rtl_ht_bounds(make):
+    # the RtL-HT window of Sec. 4 (largest node tail <= error <= sum of the node
+    # tails but one child of the root) on trees other than the balanced one
+    for trial in range(6):
+        rs = np.random.default_rng(500 + trial)
+        d = int(rs.integers(3, 6))
+        shape = tuple(int(v) for v in rs.integers(3, 6, size=d))
+        tree = htucker.tree_from_children(make(d))
+        X = _random_ht_tensor(shape, 2, 500 + trial, tree=tree)
+        X = X / np.linalg.norm(X) + 1e-2 * rs.standard_normal(shape) / np.sqrt(X.size)
+        p = 1
+        ranks = [1] + [min(htucker.node_rows(shape, nd), htucker.node_cols(shape, nd)) - p for nd in tree[1:]]
+        if min(ranks[1:]) < 1:
+            continue
+        w = [0] + [htucker.node_cols(shape, nd) for nd in tree[1:]]
+        out = htucker.sub_r_rtl_ht(X, ranks, p, w=w, seed=trial, tree=tree)
+        ref = brute.rtl_ht(X, ranks, tree=tree)
+        for nd in tree[1:]:
+            assert np.abs(out["US"][nd.id] - ref["US"][nd.id]).max() < 1e-9
+        err = np.linalg.norm(X - htucker.reconstruct(out["U"], out["B"], tree, shape))
+        tails = {}
+        for nd in tree[1:]:
+            M = tucker.set_unfold(X, nd.a, nd.b)
+            sv = np.linalg.svd(M, compute_uv=False)
+            tails[nd.id] = float(np.sum(sv[ranks[nd.id]:] ** 2))
+        lo = np.sqrt(max(tails.values()))
+        hi = np.sqrt(sum(v for k, v in tails.items() if k != tree[0].right))
+        assert lo * (1 - 1e-12) <= err <= hi * (1 + 1e-12), (shape, lo, err, hi)
+
+
+@pytest.mark.parametrize("make", [caterpillar, left_heavy])
+def test_general_tree_exact_recovery(make):
+    shape = (4, 5, 3, 6, 4)
+    tree = htucker.tree_from_children(make(5))
+    X = _random_ht_tensor(shape, 2, 11, tree=tree)
+    out = htucker.sub_r_rtl_ht(X, 2, p=1, seed=2, tree=tree)
+    assert tucker.relerr(X, htucker.reconstruct(out["U"], out["B"], tree, shape)) < 1e-10
+    # nestedness on this tree: Range(U_S) inside Range(U_l (x) U_r)
+    for nd in tree:
+        if nd.is_leaf or nd.id == 0:
+            continue
+        K = np.kron(out["US"][nd.left], out["US"][nd.right])
+        assert np.abs(out["US"][nd.id] - K @ (K.T @ out["US"][nd.id])).max() < 1e-10
+
+
+def test_binding_tree_helper_matches_oracle():
+    import paper_2603_21379_gb300 as rt
+    for ch in (caterpillar(5), left_heavy(5), caterpillar(3), htucker.children_of(htucker.balanced_tree(7))):
+        a = rt.ht_tree_from_children(ch)
+        b = htucker.tree_from_children(ch)
+        assert [tuple(x) for x in a] == [(n.a, n.b, -1 if n.is_leaf else n.left, -1 if n.is_leaf else n.right,
+                                          n.level) for n in b]
+    with pytest.raises(ValueError):
+        rt.ht_tree_from_children([(1, 2), (-1, -1)])
