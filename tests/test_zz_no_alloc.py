@@ -49,8 +49,10 @@ def test_root_transfer_noalloc_matches_decompose_twice(rt, dt, rank):
     tdt, code = _DT[dt]
     lib = rt.load_library()
     X = torch.from_numpy(synth.inv_norm_tensor(8, 6)).cuda().to(tdt)
-    _, B, Un = rt.rhtucker_decompose(X, rank, 3, seed=3, return_nodes=True)
     tree = rt.ht_tree(6)
+    # rank `rank` at the root's two children (512 x 512 unfoldings), 5 elsewhere
+    ranks = [1] + [rank if i in (tree[0][2], tree[0][3]) else 5 for i in range(1, len(tree))]
+    _, B, Un = rt.rhtucker_decompose(X, ranks, 3, seed=3, return_nodes=True)
     left, right = tree[0][2], tree[0][3]
     Ul, Ur = Un[left].contiguous(), Un[right].contiguous()
     BR = B[0].clone()
@@ -79,7 +81,7 @@ def test_root_transfer_noalloc_folds_rows_beyond_grid_limit(rt):
     Urh = rs.standard_normal((nr, 1), dtype=np.float32)
     X, Ul, Ur = (torch.from_numpy(a).cuda() for a in (Xh, Ulh, Urh))
     ref = htucker.root_transfer(Xh.astype(np.float64), Ulh.astype(np.float64), Urh.astype(np.float64))
-    bound = float(np.abs(Ulh.astype(np.float64)).T @ np.abs(Xh.astype(np.float64)) @ np.abs(Urh.astype(np.float64)))
+    bound = float((np.abs(Ulh.astype(np.float64)).T @ np.abs(Xh.astype(np.float64)) @ np.abs(Urh.astype(np.float64))).item())
     del Xh
     for _ in range(2):
         out = torch.full((1, 1, 1), float("nan"), dtype=torch.float32, device="cuda")
