@@ -99,7 +99,22 @@ typedef struct {
                           synchronises its stream once) and the faster is kept
                           in the handle for later calls.  Same result up to
                           rounding.                                            */
-  int32_t reserved[4]; /* must be zero                                          */
+  int32_t qr;          /* factorisations of the range finder (S5 and the W-step
+                          of S6, Alg. 1 / Alg. 2).  For unfoldings of at most 256
+                          rows with (n_S | 1)(r + p) <= 12288: 1 Householder QR
+                          of Z and a TSQR of B^T = Y^T Q; 2 Cholesky form of
+                          both: Z = Q R by CholeskyQR2 whose first Gram Z^T Z is
+                          summed in double-float (two float32 words; GB300's
+                          float64 rate is ~1/64 of float32), falling back to
+                          Householder when Z is rank-deficient to rounding, and
+                          the R factor of B^T from the Cholesky factor of the
+                          Gram B B^T (compensated float32 sums of the rounded
+                          products); 0 (default) Householder QR of Z with the
+                          Cholesky form of the W-step (the fastest measured).
+                          Larger unfoldings always take 1.  The one-sided Jacobi
+                          SVD of R^T is the same in all; same factors to
+                          rounding.                                            */
+  int32_t reserved[3]; /* must be zero                                          */
 } rt_options;
 
 /* ----------------------------------------------------------- handle

@@ -40,7 +40,10 @@ class RtError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("overlap", ctypes.c_int32),
-                ("core", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("core", ctypes.c_int32), ("qr", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+_QR = {"auto": 0, "householder": 1, "cholesky": 2}
 
 
 _lib = None
@@ -248,9 +251,10 @@ def rtucker_sketch(X, r, p, s=None, seed=0):
     return _split(Z, n, [rk + p for rk in r])
 
 
-def rtucker_factors(X, r, p, s=None, seed=0, with_sigma=False):
+def rtucker_factors(X, r, p, s=None, seed=0, with_sigma=False, qr="auto"):
     """S1-S6: factors U_k (n_k x r_k) with the column-sign rule; optionally the
-    singular values of Q_k^T Y_k."""
+    singular values of Q_k^T Y_k.  ``qr`` picks the range finder's factorisations
+    (rt_options.qr: "auto", "householder", "cholesky")."""
     lib = load_library()
     dt, d, n = _tensor_args(X)
     r = _as_list(r, d)
@@ -258,8 +262,8 @@ def rtucker_factors(X, r, p, s=None, seed=0, with_sigma=False):
     sig = torch.empty(sum(rk + p for rk in r), dtype=torch.float32, device=X.device) if with_sigma else None
     h = _handle(X.device.index)
     sp = _i64(_as_list(s, d)) if s is not None else None
-    _check(h, lib.rtucker_factors(h, _ptr(X), dt, d, _i64(n), _i32(r), int(p), sp, ctypes.c_uint64(seed), None,
-                                  _ptr(U), _ptr(sig)))
+    _check(h, lib.rtucker_factors(h, _ptr(X), dt, d, _i64(n), _i32(r), int(p), sp, ctypes.c_uint64(seed),
+                                  _opts("fp32", qr=qr), _ptr(U), _ptr(sig)))
     Us = _split(U, n, r)
     if with_sigma:
         return Us, list(torch.split(sig, [rk + p for rk in r]))
@@ -270,20 +274,24 @@ _PREC = {"fp32": 0, "bf16": 1}
 _CORE = {"auto": 0, "tc": 1, "ffma": 2, "tune": 3}
 
 
-def _opts(prec, overlap=False, graph=False, core="auto"):
+def _opts(prec, overlap=False, graph=False, core="auto", qr="auto"):
     """rt_options for a precision form (the overlapped core schedule, CUDA-graph
-    replay, the core kernels: "auto", "tc", "ffma" or "tune"), or None (defaults)."""
+    replay, the core kernels: "auto", "tc", "ffma" or "tune"; the range finder's
+    factorisations: "auto", "householder" or "cholesky"), or None (defaults)."""
     if prec not in _PREC:
         raise ValueError("prec must be 'fp32' or 'bf16'")
     if core not in _CORE:
         raise ValueError("core must be 'auto', 'tc', 'ffma' or 'tune'")
-    if prec == "fp32" and not overlap and not graph and core == "auto":
+    if qr not in _QR:
+        raise ValueError("qr must be 'auto', 'householder' or 'cholesky'")
+    if prec == "fp32" and not overlap and not graph and core == "auto" and qr == "auto":
         return None
     o = _Options()
     o.prec = _PREC[prec]
     o.overlap = 1 if overlap else 0
     o.use_graph = 1 if graph else 0
     o.core = _CORE[core]
+    o.qr = _QR[qr]
     return ctypes.byref(o)
 
 
@@ -305,13 +313,15 @@ def rtucker_core(X, U, prec="fp32", core="auto"):
     return G
 
 
-def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32", overlap=False, graph=False, core="auto"):
+def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32", overlap=False, graph=False, core="auto",
+                      qr="auto"):
     """S1-S7: Sub-R-HOSVD; returns (G, [U_k]).  ``out`` = (Uflat, G) reuses buffers;
     ``prec`` "fp32" (default) or "bf16" (the BF16 compute form of the core pass);
     ``overlap`` runs the pass over X on the QR factors beside the SVD part of the
     range finder (see rt_options.overlap); ``graph`` replays the kernel sequence as
     a CUDA graph for repeated calls with the same buffers and shapes
-    (rt_options.use_graph; pass ``out`` so that the output pointers repeat)."""
+    (rt_options.use_graph; pass ``out`` so that the output pointers repeat); ``qr``
+    the range finder's factorisations (rt_options.qr)."""
     lib = load_library()
     dt, d, n = _tensor_args(X)
     r = _as_list(r, d)
@@ -323,7 +333,7 @@ def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32", overlap=Fa
     h = _handle(X.device.index)
     sp = _i64(_as_list(s, d)) if s is not None else None
     _check(h, lib.rtucker_decompose(h, _ptr(X), dt, d, _i64(n), _i32(r), int(p), sp, ctypes.c_uint64(seed),
-                                    _opts(prec, overlap, graph, core), _ptr(U), _ptr(G)))
+                                    _opts(prec, overlap, graph, core, qr), _ptr(U), _ptr(G)))
     return G, _split(U, n, r)
 
 
@@ -436,7 +446,7 @@ class BatchedDecomposition:
     of all tensors live in two flat float32 buffers (``U_flat``, ``G_flat``);
     ``results()`` gives the per-tensor (G, [U_k]) views."""
 
-    def __init__(self, Xs, ranks, p, seeds, s=None, prec="fp32", graph=False):
+    def __init__(self, Xs, ranks, p, seeds, s=None, prec="fp32", graph=False, qr="auto"):
         self.lib = load_library()
         T = len(Xs)
         dts = {X.dtype for X in Xs}
@@ -482,7 +492,7 @@ class BatchedDecomposition:
         self.U_arr = (ctypes.c_void_p * T)(*[ub + 4 * uoff[t] for t in range(T)])
         self.G_arr = (ctypes.c_void_p * T)(*[gb + 4 * goff[t] for t in range(T)])
         self.seed_arr = (ctypes.c_uint64 * T)(*[int(v) for v in seeds])
-        self._opt_keep = _opts(prec, graph=graph)
+        self._opt_keep = _opts(prec, graph=graph, qr=qr)
         self.h = _handle(dev.index)
 
     def run(self):
@@ -604,7 +614,8 @@ def _ht_ranks(d, rank):
     return rk
 
 
-def rhtucker_decompose(X, rank, p, w=None, seed=0, return_nodes=False, graph=False, out=None, tree=None):
+def rhtucker_decompose(X, rank, p, w=None, seed=0, return_nodes=False, graph=False, out=None, tree=None,
+                       qr="auto"):
     """Sub-R-RtL-HT (Alg. 2) on the dimension tree ``tree`` (a child table
     [(left, right), ...], node 0 the root, (-1, -1) for leaves; None = the balanced
     tree).  Returns (U_leaf list, B dict node -> transfer tensor) and, with
@@ -634,7 +645,7 @@ def rhtucker_decompose(X, rank, p, w=None, seed=0, return_nodes=False, graph=Fal
     h = _handle(X.device.index)
     wp = _i64(_as_list(w, len(nodes))) if w is not None else None
     _check(h, lib.rhtucker_decompose(h, _ptr(X), dt, d, _i64(n), tab, _i32(rk), int(p), wp,
-                                     ctypes.c_uint64(seed), _opts("fp32", graph=graph), _ptr(Ul), _ptr(B),
+                                     ctypes.c_uint64(seed), _opts("fp32", graph=graph, qr=qr), _ptr(Ul), _ptr(B),
                                      _ptr(Un)))
     U_leaf = _split(Ul, [n[nodes[i][0]] for i in leaves], [rk[i] for i in leaves])
     Bd, off = {}, 0

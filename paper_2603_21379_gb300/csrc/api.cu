@@ -252,12 +252,13 @@ struct ProbSpec {
   float* U;           // output (device) or null -> workspace
   float* sigma_out;
   int64_t* idx_out;   // sampled indices straight to the caller (or null)
+  int qr;             // rt_options.qr: 0 auto, 1 Householder / TSQR, 2 Cholesky form
 };
 
 struct ProbPlan {
   RFProb q;
   size_t o_idx, o_off, o_Om, o_Yt, o_Zp, o_zcnt, o_Q, o_Rb, o_Q2, o_tsR, o_tsQ, o_Bp, o_Rc, o_W, o_Wsg, o_sig,
-      o_keys, o_U, o_wsR;
+      o_keys, o_U, o_wsR, o_Cp;
   int64_t units[STG_ALL];
 };
 
@@ -297,6 +298,10 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   q.node = ps.node;
   q.fh = feistel_half(N);
   q.nzc = (int)((ps.s + SK_TJ - 1) / SK_TJ);
+  // Cholesky form of S5 / S6 (rt_options.qr): unfoldings of at most QWF_MAX rows whose
+  // Z also fits the single-block Householder QR it falls back to
+  const bool chol = ps.qr != 1 && nS <= QWF_MAX && (int64_t)odd((int)nS) * c <= QR_MAXF;   // W-step
+  const bool chol_z = chol && ps.qr == 2;                                                  // S5
   // TSQR of Z
   int rb = (QR_MAXF / c - 1) & ~31;
   if (rb < 32) rb = 32;
@@ -321,8 +326,9 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
     }
   }
   q.scrows = BT_SC;
-  q.nsc = (int)((ps.s + BT_SC - 1) / BT_SC);
-  q.nbi = (int)((nS + BT_IB - 1) / BT_IB);
+  q.nsc = chol ? 0 : (int)((ps.s + BT_SC - 1) / BT_SC);
+  q.nbi = chol ? 0 : (int)((nS + BT_IB - 1) / BT_IB);
+  q.nbg = chol ? (int)((ps.s + BG_SC - 1) / BG_SC) : 0;
   // more chunk factors than the W-step stacks: an R tree over them first
   int wf = 1, tf = 1;
   while ((int64_t)odd((wf + 1) * c) * c <= WS_MAXF) ++wf;
@@ -330,7 +336,7 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   q.wfan = tf;
   q.wn[0] = q.nsc;
   int64_t wcnt = q.nsc;
-  while (wcnt > wf) {
+  while (!chol && wcnt > wf) {
     if (q.wlev == TS_MAXLEV) return fail(h, RT_ENOTSUP, "too many samples for the W-step");
     wcnt = (wcnt + tf - 1) / tf;
     q.wn[++q.wlev] = (int)wcnt;
@@ -350,8 +356,9 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   for (int j = 1; j < q.nlev; ++j) upper += (size_t)q.lev_n[j];
   pp.o_tsR = bump.take(upper ? upper * c * c * 4 : 4);
   pp.o_tsQ = bump.take(upper ? upper * c * c * 4 : 4);
-  pp.o_Bp = bump.take((size_t)q.nbi * s * c * 4);
-  pp.o_Rc = bump.take((size_t)q.nsc * c * c * 4);
+  pp.o_Bp = bump.take(std::max<size_t>(4, (size_t)q.nbi * s * c * 4));
+  pp.o_Rc = bump.take(std::max<size_t>(4, (size_t)q.nsc * c * c * 4));
+  pp.o_Cp = bump.take(std::max<size_t>(4, (size_t)q.nbg * c * c * 2 * 4));
   size_t wup = 0;   // factors produced by the R tree's levels
   for (int j = 1; j <= q.wlev; ++j) wup += (size_t)q.wn[j];
   pp.o_wsR = bump.take(wup ? wup * c * c * 4 : 4);
@@ -366,18 +373,21 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   const int64_t nrt = (nS + SK_TI - 1) / SK_TI;
   pp.units[STG_SAMPLE] = s;
   pp.units[STG_GS] = nrt * q.nzc;
-  pp.units[STG_QR1] = q.nrb;
+  pp.units[STG_QR1] = chol_z ? 0 : q.nrb;
   for (int j = 0; j < q.nlev; ++j) pp.units[stg_qr2(j)] = q.lev_n[j + 1];      // groups of level j
   for (int t = 0; t + 1 < q.nlev; ++t) pp.units[stg_qrc(t)] = q.lev_n[q.nlev - 2 - t];   // members
   for (int j = 0; j < q.wlev; ++j) pp.units[stg_wt(j)] = q.wn[j + 1];                    // groups
   pp.units[STG_QR3] = q.nrb > 1 ? q.nrb : 0;
   pp.units[STG_BTP] = (int64_t)q.nsc * q.nbi;
   pp.units[STG_BTQ] = q.nsc;
-  pp.units[STG_WSVD] = 1;
+  pp.units[STG_WSVD] = chol ? 0 : 1;
   const bool qw_fused = nS <= QWF_MAX;
-  pp.units[STG_QW] = qw_fused ? 0 : (nS + QW_TI - 1) / QW_TI;
+  pp.units[STG_QW] = (chol || qw_fused) ? 0 : (nS + QW_TI - 1) / QW_TI;
   pp.units[STG_FLIP] = pp.units[STG_QW];
-  pp.units[STG_QWF] = qw_fused ? 1 : 0;
+  pp.units[STG_QWF] = (!chol && qw_fused) ? 1 : 0;
+  pp.units[STG_QZ] = chol_z ? 1 : 0;
+  pp.units[STG_BTG] = q.nbg;
+  pp.units[STG_WSV2] = chol ? 1 : 0;
   pp.units[STG_ZSUM] = nS * c;
   return RT_OK;
 }
@@ -397,6 +407,7 @@ void bind_problem(ProbPlan& pp, char* ws) {
   q.tsQ = reinterpret_cast<float*>(ws + pp.o_tsQ);
   q.Bp = reinterpret_cast<float*>(ws + pp.o_Bp);
   q.Rc = reinterpret_cast<float*>(ws + pp.o_Rc);
+  q.Cp = reinterpret_cast<float*>(ws + pp.o_Cp);
   q.wsR = reinterpret_cast<float*>(ws + pp.o_wsR);
   if (q.wlev == 0) {
     q.Rw = q.Rc;
@@ -612,7 +623,8 @@ rt_status check_opts(rt_handle h, const rt_options* opt) {
   if (opt->prec != RT_PREC_FP32 && opt->prec != RT_PREC_BF16) return fail(h, RT_EINVAL, "unknown precision");
   if (opt->use_graph != 0 && opt->use_graph != 1) return fail(h, RT_EINVAL, "use_graph must be 0 or 1");
   if (opt->core < 0 || opt->core > 3) return fail(h, RT_EINVAL, "core must be 0, 1, 2 or 3");
-  for (int i = 0; i < 4; ++i)
+  if (opt->qr < 0 || opt->qr > 2) return fail(h, RT_EINVAL, "qr must be 0, 1 or 2");
+  for (int i = 0; i < 3; ++i)
     if (opt->reserved[i]) return fail(h, RT_EINVAL, "reserved option fields must be zero");
   return RT_OK;
 }
@@ -627,7 +639,7 @@ int64_t default_s(const int64_t* n, int d, int k) {
 // Tucker problems of one tensor appended to G.
 rt_status add_tucker_problems(rt_handle h, Group& G, Bump& bump, const void* X, rt_dtype dtype, int d,
                               const int64_t* n, const int32_t* r, int32_t p, const int64_t* s,
-                              uint64_t seed, float* U, float* sigma) {
+                              uint64_t seed, float* U, float* sigma, int qr) {
   size_t uoff = 0, soff = 0;
   for (int k = 0; k < d; ++k) {
     ProbSpec ps{};
@@ -641,6 +653,7 @@ rt_status add_tucker_problems(rt_handle h, Group& G, Bump& bump, const void* X, 
     ps.s = s ? s[k] : default_s(n, d, k);
     ps.seed = seed;
     ps.node = (uint32_t)k;
+    ps.qr = qr;
     ps.U = U ? U + uoff : nullptr;
     ps.sigma_out = sigma ? sigma + soff : nullptr;
     ProbPlan pp;
@@ -678,6 +691,8 @@ int core_mode() {
 int prec_of(const rt_options* opt) { return opt ? opt->prec : RT_PREC_FP32; }
 
 int core_of(const rt_options* opt) { return opt ? opt->core : 0; }
+
+int qr_of(const rt_options* opt) { return opt ? opt->qr : 0; }
 
 // Contractions of the core G = X x_1 U_1^T ... x_d U_d^T, last modes first.  core
 // (rt_options.core): 0 auto, 1 tensor-core pass whenever the shape allows, 2 FFMA only
@@ -1156,7 +1171,7 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
   if ((st = init_device_attrs(h)) != RT_OK) return st;
   Group Gp;
   Bump bump;
-  st = add_tucker_problems(h, Gp, bump, X, dtype, d, n, r, p, s, seed, U, sigma);
+  st = add_tucker_problems(h, Gp, bump, X, dtype, d, n, r, p, s, seed, U, sigma, qr_of(opt));
   if (st != RT_OK) return st;
   group_layout(Gp, bump);
   size_t o_zp = 0;
@@ -1882,7 +1897,7 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
   Bump bump;
   for (int t = 0; t < T; ++t) {
     st = add_tucker_problems(h, Gp, bump, X[t], dtype, d[t], n[t], r[t], p, s ? s[t] : nullptr, seeds[t], U[t],
-                             nullptr);
+                             nullptr, qr_of(opt));
     if (st != RT_OK) return st;
   }
   group_layout(Gp, bump);
@@ -2096,6 +2111,7 @@ rt_status rhtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, 
     ps.s = w ? w[i] : std::min<int64_t>(20 * nmax, N);
     ps.seed = seed;
     ps.node = (uint32_t)i;
+    ps.qr = qr_of(opt);
     ps.U = U_nodes ? U_nodes + o_unode[i] : (leaf ? U_leaf + o_leaf[i] : nullptr);
     ProbPlan pp;
     if ((st = plan_problem(h, ps, bump, pp)) != RT_OK) return st;

@@ -17,9 +17,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "rt_common.cuh"
 #include "rt_host.h"
 #include "rt_rng.cuh"
+#include "rf_svd.cuh"
 
 namespace rt {
 
@@ -1030,117 +1033,8 @@ __global__ void __launch_bounds__(QR_THREADS) k_wsvd(const RFProb* __restrict__ 
     AT[qc * LDT + i] = v;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int ne = c + (c & 1);           // even number of players (dummy = c)
-  // Convergence threshold on |a_p . a_q| / (|a_p| |a_q|): about twice the worst rounding
-  // error of the 16-term tree dot product below, so a converged pair is not rotated again
-  // on noise alone.
-  const float tol = 2e-6f;
-  // Round-robin (circle) ordering: pair pr meets columns pa, qa; each round the players
-  // other than column 0 move one seat.  One pair per 16-lane group; lane l16 holds rows
-  // l16 + 16 k.  Column stride LDT = 80 puts the two groups of a warp on opposite bank
-  // halves (their columns differ in parity).
-  const int pr = threadIdx.x >> 4, l16 = threadIdx.x & 15;
-  const int kc = (c + 15) >> 4;
-  const unsigned gm = 0xffffu << (threadIdx.x & 16);
-  // Stop after a sweep in which no pair rotated, or in which every pair's relative
-  // off-diagonal |a_p.a_q| / (|a_p||a_q|) was below sqrt(tol) / 2: cyclic Jacobi
-  // converges quadratically, so such a sweep leaves every pair below tol and the next
-  // sweep would rotate nothing.
-  const float quad_stop = 0.5f * sqrtf(tol);
-  unsigned* dmax = reinterpret_cast<unsigned*>(flag + 2);   // per sweep, as float bits (>= 0)
-  if (threadIdx.x < 2) dmax[threadIdx.x] = 0u;
-  __syncthreads();
-  bool converged = false;
-  for (int sweep = 0; sweep < WS_MAX_SWEEPS && !converged; ++sweep) {
-    int t = pr - 1, u = ne - 2 - pr;
-    int rotated = 0;
-    float dloc = 0.f;
-    for (int rnd = 0; rnd < ne - 1; ++rnd) {
-      const int pa = (pr == 0) ? 0 : 1 + t;
-      const int qa = 1 + u;
-      if (pr < ne / 2 && pa < c && qa < c) {
-        float* ap = AT + pa * LDT + l16;
-        float* aq = AT + qa * LDT + l16;
-        float x[CMAX / 16], y[CMAX / 16];
-#pragma unroll
-        for (int k = 0; k < CMAX / 16; ++k) {
-          x[k] = (k < kc) ? ap[16 * k] : 0.f;
-          y[k] = (k < kc) ? aq[16 * k] : 0.f;
-        }
-        float al = 0.f, be = 0.f, ga = 0.f;
-#pragma unroll
-        for (int k = 0; k < CMAX / 16; ++k) {
-          al = fmaf(x[k], x[k], al);
-          be = fmaf(y[k], y[k], be);
-          ga = fmaf(x[k], y[k], ga);
-        }
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(gm, al, o);
-          be += __shfl_xor_sync(gm, be, o);
-          ga += __shfl_xor_sync(gm, ga, o);
-        }
-        const float rel = (ga != 0.f) ? fabsf(ga) * rsqrt_approx(al) * rsqrt_approx(be) : 0.f;
-        dloc = fmaxf(dloc, rel);
-        if (ga != 0.f && rel > tol) {
-          // tangent of the angle that makes the pair orthogonal, smaller root
-          const float zeta = (be - al) * rcp_approx(2.f * ga);
-          const float az = fabsf(zeta);
-          float tt;
-          if (az > 1e18f) {
-            tt = 0.5f * rcp_approx(zeta);
-          } else {
-            const float s1 = fmaf(zeta, zeta, 1.f);
-            tt = copysignf(rcp_approx(az + s1 * rsqrt_approx(s1)), zeta);
-          }
-          const float cs = rsqrt_approx(fmaf(tt, tt, 1.f)), sn = cs * tt;
-#pragma unroll
-          for (int k = 0; k < CMAX / 16; ++k) {
-            if (k < kc) {
-              ap[16 * k] = cs * x[k] - sn * y[k];
-              aq[16 * k] = sn * x[k] + cs * y[k];
-            }
-          }
-          rotated = 1;
-        }
-      }
-      if (++t == ne - 1) t = 0;
-      if (++u == ne - 1) u = 0;
-      __syncthreads();
-    }
-    // flag[sweep & 1] is set by any pair that rotated; the other slot is cleared for the
-    // next sweep (it was last read before the previous barrier).
-    if (rotated) flag[sweep & 1] = 1;
-    const unsigned dw = __reduce_max_sync(0xffffffffu, __float_as_uint(dloc));
-    if ((threadIdx.x & 31) == 0 && dw) atomicMax(&dmax[sweep & 1], dw);
-    __syncthreads();
-    const int f = flag[sweep & 1];
-    const float dm = __uint_as_float(dmax[sweep & 1]);
-    if (threadIdx.x == 0) { flag[(sweep + 1) & 1] = 0; dmax[(sweep + 1) & 1] = 0u; }
-    __syncthreads();
-    converged = !f || dm < quad_stop;
-  }
-  if (!converged && threadIdx.x == 0) set_status(status, ST_NUMERIC);
-  // singular values (column norms) and descending order
-  for (int qc = warp; qc < c; qc += nw) {
-    float s2 = 0.f;
-    for (int i = lane; i < c; i += 32) s2 = fmaf(AT[qc * LDT + i], AT[qc * LDT + i], s2);
-    s2 = warp_sum(s2);
-    if (lane == 0) sig[qc] = sqrtf(s2);
-  }
-  __syncthreads();
-  if (threadIdx.x < c) {
-    const int qc = threadIdx.x;
-    const float sq = sig[qc];
-    if (!(sq == sq)) set_status(status, ST_NUMERIC);
-    int rank = 0;
-    for (int t = 0; t < c; ++t) rank += (sig[t] > sq) || (sig[t] == sq && t < qc);
-    q.sigma[rank] = sq;
-    if (q.sigma_out) q.sigma_out[rank] = sq;
-    const float inv = (sq > 0.f) ? 1.f / sq : 0.f;
-    for (int i = 0; i < c; ++i) q.W[i * c + rank] = AT[qc * LDT + i] * inv;
-  }
+  jacobi_columns(AT, c, flag, status);
+  store_sorted(q, AT, c, sig, status);
 }
 
 // ------------------------------------------------------------------ U = Q W(:, :r), sign rule
@@ -1149,11 +1043,6 @@ __device__ __forceinline__ float qw_entry(const float* __restrict__ Qrow, const 
   float acc = 0.f;
   for (int t = 0; t < c; ++t) acc = fmaf(Qrow[t], Ws[t * ldw + col], acc);
   return acc;
-}
-
-__device__ __forceinline__ unsigned long long sign_key(float v, int64_t row) {
-  return ((unsigned long long)__float_as_uint(fabsf(v)) << 32) |
-         (unsigned long long)(0xffffffffu - (uint32_t)row);
 }
 
 // Dynamic smem: Ws[CMAX*CMAX] | Qs[QW_TI*CMAX] | keys[CMAX] (u64)
@@ -1211,76 +1100,357 @@ __global__ void __launch_bounds__(256) k_flip(const RFProb* __restrict__ P,
 }
 
 // U = Q W(:, :r) and the sign rule in one CTA per problem with n_S <= QWF_MAX rows.
-// Q is staged transposed (Qt[t][i], rows padded to a multiple of 4) so that a thread's
-// 4 x 4 tile of U takes one 16-byte load of Q and one of W per t; every entry is the
-// same sequential fma chain over t as qw_entry.  The sign rule's key (|u|, lowest row)
-// of each column is a warp max-reduction over the U tile in shared memory.
 // Dynamic smem: Ws[CMAX*CMAX] | Qt[CMAX*QWF_MAX] | Us[QWF_MAX*CMAX] | sg[CMAX]
 __global__ void __launch_bounds__(512) k_qwf(const RFProb* __restrict__ P, const int64_t* __restrict__ pre,
                                              int np) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* Ws = reinterpret_cast<float*>(smem_raw);
-  float* Qt = Ws + CMAX * CMAX;
-  float* Us = Qt + QWF_MAX * CMAX;
-  float* sg = Us + QWF_MAX * CMAX;
   const int p = find_prob(pre, np, blockIdx.x);
-  const RFProb& q = P[p];
-  const int m = (int)q.nS;
-  const int c = q.c, r = q.r;
-  const int mp = (m + 3) & ~3, rp = (r + 3) & ~3;
-  for (int e = threadIdx.x; e < c * rp; e += blockDim.x) {
-    const int t = e / rp, col = e % rp;
-    Ws[t * CMAX + col] = col < r ? q.W[t * c + col] : 0.f;
+  qw_sign(P[p], reinterpret_cast<float*>(smem_raw));
+}
+
+// ================================================================== Cholesky form (qr = 2)
+// For problems whose unfolding has at most QWF_MAX rows, S5 and the factorisation
+// in S6 run as Cholesky factorisations of Gram matrices instead of Householder QRs:
+//   S5: Z = Q R by CholeskyQR2 with a double-float first Gram (the mixed-precision
+//       CholeskyQR2 of Yamazaki, Tomov and Dongarra, 2015): G = Z^T Z summed in
+//       double-float (two float32 words, about 2^-48 relative), rounded to float32,
+//       G = R1^T R1, Q1 = Z R1^-1 by substitution; then a float32 pass on Q1 (its Gram
+//       is close to I) restores orthogonality to float32 rounding.
+//   S6: B^T = Y^T Q per chunk of samples with its Gram C_chunk = B_chunk B_chunk^T in
+//       double-float; the chunks summed in a fixed order, rounded to float32, and
+//       C = R^T R: R is the R factor of B^T (B B^T = R^T R) up to row signs, so the
+//       one-sided Jacobi SVD of R^T gives the left singular vectors W of B as before;
+//       then U = Q W(:, :r) and the sign rule in the same CTA.
+// Each stage is one CTA per problem (S5, W-step) or per sample chunk (B-step Gram);
+// GB300's float64 rate is ~1/64 of float32, so the double-float sums run on the
+// float32 pipes.
+
+// hi + lo += a b with the product's and the sum's rounding errors kept (TwoProd by
+// fma, TwoSum).  Explicit _rn intrinsics: the compiler must not contract or reorder.
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+// Kahan (compensated) sum s, k: s + k tracks the sum of the added values to about one
+// rounding of each value (the values themselves rounded products here: a Gram entry's
+// error stays within u sqrt(G_ii G_jj), the scale the Cholesky and Jacobi steps need).
+__device__ __forceinline__ void kahan_add(float& s, float& k, float v) {
+  const float y = __fsub_rn(v, k);
+  const float t = __fadd_rn(s, y);
+  k = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bhi, float blo) {
+  const float s = __fadd_rn(hi, bhi);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bhi, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, blo));
+}
+
+// G[i*ldg + j] (j >= i) = sum_{t < m} A[t*lda + i] A[t*lda + j], in double-float (dd) or
+// float32, rounded to float32.  One thread per entry with four independent partial
+// sums (rows t = 4 u + v) combined at the end; consecutive threads take consecutive
+// j, so the column reads of a warp are conflict-free for odd lda.
+__device__ void gram_upper(const float* A, int lda, int m, int c, float* G, int ldg, bool dd) {
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    if (j < i) continue;
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    int t = 0;
+    if (dd) {
+      for (; t + 3 < m; t += 4) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) df_acc(hi[v], lo[v], A[(t + v) * lda + i], A[(t + v) * lda + j]);
+      }
+      for (; t < m; ++t) df_acc(hi[0], lo[0], A[t * lda + i], A[t * lda + j]);
+      df_add(hi[0], lo[0], hi[1], lo[1]);
+      df_add(hi[2], lo[2], hi[3], lo[3]);
+      df_add(hi[0], lo[0], hi[2], lo[2]);
+    } else {
+      for (; t + 3 < m; t += 4) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) hi[v] = fmaf(A[(t + v) * lda + i], A[(t + v) * lda + j], hi[v]);
+      }
+      for (; t < m; ++t) hi[0] = fmaf(A[t * lda + i], A[t * lda + j], hi[0]);
+      hi[0] = (hi[0] + hi[1]) + (hi[2] + hi[3]);
+    }
+    G[i * ldg + j] = hi[0] + lo[0];
   }
-  for (int e = threadIdx.x; e < mp * c; e += blockDim.x) {
-    const int i = e / c, t = e % c;
-    Qt[t * QWF_MAX + i] = i < m ? q.Q[e] : 0.f;
+}
+
+// Cholesky G = R^T R of the upper triangle of G (c x c), R upper triangular into R
+// (zero below the diagonal); G is overwritten.  One barrier per step.  The upper
+// triangle's entries (i, j) are listed once in ij (shared, c (c + 1) / 2 shorts
+// pairs) by decreasing i, so the trailing entries of step k (i > k) are the first
+// (c - 1 - k)(c - k) / 2 of the list and spread evenly over the threads; every
+// thread reads pivot row k.  A pivot at or below thr (a column dependent on the
+// earlier ones to rounding) gets R_kk = rzero and a zero row, and no trailing update;
+// *nzero counts them (shared).
+__device__ void chol_upper(float* G, int ldg, int c, float* R, int ldr, float thr, float rzero, int* nzero,
+                           uint32_t* ij) {
+  for (int e = threadIdx.x; e < c * ldr; e += blockDim.x) R[e] = 0.f;
+  for (int i = (int)threadIdx.x; i < c; i += blockDim.x) {   // row i after the (c-1-i)(c-i)/2 entries of rows > i
+    const int o = (c - 1 - i) * (c - i) / 2;
+    for (int j = i; j < c; ++j) ij[o + (j - i)] = ((uint32_t)i << 16) | (uint32_t)j;
   }
   __syncthreads();
-  const int nrg = mp >> 2, ncg = rp >> 2;
-  for (int tile = threadIdx.x; tile < nrg * ncg; tile += blockDim.x) {
-    const int rg = tile % nrg, cg = tile / nrg;
-    float acc[4][4];
+  for (int k = 0; k < c; ++k) {
+    const float d = G[k * ldg + k];
+    const bool zero = !(d > thr);
+    const float rk = zero ? rzero : sqrtf(d);
+    const float ik = zero ? 0.f : __frcp_rn(rk);
+    for (int j = k + (int)threadIdx.x; j < c; j += blockDim.x) R[k * ldr + j] = (j == k) ? rk : G[k * ldg + j] * ik;
+    if (!zero) {
+      const int nt = (c - 1 - k) * (c - k) / 2;
+      for (int e = threadIdx.x; e < nt; e += blockDim.x) {
+        const uint32_t w = ij[e];
+        const int i = (int)(w >> 16), j = (int)(w & 0xffffu);
+        G[i * ldg + j] = fmaf(-(G[k * ldg + i] * ik), G[k * ldg + j] * ik, G[i * ldg + j]);
+      }
+    }
+    if (zero && threadIdx.x == 0) atomicAdd(nzero, 1);
+    __syncthreads();
+  }
+}
+
+// A <- A R^-1 for R upper triangular (rinv[j] = 1 / R_jj): row i of the result solves
+// x R = a_i by forward substitution.  Four lanes per row split each partial sum over
+// k < j (k = 4 u + lane4) and combine it with two shuffles; the row's lanes then all
+// hold x_j.  m rows in groups of blockDim / 4.
+__device__ void trsm_rows(float* A, int lda, int m, int c, const float* R, int ldr, const float* rinv) {
+  const int l4 = threadIdx.x & 3;
+  const int rows_per_pass = (int)(blockDim.x >> 2);
+  for (int i0 = 0; i0 < m; i0 += rows_per_pass) {
+    const int i = i0 + (int)(threadIdx.x >> 2);
+    const bool on = i < m;
+    float* a = A + (on ? i : 0) * lda;
+    for (int j = 0; j < c; ++j) {
+      float s = 0.f;
+      if (on)
+        for (int k = l4; k < j; k += 4) s = fmaf(a[k], R[k * ldr + j], s);
+      s += __shfl_xor_sync(0xffffffffu, s, 1);
+      s += __shfl_xor_sync(0xffffffffu, s, 2);
+      if (on && l4 == 0) a[j] = (a[j] - s) * rinv[j];
+      __syncwarp();
+    }
+  }
+}
+
+constexpr int QZ_LD = CMAX + 1;   // odd row stride of Z / Q in shared memory
+constexpr int GR_LD = CMAX + 1;   // row stride of the Gram and R matrices
+
+// S5, Cholesky form: Q of Z (n_S <= QWF_MAX rows) by mixed-precision CholeskyQR2.
+// A zero pivot (Z numerically rank-deficient) falls back to the Householder QR of the
+// same Z in the same CTA.
+// Dynamic smem: max(A[QWF_MAX*QZ_LD] | G[CMAX*GR_LD] | R[CMAX*GR_LD] | rinv[CMAX] | nzero,
+//                   the Householder QR's A | Qm | tau | rdiag | vbuf)
+__global__ void __launch_bounds__(QR_THREADS) k_qz(const RFProb* __restrict__ P, const int64_t* __restrict__ pre,
+                                                   int np, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int c = q.c, m = (int)q.nS;
+  const int lda = c | 1;
+  float* A = reinterpret_cast<float*>(smem_raw);
+  float* G = A + QWF_MAX * QZ_LD;
+  float* R = G + CMAX * GR_LD;
+  float* rinv = R + CMAX * GR_LD;
+  int* nzero = reinterpret_cast<int*>(rinv + CMAX);
+  uint32_t* ij = reinterpret_cast<uint32_t*>(nzero + 4);
+  if (threadIdx.x == 0) *nzero = 0;
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) A[(e / c) * lda + e % c] = q.Zp[e];
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    gram_upper(A, lda, m, c, G, GR_LD, pass == 0);
+    __syncthreads();
+    float dmax = 0.f;
+    for (int k = 0; k < c; ++k) dmax = fmaxf(dmax, G[k * GR_LD + k]);
+    if (!(dmax < INFINITY)) {            // non-finite sketch
+      if (threadIdx.x == 0) set_status(status, ST_NUMERIC);
+      dmax = 0.f;
+    }
+    chol_upper(G, GR_LD, c, R, GR_LD, dmax * (float)(c * 3.6e-15), 0.f, nzero, ij);
+    if (*nzero) break;
+    for (int j = threadIdx.x; j < c; j += blockDim.x) rinv[j] = 1.f / R[j * GR_LD + j];
+    __syncthreads();
+    trsm_rows(A, lda, m, c, R, GR_LD, rinv);
+    __syncthreads();
+  }
+  if (*nzero == 0) {
+    for (int e = threadIdx.x; e < m * c; e += blockDim.x) q.Q[e] = A[(e / c) * lda + e % c];
+    return;
+  }
+  // Householder fallback (as k_qr1 for a single row block)
+  __syncthreads();
+  const int ld = odd_ld(m);
+  float* H = reinterpret_cast<float*>(smem_raw);
+  float* Qm = H + (size_t)ld * c;
+  float* tau = Qm + (size_t)ld * c;
+  float* rdiag = tau + CMAX;
+  float* vbuf = rdiag + CMAX;
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) H[(size_t)(e % c) * ld + e / c] = q.Zp[e];
+  __syncthreads();
+  qr_factor<QR_JPW>(H, ld, m, c, tau, rdiag, vbuf);
+  qr_form_q<QR_JPW>(H, Qm, ld, m, c, tau, rdiag, true);
+  for (int e = threadIdx.x; e < m * c; e += blockDim.x) q.Q[e] = Qm[(size_t)(e % c) * ld + e / c];
+}
+
+// S6, Cholesky form, per sample chunk sc: B^T_chunk = Y_chunk^T Q (BG_SC x c, in shared
+// memory) and its Gram C_chunk = B_chunk B_chunk^T by compensated sums of the rounded
+// products, written as sum / correction words to Cp[sc][i][j] (upper triangle).
+// Dynamic smem: Ys[32][BG_LDY] | Qs[32][CMAX] | Bs[BG_SC][CMAX | 1]
+constexpr int BG_LDY = BG_SC + 4;
+__global__ void __launch_bounds__(256) k_btg(const RFProb* __restrict__ P, const int64_t* __restrict__ pre,
+                                             int np) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* Ys = reinterpret_cast<float*>(smem_raw);
+  float* Qs = Ys + 32 * BG_LDY;
+  float* Bs = Qs + 32 * CMAX;
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int sc = (int)((int64_t)blockIdx.x - pre[p]);
+  const int c = q.c, cp = (c + 3) & ~3, ldb = c | 1;
+  const int64_t j0 = (int64_t)sc * BG_SC;
+  const int mj = (int)min((int64_t)BG_SC, q.s - j0);
+  const int ntile = (BG_SC / 4) * (cp / 4);
+  constexpr int TPT = (BG_SC / 4) * (CMAX / 4) / 256;
+  float acc[TPT][4][4];
+#pragma unroll
+  for (int u = 0; u < TPT; ++u)
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
-    for (int t = 0; t < c; ++t) {
-      const float4 qv = *reinterpret_cast<const float4*>(Qt + t * QWF_MAX + 4 * rg);
-      const float4 wv = *reinterpret_cast<const float4*>(Ws + t * CMAX + 4 * cg);
-      const float qa[4] = {qv.x, qv.y, qv.z, qv.w};
-      const float wb[4] = {wv.x, wv.y, wv.z, wv.w};
+      for (int b = 0; b < 4; ++b) acc[u][a][b] = 0.f;
+  for (int64_t it = 0; it < q.nS; it += 32) {
+    const int mi = (int)min((int64_t)32, q.nS - it);
+    __syncthreads();
+    for (int e = threadIdx.x; e < 32 * BG_SC; e += 256) {
+      const int jj = e / 32, ii = e % 32;
+      Ys[ii * BG_LDY + jj] = (jj < mj && ii < mi) ? q.Yt[(j0 + jj) * q.nS + it + ii] : 0.f;
+    }
+    for (int e = threadIdx.x; e < 32 * cp; e += 256) {
+      const int ii = e / cp, cc = e % cp;
+      Qs[ii * CMAX + cc] = (ii < mi && cc < c) ? q.Q[(it + ii) * c + cc] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < TPT; ++u) {
+      const int t = threadIdx.x + 256 * u;
+      if (t < ntile) {
+        const int jg = t % (BG_SC / 4), cg = t / (BG_SC / 4);
+#pragma unroll 8
+        for (int ii = 0; ii < 32; ++ii) {
+          const float4 y = *reinterpret_cast<const float4*>(Ys + ii * BG_LDY + jg * 4);
+          const float4 o = *reinterpret_cast<const float4*>(Qs + ii * CMAX + cg * 4);
+          const float ya[4] = {y.x, y.y, y.z, y.w};
+          const float ob[4] = {o.x, o.y, o.z, o.w};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[u][a][b] = fmaf(ya[a], ob[b], acc[u][a][b]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < TPT; ++u) {
+    const int t = threadIdx.x + 256 * u;
+    if (t < ntile) {
+      const int jg = t % (BG_SC / 4), cg = t / (BG_SC / 4);
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(qa[a], wb[b], acc[a][b]);
-    }
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) Us[(4 * rg + a) * CMAX + 4 * cg + b] = acc[a][b];
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int col = warp; col < r; col += nw) {
-    unsigned long long best = 0ull;
-    for (int i = lane; i < m; i += 32) {
-      const unsigned long long k = sign_key(Us[i * CMAX + col], i);
-      best = k > best ? k : best;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long k = __shfl_xor_sync(0xffffffffu, best, o);
-      best = k > best ? k : best;
-    }
-    if (lane == 0) {
-      const int rstar = (int)(0xffffffffu - (uint32_t)(best & 0xffffffffull));
-      sg[col] = (Us[rstar * CMAX + col] < 0.f) ? -1.f : 1.f;
+        for (int b = 0; b < 4; ++b) {
+          const int cc = cg * 4 + b;
+          if (cc < c) Bs[(jg * 4 + a) * ldb + cc] = acc[u][a][b];   // rows >= mj hold zeros
+        }
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < m * r; e += blockDim.x) q.U[e] = sg[e % r] * Us[(e / r) * CMAX + e % r];
-  for (int e = threadIdx.x; e < c * r; e += blockDim.x) q.Wsg[e] = sg[e % r] * Ws[(e / r) * CMAX + e % r];
+  float* out = q.Cp + (size_t)sc * c * c * 2;
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    if (j < i) continue;
+    float s0 = 0.f, k0 = 0.f, s1 = 0.f, k1 = 0.f;   // two independent sums (even, odd t)
+    int t = 0;
+#pragma unroll 2
+    for (; t + 1 < mj; t += 2) {
+      kahan_add(s0, k0, __fmul_rn(Bs[t * ldb + i], Bs[t * ldb + j]));
+      kahan_add(s1, k1, __fmul_rn(Bs[(t + 1) * ldb + i], Bs[(t + 1) * ldb + j]));
+    }
+    if (t < mj) kahan_add(s0, k0, __fmul_rn(Bs[t * ldb + i], Bs[t * ldb + j]));
+    float hi = s0, lo = -k0;
+    df_add(hi, lo, s1, -k1);
+    out[2 * e] = hi;
+    out[2 * e + 1] = lo;
+  }
+}
+
+// S6, Cholesky form, one CTA per problem: C = sum of the chunk Grams (double-float,
+// chunk order), C = R^T R, one-sided Jacobi on the columns of R^T, W sorted, then
+// U = Q W(:, :r) with the sign rule.
+// Dynamic smem: max(G[CMAX*GR_LD] | R[CMAX*GR_LD] | AT[CMAX*WS_LDT] | sig | flag[4] | nzero,
+//                   the U = Q W stage: CMAX*CMAX + 2*QWF_MAX*CMAX + CMAX floats)
+__global__ void __launch_bounds__(QR_THREADS) k_wsvd2(const RFProb* __restrict__ P,
+                                                      const int64_t* __restrict__ pre, int np, int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int p = find_prob(pre, np, blockIdx.x);
+  const RFProb& q = P[p];
+  const int c = q.c;
+  float* Qt = reinterpret_cast<float*>(smem_raw);       // Q^T for U = Q W, staged first
+  float* Ws = Qt + CMAX * QWF_MAX;
+  float* sg = Ws + CMAX * CMAX;
+  float* G = sg + CMAX;                                   // then G | R | AT | sig | flags,
+  float* R = G + CMAX * GR_LD;                            // reused as Us by U = Q W
+  float* AT = R + CMAX * GR_LD;
+  float* sig = AT + CMAX * WS_LDT;
+  int* flag = reinterpret_cast<int*>(sig + CMAX);
+  int* nzero = flag + 4;
+  uint32_t* ij = reinterpret_cast<uint32_t*>(flag + 8);
+  if (threadIdx.x < 4) flag[threadIdx.x] = 0;
+  if (threadIdx.x == 0) *nzero = 0;
+  qw_stage_q(q, Qt);
+  for (int e = threadIdx.x; e < c * c; e += blockDim.x) {
+    const int i = e / c, j = e % c;
+    if (j < i) continue;
+    // chunk partials loaded eight at a time (independent loads in flight), added in order
+    float hi = 0.f, lo = 0.f;
+    for (int s0 = 0; s0 < q.nbg; s0 += 8) {
+      float2 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = (s0 + u < q.nbg) ? __ldcg(reinterpret_cast<const float2*>(q.Cp + ((size_t)(s0 + u) * c * c + e) * 2))
+                                : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) df_add(hi, lo, v[u].x, v[u].y);
+    }
+    G[i * GR_LD + j] = hi + lo;
+  }
+  __syncthreads();
+  float dmax = 0.f;
+  for (int k = 0; k < c; ++k) dmax = fmaxf(dmax, G[k * GR_LD + k]);
+  if (!(dmax < INFINITY)) {
+    if (threadIdx.x == 0) set_status(status, ST_NUMERIC);
+    dmax = 0.f;
+  }
+  // dependent columns (B rank-deficient to rounding) keep a rounding-level diagonal, so
+  // that the Jacobi step still returns an orthonormal W
+  chol_upper(G, GR_LD, c, R, GR_LD, dmax * (float)(c * 3.6e-15), sqrtf(dmax) * 6e-8f, nzero, ij);
+  // AT[qc][i] = R[qc][i]: column qc of R^T is row qc of R; rows c .. CMAX-1 zero
+  for (int e = threadIdx.x; e < CMAX * CMAX; e += blockDim.x) {
+    const int qc = e / CMAX, i = e % CMAX;
+    AT[qc * WS_LDT + i] = (qc < c && i < c) ? R[qc * GR_LD + i] : 0.f;
+  }
+  __syncthreads();
+  jacobi_columns(AT, c, flag, status);
+  store_sorted(q, AT, c, sig, status, Ws);
+  qw_core(q, Ws, Qt, G, sg);
 }
 
 // S1 + S3 with one thread per sample (pi(j), its fiber offset and row j of Omega):
@@ -1366,6 +1536,15 @@ static size_t smem_wsvd() {
 static size_t smem_qw() { return (size_t)(CMAX * CMAX + QW_TI * CMAX) * 4 + CMAX * 8; }
 static size_t smem_flip() { return (size_t)(CMAX * CMAX + CMAX) * 4; }
 static size_t smem_qwf() { return (size_t)(CMAX * CMAX + 2 * QWF_MAX * CMAX + CMAX) * 4; }
+constexpr int IJ_MAX = CMAX * (CMAX + 1) / 2;   // entries of the Cholesky step list
+static size_t smem_qz() {
+  return std::max((size_t)(QWF_MAX * QZ_LD + 2 * CMAX * GR_LD + CMAX + 4 + IJ_MAX) * 4, smem_qr());
+}
+static size_t smem_btg() { return (size_t)(32 * BG_LDY + 32 * CMAX + BG_SC * (CMAX | 1)) * 4; }
+static size_t smem_wsvd2() {
+  return (size_t)(CMAX * QWF_MAX + CMAX * CMAX + CMAX +
+                  std::max(2 * CMAX * GR_LD + CMAX * WS_LDT + CMAX + 8 + IJ_MAX, QWF_MAX * CMAX)) * 4;
+}
 
 cudaError_t rf_init_attributes() {
   cudaError_t e;
@@ -1385,6 +1564,9 @@ cudaError_t rf_init_attributes() {
   RT_ATTR(k_qw, smem_qw());
   RT_ATTR(k_flip, smem_flip());
   RT_ATTR(k_qwf, smem_qwf());
+  RT_ATTR(k_qz, smem_qz());
+  RT_ATTR(k_btg, smem_btg());
+  RT_ATTR(k_wsvd2, smem_wsvd2());
 #undef RT_ATTR
   return cudaSuccess;
 }
@@ -1406,10 +1588,18 @@ int launch_rf_head(const RFGroup& g, cudaStream_t st, int* status) {
           g.probs, pre + STG_SAMPLE * stride, np, status);
     n += 1;
   }
-  k_gather_sketch<<<grid_of(g.total[STG_GS]), 256, smem_gs(), st>>>(g.probs, pre + STG_GS * stride, np);
-  ++n;
-  k_qr1<<<grid_of(g.total[STG_QR1]), QR_THREADS, smem_qr(), st>>>(g.probs, pre + STG_QR1 * stride, np);
-  ++n;
+  if (g.total[STG_GS] > 0) {
+    k_gather_sketch<<<grid_of(g.total[STG_GS]), 256, smem_gs(), st>>>(g.probs, pre + STG_GS * stride, np);
+    ++n;
+  }
+  if (g.total[STG_QZ] > 0) {                    // Cholesky form of S5
+    k_qz<<<grid_of(g.total[STG_QZ]), QR_THREADS, smem_qz(), st>>>(g.probs, pre + STG_QZ * stride, np, status);
+    ++n;
+  }
+  if (g.total[STG_QR1] > 0) {
+    k_qr1<<<grid_of(g.total[STG_QR1]), QR_THREADS, smem_qr(), st>>>(g.probs, pre + STG_QR1 * stride, np);
+    ++n;
+  }
   if (g.total[STG_QR2] > 0) {
     for (int j = 0; j < g.lmax; ++j) {          // the tree's levels, bottom-up
       const int sj = stg_qr2(j);
@@ -1426,13 +1616,19 @@ int launch_rf_head(const RFGroup& g, cudaStream_t st, int* status) {
     k_qr3<<<grid_of(g.total[STG_QR3]), 256, smem_qr3(), st>>>(g.probs, pre + STG_QR3 * stride, np);
     ++n;
   }
-  if (g.total[STG_BTP] == g.total[STG_BTQ]) {   // every problem reduces B^T over one row block
-    k_bt_fused<<<grid_of(g.total[STG_BTQ]), QR_THREADS, smem_btf(), st>>>(g.probs, pre + STG_BTQ * stride, np);
-    n += 1;
-  } else {
-    k_bt_partial<<<grid_of(g.total[STG_BTP]), 256, smem_btp(), st>>>(g.probs, pre + STG_BTP * stride, np);
-    k_bt_qr<<<grid_of(g.total[STG_BTQ]), QR_THREADS, smem_btq(), st>>>(g.probs, pre + STG_BTQ * stride, np);
-    n += 2;
+  if (g.total[STG_BTG] > 0) {                   // Cholesky form: B-step Grams
+    k_btg<<<grid_of(g.total[STG_BTG]), 256, smem_btg(), st>>>(g.probs, pre + STG_BTG * stride, np);
+    ++n;
+  }
+  if (g.total[STG_BTQ] > 0) {
+    if (g.total[STG_BTP] == g.total[STG_BTQ]) {   // every problem reduces B^T over one row block
+      k_bt_fused<<<grid_of(g.total[STG_BTQ]), QR_THREADS, smem_btf(), st>>>(g.probs, pre + STG_BTQ * stride, np);
+      n += 1;
+    } else {
+      k_bt_partial<<<grid_of(g.total[STG_BTP]), 256, smem_btp(), st>>>(g.probs, pre + STG_BTP * stride, np);
+      k_bt_qr<<<grid_of(g.total[STG_BTQ]), QR_THREADS, smem_btq(), st>>>(g.probs, pre + STG_BTQ * stride, np);
+      n += 2;
+    }
   }
   for (int j = 0; j < g.wmax; ++j) {            // R tree over many chunk factors
     const int sj = stg_wt(j);
@@ -1449,9 +1645,16 @@ int launch_rf_tail(const RFGroup& g, cudaStream_t st, int* status) {
   const int64_t* pre = g.pre;
   const int64_t stride = np + 1;
   int n = 0;
-  k_wsvd<<<grid_of(g.total[STG_WSVD]), QR_THREADS, smem_wsvd(), st>>>(g.probs, pre + STG_WSVD * stride, np,
-                                                                 status);
-  n += 1;
+  if (g.total[STG_WSVD] > 0) {
+    k_wsvd<<<grid_of(g.total[STG_WSVD]), QR_THREADS, smem_wsvd(), st>>>(g.probs, pre + STG_WSVD * stride, np,
+                                                                   status);
+    n += 1;
+  }
+  if (g.total[STG_WSV2] > 0) {                  // Cholesky form of the W-step, U = Q W, signs
+    k_wsvd2<<<grid_of(g.total[STG_WSV2]), QR_THREADS, smem_wsvd2(), st>>>(g.probs, pre + STG_WSV2 * stride, np,
+                                                                     status);
+    n += 1;
+  }
   if (g.total[STG_QWF] > 0) {
     k_qwf<<<grid_of(g.total[STG_QWF]), 512, smem_qwf(), st>>>(g.probs, pre + STG_QWF * stride, np);
     ++n;

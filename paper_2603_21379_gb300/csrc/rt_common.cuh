@@ -78,6 +78,9 @@ struct RFProb {
   unsigned long long* keys;// [r]      sign-rule argmax keys
   float* U;                // [nS][r]  output factor
   float* sigma_out;        // optional copy of sigma for the caller (or null)
+  // Cholesky form: double-float Grams of the B-step's sample chunks
+  float* Cp;               // [nbg][c][c][2] hi/lo words (upper triangles)
+  int32_t nbg;             // number of sample chunks of the B-step Gram
 };
 
 // Problem lookup: blocks (or threads) are numbered consecutively over the

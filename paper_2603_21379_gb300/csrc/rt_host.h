@@ -22,10 +22,13 @@ constexpr int WS_LDT = 80;         // column stride of R^T in the Jacobi SVD (CM
 constexpr int WS_MAX_SWEEPS = 40;  // one-sided Jacobi sweeps before ST_NUMERIC
 constexpr int QW_TI = 32;          // rows per tile of U = Q W
 constexpr int QWF_MAX = 256;       // rows up to which U = Q W and its signs take one CTA
+constexpr int BG_SC = 64;          // samples per chunk of the B-step Gram (Cholesky form)
 
+// Stages.  The Cholesky form (qr = 2) of a problem runs STG_QZ, STG_BTG and STG_WSV2
+// in place of STG_QR1 .. STG_QWF; a problem has units in one set or the other.
 enum Stage : int {
   STG_SAMPLE = 0, STG_GS, STG_QR1, STG_QR2, STG_QR3, STG_BTP, STG_BTQ, STG_WSVD, STG_QW, STG_FLIP,
-  STG_ZSUM, STG_QWF, STG_COUNT
+  STG_ZSUM, STG_QWF, STG_QZ, STG_BTG, STG_WSV2, STG_COUNT
 };
 // Stages of the TSQR tree beyond its first level: the QR of level j >= 1 and the
 // combine passes t = 0 .. (top-down); their prefix rows follow the fixed ones and

@@ -94,6 +94,10 @@ def test_option_marshalling():
     assert rt._opts("fp32", core="tune")._obj.core == 3
     with pytest.raises(ValueError):
         rt._opts("fp32", core="wmma")
+    assert rt._opts("fp32", qr="householder")._obj.qr == 1
+    assert rt._opts("fp32", qr="cholesky")._obj.qr == 2
+    with pytest.raises(ValueError):
+        rt._opts("fp32", qr="givens")
 
 
 def test_product_never_uses_the_scratch_folder():

@@ -30,7 +30,8 @@ def rt():
     return m
 
 
-def _run_and_compare(rt, X, r, p, s=None, seed=0, check_core=True, x_for_oracle=None, min_covered=None):
+def _run_and_compare(rt, X, r, p, s=None, seed=0, check_core=True, x_for_oracle=None, min_covered=None,
+                     qr="auto"):
     """Decomposition through the C ABI against the oracle.  check_core: True compares
     G with the oracle's core (signs aligned); "projection" compares G element-wise
     with the float64 projection of X on the GPU's own factors, X x_k U_k^T, at 1e-5
@@ -38,9 +39,9 @@ def _run_and_compare(rt, X, r, p, s=None, seed=0, check_core=True, x_for_oracle=
     of close singular values).  min_covered: columns per mode that must be compared
     (default: all r_k)."""
     Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
-    G, U = rt.rtucker_decompose(Xd, list(r), p, s=s, seed=seed)
+    G, U = rt.rtucker_decompose(Xd, list(r), p, s=s, seed=seed, qr=qr)
     rt.sync()          # raises if a kernel reported a device-side failure
-    _, sig = rt.rtucker_factors(Xd, list(r), p, s=s, seed=seed, with_sigma=True)
+    _, sig = rt.rtucker_factors(Xd, list(r), p, s=s, seed=seed, with_sigma=True, qr=qr)
     rt.sync()
     Xo = np.asarray(X if x_for_oracle is None else x_for_oracle, dtype=np.float64)
     ref = tucker.sub_r_hosvd(Xo, list(r), p, s=s, seed=seed, with_core=(check_core is True))
@@ -631,3 +632,64 @@ def test_graph_replay_batched(rt):
         rt.sync()
         for a, b in zip(got, want):
             _same(a, b)
+
+
+# ----------------------------------------------------------------- factorisation forms (rt_options.qr)
+_QR_CASES = {
+    "small": lambda: (synth.tucker_tensor((40, 36, 150), (4, 5, 6), noise=1e-4, data_seed=5, dtype="f32"),
+                      (4, 5, 6), 3, 11),
+    "graded48": lambda: (synth.tucker_tensor((48, 48, 48, 48), (12, 12, 12, 12), noise=1e-6, data_seed=7,
+                                             core="graded"), (12,) * 4, 6, 2),
+    "widest70": lambda: (synth.tucker_tensor((70, 48, 48), (54, 8, 8), noise=1e-4, data_seed=10), (54, 8, 8), 10, 12),
+    "tall": lambda: (synth.tucker_tensor((3000, 8, 9), (6, 3, 3), noise=1e-4, data_seed=10), (6, 3, 3), 2, 8),
+}
+
+
+@pytest.mark.parametrize("qr", ["householder", "cholesky"])
+@pytest.mark.parametrize("case", sorted(_QR_CASES))
+def test_factorisation_forms_match_oracle(rt, qr, case):
+    # S5 and the W-step's R factor by Householder QR / TSQR, or by the Cholesky form
+    # (mixed-precision CholeskyQR2 of Z, Cholesky of the double-float Gram of B);
+    # the 3000-row mode takes Householder under either setting
+    X, r, p, seed = _QR_CASES[case]()
+    gap = 5e-3 if case == "widest70" else None
+    if gap:
+        Xd = torch.from_numpy(X).cuda()
+        G, U = rt.rtucker_decompose(Xd, list(r), p, seed=seed, qr=qr)
+        _, sig = rt.rtucker_factors(Xd, list(r), p, seed=seed, with_sigma=True, qr=qr)
+        rt.sync()
+        Xo = X.astype(np.float64)
+        ref = tucker.sub_r_hosvd(Xo, list(r), p, seed=seed, with_core=False)
+        for k in range(3):
+            s_ref = ref["modes"][k]["sigma"]
+            _, dev, _, _ = compare_factor(to_np(U[k]), ref["U"][k], s_ref, gap_min=gap)
+            assert dev <= U_TOL, (k, dev)
+            assert orthonormality(to_np(U[k])) < 1e-5
+            assert np.abs(to_np(sig[k]) - s_ref).max() <= 1e-5 * s_ref[0]
+        Gp = tucker.multi_ttm_t(Xo, [to_np(u) for u in U])
+        assert np.abs(to_np(G) - Gp).max() <= 1e-5 * np.abs(Gp).max()
+    else:
+        _run_and_compare(rt, X, r, p, seed=seed, qr=qr)
+
+
+def test_cholesky_form_falls_back_on_rank_deficient_sketch(rt):
+    # an exact multilinear-rank-2 tensor with r + p = 7: Z = Y Omega has rank 2, so the
+    # CholeskyQR of Z meets zero pivots and the kernel takes Householder instead; the two
+    # determined columns per mode match the oracle and every factor is orthonormal
+    X = synth.tucker_tensor((40, 36, 50), (2, 2, 2), noise=0.0, data_seed=13, dtype="f32")
+    Xd = torch.from_numpy(X).cuda()
+    G, U = rt.rtucker_decompose(Xd, [2, 2, 2], 5, seed=4, qr="cholesky")
+    rt.sync()
+    ref = tucker.sub_r_hosvd(X.astype(np.float64), [2, 2, 2], 5, seed=4)
+    for k in range(3):
+        _, dev, _, cov = compare_factor(to_np(U[k]), ref["U"][k], ref["modes"][k]["sigma"], min_covered=2)
+        assert dev <= U_TOL
+        assert orthonormality(to_np(U[k])) < 1e-5
+    assert rt.rtucker_relerr(Xd, G, U) < 1e-5
+
+
+def test_bench_shape_householder_form(rt):
+    # the benchmark's workload with the Householder / TSQR factorisations (qr = 1)
+    cfg = synth.ORDER4_128
+    X = synth.named(cfg)
+    _run_and_compare(rt, X, cfg["ranks"], cfg["p"], seed=cfg["seed"], check_core="projection", qr="householder")
