@@ -223,9 +223,10 @@ def _event_time(fn, steps, warmup):
 
 
 def measure_forms(rt, X, r, p, seed, relerr_fp32, steps):
-    """BF16 compute form and bfloat16-stored X on the 128^4 workload, against the
-    float32 plain form: time per decomposition and the error of the result
-    measured against the float32 X (the fixed-error bar is |delta relerr| <= 1e-5)."""
+    """BF16 compute form, bfloat16-stored X and the BF16 sketch on the 128^4 workload,
+    against the float32 plain form: time per decomposition and the error of the
+    result measured against the float32 X (the fixed-error bar is
+    |delta relerr| <= 1e-5)."""
     import torch
     nbytes32 = X.numel() * 4
     out = {}
@@ -242,6 +243,12 @@ def measure_forms(rt, X, r, p, seed, relerr_fp32, steps):
                           "relerr": e, "delta_relerr": e - relerr_fp32,
                           "meets_fixed_relerr": abs(e - relerr_fp32) <= 1e-5}
     del Xb
+    ms = _event_time(lambda: rt.rtucker_decompose(X, r, p, seed=seed, sketch="bf16"), steps, 3)
+    G, U = rt.rtucker_decompose(X, r, p, seed=seed, sketch="bf16")
+    e = rt.rtucker_relerr(X, G, U)
+    out["bf16_sketch"] = {"ms_per_decomp": ms, "input_gbs": nbytes32 / (ms * 1e-3) / 1e9, "relerr": e,
+                          "delta_relerr": e - relerr_fp32, "meets_fixed_relerr": abs(e - relerr_fp32) <= 1e-5,
+                          "form": "Z = Y Omega from bfloat16-rounded fibers and Omega, CholeskyQR2 of Z"}
     return out
 
 

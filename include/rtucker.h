@@ -114,7 +114,15 @@ typedef struct {
                           Larger unfoldings always take 1.  The one-sided Jacobi
                           SVD of R^T is the same in all; same factors to
                           rounding.                                            */
-  int32_t reserved[3]; /* must be zero                                          */
+  int32_t sketch;      /* 0 (default) float32 sketch Z = Y Omega; 1 BF16 sketch:
+                          Y and Omega rounded to bfloat16 (float32 accumulate)
+                          for Z only (the W-step and the core use the float32
+                          fibers), with Z's QR by the CholeskyQR2 of qr = 2
+                          unless qr = 1.  The rounding (2^-8 relative) can hide
+                          directions whose share of the sampled fibers lies
+                          below it; the benchmark reports its error.  Tucker
+                          entry points.                                        */
+  int32_t reserved[2]; /* must be zero                                          */
 } rt_options;
 
 /* ----------------------------------------------------------- handle
@@ -283,6 +291,15 @@ rt_status rtucker_loss_grad(rt_handle h, const void* X, rt_dtype dtype, int d, c
 rt_status rtucker_core_adjoint(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
                                const int32_t* r, const float* U, const float* Gbar, float* Xbar,
                                float* Ubar);
+
+/* rt_set_grad_recompute(h, 1): rtucker_loss_grad and rtucker_core_adjoint (for dU /
+ * Ubar) recompute the prefix contractions P_m = T x_0 U_0^T ... x_{m-1} U_{m-1}^T of
+ * every partial projection instead of keeping them in workspace: the handle's
+ * workspace drops by sum_k P_k (about r_0 / n_0 of the tensor for the largest), at
+ * the cost of d (d - 1) / 2 instead of d - 1 prefix contractions (re-reading T).
+ * Same results up to rounding order (identical here: the same kernels in the same
+ * order per chain).  0 (default) keeps them.  RT_EINVAL for other values. */
+rt_status rt_set_grad_recompute(rt_handle h, int enable);
 
 /* Relative reconstruction error ||X - (U_1..U_d) G||_F / ||X||_F computed on
  * the device in float64 (evaluator; not part of the decomposition; Sec. 3.3

@@ -102,7 +102,16 @@ def sign_rule(U):
     return U * s
 
 
-def range_finder(Y, pi, r, p, seed, node):
+def round_bf16(a):
+    """Round to bfloat16 (8 significant bits, round to nearest, ties to even) by way of
+    float32, returned as float64: the rounding of the BF16 sketch form."""
+    x = np.ascontiguousarray(np.asarray(a, dtype=np.float64).astype(np.float32))
+    b = x.view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return b.view(np.float32).astype(np.float64)
+
+
+def range_finder(Y, pi, r, p, seed, node, sketch_bf16=False):
     """The range finder of the loop body of Alg. 1 (and of the per-node body of
     Alg. 2) on a sampled matrix Y (n x s):
       Omega  = Gaussian s x (r+p) test matrix (keyed by the sampled indices pi),
@@ -110,9 +119,11 @@ def range_finder(Y, pi, r, p, seed, node):
                diag(R) > 0,
       W      = dominant r left singular vectors of Q^T Y,
       U      = Q W  (then the column-sign rule).
+    ``sketch_bf16``: the BF16 sketch form, Z from Y and Omega rounded to bfloat16
+    (the W-step keeps Y as given).
     """
     Omega = rng.sketch_matrix(pi, r + p, seed, node)
-    Z = Y @ Omega
+    Z = (round_bf16(Y) @ round_bf16(Omega)) if sketch_bf16 else Y @ Omega
     Q, R = np.linalg.qr(Z)  # LAPACK Householder (geqrf/orgqr)
     d = np.sign(np.diag(R))
     d[d == 0] = 1.0
@@ -131,7 +142,7 @@ def default_samples(shape):
     return [min(10 * nk, N // nk) for nk in shape]
 
 
-def sub_r_hosvd(X, r, p, s=None, seed=0, with_core=True, nodes=None):
+def sub_r_hosvd(X, r, p, s=None, seed=0, with_core=True, nodes=None, sketch_bf16=False):
     """[S, {U_k}] = Sub-R-HOSVD(X, r, p, s) (Alg. 1).
 
     For every mode k (independently: the loop is mode-parallel):
@@ -156,7 +167,7 @@ def sub_r_hosvd(X, r, p, s=None, seed=0, with_core=True, nodes=None):
         check_sizes(nk, N, r[k], p, s[k])
         pi = rng.fiber_indices(N, s[k], seed, nodes[k])
         Y = gather_fibers(X, k, k, pi)
-        out = range_finder(Y, pi, r[k], p, seed, nodes[k])
+        out = range_finder(Y, pi, r[k], p, seed, nodes[k], sketch_bf16=sketch_bf16)
         out.update(pi=pi, Y=Y)
         modes.append(out)
     U = [m["U"] for m in modes]

@@ -23,6 +23,7 @@ __all__ = [
     "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "ht_tree_from_children", "ht_alpha_w", "last_launch_count", "workspace_bytes",
     "set_timing", "get_timing", "STAGES", "rhtucker_root_transfer_noalloc", "BatchedDecomposition",
     "rtucker_loss_grad", "rtucker_core_adjoint", "set_wait_limit", "selftest_wait", "inject_fault",
+    "set_grad_recompute", "tucker_reconstruct_into",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -40,7 +41,8 @@ class RtError(RuntimeError):
 
 class _Options(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("overlap", ctypes.c_int32),
-                ("core", ctypes.c_int32), ("qr", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("core", ctypes.c_int32), ("qr", ctypes.c_int32), ("sketch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 _QR = {"auto": 0, "householder": 1, "cholesky": 2}
@@ -105,6 +107,7 @@ def load_library():
         "rt_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_uint32]),
         "rt_selftest_wait": (ctypes.c_int, [vp]),
         "rt_inject_fault": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
+        "rt_set_grad_recompute": (ctypes.c_int, [vp, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -274,7 +277,7 @@ _PREC = {"fp32": 0, "bf16": 1}
 _CORE = {"auto": 0, "tc": 1, "ffma": 2, "tune": 3}
 
 
-def _opts(prec, overlap=False, graph=False, core="auto", qr="auto"):
+def _opts(prec, overlap=False, graph=False, core="auto", qr="auto", sketch="fp32"):
     """rt_options for a precision form (the overlapped core schedule, CUDA-graph
     replay, the core kernels: "auto", "tc", "ffma" or "tune"; the range finder's
     factorisations: "auto", "householder" or "cholesky"), or None (defaults)."""
@@ -284,7 +287,9 @@ def _opts(prec, overlap=False, graph=False, core="auto", qr="auto"):
         raise ValueError("core must be 'auto', 'tc', 'ffma' or 'tune'")
     if qr not in _QR:
         raise ValueError("qr must be 'auto', 'householder' or 'cholesky'")
-    if prec == "fp32" and not overlap and not graph and core == "auto" and qr == "auto":
+    if sketch not in ("fp32", "bf16"):
+        raise ValueError("sketch must be 'fp32' or 'bf16'")
+    if prec == "fp32" and not overlap and not graph and core == "auto" and qr == "auto" and sketch == "fp32":
         return None
     o = _Options()
     o.prec = _PREC[prec]
@@ -292,6 +297,7 @@ def _opts(prec, overlap=False, graph=False, core="auto", qr="auto"):
     o.use_graph = 1 if graph else 0
     o.core = _CORE[core]
     o.qr = _QR[qr]
+    o.sketch = 1 if sketch == "bf16" else 0
     return ctypes.byref(o)
 
 
@@ -314,14 +320,15 @@ def rtucker_core(X, U, prec="fp32", core="auto"):
 
 
 def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32", overlap=False, graph=False, core="auto",
-                      qr="auto"):
+                      qr="auto", sketch="fp32"):
     """S1-S7: Sub-R-HOSVD; returns (G, [U_k]).  ``out`` = (Uflat, G) reuses buffers;
     ``prec`` "fp32" (default) or "bf16" (the BF16 compute form of the core pass);
     ``overlap`` runs the pass over X on the QR factors beside the SVD part of the
     range finder (see rt_options.overlap); ``graph`` replays the kernel sequence as
     a CUDA graph for repeated calls with the same buffers and shapes
     (rt_options.use_graph; pass ``out`` so that the output pointers repeat); ``qr``
-    the range finder's factorisations (rt_options.qr)."""
+    the range finder's factorisations (rt_options.qr); ``sketch`` "bf16" the
+    bfloat16 sketch (rt_options.sketch)."""
     lib = load_library()
     dt, d, n = _tensor_args(X)
     r = _as_list(r, d)
@@ -333,7 +340,7 @@ def rtucker_decompose(X, r, p, s=None, seed=0, out=None, prec="fp32", overlap=Fa
     h = _handle(X.device.index)
     sp = _i64(_as_list(s, d)) if s is not None else None
     _check(h, lib.rtucker_decompose(h, _ptr(X), dt, d, _i64(n), _i32(r), int(p), sp, ctypes.c_uint64(seed),
-                                    _opts(prec, overlap, graph, core, qr), _ptr(U), _ptr(G)))
+                                    _opts(prec, overlap, graph, core, qr, sketch), _ptr(U), _ptr(G)))
     return G, _split(U, n, r)
 
 
@@ -435,6 +442,31 @@ def rtucker_core_adjoint(X, U, Gbar, Xbar=True, Ubar=True):
     _check(h, lib.rtucker_core_adjoint(h, _ptr(X), _DT[X.dtype], d, _i64(n), _i32(r), _ptr(Uf), _ptr(Gbar),
                                        _ptr(xb), _ptr(ub)))
     return xb, (_split(ub, n, r) if Ubar else None)
+
+
+def tucker_reconstruct_into(G, U, out):
+    """out = G x_1 U_1 ... x_d U_d (the Tucker reconstruction, Sec. 3), out a
+    contiguous float32 n_1 x ... x n_d device tensor: the Xbar part of
+    rtucker_core_adjoint with Gbar = G (out stands in for X, which is not read
+    when Ubar is not asked for)."""
+    lib = load_library()
+    if out.dtype != torch.float32 or not out.is_contiguous() or not out.is_cuda:
+        raise ValueError("out must be a contiguous float32 CUDA tensor")
+    d, n = out.dim(), list(out.shape)
+    r = list(G.shape)
+    if len(r) != d or G.dtype != torch.float32 or not G.is_contiguous() or G.device != out.device:
+        raise ValueError("G must be a contiguous float32 r_1 x ... x r_d tensor on out's device")
+    Uf = _flat_factors(U, n, r, out.device)
+    h = _handle()
+    _check(h, lib.rtucker_core_adjoint(h, _ptr(out), 0, d, _i64(n), _i32(r), _ptr(Uf), _ptr(G), _ptr(out), None))
+    return out
+
+
+def set_grad_recompute(enable=True, device=None):
+    """rt_set_grad_recompute: the partial projections of the gradient path recompute
+    their prefix contractions instead of keeping them (less workspace)."""
+    h = _handle(device)
+    _check(h, load_library().rt_set_grad_recompute(h, 1 if enable else 0))
 
 
 class BatchedDecomposition:

@@ -135,6 +135,7 @@ struct rt_handle_s {
   int64_t stage_cnt[RT_NSTAGES] = {0};
   // injected host-side failures (rt_inject_fault, environment RT_FAULT=alloc[:count])
   int fault_alloc = 0;         // the next this many workspace growths fail as a failed cudaMalloc
+  int grad_recompute = 0;      // rt_set_grad_recompute: partial projections without kept prefixes
 };
 
 namespace {
@@ -253,6 +254,7 @@ struct ProbSpec {
   float* sigma_out;
   int64_t* idx_out;   // sampled indices straight to the caller (or null)
   int qr;             // rt_options.qr: 0 auto, 1 Householder / TSQR, 2 Cholesky form
+  int sketch;         // rt_options.sketch: 1 = bfloat16 sketch
 };
 
 struct ProbPlan {
@@ -298,10 +300,13 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   q.node = ps.node;
   q.fh = feistel_half(N);
   q.nzc = (int)((ps.s + SK_TJ - 1) / SK_TJ);
+  q.skbf16 = ps.sketch == 1 ? 1 : 0;
   // Cholesky form of S5 / S6 (rt_options.qr): unfoldings of at most QWF_MAX rows whose
   // Z also fits the single-block Householder QR it falls back to
   const bool chol = ps.qr != 1 && nS <= QWF_MAX && (int64_t)odd((int)nS) * c <= QR_MAXF;   // W-step
-  const bool chol_z = chol && ps.qr == 2;                                                  // S5
+  // S5 by CholeskyQR2 when asked, and in the BF16 form (its second pass restores the
+  // orthogonality the bfloat16 sketch does not need to carry)
+  const bool chol_z = chol && (ps.qr == 2 || (ps.qr == 0 && ps.sketch == 1));
   // TSQR of Z
   int rb = (QR_MAXF / c - 1) & ~31;
   if (rb < 32) rb = 32;
@@ -624,7 +629,8 @@ rt_status check_opts(rt_handle h, const rt_options* opt) {
   if (opt->use_graph != 0 && opt->use_graph != 1) return fail(h, RT_EINVAL, "use_graph must be 0 or 1");
   if (opt->core < 0 || opt->core > 3) return fail(h, RT_EINVAL, "core must be 0, 1, 2 or 3");
   if (opt->qr < 0 || opt->qr > 2) return fail(h, RT_EINVAL, "qr must be 0, 1 or 2");
-  for (int i = 0; i < 3; ++i)
+  if (opt->sketch != 0 && opt->sketch != 1) return fail(h, RT_EINVAL, "sketch must be 0 or 1");
+  for (int i = 0; i < 2; ++i)
     if (opt->reserved[i]) return fail(h, RT_EINVAL, "reserved option fields must be zero");
   return RT_OK;
 }
@@ -639,7 +645,7 @@ int64_t default_s(const int64_t* n, int d, int k) {
 // Tucker problems of one tensor appended to G.
 rt_status add_tucker_problems(rt_handle h, Group& G, Bump& bump, const void* X, rt_dtype dtype, int d,
                               const int64_t* n, const int32_t* r, int32_t p, const int64_t* s,
-                              uint64_t seed, float* U, float* sigma, int qr) {
+                              uint64_t seed, float* U, float* sigma, int qr, int sketch) {
   size_t uoff = 0, soff = 0;
   for (int k = 0; k < d; ++k) {
     ProbSpec ps{};
@@ -654,6 +660,7 @@ rt_status add_tucker_problems(rt_handle h, Group& G, Bump& bump, const void* X, 
     ps.seed = seed;
     ps.node = (uint32_t)k;
     ps.qr = qr;
+    ps.sketch = sketch;
     ps.U = U ? U + uoff : nullptr;
     ps.sigma_out = sigma ? sigma + soff : nullptr;
     ProbPlan pp;
@@ -693,6 +700,8 @@ int prec_of(const rt_options* opt) { return opt ? opt->prec : RT_PREC_FP32; }
 int core_of(const rt_options* opt) { return opt ? opt->core : 0; }
 
 int qr_of(const rt_options* opt) { return opt ? opt->qr : 0; }
+
+int sketch_of(const rt_options* opt) { return opt ? opt->sketch : 0; }
 
 // Contractions of the core G = X x_1 U_1^T ... x_d U_d^T, last modes first.  core
 // (rt_options.core): 0 auto, 1 tensor-core pass whenever the shape allows, 2 FFMA only
@@ -1171,7 +1180,7 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
   if ((st = init_device_attrs(h)) != RT_OK) return st;
   Group Gp;
   Bump bump;
-  st = add_tucker_problems(h, Gp, bump, X, dtype, d, n, r, p, s, seed, U, sigma, qr_of(opt));
+  st = add_tucker_problems(h, Gp, bump, X, dtype, d, n, r, p, s, seed, U, sigma, qr_of(opt), sketch_of(opt));
   if (st != RT_OK) return st;
   group_layout(Gp, bump);
   size_t o_zp = 0;
@@ -1351,6 +1360,12 @@ rt_status rt_set_wait_limit(rt_handle h, uint32_t polls) {
   if (e == cudaSuccess) e = diag_set_wait_limit(polls);
   if (cur != h->device) cudaSetDevice(cur);
   if (e != cudaSuccess) return cuda_fail(h, e, "rt_set_wait_limit");
+  return RT_OK;
+}
+
+rt_status rt_set_grad_recompute(rt_handle h, int enable) {
+  if (!h || (enable != 0 && enable != 1)) return RT_EINVAL;
+  h->grad_recompute = enable;
   return RT_OK;
 }
 
@@ -1619,29 +1634,52 @@ int enqueue_partials(rt_handle h, const void* T, int dtype, int d, const int64_t
                      float* const* prefix, float* chainA, float* chainB, float* ybuf, float* uscratch) {
   cudaStream_t st = h->stream;
   int nl = 0;
-  const void* A = T;
-  int adt = dtype;
-  for (int k = 1; k < d; ++k) {        // P_k = P_{k-1} x_{k-1} U_{k-1}^T
-    int64_t L = 1, R = 1;
-    for (int j = 0; j < k - 1; ++j) L *= r[j];
-    for (int j = k; j < d; ++j) R *= n[j];
-    nl += launch_ttm_t(A, adt, L, n[k - 1], R, U + uoff[k - 1], r[k - 1], prefix[k], st);
-    A = prefix[k];
-    adt = DT_F32;
+  // prefix == nullptr: recompute mode, every P_m is formed again from T in the
+  // ping-pong chain buffers instead of being kept
+  const bool keep = prefix != nullptr;
+  // P_m into `dst` (or, recomputing, into a chain buffer; *ping tracks the one used)
+  auto prefix_chain = [&](int m, int* ping) -> const void* {
+    const void* A = T;
+    int adt = dtype;
+    for (int k = 1; k <= m; ++k) {
+      int64_t L = 1, R = 1;
+      for (int j = 0; j < k - 1; ++j) L *= r[j];
+      for (int j = k; j < d; ++j) R *= n[j];
+      float* o = *ping ? chainB : chainA;
+      nl += launch_ttm_t(A, adt, L, n[k - 1], R, U + uoff[k - 1], r[k - 1], o, st);
+      A = o;
+      adt = DT_F32;
+      *ping ^= 1;
+    }
+    return A;
+  };
+  if (keep) {
+    const void* A = T;
+    int adt = dtype;
+    for (int k = 1; k < d; ++k) {        // P_k = P_{k-1} x_{k-1} U_{k-1}^T
+      int64_t L = 1, R = 1;
+      for (int j = 0; j < k - 1; ++j) L *= r[j];
+      for (int j = k; j < d; ++j) R *= n[j];
+      nl += launch_ttm_t(A, adt, L, n[k - 1], R, U + uoff[k - 1], r[k - 1], prefix[k], st);
+      A = prefix[k];
+      adt = DT_F32;
+    }
   }
   if (outCore) {                       // P_{d-1} x_{d-1} U_{d-1}^T
     int64_t L = 1;
     for (int j = 0; j < d - 1; ++j) L *= r[j];
-    nl += launch_ttm_t(prefix[d - 1], DT_F32, L, n[d - 1], 1, U + uoff[d - 1], r[d - 1], outCore, st);
+    int ping = 0;
+    const void* Pd = keep ? prefix[d - 1] : prefix_chain(d - 1, &ping);
+    nl += launch_ttm_t(Pd, DT_F32, L, n[d - 1], 1, U + uoff[d - 1], r[d - 1], outCore, st);
     if (scale != 1.f) nl += launch_scale_f32(outCore, L * r[d - 1], scale, st);
   }
   if (!outU) return nl;
   for (int m = 0; m < d; ++m) {
-    const void* Y = (m == 0) ? T : (const void*)prefix[m];
+    int ping = 0;
+    const void* Y = (m == 0) ? T : (keep ? (const void*)prefix[m] : prefix_chain(m, &ping));
     int ydt = (m == 0) ? dtype : DT_F32;
     int64_t sh[MAXD];
     for (int j = 0; j < d; ++j) sh[j] = (j < m) ? r[j] : n[j];
-    int ping = 0;
     for (int j = m + 1; j < d; ++j) {
       int64_t L = 1, R = 1;
       for (int q = 0; q < j; ++q) L *= sh[q];
@@ -1696,9 +1734,15 @@ rt_status rtucker_loss_grad(rt_handle h, const void* X, rt_dtype dtype, int d, c
   size_t oS[MAXD + 1] = {0};
   size_t oCA = 0, oCB = 0, oY = 0, oUS = 0;
   if (grads) {
-    for (int k = 1; k < d; ++k) oS[k] = bump.take(pl.prefix_floats[k] * 4);
-    oCA = bump.take(pl.chain_floats * 4);
-    oCB = bump.take(pl.chain_floats * 4);
+    // recompute mode keeps no prefixes; its chain buffers also hold the largest P_k
+    size_t chain = pl.chain_floats;
+    if (h->grad_recompute) {
+      for (int k = 1; k < d; ++k) chain = std::max(chain, pl.prefix_floats[k]);
+    } else {
+      for (int k = 1; k < d; ++k) oS[k] = bump.take(pl.prefix_floats[k] * 4);
+    }
+    oCA = bump.take(chain * 4);
+    oCB = bump.take(chain * 4);
     oY = bump.take(pl.y_floats * 4);
     size_t us = 1;
     for (int m = 0; m < d; ++m) {
@@ -1725,7 +1769,8 @@ rt_status rtucker_loss_grad(rt_handle h, const void* X, rt_dtype dtype, int d, c
   if (grads) {
     float* prefix[MAXD + 1] = {nullptr};
     for (int k = 1; k < d; ++k) prefix[k] = reinterpret_cast<float*>(ws + oS[k]);
-    const int got = enqueue_partials(h, R, DT_F32, d, n, r, U, uoff, G, -1.f, dU, dG, prefix,
+    const int got = enqueue_partials(h, R, DT_F32, d, n, r, U, uoff, G, -1.f, dU, dG,
+                                     h->grad_recompute ? nullptr : prefix,
                                      reinterpret_cast<float*>(ws + oCA), reinterpret_cast<float*>(ws + oCB),
                                      reinterpret_cast<float*>(ws + oY), reinterpret_cast<float*>(ws + oUS));
     if (got < 0) return fail(h, RT_EINVAL, "internal: partial projection plan");
@@ -1750,9 +1795,15 @@ rt_status rtucker_core_adjoint(rt_handle h, const void* X, rt_dtype dtype, int d
   size_t oS[MAXD + 1] = {0};
   size_t oCA = 0, oCB = 0, oY = 0, oUS = 0;
   if (Ubar) {
-    for (int k = 1; k < d; ++k) oS[k] = bump.take(pl.prefix_floats[k] * 4);
-    oCA = bump.take(pl.chain_floats * 4);
-    oCB = bump.take(pl.chain_floats * 4);
+    // recompute mode keeps no prefixes; its chain buffers also hold the largest P_k
+    size_t chain = pl.chain_floats;
+    if (h->grad_recompute) {
+      for (int k = 1; k < d; ++k) chain = std::max(chain, pl.prefix_floats[k]);
+    } else {
+      for (int k = 1; k < d; ++k) oS[k] = bump.take(pl.prefix_floats[k] * 4);
+    }
+    oCA = bump.take(chain * 4);
+    oCB = bump.take(chain * 4);
     oY = bump.take(pl.y_floats * 4);
     size_t us = 1;
     for (int m = 0; m < d; ++m) {
@@ -1776,7 +1827,8 @@ rt_status rtucker_core_adjoint(rt_handle h, const void* X, rt_dtype dtype, int d
   if (Ubar) {
     float* prefix[MAXD + 1] = {nullptr};
     for (int k = 1; k < d; ++k) prefix[k] = reinterpret_cast<float*>(ws + oS[k]);
-    const int got = enqueue_partials(h, X, (int)dtype, d, n, r, U, uoff, Gbar, 1.f, Ubar, nullptr, prefix,
+    const int got = enqueue_partials(h, X, (int)dtype, d, n, r, U, uoff, Gbar, 1.f, Ubar, nullptr,
+                                     h->grad_recompute ? nullptr : prefix,
                                      reinterpret_cast<float*>(ws + oCA), reinterpret_cast<float*>(ws + oCB),
                                      reinterpret_cast<float*>(ws + oY), reinterpret_cast<float*>(ws + oUS));
     if (got < 0) return fail(h, RT_EINVAL, "internal: partial projection plan");
@@ -1897,7 +1949,7 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
   Bump bump;
   for (int t = 0; t < T; ++t) {
     st = add_tucker_problems(h, Gp, bump, X[t], dtype, d[t], n[t], r[t], p, s ? s[t] : nullptr, seeds[t], U[t],
-                             nullptr, qr_of(opt));
+                             nullptr, qr_of(opt), sketch_of(opt));
     if (st != RT_OK) return st;
   }
   group_layout(Gp, bump);

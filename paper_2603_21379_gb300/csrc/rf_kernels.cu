@@ -81,15 +81,17 @@ __global__ void __launch_bounds__(256) k_gather_sketch(const RFProb* __restrict_
     const int64_t o = offs[jj];
     v[t] = (i < nS && o >= 0) ? load_x(q.X, q.dtype, o + i * rs) : 0.f;
   }
+  const bool bf = q.skbf16 != 0;
 #pragma unroll
   for (int t = 0; t < PER; ++t) {
     const int jj = tid / SK_TI + t * (256 / SK_TI);
     if (i < nS && offs[jj] >= 0) q.Yt[(j0 + jj) * nS + i] = v[t];
-    Ys[jj * SK_TI + ii] = v[t];
+    Ys[jj * SK_TI + ii] = bf ? __bfloat162float(__float2bfloat16_rn(v[t])) : v[t];
   }
   for (int e = tid; e < SK_TJ * cp; e += 256) {
     const int jj = e / cp, cc = e % cp;
-    Os[jj * CMAX + cc] = (j0 + jj < q.s && cc < c) ? q.Om[(j0 + jj) * c + cc] : 0.f;
+    const float o = (j0 + jj < q.s && cc < c) ? q.Om[(j0 + jj) * c + cc] : 0.f;
+    Os[jj * CMAX + cc] = bf ? __bfloat162float(__float2bfloat16_rn(o)) : o;
   }
   __syncthreads();
   const int ncg = cp >> 2;

@@ -81,6 +81,8 @@ struct RFProb {
   // Cholesky form: double-float Grams of the B-step's sample chunks
   float* Cp;               // [nbg][c][c][2] hi/lo words (upper triangles)
   int32_t nbg;             // number of sample chunks of the B-step Gram
+  int32_t skbf16;          // BF16 form: the sketch Z = Y Omega from bfloat16-rounded Y and
+                           // Omega (float32 accumulate); Y itself stays float32
 };
 
 // Problem lookup: blocks (or threads) are numbered consecutively over the

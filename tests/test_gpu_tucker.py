@@ -693,3 +693,31 @@ def test_bench_shape_householder_form(rt):
     cfg = synth.ORDER4_128
     X = synth.named(cfg)
     _run_and_compare(rt, X, cfg["ranks"], cfg["p"], seed=cfg["seed"], check_core="projection", qr="householder")
+
+
+@pytest.mark.parametrize("case", ["graded48", "bench128"])
+def test_bf16_sketch_form_matches_its_oracle(rt, case):
+    # rt_options.sketch = 1: Z from bfloat16-rounded fibers and Omega (float32 sums),
+    # CholeskyQR2 of Z; the oracle rounds the same values (round to nearest even) and
+    # forms Z in float64.  Factors within 1e-4, core = projection on the factors, and
+    # the relative error that of the oracle's BF16 sketch form.
+    if case == "bench128":
+        cfg = synth.ORDER4_128
+        X, r, p, seed = synth.named(cfg), list(cfg["ranks"]), cfg["p"], cfg["seed"]
+    else:
+        X, r, p, seed = synth.tucker_tensor((48, 48, 48, 48), (12,) * 4, noise=1e-6, data_seed=7, core="graded"), \
+            [12] * 4, 6, 2
+    Xd = torch.from_numpy(X).cuda()
+    G, U = rt.rtucker_decompose(Xd, r, p, seed=seed, sketch="bf16")
+    rt.sync()
+    Xo = np.asarray(X, dtype=np.float64)
+    ref = tucker.sub_r_hosvd(Xo, r, p, seed=seed, with_core=False, sketch_bf16=True)
+    Un = [to_np(u) for u in U]
+    for k in range(len(r)):
+        _, dev, _, _ = compare_factor(Un[k], ref["U"][k], ref["modes"][k]["sigma"], min_covered=r[k] // 2)
+        assert dev <= U_TOL, (k, dev)
+        assert orthonormality(Un[k]) < 1e-5
+    Gp = tucker.multi_ttm_t(Xo, Un)
+    assert np.abs(to_np(G) - Gp).max() <= 1e-5 * np.abs(Gp).max()
+    er = tucker.relerr(Xo, tucker.reconstruct(tucker.multi_ttm_t(Xo, ref["U"]), ref["U"]))
+    assert abs(rt.rtucker_relerr(Xd, G, U) - er) <= RELERR_TOL

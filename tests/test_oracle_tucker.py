@@ -210,3 +210,29 @@ def test_argument_rules():
         tucker.sub_r_hosvd(X, 2, p=1, s=[2, 20, 20])  # s < r + p
     with pytest.raises(ValueError):
         tucker.sub_r_hosvd(X, 2, p=1, s=[31, 20, 20])  # s > n_{!=1} = 30
+
+
+def test_bfloat16_rounding_matches_torch_and_its_definition():
+    # round to nearest even at 8 significant bits: torch's own conversion as the
+    # independent reference, exact values unchanged, a tie rounded to even
+    torch = pytest.importorskip("torch")
+    rs = np.random.default_rng(5)
+    a = np.concatenate([rs.standard_normal(20000) * 10.0 ** rs.integers(-6, 6, 20000),
+                        [0.0, 1.0, -2.5, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 65504.0]])
+    want = torch.from_numpy(a.astype(np.float32)).to(torch.bfloat16).double().numpy()
+    got = tucker.round_bf16(a)
+    assert np.array_equal(got, want)
+    assert tucker.round_bf16([1.0 + 2 ** -8])[0] == 1.0                 # tie -> even
+    assert tucker.round_bf16([1.0 + 3 * 2 ** -8])[0] == 1.0 + 2 ** -6   # tie -> even (up)
+    assert np.all(np.abs(got - a.astype(np.float32)) <= 2 ** -8 * np.abs(a.astype(np.float32)))
+
+
+def test_bf16_sketch_form_without_rounding_error_is_the_plain_form():
+    # data that bfloat16 represents exactly: the BF16 sketch form changes nothing
+    rs = np.random.default_rng(7)
+    X = tucker.round_bf16(rs.integers(-64, 64, size=(9, 8, 7)).astype(np.float64) / 8.0).reshape(9, 8, 7)
+    a = tucker.sub_r_hosvd(X, [3, 3, 3], 2, seed=4, with_core=False)
+    b = tucker.sub_r_hosvd(X, [3, 3, 3], 2, seed=4, with_core=False, sketch_bf16=True)
+    for k in range(3):
+        Zr = a["modes"][k]["Y"] @ tucker.round_bf16(a["modes"][k]["Omega"])
+        assert np.allclose(b["modes"][k]["Z"], Zr, rtol=1e-13, atol=1e-13)
