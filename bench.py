@@ -223,8 +223,8 @@ def _event_time(fn, steps, warmup):
 
 
 def measure_forms(rt, X, r, p, seed, relerr_fp32, steps):
-    """BF16 compute form, bfloat16-stored X and the BF16 sketch on the 128^4 workload,
-    against the float32 plain form: time per decomposition and the error of the
+    """BF16 compute form, bfloat16-stored X, the BF16 sketch and float8-stored X on the
+    128^4 workload, against the float32 plain form: time per decomposition and the error of the
     result measured against the float32 X (the fixed-error bar is
     |delta relerr| <= 1e-5)."""
     import torch
@@ -249,6 +249,27 @@ def measure_forms(rt, X, r, p, seed, relerr_fp32, steps):
     out["bf16_sketch"] = {"ms_per_decomp": ms, "input_gbs": nbytes32 / (ms * 1e-3) / 1e9, "relerr": e,
                           "delta_relerr": e - relerr_fp32, "meets_fixed_relerr": abs(e - relerr_fp32) <= 1e-5,
                           "form": "Z = Y Omega from bfloat16-rounded fibers and Omega, CholeskyQR2 of Z"}
+    # float8 storage: E4M3 codes with one power-of-two scale per 128 x 128 slab, packed
+    # once (timed apart); the decomposition reads the packed buffer
+    pack_ms = _event_time(lambda: rt.quantize_fp8(X), 3, 1)
+    Xq = rt.quantize_fp8(X)
+    ms = _event_time(lambda: rt.rtucker_decompose(Xq, r, p, seed=seed), steps, 3)
+    G, U = rt.rtucker_decompose(Xq, r, p, seed=seed)
+    e = rt.rtucker_relerr(X, G, U)
+    e_stored = rt.rtucker_relerr(Xq, G, U)
+    rt.set_timing(True)
+    rt.get_timing(reset=True)
+    for _ in range(steps):
+        rt.rtucker_decompose(Xq, r, p, seed=seed)
+    stg = rt.get_timing(reset=True)
+    rt.set_timing(False)
+    out["fp8_stored"] = {"ms_per_decomp": ms, "input_gbs": Xq.data.numel() / (ms * 1e-3) / 1e9,
+                         "relerr": e, "relerr_vs_stored_values": e_stored, "delta_relerr": e - relerr_fp32,
+                         "meets_fixed_relerr": abs(e - relerr_fp32) <= 1e-5, "pack_ms": pack_ms,
+                         "stage_ms_per_decomp": {k: v[0] / steps for k, v in stg.items() if v[1]},
+                         "form": "X as E4M3 codes + per-slab power-of-two scales (1 byte/element); "
+                                 "core pass kind::f8f6f4 with U_2 in four E4M3 terms"}
+    del Xq
     return out
 
 

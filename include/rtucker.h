@@ -51,7 +51,17 @@ typedef enum {
   RT_ENOTSUP = 7    /* valid but unsupported combination                       */
 } rt_status;
 
-typedef enum { RT_F32 = 0, RT_F64 = 1, RT_BF16 = 2 } rt_dtype; /* storage type of X */
+/* Storage type of X.  RT_F8E4M3 is a packed float8 form made by rt_quantize_fp8:
+ * one E4M3 byte per element (C order; 1 sign, 4 exponent bits with bias 7,
+ * 3 mantissa bits, no infinity) followed, at byte offset rt_fp8_scale_offset,
+ * by one float32 scale per slab of the last two modes (X[i_0..i_{d-3}, :, :],
+ * slab index in C order; the whole matrix when d = 2).  Element value = code
+ * value x its slab's scale.  The buffer is rt_fp8_bytes long and 16-byte
+ * aligned.  Entry points that take it: rtucker_sketch, rtucker_factors,
+ * rtucker_core, rtucker_decompose and rtucker_relerr, for shapes the tensor-core
+ * pass over X takes (n_{d-2} <= 128, n_{d-1} a multiple of 16, r_{d-2} <= 64,
+ * r_{d-1} <= 32); RT_ENOTSUP for other shapes and other entry points. */
+typedef enum { RT_F32 = 0, RT_F64 = 1, RT_BF16 = 2, RT_F8E4M3 = 3 } rt_dtype;
 
 typedef enum {
   RT_PREC_FP32 = 0, /* float32-accurate arithmetic throughout (default)         */
@@ -300,6 +310,30 @@ rt_status rtucker_core_adjoint(rt_handle h, const void* X, rt_dtype dtype, int d
  * Same results up to rounding order (identical here: the same kernels in the same
  * order per chain).  0 (default) keeps them.  RT_EINVAL for other values. */
 rt_status rt_set_grad_recompute(rt_handle h, int enable);
+
+/* ------------------------------------------------------- float8 storage of X
+ * The FP8 form of the pass over X (an extension of Alg. 1, which computes in the
+ * input's precision): X stored as E4M3 bytes with one power-of-two scale per slab
+ * of the last two modes, a quarter of float32's bytes.  The decomposition of the
+ * packed tensor is that of its stored values (code x scale), computed with the
+ * float32-level arithmetic of the plain form; the storage error itself is the
+ * rounding of X to the E4M3 grid (at most 2^-4 relative for elements above 2^-14
+ * of their slab's largest magnitude).
+ *
+ * rt_fp8_bytes: size in bytes of the packed buffer of a tensor of order d and
+ * sizes n (0 for invalid sizes).  rt_fp8_scale_offset: byte offset of its scales
+ * (the element count rounded up to 256). */
+size_t rt_fp8_bytes(int d, const int64_t* n);
+size_t rt_fp8_scale_offset(int d, const int64_t* n);
+
+/* rt_quantize_fp8: pack the DEVICE tensor X (float32 / float64 / bfloat16, C
+ * order) into the DEVICE buffer Xq (rt_fp8_bytes, 16-byte aligned, caller-owned).
+ * Per slab: amax = max |x|, written amax = f 2^e with 0.5 <= f < 1 (e = 0 for an
+ * all-zero slab); the scale is 2^(e-8), so |x| / scale < 256; each code is the
+ * E4M3 value nearest to x / scale, ties to the even mantissa (the division by a
+ * power of two is exact, so the rounding decision is exact).  X must be finite.
+ * Asynchronous on the handle's stream; allocates nothing. */
+rt_status rt_quantize_fp8(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, void* Xq);
 
 /* Relative reconstruction error ||X - (U_1..U_d) G||_F / ||X||_F computed on
  * the device in float64 (evaluator; not part of the decomposition; Sec. 3.3

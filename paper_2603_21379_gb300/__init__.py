@@ -23,13 +23,13 @@ __all__ = [
     "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "ht_tree_from_children", "ht_alpha_w", "last_launch_count", "workspace_bytes",
     "set_timing", "get_timing", "STAGES", "rhtucker_root_transfer_noalloc", "BatchedDecomposition",
     "rtucker_loss_grad", "rtucker_core_adjoint", "set_wait_limit", "selftest_wait", "inject_fault",
-    "set_grad_recompute", "tucker_reconstruct_into",
+    "set_grad_recompute", "tucker_reconstruct_into", "Fp8Tensor", "quantize_fp8",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIBNAME = "librtucker.so"
 
-RT_F32, RT_F64, RT_BF16 = 0, 1, 2
+RT_F32, RT_F64, RT_BF16, RT_F8E4M3 = 0, 1, 2, 3
 _DT = {torch.float32: RT_F32, torch.float64: RT_F64, torch.bfloat16: RT_BF16}
 
 
@@ -108,6 +108,9 @@ def load_library():
         "rt_selftest_wait": (ctypes.c_int, [vp]),
         "rt_inject_fault": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int]),
         "rt_set_grad_recompute": (ctypes.c_int, [vp, ctypes.c_int]),
+        "rt_fp8_bytes": (ctypes.c_size_t, [ctypes.c_int, P64]),
+        "rt_fp8_scale_offset": (ctypes.c_size_t, [ctypes.c_int, P64]),
+        "rt_quantize_fp8": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -176,7 +179,60 @@ def _as_list(v, d):
     return [int(v)] * d
 
 
+class Fp8Tensor:
+    """A tensor in the library's float8 storage (RT_F8E4M3, made by
+    ``quantize_fp8``): ``data`` is the packed device buffer (uint8, E4M3 codes in
+    C order, then one float32 power-of-two scale per slab of the last two modes),
+    ``shape`` the tensor's sizes.  Accepted wherever the header lists RT_F8E4M3."""
+
+    def __init__(self, data, shape):
+        self.data = data
+        self.shape = tuple(int(v) for v in shape)
+        self.is_cuda = data.is_cuda
+        self.device = data.device
+
+    def data_ptr(self):
+        return self.data.data_ptr()
+
+    def dim(self):
+        return len(self.shape)
+
+    def is_contiguous(self):
+        return True
+
+    @property
+    def codes(self):
+        """The E4M3 codes, uint8, in the tensor's shape (a view of ``data``)."""
+        return self.data[:_prod(self.shape)].view(self.shape)
+
+    @property
+    def scales(self):
+        """The per-slab scales, float32 (a view of ``data``)."""
+        off = int(load_library().rt_fp8_scale_offset(len(self.shape), _i64(self.shape)))
+        nslab = _prod(self.shape[:-2])
+        return self.data[off:off + 4 * nslab].view(torch.float32)
+
+
+def quantize_fp8(X):
+    """Pack a CUDA tensor (float32 / float64 / bfloat16, C order) into float8 storage
+    (rt_quantize_fp8): per slab of the last two modes a power-of-two scale 2^(e-8)
+    with max |x| = f 2^e, 0.5 <= f < 1, and the nearest E4M3 code of x / scale."""
+    lib = load_library()
+    dt, d, n = _tensor_args(X)
+    if dt == 3:
+        return X
+    nbytes = int(lib.rt_fp8_bytes(d, _i64(n)))
+    if nbytes == 0:
+        raise ValueError("invalid sizes for float8 storage")
+    data = torch.empty(nbytes, dtype=torch.uint8, device=X.device)
+    h = _handle(X.device.index)
+    _check(h, lib.rt_quantize_fp8(h, _ptr(X), dt, d, _i64(n), _ptr(data)))
+    return Fp8Tensor(data, n)
+
+
 def _tensor_args(X):
+    if isinstance(X, Fp8Tensor):
+        return 3, len(X.shape), list(X.shape)
     if not X.is_cuda:
         raise ValueError("X must be a CUDA tensor")
     if X.dtype not in _DT:

@@ -208,7 +208,25 @@ void drain_timing(rt_handle h) {
   h->ev_open.clear();
 }
 
-int dtype_size(rt_dtype t) { return t == RT_F64 ? 8 : (t == RT_BF16 ? 2 : 4); }
+int dtype_size(rt_dtype t) { return t == RT_F64 ? 8 : t == RT_BF16 ? 2 : t == RT_F8E4M3 ? 1 : 4; }
+
+// Packed float8 storage: codes (prod n bytes), then at the element count rounded up
+// to 256 bytes one float32 scale per slab of the last two modes.
+size_t fp8_scale_offset(int d, const int64_t* n) {
+  size_t t = 1;
+  for (int k = 0; k < d; ++k) t *= (size_t)n[k];
+  return (t + 255) & ~(size_t)255;
+}
+
+int64_t fp8_slabs(int d, const int64_t* n) {
+  int64_t S = 1;
+  for (int k = 0; k + 2 < d; ++k) S *= n[k];
+  return S;
+}
+
+const float* fp8_scales(const void* X, int d, const int64_t* n) {
+  return reinterpret_cast<const float*>(static_cast<const char*>(X) + fp8_scale_offset(d, n));
+}
 
 bool mul_ok(int64_t a, int64_t b, int64_t* out) {
   if (a <= 0 || b <= 0) return false;
@@ -290,6 +308,10 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   if (nS >= ((int64_t)1 << 31)) return fail(h, RT_ENOTSUP, "unfolding with 2^31 or more rows");
   q.X = ps.X;
   q.dtype = (int)ps.dtype;
+  if (ps.dtype == RT_F8E4M3) {
+    q.xsc = fp8_scales(ps.X, d, ps.n);
+    q.xslab = ps.n[d - 2] * ps.n[d - 1];
+  }
   q.nS = nS;
   q.N = N;
   q.rowstride = stride[ps.b];
@@ -607,10 +629,14 @@ size_t group_stage_bytes(const Group& G) {
   return align_up(sizeof(RFProb) * np) + align_up(sizeof(int64_t) * group_rows(G, nullptr) * (np + 1));
 }
 
-rt_status check_tensor(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, int64_t* total) {
+rt_status check_tensor(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, int64_t* total,
+                       bool allow_f8 = false) {
   if (!h) return RT_EINVAL;
   if (!X) return fail(h, RT_EINVAL, "X is null");
-  if (dtype != RT_F32 && dtype != RT_F64 && dtype != RT_BF16) return fail(h, RT_EINVAL, "unknown dtype");
+  if (dtype == RT_F8E4M3 && !allow_f8)
+    return fail(h, RT_ENOTSUP, "float8 storage is taken by rtucker_sketch/factors/core/decompose/relerr only");
+  if (dtype != RT_F32 && dtype != RT_F64 && dtype != RT_BF16 && dtype != RT_F8E4M3)
+    return fail(h, RT_EINVAL, "unknown dtype");
   if (d < 2 || d > MAXD) return fail(h, RT_EINVAL, "need 2 <= d <= 16");
   if (!n) return fail(h, RT_EINVAL, "n is null");
   int64_t t = 1;
@@ -618,8 +644,20 @@ rt_status check_tensor(rt_handle h, const void* X, rt_dtype dtype, int d, const 
     if (n[k] < 1) return fail(h, RT_EINVAL, "need n_k >= 1");
     if (!mul_ok(t, n[k], &t)) return fail(h, RT_EINVAL, "tensor too large (prod n >= 2^62)");
   }
-  if (((uintptr_t)X) % (uintptr_t)dtype_size(dtype)) return fail(h, RT_EINVAL, "X is misaligned");
+  if (((uintptr_t)X) % (uintptr_t)(dtype == RT_F8E4M3 ? 16 : dtype_size(dtype)))
+    return fail(h, RT_EINVAL, "X is misaligned");
   if (total) *total = t;
+  return RT_OK;
+}
+
+// Shapes whose float8 storage the library takes: those of the tensor-core pass over X
+// (its FP8 form reads the codes with TMA and contracts them with kind::f8f6f4 MMAs).
+rt_status check_fp8_shape(rt_handle h, int d, const int64_t* n, const int32_t* r) {
+  if (!r) return fail(h, RT_EINVAL, "r is null");
+  if (n[d - 2] > 128 || n[d - 1] % 16 != 0 || r[d - 2] > 64 || r[d - 1] > 32 || r[d - 2] < 1 || r[d - 1] < 1)
+    return fail(h, RT_ENOTSUP,
+                "float8 storage needs n_{d-2} <= 128, n_{d-1} a multiple of 16, r_{d-2} <= 64, r_{d-1} <= 32");
+  if (fp8_slabs(d, n) * n[d - 2] >= ((int64_t)1 << 31)) return fail(h, RT_ENOTSUP, "float8 storage: too many rows");
   return RT_OK;
 }
 
@@ -728,17 +766,21 @@ int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_
   // the last two modes in one tensor-core pass over X, when the shape allows
   const bool tc_pref = core == 1 || (core == 0 && n[d - 2] >= TC_MIN_SIDE && n[d - 1] >= TC_MIN_SIDE) ||
                        (core == 0 && !slab2_fits(n[d - 2], n[d - 1], 1, r[d - 2], r[d - 1]));
-  if (core != 2 && tc_pref && (dtype == RT_F32 || dtype == RT_BF16) && d >= 2) {
+  if (dtype == RT_F8E4M3) core = 1;   // the float8 codes are read by the tensor-core pass only
+  if (core != 2 && (tc_pref || dtype == RT_F8E4M3) && (dtype == RT_F32 || dtype == RT_BF16 || dtype == RT_F8E4M3) &&
+      d >= 2) {
     int64_t S = 1;
     for (int j = 0; j < d - 2; ++j) S *= n[j];
     float* out = (d == 2) ? G : bufA;
     int got = 0;
     {
       StageTimer tm(h, 1);
-      const int xmode = (dtype == RT_BF16) ? 1 : (prec == RT_PREC_BF16 ? 2 : 0);
+      const int xmode = (dtype == RT_F8E4M3) ? 3 : (dtype == RT_BF16) ? 1 : (prec == RT_PREC_BF16 ? 2 : 0);
       got = launch_core2_tc(xmode, X, S, (int)n[d - 2], (int)n[d - 1], U + uoff[d - 2],
-                            r[d - 2], U + uoff[d - 1], r[d - 1], out, h->d_status, st);
+                            r[d - 2], U + uoff[d - 1], r[d - 1], out, h->d_status, st, 0,
+                            dtype == RT_F8E4M3 ? fp8_scales(X, d, n) : nullptr);
     }
+    if (got == 0 && dtype == RT_F8E4M3) return -1;   // no other kernel reads the codes
     if (got > 0) {
       nl += got;
       A = out;
@@ -1173,9 +1215,11 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
                      int32_t p, const int64_t* s, uint64_t seed, const rt_options* opt, float* U,
                      float* sigma, float* G, float* Zout) {
   rt_status st;
-  if ((st = check_tensor(h, X, dtype, d, n, nullptr)) != RT_OK) return st;
+  if ((st = check_tensor(h, X, dtype, d, n, nullptr, true)) != RT_OK) return st;
   if ((st = check_opts(h, opt)) != RT_OK) return st;
   if (!r) return fail(h, RT_EINVAL, "r is null");
+  if (dtype == RT_F8E4M3 && (st = check_fp8_shape(h, d, n, r)) != RT_OK) return st;
+  if (dtype == RT_F8E4M3 && core_of(opt) == 2) return fail(h, RT_ENOTSUP, "float8 storage needs the tensor-core pass");
   if ((st = check_prior_status(h)) != RT_OK) return st;
   if ((st = init_device_attrs(h)) != RT_OK) return st;
   Group Gp;
@@ -1208,6 +1252,7 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
   if (overlap && (st = ensure_side(h)) != RT_OK) return st;
   if (G && !U) return fail(h, RT_EINVAL, "U is required with G");
   int core = core_of(opt);
+  if (core == 3 && dtype == RT_F8E4M3) core = 1;
   if (core == 3) {
     if (G && !overlap) {
       if ((st = tune_core(h, X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + o_bufA),
@@ -1285,9 +1330,12 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
       *nk += launch_range_finder(Gp.g, h->stream, h->d_status);
     }
     if (Zout) *nk += launch_sketch_sum(Gp.g, reinterpret_cast<float* const*>(h->ws + o_zp), h->stream);
-    if (G)
-      *nk += enqueue_core(h, X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + o_bufA),
-                          reinterpret_cast<float*>(h->ws + o_bufB), prec_of(opt), core);
+    if (G) {
+      const int got = enqueue_core(h, X, dtype, d, n, r, U, G, reinterpret_cast<float*>(h->ws + o_bufA),
+                                   reinterpret_cast<float*>(h->ws + o_bufB), prec_of(opt), core);
+      if (got < 0) return fail(h, RT_ENOTSUP, "float8 storage: the tensor-core pass did not take the shape");
+      *nk += got;
+    }
     return RT_OK;
   });
   if (st != RT_OK) return st;
@@ -1367,6 +1415,32 @@ rt_status rt_set_grad_recompute(rt_handle h, int enable) {
   if (!h || (enable != 0 && enable != 1)) return RT_EINVAL;
   h->grad_recompute = enable;
   return RT_OK;
+}
+
+size_t rt_fp8_scale_offset(int d, const int64_t* n) {
+  if (d < 2 || d > MAXD || !n) return 0;
+  int64_t t = 1;
+  for (int k = 0; k < d; ++k)
+    if (n[k] < 1 || !mul_ok(t, n[k], &t)) return 0;
+  return fp8_scale_offset(d, n);
+}
+
+size_t rt_fp8_bytes(int d, const int64_t* n) {
+  const size_t off = rt_fp8_scale_offset(d, n);
+  if (!off) return 0;
+  return (off + 4 * (size_t)fp8_slabs(d, n) + 15) & ~(size_t)15;
+}
+
+rt_status rt_quantize_fp8(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, void* Xq) {
+  rt_status st;
+  if ((st = check_tensor(h, X, dtype, d, n, nullptr)) != RT_OK) return st;
+  if (!Xq || ((uintptr_t)Xq & 15u)) return fail(h, RT_EINVAL, "Xq must be a 16-byte aligned device pointer");
+  if ((st = check_prior_status(h)) != RT_OK) return st;
+  const int64_t S = fp8_slabs(d, n), slab = n[d - 2] * n[d - 1];
+  float* sc = reinterpret_cast<float*>(static_cast<char*>(Xq) + fp8_scale_offset(d, n));
+  const int nl = launch_quantize_fp8(X, (int)dtype, S, slab, static_cast<unsigned char*>(Xq), sc, h->stream);
+  if (nl < 0) return fail(h, RT_ENOTSUP, "float8 packing: too many slab chunks");
+  return finish(h, nl);
 }
 
 rt_status rt_selftest_wait(rt_handle h) {
@@ -1519,11 +1593,13 @@ rt_status rtucker_decompose(rt_handle h, const void* X, rt_dtype dtype, int d, c
 rt_status rtucker_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
                        const float* U, const rt_options* opt, float* G) {
   rt_status st;
-  if ((st = check_tensor(h, X, dtype, d, n, nullptr)) != RT_OK) return st;
+  if ((st = check_tensor(h, X, dtype, d, n, nullptr, true)) != RT_OK) return st;
   if ((st = check_opts(h, opt)) != RT_OK) return st;
   if (!r || !U || !G) return fail(h, RT_EINVAL, "r, U and G are required");
   for (int k = 0; k < d; ++k)
     if (r[k] < 1) return fail(h, RT_EINVAL, "need r_k >= 1");
+  if (dtype == RT_F8E4M3 && (st = check_fp8_shape(h, d, n, r)) != RT_OK) return st;
+  if (dtype == RT_F8E4M3 && core_of(opt) == 2) return fail(h, RT_ENOTSUP, "float8 storage needs the tensor-core pass");
   if ((st = check_prior_status(h)) != RT_OK) return st;
   if ((st = init_device_attrs(h)) != RT_OK) return st;
   Bump bump;
@@ -1533,9 +1609,11 @@ rt_status rtucker_core(rt_handle h, const void* X, rt_dtype dtype, int d, const 
   float* bufA = reinterpret_cast<float*>(h->ws + oA);
   float* bufB = reinterpret_cast<float*>(h->ws + oB);
   int core = core_of(opt);
+  if (core == 3 && dtype == RT_F8E4M3) core = 1;
   if (core == 3 && (st = tune_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec_of(opt), &core)) != RT_OK)
     return st;
   const int nl = enqueue_core(h, X, dtype, d, n, r, U, G, bufA, bufB, prec_of(opt), core);
+  if (nl < 0) return fail(h, RT_ENOTSUP, "float8 storage: the tensor-core pass did not take the shape");
   return finish(h, nl);
 }
 
@@ -2092,8 +2170,10 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
 rt_status rtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
                          const float* U, const float* G, double* out) {
   rt_status st;
-  if ((st = check_tensor(h, X, dtype, d, n, nullptr)) != RT_OK) return st;
+  if ((st = check_tensor(h, X, dtype, d, n, nullptr, true)) != RT_OK) return st;
   if (!r || !U || !G || !out) return fail(h, RT_EINVAL, "r, U, G and out are required");
+  if (dtype == RT_F8E4M3 && !tucker_relerr_slab_fits(d, n, r))
+    return fail(h, RT_ENOTSUP, "evaluator: float8 storage needs r_{d-2} n_{d-1} doubles within 200 KB");
   const size_t sd = tucker_relerr_scratch(d, n, r);
   Bump bump;
   const size_t o = bump.take(sd * 8);
@@ -2105,7 +2185,7 @@ rt_status rtucker_relerr(rt_handle h, const void* X, rt_dtype dtype, int d, cons
   if (!tucker_relerr_supported(d, n, r)) return fail(h, RT_ENOTSUP, "evaluator: r_d above 64 with a large slab");
   double* res = reinterpret_cast<double*>(h->ws + o_res);
   const int nl = launch_tucker_relerr(X, (int)dtype, d, n, r, Uk, G, reinterpret_cast<double*>(h->ws + o), sd, res,
-                                      h->stream);
+                                      h->stream, dtype == RT_F8E4M3 ? fp8_scales(X, d, n) : nullptr);
   h->launches = nl;
   RT_CUDA(h, cudaGetLastError());
   double hr[2];

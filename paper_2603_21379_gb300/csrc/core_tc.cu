@@ -13,7 +13,14 @@
 // the result carries float32-level accuracy (about 2^-16 relative per
 // product).  X modes: 0 = float32 X split into hi + lo (default); 1 = bfloat16
 // X as stored (one term); 2 = float32 X rounded to one bf16 term (the BF16
-// compute form).  U_1, U_2 and the intermediate T are always split in two.
+// compute form); 3 = E4M3 codes with one power-of-two scale per slab (the FP8
+// storage form).  U_1 and the intermediate T are always split in two bf16
+// terms; U_2 too, except in mode 3, where MMA1 is kind::f8f6f4 (K = 32 per
+// instruction, A = the codes straight from the stage) and U_2 is four E4M3
+// terms u = sigma (t_1 + t_2 / 32 + t_3 / 32^2 + t_4 / 32^3), each term the
+// nearest E4M3 value to what the previous ones left (about 2^-16 relative in
+// all, as two bf16 terms); the code values are exact, so each product is exact
+// and only the float32 accumulation rounds.
 //
 // Data path per CTA (persistent, one per SM, warp-specialised, 14 warps):
 //   warp 0      TMA producer: 128-byte-wide boxes (32 float32 or 64 bf16
@@ -113,6 +120,7 @@ struct Core2Args {
   const float* U1;   // n1 x r1
   const float* U2;   // n2 x r2
   float* P;          // S x r1 x r2
+  const float* xscale;  // mode 3: one scale per slab
   int64_t S;
   int n1, n2, r1, r2;
   int* status;
@@ -133,6 +141,17 @@ __device__ __forceinline__ void mma_bf16_ts(uint32_t d, uint32_t a, uint64_t b, 
       "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(
           d),
       "r"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// 8-bit MMA operands (kind::f8f6f4), E4M3 A and B, f32 D.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_f8_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
 // (hi, lo) bf16 pairs of two floats packed low = x0, high = x1.
@@ -158,6 +177,11 @@ __device__ __forceinline__ int sw_off16(int row, int k, int rows) {
   const int kc = k >> 6, kl = k & 63;
   return kc * rows * 128 + row * 128 + ((((kl >> 3) ^ (row & 7)) << 4) | ((kl & 7) << 1));
 }
+// The same for 8-bit elements: 128-element K chunks.
+__device__ __forceinline__ int sw_off8(int row, int k, int rows) {
+  const int kc = k >> 7, kl = k & 127;
+  return kc * rows * 128 + row * 128 + ((((kl >> 4) ^ (row & 7)) << 4) | (kl & 15));
+}
 
 constexpr int NCONV = 8;                       // converter warps: two groups of four quadrants
 constexpr int W_CONV0 = 2, W_EPI0 = W_CONV0 + NCONV;
@@ -172,19 +196,24 @@ static_assert(NA % 2 == 0, "A buffers must be even");
 
 template <int R2P, int XM>
 struct Layout {
-  static constexpr int N1 = 2 * R2P;           // MMA1: X_s [hi(U2) | lo(U2)], M = 128 rows of the slab
   static constexpr bool XBF16 = (XM == 1);      // X stored as bf16: MMA1 reads the stage
-  static constexpr int KCX = XBF16 ? 64 : 32;  // X columns per stage (128 bytes)
+  static constexpr bool XF8 = (XM == 3);        // E4M3 codes: kind::f8f6f4 MMA1 reads the stage
+  static constexpr bool XSMEM = XBF16 || XF8;   // A operand of MMA1 in shared memory
+  static constexpr int NUT = XF8 ? 4 : 2;       // terms of U_2
+  static constexpr int N1 = NUT * R2P;          // MMA1: X_s [terms of U2], M = 128 rows of the slab
+  static constexpr int KCX = XF8 ? 128 : XBF16 ? 64 : 32;  // X columns per stage (128 bytes)
+  static constexpr int KB = XF8 ? 128 : 64;     // K elements per 128-byte chunk of B1
+  static_assert(!XF8 || R2P <= 32, "FP8 form: r_2 <= 32 (TMEM columns)");
   static constexpr int SPB = 128 / R2P;        // slabs per MMA2 batch (N = 128 columns of T)
   static constexpr int N2 = 128;               // MMA2: U_1^T [T of SPB slabs], M = 64 (rows a < r1)
   static constexpr int A_COL = 0;              // TMEM: NA A buffers of 32 columns (float32 X only)
-  static constexpr int D1_COL = XBF16 ? 0 : NA * 32;
+  static constexpr int D1_COL = XSMEM ? 0 : NA * 32;
   static constexpr int D2_COL = D1_COL + 2 * N1;
   static constexpr int ND2 = (D2_COL + 2 * N2 <= 512) ? 2 : 1;   // D2 buffers
   static constexpr int TMEM_USED = D2_COL + ND2 * N2;
   static constexpr int NS = (R2P == 64) ? 4 : 6;                 // X stages (shared-memory budget)
   static_assert(NS % 2 == 0, "stages must be even");
-  static constexpr int TCH = R2P < 32 ? R2P : 32;                // T columns per epilogue round
+  static constexpr int TCH = XF8 ? (R2P < 16 ? R2P : 16) : (R2P < 32 ? R2P : 32);   // T columns per epilogue round
   static constexpr int TMEM_COLS = TMEM_USED <= 128 ? 128 : TMEM_USED <= 256 ? 256 : 512;
   // T of a batch as the MN-major B operand of MMA2: K = 128 rows (i) x N = 128 columns
   // (slab j, column b), 128-byte swizzle, atoms of 8 rows x 64 columns; the 16 row
@@ -203,13 +232,13 @@ template <int R2P, int XM>
 __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_constant__ CUtensorMap tmap, Core2Args args) {
   using LY = Layout<R2P, XM>;
   constexpr int NS3 = LY::NS, ND2 = LY::ND2;
-  constexpr bool XBF16 = LY::XBF16;
+  constexpr bool XSMEM = LY::XSMEM, XF8 = LY::XF8;
   constexpr bool XLO = (XM == 0);                  // float32 X keeps its lo term
   constexpr int N1 = LY::N1, N2 = LY::N2, KCX = LY::KCX, SPB = LY::SPB;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int nkc = (args.n2 + KCX - 1) / KCX;       // stages per slab
-  const int nkb = (args.n2 + 63) / 64;             // 64-wide K chunks of B1
+  const int nkb = (args.n2 + LY::KB - 1) / LY::KB; // 128-byte K chunks of B1
   unsigned char* BT = base;
   unsigned char* B1 = BT + 2 * LY::BT_TERM;
   unsigned char* AU = B1 + (size_t)nkb * N1 * 128;
@@ -236,7 +265,7 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
   const int64_t nbatch = (nmine + SPB - 1) / SPB;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NS3; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], XBF16 ? 1 : 4); }
+    for (int i = 0; i < NS3; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], XSMEM ? 1 : 4); }
     for (int i = 0; i < NA; ++i) { mbar_init(&afull[i], 4); mbar_init(&aempty[i], 1); }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&d1full[i], 1); mbar_init(&d1empty[i], 4);
@@ -248,13 +277,43 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // B1 = [hi(U2) | lo(U2)] (rows n < R2P: hi), AU = hi(U1)^T, lo(U1)^T (rows a >= r1 zero),
-  // bf16, K-major, swizzled
-  for (int e = threadIdx.x; e < nkb * 64 * R2P; e += NTHREADS_V2) {
-    const int k = e / R2P, col = e % R2P;
-    unsigned short hi = 0, lo = 0;
-    if (k < n2 && col < r2) split1_bf16(__ldg(args.U2 + (int64_t)k * r2 + col), hi, lo);
-    *reinterpret_cast<unsigned short*>(B1 + sw_off16(col, k, N1)) = hi;
-    *reinterpret_cast<unsigned short*>(B1 + sw_off16(R2P + col, k, N1)) = lo;
+  // bf16, K-major, swizzled.  FP8 form: B1 = [t_1 | t_2 | t_3 | t_4] of U2 / sigma, E4M3.
+  __shared__ unsigned int s_umax;
+  float usig = 1.f;
+  if constexpr (XF8) {
+    if (threadIdx.x == 0) s_umax = 0u;
+    __syncthreads();
+    unsigned int m = 0u;
+    for (int e = threadIdx.x; e < n2 * r2; e += NTHREADS_V2) m = max(m, __float_as_uint(fabsf(__ldg(args.U2 + e))));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) atomicMax(&s_umax, m);
+    __syncthreads();
+    // max |U2| = f 2^ex with 0.5 <= f < 1: sigma = 2^(ex - 8) keeps every |u| / sigma below 256
+    int ex = 0;
+    const float umax = __uint_as_float(s_umax);
+    if (umax > 0.f) frexpf(umax, &ex);
+    usig = ldexpf(1.f, ex - 8);
+    for (int e = threadIdx.x; e < nkb * 128 * R2P; e += NTHREADS_V2) {
+      const int k = e / R2P, col = e % R2P;
+      float v = (k < n2 && col < r2) ? ldexpf(__ldg(args.U2 + (int64_t)k * r2 + col), 8 - ex) : 0.f;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        // the residual of a nearest E4M3 value is exact in float32 and at most 2^-4 of |v|,
+        // so 32 x residual stays within the 256 bound of the next term
+        const uint32_t code = e4m3_code(v);
+        B1[sw_off8(t * R2P + col, k, N1)] = (unsigned char)code;
+        v = (v - e4m3_value(code)) * 32.f;
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < nkb * 64 * R2P; e += NTHREADS_V2) {
+      const int k = e / R2P, col = e % R2P;
+      unsigned short hi = 0, lo = 0;
+      if (k < n2 && col < r2) split1_bf16(__ldg(args.U2 + (int64_t)k * r2 + col), hi, lo);
+      *reinterpret_cast<unsigned short*>(B1 + sw_off16(col, k, N1)) = hi;
+      *reinterpret_cast<unsigned short*>(B1 + sw_off16(R2P + col, k, N1)) = lo;
+    }
   }
   for (int e = threadIdx.x; e < 128 * 64; e += NTHREADS_V2) {
     const int i = e / 64, a = e % 64;
@@ -278,7 +337,7 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
   fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t box_bytes = (uint32_t)n1 * 128;
-  constexpr uint32_t idesc1 = idesc_bf16(128, N1);
+  constexpr uint32_t idesc1 = XF8 ? idesc_e4m3(128, N1) : idesc_bf16(128, N1);
   constexpr uint32_t idesc2 = idesc_bf16(64, N2) | (1u << 16);   // B (T) MN-major
 
   if (warp == 0) {
@@ -330,7 +389,7 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
         fence_after();
         const uint32_t dcol = tmem + LY::D1_COL + db * N1;
         for (int kc = 0; kc < nkc; ++kc, ++c) {
-          if (XBF16) {
+          if (XSMEM) {
             const int st = (int)(c % NS3);
             if (!(ok = mbar_wait(&full[st], (uint32_t)((c / NS3) & 1), abort_flag, args.status))) break;
             fence_after();
@@ -339,7 +398,8 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
             for (int kk = 0; kk < 4; ++kk) {
               const int kg = kc * 4 + kk;    // global 16-wide K step
               const uint32_t baddr = saddr(B1 + (kg >> 2) * N1 * 128 + (kg & 3) * 32);
-              mma_bf16_ss(dcol, sw128_desc(sbase + kk * 32), sw128_desc(baddr), idesc1, (kc | kk) ? 1u : 0u);
+              if (XF8) mma_f8_ss(dcol, sw128_desc(sbase + kk * 32), sw128_desc(baddr), idesc1, (kc | kk) ? 1u : 0u);
+              else mma_bf16_ss(dcol, sw128_desc(sbase + kk * 32), sw128_desc(baddr), idesc1, (kc | kk) ? 1u : 0u);
             }
             mma_commit(&empty[st]);
           } else {
@@ -369,7 +429,7 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
     }
   } else if (warp < W_EPI0) {
     // ---------------------------------------------------------------- converters (float32 X)
-    if (!XBF16) {
+    if (!XSMEM) {
       const int grp = (warp - W_CONV0) >> 2;
       const int q = warp & 3;
       const int row = q * 32 + lane;
@@ -465,6 +525,8 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
       // the TMA box does not cover).  The first slab of a batch first reads P of the
       // previous batch (which frees T).
       bool first = true;
+      // FP8 form: T = scale_s sigma (D_1 + D_2 / 32 + D_3 / 32^2 + D_4 / 32^3)
+      const float tsc = XF8 ? __ldg(args.xscale + blockIdx.x + t * gridDim.x) * usig : 1.f;
 #pragma unroll
       for (int h0 = 0; h0 < R2P; h0 += LY::TCH) {
         uint32_t dh[LY::TCH], dl[LY::TCH];
@@ -473,7 +535,26 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
           tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D1_COL + db * N1 + h0 + cc * 8, dh + 8 * cc);
           tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D1_COL + db * N1 + R2P + h0 + cc * 8, dl + 8 * cc);
         }
-        tmem_wait_ld();
+        if constexpr (XF8) {
+          uint32_t d3[LY::TCH], d4[LY::TCH];
+#pragma unroll
+          for (int cc = 0; cc < LY::TCH / 8; ++cc) {
+            tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D1_COL + db * N1 + 2 * R2P + h0 + cc * 8, d3 + 8 * cc);
+            tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D1_COL + db * N1 + 3 * R2P + h0 + cc * 8, d4 + 8 * cc);
+          }
+          tmem_wait_ld();
+          // fold the four term sums into dh (dl = 0), Horner in powers of 1/32 (exact scalings)
+#pragma unroll
+          for (int b = 0; b < LY::TCH; ++b) {
+            float v = __uint_as_float(d4[b]) * 0.03125f + __uint_as_float(d3[b]);
+            v = v * 0.03125f + __uint_as_float(dl[b]);
+            v = v * 0.03125f + __uint_as_float(dh[b]);
+            dh[b] = __float_as_uint(v * tsc);
+            dl[b] = 0u;
+          }
+        } else {
+          tmem_wait_ld();
+        }
         if (h0 + LY::TCH >= R2P) {
           fence_before();
           __syncwarp();
@@ -528,7 +609,7 @@ static size_t smem_bytes(int nkb) {
 
 template <int R2P, int XM>
 static int launch_v3(const CUtensorMap& map, const Core2Args& a, int grid, cudaStream_t st) {
-  const int nkb = (a.n2 + 63) / 64;
+  const int nkb = (a.n2 + Layout<R2P, XM>::KB - 1) / Layout<R2P, XM>::KB;
   const size_t sm = smem_bytes<R2P, XM>(nkb);
   if (sm > 227 * 1024) return -1;
   cudaFuncSetAttribute(k_core2_tc<R2P, XM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -541,17 +622,18 @@ static int launch_v3(const CUtensorMap& map, const Core2Args& a, int grid, cudaS
 // Returns the number of launches (1), or 0 when the shape is not supported
 // by the tensor-core path (the caller then uses the FFMA chain).
 // xmode: 0 float32 X split into two bf16 terms, 1 bfloat16 X, 2 float32 X
-// rounded to one bf16 term.
+// rounded to one bf16 term, 3 E4M3 codes with per-slab scales (xscale).
 cudaError_t core_tc_set_wait_limit(uint32_t polls) { return tma::set_wait_limit(polls); }
 
 int launch_core2_tc(int xmode, const void* X, int64_t S, int n1, int n2, const float* U1, int r1, const float* U2,
-                    int r2, float* P, int* status, cudaStream_t st, int max_ctas) {
+                    int r2, float* P, int* status, cudaStream_t st, int max_ctas, const float* xscale) {
   using namespace tc;
-  if (xmode < 0 || xmode > 2) return 0;
-  const bool xbf16 = (xmode == 1);
-  const int esz = xbf16 ? 2 : 4;
+  if (xmode < 0 || xmode > 3) return 0;
+  const bool xbf16 = (xmode == 1), xf8 = (xmode == 3);
+  const int esz = xf8 ? 1 : xbf16 ? 2 : 4;
   if (n1 < 1 || n1 > ROWS || n2 < 1 || ((int64_t)n2 * esz) % 16 != 0 || r1 < 1 || r1 > 64 || r2 < 1 || r2 > 64)
     return 0;
+  if (xf8 && (r2 > 32 || !xscale)) return 0;
   if ((reinterpret_cast<uintptr_t>(X) & 15u) != 0) return 0;
   if (S * (int64_t)n1 >= ((int64_t)1 << 31)) return 0;
   EncodeTiledFn enc = encode_tiled_fn();
@@ -561,7 +643,10 @@ int launch_core2_tc(int xmode, const void* X, int64_t S, int n1, int n2, const f
   const cuuint64_t gstride[1] = {(cuuint64_t)n2 * esz};
   const cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)n1};
   const cuuint32_t estride[2] = {1, 1};
-  if (enc(&map, xbf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(X),
+  if (enc(&map,
+          xf8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+              : xbf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+          2, const_cast<void*>(X),
           gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return 0;
@@ -570,18 +655,25 @@ int launch_core2_tc(int xmode, const void* X, int64_t S, int n1, int n2, const f
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   int64_t grid = std::min<int64_t>(S, nsm);
   if (max_ctas > 0) grid = std::min<int64_t>(grid, max_ctas);
-  Core2Args a{X, U1, U2, P, S, n1, n2, r1, r2, status};
+  Core2Args a{X, U1, U2, P, xscale, S, n1, n2, r1, r2, status};
   const int r2p = r2 <= 8 ? 8 : r2 <= 16 ? 16 : r2 <= 32 ? 32 : 64;
   int rc = 0;
 #define RT_TC_CASE(B)                                                            \
   if (r2p == B) {                                                                \
     rc = xmode == 1   ? launch_v3<B, 1>(map, a, (int)grid, st)                   \
          : xmode == 2 ? launch_v3<B, 2>(map, a, (int)grid, st)                   \
+         : xmode == 3 ? launch_v3<B, 3>(map, a, (int)grid, st)                   \
                       : launch_v3<B, 0>(map, a, (int)grid, st);                  \
     return rc < 0 ? 0 : rc;                                                      \
   }
-  RT_TC_CASE(8) RT_TC_CASE(16) RT_TC_CASE(32) RT_TC_CASE(64)
+  RT_TC_CASE(8) RT_TC_CASE(16) RT_TC_CASE(32)
 #undef RT_TC_CASE
+  if (r2p == 64) {
+    rc = xmode == 1 ? launch_v3<64, 1>(map, a, (int)grid, st)
+         : xmode == 2 ? launch_v3<64, 2>(map, a, (int)grid, st)
+         : xmode == 0 ? launch_v3<64, 0>(map, a, (int)grid, st) : -1;
+    return rc < 0 ? 0 : rc;
+  }
   return 0;
 }
 

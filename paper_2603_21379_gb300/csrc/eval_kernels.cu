@@ -21,6 +21,7 @@ namespace rt {
 
 __device__ __forceinline__ double ldxd(const void* X, int dtype, int64_t e) {
   if (dtype == DT_F32) return (double)__ldg(reinterpret_cast<const float*>(X) + e);
+  if (dtype == DT_F8) return (double)e4m3_value(__ldg(reinterpret_cast<const unsigned char*>(X) + e));
   if (dtype == DT_F64) return __ldg(reinterpret_cast<const double*>(X) + e);
   return (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(X)[e]);
 }
@@ -48,12 +49,13 @@ __global__ void k_expand_f64(const double* __restrict__ A, const float* __restri
 __global__ void __launch_bounds__(256) k_tucker_slab_err(
     const void* __restrict__ X, int dtype, const double* __restrict__ H, const float* __restrict__ Hf,
     int64_t nslab, int64_t n1, int r1, int64_t n2, int r2, const float* __restrict__ U1,
-    const float* __restrict__ U2, double* __restrict__ part) {
+    const float* __restrict__ U2, double* __restrict__ part, const float* __restrict__ xsc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* T = reinterpret_cast<double*>(smem_raw);
   __shared__ double red[64];
   double se = 0.0, sx = 0.0;
   for (int64_t s = blockIdx.x; s < nslab; s += gridDim.x) {
+    const double xs = xsc ? (double)__ldg(xsc + s) : 1.0;   // float8 storage: the slab's scale
     __syncthreads();
     for (int64_t e = threadIdx.x; e < (int64_t)r1 * n2; e += blockDim.x) {
       const int a = (int)(e / n2);
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(256) k_tucker_slab_err(
       const int64_t i = e / n2, j = e % n2;
       double xh = 0.0;
       for (int a = 0; a < r1; ++a) xh = fma((double)__ldg(U1 + i * r1 + a), T[a * n2 + j], xh);
-      const double x = ldxd(X, dtype, s * n1 * n2 + e);
+      const double x = ldxd(X, dtype, s * n1 * n2 + e) * xs;
       se = fma(x - xh, x - xh, se);
       sx = fma(x, x, sx);
     }
@@ -114,6 +116,8 @@ static bool relerr_slab_fits(int d, const int64_t* n, const int32_t* r) {
   return (size_t)r[d - 2] * n[d - 1] * 8 <= 200 * 1024;
 }
 
+bool tucker_relerr_slab_fits(int d, const int64_t* n, const int32_t* r) { return relerr_slab_fits(d, n, r); }
+
 bool tucker_relerr_supported(int d, const int64_t* n, const int32_t* r) {
   return relerr_slab_fits(d, n, r) || r[d - 1] <= CMAX;
 }
@@ -143,7 +147,7 @@ static int launch_rows_err(const void* X, int dtype, int64_t M, int64_t n2, cons
 
 int launch_tucker_relerr(const void* X, int dtype, int d, const int64_t* n, const int32_t* r,
                          const float* const* U, const float* G, double* scratch, size_t scratch_doubles,
-                         double* result2, cudaStream_t st) {
+                         double* result2, cudaStream_t st, const float* xsc) {
   (void)scratch_doubles;
   int nl = 0;
   const size_t half = relerr_half(d, n, r);
@@ -179,7 +183,7 @@ int launch_tucker_relerr(const void* X, int dtype, int d, const int64_t* n, cons
   const size_t smem = (size_t)r1 * n2 * sizeof(double);
   cudaFuncSetAttribute(k_tucker_slab_err, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int nb = (int)(L < EV_BLOCKS ? L : EV_BLOCKS);
-  k_tucker_slab_err<<<nb, 256, smem, st>>>(X, dtype, H, Hf, L, n1, r1, n2, r2, U[d - 2], U[d - 1], part);
+  k_tucker_slab_err<<<nb, 256, smem, st>>>(X, dtype, H, Hf, L, n1, r1, n2, r2, U[d - 2], U[d - 1], part, xsc);
   k_reduce_pairs<<<1, 1024, 0, st>>>(part, nb, result2);
   return nl + 2;
 }

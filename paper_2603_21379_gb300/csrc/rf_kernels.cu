@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) k_gather_sketch(const RFProb* __restrict_
   for (int t = 0; t < PER; ++t) {
     const int jj = tid / SK_TI + t * (256 / SK_TI);
     const int64_t o = offs[jj];
-    v[t] = (i < nS && o >= 0) ? load_x(q.X, q.dtype, o + i * rs) : 0.f;
+    v[t] = (i < nS && o >= 0) ? load_xq(q, o + i * rs) : 0.f;
   }
   const bool bf = q.skbf16 != 0;
 #pragma unroll

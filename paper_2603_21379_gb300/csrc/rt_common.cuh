@@ -24,7 +24,25 @@ __device__ __forceinline__ void set_status(int* st, int code) {
   if (st) atomicCAS(st, 0, code);
 }
 
-enum : int { DT_F32 = 0, DT_F64 = 1, DT_BF16 = 2 };
+enum : int { DT_F32 = 0, DT_F64 = 1, DT_BF16 = 2, DT_F8 = 3 };
+
+// Value of an E4M3 code (1 sign, 4 exponent bits with bias 7, 3 mantissa bits;
+// exponent field 0: subnormals m 2^-9), from the bit fields.  The NaN code
+// S.1111.111 is never stored by the quantiser (its magnitudes stay below 256) and
+// decodes as 480 here.
+__device__ __forceinline__ float e4m3_value(uint32_t c) {
+  const uint32_t ef = (c >> 3) & 15u, m = c & 7u;
+  const float v = ef ? __uint_as_float(((ef + 120u) << 23) | (m << 20)) : (float)m * 0x1p-9f;
+  return (c & 0x80u) ? -v : v;
+}
+
+// Nearest E4M3 code to y, ties to the even mantissa, magnitudes beyond 448 saturated
+// (the conversion instruction's round-to-nearest-even, satfinite form).
+__device__ __forceinline__ uint32_t e4m3_code(float y) {
+  unsigned short r;
+  asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(0.f), "f"(y));
+  return r & 0xFFu;
+}
 
 struct RFProb {
   // input tensor and the geometry of the set unfolding X^(S), S = {a..b}
@@ -83,6 +101,9 @@ struct RFProb {
   int32_t nbg;             // number of sample chunks of the B-step Gram
   int32_t skbf16;          // BF16 form: the sketch Z = Y Omega from bfloat16-rounded Y and
                            // Omega (float32 accumulate); Y itself stays float32
+  // float8 storage of X (dtype DT_F8): element e = code x xsc[e / xslab]
+  const float* xsc;        // per-slab scales
+  int64_t xslab;           // elements per slab (the last two modes)
 };
 
 // Problem lookup: blocks (or threads) are numbered consecutively over the
@@ -100,6 +121,14 @@ __device__ __forceinline__ float load_x(const void* X, int dtype, int64_t e) {
   if (dtype == DT_F32) return __ldg(reinterpret_cast<const float*>(X) + e);
   if (dtype == DT_F64) return (float)__ldg(reinterpret_cast<const double*>(X) + e);
   return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(X)[e]);
+}
+
+// Element e of a problem's tensor, float8 storage included (the product of an E4M3
+// value and a power-of-two scale is exact in float32).
+__device__ __forceinline__ float load_xq(const RFProb& q, int64_t e) {
+  if (q.dtype == DT_F8)
+    return e4m3_value(__ldg(reinterpret_cast<const unsigned char*>(q.X) + e)) * __ldg(q.xsc + e / q.xslab);
+  return load_x(q.X, q.dtype, e);
 }
 
 // Single-instruction approximations (flush-to-zero) used where a few ulp do not matter:

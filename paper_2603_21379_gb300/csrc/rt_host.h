@@ -134,10 +134,16 @@ int launch_unfold_contract(const float* Y, const float* C, int64_t P, int64_t n,
                            float* out, float* scratch, cudaStream_t st);
 int launch_scale_f32(float* x, int64_t n, float s, cudaStream_t st);
 // Fused pass over X on tensor cores: P[s] = U1^T X[s] U2 for S slabs of
-// n1 x n2.  X float32 (xbf16 = 0: two bf16 terms) or bfloat16 (xbf16 = 1).
-// Returns 0 when the shape is unsupported.
+// n1 x n2.  xmode 0: float32 X as two bf16 terms; 1: bfloat16 X; 2: float32 X
+// rounded to one bf16 term; 3: E4M3 codes with one float32 scale per slab
+// (xscale).  Returns 0 when the shape is unsupported.
 int launch_core2_tc(int xmode, const void* X, int64_t S, int n1, int n2, const float* U1, int r1, const float* U2,
-                    int r2, float* P, int* status, cudaStream_t st, int max_ctas = 0);
+                    int r2, float* P, int* status, cudaStream_t st, int max_ctas = 0, const float* xscale = nullptr);
+
+// ---- float8 storage (fp8_kernels.cu): codes q (S slabs of `slab` elements) and one
+// power-of-two scale per slab; 3 launches, or -1 when the grid would be too large.
+int launch_quantize_fp8(const void* X, int dtype, int64_t S, int64_t slab, unsigned char* q, float* scales,
+                        cudaStream_t st);
 
 // ---- H-Tucker (ht_kernels.cu)
 struct TransferJob {     // B_S(i, j, k) = sum_{a,b} U_S[a n_r + b][i] U_l[a][j] U_r[b][k]
@@ -182,7 +188,8 @@ size_t root_scratch_floats(int64_t nl, int64_t nr, int rl, int rr);
 // ---- evaluators (eval_kernels.cu), float64
 int launch_tucker_relerr(const void* X, int dtype, int d, const int64_t* n, const int32_t* r,
                          const float* const* U, const float* G, double* scratch, size_t scratch_doubles,
-                         double* result2, cudaStream_t st);
+                         double* result2, cudaStream_t st, const float* xsc = nullptr);
+bool tucker_relerr_slab_fits(int d, const int64_t* n, const int32_t* r);
 bool tucker_relerr_supported(int d, const int64_t* n, const int32_t* r);
 size_t tucker_relerr_scratch(int d, const int64_t* n, const int32_t* r);
 int launch_ht_relerr(const void* X, int dtype, int64_t nl, int64_t nr, const double* Ul, int rl,

@@ -118,3 +118,18 @@ def test_product_never_uses_the_scratch_folder():
                 if pat.search(line):
                     hits.append("%s:%d" % (f, i))
     assert not hits, hits
+
+
+def test_fp8_storage_sizes(lib):
+    # packed float8 storage: codes, then at the element count rounded up to 256 one
+    # float32 scale per slab of the last two modes, the whole rounded up to 16 bytes
+    lib.rt_fp8_bytes.restype = ctypes.c_size_t
+    lib.rt_fp8_scale_offset.restype = ctypes.c_size_t
+
+    def call(fn, n):
+        return fn(len(n), (ctypes.c_int64 * len(n))(*n))
+    assert call(lib.rt_fp8_scale_offset, [3, 2, 12, 20]) == 1536
+    assert call(lib.rt_fp8_bytes, [3, 2, 12, 20]) == 1536 + 6 * 4 + 8
+    assert call(lib.rt_fp8_bytes, [300, 200]) == 60160 + 16        # one slab
+    assert call(lib.rt_fp8_bytes, [128] * 4) == 128 ** 4 + 4 * 128 ** 2
+    assert call(lib.rt_fp8_bytes, [7]) == 0 and call(lib.rt_fp8_bytes, [4, 0, 3]) == 0
