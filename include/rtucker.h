@@ -119,8 +119,15 @@ typedef struct {
                           Householder when Z is rank-deficient to rounding, and
                           the R factor of B^T from the Cholesky factor of the
                           Gram B B^T (compensated float32 sums of the rounded
-                          products); 0 (default) Householder QR of Z with the
-                          Cholesky form of the W-step (the fastest measured).
+                          products); 3 as 2 with Z = Q R by shifted CholeskyQR3
+                          (Fukaya et al., SIAM J. Sci. Comput. 2020): a first
+                          pass on Z^T Z + s I, s = 11 (m c + c (c + 1)) 2^-24
+                          ||Z||_F^2 (m rows, c = r + p columns), which cannot
+                          break down for cond(Z) up to about 2^24, then two
+                          CholeskyQR passes (the Householder fallback stays for
+                          a Z that is rank-deficient to rounding); 0 (default)
+                          Householder QR of Z with the Cholesky form of the
+                          W-step (the fastest measured).
                           Larger unfoldings always take 1.  The one-sided Jacobi
                           SVD of R^T is the same in all; same factors to
                           rounding.                                            */

@@ -45,7 +45,7 @@ class _Options(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 2)]
 
 
-_QR = {"auto": 0, "householder": 1, "cholesky": 2}
+_QR = {"auto": 0, "householder": 1, "cholesky": 2, "shifted_cholesky3": 3}
 
 
 _lib = None
@@ -313,7 +313,7 @@ def rtucker_sketch(X, r, p, s=None, seed=0):
 def rtucker_factors(X, r, p, s=None, seed=0, with_sigma=False, qr="auto"):
     """S1-S6: factors U_k (n_k x r_k) with the column-sign rule; optionally the
     singular values of Q_k^T Y_k.  ``qr`` picks the range finder's factorisations
-    (rt_options.qr: "auto", "householder", "cholesky")."""
+    (rt_options.qr: "auto", "householder", "cholesky", "shifted_cholesky3")."""
     lib = load_library()
     dt, d, n = _tensor_args(X)
     r = _as_list(r, d)
@@ -336,13 +336,13 @@ _CORE = {"auto": 0, "tc": 1, "ffma": 2, "tune": 3}
 def _opts(prec, overlap=False, graph=False, core="auto", qr="auto", sketch="fp32"):
     """rt_options for a precision form (the overlapped core schedule, CUDA-graph
     replay, the core kernels: "auto", "tc", "ffma" or "tune"; the range finder's
-    factorisations: "auto", "householder" or "cholesky"), or None (defaults)."""
+    factorisations: "auto", "householder", "cholesky" or "shifted_cholesky3"), or None (defaults)."""
     if prec not in _PREC:
         raise ValueError("prec must be 'fp32' or 'bf16'")
     if core not in _CORE:
         raise ValueError("core must be 'auto', 'tc', 'ffma' or 'tune'")
     if qr not in _QR:
-        raise ValueError("qr must be 'auto', 'householder' or 'cholesky'")
+        raise ValueError("qr must be 'auto', 'householder', 'cholesky' or 'shifted_cholesky3'")
     if sketch not in ("fp32", "bf16"):
         raise ValueError("sketch must be 'fp32' or 'bf16'")
     if prec == "fp32" and not overlap and not graph and core == "auto" and qr == "auto" and sketch == "fp32":

@@ -328,7 +328,8 @@ rt_status plan_problem(rt_handle h, const ProbSpec& ps, Bump& bump, ProbPlan& pp
   const bool chol = ps.qr != 1 && nS <= QWF_MAX && (int64_t)odd((int)nS) * c <= QR_MAXF;   // W-step
   // S5 by CholeskyQR2 when asked, and in the BF16 form (its second pass restores the
   // orthogonality the bfloat16 sketch does not need to carry)
-  const bool chol_z = chol && (ps.qr == 2 || (ps.qr == 0 && ps.sketch == 1));
+  const bool chol_z = chol && (ps.qr == 2 || ps.qr == 3 || (ps.qr == 0 && ps.sketch == 1));
+  q.zshift = (chol_z && ps.qr == 3) ? 1 : 0;
   // TSQR of Z
   int rb = (QR_MAXF / c - 1) & ~31;
   if (rb < 32) rb = 32;
@@ -666,7 +667,7 @@ rt_status check_opts(rt_handle h, const rt_options* opt) {
   if (opt->prec != RT_PREC_FP32 && opt->prec != RT_PREC_BF16) return fail(h, RT_EINVAL, "unknown precision");
   if (opt->use_graph != 0 && opt->use_graph != 1) return fail(h, RT_EINVAL, "use_graph must be 0 or 1");
   if (opt->core < 0 || opt->core > 3) return fail(h, RT_EINVAL, "core must be 0, 1, 2 or 3");
-  if (opt->qr < 0 || opt->qr > 2) return fail(h, RT_EINVAL, "qr must be 0, 1 or 2");
+  if (opt->qr < 0 || opt->qr > 3) return fail(h, RT_EINVAL, "qr must be 0, 1, 2 or 3");
   if (opt->sketch != 0 && opt->sketch != 1) return fail(h, RT_EINVAL, "sketch must be 0 or 1");
   for (int i = 0; i < 2; ++i)
     if (opt->reserved[i]) return fail(h, RT_EINVAL, "reserved option fields must be zero");

@@ -1247,9 +1247,15 @@ __device__ void trsm_rows(float* A, int lda, int m, int c, const float* R, int l
 constexpr int QZ_LD = CMAX + 1;   // odd row stride of Z / Q in shared memory
 constexpr int GR_LD = CMAX + 1;   // row stride of the Gram and R matrices
 
-// S5, Cholesky form: Q of Z (n_S <= QWF_MAX rows) by mixed-precision CholeskyQR2.
-// A zero pivot (Z numerically rank-deficient) falls back to the Householder QR of the
-// same Z in the same CTA.
+// S5, Cholesky form: Q of Z (n_S <= QWF_MAX rows) by mixed-precision CholeskyQR2, or
+// (q.zshift) by shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Zhang, Yamamoto,
+// SIAM J. Sci. Comput. 2020): the first pass factors Z^T Z + s I with
+// s = 11 (m c + c (c + 1)) u ||Z||_F^2, u = 2^-24 the unit roundoff of the float32
+// Cholesky (||Z||_F^2 >= ||Z||_2^2), which keeps every pivot positive for cond(Z) up to
+// about 1/u and leaves Z R^-1 with a condition number CholeskyQR2 then handles; the
+// factor R of Z is the product of the three, Q = Z R^-1 the same Q.  A zero pivot
+// (Z numerically rank-deficient) falls back to the Householder QR of the same Z in the
+// same CTA.
 // Dynamic smem: max(A[QWF_MAX*QZ_LD] | G[CMAX*GR_LD] | R[CMAX*GR_LD] | rinv[CMAX] | nzero,
 //                   the Householder QR's A | Qm | tau | rdiag | vbuf)
 __global__ void __launch_bounds__(QR_THREADS) k_qz(const RFProb* __restrict__ P, const int64_t* __restrict__ pre,
@@ -1268,14 +1274,25 @@ __global__ void __launch_bounds__(QR_THREADS) k_qz(const RFProb* __restrict__ P,
   if (threadIdx.x == 0) *nzero = 0;
   for (int e = threadIdx.x; e < m * c; e += blockDim.x) A[(e / c) * lda + e % c] = q.Zp[e];
   __syncthreads();
-  for (int pass = 0; pass < 2; ++pass) {
+  const int npass = q.zshift ? 3 : 2;
+  for (int pass = 0; pass < npass; ++pass) {
     gram_upper(A, lda, m, c, G, GR_LD, pass == 0);
     __syncthreads();
-    float dmax = 0.f;
-    for (int k = 0; k < c; ++k) dmax = fmaxf(dmax, G[k * GR_LD + k]);
+    float dmax = 0.f, tr = 0.f;
+    for (int k = 0; k < c; ++k) {
+      dmax = fmaxf(dmax, G[k * GR_LD + k]);
+      tr += G[k * GR_LD + k];
+    }
     if (!(dmax < INFINITY)) {            // non-finite sketch
       if (threadIdx.x == 0) set_status(status, ST_NUMERIC);
       dmax = 0.f;
+      tr = 0.f;
+    }
+    if (q.zshift && pass == 0) {
+      const float shift = 11.f * (float)(m * c + c * (c + 1)) * 0x1p-24f * tr;
+      __syncthreads();
+      for (int k = threadIdx.x; k < c; k += blockDim.x) G[k * GR_LD + k] += shift;
+      __syncthreads();
     }
     chol_upper(G, GR_LD, c, R, GR_LD, dmax * (float)(c * 3.6e-15), 0.f, nzero, ij);
     if (*nzero) break;

@@ -104,6 +104,7 @@ struct RFProb {
   // float8 storage of X (dtype DT_F8): element e = code x xsc[e / xslab]
   const float* xsc;        // per-slab scales
   int64_t xslab;           // elements per slab (the last two modes)
+  int32_t zshift;          // S5 by shifted CholeskyQR3 (rt_options.qr = 3)
 };
 
 // Problem lookup: blocks (or threads) are numbered consecutively over the

@@ -642,15 +642,27 @@ _QR_CASES = {
                                              core="graded"), (12,) * 4, 6, 2),
     "widest70": lambda: (synth.tucker_tensor((70, 48, 48), (54, 8, 8), noise=1e-4, data_seed=10), (54, 8, 8), 10, 12),
     "tall": lambda: (synth.tucker_tensor((3000, 8, 9), (6, 3, 3), noise=1e-4, data_seed=10), (6, 3, 3), 2, 8),
+    "illcond": lambda: _illconditioned(),
 }
 
 
-@pytest.mark.parametrize("qr", ["householder", "cholesky"])
+def _illconditioned():
+    # sum of 10 rank-1 terms with weights 10^(-0.6 j): every unfolding has singular
+    # values 1 ... 10^-5.4, so the sketch Z (r + p = 10 columns) has cond(Z) ~ 2.5e5,
+    # beyond the 2^12 a float32 CholeskyQR2 covers and within the 2^24 of the shifted form
+    rs = np.random.default_rng(44)
+    A = [synth.haar(n, 10, rs) for n in (60, 50, 40)]
+    w = 10.0 ** (-0.6 * np.arange(10))
+    X = np.einsum("j,aj,bj,cj->abc", w, *A) + 1e-9 * rs.standard_normal((60, 50, 40))
+    return X.astype(np.float32), (5, 5, 5), 5, 3
+
+
+@pytest.mark.parametrize("qr", ["householder", "cholesky", "shifted_cholesky3"])
 @pytest.mark.parametrize("case", sorted(_QR_CASES))
 def test_factorisation_forms_match_oracle(rt, qr, case):
     # S5 and the W-step's R factor by Householder QR / TSQR, or by the Cholesky form
-    # (mixed-precision CholeskyQR2 of Z, Cholesky of the double-float Gram of B);
-    # the 3000-row mode takes Householder under either setting
+    # (mixed-precision CholeskyQR2 of Z, or shifted CholeskyQR3; Cholesky of the
+    # double-float Gram of B); the 3000-row mode takes Householder under every setting
     X, r, p, seed = _QR_CASES[case]()
     gap = 5e-3 if case == "widest70" else None
     if gap:
