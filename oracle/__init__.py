@@ -23,6 +23,11 @@ randomization") that it follows:
 * ``tucker_grad`` - gradients of the Tucker misfit 1/2 ||X - G x_k U_k||^2 and
                  the adjoint of the core projection (Sec. 3 format, Alg. 1
                  core step); the differentiable extension, not in the paper.
+* ``fp8``      - float8 (E4M3) storage of X with one power-of-two scale per
+                 slab of the last two modes (the FP8 form; not in the paper).
+* ``rhkron``   - randomized HOSVD with Kronecker-structured Gaussian test
+                 matrices, the rHKron comparison method of Sec. 3.3 (its
+                 reduced core factored mode by mode).
 
 Precision: every floating-point step runs in float64 (the paper's NumPy
 implementation does not state a precision; float64 is NumPy's default).

@@ -26,7 +26,8 @@ counter-based generator so both sides draw the same numbers from a seed:
   test matrix of R-HOSVD, Sec. 3, when s_k = n_{!=k}).
 
 Stream separation: word 3 of the Philox counter is (stream << 16) | node with
-stream 1 for the Feistel rounds and 2 for the Gaussians; ``node`` is the mode k
+stream 1 for the Feistel rounds, 2 for the Gaussians of the sketch and 3 for the
+per-mode Gaussians of the Kronecker-structured sketch; ``node`` is the mode k
 (Tucker) or the node id of the dimension tree (H-Tucker).  The key is the
 64-bit seed split into two 32-bit words.
 """
@@ -40,6 +41,7 @@ PHILOX4x64 = dict(W=64, M0=0xD2E7470EE14C6C93, M1=0xCA5A826395121157,
 
 STREAM_FEISTEL = 1
 STREAM_GAUSS = 2
+STREAM_KRON = 3     # the per-mode Gaussians of the Kronecker-structured sketch (oracle/rhkron.py)
 TWO_PI = 6.283185307179586  # 2*pi rounded to float64
 FEISTEL_ROUNDS = 4
 
@@ -140,20 +142,23 @@ def fiber_indices(N, s, seed, node):
     return out.astype(np.int64)
 
 
-def gaussian(m, c, seed, node):
+def gaussian(m, c, seed, node, stream=None):
     """N(0,1) entries g(seed, node, m, c) by Box-Muller, float64.
 
     (u0, u1) = first two words of Philox4x32-10(ctr = (m mod 2^32, m >> 32, c,
     (2 << 16) | node), key = seed); a = (u0 + 1/2) 2^-32, b = (u1 + 1/2) 2^-32
     (both in (0, 1)); g = sqrt(-2 ln a) cos(2 pi b).  ``m`` and ``c`` broadcast.
+    ``stream`` replaces the 2 in word 3 (default: the sketch's stream).
     """
+    if stream is None:
+        stream = STREAM_GAUSS
     m = np.asarray(m, dtype=np.uint64)
     c = np.asarray(c, dtype=np.uint64)
     m, c = np.broadcast_arrays(m, c)
     k0, k1 = seed_key(seed)
     lo = m & np.uint64(0xFFFFFFFF)
     hi = m >> np.uint64(32)
-    w3 = np.zeros_like(m) + np.uint64((STREAM_GAUSS << 16) | int(node))
+    w3 = np.zeros_like(m) + np.uint64((int(stream) << 16) | int(node))
     u0, u1, _, _ = philox4((lo, hi, c, w3), (k0, k1))
     a = (u0.astype(np.float64) + 0.5) * 2.0 ** -32
     b = (u1.astype(np.float64) + 0.5) * 2.0 ** -32
