@@ -342,6 +342,40 @@ size_t rt_fp8_scale_offset(int d, const int64_t* n);
  * Asynchronous on the handle's stream; allocates nothing. */
 rt_status rt_quantize_fp8(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, void* Xq);
 
+/* -------------------------------------------- Kronecker-structured sketches
+ * The rHKron comparison method of Sec. 3.3 (Minster et al.): randomized HOSVD
+ * whose mode-k test matrix is the Kronecker product of small per-mode Gaussians,
+ * so that one pass over X forms every mode's sketch.
+ *
+ * rtucker_kron_sketch: Omega_j (n_j x l_j, j = 0..d-1) Gaussian, entry (i, a) the
+ * Box-Muller normal of Philox4x32-10 counter (i, a, (3 << 16) | j) with the seed as
+ * key; Z_k = X^(k) (Omega_0 (x) .. (x) Omega_{k-1} (x) Omega_{k+1} (x) .. (x) Omega_{d-1}),
+ * the unfolding along k of X x_{j != k} Omega_j^T, n_k x L_k with L_k =
+ * prod_{j != k} l_j, columns in natural (C) order of the other modes.  Z =
+ * concat_k of the n_k x L_k row-major blocks (DEVICE float32).  One read of X (the
+ * slabs of its last two modes) forms all d sketches.  ell: HOST int32[d], 1 <= l_j
+ * <= n_j.  Supported (else RT_ENOTSUP): d >= 3, l_{d-2}, l_{d-1} <= 8, n_{d-1} a
+ * multiple of 4, n_{d-2}, n_{d-1} <= 1024, n_{d-2} L_{d-2} and n_{d-1} L_{d-1} at
+ * most 8192, the slab (plus its double buffer) within shared memory.  float32 X
+ * must be 16-byte aligned.  Arithmetic: float32 FMAs; the CTAs' partial sums are
+ * added in a fixed order (deterministic). */
+rt_status rtucker_kron_sketch(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                              const int32_t* ell, uint64_t seed, const rt_options* opt, float* Z);
+
+/* rtucker_rhkron: Tucker factors U (concat n_k x r_k, DEVICE float32, the
+ * column-sign rule applied) and core G (r_0 x .. x r_{d-1}, C order) by
+ *   1. the sketches Z_k of rtucker_kron_sketch;
+ *   2. Q_k = orthonormal factor of the thin QR of Z_k (diag(R) > 0);
+ *   3. the reduced tensor C = X x_0 Q_0^T .. x_{d-1} Q_{d-1}^T (L_0 x .. x L_{d-1});
+ *   4. W_k = dominant r_k left singular vectors of C^(k) for every mode at once
+ *      (the paper's rHKron takes an ST-HOSVD of C; the modes are factored
+ *      independently here, as in T-HOSVD, so that they run in parallel);
+ *   5. U_k = Q_k W_k and G = C x_k W_k^T (= X x_k U_k^T).
+ * Needs r_k <= L_k <= min(n_k, 64) and the shapes rtucker_kron_sketch takes.
+ * rt_options: qr applies to step 4; core to steps 3 and 5. */
+rt_status rtucker_rhkron(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
+                         const int32_t* ell, uint64_t seed, const rt_options* opt, float* U, float* G);
+
 /* Relative reconstruction error ||X - (U_1..U_d) G||_F / ||X||_F computed on
  * the device in float64 (evaluator; not part of the decomposition; Sec. 3.3
  * reports this measure).  G (r_1 x ... x r_d, C order) and the concatenated

@@ -23,7 +23,8 @@ __all__ = [
     "rhtucker_decompose", "rhtucker_relerr", "ht_tree", "ht_tree_from_children", "ht_alpha_w", "last_launch_count", "workspace_bytes",
     "set_timing", "get_timing", "STAGES", "rhtucker_root_transfer_noalloc", "BatchedDecomposition",
     "rtucker_loss_grad", "rtucker_core_adjoint", "set_wait_limit", "selftest_wait", "inject_fault",
-    "set_grad_recompute", "tucker_reconstruct_into", "Fp8Tensor", "quantize_fp8",
+    "set_grad_recompute", "tucker_reconstruct_into", "Fp8Tensor", "quantize_fp8", "rtucker_kron_sketch",
+    "rtucker_rhkron", "kron_widths",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -111,6 +112,8 @@ def load_library():
         "rt_fp8_bytes": (ctypes.c_size_t, [ctypes.c_int, P64]),
         "rt_fp8_scale_offset": (ctypes.c_size_t, [ctypes.c_int, P64]),
         "rt_quantize_fp8": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, vp]),
+        "rtucker_kron_sketch": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, u64, PO, vp]),
+        "rtucker_rhkron": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, P32, u64, PO, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -617,6 +620,53 @@ def rtucker_relerr(X, G, U):
     h = _handle(X.device.index)
     _check(h, lib.rtucker_relerr(h, _ptr(X), dt, d, _i64(n), _i32(r), _ptr(Uc), _ptr(Gc), ctypes.byref(out)))
     return out.value
+
+
+# ------------------------------------------------------------------ Kronecker-structured sketches
+def _kron_L(ell):
+    d = len(ell)
+    return [_prod([ell[j] for j in range(d) if j != k]) for k in range(d)]
+
+
+def kron_widths(shape, r, p=10):
+    """Per-mode widths l_j for rtucker_rhkron: the smallest common l with
+    l^(d-1) >= max_k r_k + p, capped so that every L_k = l^(d-1) stays within n_k
+    and 64 where that is possible."""
+    d = len(shape)
+    rmax = max(_as_list(r, d))
+    ell = 1
+    while ell ** (d - 1) < rmax + p:
+        ell += 1
+    return [ell] * d
+
+
+def rtucker_kron_sketch(X, ell, seed=0):
+    """The Kronecker-structured sketches Z_k = X^(k) (kron_{j != k} Omega_j) of every
+    mode from one pass over X (rHKron, Sec. 3.3); returns [Z_k] (n_k x L_k)."""
+    lib = load_library()
+    dt, d, n = _tensor_args(X)
+    ell = _as_list(ell, d)
+    L = _kron_L(ell)
+    Z = torch.empty(sum(nk * lk for nk, lk in zip(n, L)), dtype=torch.float32, device=X.device)
+    h = _handle(X.device.index)
+    _check(h, lib.rtucker_kron_sketch(h, _ptr(X), dt, d, _i64(n), _i32(ell), ctypes.c_uint64(seed), None, _ptr(Z)))
+    return _split(Z, n, L)
+
+
+def rtucker_rhkron(X, r, ell, seed=0, qr="auto", core="auto"):
+    """Randomized HOSVD with Kronecker-structured test matrices (rHKron, Sec. 3.3):
+    one-pass sketches, their QR, the reduced core X x_k Q_k^T and its mode-wise
+    factorisation; returns (G, [U_k])."""
+    lib = load_library()
+    dt, d, n = _tensor_args(X)
+    r = _as_list(r, d)
+    ell = _as_list(ell, d)
+    U = torch.empty(sum(nk * rk for nk, rk in zip(n, r)), dtype=torch.float32, device=X.device)
+    G = torch.empty(r, dtype=torch.float32, device=X.device)
+    h = _handle(X.device.index)
+    _check(h, lib.rtucker_rhkron(h, _ptr(X), dt, d, _i64(n), _i32(r), _i32(ell), ctypes.c_uint64(seed),
+                                 _opts("fp32", core=core, qr=qr), _ptr(U), _ptr(G)))
+    return G, _split(U, n, r)
 
 
 # ------------------------------------------------------------------ Sub-R-RtL-HT

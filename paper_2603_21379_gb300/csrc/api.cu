@@ -1343,6 +1343,73 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
   return finish(h, nl);
 }
 
+// Kronecker-structured sketch (rHKron, Sec. 3.3): checks, launch shape and workspace.
+struct KronPlan {
+  KronArgs a{};
+  int grid = 0;
+  size_t o_om = 0, o_p1 = 0, o_p2 = 0, o_ts = 0;
+  int64_t L[MAXD];
+};
+
+rt_status plan_kron(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* ell,
+                    Bump& bump, KronPlan& kp) {
+  if (!ell) return fail(h, RT_EINVAL, "ell is null");
+  if (d < 3) return fail(h, RT_ENOTSUP, "the Kronecker sketch needs d >= 3");
+  KronArgs& a = kp.a;
+  a.X = X;
+  a.dtype = (int)dtype;
+  a.d = d;
+  int64_t K = 1, S = 1;
+  a.om_off[0] = 0;
+  for (int j = 0; j < d; ++j) {
+    if (ell[j] < 1 || ell[j] > n[j]) return fail(h, RT_EINVAL, "need 1 <= l_j <= n_j");
+    a.n[j] = n[j];
+    a.ell[j] = ell[j];
+    a.om_off[j + 1] = a.om_off[j] + n[j] * ell[j];
+    if (j < d - 2) {
+      K *= ell[j];
+      S *= n[j];
+    }
+  }
+  for (int k = 0; k < d; ++k) {
+    kp.L[k] = 1;
+    for (int j = 0; j < d; ++j)
+      if (j != k) kp.L[k] *= ell[j];
+  }
+  a.om_total = a.om_off[d];
+  a.S = S;
+  a.n1 = (int)n[d - 2];
+  a.n2 = (int)n[d - 1];
+  a.la = ell[d - 2];
+  a.lb = ell[d - 1];
+  if (a.la > KRON_LMAX || a.lb > KRON_LMAX) return fail(h, RT_ENOTSUP, "l_{d-2} and l_{d-1} must be at most 8");
+  if (n[d - 1] % 4 != 0 || n[d - 2] > 1024 || n[d - 1] > 1024)
+    return fail(h, RT_ENOTSUP, "the Kronecker sketch needs n_{d-1} a multiple of 4 and n_{d-2}, n_{d-1} <= 1024");
+  if (K > 1024 || a.n1 * K * a.lb > KRON_ZMAX || a.n2 * K * a.la > KRON_ZMAX)
+    return fail(h, RT_ENOTSUP, "the Kronecker sketch needs n_{d-2} L_{d-2} and n_{d-1} L_{d-1} at most 8192");
+  if (dtype == RT_F32 && ((uintptr_t)X & 15u)) return fail(h, RT_EINVAL, "float32 X must be 16-byte aligned");
+  a.K = (int)K;
+  const int nq = a.n2 / 4;
+  a.ha = std::max(1, std::min(256 / std::max(1, a.n1), nq));
+  a.hb = std::max(1, std::min(256 / std::max(1, nq), a.n1));
+  if (kron_sketch_smem(a) > 227 * 1024) return fail(h, RT_ENOTSUP, "the Kronecker sketch's slab does not fit shared memory");
+  int nsm = 148;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  kp.grid = (int)std::min<int64_t>(S, nsm);
+  kp.o_om = bump.take((size_t)a.om_total * 4);
+  kp.o_p1 = bump.take((size_t)kp.grid * a.n1 * K * a.lb * 4);
+  kp.o_p2 = bump.take((size_t)kp.grid * a.n2 * K * a.la * 4);
+  kp.o_ts = bump.take((size_t)S * a.la * a.lb * 4);
+  return RT_OK;
+}
+
+void bind_kron(KronPlan& kp, char* ws) {
+  kp.a.om = reinterpret_cast<float*>(ws + kp.o_om);
+  kp.a.part1 = reinterpret_cast<float*>(ws + kp.o_p1);
+  kp.a.part2 = reinterpret_cast<float*>(ws + kp.o_p2);
+  kp.a.Ts = reinterpret_cast<float*>(ws + kp.o_ts);
+}
+
 }  // namespace
 
 // ============================================================================ C ABI
@@ -2165,6 +2232,176 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
     return RT_OK;
   });
   if (st != RT_OK) return st;
+  return finish(h, nl);
+}
+
+rt_status rtucker_kron_sketch(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
+                              const int32_t* ell, uint64_t seed, const rt_options* opt, float* Z) {
+  rt_status st;
+  if ((st = check_tensor(h, X, dtype, d, n, nullptr)) != RT_OK) return st;
+  if ((st = check_opts(h, opt)) != RT_OK) return st;
+  if (!Z) return fail(h, RT_EINVAL, "Z is null");
+  if ((st = check_prior_status(h)) != RT_OK) return st;
+  Bump bump;
+  KronPlan kp;
+  if ((st = plan_kron(h, X, dtype, d, n, ell, bump, kp)) != RT_OK) return st;
+  if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
+  bind_kron(kp, h->ws);
+  size_t off = 0;
+  for (int k = 0; k < d; ++k) {
+    kp.a.z[k] = Z + off;
+    off += (size_t)n[k] * kp.L[k];
+  }
+  int nl = 0;
+  {
+    StageTimer tm(h, 0);
+    nl += launch_kron_omega(kp.a, seed, h->stream);
+    nl += launch_kron_sketch(kp.a, kp.grid, h->stream);
+  }
+  return finish(h, nl);
+}
+
+rt_status rtucker_rhkron(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n, const int32_t* r,
+                         const int32_t* ell, uint64_t seed, const rt_options* opt, float* U, float* G) {
+  rt_status st;
+  if ((st = check_tensor(h, X, dtype, d, n, nullptr)) != RT_OK) return st;
+  if ((st = check_opts(h, opt)) != RT_OK) return st;
+  if (!r || !ell || !U || !G) return fail(h, RT_EINVAL, "r, ell, U and G are required");
+  if ((st = check_prior_status(h)) != RT_OK) return st;
+  if ((st = init_device_attrs(h)) != RT_OK) return st;
+  Bump bump;
+  KronPlan kp;
+  if ((st = plan_kron(h, X, dtype, d, n, ell, bump, kp)) != RT_OK) return st;
+  int32_t L32[MAXD];
+  for (int k = 0; k < d; ++k) {
+    if (r[k] < 1 || r[k] > kp.L[k] || kp.L[k] > n[k])
+      return fail(h, RT_EINVAL, "need r_k <= L_k = prod_{j != k} l_j <= n_k");
+    if (kp.L[k] > CMAX) return fail(h, RT_ENOTSUP, "L_k above 64 is not supported");
+    L32[k] = (int32_t)kp.L[k];
+  }
+  // S5 of every sketch: problems with r + p = L_k whose sketch the Kronecker pass writes
+  Group G1;
+  for (int k = 0; k < d; ++k) {
+    ProbSpec ps{};
+    ps.X = X;
+    ps.dtype = dtype;
+    ps.d = d;
+    for (int j = 0; j < d; ++j) ps.n[j] = n[j];
+    ps.a = ps.b = k;
+    ps.r = L32[k];
+    ps.p = 0;
+    ps.s = kp.L[k];
+    ps.seed = seed;
+    ps.node = (uint32_t)k;
+    ps.qr = 1;
+    ProbPlan pp;
+    if ((st = plan_problem(h, ps, bump, pp)) != RT_OK) return st;
+    G1.pp.push_back(pp);
+  }
+  group_layout(G1, bump);
+  size_t qoff[MAXD], woff[MAXD], qtot = 0, wtot = 0, ctot = 1;
+  int roff[MAXD], rtot = 0;
+  for (int k = 0; k < d; ++k) {
+    qoff[k] = qtot;
+    qtot += (size_t)n[k] * kp.L[k];
+    woff[k] = wtot;
+    wtot += (size_t)kp.L[k] * r[k];
+    roff[k] = rtot;
+    rtot += r[k];
+    ctot *= (size_t)kp.L[k];
+  }
+  const size_t o_q = bump.take(qtot * 4), o_c = bump.take(ctot * 4), o_w = bump.take(wtot * 4);
+  const size_t o_sg = bump.take((size_t)rtot * 4);
+  const size_t cb = std::max(core_buffer_floats(d, n, L32), core_buffer_floats(d, kp.L, r));
+  const size_t o_bA = bump.take(cb * 4), o_bB = bump.take(cb * 4);
+  // the reduced tensor C = X x_k Q_k^T factored mode by mode: every fiber sampled and
+  // r + p = L_k, so Q spans R^{L_k} and U = Q W holds the exact dominant singular vectors
+  Group G2;
+  for (int k = 0; k < d; ++k) {
+    ProbSpec ps{};
+    ps.X = nullptr;
+    ps.dtype = RT_F32;
+    ps.d = d;
+    int64_t N = 1;
+    for (int j = 0; j < d; ++j) {
+      ps.n[j] = kp.L[j];
+      if (j != k) N *= kp.L[j];
+    }
+    ps.a = ps.b = k;
+    ps.r = r[k];
+    ps.p = L32[k] - r[k];
+    ps.s = N;
+    ps.seed = seed;
+    ps.node = (uint32_t)k;
+    ps.qr = qr_of(opt);
+    ProbPlan pp;
+    if ((st = plan_problem(h, ps, bump, pp)) != RT_OK) return st;
+    G2.pp.push_back(pp);
+  }
+  group_layout(G2, bump);
+  if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
+  bind_kron(kp, h->ws);
+  float* Qc = reinterpret_cast<float*>(h->ws + o_q);
+  float* C = reinterpret_cast<float*>(h->ws + o_c);
+  float* Wc = reinterpret_cast<float*>(h->ws + o_w);
+  float* bufA = reinterpret_cast<float*>(h->ws + o_bA);
+  float* bufB = reinterpret_cast<float*>(h->ws + o_bB);
+  for (int k = 0; k < d; ++k) {
+    kp.a.z[k] = reinterpret_cast<float*>(h->ws + G1.pp[k].o_Zp);
+    G2.pp[k].q.X = C;
+    G2.pp[k].q.U = Wc + woff[k];
+  }
+  const size_t sb = group_stage_bytes(G1) + group_stage_bytes(G2);
+  if ((st = ensure_stage(h, sb)) != RT_OK) return st;
+  if ((st = group_upload(h, G1, h->h_stage, 0)) != RT_OK) return st;
+  if ((st = group_upload(h, G2, h->h_stage, group_stage_bytes(G1))) != RT_OK) return st;
+  int nl = 0;
+  if ((st = stage_commit(h, &nl)) != RT_OK) return st;
+  {
+    StageTimer tm(h, 0);
+    nl += launch_kron_omega(kp.a, seed, h->stream);
+    nl += launch_kron_sketch(kp.a, kp.grid, h->stream);
+    nl += launch_rf_qr(G1.g, h->stream, h->d_status);
+    for (int k = 0; k < d; ++k)
+      RT_CUDA(h, cudaMemcpyAsync(Qc + qoff[k], G1.pp[k].q.Q, (size_t)n[k] * kp.L[k] * 4, cudaMemcpyDeviceToDevice,
+                                 h->stream));
+  }
+  const int core = core_of(opt) == 3 ? 0 : core_of(opt);
+  int got = enqueue_core(h, X, dtype, d, n, L32, Qc, C, bufA, bufB, RT_PREC_FP32, core);
+  if (got < 0) return fail(h, RT_ENOTSUP, "reduced core");
+  nl += got;
+  {
+    StageTimer tm(h, 0);
+    nl += launch_range_finder(G2.g, h->stream, h->d_status);
+  }
+  got = enqueue_core(h, C, RT_F32, d, kp.L, r, Wc, G, bufA, bufB, RT_PREC_FP32, core);
+  if (got < 0) return fail(h, RT_ENOTSUP, "core of the reduced tensor");
+  nl += got;
+  KronFinish f{};
+  f.d = d;
+  f.Q = Qc;
+  f.W = Wc;
+  f.U = U;
+  f.G = G;
+  f.sign = reinterpret_cast<float*>(h->ws + o_sg);
+  f.uoff[0] = 0;
+  f.gtotal = 1;
+  for (int k = 0; k < d; ++k) {
+    f.n[k] = n[k];
+    f.r[k] = r[k];
+    f.L[k] = L32[k];
+    f.qoff[k] = (int64_t)qoff[k];
+    f.woff[k] = (int64_t)woff[k];
+    f.roff[k] = roff[k];
+    f.uoff[k + 1] = f.uoff[k] + n[k] * r[k];
+    f.gtotal *= r[k];
+  }
+  f.utotal = f.uoff[d];
+  f.rtotal = rtot;
+  {
+    StageTimer tm(h, 0);
+    nl += launch_kron_finish(f, h->stream);
+  }
   return finish(h, nl);
 }
 

@@ -1593,24 +1593,13 @@ cudaError_t rf_init_attributes() {
 static inline unsigned grid_of(int64_t units) { return (unsigned)units; }
 
 // S1-S5 and the B-step of S6 (up to the R factors of B^T).
-int launch_rf_head(const RFGroup& g, cudaStream_t st, int* status) {
+// S5 of every problem of a group: the Cholesky form, or Householder QR of single-block
+// sketches and the TSQR tree of tall ones.  The sketches are read from chunk 0 of Zp.
+int launch_rf_qr(const RFGroup& g, cudaStream_t st, int* status) {
   const int np = g.nprob;
   const int64_t* pre = g.pre;
   const int64_t stride = np + 1;
   int n = 0;
-  if (g.total[STG_SAMPLE] > 0) {
-    if (g.total[STG_SAMPLE] <= SO_WARP_MAX)
-      k_sample_omega<<<(unsigned)((g.total[STG_SAMPLE] * 32 + 127) / 128), 128, 0, st>>>(
-          g.probs, pre + STG_SAMPLE * stride, np, status);
-    else
-      k_sample_omega_t<<<(unsigned)((g.total[STG_SAMPLE] + 127) / 128), 128, 0, st>>>(
-          g.probs, pre + STG_SAMPLE * stride, np, status);
-    n += 1;
-  }
-  if (g.total[STG_GS] > 0) {
-    k_gather_sketch<<<grid_of(g.total[STG_GS]), 256, smem_gs(), st>>>(g.probs, pre + STG_GS * stride, np);
-    ++n;
-  }
   if (g.total[STG_QZ] > 0) {                    // Cholesky form of S5
     k_qz<<<grid_of(g.total[STG_QZ]), QR_THREADS, smem_qz(), st>>>(g.probs, pre + STG_QZ * stride, np, status);
     ++n;
@@ -1635,6 +1624,28 @@ int launch_rf_head(const RFGroup& g, cudaStream_t st, int* status) {
     k_qr3<<<grid_of(g.total[STG_QR3]), 256, smem_qr3(), st>>>(g.probs, pre + STG_QR3 * stride, np);
     ++n;
   }
+  return n;
+}
+
+int launch_rf_head(const RFGroup& g, cudaStream_t st, int* status) {
+  const int np = g.nprob;
+  const int64_t* pre = g.pre;
+  const int64_t stride = np + 1;
+  int n = 0;
+  if (g.total[STG_SAMPLE] > 0) {
+    if (g.total[STG_SAMPLE] <= SO_WARP_MAX)
+      k_sample_omega<<<(unsigned)((g.total[STG_SAMPLE] * 32 + 127) / 128), 128, 0, st>>>(
+          g.probs, pre + STG_SAMPLE * stride, np, status);
+    else
+      k_sample_omega_t<<<(unsigned)((g.total[STG_SAMPLE] + 127) / 128), 128, 0, st>>>(
+          g.probs, pre + STG_SAMPLE * stride, np, status);
+    n += 1;
+  }
+  if (g.total[STG_GS] > 0) {
+    k_gather_sketch<<<grid_of(g.total[STG_GS]), 256, smem_gs(), st>>>(g.probs, pre + STG_GS * stride, np);
+    ++n;
+  }
+  n += launch_rf_qr(g, st, status);
   if (g.total[STG_BTG] > 0) {                   // Cholesky form: B-step Grams
     k_btg<<<grid_of(g.total[STG_BTG]), 256, smem_btg(), st>>>(g.probs, pre + STG_BTG * stride, np);
     ++n;

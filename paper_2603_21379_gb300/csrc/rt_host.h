@@ -145,6 +145,46 @@ int launch_core2_tc(int xmode, const void* X, int64_t S, int n1, int n2, const f
 int launch_quantize_fp8(const void* X, int dtype, int64_t S, int64_t slab, unsigned char* q, float* scales,
                         cudaStream_t st);
 
+// ---- Kronecker-structured sketch (kron_kernels.cu)
+constexpr int KRON_ZMAX = 8192;   // entries of Z_{d-2} (and of Z_{d-1}) one CTA accumulates
+constexpr int KRON_LMAX = 8;      // l_{d-2}, l_{d-1} at most
+struct KronArgs {
+  const void* X;
+  int dtype;
+  int d;
+  int64_t n[MAXD];
+  int ell[MAXD];
+  int64_t S;                  // slabs: product of the leading d-2 sizes
+  int n1, n2;                 // n_{d-2}, n_{d-1}
+  int la, lb;                 // l_{d-2}, l_{d-1}
+  int K;                      // product of the leading l_j
+  int ha, hb;                 // column chunks of A, row chunks of Bt per slab
+  float* om;                  // Omega_j concatenated (n_j x l_j each)
+  int64_t om_off[MAXD + 1];
+  int64_t om_total;
+  float* part1;               // [grid][n1 K l_b]
+  float* part2;               // [grid][n2 K l_a]
+  float* Ts;                  // [S][l_a l_b]
+  float* z[MAXD];             // outputs Z_k (n_k x L_k)
+};
+struct KronFinish {
+  int d;
+  int64_t n[MAXD];
+  int r[MAXD], L[MAXD];
+  const float* Q;  int64_t qoff[MAXD];      // Q_k (n_k x L_k)
+  const float* W;  int64_t woff[MAXD];      // W_k (L_k x r_k)
+  float* U;        int64_t uoff[MAXD + 1];  // U_k (n_k x r_k)
+  int64_t utotal;
+  float* G;        int64_t gtotal;
+  float* sign;     int roff[MAXD];          // column signs
+  int rtotal;
+};
+size_t kron_sketch_smem(const KronArgs& a);
+int launch_kron_omega(const KronArgs& a, uint64_t seed, cudaStream_t st);
+int launch_kron_sketch(const KronArgs& a, int grid, cudaStream_t st);   // sketch, reduce, leading modes
+int launch_kron_finish(const KronFinish& f, cudaStream_t st);           // U = Q W, signs, core flips
+int launch_rf_qr(const RFGroup& g, cudaStream_t st, int* status);       // S5 of a group only
+
 // ---- H-Tucker (ht_kernels.cu)
 struct TransferJob {     // B_S(i, j, k) = sum_{a,b} U_S[a n_r + b][i] U_l[a][j] U_r[b][k]
   const float* US; const float* Ul; const float* Ur; float* B;

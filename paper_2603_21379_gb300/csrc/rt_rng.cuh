@@ -77,9 +77,12 @@ __device__ __forceinline__ uint64_t sample_index(uint64_t j, uint64_t N, int h, 
   return y;
 }
 
-__device__ __forceinline__ float gauss_entry(uint64_t m, uint32_t col, PhiloxKey key, uint32_t node) {
+// N(0,1) entry keyed by (m, col) in stream `stream` (2: the sketch's Omega; 3: the
+// per-mode Gaussians of the Kronecker-structured sketch) of node `node`.
+__device__ __forceinline__ float gauss_entry(uint64_t m, uint32_t col, PhiloxKey key, uint32_t node,
+                                             uint32_t stream = 2u) {
   const uint4 o = philox4x32_10(
-      make_uint4((uint32_t)(m & 0xffffffffull), (uint32_t)(m >> 32), col, (2u << 16) | node), key);
+      make_uint4((uint32_t)(m & 0xffffffffull), (uint32_t)(m >> 32), col, (stream << 16) | node), key);
   const float two_m32 = 2.3283064365386963e-10f;  // 2^-32
   float lna;
   if (o.x & 0x80000000u) {          // a > 1/2: ln a = log1p(-(1 - a))
