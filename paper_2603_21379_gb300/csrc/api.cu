@@ -1347,7 +1347,7 @@ rt_status tucker_run(rt_handle h, const void* X, rt_dtype dtype, int d, const in
 struct KronPlan {
   KronArgs a{};
   int grid = 0;
-  size_t o_om = 0, o_p1 = 0, o_p2 = 0, o_ts = 0;
+  size_t o_om = 0, o_p1 = 0, o_p2 = 0, o_ts = 0, o_wt = 0;
   int64_t L[MAXD];
 };
 
@@ -1385,8 +1385,11 @@ rt_status plan_kron(rt_handle h, const void* X, rt_dtype dtype, int d, const int
   if (a.la > KRON_LMAX || a.lb > KRON_LMAX) return fail(h, RT_ENOTSUP, "l_{d-2} and l_{d-1} must be at most 8");
   if (n[d - 1] % 4 != 0 || n[d - 2] > 1024 || n[d - 1] > 1024)
     return fail(h, RT_ENOTSUP, "the Kronecker sketch needs n_{d-1} a multiple of 4 and n_{d-2}, n_{d-1} <= 1024");
-  if (K > 1024 || a.n1 * K * a.lb > KRON_ZMAX || a.n2 * K * a.la > KRON_ZMAX)
-    return fail(h, RT_ENOTSUP, "the Kronecker sketch needs n_{d-2} L_{d-2} and n_{d-1} L_{d-1} at most 8192");
+  a.K = (int)std::min<int64_t>(K, 1 << 20);
+  if (K > 1024 || n[d - 2] > 256 || n[d - 1] > 256 || !kron_shares_fit(a))
+    return fail(h, RT_ENOTSUP,
+                "the Kronecker sketch needs n_{d-2}, n_{d-1} <= 256 and ceil(K / (256 / n)) max(4, l) <= 32 for "
+                "n = n_{d-2}, n_{d-1}, K the product of the leading l_j");
   if (dtype == RT_F32 && ((uintptr_t)X & 15u)) return fail(h, RT_EINVAL, "float32 X must be 16-byte aligned");
   a.K = (int)K;
   const int nq = a.n2 / 4;
@@ -1395,11 +1398,14 @@ rt_status plan_kron(rt_handle h, const void* X, rt_dtype dtype, int d, const int
   if (kron_sketch_smem(a) > 227 * 1024) return fail(h, RT_ENOTSUP, "the Kronecker sketch's slab does not fit shared memory");
   int nsm = 148;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+  if (S * K >= ((int64_t)1 << 31) || S * a.la * a.lb >= ((int64_t)1 << 31))
+    return fail(h, RT_ENOTSUP, "the Kronecker sketch: too many slabs");
   kp.grid = (int)std::min<int64_t>(S, nsm);
   kp.o_om = bump.take((size_t)a.om_total * 4);
   kp.o_p1 = bump.take((size_t)kp.grid * a.n1 * K * a.lb * 4);
   kp.o_p2 = bump.take((size_t)kp.grid * a.n2 * K * a.la * 4);
   kp.o_ts = bump.take((size_t)S * a.la * a.lb * 4);
+  kp.o_wt = bump.take((size_t)S * K * 4);
   return RT_OK;
 }
 
@@ -1408,6 +1414,7 @@ void bind_kron(KronPlan& kp, char* ws) {
   kp.a.part1 = reinterpret_cast<float*>(ws + kp.o_p1);
   kp.a.part2 = reinterpret_cast<float*>(ws + kp.o_p2);
   kp.a.Ts = reinterpret_cast<float*>(ws + kp.o_ts);
+  kp.a.Wt = reinterpret_cast<float*>(ws + kp.o_wt);
 }
 
 }  // namespace
@@ -2314,8 +2321,30 @@ rt_status rtucker_rhkron(rt_handle h, const void* X, rt_dtype dtype, int d, cons
   const size_t o_sg = bump.take((size_t)rtot * 4);
   const size_t cb = std::max(core_buffer_floats(d, n, L32), core_buffer_floats(d, kp.L, r));
   const size_t o_bA = bump.take(cb * 4), o_bB = bump.take(cb * 4);
-  // the reduced tensor C = X x_k Q_k^T factored mode by mode: every fiber sampled and
-  // r + p = L_k, so Q spans R^{L_k} and U = Q W holds the exact dominant singular vectors
+  if (ctot >= ((size_t)1 << 31)) return fail(h, RT_ENOTSUP, "reduced tensor of 2^31 or more entries");
+  // the reduced tensor C = X x_k Q_k^T factored mode by mode by the W-step's Cholesky
+  // form on the exact Gram C^(k) C^(k)^T (k_mode_gram) with Q = I: W_k = the dominant
+  // r_k left singular vectors of C^(k).  The problems are planned with the fewest
+  // samples (one Gram chunk); only their W-step kernel runs.
+  ModeGram mg{};
+  mg.d = d;
+  mg.ctas = 1;
+  {
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+    mg.ctas = std::max(1, 2 * nsm / d);
+  }
+  size_t ptot = 0;
+  for (int k = 0; k < d; ++k) {
+    mg.L[k] = L32[k];
+    int64_t Bk = 1;
+    for (int j = k + 1; j < d; ++j) Bk *= kp.L[j];
+    mg.B[k] = (int)Bk;
+    mg.N[k] = (int)(ctot / (size_t)kp.L[k]);
+    mg.poff[k] = (int64_t)ptot;
+    ptot += (size_t)mg.ctas * kp.L[k] * kp.L[k] * 2;
+  }
+  const size_t o_mg = bump.take(ptot * 4);
   Group G2;
   for (int k = 0; k < d; ++k) {
     ProbSpec ps{};
@@ -2330,10 +2359,10 @@ rt_status rtucker_rhkron(rt_handle h, const void* X, rt_dtype dtype, int d, cons
     ps.a = ps.b = k;
     ps.r = r[k];
     ps.p = L32[k] - r[k];
-    ps.s = N;
+    ps.s = std::min<int64_t>(N, L32[k]);
     ps.seed = seed;
     ps.node = (uint32_t)k;
-    ps.qr = qr_of(opt);
+    ps.qr = 0;
     ProbPlan pp;
     if ((st = plan_problem(h, ps, bump, pp)) != RT_OK) return st;
     G2.pp.push_back(pp);
@@ -2370,9 +2399,18 @@ rt_status rtucker_rhkron(rt_handle h, const void* X, rt_dtype dtype, int d, cons
   int got = enqueue_core(h, X, dtype, d, n, L32, Qc, C, bufA, bufB, RT_PREC_FP32, core);
   if (got < 0) return fail(h, RT_ENOTSUP, "reduced core");
   nl += got;
+  mg.C = C;
+  mg.part = reinterpret_cast<float*>(h->ws + o_mg);
+  for (int k = 0; k < d; ++k) {
+    if (G2.pp[k].q.nbg != 1 || G2.pp[k].units[STG_WSV2] != 1)
+      return fail(h, RT_ENOTSUP, "internal: reduced-tensor W-step plan");
+    mg.cp[k] = G2.pp[k].q.Cp;
+    mg.qeye[k] = G2.pp[k].q.Q;
+  }
   {
     StageTimer tm(h, 0);
-    nl += launch_range_finder(G2.g, h->stream, h->d_status);
+    nl += launch_mode_gram(mg, h->stream);
+    nl += launch_rf_tail(G2.g, h->stream, h->d_status);
   }
   got = enqueue_core(h, C, RT_F32, d, kp.L, r, Wc, G, bufA, bufB, RT_PREC_FP32, core);
   if (got < 0) return fail(h, RT_ENOTSUP, "core of the reduced tensor");

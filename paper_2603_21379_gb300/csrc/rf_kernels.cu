@@ -1127,34 +1127,6 @@ __global__ void __launch_bounds__(512) k_qwf(const RFProb* __restrict__ P, const
 // GB300's float64 rate is ~1/64 of float32, so the double-float sums run on the
 // float32 pipes.
 
-// hi + lo += a b with the product's and the sum's rounding errors kept (TwoProd by
-// fma, TwoSum).  Explicit _rn intrinsics: the compiler must not contract or reorder.
-__device__ __forceinline__ void df_acc(float& hi, float& lo, float a, float b) {
-  const float p = __fmul_rn(a, b);
-  const float pe = __fmaf_rn(a, b, -p);
-  const float s = __fadd_rn(hi, p);
-  const float bb = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(e, pe));
-}
-// Kahan (compensated) sum s, k: s + k tracks the sum of the added values to about one
-// rounding of each value (the values themselves rounded products here: a Gram entry's
-// error stays within u sqrt(G_ii G_jj), the scale the Cholesky and Jacobi steps need).
-__device__ __forceinline__ void kahan_add(float& s, float& k, float v) {
-  const float y = __fsub_rn(v, k);
-  const float t = __fadd_rn(s, y);
-  k = __fsub_rn(__fsub_rn(t, s), y);
-  s = t;
-}
-__device__ __forceinline__ void df_add(float& hi, float& lo, float bhi, float blo) {
-  const float s = __fadd_rn(hi, bhi);
-  const float bb = __fsub_rn(s, hi);
-  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bhi, bb));
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(e, blo));
-}
-
 // G[i*ldg + j] (j >= i) = sum_{t < m} A[t*lda + i] A[t*lda + j], in double-float (dd) or
 // float32, rounded to float32.  One thread per entry with four independent partial
 // sums (rows t = 4 u + v) combined at the end; consecutive threads take consecutive

@@ -132,6 +132,35 @@ __device__ __forceinline__ float load_xq(const RFProb& q, int64_t e) {
   return load_x(q.X, q.dtype, e);
 }
 
+// Compensated float32 sums (GB300's float64 rate is ~1/64 of float32).
+// hi + lo += a b with the product's and the sum's rounding errors kept (TwoProd by
+// fma, TwoSum).  Explicit _rn intrinsics: the compiler must not contract or reorder.
+__device__ __forceinline__ void df_acc(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+// Kahan (compensated) sum s, k: s + k tracks the sum of the added values to about one
+// rounding of each value (the values themselves rounded products here: a Gram entry's
+// error stays within u sqrt(G_ii G_jj), the scale the Cholesky and Jacobi steps need).
+__device__ __forceinline__ void kahan_add(float& s, float& k, float v) {
+  const float y = __fsub_rn(v, k);
+  const float t = __fadd_rn(s, y);
+  k = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bhi, float blo) {
+  const float s = __fadd_rn(hi, bhi);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(bhi, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, blo));
+}
+
 // Single-instruction approximations (flush-to-zero) used where a few ulp do not matter:
 // the rotation parameters of the Jacobi SVD, whose orthogonality comes from cs^2 + sn^2
 // = 1, not from the exact angle.

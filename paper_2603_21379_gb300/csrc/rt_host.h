@@ -165,6 +165,7 @@ struct KronArgs {
   float* part1;               // [grid][n1 K l_b]
   float* part2;               // [grid][n2 K l_a]
   float* Ts;                  // [S][l_a l_b]
+  float* Wt;                  // [S][K] Kronecker weights of the slabs
   float* z[MAXD];             // outputs Z_k (n_k x L_k)
 };
 struct KronFinish {
@@ -179,7 +180,20 @@ struct KronFinish {
   float* sign;     int roff[MAXD];          // column signs
   int rtotal;
 };
+struct ModeGram {            // Grams of the mode unfoldings of the reduced tensor C
+  const float* C;
+  int d;
+  int L[MAXD];                // sizes of C (<= 64 each)
+  int N[MAXD], B[MAXD];       // columns of C^(k); product of the sizes after mode k
+  int ctas;                   // CTAs per mode
+  float* part;                // partial Grams [ctas][L_k][L_k][2] per mode, at poff[k]
+  int64_t poff[MAXD];
+  float* cp[MAXD];            // the W-step's Gram words of mode k
+  float* qeye[MAXD];          // the W-step's Q of mode k (set to I)
+};
+int launch_mode_gram(const ModeGram& g, cudaStream_t st);
 size_t kron_sketch_smem(const KronArgs& a);
+bool kron_shares_fit(const KronArgs& a);
 int launch_kron_omega(const KronArgs& a, uint64_t seed, cudaStream_t st);
 int launch_kron_sketch(const KronArgs& a, int grid, cudaStream_t st);   // sketch, reduce, leading modes
 int launch_kron_finish(const KronFinish& f, cudaStream_t st);           // U = Q W, signs, core flips
