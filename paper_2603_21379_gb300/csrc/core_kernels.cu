@@ -358,52 +358,94 @@ __global__ void __launch_bounds__(TL_THREADS) k_last2(const float* __restrict__ 
 // its L x n tensor with U_q (n x r <= RW), one thread per row.  pre[j] counts CTAs of
 // TL_THREADS rows before job j.  A's element type T (the batch's X type at the first
 // level); 16-byte loads for float rows with n % 4 == 0.
-template <typename T, int RW>
-__global__ void __launch_bounds__(TL_THREADS) k_ttm_last_grouped(const TTMJob* __restrict__ jobs,
-                                                                 const int64_t* __restrict__ pre, int njobs) {
-  extern __shared__ __align__(16) float us[];   // [n][RW], zero beyond r
-  const int j = find_prob(pre, njobs, blockIdx.x);
-  const TTMJob& q = jobs[j];
+constexpr int TL_RB = 8;   // 128-row blocks per CTA of the grouped last-mode kernel
+
+// Rows [lb0, lb0 + TL_RB TL_THREADS) of one job, RWJ >= r output columns: U in us
+// ([n][RWJ], zero beyond r).  Each warp walks its 32-row groups in 32-column chunks:
+// a chunk is read by 32 coalesced row loads into registers one chunk ahead (so the
+// loads of the next chunk are in flight while this one is computed), transposed
+// through the warp's 32 x 33 tile, and lane i takes row i.
+template <typename T, int RWJ>
+__device__ __forceinline__ void last_rows(const TTMJob& q, const float* us, float* tile, int64_t lb0) {
   const int n = (int)q.n, r = q.r;
-  for (int e = threadIdx.x; e < n * RW; e += TL_THREADS) {
-    const int i = e / RW, a = e % RW;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = (n + 31) >> 5;
+  int nrb = 0;                                   // this warp's row groups
+  while (nrb < TL_RB && lb0 + (int64_t)nrb * TL_THREADS + warp * 32 < q.L) ++nrb;
+  const int nchunk = nrb * nk;
+  float v[32];
+  auto fetch = [&](int c) {
+    const int rb = c / nk, k0 = (c % nk) * 32;
+    const int64_t l0 = lb0 + (int64_t)rb * TL_THREADS + warp * 32;
+    const int nrow = (int)(q.L - l0 < 32 ? q.L - l0 : 32);
+    const T* base = static_cast<const T*>(q.A) + l0 * n;
+    const bool col = k0 + lane < n;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = (i < nrow && col) ? ldf<T>(base + (int64_t)i * n, k0 + lane) : 0.f;
+  };
+  if (nchunk > 0) fetch(0);
+  float acc[RWJ];
+#pragma unroll
+  for (int a = 0; a < RWJ; ++a) acc[a] = 0.f;
+  for (int c = 0; c < nchunk; ++c) {
+#pragma unroll
+    for (int i = 0; i < 32; ++i) tile[i * 33 + lane] = v[i];
+    __syncwarp();
+    if (c + 1 < nchunk) fetch(c + 1);
+    const int rb = c / nk, k0 = (c % nk) * 32, kw = min(32, n - k0);
+    for (int kk = 0; kk < kw; ++kk) {
+      const float x = tile[lane * 33 + kk];
+      const float* ui = us + (k0 + kk) * RWJ;
+#pragma unroll
+      for (int a = 0; a < RWJ; a += 4) {
+        const float4 u = *reinterpret_cast<const float4*>(ui + a);
+        acc[a] = fmaf(x, u.x, acc[a]);
+        acc[a + 1] = fmaf(x, u.y, acc[a + 1]);
+        acc[a + 2] = fmaf(x, u.z, acc[a + 2]);
+        acc[a + 3] = fmaf(x, u.w, acc[a + 3]);
+      }
+    }
+    __syncwarp();
+    if (k0 + 32 >= n) {                          // the row group is complete
+      const int64_t l0 = lb0 + (int64_t)rb * TL_THREADS + warp * 32;
+      if (l0 + lane < q.L) {
+        float* o = q.out + (l0 + lane) * r;
+#pragma unroll
+        for (int a = 0; a < RWJ; ++a)
+          if (a < r) o[a] = acc[a];
+      }
+#pragma unroll
+      for (int a = 0; a < RWJ; ++a) acc[a] = 0.f;
+    }
+  }
+}
+
+template <typename T, int RWJ>
+__device__ __forceinline__ void last_job(const TTMJob& q, float* us, int64_t lb0) {
+  const int n = (int)q.n, r = q.r;
+  for (int e = threadIdx.x; e < n * RWJ; e += TL_THREADS) {
+    const int i = e / RWJ, a = e % RWJ;
     us[e] = a < r ? q.U[i * r + a] : 0.f;
   }
   __syncthreads();
-  const int64_t l = ((int64_t)blockIdx.x - pre[j]) * TL_THREADS + threadIdx.x;
-  if (l >= q.L) return;
-  const T* row = static_cast<const T*>(q.A) + l * n;
-  float acc[RW];
-#pragma unroll
-  for (int a = 0; a < RW; ++a) acc[a] = 0.f;
-  const bool v4 = sizeof(T) == 4 && (n % 4) == 0 && (reinterpret_cast<uintptr_t>(q.A) & 15) == 0;
-  for (int i0 = 0; i0 < n; i0 += 4) {
-    float x[4];
-    if (v4) {
-      const float4 f = __ldg(reinterpret_cast<const float4*>(row + i0));
-      x[0] = f.x; x[1] = f.y; x[2] = f.z; x[3] = f.w;
-    } else {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) x[t] = i0 + t < n ? ldf<T>(row, i0 + t) : 0.f;
-    }
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if (i0 + t >= n) break;
-      const float* ui = us + (i0 + t) * RW;
-#pragma unroll
-      for (int a = 0; a < RW; a += 4) {
-        const float4 u = *reinterpret_cast<const float4*>(ui + a);
-        acc[a] = fmaf(x[t], u.x, acc[a]);
-        acc[a + 1] = fmaf(x[t], u.y, acc[a + 1]);
-        acc[a + 2] = fmaf(x[t], u.z, acc[a + 2]);
-        acc[a + 3] = fmaf(x[t], u.w, acc[a + 3]);
-      }
-    }
-  }
-  float* o = q.out + l * r;
-#pragma unroll
-  for (int a = 0; a < RW; ++a)
-    if (a < r) o[a] = acc[a];
+  float* tile = us + (((n * RWJ) + 3) & ~3) + (threadIdx.x >> 5) * (32 * 33);
+  last_rows<T, RWJ>(q, us, tile, lb0);
+}
+
+// One launch for the last-mode contraction of many jobs (out[l][a] = sum_i A[l][i] U[i][a],
+// row-major A of L x n): CTAs mapped onto jobs by prefix, TL_RB row blocks each, U of
+// the job staged once per CTA at the job's own rank width (8, 16, 24 or 32 <= RW).
+template <typename T, int RW>
+__global__ void __launch_bounds__(TL_THREADS) k_ttm_last_grouped(const TTMJob* __restrict__ jobs,
+                                                                 const int64_t* __restrict__ pre, int njobs) {
+  extern __shared__ __align__(16) float us[];   // [n][RWJ] | per warp a 32 x 33 tile
+  const int j = find_prob(pre, njobs, blockIdx.x);
+  const TTMJob& q = jobs[j];
+  const int64_t lb0 = ((int64_t)blockIdx.x - pre[j]) * (TL_THREADS * TL_RB);
+  if (q.r <= 8) last_job<T, 8>(q, us, lb0);
+  else if (RW >= 16 && q.r <= 16) last_job<T, (RW >= 16 ? 16 : 8)>(q, us, lb0);
+  else if (RW >= 24 && q.r <= 24) last_job<T, (RW >= 24 ? 24 : 8)>(q, us, lb0);
+  else if (RW >= 32) last_job<T, (RW >= 32 ? 32 : 8)>(q, us, lb0);
 }
 
 // ---------------------------------------------------------------- two modes of small slabs
@@ -609,16 +651,19 @@ int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, cons
   return 1;
 }
 
-int64_t ttm_last_job_ctas(const TTMJob& q) { return (q.L + TL_THREADS - 1) / TL_THREADS; }
+int64_t ttm_last_job_ctas(const TTMJob& q) { return (q.L + TL_THREADS * TL_RB - 1) / (TL_THREADS * TL_RB); }
 
 int launch_ttm_last_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs, int64_t total_ctas,
                             int dtype, int nmax, int rmax, cudaStream_t st) {
   if (njobs < 1 || total_ctas < 1 || nmax > 256 || rmax > 32) return 0;
   const int rw = rmax <= 8 ? 8 : rmax <= 16 ? 16 : rmax <= 24 ? 24 : 32;
-  const size_t smem = (size_t)nmax * rw * 4;
+  const size_t smem = (((size_t)nmax * rw + 3) & ~(size_t)3) * 4 + (size_t)(TL_THREADS / 32) * 32 * 33 * 4;
   const unsigned grid = (unsigned)total_ctas;
-#define RT_TLG(T, RWV)                                                                       \
-  k_ttm_last_grouped<T, RWV><<<grid, TL_THREADS, smem, st>>>(jobs_dev, pre_dev, njobs)
+#define RT_TLG(T, RWV)                                                                                     \
+  do {                                                                                                     \
+    cudaFuncSetAttribute(k_ttm_last_grouped<T, RWV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    k_ttm_last_grouped<T, RWV><<<grid, TL_THREADS, smem, st>>>(jobs_dev, pre_dev, njobs);                   \
+  } while (0)
 #define RT_TLG_RW(T)                                                                          \
   if (rw == 8) RT_TLG(T, 8); else if (rw == 16) RT_TLG(T, 16); else if (rw == 24) RT_TLG(T, 24); else RT_TLG(T, 32)
   if (dtype == DT_F32) { RT_TLG_RW(float); }
