@@ -124,9 +124,12 @@ __device__ __forceinline__ float load_x(const void* X, int dtype, int64_t e) {
   return __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(X)[e]);
 }
 
-// Element e of a problem's tensor, float8 storage included (the product of an E4M3
-// value and a power-of-two scale is exact in float32).
+// Element e of a problem's tensor for the fiber gathers, float8 storage included (the
+// product of an E4M3 value and a power-of-two scale is exact in float32).  float32 X
+// is read with ld.global.cg (cached in L2 only): a scattered 4-byte read then costs one
+// 32-byte L2 sector instead of a 128-byte L1 line fill.
 __device__ __forceinline__ float load_xq(const RFProb& q, int64_t e) {
+  if (q.dtype == DT_F32) return __ldcg(reinterpret_cast<const float*>(q.X) + e);
   if (q.dtype == DT_F8)
     return e4m3_value(__ldg(reinterpret_cast<const unsigned char*>(q.X) + e)) * __ldg(q.xsc + e / q.xslab);
   return load_x(q.X, q.dtype, e);
