@@ -108,7 +108,10 @@ typedef struct {
                           with CUDA events on the call's own buffers (the call
                           synchronises its stream once) and the faster is kept
                           in the handle for later calls.  Same result up to
-                          rounding.                                            */
+                          rounding.  rtucker_decompose_batched: 3 times each
+                          contraction level's schedules instead (grouped tiles,
+                          or one row per lane with 1..16 row blocks per CTA;
+                          see rt_last_schedule); other values its defaults.    */
   int32_t qr;          /* factorisations of the range finder (S5 and the W-step
                           of S6, Alg. 1 / Alg. 2).  For unfoldings of at most 256
                           rows with (n_S | 1)(r + p) <= 12288: 1 Householder QR
@@ -308,6 +311,17 @@ rt_status rtucker_loss_grad(rt_handle h, const void* X, rt_dtype dtype, int d, c
 rt_status rtucker_core_adjoint(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_t* n,
                                const int32_t* r, const float* U, const float* Gbar, float* Xbar,
                                float* Ubar);
+
+/* rt_last_schedule: the per-level schedules of the core contractions of the last
+ * rtucker_decompose_batched call on h (level k contracts mode d_t - 1 - k of every
+ * tensor): 0 = generic grouped tiles (32 output rows x 128 columns), b > 0 = one row
+ * per lane, b 128-row blocks per CTA.  With rt_options.core = 3 the batched call picks
+ * each level's schedule among these by timing them once per set of shapes on its own
+ * buffers (cached in the handle); otherwise the defaults are 8 row blocks where the
+ * row form applies (every job a last-mode contraction of <= 256 rows into <= 32
+ * columns) and the tiles elsewhere.  Writes min(levels, cap) entries to out (HOST)
+ * and returns the number of levels (0 before any batched call, -1 for a null h). */
+int rt_last_schedule(rt_handle h, int32_t* out, int cap);
 
 /* rt_set_grad_recompute(h, 1): rtucker_loss_grad and rtucker_core_adjoint (for dU /
  * Ubar) recompute the prefix contractions P_m = T x_0 U_0^T ... x_{m-1} U_{m-1}^T of

@@ -112,6 +112,7 @@ def load_library():
         "rt_fp8_bytes": (ctypes.c_size_t, [ctypes.c_int, P64]),
         "rt_fp8_scale_offset": (ctypes.c_size_t, [ctypes.c_int, P64]),
         "rt_quantize_fp8": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, vp]),
+        "rt_last_schedule": (ctypes.c_int, [vp, P32, ctypes.c_int]),
         "rtucker_kron_sketch": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, u64, PO, vp]),
         "rtucker_rhkron": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, P64, P32, P32, u64, PO, vp, vp]),
     }
@@ -537,7 +538,7 @@ class BatchedDecomposition:
     of all tensors live in two flat float32 buffers (``U_flat``, ``G_flat``);
     ``results()`` gives the per-tensor (G, [U_k]) views."""
 
-    def __init__(self, Xs, ranks, p, seeds, s=None, prec="fp32", graph=False, qr="auto"):
+    def __init__(self, Xs, ranks, p, seeds, s=None, prec="fp32", graph=False, qr="auto", core="auto"):
         self.lib = load_library()
         T = len(Xs)
         dts = {X.dtype for X in Xs}
@@ -583,7 +584,7 @@ class BatchedDecomposition:
         self.U_arr = (ctypes.c_void_p * T)(*[ub + 4 * uoff[t] for t in range(T)])
         self.G_arr = (ctypes.c_void_p * T)(*[gb + 4 * goff[t] for t in range(T)])
         self.seed_arr = (ctypes.c_uint64 * T)(*[int(v) for v in seeds])
-        self._opt_keep = _opts(prec, graph=graph, qr=qr)
+        self._opt_keep = _opts(prec, graph=graph, qr=qr, core=core)
         self.h = _handle(dev.index)
 
     def run(self):
@@ -591,6 +592,14 @@ class BatchedDecomposition:
                                                           self.r_arr, self.p, self.s_arr, self.seed_arr,
                                                           self._opt_keep, self.U_arr, self.G_arr))
         return self
+
+    def schedule(self):
+        """Per-level schedules of the last run's core contractions (rt_last_schedule):
+        0 = grouped tiles, b > 0 = one row per lane with b 128-row blocks per CTA.
+        ``core="tune"`` picks them by timing on the first run."""
+        out = (ctypes.c_int32 * 16)()
+        nlev = self.lib.rt_last_schedule(self.h, out, 16)
+        return [int(out[k]) for k in range(max(0, min(nlev, 16)))]
 
     def results(self):
         out = []

@@ -11,6 +11,7 @@
 #include <cstdlib>
 
 #include <algorithm>
+#include <array>
 #include <map>
 #include <string>
 #include <vector>
@@ -122,6 +123,8 @@ struct rt_handle_s {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // core kernels picked by timing (rt_options.core = 3), per shape
   std::map<std::vector<int64_t>, int> core_tuned;
+  std::map<std::vector<int64_t>, std::vector<int>> batched_tuned;   // per-level schedules
+  std::vector<int> last_schedule;   // the last batched call's per-level schedules
   // CUDA-graph replay: capture stream and cache
   cudaStream_t gstream = nullptr;
   bool capturing = false;            // a graph capture is running (stage timing records nodes)
@@ -1518,6 +1521,13 @@ rt_status rt_quantize_fp8(rt_handle h, const void* X, rt_dtype dtype, int d, con
   return finish(h, nl);
 }
 
+int rt_last_schedule(rt_handle h, int32_t* out, int cap) {
+  if (!h) return -1;
+  const int nlev = (int)h->last_schedule.size();
+  for (int k = 0; k < nlev && k < cap && out; ++k) out[k] = h->last_schedule[k];
+  return nlev;
+}
+
 rt_status rt_selftest_wait(rt_handle h) {
   if (!h) return RT_EINVAL;
   rt_status st;
@@ -2120,12 +2130,21 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
   std::vector<int> njob(dmax, 0);
   for (int t = 0; t < T; ++t)
     for (int k = 0; k < d[t]; ++k) ++njob[k];
-  std::vector<size_t> o_jobs(dmax), o_lpre(dmax);
+  // Schedules of a level (rt_options.core = 3 times them): candidate 0 the generic grouped
+  // tiles, candidate c >= 1 the one-row-per-lane form with kRowBlocks[c - 1] 128-row blocks
+  // per CTA (levels whose jobs all contract a last mode of <= 256 rows into <= 32 columns).
+  static const int kRowBlocks[] = {1, 2, 4, 8, 16};
+  constexpr int NCAND = 6, CAND_DEFAULT_ROWS = 4;   // default: 8 row blocks
+  std::vector<size_t> o_jobs(dmax);
+  std::vector<std::array<size_t, NCAND>> o_lpre(dmax);
   size_t job_bytes = 0;
   for (int k = 0; k < dmax; ++k) {
     o_jobs[k] = bump.take(sizeof(TTMJob) * njob[k]);
-    o_lpre[k] = bump.take(sizeof(int64_t) * (njob[k] + 1));
-    job_bytes += align_up(sizeof(TTMJob) * njob[k]) + align_up(sizeof(int64_t) * (njob[k] + 1));
+    job_bytes += align_up(sizeof(TTMJob) * njob[k]);
+    for (int c = 0; c < NCAND; ++c) {
+      o_lpre[k][c] = bump.take(sizeof(int64_t) * (njob[k] + 1));
+      job_bytes += align_up(sizeof(int64_t) * (njob[k] + 1));
+    }
   }
   if ((st = ensure_ws(h, bump.off)) != RT_OK) return st;
   const size_t gsb = group_stage_bytes(Gp);
@@ -2133,7 +2152,7 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
   if ((st = group_upload(h, Gp, h->h_stage, 0)) != RT_OK) return st;
   // job tables (workspace addresses are final once it is sized), staged after the
   // range-finder tables and uploaded with them
-  std::vector<int64_t> ltiles(dmax, 0);
+  std::vector<std::array<int64_t, NCAND>> ltiles(dmax);
   std::vector<char> last_rows(dmax, 0);
   std::vector<int> lnmax(dmax, 0), lrmax(dmax, 0);
   {
@@ -2141,10 +2160,13 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
     for (int k = 0; k < dmax; ++k) {
       TTMJob* js = reinterpret_cast<TTMJob*>(h->h_stage + so);
       so += align_up(sizeof(TTMJob) * njob[k]);
-      int64_t* ps = reinterpret_cast<int64_t*>(h->h_stage + so);
-      so += align_up(sizeof(int64_t) * (njob[k] + 1));
+      int64_t* ps[NCAND];
+      for (int c = 0; c < NCAND; ++c) {
+        ps[c] = reinterpret_cast<int64_t*>(h->h_stage + so);
+        so += align_up(sizeof(int64_t) * (njob[k] + 1));
+      }
       int q_i = 0;
-      int64_t acc = 0;
+      int64_t acc[NCAND] = {0, 0, 0, 0, 0, 0};
       // a level whose jobs all contract a last mode of <= 256 rows into <= 32 columns
       // takes the one-thread-per-row form (CTAs counted per job by rows)
       bool rows = true;
@@ -2173,25 +2195,83 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
         int64_t uo = 0;
         for (int j = 0; j < m; ++j) uo += n[t][j] * r[t][j];
         q.U = U[t] + uo;
-        ps[q_i] = acc;
-        const int64_t tiles = ttm_job_tiles(q);   // also sets tiles_x
+        for (int c = 0; c < NCAND; ++c) ps[c][q_i] = acc[c];
+        acc[0] += ttm_job_tiles(q);   // also sets tiles_x
         if (rows) {
-          acc += ttm_last_job_ctas(q);
+          for (int c = 1; c < NCAND; ++c) acc[c] += ttm_last_job_ctas(q, kRowBlocks[c - 1]);
           lnmax[k] = std::max<int>(lnmax[k], (int)q.n);
           lrmax[k] = std::max<int>(lrmax[k], q.r);
-        } else {
-          acc += tiles;
         }
         js[q_i++] = q;
       }
-      ps[q_i] = acc;
-      ltiles[k] = acc;
+      for (int c = 0; c < NCAND; ++c) {
+        ps[c][q_i] = acc[c];
+        ltiles[k][c] = acc[c];
+      }
       if ((st = stage_put(h, h->ws + o_jobs[k], js, sizeof(TTMJob) * njob[k])) != RT_OK) return st;
-      if ((st = stage_put(h, h->ws + o_lpre[k], ps, sizeof(int64_t) * (njob[k] + 1))) != RT_OK) return st;
+      for (int c = 0; c < NCAND; ++c)
+        if ((st = stage_put(h, h->ws + o_lpre[k][c], ps[c], sizeof(int64_t) * (njob[k] + 1))) != RT_OK) return st;
     }
   }
   int nl = 0;
   if ((st = stage_commit(h, &nl)) != RT_OK) return st;
+  auto launch_level = [&](int k, int c) -> int {
+    const int dt = k == 0 ? (int)dtype : DT_F32;
+    const TTMJob* jd = reinterpret_cast<const TTMJob*>(h->ws + o_jobs[k]);
+    const int64_t* pd = reinterpret_cast<const int64_t*>(h->ws + o_lpre[k][c]);
+    if (c == 0) return launch_ttm_grouped(jd, pd, njob[k], ltiles[k][0], dt, h->stream);
+    return launch_ttm_last_grouped(jd, pd, njob[k], ltiles[k][c], dt, lnmax[k], lrmax[k], kRowBlocks[c - 1],
+                                   h->stream);
+  };
+  // per-level schedule: fixed defaults, or (core = 3) the fastest candidate, timed once per
+  // set of shapes on the call's own buffers (the values the candidates read and write do
+  // not matter for the time; the decomposition below recomputes everything)
+  std::vector<int> sched(dmax);
+  for (int k = 0; k < dmax; ++k) sched[k] = last_rows[k] ? CAND_DEFAULT_ROWS : 0;
+  if (core_of(opt) == 3) {
+    std::vector<int64_t> tk = {(int64_t)dtype, T};
+    for (int t = 0; t < T; ++t) {
+      tk.push_back(d[t]);
+      for (int k = 0; k < d[t]; ++k) { tk.push_back(n[t][k]); tk.push_back(r[t][k]); }
+    }
+    auto it = h->batched_tuned.find(tk);
+    if (it != h->batched_tuned.end()) {
+      sched = it->second;
+    } else {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(h, RT_ECUDA, "batched tuning: event creation");
+      }
+      const bool timing = h->timing;
+      h->timing = false;
+      cudaError_t ce = cudaSuccess;
+      for (int k = 0; k < dmax && ce == cudaSuccess; ++k) {
+        float best = 0.f;
+        for (int c = 0; c < (last_rows[k] ? NCAND : 1) && ce == cudaSuccess; ++c) {
+          launch_level(k, c);
+          cudaEventRecord(e0, h->stream);
+          for (int rep = 0; rep < 2; ++rep) launch_level(k, c);
+          cudaEventRecord(e1, h->stream);
+          float ms = 0.f;
+          ce = cudaEventSynchronize(e1);
+          if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+          if (ce == cudaSuccess) ce = cudaGetLastError();
+          if (ce == cudaSuccess && (c == 0 || ms < best)) {
+            best = ms;
+            sched[k] = c;
+          }
+        }
+      }
+      h->timing = timing;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (ce != cudaSuccess) return cuda_fail(h, ce, "batched tuning");
+      h->batched_tuned[tk] = sched;
+    }
+  }
+  h->last_schedule.assign(dmax, 0);
+  for (int k = 0; k < dmax; ++k) h->last_schedule[k] = sched[k] == 0 ? 0 : kRowBlocks[sched[k] - 1];
   const bool graph = opt && opt->use_graph;
   GraphKey key;
   if (graph) {
@@ -2211,12 +2291,12 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
     }
     for (int k = 0; k < dmax; ++k) {
       key.add((uint64_t)njob[k]);
-      key.add((uint64_t)ltiles[k]);
-      key.add((uint64_t)last_rows[k]);
+      key.add((uint64_t)sched[k]);
+      key.add((uint64_t)ltiles[k][sched[k]]);
       key.add((uint64_t)lnmax[k]);
       key.add((uint64_t)lrmax[k]);
       key.add(o_jobs[k]);
-      key.add(o_lpre[k]);
+      key.add(o_lpre[k][sched[k]]);
     }
     key.group(Gp.g);
   }
@@ -2227,14 +2307,7 @@ rt_status rtucker_decompose_batched(rt_handle h, int T, const void* const* X, rt
     }
     for (int k = 0; k < dmax; ++k) {
       StageTimer tm(h, k == 0 ? 1 : 2);
-      if (last_rows[k])
-        *nk += launch_ttm_last_grouped(reinterpret_cast<const TTMJob*>(h->ws + o_jobs[k]),
-                                       reinterpret_cast<const int64_t*>(h->ws + o_lpre[k]), njob[k], ltiles[k],
-                                       k == 0 ? (int)dtype : DT_F32, lnmax[k], lrmax[k], h->stream);
-      else
-        *nk += launch_ttm_grouped(reinterpret_cast<const TTMJob*>(h->ws + o_jobs[k]),
-                                  reinterpret_cast<const int64_t*>(h->ws + o_lpre[k]), njob[k], ltiles[k],
-                                  k == 0 ? (int)dtype : DT_F32, h->stream);
+      *nk += launch_level(k, sched[k]);
     }
     return RT_OK;
   });

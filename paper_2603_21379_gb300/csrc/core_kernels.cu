@@ -358,20 +358,18 @@ __global__ void __launch_bounds__(TL_THREADS) k_last2(const float* __restrict__ 
 // its L x n tensor with U_q (n x r <= RW), one thread per row.  pre[j] counts CTAs of
 // TL_THREADS rows before job j.  A's element type T (the batch's X type at the first
 // level); 16-byte loads for float rows with n % 4 == 0.
-constexpr int TL_RB = 8;   // 128-row blocks per CTA of the grouped last-mode kernel
-
-// Rows [lb0, lb0 + TL_RB TL_THREADS) of one job, RWJ >= r output columns: U in us
+// Rows [lb0, lb0 + rb TL_THREADS) of one job, RWJ >= r output columns: U in us
 // ([n][RWJ], zero beyond r).  Each warp walks its 32-row groups in 32-column chunks:
 // a chunk is read by 32 coalesced row loads into registers one chunk ahead (so the
 // loads of the next chunk are in flight while this one is computed), transposed
 // through the warp's 32 x 33 tile, and lane i takes row i.
 template <typename T, int RWJ>
-__device__ __forceinline__ void last_rows(const TTMJob& q, const float* us, float* tile, int64_t lb0) {
+__device__ __forceinline__ void last_rows(const TTMJob& q, const float* us, float* tile, int64_t lb0, int rbn) {
   const int n = (int)q.n, r = q.r;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = (n + 31) >> 5;
   int nrb = 0;                                   // this warp's row groups
-  while (nrb < TL_RB && lb0 + (int64_t)nrb * TL_THREADS + warp * 32 < q.L) ++nrb;
+  while (nrb < rbn && lb0 + (int64_t)nrb * TL_THREADS + warp * 32 < q.L) ++nrb;
   const int nchunk = nrb * nk;
   float v[32];
   auto fetch = [&](int c) {
@@ -421,7 +419,7 @@ __device__ __forceinline__ void last_rows(const TTMJob& q, const float* us, floa
 }
 
 template <typename T, int RWJ>
-__device__ __forceinline__ void last_job(const TTMJob& q, float* us, int64_t lb0) {
+__device__ __forceinline__ void last_job(const TTMJob& q, float* us, int64_t lb0, int rbn) {
   const int n = (int)q.n, r = q.r;
   for (int e = threadIdx.x; e < n * RWJ; e += TL_THREADS) {
     const int i = e / RWJ, a = e % RWJ;
@@ -429,23 +427,25 @@ __device__ __forceinline__ void last_job(const TTMJob& q, float* us, int64_t lb0
   }
   __syncthreads();
   float* tile = us + (((n * RWJ) + 3) & ~3) + (threadIdx.x >> 5) * (32 * 33);
-  last_rows<T, RWJ>(q, us, tile, lb0);
+  last_rows<T, RWJ>(q, us, tile, lb0, rbn);
 }
 
 // One launch for the last-mode contraction of many jobs (out[l][a] = sum_i A[l][i] U[i][a],
-// row-major A of L x n): CTAs mapped onto jobs by prefix, TL_RB row blocks each, U of
-// the job staged once per CTA at the job's own rank width (8, 16, 24 or 32 <= RW).
+// row-major A of L x n): CTAs mapped onto jobs by prefix, rbn 128-row blocks each (the
+// batched autotuner's choice), U of the job staged once per CTA at the job's own rank
+// width (8, 16, 24 or 32 <= RW).
 template <typename T, int RW>
 __global__ void __launch_bounds__(TL_THREADS) k_ttm_last_grouped(const TTMJob* __restrict__ jobs,
-                                                                 const int64_t* __restrict__ pre, int njobs) {
+                                                                 const int64_t* __restrict__ pre, int njobs,
+                                                                 int rbn) {
   extern __shared__ __align__(16) float us[];   // [n][RWJ] | per warp a 32 x 33 tile
   const int j = find_prob(pre, njobs, blockIdx.x);
   const TTMJob& q = jobs[j];
-  const int64_t lb0 = ((int64_t)blockIdx.x - pre[j]) * (TL_THREADS * TL_RB);
-  if (q.r <= 8) last_job<T, 8>(q, us, lb0);
-  else if (RW >= 16 && q.r <= 16) last_job<T, (RW >= 16 ? 16 : 8)>(q, us, lb0);
-  else if (RW >= 24 && q.r <= 24) last_job<T, (RW >= 24 ? 24 : 8)>(q, us, lb0);
-  else if (RW >= 32) last_job<T, (RW >= 32 ? 32 : 8)>(q, us, lb0);
+  const int64_t lb0 = ((int64_t)blockIdx.x - pre[j]) * (TL_THREADS * (int64_t)rbn);
+  if (q.r <= 8) last_job<T, 8>(q, us, lb0, rbn);
+  else if (RW >= 16 && q.r <= 16) last_job<T, (RW >= 16 ? 16 : 8)>(q, us, lb0, rbn);
+  else if (RW >= 24 && q.r <= 24) last_job<T, (RW >= 24 ? 24 : 8)>(q, us, lb0, rbn);
+  else if (RW >= 32) last_job<T, (RW >= 32 ? 32 : 8)>(q, us, lb0, rbn);
 }
 
 // ---------------------------------------------------------------- two modes of small slabs
@@ -651,18 +651,20 @@ int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, cons
   return 1;
 }
 
-int64_t ttm_last_job_ctas(const TTMJob& q) { return (q.L + TL_THREADS * TL_RB - 1) / (TL_THREADS * TL_RB); }
+int64_t ttm_last_job_ctas(const TTMJob& q, int rbn) {
+  return (q.L + (int64_t)TL_THREADS * rbn - 1) / ((int64_t)TL_THREADS * rbn);
+}
 
 int launch_ttm_last_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs, int64_t total_ctas,
-                            int dtype, int nmax, int rmax, cudaStream_t st) {
-  if (njobs < 1 || total_ctas < 1 || nmax > 256 || rmax > 32) return 0;
+                            int dtype, int nmax, int rmax, int rbn, cudaStream_t st) {
+  if (njobs < 1 || total_ctas < 1 || nmax > 256 || rmax > 32 || rbn < 1) return 0;
   const int rw = rmax <= 8 ? 8 : rmax <= 16 ? 16 : rmax <= 24 ? 24 : 32;
   const size_t smem = (((size_t)nmax * rw + 3) & ~(size_t)3) * 4 + (size_t)(TL_THREADS / 32) * 32 * 33 * 4;
   const unsigned grid = (unsigned)total_ctas;
 #define RT_TLG(T, RWV)                                                                                     \
   do {                                                                                                     \
     cudaFuncSetAttribute(k_ttm_last_grouped<T, RWV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    k_ttm_last_grouped<T, RWV><<<grid, TL_THREADS, smem, st>>>(jobs_dev, pre_dev, njobs);                   \
+    k_ttm_last_grouped<T, RWV><<<grid, TL_THREADS, smem, st>>>(jobs_dev, pre_dev, njobs, rbn);              \
   } while (0)
 #define RT_TLG_RW(T)                                                                          \
   if (rw == 8) RT_TLG(T, 8); else if (rw == 16) RT_TLG(T, 16); else if (rw == 24) RT_TLG(T, 24); else RT_TLG(T, 32)

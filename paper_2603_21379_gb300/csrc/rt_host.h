@@ -82,7 +82,7 @@ int launch_ttm_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs
                        cudaStream_t st);
 // Grouped last-mode contractions (every job R = 1, n <= 256, r <= 32): pre counts
 // ttm_last_job_ctas per job; returns 0 when a job does not fit.
-int64_t ttm_last_job_ctas(const TTMJob& q);
+int64_t ttm_last_job_ctas(const TTMJob& q, int rbn);   // rbn 128-row blocks per CTA
 // Two neighbouring modes of small slabs in one read: out(l, a, b, rho) =
 // sum_{i,j} U1[i][a] U2[j][b] A(l, i, j, rho), A (L, n1, n2, R) of the launch's dtype.
 // slab2_fits: whether a slab (n1 n2 R values) and its partial products fit shared
@@ -96,7 +96,7 @@ int launch_last2(const float* X, int64_t S, int64_t n1, int64_t n2, const float*
 int launch_slab2(const void* A, int dtype, int64_t L, int64_t n1, int64_t n2, int64_t R, const float* U1, int r1,
                  const float* U2, int r2, float* out, cudaStream_t st);
 int launch_ttm_last_grouped(const TTMJob* jobs_dev, const int64_t* pre_dev, int njobs, int64_t total_ctas,
-                            int dtype, int nmax, int rmax, cudaStream_t st);
+                            int dtype, int nmax, int rmax, int rbn, cudaStream_t st);
 cudaError_t core_init_attributes();
 // Poll limit of the bounded mbarrier waits (0 = default) in each unit that has them.
 cudaError_t core_tc_set_wait_limit(uint32_t polls);

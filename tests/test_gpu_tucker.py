@@ -620,6 +620,33 @@ def test_graph_replay_matches_direct_launches(rt, overlap):
     _same(g6, d2)
 
 
+def test_batched_tuned_schedules(rt):
+    # rt_options.core = 3 on a batch: each contraction level's schedule picked by timing
+    # (grouped tiles or one row per lane with 1..16 row blocks per CTA), cached per set of
+    # shapes; the cores equal the default schedules' to rounding (the row form with any
+    # block count is bit-identical, the tiles sum in another order)
+    shapes, ranks = synth.batched_shapes(T=24, data_seed=57)
+    Xs = [torch.from_numpy(synth.tucker_tensor(s, r, 1e-4, 60 + i)).cuda() for i, (s, r) in enumerate(zip(shapes, ranks))]
+    seeds = list(range(24))
+    ref = rt.BatchedDecomposition(Xs, [list(r) for r in ranks], 3, seeds).run()
+    want = _clone_all(ref.results())
+    assert ref.schedule() == [8, 0, 0]          # defaults: rows (8 blocks) for the last mode, tiles after
+    bt = rt.BatchedDecomposition(Xs, [list(r) for r in ranks], 3, seeds, core="tune")
+    for _ in range(2):                          # tuned, then the cached choice
+        got = bt.run().results()
+        rt.sync()
+        sch = bt.schedule()
+        assert len(sch) == 3 and sch[0] in (0, 1, 2, 4, 8, 16) and sch[1] == 0 and sch[2] == 0
+        for (Ga, Ua), (Gb, Ub) in zip(got, want):
+            assert torch.allclose(Ga, Gb, rtol=1e-5, atol=1e-5 * float(Gb.abs().max()))
+            for a, b in zip(Ua, Ub):
+                assert torch.equal(a, b)
+
+
+def _clone_all(res):
+    return [(G.clone(), [u.clone() for u in U]) for G, U in res]
+
+
 def test_graph_replay_batched(rt):
     shapes = [(20, 24, 28), (33, 17, 40), (16, 16, 16, 16)]
     ranks = [(3, 4, 5), (4, 3, 6), (3, 3, 3, 3)]
