@@ -371,7 +371,7 @@ def measure_ht(rt, steps, peak, n=None, d=None):
                               "frac": nbytes / (root_ms * 1e-3) / 1e9 / peak}}
 
 
-def measure_scaling(rt, steps):
+def measure_scaling(rt, steps, ns=None):
     """The paper's scaling workloads on one GPU (its parallel experiments):
     Sub-R-HOSVD of order-8 low-rank tensors (rank 5, n = 16, 18, 20: 17 to 102 GB
     float32, s = 10^4 fibers per mode) and Sub-R-RtL-HT of f = 1/||x|| on n^8 grids
@@ -381,7 +381,7 @@ def measure_scaling(rt, steps):
     import synth
     out = {"tucker": [], "ht": []}
     ct = synth.SCALING_TUCKER
-    for n in ct["ns"]:
+    for n in (ns or ct["ns"]):
         shape, r = (n,) * ct["d"], [ct["rank"]] * ct["d"]
         X = synth.tucker_tensor_torch(shape, tuple(r), noise=ct["noise"], data_seed=n, device="cuda")
         nbytes = X.numel() * 4
@@ -404,7 +404,7 @@ def measure_scaling(rt, steps):
         del X, U, G, Us
         torch.cuda.empty_cache()
     ch = synth.SCALING_HT
-    for n in ch["ns"]:
+    for n in (ns or ch["ns"]):
         X = synth.inv_norm_tensor_torch(n, ch["d"], ch["lo"], ch["hi"], device="cuda")
         nbytes = X.numel() * 4
         w = ch["w_per_n"] * n
@@ -428,7 +428,7 @@ def measure_scaling(rt, steps):
     out["workload"] = ("Sub-R-HOSVD: order-8 float32 tensors n^8, n = %s (Gaussian 5^8 core, Q-of-Gaussian "
                        "factors, 1e-6 noise, built on the device), r = 5, p = 5, s = 10^4 per mode; "
                        "Sub-R-RtL-HT: f = 1/||x|| on n^8 grids over [1,2]^8, rank 6, p = 5, w = 20 n"
-                       % (list(ct["ns"]),))
+                       % (list(ns or ct["ns"]),))
     return out
 
 
@@ -533,6 +533,9 @@ def run_ours(args):
         del Xpin, Uh, Gh
         extra["ht"] = measure_ht(rt, max(2, min(args.steps, 5)), peak0)
         extra["grad"] = measure_grad(rt, max(3, min(args.steps, 10)), peak0)
+        # the paper's order-8 scaling workloads at n = 16 (17.2 GB each); 18 and 20 with
+        # --only scaling
+        extra["scaling_n16"] = measure_scaling(rt, max(2, min(args.steps, 3)), ns=(16,))
 
     if rank == 0:
         peak, peak_src = measured_peaks()
