@@ -626,6 +626,12 @@ def run_only(args):
         out = measure_grad(rt, args.steps, peak)
     elif args.only == "scaling":
         out = measure_scaling(rt, args.steps)
+    elif args.only == "rhkron":
+        import synth
+        cfg = synth.ORDER4_128
+        X = torch.from_numpy(synth.named(cfg)).cuda()
+        G, U = rt.rtucker_decompose(X, list(cfg["ranks"]), cfg["p"], seed=cfg["seed"])
+        out = measure_rhkron(rt, X, list(cfg["ranks"]), cfg["seed"], rt.rtucker_relerr(X, G, U), args.steps, peak)
     else:
         out = measure_batched(rt, args.steps)
     print(json.dumps({"only": args.only, **out}))
@@ -639,7 +645,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["ht", "batched", "grad", "scaling"], default=None,
+    ap.add_argument("--only", choices=["ht", "batched", "grad", "scaling", "rhkron"], default=None,
                     help="run one extra workload alone (profiling), not the benchmark line")
     ap.add_argument("--ht-n", type=int, default=None, help="grid size of the H-Tucker workload with --only ht")
     ap.add_argument("--ht-d", type=int, default=None, help="order of the H-Tucker workload with --only ht")
