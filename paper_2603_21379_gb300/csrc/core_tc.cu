@@ -29,15 +29,18 @@
 //   warp 1      TMEM allocator and MMA issuer.  MMA1 per K step:
 //               D1 (n1 x 2 r2p) += X_s [hi(U_2) | lo(U_2)], A = X terms from
 //               TMEM (float32 X) or from the stage (bf16 X).  MMA2 per batch
-//               of 128 / r2p slabs: D2 (64 x 128, rows a < r1) = U_1^T T with
-//               U_1^T (K-major A) and T of the batch (MN-major B, 128 columns)
-//               as bf16 terms in shared memory, three term products.
+//               of 128 / r2p slabs: D2 (128 x 128) = A_U T, where row 2a + t of
+//               A_U is term t (hi, lo) of column a of U_1 (K-major A) and T of
+//               the batch (MN-major B, 128 columns) is split in bf16 terms: two
+//               MMAs per K step (T's terms) give all four term products, and
+//               P = D2 row 2a + D2 row 2a + 1.
 //   warps 2-9   converters (float32 X): two groups of four quadrant warps take
 //               alternate stages; each thread splits one row into bf16 terms
 //               and stores them to a TMEM A buffer (tcgen05.st).
 //   warps 10-13 epilogue: T = D1_hi + D1_lo from TMEM, each thread writes its
 //               row of T as bf16 hi/lo terms with 16-byte stores; after MMA2,
-//               P_s rows from the M = 64 accumulator to global memory.
+//               the two rows of each a are added (lane pairs) and P_s rows
+//               written to global memory.
 // Every mbarrier wait is bounded; on expiry the CTA records the timeout in the
 // status word, stops issuing work, drains and frees its TMEM, and returns.
 #include <cuda.h>
@@ -54,7 +57,6 @@ namespace tc {
 
 using namespace tma;
 
-constexpr int NA = 4;            // TMEM A buffers (32 columns each)
 constexpr int ROWS = 128;        // rows per tile (M)
 constexpr int KC = 32;           // columns per K-chunk (one 128-byte swizzle span)
 constexpr int STAGE_BYTES = ROWS * KC * 4;
@@ -192,7 +194,6 @@ constexpr int NTHREADS_V2 = NWARPS * 32;       // 448
 // could otherwise test a phase two behind and pass), so the number of stages
 // and of TMEM A buffers must be even: stage c % NS and buffer c % NA then
 // always belong to the same group.
-static_assert(NA % 2 == 0, "A buffers must be even");
 
 template <int R2P, int XM>
 struct Layout {
@@ -205,8 +206,10 @@ struct Layout {
   static constexpr int KB = XF8 ? 128 : 64;     // K elements per 128-byte chunk of B1
   static_assert(!XF8 || R2P <= 32, "FP8 form: r_2 <= 32 (TMEM columns)");
   static constexpr int SPB = 128 / R2P;        // slabs per MMA2 batch (N = 128 columns of T)
-  static constexpr int N2 = 128;               // MMA2: U_1^T [T of SPB slabs], M = 64 (rows a < r1)
-  static constexpr int A_COL = 0;              // TMEM: NA A buffers of 32 columns (float32 X only)
+  static constexpr int N2 = 128;               // MMA2: A_U [T of SPB slabs], M = 128 (2 terms x a < 64)
+  static constexpr int NA = 4;                 // TMEM A buffers of 32 columns (float32 X only)
+  static_assert(NA % 2 == 0, "A buffers must be even");
+  static constexpr int A_COL = 0;
   static constexpr int D1_COL = XSMEM ? 0 : NA * 32;
   static constexpr int D2_COL = D1_COL + 2 * N1;
   static constexpr int ND2 = (D2_COL + 2 * N2 <= 512) ? 2 : 1;   // D2 buffers
@@ -220,18 +223,19 @@ struct Layout {
   // atoms of a 64-column group are contiguous (1 KB apart), the two groups 16 KB apart.
   static constexpr int BT_TERM = 128 * 128 * 2;
   static constexpr int BT_NATOM = 16 * 1024;
-  // U_1^T as the K-major A operand of MMA2: 64 rows (a) x K = 128 (i), two 64-wide K chunks
-  static constexpr int AU_TERM = 64 * 128 * 2;
+  // A_U, the K-major A operand of MMA2: 128 rows (2a + term) x K = 128 (i), two 64-wide
+  // K chunks of 16 KB
+  static constexpr int AU_BYTES = 128 * 128 * 2;
   static_assert(TMEM_USED <= 512, "TMEM columns");
 };
 
 // Dynamic shared memory (1024-aligned):
-//   BT[2 terms][2 groups][16 atoms][8][64 bf16] | B1[nkb][N1][64 bf16] | AU[2 terms][2 chunks][64][64 bf16] |
+//   BT[2 terms][2 groups][16 atoms][8][64 bf16] | B1[nkb][N1][64 bf16] | AU[2 chunks][128 rows 2a+t][64 bf16] |
 //   stages[NS3][16 KB] | bars
 template <int R2P, int XM>
 __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_constant__ CUtensorMap tmap, Core2Args args) {
   using LY = Layout<R2P, XM>;
-  constexpr int NS3 = LY::NS, ND2 = LY::ND2;
+  constexpr int NS3 = LY::NS, ND2 = LY::ND2, NA = LY::NA;
   constexpr bool XSMEM = LY::XSMEM, XF8 = LY::XF8;
   constexpr bool XLO = (XM == 0);                  // float32 X keeps its lo term
   constexpr int N1 = LY::N1, N2 = LY::N2, KCX = LY::KCX, SPB = LY::SPB;
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
   unsigned char* BT = base;
   unsigned char* B1 = BT + 2 * LY::BT_TERM;
   unsigned char* AU = B1 + (size_t)nkb * N1 * 128;
-  unsigned char* stages = AU + 2 * LY::AU_TERM;
+  unsigned char* stages = AU + LY::AU_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(stages + NS3 * STAGE_BYTES);
   uint64_t* full = bars;
   uint64_t* empty = full + NS3;
@@ -319,8 +323,8 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
     const int i = e / 64, a = e % 64;
     unsigned short hi = 0, lo = 0;
     if (i < n1 && a < r1) split1_bf16(__ldg(args.U1 + (int64_t)i * r1 + a), hi, lo);
-    *reinterpret_cast<unsigned short*>(AU + sw_off16(a, i, 64)) = hi;
-    *reinterpret_cast<unsigned short*>(AU + LY::AU_TERM + sw_off16(a, i, 64)) = lo;
+    *reinterpret_cast<unsigned short*>(AU + sw_off16(2 * a, i, 128)) = hi;
+    *reinterpret_cast<unsigned short*>(AU + sw_off16(2 * a + 1, i, 128)) = lo;
   }
   // T starts at zero: rows i >= n1 and the columns of a partial batch stay zero
   for (int e = threadIdx.x; e < 2 * LY::BT_TERM / 16; e += NTHREADS_V2)
@@ -338,7 +342,7 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
   const uint32_t tmem = *tmem_slot;
   const uint32_t box_bytes = (uint32_t)n1 * 128;
   constexpr uint32_t idesc1 = XF8 ? idesc_e4m3(128, N1) : idesc_bf16(128, N1);
-  constexpr uint32_t idesc2 = idesc_bf16(64, N2) | (1u << 16);   // B (T) MN-major
+  constexpr uint32_t idesc2 = idesc_bf16(128, N2) | (1u << 16);  // B (T) MN-major
 
   if (warp == 0) {
     // ---------------------------------------------------------------- producer
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       bool ok = true;
-      auto mma2 = [&](int64_t g) -> bool {   // P of batch g: D2 = U1^T T (three products of the bf16 terms)
+      auto mma2 = [&](int64_t g) -> bool {   // P of batch g: D2 = A_U (hi T + lo T)
         // T of batch g is announced on tready[g & 1] (two barriers, by batch parity); the
         // accumulator uses buffer g % ND2
         if (!mbar_wait(&tready[g & 1], (uint32_t)((g >> 1) & 1), abort_flag, args.status)) return false;
@@ -370,13 +374,11 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
         const uint32_t dcol = tmem + LY::D2_COL + b * N2;
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {     // K = 128 in steps of 16
+          const uint64_t adesc = sw128_desc(saddr(AU + (kk >> 2) * 128 * 128 + (kk & 3) * 32));
 #pragma unroll
-          for (int pr = 0; pr < 3; ++pr) {   // (hi U1, hi T), (hi U1, lo T), (lo U1, hi T)
-            const int ta = pr == 2 ? 1 : 0, tb = pr == 1 ? 1 : 0;
-            const uint32_t aaddr = saddr(AU + ta * LY::AU_TERM + (kk >> 2) * 64 * 128 + (kk & 3) * 32);
+          for (int tb = 0; tb < 2; ++tb) {   // hi T, lo T (both terms of U_1 in the rows of A_U)
             const uint32_t baddr = saddr(BT + tb * LY::BT_TERM + kk * 2048);
-            mma_bf16_ss(dcol, sw128_desc(aaddr), mn128_desc(baddr, LY::BT_NATOM, 1024), idesc2,
-                        (kk | pr) ? 1u : 0u);
+            mma_bf16_ss(dcol, adesc, mn128_desc(baddr, LY::BT_NATOM, 1024), idesc2, (kk | tb) ? 1u : 0u);
           }
         }
         mma_commit(&d2full[b]);
@@ -474,10 +476,13 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
       bool ok = __all_sync(0xffffffffu, mbar_wait(&d2full[bb], ph, abort_flag, args.status));
       if (!ok) return false;
       fence_after();
-      // M = 64 accumulator: row a in TMEM lane 32 (a / 16) + a % 16, so warp q holds rows
-      // a = 16 q + lane (lane < 16); column n = j R2P + b of slab j
+      // M = 128 accumulator: row m in TMEM lane m, so warp q holds rows 32 q + lane, i.e.
+      // a = 16 q + lane / 2 with the hi term of U_1 in the even lane and the lo term in the
+      // odd one; column n = j R2P + b of slab j.  Both lanes of a pair form the same sum
+      // and each writes half of the columns.
       if (16 * q < r1) {
-        const int a = 16 * q + lane;
+        const int a = 16 * q + (lane >> 1);
+        const int half = (lane & 1) * (LY::TCH / 2);
 #pragma unroll
         for (int j = 0; j < SPB; ++j) {
           const int64_t t = g * SPB + j;
@@ -488,19 +493,24 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
             for (int cc = 0; cc < LY::TCH / 8; ++cc)
               tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + LY::D2_COL + bb * N2 + j * R2P + b0 + cc * 8, d + 8 * cc);
             tmem_wait_ld();
-            if (lane < 16 && a < r1 && t < nmine) {
-              float* Pout = args.P + ((blockIdx.x + t * gridDim.x) * (int64_t)r1 + a) * r2 + b0;
+            float v[LY::TCH / 2];
+#pragma unroll
+            for (int b = 0; b < LY::TCH; ++b) {
+              const float x = __uint_as_float(d[b]);
+              const float y = x + __shfl_xor_sync(0xffffffffu, x, 1);
+              if ((b < LY::TCH / 2) == ((lane & 1) == 0)) v[b % (LY::TCH / 2)] = y;
+            }
+            if (a < r1 && t < nmine) {
+              float* Pout = args.P + ((blockIdx.x + t * gridDim.x) * (int64_t)r1 + a) * r2 + b0 + half;
               if ((r2 & 3) == 0) {
 #pragma unroll
-                for (int b = 0; b < LY::TCH; b += 4)
-                  if (b0 + b < r2)
-                    *reinterpret_cast<float4*>(Pout + b) =
-                        make_float4(__uint_as_float(d[b]), __uint_as_float(d[b + 1]), __uint_as_float(d[b + 2]),
-                                    __uint_as_float(d[b + 3]));
+                for (int b = 0; b < LY::TCH / 2; b += 4)
+                  if (b0 + half + b < r2)
+                    *reinterpret_cast<float4*>(Pout + b) = make_float4(v[b], v[b + 1], v[b + 2], v[b + 3]);
               } else {
 #pragma unroll
-                for (int b = 0; b < LY::TCH; ++b)
-                  if (b0 + b < r2) Pout[b] = __uint_as_float(d[b]);
+                for (int b = 0; b < LY::TCH / 2; ++b)
+                  if (b0 + half + b < r2) Pout[b] = v[b];
               }
             }
           }
@@ -603,8 +613,8 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
 template <int R2P, int XM>
 static size_t smem_bytes(int nkb) {
   using LY = Layout<R2P, XM>;
-  return 1024 + 2 * (size_t)LY::BT_TERM + (size_t)nkb * LY::N1 * 128 + 2 * (size_t)LY::AU_TERM +
-         (size_t)LY::NS * STAGE_BYTES + 8 * (2 * LY::NS + 2 * NA + 11) + 16;
+  return 1024 + 2 * (size_t)LY::BT_TERM + (size_t)nkb * LY::N1 * 128 + (size_t)LY::AU_BYTES +
+         (size_t)LY::NS * STAGE_BYTES + 8 * (2 * LY::NS + 2 * LY::NA + 11) + 16;
 }
 
 template <int R2P, int XM>
