@@ -180,11 +180,12 @@ __global__ void __launch_bounds__(AW * TN / 64) k_ttm_f32(const float* __restric
     }
   };
 
-  float acc[8][8];
+  // acc2[x][m] holds outputs (x, 2m) and (x, 2m + 1): one packed fma.rn.f32x2 per pair
+  uint64_t acc2[8][4];
 #pragma unroll
   for (int x = 0; x < 8; ++x)
 #pragma unroll
-    for (int y = 0; y < 8; ++y) acc[x][y] = 0.f;
+    for (int m = 0; m < 4; ++m) acc2[x][m] = 0ull;
 
 #pragma unroll
   for (int s = 0; s < TF_TS - 1; ++s) {
@@ -205,11 +206,13 @@ __global__ void __launch_bounds__(AW * TN / 64) k_ttm_f32(const float* __restric
       const float4 b0 = *reinterpret_cast<const float4*>(as + kk * TN);
       const float4 b1 = *reinterpret_cast<const float4*>(as + kk * TN + TN / 2);
       const float ua[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
-      const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      const uint64_t bb[4] = {f2_pack(b0.x, b0.y), f2_pack(b0.z, b0.w), f2_pack(b1.x, b1.y), f2_pack(b1.z, b1.w)};
 #pragma unroll
-      for (int x = 0; x < 8; ++x)
+      for (int x = 0; x < 8; ++x) {
+        const uint64_t uu = f2_pack(ua[x], ua[x]);
 #pragma unroll
-        for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(ua[x], bb[y], acc[x][y]);
+        for (int m = 0; m < 4; ++m) acc2[x][m] = f2_fma(uu, bb[m], acc2[x][m]);
+      }
     }
   }
   cp_async_wait<0>();
@@ -222,12 +225,15 @@ __global__ void __launch_bounds__(AW * TN / 64) k_ttm_f32(const float* __restric
       const int a = a0 + ta * 8 + x;
       if (a >= r) continue;
       float* o = out + (l * r + a) * R + rho;
+      float v[4];
+      f2_unpack(acc2[x][2 * h], v[0], v[1]);
+      f2_unpack(acc2[x][2 * h + 1], v[2], v[3]);
       if (rho + 4 <= R) {
-        *reinterpret_cast<float4*>(o) = make_float4(acc[x][4 * h], acc[x][4 * h + 1], acc[x][4 * h + 2], acc[x][4 * h + 3]);
+        *reinterpret_cast<float4*>(o) = make_float4(v[0], v[1], v[2], v[3]);
       } else {
 #pragma unroll
         for (int y = 0; y < 4; ++y)
-          if (rho + y < R) o[y] = acc[x][4 * h + y];
+          if (rho + y < R) o[y] = v[y];
       }
     }
   }

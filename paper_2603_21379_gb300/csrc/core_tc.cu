@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (row < n1) f = *reinterpret_cast<const float4*>(rowp + ((j ^ (row & 7)) << 4));
+          if (row < n1) f = lds128_slot(rowp + ((j ^ (row & 7)) << 4));
           if (XLO) {
             split_bf16(f.x, f.y, v[2 * j], v[16 + 2 * j]);
             split_bf16(f.z, f.w, v[2 * j + 1], v[16 + 2 * j + 1]);

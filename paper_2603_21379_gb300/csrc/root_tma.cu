@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(RS_THREADS, RS_CTAS_PER_SM) k_root_rows(const 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* xs = base;                                   // [RS_NS][64 rows][128 B], swizzled
-  float* us = reinterpret_cast<float*>(base + RS_NS * RS_XBYTES);  // [RS_NS][32][RR]
+  float* us = reinterpret_cast<float*>(base + RS_NS * RS_XBYTES);  // [RS_NS][32][RE]
   uint64_t* full = reinterpret_cast<uint64_t*>(base + RS_NS * (RS_XBYTES + RS_UBYTES));
   uint64_t* empty = full + RS_NS;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + RS_NS);
@@ -69,7 +69,8 @@ __global__ void __launch_bounds__(RS_THREADS, RS_CTAS_PER_SM) k_root_rows(const 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nitems = (nl + RS_ROWS - 1) / RS_ROWS;
   const int64_t nst = nr / RS_COLS;        // stages per item (nr: columns padded to a multiple of 32)
-  const uint32_t ubytes = (uint32_t)(RS_COLS * RR * 4);
+  constexpr int RE = RR + (RR & 1), RP = RE / 2;   // U_r columns padded to pairs
+  const uint32_t ubytes = (uint32_t)(RS_COLS * RE * 4);
   if (threadIdx.x == 0) {
     for (int i = 0; i < RS_NS; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], RS_CONS); }
     *abort_flag = 0;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(RS_THREADS, RS_CTAS_PER_SM) k_root_rows(const 
           if (!(ok = mbar_wait(&empty[slot], (uint32_t)(((c / RS_NS) & 1) ^ 1), abort_flag, status))) break;
           mbar_arrive_tx(&full[slot], (uint32_t)RS_XBYTES + ubytes);
           tma_load_2d(saddr(xs + slot * RS_XBYTES), &tmap, (int)(s * RS_COLS), (int)(it * RS_ROWS), &full[slot]);
-          bulk_load(saddr(us + slot * (RS_UBYTES / 4)), Ur + s * RS_COLS * RR, ubytes, &full[slot]);
+          bulk_load(saddr(us + slot * (RS_UBYTES / 4)), Ur + s * RS_COLS * RE, ubytes, &full[slot]);
         }
       }
       // the CTA may exit only when no copy into its shared memory is in flight
@@ -111,23 +112,27 @@ __global__ void __launch_bounds__(RS_THREADS, RS_CTAS_PER_SM) k_root_rows(const 
   static_assert(RS_CONS == 4 && RPT == 4 && RSTEP == 16, "lane map below assumes 4 warps of 8 x 4 threads");
   const int rs = 8 * (warp & 1) + (lane >> 2), g = 4 * (warp >> 1) + (lane & 3);
   int64_t c = 0;
+  // Accumulators hold the pairs (k, k + 1) of U_r columns in one packed register pair:
+  // one fma.rn.f32x2 does the two scalar FMAs, rounded the same way.
+  const uint64_t one2 = f2_pack(1.f, 1.f);
   for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x) {
-    float acc[RPT][RR], tot[RPT][RR];
+    uint64_t acc[RPT][RP], tot[RPT][RP];
 #pragma unroll
     for (int h = 0; h < RPT; ++h)
 #pragma unroll
-      for (int k = 0; k < RR; ++k) acc[h][k] = tot[h][k] = 0.f;
+      for (int m = 0; m < RP; ++m) acc[h][m] = tot[h][m] = 0ull;
     bool ok = true;
     for (int64_t s = 0; s < nst; ++s, ++c) {
       const int slot = (int)(c % RS_NS);
       if (!(ok = __all_sync(0xffffffffu, mbar_wait(&full[slot], (uint32_t)((c / RS_NS) & 1), abort_flag, status))))
         break;
-      float u[CPT * RR];
-      const float4* u4 = reinterpret_cast<const float4*>(us + slot * (RS_UBYTES / 4) + CPT * g * RR);
+      uint64_t u2[CPT * RP];            // u2[cc RP + m] = (U_r(col, 2m), U_r(col, 2m + 1))
+      const float4* u4 = reinterpret_cast<const float4*>(us + slot * (RS_UBYTES / 4) + CPT * g * RE);
 #pragma unroll
-      for (int v = 0; v < CPT * RR / 4; ++v) {
-        const float4 w = u4[v];
-        u[4 * v] = w.x; u[4 * v + 1] = w.y; u[4 * v + 2] = w.z; u[4 * v + 3] = w.w;
+      for (int v = 0; v < CPT * RE / 4; ++v) {
+        const float4 w = lds128_slot(u4 + v);
+        u2[2 * v] = f2_pack(w.x, w.y);
+        u2[2 * v + 1] = f2_pack(w.z, w.w);
       }
 #pragma unroll
       for (int h = 0; h < RPT; ++h) {
@@ -136,13 +141,15 @@ __global__ void __launch_bounds__(RS_THREADS, RS_CTAS_PER_SM) k_root_rows(const 
         float x[CPT];
 #pragma unroll
         for (int q = 0; q < CPT / 4; ++q) {
-          const float4 xv = *reinterpret_cast<const float4*>(rp + ((((CPT / 4) * g + q) ^ (row & 7)) << 4));
+          const float4 xv = lds128_slot(rp + ((((CPT / 4) * g + q) ^ (row & 7)) << 4));
           x[4 * q] = xv.x; x[4 * q + 1] = xv.y; x[4 * q + 2] = xv.z; x[4 * q + 3] = xv.w;
         }
 #pragma unroll
-        for (int cc = 0; cc < CPT; ++cc)
+        for (int cc = 0; cc < CPT; ++cc) {
+          const uint64_t xx = f2_pack(x[cc], x[cc]);
 #pragma unroll
-          for (int k = 0; k < RR; ++k) acc[h][k] = fmaf(x[cc], u[cc * RR + k], acc[h][k]);
+          for (int m = 0; m < RP; ++m) acc[h][m] = f2_fma(xx, u2[cc * RP + m], acc[h][m]);
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[slot]);
@@ -150,9 +157,9 @@ __global__ void __launch_bounds__(RS_THREADS, RS_CTAS_PER_SM) k_root_rows(const 
 #pragma unroll
         for (int h = 0; h < RPT; ++h)
 #pragma unroll
-          for (int k = 0; k < RR; ++k) {
-            tot[h][k] += acc[h][k];
-            acc[h][k] = 0.f;
+          for (int m = 0; m < RP; ++m) {
+            tot[h][m] = f2_fma(acc[h][m], one2, tot[h][m]);   // tot + acc, one rounding
+            acc[h][m] = 0ull;
           }
       }
     }
@@ -165,11 +172,18 @@ __global__ void __launch_bounds__(RS_THREADS, RS_CTAS_PER_SM) k_root_rows(const 
     for (int h = 0; h < RPT; ++h) {
       const int64_t a = it * RS_ROWS + rs + RSTEP * h;
 #pragma unroll
-      for (int k = 0; k < RR; ++k) {
-        float v = tot[h][k];
-        v += __shfl_xor_sync(0xffffffffu, v, 1);
-        v += __shfl_xor_sync(0xffffffffu, v, 2);
-        if ((lane & 3) == 0 && a < nl) T[(a * 2 + half) * RR + k] = v;
+      for (int m = 0; m < RP; ++m) {
+        float tv[2];
+        f2_unpack(tot[h][m], tv[0], tv[1]);
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int k = 2 * m + e;
+          if (k >= RR) continue;
+          float v = tv[e];
+          v += __shfl_xor_sync(0xffffffffu, v, 1);
+          v += __shfl_xor_sync(0xffffffffu, v, 2);
+          if ((lane & 3) == 0 && a < nl) T[(a * 2 + half) * RR + k] = v;
+        }
       }
     }
   }
@@ -224,8 +238,12 @@ static size_t stream_base_floats(int64_t nl, int rl, int rr) {
 
 cudaError_t root_tma_set_wait_limit(uint32_t polls) { return tma::set_wait_limit(polls); }
 
+// U_r goes through a zero-padded copy when n_r is not a multiple of the 32-column stage
+// or r_r is odd (the kernel reads U_r rows of r_r + (r_r & 1) floats: column pairs).
+static bool needs_upad(int64_t nr, int rr) { return (nr % RS_COLS) != 0 || (rr & 1) != 0; }
+
 size_t root_stream_scratch_floats(int64_t nl, int64_t nr, int rl, int rr) {
-  const size_t upad = nr % RS_COLS ? (size_t)cols_padded(nr) * rr : 0;
+  const size_t upad = needs_upad(nr, rr) ? (size_t)cols_padded(nr) * (rr + (rr & 1)) : 0;
   return stream_base_floats(nl, rl, rr) + upad;
 }
 
@@ -233,7 +251,8 @@ size_t root_stream_scratch_floats(int64_t nl, int64_t nr, int rl, int rr) {
 // aligned X and U_r and r_l, r_r <= 12.  When n_r is not a multiple of the 32-column
 // stage, the last stage's TMA box overhangs the rows (the copy fills those columns
 // with zeros) and U_r is first copied into a zero-padded buffer of ceil(n_r / 32) * 32
-// rows, so that every stage's bulk copy of U_r stays inside it.  Returns the number
+// rows, so that every stage's bulk copy of U_r stays inside it; for odd r_r the copy
+// also gets a zero column (rows of r_r + 1 floats).  Returns the number
 // of launches, or 0 when the shape does not qualify (the caller then uses the tiled
 // kernel).  `scratch` holds root_stream_scratch_floats() floats; `reduce` launches the
 // final float64 sum.
@@ -258,11 +277,13 @@ int launch_root_stream(const float* X, int64_t nl, int64_t nr, const float* Ul, 
   const int64_t ncols = cols_padded(nr);
   const float* Urs = Ur;
   int n = 0;
-  if (ncols != nr) {
+  if (needs_upad(nr, rr)) {
+    const int re = rr + (rr & 1);
     float* Urp = scratch + stream_base_floats(nl, rl, rr);
     if ((reinterpret_cast<uintptr_t>(Urp) & 15u) ||
-        cudaMemcpyAsync(Urp, Ur, (size_t)nr * rr * 4, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(Urp + (size_t)nr * rr, 0, (size_t)(ncols - nr) * rr * 4, st) != cudaSuccess)
+        cudaMemsetAsync(Urp, 0, (size_t)ncols * re * 4, st) != cudaSuccess ||
+        cudaMemcpy2DAsync(Urp, (size_t)re * 4, Ur, (size_t)rr * 4, (size_t)rr * 4, (size_t)nr,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       return 0;
     Urs = Urp;
   }

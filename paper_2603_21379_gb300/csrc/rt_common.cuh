@@ -167,6 +167,24 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float bhi, float bl
 // Single-instruction approximations (flush-to-zero) used where a few ulp do not matter:
 // the rotation parameters of the Jacobi SVD, whose orthogonality comes from cs^2 + sn^2
 // = 1, not from the exact angle.
+// Pairs of float32 in one 64-bit register pair for the packed FMA of sm_100-class
+// GPUs: fma.rn.f32x2 rounds each lane exactly as a scalar fmaf does, so a kernel that
+// packs two independent accumulators gives bit-identical results with half the FMA
+// instructions.
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 __device__ __forceinline__ float rsqrt_approx(float x) {
   float y;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));

@@ -66,6 +66,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   return false;
 }
 
+// 16-byte shared-memory read of a ring slot that a bulk/TMA copy refills once this
+// thread's warp arrives on the slot's empty barrier.  The read must happen before that
+// arrival and only then: a plain load may be repeated by the compiler after the
+// arrival (it sees no store to the slot in between; the copy is invisible to it), which
+// would read the next use's data.  A volatile load is neither moved nor repeated.
+__device__ __forceinline__ float4 lds128_slot(const void* p) {
+  float4 v;
+  asm volatile("ld.volatile.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(saddr(p)));
+  return v;
+}
+
 // 2D tiled tensor load into shared memory, completing on `bar`.
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(

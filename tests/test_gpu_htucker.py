@@ -119,6 +119,16 @@ def test_root_stream_wide(rt):
     _compare_ht(rt, X, 7, 3, seed=6)
 
 
+@pytest.mark.parametrize("rank", [7, 8])
+def test_root_stream_rank8_rows(rt, rank):
+    # 16^3 x 40: X^(R_l) is 256 x 640 (20 column stages, more than the 8-slot ring twice
+    # over) with U_r rows of 8 floats (rank 8, and rank 7 padded to 8): the case where
+    # ring slots read with plain shared loads were read again after their release
+    rs = np.random.default_rng(21)
+    X = rs.standard_normal((16, 16, 16, 40)).astype(np.float32)
+    _compare_ht(rt, X, rank, 2, seed=2)
+
+
 def test_exact_hierarchical_rank_recovery(rt):
     rs = np.random.default_rng(3)
     shape = (5, 6, 4, 5, 6)
