@@ -549,6 +549,34 @@ def test_order4_128_full_size(rt):
     assert abs(eb - ebr) <= RELERR_TOL, (eb, ebr)
 
 
+def test_decompositions_in_flight_on_several_streams(rt):
+    # the benchmark's timed run: decompositions of the 128^4 workload on four CUDA
+    # streams at once (one library handle, input copy and output per stream, graph
+    # replay), round robin; every result equals the one-at-a-time result bit for bit,
+    # and that result is the oracle's (test_order4_128_full_size)
+    cfg = synth.ORDER4_128
+    X = torch.from_numpy(synth.named(cfg)).cuda()
+    r, p, seed = list(cfg["ranks"]), cfg["p"], cfg["seed"]
+    n = list(X.shape)
+    nu = sum(a * b for a, b in zip(n, r))
+    G0, U0 = rt.rtucker_decompose(X, r, p, seed=seed)
+    U0 = torch.cat([u.reshape(-1) for u in U0])
+    P = 4
+    streams = [torch.cuda.Stream() for _ in range(P)]
+    Xs = [X.clone() for _ in range(P)]
+    outs = [(torch.empty(nu, device="cuda"), torch.empty(r, device="cuda")) for _ in range(P)]
+    torch.cuda.synchronize()
+    for i in range(3 * P):
+        k = i % P
+        with torch.cuda.stream(streams[k]):
+            rt.rtucker_decompose(Xs[k], r, p, seed=seed, out=outs[k], graph=True)
+    torch.cuda.synchronize()
+    for k in range(P):
+        with torch.cuda.stream(streams[k]):
+            rt.sync()
+        assert torch.equal(outs[k][0], U0) and torch.equal(outs[k][1], G0), k
+
+
 def test_repeated_calls_reuse_tables_safely(rt):
     # identical calls may skip re-uploading the problem tables; any other use of the
     # workspace in between (another decomposition, a core or gradient call) must not
