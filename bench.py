@@ -222,6 +222,30 @@ def _event_time(fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
+def _inflight_time(streams, fns, steps, warmup):
+    """ms per step with len(fns) steps in flight: step i calls fns[i % P] on
+    streams[i % P] (each slot with its own library handle, inputs and outputs)."""
+    import torch
+    P = len(fns)
+    for i in range(warmup * P):
+        with torch.cuda.stream(streams[i % P]):
+            fns[i % P]()
+    torch.cuda.synchronize()
+    main = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(main)
+    for sk in streams:
+        sk.wait_event(e0)
+    for i in range(steps):
+        with torch.cuda.stream(streams[i % P]):
+            fns[i % P]()
+    for sk in streams:
+        main.wait_stream(sk)
+    e1.record(main)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
 def measure_forms(rt, X, r, p, seed, relerr_fp32, steps):
     """BF16 compute form, bfloat16-stored X, the BF16 sketch and float8-stored X on the
     128^4 workload, against the float32 plain form: time per decomposition and the error of the
@@ -312,6 +336,19 @@ def measure_batched(rt, steps):
     dflt = rt.BatchedDecomposition(Xs, ranks, p, seeds, graph=True)
     ms_d = _event_time(dflt.run, steps, 2)
     del dflt
+    # two batches in flight (two streams, each with its own plan, handle and copy of the
+    # 256 tensors): one batch's range finder runs beside the other's contractions
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    plans = []
+    for k in range(2):
+        with torch.cuda.stream(streams[k]):
+            Xk = Xs if k == 0 else [x.clone() for x in Xs]
+            pk = rt.BatchedDecomposition(Xk, ranks, p, seeds, graph=True, core="tune")
+            pk.run()
+            plans.append((pk, Xk))
+    torch.cuda.synchronize()
+    ms_b2 = _inflight_time(streams, [pl.run for pl, _ in plans], 2 * steps, 1)
+    del plans
 
     def plain():
         for X, rk, sd in zip(Xs, ranks, seeds):
@@ -328,6 +365,9 @@ def measure_batched(rt, steps):
             "api": "rtucker_decompose_batched, use_graph=1, core=3 (schedules tuned on the first call)",
             "schedule": sched, "ms_per_batch_default_schedule": ms_d,
             "ms_per_batch": ms_b, "tensors_per_s": cfg["T"] / (ms_b * 1e-3),
+            "inflight2": {"ms_per_batch": ms_b2, "tensors_per_s": cfg["T"] / (ms_b2 * 1e-3),
+                          "input_gbs": nbytes / (ms_b2 * 1e-3) / 1e9,
+                          "how": "two batches in flight on two streams, one plan and copy of the tensors each"},
             "input_gbs": nbytes / (ms_b * 1e-3) / 1e9,
             "plain_loop_ms": ms_p, "plain_loop_tensors_per_s": cfg["T"] / (ms_p * 1e-3),
             "max_delta_relerr_vs_plain": dmax}
@@ -359,12 +399,22 @@ def measure_ht(rt, steps, peak, n=None, d=None):
     root_ms = stg["ht_root_pass"][0] / max(1, stg["ht_root_pass"][1])
     U_leaf, B = step()
     e = rt.rhtucker_relerr(X, U_leaf, B, cfg["rank"])
-    del X
+    del U_leaf, B
+    # two decompositions in flight (two streams, each with its own handle and copy of X):
+    # one's range finder runs beside the other's root pass
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    Xs = [X, X.clone()]
+    fns = [lambda k=k: rt.rhtucker_decompose(Xs[k], cfg["rank"], cfg["p"], w=cfg["w"], seed=cfg["seed"])
+           for k in range(2)]
+    ms2 = _inflight_time(streams, fns, 2 * max(1, steps // 2), 1)
+    del Xs, fns, X
     torch.cuda.empty_cache()
     return {"workload": "Sub-R-RtL-HT, f=1/||x|| on a %d^%d grid over [1,2]^%d (%.2f GB float32), balanced "
                         "tree, rank 10, p=5, w=320 columns per node, seed 3"
                         % (cfg["n"], cfg["d"], cfg["d"], nbytes / 1e9),
             "ms_per_decomp": ms, "input_gbs": nbytes / (ms * 1e-3) / 1e9, "relerr": e,
+            "inflight2": {"ms_per_decomp": ms2, "input_gbs": nbytes / (ms2 * 1e-3) / 1e9,
+                          "how": "two decompositions in flight on two streams, one handle and copy of X each"},
             "stage_ms": {k: v[0] / max(1, v[1]) for k, v in stg.items() if v[1]},
             "root_roofline": {"bound": "hbm", "kernel": "k_root (B_R = U_l^T X U_r, one read of X)",
                               "achieved": nbytes / (root_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
