@@ -750,7 +750,8 @@ int sketch_of(const rt_options* opt) { return opt ? opt->sketch : 0; }
 // (also RT_CORE_MODE=0).  Auto takes the tensor-core pass over X for slabs of at least
 // TC_MIN_SIDE x TC_MIN_SIDE (its MMA tiles are 128 rows; smaller slabs leave most of
 // each tile empty); then, from the last remaining modes down, two modes at a time
-// with k_slab2 where a slab fits shared memory, else one mode.  prec RT_PREC_BF16
+// with k_slab2 where a slab fits shared memory, else one mode (after the tensor-core
+// pass, on the tensor cores too where the shape allows: k_ttm_tc).  prec RT_PREC_BF16
 // rounds float32 X to one bf16 term in the tensor-core pass (the factors and the
 // intermediate keep two terms); the FFMA kernels compute in float32.
 constexpr int64_t TC_MIN_SIDE = 64;
@@ -766,6 +767,7 @@ int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_
   int adt = (int)dtype;
   int ping = 0;
   int k = d - 1;
+  bool tc_core = false;     // the tensor-core pass ran: the later one-mode contractions too
   if (core_mode() == 0) core = 2;
   // the last two modes in one tensor-core pass over X, when the shape allows
   const bool tc_pref = core == 1 || (core == 0 && n[d - 2] >= TC_MIN_SIDE && n[d - 1] >= TC_MIN_SIDE) ||
@@ -791,6 +793,7 @@ int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_
       adt = DT_F32;
       ping = 1;
       k = d - 3;
+      tc_core = true;
     }
   }
   if (A == X && k == d - 1 && dtype == RT_F32 && last2_fits(n[d - 2], n[d - 1], r[d - 2], r[d - 1])) {
@@ -834,7 +837,10 @@ int enqueue_core(rt_handle h, const void* X, rt_dtype dtype, int d, const int64_
     float* out = (k == 0) ? G : (ping ? bufB : bufA);
     {
       StageTimer tm(h, A == X ? 1 : 2);
-      nl += launch_ttm_t(A, adt, L, n[k], R, U + uoff[k], r[k], out, st);
+      int got = 0;
+      if (tc_core && adt == DT_F32)
+        got = launch_ttm_tc(static_cast<const float*>(A), L, n[k], R, U + uoff[k], r[k], out, h->d_status, st);
+      nl += got > 0 ? got : launch_ttm_t(A, adt, L, n[k], R, U + uoff[k], r[k], out, st);
     }
     A = out;
     adt = DT_F32;

@@ -51,6 +51,7 @@
 #include "rt_common.cuh"
 #include "rt_host.h"
 #include "tma_util.cuh"
+#include "tc_util.cuh"
 
 namespace rt {
 namespace tc {
@@ -60,61 +61,6 @@ using namespace tma;
 constexpr int ROWS = 128;        // rows per tile (M)
 constexpr int KC = 32;           // columns per K-chunk (one 128-byte swizzle span)
 constexpr int STAGE_BYTES = ROWS * KC * 4;
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t addr) {
-  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
-  d |= (uint64_t)1 << 46;              // descriptor version
-  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
-  return d;
-}
-
-// Shared-memory matrix descriptor: MN-major, 128-byte swizzle (atoms of 8 K-rows x 128
-// bytes of MN); lbo = bytes between atoms along MN, sbo = bytes between 8-row groups
-// along K.
-__device__ __forceinline__ uint64_t mn128_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(bar))
-               : "memory");
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
-      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
-      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
-      : "memory");
-}
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-      : "memory");
-}
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-               : "r"(taddr)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 
 struct Core2Args {
@@ -128,62 +74,6 @@ struct Core2Args {
   int* status;
 };
 
-// 16-bit MMA operands.  Instruction descriptor for kind::f16 with bf16 A/B, f32 D.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_bf16_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void mma_bf16_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(
-          d),
-      "r"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-// 8-bit MMA operands (kind::f8f6f4), E4M3 A and B, f32 D.
-__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N) {
-  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void mma_f8_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-          d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
-}
-// (hi, lo) bf16 pairs of two floats packed low = x0, high = x1.
-__device__ __forceinline__ uint32_t pack_bf16(float x0, float x1) {
-  uint32_t r;
-  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
-  return r;
-}
-__device__ __forceinline__ void split_bf16(float x0, float x1, uint32_t& hi, uint32_t& lo) {
-  hi = pack_bf16(x0, x1);
-  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
-  lo = pack_bf16(x0 - h0, x1 - h1);
-}
-__device__ __forceinline__ void split1_bf16(float x, unsigned short& hi, unsigned short& lo) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(x);
-  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-  hi = *reinterpret_cast<const unsigned short*>(&h);
-  lo = *reinterpret_cast<const unsigned short*>(&l);
-}
-// Byte offset of bf16 element (row, k) in a K-major, 128-byte-swizzled operand
-// whose K range is split into 64-element chunks of `rows` x 128 bytes.
-__device__ __forceinline__ int sw_off16(int row, int k, int rows) {
-  const int kc = k >> 6, kl = k & 63;
-  return kc * rows * 128 + row * 128 + ((((kl >> 3) ^ (row & 7)) << 4) | ((kl & 7) << 1));
-}
-// The same for 8-bit elements: 128-element K chunks.
-__device__ __forceinline__ int sw_off8(int row, int k, int rows) {
-  const int kc = k >> 7, kl = k & 127;
-  return kc * rows * 128 + row * 128 + ((((kl >> 4) ^ (row & 7)) << 4) | (kl & 15));
-}
 
 constexpr int NCONV = 8;                       // converter warps: two groups of four quadrants
 constexpr int W_CONV0 = 2, W_EPI0 = W_CONV0 + NCONV;
@@ -311,20 +201,43 @@ __global__ void __launch_bounds__(NTHREADS_V2, 1) k_core2_tc(const __grid_consta
       }
     }
   } else {
-    for (int e = threadIdx.x; e < nkb * 64 * R2P; e += NTHREADS_V2) {
-      const int k = e / R2P, col = e % R2P;
-      unsigned short hi = 0, lo = 0;
-      if (k < n2 && col < r2) split1_bf16(__ldg(args.U2 + (int64_t)k * r2 + col), hi, lo);
-      *reinterpret_cast<unsigned short*>(B1 + sw_off16(col, k, N1)) = hi;
-      *reinterpret_cast<unsigned short*>(B1 + sw_off16(R2P + col, k, N1)) = lo;
+    // (eight loads of a thread in flight per round: a loop of dependent load-then-store
+    // steps would pay the load latency once per element before the first X stage)
+    const int tot2 = nkb * 64 * R2P;
+    for (int e0 = threadIdx.x; e0 < tot2; e0 += 8 * NTHREADS_V2) {
+      float uv[8];
+#pragma unroll
+      for (int q2 = 0; q2 < 8; ++q2) {
+        const int e = e0 + q2 * NTHREADS_V2, k = e / R2P, col = e % R2P;
+        uv[q2] = (e < tot2 && k < n2 && col < r2) ? __ldg(args.U2 + (int64_t)k * r2 + col) : 0.f;
+      }
+#pragma unroll
+      for (int q2 = 0; q2 < 8; ++q2) {
+        const int e = e0 + q2 * NTHREADS_V2, k = e / R2P, col = e % R2P;
+        if (e >= tot2) break;
+        unsigned short hi, lo;
+        split1_bf16(uv[q2], hi, lo);
+        *reinterpret_cast<unsigned short*>(B1 + sw_off16(col, k, N1)) = hi;
+        *reinterpret_cast<unsigned short*>(B1 + sw_off16(R2P + col, k, N1)) = lo;
+      }
     }
   }
-  for (int e = threadIdx.x; e < 128 * 64; e += NTHREADS_V2) {
-    const int i = e / 64, a = e % 64;
-    unsigned short hi = 0, lo = 0;
-    if (i < n1 && a < r1) split1_bf16(__ldg(args.U1 + (int64_t)i * r1 + a), hi, lo);
-    *reinterpret_cast<unsigned short*>(AU + sw_off16(2 * a, i, 128)) = hi;
-    *reinterpret_cast<unsigned short*>(AU + sw_off16(2 * a + 1, i, 128)) = lo;
+  for (int e0 = threadIdx.x; e0 < 128 * 64; e0 += 8 * NTHREADS_V2) {
+    float uv[8];
+#pragma unroll
+    for (int q2 = 0; q2 < 8; ++q2) {
+      const int e = e0 + q2 * NTHREADS_V2, i = e / 64, a = e % 64;
+      uv[q2] = (e < 128 * 64 && i < n1 && a < r1) ? __ldg(args.U1 + (int64_t)i * r1 + a) : 0.f;
+    }
+#pragma unroll
+    for (int q2 = 0; q2 < 8; ++q2) {
+      const int e = e0 + q2 * NTHREADS_V2, i = e / 64, a = e % 64;
+      if (e >= 128 * 64) break;
+      unsigned short hi, lo;
+      split1_bf16(uv[q2], hi, lo);
+      *reinterpret_cast<unsigned short*>(AU + sw_off16(2 * a, i, 128)) = hi;
+      *reinterpret_cast<unsigned short*>(AU + sw_off16(2 * a + 1, i, 128)) = lo;
+    }
   }
   // T starts at zero: rows i >= n1 and the columns of a partial batch stay zero
   for (int e = threadIdx.x; e < 2 * LY::BT_TERM / 16; e += NTHREADS_V2)

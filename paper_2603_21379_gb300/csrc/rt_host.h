@@ -67,6 +67,11 @@ cudaError_t rf_init_attributes();
 // out(L, r, R) = sum_i U[i][a] A(L, n, R): mode contraction with U^T.
 int launch_ttm_t(const void* A, int dtype, int64_t L, int64_t n, int64_t R, const float* U, int r,
                  float* out, cudaStream_t st);
+// The same for float32 A on the tensor cores (ttm_tc.cu; bf16 hi/lo terms of A and U,
+// float32 accumulate): n <= 128, r <= 64, R % 4 == 0, 16-byte aligned A and out.
+// Returns the number of launches, or 0 when the shape does not qualify.
+int launch_ttm_tc(const float* A, int64_t L, int64_t n, int64_t R, const float* U, int r, float* out, int* status,
+                  cudaStream_t st);
 // One mode contraction out(l, a, rho) = sum_i U[i][a] A(l, i, rho) of a grouped launch
 // (A's element type is the launch's dtype).
 struct TTMJob {
