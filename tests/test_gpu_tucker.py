@@ -292,8 +292,8 @@ def test_core_tensor_core_pass_ranks_up_to_64(rt, dtype):
 
 def test_core_wide_rho_ragged_tiles(rt):
     # order 4: the tensor-core pass contracts modes 3, 4 (P has 12*12 = 144 trailing
-    # entries per slab), then the register-tiled FP32 contraction runs twice with ragged
-    # rho tiles (144 and 7*144 = 1008), ragged i (45, 37) and a-blocks of 5 and 7 rows
+    # entries per slab), then the tensor-core one-mode contraction runs twice with ragged
+    # 128-column tiles (144 and 7*144 = 1008), K below 128 (45, 37) and 5 and 7 rows of U
     rs = np.random.default_rng(5)
     shape, ranks = (37, 45, 24, 20), (5, 7, 12, 12)
     X = rs.standard_normal(shape).astype(np.float32)
@@ -304,6 +304,22 @@ def test_core_wide_rho_ragged_tiles(rt):
     Gr = tucker.multi_ttm_t(X.astype(np.float64), Uf)
     assert G.shape == tuple(ranks)
     assert np.abs(to_np(G) - Gr).max() <= 1e-4 * np.abs(Gr).max()
+
+
+@pytest.mark.parametrize("shape,ranks", [
+    ((20, 128, 64, 64), (50, 64, 8, 8)),        # tensor-core contractions: n = 128 and r = 64
+                                                # (four TMEM lane quadrants), then n = 20, r = 50
+    ((150, 72, 64, 64), (9, 33, 6, 10)),        # n = 72 on the tensor cores, then n = 150 > 128:
+                                                # the FFMA contraction for the last one
+])
+def test_core_tensor_core_contraction_shapes(rt, shape, ranks):
+    rs = np.random.default_rng(sum(shape))
+    X = rs.standard_normal(shape).astype(np.float32)
+    U = [np.linalg.qr(rs.standard_normal((n, k)))[0].astype(np.float32) for n, k in zip(shape, ranks)]
+    G = rt.rtucker_core(torch.from_numpy(X).cuda(), [torch.from_numpy(u).cuda() for u in U], core="tc")
+    rt.sync()
+    Gr = tucker.multi_ttm_t(X.astype(np.float64), [u.astype(np.float64) for u in U])
+    assert np.abs(to_np(G) - Gr).max() <= 1e-5 * np.abs(Gr).max()
 
 
 @pytest.mark.parametrize("shape,ranks,dtype", [
