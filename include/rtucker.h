@@ -100,6 +100,8 @@ typedef struct {
   int32_t core;        /* kernels of the core contraction (rtucker_decompose,
                           rtucker_core): 0 (default) auto: the tensor-core pass
                           over X for slabs of at least 64 x 64 (last two modes),
+                          after it the remaining one-mode contractions on the
+                          tensor cores too where n_k <= 128 and r_k <= 64;
                           two-mode FFMA passes over small slabs that fit shared
                           memory, one-mode FFMA contractions otherwise; 1 the
                           tensor-core pass whenever the shape allows it; 2 FFMA
