@@ -81,13 +81,17 @@ __global__ void __launch_bounds__(SO_THREADS) k_tucker_slab_out(
     __syncthreads();
     for (int j = threadIdx.x; j < n2p; j += SO_THREADS) {
       for (int a0 = 0; a0 < r1; a0 += 4) {
-        float t4[4] = {0.f, 0.f, 0.f, 0.f};
+        uint64_t t01 = 0ull, t23 = 0ull;          // (a0, a0 + 1), (a0 + 2, a0 + 3), packed
         for (int b = 0; b < r2; ++b) {
           const float u = U2t[b * n2p + j];
+          const uint64_t uu = f2_pack(u, u);
           const float4 hv = *reinterpret_cast<const float4*>(HsT + b * r1p + a0);
-          t4[0] = fmaf(hv.x, u, t4[0]); t4[1] = fmaf(hv.y, u, t4[1]);
-          t4[2] = fmaf(hv.z, u, t4[2]); t4[3] = fmaf(hv.w, u, t4[3]);
+          t01 = f2_fma(f2_pack(hv.x, hv.y), uu, t01);
+          t23 = f2_fma(f2_pack(hv.z, hv.w), uu, t23);
         }
+        float t4[4];
+        f2_unpack(t01, t4[0], t4[1]);
+        f2_unpack(t23, t4[2], t4[3]);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           if (a0 + q < r1) T[(a0 + q) * n2p + j] = t4[q];
@@ -100,6 +104,7 @@ __global__ void __launch_bounds__(SO_THREADS) k_tucker_slab_out(
       const int rg = g / ncg, cg = g % ncg;
       const int i0 = 4 * rg, j0 = 4 * cg;
       float xv[4][4], acc[4][4];
+      uint64_t acc2[4][2];                        // columns (j0, j0 + 1), (j0 + 2, j0 + 3), packed
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i = i0 + u;
@@ -112,18 +117,24 @@ __global__ void __launch_bounds__(SO_THREADS) k_tucker_slab_out(
 #pragma unroll
           for (int v = 0; v < 4; ++v) xv[u][v] = (X && i < n1 && j0 + v < n2) ? ldx(X, dtype, e + v) : 0.f;
         }
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+        acc2[u][0] = acc2[u][1] = 0ull;
       }
       for (int a = 0; a < r1; ++a) {
         const float4 t = *reinterpret_cast<const float4*>(T + a * n2p + j0);
         const float4 uu = *reinterpret_cast<const float4*>(U1t + a * n1p + i0);
         const float ur[4] = {uu.x, uu.y, uu.z, uu.w};
-        const float tc[4] = {t.x, t.y, t.z, t.w};
+        const uint64_t t01 = f2_pack(t.x, t.y), t23 = f2_pack(t.z, t.w);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < 4; ++u) {
+          const uint64_t uw = f2_pack(ur[u], ur[u]);
+          acc2[u][0] = f2_fma(uw, t01, acc2[u][0]);
+          acc2[u][1] = f2_fma(uw, t23, acc2[u][1]);
+        }
+      }
 #pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ur[u], tc[v], acc[u][v]);
+      for (int u = 0; u < 4; ++u) {
+        f2_unpack(acc2[u][0], acc[u][0], acc[u][1]);
+        f2_unpack(acc2[u][1], acc[u][2], acc[u][3]);
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
